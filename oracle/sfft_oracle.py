@@ -1,0 +1,336 @@
+"""Plain FP64 CPU oracle of the multidimensional phase-shift sparse FFT
+(Choi, Christlieb, Wang, "High-Dimensional Sparse Fourier Algorithms").
+
+TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct reference
+that the CUDA path is checked against.  Only the tests, the smoke check and the
+CPU-baseline leg of the benchmark may import it; the library never does.  It
+shares no code with the CUDA path: its only common input is the seeded signal
+generator, which holds none of the method's arithmetic.
+
+What it computes (Algorithm 2, MultiPhaseshift, in its general form):
+
+  round i = 1, 2, ...:
+    k* = max(k - |R|, 1); p = the i-th prime >= c k*             (Alg. 2, prime choice)
+    u  = line direction of round i: the partial-unwrap vector of  (Sec. 4.1, Eq. 35-38)
+         block m = i mod B, u_l = N^r on the block's r-th digit
+    y_n[x] = (f - g)(x u / p + s_n), x = 0..p-1, n = 0..d,        (Alg. 2 sampling; Eq. 41)
+         s_0 = 0, s_n = e_n / N  (one shifted copy per coordinate)
+    Y_n = DFT_p(y_n)                                             (Eq. 3)
+    for every bin h with |Y_0[h]| above the empty-bin level:
+         accept iff | |Y_n[h]| / |Y_0[h]| - 1 | < tau for all n   (Eq. 8, Eq. 42)
+         w_n = N Arg(Y_n[h] / Y_0[h]) / (2 pi), rounded            (Eq. 7, Eq. 41 with eps = 1/N)
+         a   = Y_0[h] / p                                         (Eq. 7, Eq. 41)
+    R <- R merged with the accepted (w, a); prune small |a|       (Alg. 2 registry update)
+  until a round finds no bin above the empty-bin level (the residual is empty).
+
+Readings of the paper taken here (each is listed with its reason in the design
+notes): per-coordinate shifts e_n / N instead of eps times a block vector; the
+box [0, N)^d by default (the paper's [-N/2, N/2)^d via box_lo = -N/2); every
+occupied bin is examined instead of the k* largest after a sort; the ratio
+tolerance tau is its own parameter; an accepted vector must land in its own bin
+((w . u) mod p == h) and round to within delta of an integer; a duplicate key
+adds its coefficient to the registry entry; the empty-bin level is rho p A_ref
+with A_ref the largest first-round bin divided by p, plus 6 sigma sqrt(p) when
+the samples carry noise.
+
+Arithmetic is float64 / complex128 throughout; integer phase indices are
+reduced exactly in int64 before any floating point is applied.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# Prime schedule (Alg. 1 and Alg. 2: "p <- i-th prime number >= c k*"; c = 5, Sec. 5)
+# --------------------------------------------------------------------------
+
+
+def is_prime(n: int) -> bool:
+    """Trial division."""
+    if n < 2:
+        return False
+    if n % 2 == 0:
+        return n == 2
+    f = 3
+    while f * f <= n:
+        if n % f == 0:
+            return False
+        f += 2
+    return True
+
+
+def ith_prime_at_least(i: int, lo: int) -> int:
+    """The i-th smallest prime that is >= lo (i >= 1)."""
+    if i < 1:
+        raise ValueError("i >= 1")
+    n, count = max(lo, 2), 0
+    while True:
+        if is_prime(n):
+            count += 1
+            if count == i:
+                return n
+        n += 1
+
+
+# --------------------------------------------------------------------------
+# Line directions: partial unwrapping (Sec. 4.1, Eq. 35-38)
+# --------------------------------------------------------------------------
+
+
+def block_starts(blocks) -> list:
+    starts, s = [], 0
+    for b in blocks:
+        starts.append(s)
+        s += b
+    return starts
+
+
+def unwrap_vector(d: int, N: int, blocks, m: int) -> np.ndarray:
+    """u with u_l = N^r for coordinate l = (start of block m) + r, r = 0..d_m - 1, else 0.
+
+    Along t = x u / p the phase of mode w is x * (sum_r N^r w_{start+r}) / p, i.e. the
+    block-m coordinates unwrapped to one integer (Eq. 35) and sampled at rate 1/p."""
+    if sum(blocks) != d:
+        raise ValueError("block sizes must add up to d")
+    u = np.zeros(d, dtype=object)
+    s = block_starts(blocks)[m]
+    for r in range(blocks[m]):
+        u[s + r] = N ** r
+    return u
+
+
+def line_direction(d: int, N: int, blocks, i: int, dirs=None) -> np.ndarray:
+    """Direction of round i (1-based).  With blocks: block m = i mod B (0-based), which is
+    the paper's m <- (i mod d2) + 1 in 1-based numbering.  An explicit list of integer
+    directions (tilted lines) is used in the same rotation."""
+    if dirs is not None and len(dirs) > 0:
+        return np.array(dirs[i % len(dirs)], dtype=object)
+    return unwrap_vector(d, N, blocks, i % len(blocks))
+
+
+# --------------------------------------------------------------------------
+# Sampling of f - g along the line and its shifted copies (Alg. 2 sampling lines, Eq. 41)
+# --------------------------------------------------------------------------
+
+
+def sample_sets(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int,
+                chunk: int = 4096) -> np.ndarray:
+    """y[n, x] = sum_j coeffs_j exp(2 pi i w_j . t_{n,x}),  t_{n,x} = x u / p + s_n,
+    s_0 = 0 and s_n = e_n / N, for x = 0..p-1 and n = 0..d.
+
+    f is 1-periodic in every coordinate, so only w . t mod 1 matters.  It is reduced
+    exactly: w . (x u / p) = x (w . u) / p, whose fractional part is ((x (w . u)) mod p) / p,
+    and w . s_n = w_n / N, whose fractional part is (w_n mod N) / N.  Registry modes enter
+    with negated coefficients, so the same call evaluates f - g."""
+    freqs = np.asarray(freqs, dtype=np.int64)
+    coeffs = np.asarray(coeffs, dtype=np.complex128)
+    K, d = freqs.shape
+    y = np.zeros((d + 1, p), dtype=np.complex128)
+    if K == 0:
+        return y
+    u_mod = np.array([int(v) % p for v in u], dtype=np.int64)
+    alpha = (freqs @ u_mod) % p                       # (w . u) mod p, exact
+    shift_frac = np.mod(freqs, N) / N                 # frac(w . s_n) for n = 1..d
+    for x0 in range(0, p, chunk):
+        x = np.arange(x0, min(p, x0 + chunk), dtype=np.int64)
+        line_frac = ((alpha[:, None] * x[None, :]) % p) / p
+        for n in range(d + 1):
+            frac = line_frac if n == 0 else line_frac + shift_frac[:, n - 1][:, None]
+            y[n, x0:x0 + x.size] = coeffs @ np.exp(2j * np.pi * frac)
+    return y
+
+
+def dft(y: np.ndarray) -> np.ndarray:
+    """Y[h] = sum_x y[x] exp(-2 pi i h x / p) along the last axis (the DFT defined in Sec. 2.1)."""
+    return np.fft.fft(y, axis=-1)
+
+
+# --------------------------------------------------------------------------
+# Bin test, frequency and coefficient read-out (Eq. 7-8, Eq. 41-42)
+# --------------------------------------------------------------------------
+
+
+def arg(z: np.ndarray) -> np.ndarray:
+    """Arg in [-pi, pi) (Sec. 2.1)."""
+    a = np.angle(z)
+    return np.where(a >= np.pi, a - 2 * np.pi, a)
+
+
+@dataclass
+class Thresholds:
+    tau: float = 1e-7        # ratio-test tolerance (Eq. 8, Eq. 42)
+    rho: float = 2.0 ** -40  # empty-bin level relative to the first round's largest bin
+    delta: float = 0.1       # largest distance of N Arg / (2 pi) from an integer
+    sigma: float = 0.0       # noise level of the samples (adds 6 sigma sqrt(p) to the level)
+
+
+def classify(Y: np.ndarray, p: int, u, N: int, eta_bin: float, th: Thresholds,
+             box_lo: int = 0):
+    """All bins h = 0..p-1 that hold exactly one mode, with the mode read off.
+
+    Returns a list of (h, w, a), w a tuple of d ints, in increasing h."""
+    D = Y.shape[0] - 1
+    Y0 = Y[0]
+    occupied = np.abs(Y0) > eta_bin
+    out = []
+    u_mod = np.array([int(v) % p for v in u], dtype=np.int64)
+    for h in np.nonzero(occupied)[0]:
+        ratio = np.abs(Y[1:, h]) / np.abs(Y0[h])                    # Eq. 42, every n
+        if not np.all(np.abs(ratio - 1.0) < th.tau):
+            continue
+        v = N * arg(Y[1:, h] / Y0[h]) / (2 * np.pi)                 # Eq. 41 with eps = 1/N
+        r = np.round(v)
+        if not np.all(np.abs(v - r) <= th.delta):
+            continue
+        w = (np.mod(r.astype(np.int64) - box_lo, N) + box_lo).astype(np.int64)
+        if int(w @ u_mod) % p != h:                                  # lands in its own bin
+            continue
+        out.append((int(h), tuple(int(c) for c in w), complex(Y0[h] / p)))   # Eq. 41: a = Y_0/p
+    return out
+
+
+# --------------------------------------------------------------------------
+# Algorithm 2 driver
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class Result:
+    freqs: np.ndarray            # int64 [n, d], lexicographically sorted
+    coeffs: np.ndarray           # complex128 [n]
+    converged: bool
+    rounds: list = field(default_factory=list)   # per-round dicts
+
+    @property
+    def n_found(self) -> int:
+        return int(self.freqs.shape[0])
+
+    @property
+    def samples(self) -> int:
+        return int(sum(r["samples"] for r in self.rounds))
+
+
+def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int = 5,
+                     th: Thresholds | None = None, max_rounds: int | None = None,
+                     box_lo: int = 0, primes=None, dirs=None, noise=None) -> Result:
+    """Algorithm 2 (MultiPhaseshift) on the black box f = sum_j coeffs_j e^{2 pi i freqs_j . t}.
+
+    ``primes``, if given, overrides the prime rule (round i uses primes[i-1]).
+    ``noise``, if given, is a callable (i, p, d) -> complex array [d+1, p] added to the
+    black-box samples of round i."""
+    th = th or Thresholds()
+    freqs = np.asarray(freqs, dtype=np.int64).reshape(-1, d)
+    coeffs = np.asarray(coeffs, dtype=np.complex128).reshape(-1)
+    if blocks is None:
+        blocks = (d,)
+    if max_rounds is None:
+        max_rounds = 64 + 4 * max(1, math.ceil(math.log2(max(k, 2))))
+    R: dict = {}                       # registry: w -> a, in insertion order
+    a_ref = None
+    rounds = []
+    converged = False
+    for i in range(1, max_rounds + 1):
+        k_star = max(k - len(R), 1)
+        p = int(primes[i - 1]) if primes is not None else ith_prime_at_least(i, c * k_star)
+        u = line_direction(d, N, blocks, i, dirs)
+        # f - g: black-box modes with +a, registry modes with -a (Alg. 2: g is built from R)
+        if R:
+            reg_w = np.array(list(R.keys()), dtype=np.int64).reshape(-1, d)
+            reg_a = -np.array(list(R.values()), dtype=np.complex128)
+            all_w = np.concatenate([freqs, reg_w])
+            all_a = np.concatenate([coeffs, reg_a])
+        else:
+            all_w, all_a = freqs, coeffs
+        y = sample_sets(all_w, all_a, p, u, N)
+        if noise is not None:
+            y = y + noise(i, p, d)
+        Y = dft(y)
+        if a_ref is None:
+            a_ref = float(np.max(np.abs(Y[0]))) / p if p > 0 else 0.0
+        eta_bin = max(th.rho * p * a_ref, 6.0 * th.sigma * math.sqrt(p))
+        stat = {"round": i, "p": p, "k_star": k_star, "terms": int(all_w.shape[0]),
+                "samples": (d + 1) * p, "eta_bin": eta_bin}
+        if not np.any(np.abs(Y[0]) > eta_bin):
+            stat.update(accepted=0, registry=len(R))
+            rounds.append(stat)
+            converged = True
+            break
+        acc = classify(Y, p, u, N, eta_bin, th, box_lo)
+        for _, w, a in acc:                                    # R <- R u (w, a)
+            R[w] = R.get(w, 0j) + a
+        eta_prune = max(th.rho * a_ref, 6.0 * th.sigma / math.sqrt(p))
+        for w in [w for w, a in R.items() if abs(a) < eta_prune]:   # prune small coefficients
+            del R[w]
+        stat.update(accepted=len(acc), registry=len(R))
+        rounds.append(stat)
+    keys = sorted(R.keys())
+    out_w = np.array(keys, dtype=np.int64).reshape(-1, d)
+    out_a = np.array([R[w] for w in keys], dtype=np.complex128)
+    return Result(out_w, out_a, converged, rounds)
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1 (one-dimensional Phaseshift), kept literal as a special-case check
+# --------------------------------------------------------------------------
+
+
+def phaseshift_1d(freqs, coeffs, N: int, k: int, c: int = 5, tau: float = 1e-7,
+                  max_rounds: int = 200, rho: float = 2.0 ** -40):
+    """Alg. 1 with eps = 1/N: samples f - g at h/p and h/p + eps, FFTs both, sorts the
+    unshifted transform by magnitude, tests the k* largest bins, reads w and a (Eq. 7),
+    merges into R, prunes, repeats while |R| < k.  Frequencies are taken in [0, N)."""
+    freqs = np.asarray(freqs, dtype=np.int64).reshape(-1)
+    coeffs = np.asarray(coeffs, dtype=np.complex128).reshape(-1)
+    R: dict = {}
+    a_ref = None
+    for i in range(1, max_rounds + 1):
+        if len(R) >= k:
+            break
+        k_star = k - len(R)
+        p = ith_prime_at_least(i, c * k_star)
+        ws = np.array(list(freqs) + list(R.keys()), dtype=np.int64)
+        as_ = np.array(list(coeffs) + [-a for a in R.values()], dtype=np.complex128)
+        x = np.arange(p)
+        t0 = x / p
+        f0 = np.array([np.sum(as_ * np.exp(2j * np.pi * ws * t)) for t in t0])
+        fe = np.array([np.sum(as_ * np.exp(2j * np.pi * ws * (t + 1.0 / N))) for t in t0])
+        F0, Fe = np.fft.fft(f0), np.fft.fft(fe)
+        if a_ref is None:
+            a_ref = np.max(np.abs(F0)) / p
+        order = np.argsort(-np.abs(F0), kind="stable")             # SORT by |F_0|
+        for h in order[:k_star]:
+            if np.abs(F0[h]) <= rho * p * a_ref:
+                continue
+            if abs(np.abs(Fe[h]) / np.abs(F0[h]) - 1.0) < tau:      # Eq. 8
+                w = int(np.round(N * arg(Fe[h] / F0[h]) / (2 * np.pi))) % N   # Eq. 7
+                R[w] = R.get(w, 0j) + F0[h] / p
+        for w in [w for w, a in R.items() if abs(a) < rho * a_ref]:
+            del R[w]
+    keys = sorted(R.keys())
+    return np.array(keys, dtype=np.int64), np.array([R[w] for w in keys], dtype=np.complex128)
+
+
+# --------------------------------------------------------------------------
+# Brute-force checker: full d-dimensional DFT of the black box on its grid
+# --------------------------------------------------------------------------
+
+
+def full_grid_coefficients(freqs, coeffs, d: int, N: int, box_lo: int = 0) -> np.ndarray:
+    """Samples f on the grid t = g / N, g in [0, N)^d, and returns the d-dimensional DFT
+    divided by N^d: entry (w - box_lo) mod N holds the coefficient of frequency w.
+    Only for N^d small enough to hold in memory."""
+    freqs = np.asarray(freqs, dtype=np.int64).reshape(-1, d)
+    coeffs = np.asarray(coeffs, dtype=np.complex128)
+    grids = np.meshgrid(*[np.arange(N)] * d, indexing="ij")
+    f = np.zeros([N] * d, dtype=np.complex128)
+    for w, a in zip(freqs, coeffs):
+        ph = sum(int(w[l]) * grids[l] for l in range(d)) % N
+        f += a * np.exp(2j * np.pi * ph / N)
+    F = np.fft.fftn(f) / N ** d
+    # fftn uses e^{-2 pi i g.v/N}: the coefficient of w sits at index v = w mod N
+    if box_lo != 0:
+        F = np.roll(F, shift=[-box_lo] * d, axis=tuple(range(d)))
+    return F

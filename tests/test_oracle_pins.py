@@ -1,0 +1,319 @@
+"""Pins of the FP64 oracle to facts outside itself (CPU only).
+
+Each check ties one step of the oracle to something the paper or mathematics fixes:
+printed worked examples (tests/golden), closed forms, brute force on tiny inputs,
+a textbook routine (the full d-dimensional FFT), and invariants (Parseval).
+``test_planted_mistakes_are_caught`` plants plausible slips in the oracle and
+shows that these checks notice each one.
+"""
+from fractions import Fraction
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle.sfft_oracle as O
+from paper_1606_07407_gb300.inputs import draw_signal, Stream
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rows(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        return [ln.split() for ln in fh if ln.strip() and not ln.startswith("#")]
+
+
+def _sieve(n):
+    s = np.ones(n + 1, dtype=bool)
+    s[:2] = False
+    for q in range(2, int(n ** 0.5) + 1):
+        if s[q]:
+            s[q * q::q] = False
+    return np.nonzero(s)[0]
+
+
+# ---------------------------------------------------------------- primes
+
+def test_prime_rule_matches_sieve_and_golden():
+    pr = _sieve(600000)
+    for lo in (2, 5, 80, 997, 5000, 50000, 500000):
+        first = np.searchsorted(pr, lo)
+        for i in (1, 2, 7):
+            assert O.ith_prime_at_least(i, lo) == pr[first + i - 1]
+    for row in _rows("primes_first_round.txt"):
+        if len(row) == 3 and int(row[1]) == 5 * int(row[0]):
+            assert O.ith_prime_at_least(1, int(row[1])) == int(row[2])
+        else:
+            i, lo, p = map(int, row)
+            assert O.ith_prime_at_least(i, lo) == p
+
+
+# ---------------------------------------------------------------- directions
+
+def test_unwrap_matches_4d_example():
+    for N, m, *u in (list(map(int, r)) for r in _rows("unwrap_4d.txt")):
+        got = O.unwrap_vector(4, N, (2, 2), m)
+        assert [int(v) for v in got] == u
+
+
+def test_unwrapping_is_injective_on_a_block():
+    # Eq. 35 is one-to-one on [0, N)^{d1}: every digit vector gives a distinct integer.
+    N, d1 = 5, 3
+    u = O.unwrap_vector(d1, N, (d1,), 0)
+    vals = {int(np.dot(w, u)) for w in np.ndindex(*([N] * d1))}
+    assert len(vals) == N ** d1 and min(vals) == 0 and max(vals) == N ** d1 - 1
+
+
+# ---------------------------------------------------------------- sampling
+
+def _check_samples_against_rationals(sample_fn):
+    rng = Stream(11)
+    d, N, p = 3, 8, 7
+    freqs = rng.integers(4 * d, 0, N).reshape(4, d)
+    coeffs = rng.uniform(4) + 1j * rng.uniform(4)
+    u = [1, N, 0]
+    y = sample_fn(freqs, coeffs, p, u, N)
+    for n in range(d + 1):
+        for x in range(p):
+            t = [Fraction(x * u[l], p) + (Fraction(1, N) if l == n - 1 else 0) for l in range(d)]
+            want = 0j
+            for w, a in zip(freqs, coeffs):
+                ph = sum(int(w[l]) * t[l] for l in range(d))
+                ph -= math.floor(ph)
+                want += a * complex(math.cos(2 * math.pi * ph), math.sin(2 * math.pi * ph))
+            assert abs(y[n, x] - want) < 1e-12
+
+
+def test_samples_equal_exact_rational_evaluation():
+    _check_samples_against_rationals(O.sample_sets)
+
+
+def test_samples_equal_direct_real_point_evaluation():
+    # f evaluated at the real point t = x u / p + s_n without any reduction (small numbers).
+    sig = draw_signal(2, 16, 5, seed=3)
+    p, u = 11, [1, 16]
+    y = O.sample_sets(sig.freqs, sig.coeffs, p, u, 16)
+    for n in range(3):
+        for x in range(p):
+            t = np.array([x * u[0] / p, x * u[1] / p]) + (np.eye(2)[n - 1] / 16 if n else 0)
+            f = np.sum(sig.coeffs * np.exp(2j * np.pi * (sig.freqs @ t)))
+            assert abs(y[n, x] - f) < 1e-11
+
+
+# ---------------------------------------------------------------- DFT
+
+def test_dft_equals_definition():
+    for p in (2, 3, 5, 13, 61):
+        rng = Stream(p)
+        y = rng.uniform(3 * p).reshape(3, p) + 1j * rng.uniform(3 * p).reshape(3, p)
+        F = np.array([[sum(y[r, x] * complex(math.cos(-2 * math.pi * h * x / p),
+                                              math.sin(-2 * math.pi * h * x / p))
+                            for x in range(p)) for h in range(p)] for r in range(3)])
+        assert np.max(np.abs(O.dft(y) - F)) < 1e-11
+
+
+def _check_single_mode_closed_form(sample_fn, dft_fn):
+    # Eq. 3-5 and Eq. 41: one mode gives a single occupied bin h = (w . u) mod p holding
+    # p a, and Y_n / Y_0 = exp(2 pi i w_n / N) there.
+    d, N, p = 4, 1024, 83
+    w = np.array([[700, 13, 1000, 512]])
+    a = np.array([1.5 - 0.25j])
+    u = [1, N, 0, 0]
+    h = (700 + 13 * N) % p
+    Y = dft_fn(sample_fn(w, a, p, u, N))
+    assert abs(Y[0, h] - p * a[0]) < 1e-9
+    Y0 = Y[0].copy()
+    Y0[h] = 0
+    assert np.max(np.abs(Y0)) < 1e-9
+    for n in range(1, d + 1):
+        assert abs(Y[n, h] / Y[0, h] - np.exp(2j * np.pi * w[0, n - 1] / N)) < 1e-12
+
+
+def test_single_mode_closed_form():
+    _check_single_mode_closed_form(O.sample_sets, O.dft)
+
+
+def test_parseval_on_samples():
+    sig = draw_signal(3, 256, 40, seed=5)
+    y = O.sample_sets(sig.freqs, sig.coeffs, 211, [1, 256, 0], 256)
+    Y = O.dft(y)
+    lhs = np.sum(np.abs(y) ** 2, axis=1)
+    rhs = np.sum(np.abs(Y) ** 2, axis=1) / 211
+    assert np.allclose(lhs, rhs, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- bin test and decode
+
+def _check_collision_rejected(classify_fn):
+    # Two modes in one bin that differ in coordinate 2 only: Eq. 42 fails for n = 2 and the
+    # bin is rejected.  A lone mode in another bin is read off exactly.
+    d, N, p = 3, 64, 31
+    u = [1, 0, 0]
+    w = np.array([[5, 10, 7], [5, 40, 7], [20, 3, 60]])
+    a = np.array([1.0 + 0.2j, 0.8 - 0.5j, -1.1 + 0.3j])
+    Y = O.dft(O.sample_sets(w, a, p, u, N))
+    acc = classify_fn(Y, p, u, N, 1e-6, O.Thresholds())
+    assert [(h, wv) for h, wv, _ in acc] == [(20, (20, 3, 60))]
+    assert abs(acc[0][2] - a[2]) < 1e-12
+
+
+def test_collision_is_rejected_and_lone_mode_read_off():
+    _check_collision_rejected(O.classify)
+
+
+def test_arg_range_is_half_open():
+    z = np.array([-1 + 0j, -1 - 1e-300j, 1j, -1j])
+    a = O.arg(z)
+    assert np.all(a >= -np.pi) and np.all(a < np.pi)
+    assert a[0] == -np.pi
+
+
+# ---------------------------------------------------------------- whole loop
+
+def _recover(sig, blocks, **kw):
+    return O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, blocks,
+                              box_lo=sig.box_lo, **kw)
+
+
+def _assert_exact(res, sig, tol):
+    order = np.lexsort(sig.freqs.T[::-1])
+    assert res.converged
+    assert np.array_equal(res.freqs, sig.freqs[order].astype(np.int64))
+    rel = np.abs(res.coeffs - sig.coeffs[order]) / np.abs(sig.coeffs[order])
+    assert np.max(rel) < tol
+
+
+def _check_full_grid(recover_fn):
+    # The textbook d-dimensional FFT of f on its full grid is the ground truth.
+    for d, N, k, seed in ((2, 32, 8, 1), (3, 16, 12, 2), (2, 64, 30, 3)):
+        sig = draw_signal(d, N, k, seed=seed)
+        F = O.full_grid_coefficients(sig.freqs, sig.coeffs, d, N)
+        support = np.argwhere(np.abs(F) > 1e-9)
+        res = recover_fn(sig)
+        assert res.converged
+        assert np.array_equal(res.freqs, support)          # argwhere is lexicographic
+        assert np.max(np.abs(res.coeffs - F[tuple(support.T)])) < 1e-12
+
+
+def test_recovery_equals_full_grid_fft():
+    _check_full_grid(lambda s: _recover(s, (1,) * s.d))
+
+
+def test_recovery_equals_full_grid_fft_signed_box():
+    sig = draw_signal(2, 32, 10, seed=9, box_lo=-16)
+    F = O.full_grid_coefficients(sig.freqs, sig.coeffs, 2, 32, box_lo=-16)
+    support = np.argwhere(np.abs(F) > 1e-9) - 16
+    res = _recover(sig, (1, 1))
+    assert np.array_equal(res.freqs, support)
+
+
+def test_workload_d2_recovers_planted_set():
+    sig = draw_signal(2, 1024, 16, seed=1606074071, r_lo=1.0, r_hi=2.0)
+    res = _recover(sig, (1, 1))
+    _assert_exact(res, sig, 1e-12)
+    assert res.rounds[0]["p"] == 83
+
+
+def test_d5_full_unwrap_and_partial_unwrap():
+    sig = draw_signal(5, 1024, 200, seed=77, r_lo=1, r_hi=10)
+    _assert_exact(_recover(sig, (3, 2)), sig, 1e-12)
+    _assert_exact(_recover(sig, (5,)), sig, 1e-12)
+
+
+def test_d1_general_form_equals_algorithm_1():
+    sig = draw_signal(1, 4096, 40, seed=4)
+    w1, a1 = O.phaseshift_1d(sig.freqs[:, 0], sig.coeffs, 4096, 40)
+    res = _recover(sig, (1,))
+    assert np.array_equal(res.freqs[:, 0], w1)
+    # Alg. 1 as printed evaluates f at the unreduced real point t, whose phase 2 pi w t
+    # reaches 2 pi N: its double rounding is about N * 2 pi * 2^-53 ~ 3e-12 per term.
+    assert np.max(np.abs(res.coeffs - a1)) < 1e-10
+    _assert_exact(res, sig, 1e-12)
+
+
+def test_4d_two_by_two_example():
+    sig = draw_signal(4, 32, 60, seed=8)
+    _assert_exact(_recover(sig, (2, 2)), sig, 1e-12)
+
+
+def test_fig2_collision_story():
+    rows = _rows("fig2_collisions.txt")
+    w = np.array([[int(r[1]), int(r[2])] for r in rows])
+    a = np.array([float(r[3]) + 1j * float(r[4]) for r in rows])
+    # round i uses dirs[i mod 2]: round 1 projects on the horizontal axis, round 2 on the vertical.
+    res = O.multi_phaseshift(w, a, 2, 16, 3, dirs=[[0, 1], [1, 0]], primes=[17, 17, 17, 17])
+    assert res.rounds[0]["accepted"] == 1 and res.rounds[0]["registry"] == 1
+    assert res.rounds[1]["accepted"] == 2 and res.rounds[1]["registry"] == 3
+    assert res.converged and res.n_found == 3
+
+
+def test_paper_workload_shape_error_below_claim():
+    # Sec. 5 / Sec. 5.1: d = 100, d1 = 5, d2 = 20, N = 20, |a_j| = 1, box [-N/2, N/2)^d;
+    # frequencies exact and the l2 coefficient error at double round-off (the paper reports
+    # an average below 2^-52; a few ulps per coefficient are allowed here).
+    for k, seed in ((1, 1), (4, 2), (16, 3)):
+        sig = draw_signal(100, 20, k, seed=seed, box_lo=-10, unit_modulus=True)
+        res = _recover(sig, (5,) * 20)
+        order = np.lexsort(sig.freqs.T[::-1])
+        assert np.array_equal(res.freqs, sig.freqs[order].astype(np.int64))
+        err = np.linalg.norm(res.coeffs - sig.coeffs[order])
+        assert err < 16 * 2.0 ** -52 * math.sqrt(k)
+
+
+def test_sample_count_grows_like_d_times_k():
+    # Theorem 3: E[S(k)] = Theta(d k).  Samples / (d k) stays in a narrow band.
+    ratios = []
+    for d, k in ((2, 8), (2, 64), (4, 64), (4, 256)):
+        sig = draw_signal(d, 1 << 12, k, seed=d * 1000 + k)
+        res = _recover(sig, (1,) * d if d == 2 else (2, 2))
+        ratios.append(res.samples / ((d + 1) * k))
+    assert max(ratios) / min(ratios) < 4.0 and min(ratios) > 5.0
+
+
+# ---------------------------------------------------------------- the pins catch slips
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Plant plausible mistakes in the oracle and check that some pin fails for each."""
+    real_sample = O.sample_sets
+    real_classify = O.classify
+
+    def wrong_sign(freqs, coeffs, p, u, N):      # e^{-2 pi i ...} in the black box
+        return np.conj(real_sample(freqs, np.conj(coeffs), p, u, N))
+
+    def dropped_shift(freqs, coeffs, p, u, N):   # the shift term w_n / N left out
+        y = real_sample(freqs, coeffs, p, u, N)
+        y[1:] = y[0]
+        return y
+
+    def transposed_u(freqs, coeffs, p, u, N):    # direction applied to the wrong coordinates
+        return real_sample(freqs, coeffs, p, list(u)[::-1], N)
+
+    def off_by_one_shift(freqs, coeffs, p, u, N):   # shift along e_{n+1} instead of e_n
+        y = real_sample(freqs, coeffs, p, u, N)
+        return np.concatenate([y[:1], np.roll(y[1:], 1, axis=0)])
+
+    for bad in (wrong_sign, dropped_shift, transposed_u, off_by_one_shift):
+        with pytest.raises(AssertionError):
+            _check_samples_against_rationals(bad)
+        with pytest.raises(AssertionError):
+            _check_single_mode_closed_form(bad, O.dft)
+
+    def ratio_inverted(Y, p, u, N, eta, th, box_lo=0):   # Arg of Y_0 / Y_n (sign slip)
+        return real_classify(np.concatenate([Y[:1], np.conj(Y[1:]) * (Y[:1] / np.conj(Y[:1]))]),
+                             p, u, N, eta, th, box_lo)
+
+    def no_ratio_test(Y, p, u, N, eta, th, box_lo=0):
+        return real_classify(Y, p, u, N, eta, O.Thresholds(tau=1e9, delta=0.5), box_lo)
+
+    for bad in (ratio_inverted, no_ratio_test):
+        with pytest.raises(AssertionError):
+            _check_collision_rejected(bad)
+
+    def coeff_conj(sig):                           # a = conj(Y_0)/p
+        res = _recover(sig, (1,) * sig.d)
+        res.coeffs = np.conj(res.coeffs)
+        return res
+
+    with pytest.raises(AssertionError):
+        _check_full_grid(coeff_conj)
