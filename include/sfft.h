@@ -1,0 +1,173 @@
+/*
+ * sfft.h — C ABI of the GB300 multidimensional phase-shift sparse FFT.
+ *
+ * The library recovers the k integer frequency vectors w_j in a box of side N
+ * and the complex coefficients a_j of a d-variate black-box signal
+ *     f(t) = sum_j a_j exp(2 pi i w_j . t)                 (Sec. 2.2, Eq. 9; Eq. 32)
+ * by Algorithm 2 (MultiPhaseshift) in its general form.  Each round samples
+ * f - g along a line t = x u / p (u an integer direction, p prime, x = 0..p-1)
+ * and along its copies shifted by e_n / N, n = 1..d (Eq. 41), takes the length-p
+ * DFTs of the d + 1 sample sets (Eq. 3), keeps the bins that pass the ratio test
+ * for every n (Eq. 42), reads each coordinate off the phase of Y_n / Y_0 and the
+ * coefficient off Y_0 / p (Eq. 41), and merges the result into the registry R
+ * whose model g is subtracted in the next round.
+ *
+ * Conventions for every call:
+ *  - Arguments named *_dev are device pointers (any allocator); the caller owns
+ *    them and keeps them valid until the call returns.  Other pointers are host.
+ *  - Complex numbers are interleaved (re, im).  "complex128" is two doubles,
+ *    "complex64" two floats.  Frequencies are int32, row-major [count x d].
+ *  - Every call returns an sfft_status; no call throws or aborts.  After
+ *    SFFT_ERR_CUDA, sfft_last_cuda_error() returns the cudaError_t value.
+ *  - All work is issued on the plan's stream; calls that return host-visible
+ *    results (counts, stats) synchronise that stream before returning.
+ *  - A plan is not thread-safe: one call at a time per plan.
+ */
+#ifndef SFFT_H_
+#define SFFT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SFFT_OK = 0,
+  SFFT_ERR_INVALID_ARG = 1,   /* a size, pointer or option is out of range            */
+  SFFT_ERR_NOT_CONVERGED = 2, /* max_rounds reached with bins still occupied           */
+  SFFT_ERR_CAPACITY = 3,      /* an output, registry or scratch capacity was exceeded   */
+  SFFT_ERR_PRECISION = 4,     /* the requested N is beyond the policy's phase resolution */
+  SFFT_ERR_INCONSISTENT = 5,  /* converged with more than k modes in the registry       */
+  SFFT_ERR_CUDA = 6,          /* a CUDA runtime call failed (see sfft_last_cuda_error)  */
+  SFFT_ERR_TIMEOUT = 7        /* a bounded device-side wait ran out                     */
+} sfft_status;
+
+/* Arithmetic of the hot path.  FP32 bulk: sampling and DFT in float, the phase
+ * ratio, the frequency read-out and the coefficient estimate in double.  FP64:
+ * every step in double. */
+typedef enum {
+  SFFT_PREC_FP32_FP64RATIO = 0,
+  SFFT_PREC_FP32 = 1,
+  SFFT_PREC_FP64 = 2
+} sfft_precision;
+
+typedef struct sfft_plan_s* sfft_plan;
+typedef struct sfft_signal_s* sfft_signal;
+
+/* Prime schedule (Alg. 1 and Alg. 2: p = i-th prime >= c k*, c = 5 in Sec. 5).
+ * primes != NULL overrides the rule: round i uses primes[(i-1) mod n_primes]. */
+typedef struct {
+  int c_prime;            /* c; 0 means 5 */
+  int n_primes;
+  const int64_t* primes;  /* host, n_primes entries, each prime and >= 5 */
+} sfft_pschedule;
+
+/* Line directions (Sec. 3.2, 3.3, 4.1).  Either n_dirs explicit integer
+ * directions (tilted lines), row-major [n_dirs x d], or partial unwrapping:
+ * n_blocks blocks of the coordinates, block q covering block_sizes[q]
+ * consecutive coordinates, whose direction has N^r on the block's r-th
+ * coordinate (Eq. 35-38).  Round i uses direction / block (i mod count), the
+ * paper's m = (i mod d2) + 1 in 1-based numbering.  Both empty means one block
+ * per the default rule: the smallest b with N^b >= 4 c k, d / b blocks. */
+typedef struct {
+  int n_dirs;
+  const int64_t* dirs;      /* host */
+  int n_blocks;
+  const int* block_sizes;   /* host */
+} sfft_tilts;
+
+typedef struct {
+  int precision;     /* sfft_precision */
+  int box_lo;        /* 0: frequencies in [0, N); -N/2: the paper's [-N/2, N/2) */
+  double tau;        /* ratio-test tolerance (Eq. 8, 42); 0 = policy default      */
+  double rho;        /* empty-bin level / (p * first-round largest bin / p); 0 = default */
+  double delta;      /* max distance of N Arg/(2 pi) from an integer; 0 = default */
+  double noise_sigma;/* known noise level of the samples; adds 6 sigma sqrt(p)   */
+  int max_rounds;    /* 0 = 64 + 4 ceil(log2 k)                                   */
+} sfft_opts;
+
+#define SFFT_STATS_MAX_ROUNDS 256
+typedef struct {
+  int rounds;                     /* rounds run, including the final empty one  */
+  int converged;                  /* 1 when the last round found no occupied bin */
+  int64_t samples;                /* black-box samples, sum over rounds of (d+1) p */
+  int64_t terms;                  /* sample terms, sum over rounds of (d+1) p K */
+  int64_t p[SFFT_STATS_MAX_ROUNDS];
+  int32_t K[SFFT_STATS_MAX_ROUNDS];        /* modes evaluated per sample (k + |R|) */
+  int32_t accepted[SFFT_STATS_MAX_ROUNDS]; /* bins accepted in the round */
+  int32_t registry[SFFT_STATS_MAX_ROUNDS]; /* live registry entries after the round */
+} sfft_stats;
+
+/* Create a plan for signals of dimension d, box side N and sparsity k.
+ * Allocates every device buffer the hot path needs for any round (sized by k,
+ * d and the largest prime the schedule can reach); nothing is allocated
+ * during execute.  stream: a cudaStream_t, or NULL for the default stream.
+ * pschedule, tilts, opts may be NULL (defaults).  Errors: INVALID_ARG for
+ * d < 1, N < 2, k < 0, N^? direction overflow or bad options; PRECISION when
+ * N exceeds 2^24 under an FP32 policy; CUDA when an allocation fails. */
+sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* pschedule,
+                             const sfft_tilts* tilts, const sfft_opts* opts, void* stream,
+                             sfft_plan* plan_out);
+void sfft_plan_destroy(sfft_plan plan);
+
+/* A synthetic black box f(t) = sum_j coeffs_j exp(2 pi i freqs_j . t) with k
+ * modes.  freqs_dev: int32 [k x d] device; coeffs_dev: complex128 [k] device.
+ * Both are copied; the handle owns its copy until sfft_signal_destroy.
+ * noise_sigma > 0 is reserved (INVALID_ARG for now). */
+sfft_status sfft_signal_synthetic(int d, int64_t N, int64_t k, const int32_t* freqs_dev,
+                                  const double* coeffs_dev, double noise_sigma,
+                                  uint64_t noise_seed, sfft_signal* signal_out);
+void sfft_signal_destroy(sfft_signal signal);
+
+/* Run Algorithm 2 on the signal until a round finds no occupied bin.
+ * Writes the live registry (unordered) to freqs_out_dev (int32 [capacity x d])
+ * and coeffs_out_dev (complex128 [capacity]); *n_found = number of entries.
+ * stats may be NULL.  Returns NOT_CONVERGED after max_rounds (outputs still
+ * written), CAPACITY if more than capacity entries are live (nothing written
+ * beyond capacity), INCONSISTENT if more than k entries are live at the end. */
+sfft_status sfft_execute(sfft_plan plan, sfft_signal signal, int64_t capacity,
+                         int32_t* freqs_out_dev, double* coeffs_out_dev, int64_t* n_found,
+                         sfft_stats* stats);
+
+/* ---- the steps of one round, callable on their own ------------------------ */
+
+/* Kernel (a), sample-and-residual (Alg. 2 sampling; Eq. 41): for the K modes
+ * (freqs_dev int32 [K x d], coeffs_dev complex128 [K]) writes
+ *     y[n][x] = sum_j coeffs_j exp(2 pi i w_j . (x u / p + s_n)),
+ * s_0 = 0, s_n = e_n / N, x < p, n <= d, to y_out_dev, row-major [(d+1) x p],
+ * complex64 for FP32 plans and complex128 for FP64 plans.  u: host int64 [d].
+ * Requires 5 <= p <= the plan's largest prime and K <= the plan's mode capacity. */
+sfft_status sfft_sample(sfft_plan plan, int64_t p, const int64_t* u, int64_t K,
+                        const int32_t* freqs_dev, const double* coeffs_dev, void* y_out_dev);
+
+/* Kernel (b), batched prime-length DFT (Eq. 3): Y[r][h] = sum_x y[r][x]
+ * exp(-2 pi i h x / p) for rows r < n_rows, h < p.  y_dev and Y_out_dev are
+ * [n_rows x p] in the plan's complex type; n_rows <= d + 1. */
+sfft_status sfft_dft(sfft_plan plan, int64_t p, int n_rows, const void* y_dev, void* Y_out_dev);
+
+/* Kernel (c), bin classification and read-out (Eq. 41-42): for the (d+1) x p
+ * transforms Y_dev (plan's complex type) of the line with direction u (host
+ * int64 [d]) returns every bin h with |Y_0[h]| > eta_bin that passes the ratio
+ * test for all n, whose read-out rounds to integers within delta and lands in
+ * its own bin.  Outputs (device): h_out int32 [capacity], freqs_out int32
+ * [capacity x d], coeffs_out complex128 [capacity] (a = Y_0[h] / p);
+ * *n_out = count (order unspecified).  CAPACITY if more bins pass than fit. */
+sfft_status sfft_classify(sfft_plan plan, int64_t p, const int64_t* u, const void* Y_dev,
+                          double eta_bin, int64_t capacity, int32_t* h_out_dev,
+                          int32_t* freqs_out_dev, double* coeffs_out_dev, int64_t* n_out);
+
+/* Plan facts: largest prime any round can use, mode capacity (k + registry),
+ * bytes of device memory the plan holds. */
+int64_t sfft_plan_max_prime(sfft_plan plan);
+int64_t sfft_plan_mode_capacity(sfft_plan plan);
+int64_t sfft_plan_device_bytes(sfft_plan plan);
+
+/* The last cudaError_t seen by any call of this thread (0 if none). */
+int sfft_last_cuda_error(void);
+const char* sfft_status_string(sfft_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFFT_H_ */

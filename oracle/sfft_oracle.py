@@ -117,25 +117,27 @@ def line_direction(d: int, N: int, blocks, i: int, dirs=None) -> np.ndarray:
 
 
 def sample_sets(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int,
-                chunk: int = 4096) -> np.ndarray:
+                chunk: int = 4096, x_values=None) -> np.ndarray:
     """y[n, x] = sum_j coeffs_j exp(2 pi i w_j . t_{n,x}),  t_{n,x} = x u / p + s_n,
     s_0 = 0 and s_n = e_n / N, for x = 0..p-1 and n = 0..d.
 
     f is 1-periodic in every coordinate, so only w . t mod 1 matters.  It is reduced
     exactly: w . (x u / p) = x (w . u) / p, whose fractional part is ((x (w . u)) mod p) / p,
     and w . s_n = w_n / N, whose fractional part is (w_n mod N) / N.  Registry modes enter
-    with negated coefficients, so the same call evaluates f - g."""
+    with negated coefficients, so the same call evaluates f - g.  ``x_values``, if given,
+    restricts the evaluation to those sample indices (columns in the given order)."""
     freqs = np.asarray(freqs, dtype=np.int64)
     coeffs = np.asarray(coeffs, dtype=np.complex128)
     K, d = freqs.shape
-    y = np.zeros((d + 1, p), dtype=np.complex128)
+    xs = np.arange(p, dtype=np.int64) if x_values is None else np.asarray(x_values, dtype=np.int64)
+    y = np.zeros((d + 1, xs.size), dtype=np.complex128)
     if K == 0:
         return y
     u_mod = np.array([int(v) % p for v in u], dtype=np.int64)
     alpha = (freqs @ u_mod) % p                       # (w . u) mod p, exact
     shift_frac = np.mod(freqs, N) / N                 # frac(w . s_n) for n = 1..d
-    for x0 in range(0, p, chunk):
-        x = np.arange(x0, min(p, x0 + chunk), dtype=np.int64)
+    for x0 in range(0, xs.size, chunk):
+        x = xs[x0:x0 + chunk]
         line_frac = ((alpha[:, None] * x[None, :]) % p) / p
         for n in range(d + 1):
             frac = line_frac if n == 0 else line_frac + shift_frac[:, n - 1][:, None]
@@ -218,7 +220,7 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
                      box_lo: int = 0, primes=None, dirs=None, noise=None) -> Result:
     """Algorithm 2 (MultiPhaseshift) on the black box f = sum_j coeffs_j e^{2 pi i freqs_j . t}.
 
-    ``primes``, if given, overrides the prime rule (round i uses primes[i-1]).
+    ``primes``, if given, overrides the prime rule (round i uses primes[(i-1) mod len]).
     ``noise``, if given, is a callable (i, p, d) -> complex array [d+1, p] added to the
     black-box samples of round i."""
     th = th or Thresholds()
@@ -234,7 +236,8 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
     converged = False
     for i in range(1, max_rounds + 1):
         k_star = max(k - len(R), 1)
-        p = int(primes[i - 1]) if primes is not None else ith_prime_at_least(i, c * k_star)
+        p = (int(primes[(i - 1) % len(primes)]) if primes is not None
+             else ith_prime_at_least(i, c * k_star))
         u = line_direction(d, N, blocks, i, dirs)
         # f - g: black-box modes with +a, registry modes with -a (Alg. 2: g is built from R)
         if R:

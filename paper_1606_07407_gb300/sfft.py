@@ -1,0 +1,250 @@
+"""Python binding of the C ABI in include/sfft.h (argument marshalling only).
+
+Every call goes to libsfft.so; nothing here computes any step of the method.
+Device buffers are torch CUDA tensors; the plan runs on torch's current CUDA
+stream unless another stream is given.  Import fails loudly when the library
+has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+PREC = {"fp32": 0, "fp32_fp64ratio": 0, "fp32_only": 1, "fp64": 2}
+STATUS = {0: "ok", 1: "invalid argument", 2: "not converged", 3: "capacity exceeded",
+          4: "beyond phase resolution", 5: "more modes than k", 6: "cuda error", 7: "device wait timed out"}
+MAX_ROUNDS = 256
+
+
+class SfftError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+class _PSchedule(C.Structure):
+    _fields_ = [("c_prime", C.c_int), ("n_primes", C.c_int), ("primes", C.POINTER(C.c_int64))]
+
+
+class _Tilts(C.Structure):
+    _fields_ = [("n_dirs", C.c_int), ("dirs", C.POINTER(C.c_int64)), ("n_blocks", C.c_int),
+                ("block_sizes", C.POINTER(C.c_int))]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("box_lo", C.c_int), ("tau", C.c_double), ("rho", C.c_double),
+                ("delta", C.c_double), ("noise_sigma", C.c_double), ("max_rounds", C.c_int)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("rounds", C.c_int), ("converged", C.c_int), ("samples", C.c_int64), ("terms", C.c_int64),
+                ("p", C.c_int64 * MAX_ROUNDS), ("K", C.c_int32 * MAX_ROUNDS),
+                ("accepted", C.c_int32 * MAX_ROUNDS), ("registry", C.c_int32 * MAX_ROUNDS)]
+
+
+EXPORTS = ["sfft_plan_create", "sfft_plan_destroy", "sfft_signal_synthetic", "sfft_signal_destroy",
+           "sfft_execute", "sfft_sample", "sfft_dft", "sfft_classify", "sfft_plan_max_prime",
+           "sfft_plan_mode_capacity", "sfft_plan_device_bytes", "sfft_last_cuda_error", "sfft_status_string"]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Loads libsfft.so (built by paper_1606_07407_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsfft.so not built ({path}); run paper_1606_07407_gb300.build.build()")
+    L = C.CDLL(path)
+    vp, i64, i32p, dp = C.c_void_p, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double)
+    L.sfft_plan_create.argtypes = [C.c_int, i64, i64, C.POINTER(_PSchedule), C.POINTER(_Tilts), C.POINTER(_Opts),
+                                   vp, C.POINTER(vp)]
+    L.sfft_plan_create.restype = C.c_int
+    L.sfft_plan_destroy.argtypes = [vp]
+    L.sfft_plan_destroy.restype = None
+    L.sfft_signal_synthetic.argtypes = [C.c_int, i64, i64, vp, vp, C.c_double, C.c_uint64, C.POINTER(vp)]
+    L.sfft_signal_synthetic.restype = C.c_int
+    L.sfft_signal_destroy.argtypes = [vp]
+    L.sfft_signal_destroy.restype = None
+    L.sfft_execute.argtypes = [vp, vp, i64, vp, vp, C.POINTER(i64), C.POINTER(_Stats)]
+    L.sfft_execute.restype = C.c_int
+    L.sfft_sample.argtypes = [vp, i64, C.POINTER(i64), i64, vp, vp, vp]
+    L.sfft_sample.restype = C.c_int
+    L.sfft_dft.argtypes = [vp, i64, C.c_int, vp, vp]
+    L.sfft_dft.restype = C.c_int
+    L.sfft_classify.argtypes = [vp, i64, C.POINTER(i64), vp, C.c_double, i64, vp, vp, vp, C.POINTER(i64)]
+    L.sfft_classify.restype = C.c_int
+    for f in ("sfft_plan_max_prime", "sfft_plan_mode_capacity", "sfft_plan_device_bytes"):
+        getattr(L, f).argtypes = [vp]
+        getattr(L, f).restype = i64
+    L.sfft_last_cuda_error.argtypes = []
+    L.sfft_last_cuda_error.restype = C.c_int
+    L.sfft_status_string.argtypes = [C.c_int]
+    L.sfft_status_string.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(st: int, what: str, ok=(0,)):
+    if st not in ok:
+        if st == 6:
+            what += f" (cudaError {load().sfft_last_cuda_error()})"
+        raise SfftError(st, what)
+    return st
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _i64_array(vals):
+    arr = (C.c_int64 * len(vals))(*[int(v) for v in vals])
+    return arr
+
+
+class Signal:
+    """Synthetic black box f(t) = sum_j coeffs_j e^{2 pi i freqs_j . t} held on the device."""
+
+    def __init__(self, freqs, coeffs, N: int):
+        L = load()
+        freqs = torch.as_tensor(np.asarray(freqs) if not torch.is_tensor(freqs) else freqs)
+        coeffs = torch.as_tensor(np.asarray(coeffs) if not torch.is_tensor(coeffs) else coeffs)
+        self.k, self.d = int(freqs.shape[0]), int(freqs.shape[1])
+        self.N = int(N)
+        fw = freqs.to(device="cuda", dtype=torch.int32).contiguous()
+        ca = coeffs.to(device="cuda", dtype=torch.complex128).contiguous()
+        h = C.c_void_p()
+        _check(L.sfft_signal_synthetic(self.d, self.N, self.k, _ptr(fw), _ptr(ca), 0.0, 0, C.byref(h)),
+               "sfft_signal_synthetic")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sfft_signal_destroy(h)
+            self._h = None
+
+
+class Plan:
+    """An sfft plan: d, N, k, prime schedule, line directions and precision policy."""
+
+    def __init__(self, d: int, N: int, k: int, blocks=None, dirs=None, primes=None, c: int = 5,
+                 precision: str = "fp32", box_lo: int = 0, tau: float = 0.0, rho: float = 0.0,
+                 delta: float = 0.0, noise_sigma: float = 0.0, max_rounds: int = 0, stream=None):
+        L = load()
+        self.d, self.N, self.k = int(d), int(N), int(k)
+        self.precision = precision
+        self.cdtype = torch.complex128 if precision == "fp64" else torch.complex64
+        self._keep = []
+        ps = _PSchedule(int(c), 0, None)
+        if primes is not None and len(primes):
+            arr = _i64_array(primes)
+            self._keep.append(arr)
+            ps.n_primes, ps.primes = len(primes), arr
+        tl = _Tilts(0, None, 0, None)
+        if dirs is not None and len(dirs):
+            flat = [int(v) for row in dirs for v in row]
+            arr = _i64_array(flat)
+            self._keep.append(arr)
+            tl.n_dirs, tl.dirs = len(dirs), arr
+        elif blocks is not None:
+            arr = (C.c_int * len(blocks))(*[int(b) for b in blocks])
+            self._keep.append(arr)
+            tl.n_blocks, tl.block_sizes = len(blocks), arr
+        op = _Opts(PREC[precision], int(box_lo), float(tau), float(rho), float(delta), float(noise_sigma),
+                   int(max_rounds))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        _check(L.sfft_plan_create(self.d, self.N, self.k, C.byref(ps), C.byref(tl), C.byref(op),
+                                  C.c_void_p(stream.cuda_stream), C.byref(h)), "sfft_plan_create")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sfft_plan_destroy(h)
+            self._h = None
+
+    @property
+    def max_prime(self) -> int:
+        return int(load().sfft_plan_max_prime(self._h))
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load().sfft_plan_device_bytes(self._h))
+
+    def execute(self, signal: Signal, capacity: int | None = None, out=None, allow=(0,)):
+        """Runs Algorithm 2; returns (freqs int32 [n, d], coeffs complex128 [n], status, stats) on the device."""
+        L = load()
+        cap = int(capacity if capacity is not None else max(2 * self.k + 16, 16))
+        if out is None:
+            fo = torch.empty((cap, self.d), dtype=torch.int32, device="cuda")
+            co = torch.empty((cap,), dtype=torch.complex128, device="cuda")
+        else:
+            fo, co = out
+        n = C.c_int64(0)
+        st = _Stats()
+        status = L.sfft_execute(self._h, signal._h, cap, _ptr(fo), _ptr(co), C.byref(n), C.byref(st))
+        _check(status, "sfft_execute", ok=allow)
+        m = min(int(n.value), cap)
+        r = st.rounds
+        stats = {"rounds": r, "converged": bool(st.converged), "samples": int(st.samples),
+                 "terms": int(st.terms), "p": list(st.p[:r]), "K": list(st.K[:r]),
+                 "accepted": list(st.accepted[:r]), "registry": list(st.registry[:r])}
+        return fo[:m], co[:m], status, stats
+
+    def sample(self, p: int, u, freqs: torch.Tensor, coeffs: torch.Tensor) -> torch.Tensor:
+        L = load()
+        fw = freqs.to(device="cuda", dtype=torch.int32).contiguous()
+        ca = coeffs.to(device="cuda", dtype=torch.complex128).contiguous()
+        y = torch.empty((self.d + 1, int(p)), dtype=self.cdtype, device="cuda")
+        ua = _i64_array(u)
+        _check(L.sfft_sample(self._h, int(p), ua, int(fw.shape[0]), _ptr(fw), _ptr(ca), _ptr(y)), "sfft_sample")
+        return y
+
+    def dft(self, p: int, y: torch.Tensor) -> torch.Tensor:
+        L = load()
+        y = y.to(device="cuda", dtype=self.cdtype).contiguous()
+        Y = torch.empty_like(y)
+        _check(L.sfft_dft(self._h, int(p), int(y.shape[0]), _ptr(y), _ptr(Y)), "sfft_dft")
+        return Y
+
+    def classify(self, p: int, u, Y: torch.Tensor, eta_bin: float, capacity: int | None = None):
+        L = load()
+        Y = Y.to(device="cuda", dtype=self.cdtype).contiguous()
+        cap = int(capacity if capacity is not None else p)
+        h = torch.empty((max(cap, 1),), dtype=torch.int32, device="cuda")
+        w = torch.empty((max(cap, 1), self.d), dtype=torch.int32, device="cuda")
+        a = torch.empty((max(cap, 1),), dtype=torch.complex128, device="cuda")
+        n = C.c_int64(0)
+        ua = _i64_array(u)
+        _check(L.sfft_classify(self._h, int(p), ua, _ptr(Y), float(eta_bin), cap, _ptr(h), _ptr(w), _ptr(a),
+                               C.byref(n)), "sfft_classify")
+        m = int(n.value)
+        return h[:m], w[:m], a[:m]
+
+
+def sort_result(freqs: np.ndarray, coeffs: np.ndarray):
+    """Lexicographic order of the frequency vectors (the result is a set)."""
+    freqs = np.asarray(freqs)
+    if freqs.shape[0] == 0:
+        return freqs.astype(np.int64), np.asarray(coeffs)
+    order = np.lexsort(freqs.T[::-1])
+    return freqs[order].astype(np.int64), np.asarray(coeffs)[order]

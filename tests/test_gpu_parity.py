@@ -1,0 +1,301 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Step by step: samples of kernel (a), DFTs of kernel (b), bin read-out of kernel
+(c); then whole recoveries, where the recovered frequency set must equal the
+oracle's and the planted set exactly and the coefficients agree within 1e-5
+relative (FP32 bulk) or 1e-12 (FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle.sfft_oracle as O
+from paper_1606_07407_gb300.inputs import WORKLOADS, Stream, draw_signal
+
+pytestmark = pytest.mark.gpu
+
+FP32_COEFF_TOL = 1e-5
+FP64_COEFF_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def sfft():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_1606_07407_gb300 import build as B
+    B.build()
+    from paper_1606_07407_gb300 import sfft as S
+    S.load()
+    return S
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+# ------------------------------------------------------------------ kernel (a)
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("d,N,K,p,blocks", [
+    (2, 1024, 16, 83, (1, 1)),        # one tile, one mode chunk
+    (3, 4096, 100, 1031, (2, 1)),      # 3 tiles (ragged), 4 mode chunks (ragged)
+    (5, 1024, 1000, 5003, (3, 2)),     # first round of the d=5 workload
+    (12, 256, 70, 211, (3,) * 4),      # 13 sets: two set groups
+])
+def test_samples_match_oracle(sfft, prec, d, N, K, p, blocks):
+    sig = draw_signal(d, N, K, seed=1000 + K, r_lo=1.0, r_hi=10.0)
+    plan = sfft.Plan(d, N, max(K, 16), blocks=blocks, precision=prec)
+    for m in range(len(blocks)):
+        u = [int(v) for v in O.unwrap_vector(d, N, blocks, m)]
+        y = _np(plan.sample(p, u, torch.tensor(sig.freqs), torch.tensor(sig.coeffs)))
+        ref = O.sample_sets(sig.freqs, sig.coeffs, p, u, N)
+        scale = np.sum(np.abs(sig.coeffs))
+        tol = (2.0 ** -20 if prec == "fp32" else 2.0 ** -48) * scale
+        assert np.max(np.abs(y - ref)) < tol
+
+
+def test_samples_registry_sign_and_empty(sfft):
+    # K = 0 gives exact zeros; negated coefficients give negated samples (f - g).
+    plan = sfft.Plan(2, 64, 8, blocks=(1, 1))
+    y0 = _np(plan.sample(13, [1, 0], torch.zeros((0, 2), dtype=torch.int32), torch.zeros(0, dtype=torch.complex128)))
+    assert np.all(y0 == 0)
+    w = torch.tensor([[3, 5], [7, 60]], dtype=torch.int32)
+    a = torch.tensor([1 + 1j, -0.5 + 2j], dtype=torch.complex128)
+    yp, ym = _np(plan.sample(13, [1, 0], w, a)), _np(plan.sample(13, [1, 0], w, -a))
+    assert np.max(np.abs(yp + ym)) == 0.0
+
+
+def test_samples_sampled_at_large_size(sfft):
+    # d = 10, N = 2^16, K = 10000 modes, p = 50021: compare 64 sampled columns.
+    sig = draw_signal(10, 1 << 16, 10000, seed=3, r_lo=1.0, r_hi=10.0)
+    blocks = (2,) * 5
+    plan = sfft.Plan(10, 1 << 16, 10000, blocks=blocks)
+    u = [int(v) for v in O.unwrap_vector(10, 1 << 16, blocks, 1)]
+    y = _np(plan.sample(50021, u, torch.tensor(sig.freqs), torch.tensor(sig.coeffs)))
+    xs = np.array(sorted(set(Stream(5).integers(64, 0, 50021).tolist()) | {0, 50020}))
+    ref = O.sample_sets(sig.freqs, sig.coeffs, 50021, u, 1 << 16, x_values=xs)
+    assert np.max(np.abs(y[:, xs] - ref)) < 2.0 ** -20 * np.sum(np.abs(sig.coeffs))
+
+
+# ------------------------------------------------------------------ kernel (b)
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("p", [2, 5, 83, 911, 2039, 2053, 5003, 50021])
+def test_dft_matches_definition(sfft, prec, p):
+    # 2039 is the largest single-block length (L = 4096); 2053 the first four-step one.
+    rows = 3
+    plan = sfft.Plan(2, 1 << 16, 12000, blocks=(1, 1), precision=prec)
+    st = Stream(p)
+    y = (st.uniform(rows * p) - 0.5 + 1j * (st.uniform(rows * p) - 0.5)).reshape(rows, p)
+    Yg = _np(plan.dft(p, torch.tensor(y)))
+    ycast = y.astype(np.complex64).astype(np.complex128) if prec == "fp32" else y
+    ref = O.dft(ycast)
+    L = 1 << math.ceil(math.log2(2 * p - 1))
+    eps = 2.0 ** -24 if prec == "fp32" else 2.0 ** -53
+    for r in range(rows):
+        tol = 16 * eps * math.log2(L) * np.linalg.norm(ycast[r])
+        assert np.max(np.abs(Yg[r] - ref[r])) < tol
+
+
+def test_dft_single_mode_closed_form(sfft):
+    # Eq. 3-5: samples of one mode transform to p a at its bin and ~0 elsewhere.
+    p, N = 5003, 1024
+    plan = sfft.Plan(5, N, 1000, blocks=(3, 2))
+    w = torch.tensor([[700, 13, 1000, 512, 9]], dtype=torch.int32)
+    a = torch.tensor([1.5 - 0.25j], dtype=torch.complex128)
+    u = [1, N, N * N, 0, 0]
+    Y = _np(plan.dft(p, plan.sample(p, u, w, a)))
+    h = (700 + 13 * N + 1000 * N * N) % p
+    assert abs(Y[0, h] - p * a[0].item()) < 1e-5 * p
+    mask = np.ones(p, bool)
+    mask[h] = False
+    assert np.max(np.abs(Y[:, mask])) < 1e-5 * p
+    for n in range(1, 6):
+        assert abs(Y[n, h] / Y[0, h] - np.exp(2j * np.pi * int(w[0, n - 1]) / N)) < 1e-6
+
+
+def test_dft_large_prime_sampled(sfft):
+    # the largest lengths a d=20, N=2^20, k=10^5 plan reaches (L = 2^20): sampled bins
+    p = 500009
+    plan = sfft.Plan(1, 1 << 20, 100000, blocks=(1,))
+    st = Stream(9)
+    y = (st.uniform(p) - 0.5 + 1j * (st.uniform(p) - 0.5)).reshape(1, p)
+    Yg = _np(plan.dft(p, torch.tensor(y)))
+    yc = y.astype(np.complex64).astype(np.complex128)[0]
+    hs = np.array([0, 1, 2, 77777, p // 2, p - 1])
+    x = np.arange(p)
+    for h in hs:
+        ref = np.sum(yc * np.exp(-2j * np.pi * ((h * x) % p) / p))
+        assert abs(Yg[0, h] - ref) < 16 * 2.0 ** -24 * 20 * np.linalg.norm(yc)
+
+
+# ------------------------------------------------------------------ kernel (c)
+
+def _designed_transforms(d, N, p, u, w, a):
+    return O.dft(O.sample_sets(np.array(w), np.array(a), p, u, N))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_classify_matches_oracle(sfft, prec):
+    d, N, p = 3, 64, 31
+    u = [1, 0, 0]
+    # bin 5: two modes differing in coordinate 2 (rejected); bins 20, 9: lone modes;
+    # bin 12: two modes differing in coordinate 1 by p (rejected)
+    w = [[5, 10, 7], [5, 40, 7], [20, 3, 60], [40, 33, 1], [12, 0, 0], [43, 0, 0]]
+    a = [1.0 + 0.2j, 0.8 - 0.5j, -1.1 + 0.3j, 0.6 + 0.6j, 1.0, 0.7j]
+    Y = _designed_transforms(d, N, p, u, w, a)
+    plan = sfft.Plan(d, N, 16, blocks=(1, 1, 1), precision=prec)
+    Yc = Y.astype(np.complex64 if prec == "fp32" else np.complex128)
+    h, gw, ga = plan.classify(p, u, torch.tensor(Yc), 1e-3)
+    th = O.Thresholds(tau=plan_tau(prec), delta=plan_delta(prec))
+    ref = O.classify(Yc.astype(np.complex128), p, u, N, 1e-3, th)
+    got = sorted(zip(_np(h).tolist(), map(tuple, _np(gw).tolist()), _np(ga).tolist()))
+    assert [(x[0], x[1]) for x in got] == [(r[0], r[1]) for r in ref] == [(9, (40, 33, 1)), (20, (20, 3, 60))]
+    for g, r in zip(got, ref):
+        assert abs(g[2] - r[2]) <= 1e-12 * abs(r[2])
+
+
+def plan_tau(prec):
+    return 1e-7 if prec == "fp64" else 1e-3
+
+
+def plan_delta(prec):
+    return 0.1 if prec == "fp64" else 0.25
+
+
+def test_classify_random_round_matches_oracle(sfft):
+    # a first round of the d=5 workload: the accepted (bin, vector) sets are identical
+    wl = WORKLOADS["d5_N1024_k1000"]
+    sig = wl.signal()
+    p = 5003
+    u = [int(v) for v in O.unwrap_vector(5, 1024, wl.blocks, 1)]
+    plan = sfft.Plan(5, 1024, 1000, blocks=wl.blocks)
+    Y = _np(plan.dft(p, plan.sample(p, u, torch.tensor(sig.freqs), torch.tensor(sig.coeffs))))
+    eta = 2.0 ** -17 * np.max(np.abs(Y[0]))
+    h, gw, ga = plan.classify(p, u, torch.tensor(Y), eta)
+    ref = O.classify(Y.astype(np.complex128), p, u, 1024, eta, O.Thresholds(tau=1e-3, delta=0.25))
+    got = sorted(zip(_np(h).tolist(), map(tuple, _np(gw).tolist())))
+    assert got == [(r[0], r[1]) for r in ref]
+    assert len(got) > 700
+    planted = {tuple(r) for r in sig.freqs.tolist()}
+    assert all(g[1] in planted for g in got)
+
+
+# ------------------------------------------------------------------ whole recovery
+
+def _run_both(sfft, sig, blocks=None, prec="fp32", dirs=None, primes=None, box_lo=0):
+    plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=blocks, dirs=dirs, primes=primes, precision=prec, box_lo=box_lo)
+    f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N))
+    gf, ga = sfft.sort_result(_np(f), _np(a))
+    th = O.Thresholds() if prec == "fp64" else O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
+    ref = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, blocks, th=th, dirs=dirs,
+                             primes=primes, box_lo=box_lo)
+    return gf, ga, status, stats, ref
+
+
+def _assert_parity(sig, gf, ga, status, stats, ref, tol):
+    planted = sig.freqs[np.lexsort(sig.freqs.T[::-1])].astype(np.int64)
+    assert status == 0 and stats["converged"] and ref.converged
+    assert np.array_equal(gf, ref.freqs)
+    assert np.array_equal(gf, planted)
+    rel = np.abs(ga - ref.coeffs) / np.abs(ref.coeffs)
+    assert np.max(rel) < tol
+    assert stats["p"] == [r["p"] for r in ref.rounds]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4])
+def test_recovery_d2_workload(sfft, seed):
+    wl = WORKLOADS["d2_N1024_k16"]
+    sig = wl.signal(seed_offset=seed * 101)
+    _assert_parity(sig, *_run_both(sfft, sig, wl.blocks), FP32_COEFF_TOL)
+
+
+def test_recovery_d5_workload_full_size(sfft):
+    wl = WORKLOADS["d5_N1024_k1000"]
+    sig = wl.signal()
+    _assert_parity(sig, *_run_both(sfft, sig, wl.blocks), FP32_COEFF_TOL)
+
+
+@pytest.mark.parametrize("case", ["d1", "d4_2x2", "d3_full_unwrap", "d6_tilted", "signed_box", "d12"])
+def test_recovery_shapes(sfft, case):
+    if case == "d1":
+        sig, blocks = draw_signal(1, 4096, 40, seed=4), (1,)
+    elif case == "d4_2x2":
+        sig, blocks = draw_signal(4, 32, 60, seed=8), (2, 2)
+    elif case == "d3_full_unwrap":
+        sig, blocks = draw_signal(3, 64, 100, seed=5), (3,)
+    elif case == "d6_tilted":
+        sig, blocks = draw_signal(6, 128, 150, seed=6), (2, 2, 2)
+    elif case == "signed_box":
+        sig, blocks = draw_signal(3, 256, 80, seed=7, box_lo=-128), (2, 1)
+    else:
+        sig, blocks = draw_signal(12, 64, 120, seed=12), (3,) * 4
+    dirs = None
+    if case == "d6_tilted":
+        dirs = [[1, 128, 7, 0, 0, 3], [0, 5, 1, 128, 0, 0], [11, 0, 0, 0, 1, 128]]
+        blocks = None
+    _assert_parity(sig, *_run_both(sfft, sig, blocks, dirs=dirs, box_lo=sig.box_lo), FP32_COEFF_TOL)
+
+
+def test_recovery_fp64_policy(sfft):
+    wl = WORKLOADS["d5_N1024_k1000"]
+    sig = draw_signal(5, 1024, 300, seed=31, r_lo=1.0, r_hi=10.0)
+    _assert_parity(sig, *_run_both(sfft, sig, wl.blocks, prec="fp64"), FP64_COEFF_TOL)
+
+
+def test_fig2_collision_story_on_gpu(sfft):
+    w = np.array([[3, 5], [9, 5], [3, 12]])
+    a = np.array([1.0 + 0.5j, -0.7 + 1.2j, 0.4 - 1.1j])
+    from paper_1606_07407_gb300.inputs import Signal
+    sig = Signal(2, 16, w.astype(np.int32), a)
+    gf, ga, status, stats, ref = _run_both(sfft, sig, dirs=[[0, 1], [1, 0]], primes=[17])
+    assert stats["accepted"][:2] == [1, 2]
+    _assert_parity(sig, gf, ga, status, stats, ref, FP32_COEFF_TOL)
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_empty_signal(sfft):
+    plan = sfft.Plan(3, 1024, 10, blocks=(2, 1))
+    s = sfft.Signal(np.zeros((0, 3), np.int32), np.zeros(0, np.complex128), 1024)
+    f, a, status, stats = plan.execute(s)
+    assert status == 0 and f.shape[0] == 0 and stats["rounds"] == 1
+
+
+def test_single_mode(sfft):
+    sig = draw_signal(4, 1 << 16, 1, seed=2)
+    _assert_parity(sig, *_run_both(sfft, sig, (2, 2)), FP32_COEFF_TOL)
+
+
+def test_capacity_overflow_reported(sfft):
+    sig = draw_signal(2, 1024, 16, seed=1)
+    plan = sfft.Plan(2, 1024, 16, blocks=(1, 1))
+    f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, 1024), capacity=4, allow=(3,))
+    assert status == 3 and f.shape[0] == 4
+
+
+def test_not_converged_reported(sfft):
+    # two modes that differ only in coordinate 2, projected on coordinate 1 every round, never separate
+    w = np.array([[5, 10], [5, 11]], np.int32)
+    a = np.array([1.0, 1.0j])
+    plan = sfft.Plan(2, 1024, 2, dirs=[[1, 0]], max_rounds=6)
+    f, _, status, stats = plan.execute(sfft.Signal(w, a, 1024), allow=(2,))
+    assert status == 2 and stats["rounds"] == 6 and not stats["converged"]
+
+
+def test_repeated_execute_is_stable(sfft):
+    wl = WORKLOADS["d5_N1024_k1000"]
+    sig = wl.signal()
+    plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=wl.blocks)
+    s = sfft.Signal(sig.freqs, sig.coeffs, sig.N)
+    first = None
+    for _ in range(3):
+        f, a, status, _ = plan.execute(s)
+        gf, ga = sfft.sort_result(_np(f), _np(a))
+        if first is None:
+            first = (gf, ga)
+        assert status == 0 and np.array_equal(gf, first[0])
+        assert np.max(np.abs(ga - first[1]) / np.abs(first[1])) < 1e-5
