@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark of the sparse-FFT hot path: modes recovered per second at exact frequency recovery.
+
+Workload (default): d = 5, N = 1024, k = 1000 planted modes per signal, r ~ U[1, 10],
+noiseless, line directions from partial unwrapping with blocks (3, 2), FP32 sampling and
+DFT with an FP64 phase-ratio step.  One step recovers a batch of independent signals
+(--batch, all resident in HBM before timing) by full runs of Algorithm 2; a step counts
+only if every recovered frequency set equals the planted one.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+if "--impl" in sys.argv and "reference" in sys.argv or "--cpu-baseline-only" in sys.argv:
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+import numpy as np  # noqa: E402
+
+from paper_1606_07407_gb300.inputs import WORKLOADS  # noqa: E402
+
+METRIC = "modes recovered/s at exact freq recovery"
+UNIT = "modes/s"
+DEFAULT_WORKLOAD = "d5_N1024_k1000"
+FP32_ALU_LANES_PER_SM = 128      # FP32 FMA lanes per SM (Blackwell)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def oracle_throughput(workload: str, min_seconds: float, max_recoveries: int, seed_base: int):
+    """Runs the FP64 oracle on successive signals of the workload until min_seconds of CPU
+    work (or max_recoveries).  Returns (modes/s, recoveries, seconds, exact)."""
+    import oracle.sfft_oracle as O
+    wl = WORKLOADS[workload]
+    th = O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
+    n, modes, t_total, exact = 0, 0, 0.0, True
+    while n < max_recoveries and (t_total < min_seconds or n == 0):
+        sig = wl.signal(seed_offset=seed_base + n)
+        t0 = time.perf_counter()
+        res = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, wl.blocks, th=th)
+        t_total += time.perf_counter() - t0
+        planted = sig.freqs[np.lexsort(sig.freqs.T[::-1])].astype(np.int64)
+        exact = exact and res.converged and np.array_equal(res.freqs, planted)
+        n += 1
+        modes += sig.k
+    return modes / t_total, n, t_total, exact
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append((time.perf_counter(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        inside = [s for t, s in self.samples if t0 <= t <= t1]
+        if not inside and self.samples:
+            mid = 0.5 * (t0 + t1)
+            inside = [min(self.samples, key=lambda ts: abs(ts[0] - mid))[1]]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(s[0]) for s in inside if num(s[0]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in inside for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": num(inside[0][1]), "reasons": reasons, "samples": len(inside)}
+
+
+# ------------------------------------------------------------------ distributed helpers
+
+def _dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if n_gpus > 0 else "gloo")
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]
+    for w in range(args.warmup):
+        oracle_throughput(args.workload, 0.0, 1, seed_base=10_000 + w)
+    t = 0.0
+    modes = 0
+    exact = True
+    for s in range(args.steps):
+        v, n, secs, ok = oracle_throughput(args.workload, 0.0, 1, seed_base=s)
+        t += secs
+        modes += n * wl.k
+        exact = exact and ok
+    value = modes / t if exact else 0.0
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded planted sparse signals)",
+        "config": {"workload": args.workload, "d": wl.d, "N": wl.N, "k": wl.k, "blocks": list(wl.blocks),
+                   "signals_per_step": 1, "form": "FP64 CPU oracle, one recovery per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full recoveries, one per step, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def _timed_steps(torch, stream, flush, steps, step_fn):
+    """Runs `steps` steps, each bracketed by CUDA events on the launch stream, with an L2
+    flush (a 256 MiB write) before each step outside the events.  Returns ms per step and
+    the per-step results."""
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ms, outs = [], []
+    for _ in range(steps):
+        flush.zero_()
+        ev0.record(stream)
+        outs.append(step_fn())
+        ev1.record(stream)
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    return ms, outs
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = _dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_1606_07407_gb300 import build as B
+    if rank == 0:
+        B.build()
+    _barrier(world)
+    from paper_1606_07407_gb300 import sfft
+
+    wl = WORKLOADS[args.workload]
+    stream = torch.cuda.current_stream()
+    nb = args.batch
+    # inputs resident in HBM before timing: distinct signals per rank and batch slot
+    sigs = [wl.signal(seed_offset=1000 * rank + b) for b in range(nb)]
+    dev = [sfft.Signal(s.freqs, s.coeffs, s.N) for s in sigs]
+    planted = [s.freqs[np.lexsort(s.freqs.T[::-1])].astype(np.int64) for s in sigs]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    plan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, precision=args.precision, graph=True, stream=stream)
+    batch = sfft.Batch([plan] * nb, graph=True, stream=stream)
+    bout = batch.outputs()
+    allow = (0, 2, 3, 5)
+
+    def step_batched():
+        res, sts, st = batch.execute(dev, out=bout, allow=allow)
+        return sts, st, res
+
+    cap = 2 * wl.k + 16
+    pouts = [(torch.empty((cap, wl.d), dtype=torch.int32, device="cuda"),
+              torch.empty((cap,), dtype=torch.complex128, device="cuda")) for _ in range(nb)]
+
+    def step_plain():
+        sts, res, st = [], [], None
+        for b in range(nb):
+            f, a, status, st = plan.execute(dev[b], capacity=cap, out=pouts[b], allow=allow)
+            sts.append(status)
+            res.append((f, a))
+        return sts, st, res
+
+    head_fn = step_batched if args.form == "batched" else step_plain
+    for _ in range(args.warmup):
+        head_fn()
+    torch.cuda.synchronize()
+
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        try:
+            gpu_index = int(cvd.split(",")[local])
+        except (ValueError, IndexError):
+            gpu_index = local
+    sampler = ClockSampler(gpu_index) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    _barrier(world)
+    torch.cuda.synchronize()
+    t_host0 = time.perf_counter()
+    step_ms, outs = _timed_steps(torch, stream, flush, args.steps, head_fn)
+    torch.cuda.synchronize()
+    t_host1 = time.perf_counter()
+    _barrier(world)
+    clocks = sampler.summary(t_host0, t_host1) if sampler else None
+    if sampler:
+        sampler.stop()
+
+    # every step's statuses, and the last step's sets element by element against the planted ones
+    ok_all = all(all(x == 0 for x in sts) for sts, _, _ in outs)
+    for b, (f, a) in enumerate(outs[-1][2]):
+        gf, _ = sfft.sort_result(f.cpu().numpy(), a.cpu().numpy())
+        ok_all = ok_all and np.array_equal(gf, planted[b])
+    total_ms = _max_over_ranks(world, float(sum(step_ms)))
+    modes = _sum_over_ranks(world, float(args.steps * nb * wl.k)) if ok_all else 0.0
+    value = modes / (total_ms / 1e3)
+    launches_step = outs[-1][1]["launches"] if args.form == "batched" else None
+    gpu_launches = int(sum(sum(st["launches"].values()) for _, st, _ in outs)) if args.form == "batched" else \
+        int(args.steps * nb * sum(outs[-1][1]["launches"].values()))
+
+    # the other form, on the same signals, for comparison
+    other_fn = step_plain if args.form == "batched" else step_batched
+    other_fn()
+    other_ms, other_outs = _timed_steps(torch, stream, flush, args.other_steps, other_fn)
+    other_ok = all(all(x == 0 for x in sts) for sts, _, _ in other_outs)
+    other_value = (args.other_steps * nb * wl.k) / (sum(other_ms) / 1e3) if other_ok else 0.0
+
+    # profiled pass (same batch, rounds enqueued from the host with CUDA events around each
+    # kernel class on the launch stream): kernel shares and the sampling kernel's roofline
+    pplan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, precision=args.precision, profile=True, stream=stream)
+    pbatch = sfft.Batch([pplan] * nb, graph=False, stream=stream)
+    pout = pbatch.outputs()
+    pbatch.execute(dev, out=pout, allow=allow)
+    prof_ms, prof = _timed_steps(torch, stream, flush, args.profile_steps,
+                                 lambda: pbatch.execute(dev, out=pout, allow=allow))
+    pstats = [o[2] for o in prof]
+    terms = sum(st["terms"] for st in pstats)
+    sample_ms = sum(st["kernel_ms"]["sample"] for st in pstats)
+    class_ms = {k: sum(st["kernel_ms"][k] for st in pstats) for k in sfft.KCLASSES}
+    sample_launches = sum(st["launches"]["sample"] for st in pstats)
+    flops = 8.0 * terms                      # one complex multiply-add (4 FMA) per term
+    achieved = flops / (sample_ms / 1e3) / 1e12 if sample_ms > 0 else 0.0
+    props = torch.cuda.get_device_properties(local)
+    sm_max = (clocks or {}).get("sm_max_mhz") or _peaks().get("sm_max_mhz", 2070.0)
+    peak = props.multi_processor_count * FP32_ALU_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    tot_class = sum(class_ms.values())
+
+    # end to end through the public API with host buffers: pinned host -> device copies of each
+    # step's inputs, the signal handles refilled in place, recovery, device -> host of the results
+    host_in = [(torch.from_numpy(s.freqs.astype(np.int32)).pin_memory(),
+                torch.from_numpy(s.coeffs.astype(np.complex128)).pin_memory()) for s in sigs]
+    dev_in = [(torch.empty_like(f, device="cuda"), torch.empty_like(c, device="cuda")) for f, c in host_in]
+    h2d = sum(f.numel() * 4 + c.numel() * 16 for f, c in host_in)
+    host_fo = torch.empty(bout[1].shape, dtype=torch.int32).pin_memory()
+    host_co = torch.empty(bout[2].shape, dtype=torch.complex128).pin_memory()
+    d2h = host_fo.numel() * 4 + host_co.numel() * 16
+    e2e_ms = 0.0
+    e2e_ok = True
+    for _ in range(args.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b in range(nb):
+            dev_in[b][0].copy_(host_in[b][0], non_blocking=True)
+            dev_in[b][1].copy_(host_in[b][1], non_blocking=True)
+            dev[b].assign(dev_in[b][0], dev_in[b][1])
+        res, sts, _ = batch.execute(dev, out=bout, allow=allow)
+        host_fo.copy_(bout[1], non_blocking=True)
+        host_co.copy_(bout[2], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+        e2e_ok = e2e_ok and all(x == 0 for x in sts)
+    e2e_ms = _max_over_ranks(world, e2e_ms)
+    e2e_modes = _sum_over_ranks(world, float(args.e2e_steps * nb * wl.k)) if e2e_ok else 0.0
+    e2e_value = e2e_modes / (e2e_ms / 1e3)
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp32" if args.precision != "fp64" else "f64",
+        "data": "synthetic (seeded planted sparse signals, resident in HBM)",
+        "config": {"workload": args.workload, "d": wl.d, "N": wl.N, "k": wl.k, "blocks": list(wl.blocks),
+                   "signals_per_step": nb,
+                   "form": ("batched: all signals in every launch, device-ended CUDA-graph round loop"
+                            if args.form == "batched" else "plain: one signal per execute, CUDA-graph round loop"),
+                   "precision": "FP32 sampling, DFT and phase ratio (N <= 2^14)" if args.precision == "fp32"
+                   else args.precision,
+                   "l2": "flushed between timed steps (256 MiB write)", "exact_recovery": bool(ok_all)},
+        "other_form": {"form": "plain" if args.form == "batched" else "batched", "value": other_value,
+                       "unit": UNIT, "steps": args.other_steps,
+                       "ms_per_step": sum(other_ms) / max(len(other_ms), 1)},
+        "roofline": {"bound": "alu", "kernel": "k_sample", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
+                     "peak_basis": f"{props.multi_processor_count} SMs x {FP32_ALU_LANES_PER_SM} FP32 FMA lanes x 2 "
+                                   f"x {sm_max:.0f} MHz",
+                     "measured": f"CUDA events around each sampling launch, {args.profile_steps} profiled steps "
+                                 "of the same batch (rounds enqueued from the host)",
+                     "launches": sample_launches,
+                     "avg_launch_us": 1e3 * sample_ms / max(sample_launches, 1),
+                     "profiled_ms_per_step": sum(prof_ms) / max(len(prof_ms), 1)},
+        "kernel_share": {k: round(v / tot_class, 4) if tot_class else None for k, v in class_ms.items()},
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "steps": args.e2e_steps},
+    }
+    if launches_step is not None:
+        line["launches_per_step"] = launches_step
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def cpu_baseline(args):
+    """The oracle, single-threaded, in a child process on a bounded sample of the workload."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-only", "--workload", args.workload,
+           "--cpu-seconds", str(args.cpu_seconds)]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as exc:  # noqa: BLE001
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=256, help="signals recovered per step")
+    ap.add_argument("--form", default="batched", choices=["batched", "plain"])
+    ap.add_argument("--other-steps", type=int, default=3)
+    ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-baseline-only", action="store_true")
+    args = ap.parse_args(argv)
+    if args.cpu_baseline_only:
+        v, n, secs, exact = oracle_throughput(args.workload, args.cpu_seconds, 1000, seed_base=0)
+        print(json.dumps({"value": v if exact else 0.0, "unit": UNIT, "cores": 1, "kind": "oracle",
+                          "sample": f"{n} full recoveries of the workload ({secs:.1f} s, single thread)"}))
+        return 0
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -43,17 +43,21 @@ typedef enum {
   SFFT_ERR_TIMEOUT = 7        /* a bounded device-side wait ran out                     */
 } sfft_status;
 
-/* Arithmetic of the hot path.  FP32 bulk: sampling and DFT in float, the phase
- * ratio, the frequency read-out and the coefficient estimate in double.  FP64:
- * every step in double. */
+/* Arithmetic of the hot path.  AUTO: sampling and DFT in float; the phase
+ * ratio, frequency read-out and coefficient estimate in double when N > 2^14
+ * (where float's phase resolution starts to matter against pi / N), else in
+ * float.  FP32_FP64RATIO: the same with the ratio step always in double.
+ * FP32: every step in float.  FP64: every step in double. */
 typedef enum {
-  SFFT_PREC_FP32_FP64RATIO = 0,
-  SFFT_PREC_FP32 = 1,
-  SFFT_PREC_FP64 = 2
+  SFFT_PREC_AUTO = 0,
+  SFFT_PREC_FP32_FP64RATIO = 1,
+  SFFT_PREC_FP32 = 2,
+  SFFT_PREC_FP64 = 3
 } sfft_precision;
 
 typedef struct sfft_plan_s* sfft_plan;
 typedef struct sfft_signal_s* sfft_signal;
+typedef struct sfft_batch_s* sfft_batch;
 
 /* Prime schedule (Alg. 1 and Alg. 2: p = i-th prime >= c k*, c = 5 in Sec. 5).
  * primes != NULL overrides the rule: round i uses primes[(i-1) mod n_primes]. */
@@ -85,9 +89,18 @@ typedef struct {
   double delta;      /* max distance of N Arg/(2 pi) from an integer; 0 = default */
   double noise_sigma;/* known noise level of the samples; adds 6 sigma sqrt(p)   */
   int max_rounds;    /* 0 = 64 + 4 ceil(log2 k)                                   */
+  int profile;       /* 1: time each kernel class with CUDA events into sfft_stats */
+  int graph;         /* 1: run the round loop as one CUDA graph whose while-loop the device ends */
+  int coef_set0;     /* 1: coefficient a = Y_0[h] / p as printed in Eq. 41; 0 (default): the mean
+                        over the d + 1 sets of Y_n[h] e^{-2 pi i w_n / N} / p, equal to it for a
+                        single-mode bin and less affected by rounding */
 } sfft_opts;
 
 #define SFFT_STATS_MAX_ROUNDS 256
+/* kernel classes of sfft_stats.kernel_ms / kernel_launches: round setup and
+ * per-prime tables, mode projection, sampling, DFT, classification, registry
+ * merge + prune + output */
+#define SFFT_NKCLASS 6
 typedef struct {
   int rounds;                     /* rounds run, including the final empty one  */
   int converged;                  /* 1 when the last round found no occupied bin */
@@ -97,6 +110,8 @@ typedef struct {
   int32_t K[SFFT_STATS_MAX_ROUNDS];        /* modes evaluated per sample (k + |R|) */
   int32_t accepted[SFFT_STATS_MAX_ROUNDS]; /* bins accepted in the round */
   int32_t registry[SFFT_STATS_MAX_ROUNDS]; /* live registry entries after the round */
+  int64_t kernel_launches[SFFT_NKCLASS];   /* kernels launched, per class */
+  double kernel_ms[SFFT_NKCLASS];          /* CUDA-event time per class (opts.profile) */
 } sfft_stats;
 
 /* Create a plan for signals of dimension d, box side N and sparsity k.
@@ -104,8 +119,9 @@ typedef struct {
  * d and the largest prime the schedule can reach); nothing is allocated
  * during execute.  stream: a cudaStream_t, or NULL for the default stream.
  * pschedule, tilts, opts may be NULL (defaults).  Errors: INVALID_ARG for
- * d < 1, N < 2, k < 0, N^? direction overflow or bad options; PRECISION when
- * N exceeds 2^24 under an FP32 policy; CUDA when an allocation fails. */
+ * d < 1, N < 2, k < 0, a direction that overflows int64, a largest prime at or
+ * above 2^22 under a float policy, or bad options; PRECISION when N exceeds
+ * 2^23 under a float policy; CUDA when an allocation fails. */
 sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* pschedule,
                              const sfft_tilts* tilts, const sfft_opts* opts, void* stream,
                              sfft_plan* plan_out);
@@ -120,6 +136,13 @@ sfft_status sfft_signal_synthetic(int d, int64_t N, int64_t k, const int32_t* fr
                                   uint64_t noise_seed, sfft_signal* signal_out);
 void sfft_signal_destroy(sfft_signal signal);
 
+/* Replace the modes of an existing black box with k new ones (k at most the
+ * count it was created with; same d and N).  freqs_dev / coeffs_dev as in
+ * sfft_signal_synthetic.  Allocates nothing; the copy runs on the legacy
+ * default stream and has finished when the call returns. */
+sfft_status sfft_signal_assign(sfft_signal signal, int64_t k, const int32_t* freqs_dev,
+                               const double* coeffs_dev);
+
 /* Run Algorithm 2 on the signal until a round finds no occupied bin.
  * Writes the live registry (unordered) to freqs_out_dev (int32 [capacity x d])
  * and coeffs_out_dev (complex128 [capacity]); *n_found = number of entries.
@@ -130,14 +153,37 @@ sfft_status sfft_execute(sfft_plan plan, sfft_signal signal, int64_t capacity,
                          int32_t* freqs_out_dev, double* coeffs_out_dev, int64_t* n_found,
                          sfft_stats* stats);
 
+/* ---- batches: many independent signals in every launch -------------------- */
+
+/* A batch of n signal slots; slot s takes d, N, k, schedule, directions and
+ * thresholds from plans[s] (the same plan may appear many times).  All plans
+ * must share the float-or-double choice of their precision.  The batch owns
+ * its own device buffers; the plans may be destroyed afterwards.  graph = 1
+ * runs the rounds as one CUDA graph with a device-ended while-loop. */
+sfft_status sfft_batch_create(int n, const sfft_plan* plans, void* stream, int graph, sfft_batch* batch_out);
+void sfft_batch_destroy(sfft_batch batch);
+int64_t sfft_batch_device_bytes(sfft_batch batch);
+
+/* Recover all n signals (signals[s] must match slot s's d and N, with at most
+ * its k modes).  Outputs are packed: slot s writes up to capacities[s] rows
+ * starting at row sum_{t<s} capacities[t] of coeffs_out_dev (complex128) and
+ * at element sum_{t<s} capacities[t] d_t of freqs_out_dev (int32).
+ * n_found[s] and status[s] (an sfft_status) are host arrays of n entries.
+ * Returns the first non-OK slot status, else OK.  stats (nullable) sums the
+ * work over slots and records the per-round history of slot 0. */
+sfft_status sfft_batch_execute(sfft_batch batch, const sfft_signal* signals, const int64_t* capacities,
+                               int32_t* freqs_out_dev, double* coeffs_out_dev, int64_t* n_found,
+                               int32_t* status, sfft_stats* stats);
+
 /* ---- the steps of one round, callable on their own ------------------------ */
 
 /* Kernel (a), sample-and-residual (Alg. 2 sampling; Eq. 41): for the K modes
  * (freqs_dev int32 [K x d], coeffs_dev complex128 [K]) writes
  *     y[n][x] = sum_j coeffs_j exp(2 pi i w_j . (x u / p + s_n)),
  * s_0 = 0, s_n = e_n / N, x < p, n <= d, to y_out_dev, row-major [(d+1) x p],
- * complex64 for FP32 plans and complex128 for FP64 plans.  u: host int64 [d].
- * Requires 5 <= p <= the plan's largest prime and K <= the plan's mode capacity. */
+ * complex64 for float plans and complex128 for FP64 plans.  u: host int64 [d].
+ * Requires 2 <= p <= the plan's largest prime; CAPACITY when K exceeds the
+ * plan's k. */
 sfft_status sfft_sample(sfft_plan plan, int64_t p, const int64_t* u, int64_t K,
                         const int32_t* freqs_dev, const double* coeffs_dev, void* y_out_dev);
 

@@ -170,9 +170,12 @@ class Thresholds:
 
 
 def classify(Y: np.ndarray, p: int, u, N: int, eta_bin: float, th: Thresholds,
-             box_lo: int = 0):
+             box_lo: int = 0, estimator: str = "set0"):
     """All bins h = 0..p-1 that hold exactly one mode, with the mode read off.
 
+    The coefficient is a = Y_0[h] / p (Eq. 41, estimator "set0") or, with estimator
+    "mean", the mean over n = 0..d of Y_n[h] exp(-2 pi i w_n / N) / p, which for a bin
+    holding one mode has every term equal to a (Eq. 41 applied to each shifted set).
     Returns a list of (h, w, a), w a tuple of d ints, in increasing h."""
     D = Y.shape[0] - 1
     Y0 = Y[0]
@@ -190,7 +193,12 @@ def classify(Y: np.ndarray, p: int, u, N: int, eta_bin: float, th: Thresholds,
         w = (np.mod(r.astype(np.int64) - box_lo, N) + box_lo).astype(np.int64)
         if int(w @ u_mod) % p != h:                                  # lands in its own bin
             continue
-        out.append((int(h), tuple(int(c) for c in w), complex(Y0[h] / p)))   # Eq. 41: a = Y_0/p
+        if estimator == "mean":
+            rot = np.concatenate([[1.0 + 0j], np.exp(-2j * np.pi * np.mod(w, N) / N)])
+            a = complex(np.mean(Y[:, h] * rot) / p)
+        else:
+            a = complex(Y0[h] / p)                                   # Eq. 41: a = Y_0 / p
+        out.append((int(h), tuple(int(c) for c in w), a))
     return out
 
 
@@ -217,7 +225,8 @@ class Result:
 
 def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int = 5,
                      th: Thresholds | None = None, max_rounds: int | None = None,
-                     box_lo: int = 0, primes=None, dirs=None, noise=None) -> Result:
+                     box_lo: int = 0, primes=None, dirs=None, noise=None,
+                     estimator: str = "set0") -> Result:
     """Algorithm 2 (MultiPhaseshift) on the black box f = sum_j coeffs_j e^{2 pi i freqs_j . t}.
 
     ``primes``, if given, overrides the prime rule (round i uses primes[(i-1) mod len]).
@@ -261,7 +270,7 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
             rounds.append(stat)
             converged = True
             break
-        acc = classify(Y, p, u, N, eta_bin, th, box_lo)
+        acc = classify(Y, p, u, N, eta_bin, th, box_lo, estimator)
         for _, w, a in acc:                                    # R <- R u (w, a)
             R[w] = R.get(w, 0j) + a
         eta_prune = max(th.rho * a_ref, 6.0 * th.sigma / math.sqrt(p))

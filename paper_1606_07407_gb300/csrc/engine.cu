@@ -1,0 +1,1673 @@
+// Kernels and host driver of the batched round engine (Algorithm 2 for many
+// signals at once).  One round, for every active signal s of the batch:
+//
+//   k_plan      (one block)  k* = max(k - |R|, 1), p = i-th prime >= c k* (Alg. 2), direction
+//                            u of the round reduced mod p, work geometry, exclusive scans of the
+//                            per-signal work counts; ends the device loop when no signal is left
+//   k_tables                 W[m] = e^{2 pi i m / p} and chirp[x] = e^{-pi i x^2 / p}
+//   k_sample    (persistent) y_n[x] = (f - g)(x u / p + e_n / N) for all n (Eq. 41), the modes'
+//                            projection alpha = (w . u) mod p fused into the staging
+//   k_filter / k_dft         Bluestein DFT (Eq. 3) in shared memory, or the four-step passes
+//   k_big{A,B,C}             for lengths above one block
+//   k_classify               ratio test, read-out, own-bin check (Eq. 41-42), hash merge into the
+//                            registry with pruning, empty-bin flag for the stop rule
+//
+// The host only enqueues rounds (or launches one CUDA graph whose while-loop the
+// plan kernel ends), and reads results back once.
+#include <algorithm>
+#include <cstring>
+#include <memory>
+
+#include "engine_kernels.cuh"
+#include "fft_smem.cuh"
+
+namespace sfft {
+
+namespace {
+
+constexpr int kSampleThreads = kSampleWarps * 32;
+constexpr int kBindArrays = 6;   // per-signal arrays staged by bind()
+
+// ------------------------------------------------------------------ init / bind
+
+__global__ void k_init(int n, SigRun* run, const int64_t* __restrict__ k_sig) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    SigRun r;
+    memset(&r, 0, sizeof(r));
+    r.active = 1;
+    r.k_sig = (int)k_sig[s];
+    run[s] = r;
+  }
+}
+
+// unit twiddles e^{2 pi i w_{j,l} / N} of the bound signals' modes
+template <typename T>
+__global__ void k_bind_tw(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run,
+                          const int32_t* const* __restrict__ sig_w, c2<T>* __restrict__ tw) {
+  const int s = blockIdx.y;
+  if (s >= n) return;
+  const SigCfg& c = cfg[s];
+  const int64_t total = (int64_t)run[s].k_sig * c.d;
+  const int32_t* w = sig_w[s];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t m = (int64_t)w[e] % c.N;
+    if (m < 0) m += c.N;
+    tw[c.tw_off + e] = unit_root<T>(m, c.N);
+  }
+}
+
+// ------------------------------------------------------------------ plan
+
+struct PlanArgs {
+  int n;
+  int64_t part_cap;
+  int n_sm;
+  int single_max_logL;
+  int force;            // step calls: slot 0 uses force_p and the direction already in its u slot
+  int64_t force_p;
+  int force_K;          // modes bound for the step call
+  int use_cond;
+  cudaGraphConditionalHandle cond;
+  int hard_rounds;      // stop the device loop after this many rounds
+};
+
+__device__ __forceinline__ int ceil_log2(int64_t v) {
+  int r = 0;
+  while ((1LL << r) < v) ++r;
+  return r;
+}
+
+__device__ __forceinline__ void big_geom(int logL, int* M1, int* M2, int* CT, int* RT) {
+  const int l1 = logL / 2, l2 = logL - l1;
+  *M1 = 1 << l1;
+  *M2 = 1 << l2;
+  *CT = min(*M2, max(1, kBigColElems / *M1));
+  *RT = min(*M1, max(1, kBigRowElems / *M2));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg* __restrict__ cfg, SigRun* run,
+                                                       RoundCtl* ctl, Scans sc, const int32_t* __restrict__ ptab,
+                                                       int n_ptab, const int64_t* __restrict__ dirs,
+                                                       const int64_t* __restrict__ plist, int64_t* ubuf,
+                                                       HistRec* hist) {
+  __shared__ int s_S;
+  const int n = a.n;
+  int64_t tiles = 0, active = 0;
+  // pass 1: stop rule and round parameters of every signal
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    SigRun r = run[s];
+    const SigCfg& c = cfg[s];
+    if (s == 0 && hist != nullptr && r.round >= 1 && r.round <= SFFT_STATS_MAX_ROUNDS) {
+      hist[r.round - 1].accepted = r.n_acc;
+      hist[r.round - 1].live = r.n_live;
+    }
+    if (r.active && !a.force) {
+      if (r.round > 0 && !r.any_occupied) {
+        r.active = 0;                        // the residual is empty: done
+        r.status = SFFT_OK;
+      } else if (r.err) {
+        r.active = 0;
+        r.status = SFFT_ERR_CAPACITY;
+      } else if (r.round >= c.max_rounds || r.round >= a.hard_rounds) {
+        r.active = 0;
+        r.status = SFFT_ERR_NOT_CONVERGED;
+      }
+    }
+    if (r.active) {
+      const int i = r.round + 1;
+      int64_t p;
+      if (a.force) {
+        p = a.force_p;
+      } else if (c.n_primes > 0) {
+        p = plist[c.primes_off + (i - 1) % c.n_primes];
+      } else {
+        const int64_t kstar = max((int64_t)c.k - r.n_live, (int64_t)1);
+        const int64_t lo = max((int64_t)c.c * kstar, (int64_t)2);
+        int L0 = 0, H0 = n_ptab;   // first prime >= lo
+        while (L0 < H0) {
+          const int mid = (L0 + H0) >> 1;
+          if (ptab[mid] < lo) L0 = mid + 1;
+          else H0 = mid;
+        }
+        const int idx = L0 + i - 1;
+        p = idx < n_ptab ? ptab[idx] : -1;
+      }
+      if (p < 2 || p > c.p_max) {
+        r.active = 0;
+        r.status = SFFT_ERR_INVALID_ARG;
+      } else {
+        r.p = p;
+        r.mod_m = ~0ull / (uint64_t)p;
+        r.round = i;
+        if (!a.force) {
+          const int di = i % c.n_dirs;
+          for (int l = 0; l < c.d; ++l) {
+            int64_t v = dirs[c.dirs_off + (int64_t)di * c.d + l] % p;
+            ubuf[c.u_off + l] = v < 0 ? v + p : v;
+          }
+        }
+        const int K = a.force ? a.force_K : r.k_sig + min(r.K_reg, c.reg_cap);
+        r.logL = ceil_log2(2 * p - 1);
+        if (r.logL < 1) r.logL = 1;
+        r.big = r.logL > a.single_max_logL;
+        r.groups = (c.n_sets + kMaxSetGroup - 1) / kMaxSetGroup;
+        r.gsize = (c.n_sets + r.groups - 1) / r.groups;
+        r.n_xt = (int)((p + tile_x(r.gsize) - 1) / tile_x(r.gsize));
+        r.chunks = K > 0 ? (K + kSampleChunk - 1) / kSampleChunk : 1;
+        r.any_occupied = 0;
+        r.n_acc = 0;
+        r.maxy0_bits = 0ull;
+        r.samples += (int64_t)c.n_sets * p;
+        r.terms += (int64_t)c.n_sets * p * K;
+        if (s == 0 && hist != nullptr && i <= SFFT_STATS_MAX_ROUNDS) {
+          hist[i - 1].p = p;
+          hist[i - 1].K = K;
+          hist[i - 1].accepted = 0;
+          hist[i - 1].live = r.n_live;
+        }
+      }
+    }
+    run[s] = r;
+    if (r.active) {
+      tiles += (int64_t)r.n_xt * r.groups;
+      active += 1;
+    }
+  }
+  __syncthreads();
+  const int64_t tot_tiles = block_sum(tiles);
+  const int64_t tot_active = block_sum(active);
+  // mode splits: enough sampling items to fill the GPU, within the partial-sum arena
+  if (threadIdx.x == 0) {
+    const int64_t target = 8LL * a.n_sm;
+    int64_t S = tot_tiles > 0 ? (target + tot_tiles - 1) / tot_tiles : 1;
+    s_S = (int)min(max(S, (int64_t)1), (int64_t)64);
+  }
+  __syncthreads();
+  for (;;) {
+    const int S = s_S;
+    int64_t part = 0;
+    for (int s = threadIdx.x; s < n; s += blockDim.x) {
+      const SigRun& r = run[s];
+      if (!r.active) continue;
+      part += (int64_t)min(S, r.chunks) * cfg[s].n_sets * r.p;
+    }
+    const int64_t tot = block_sum(part);
+    __syncthreads();
+    if (tot <= a.part_cap || S == 1) break;
+    if (threadIdx.x == 0) s_S = S / 2;
+    __syncthreads();
+  }
+  const int S = s_S;
+  // pass 2: per-signal work counts and their exclusive scans
+  int64_t carry[kNumScans];
+  for (int q = 0; q < kNumScans; ++q) carry[q] = 0;
+  int64_t part_carry = 0;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int s = base + threadIdx.x;
+    int64_t v[kNumScans + 1];
+    for (int q = 0; q <= kNumScans; ++q) v[q] = 0;
+    SigRun r;
+    if (s < n) {
+      r = run[s];
+      if (r.active) {
+        const SigCfg& c = cfg[s];
+        const int K = a.force ? a.force_K : r.k_sig + min(r.K_reg, c.reg_cap);
+        int sp = min(S, r.chunks);
+        r.jper = ((r.chunks + sp - 1) / sp) * kSampleChunk;
+        r.splits = K > 0 ? (K + r.jper - 1) / r.jper : 1;
+        v[SC_TAB] = r.p;
+        v[SC_MODE] = K;
+        v[SC_SAMP0 + r.gsize - 1] = (int64_t)r.n_xt * r.groups * r.splits;
+        v[SC_BINS] = r.p;
+        if (!r.big) {
+          v[SC_ROWS] = c.n_sets;
+          v[SC_FILT] = 1;
+        } else {
+          int M1, M2, CT, RT;
+          big_geom(r.logL, &M1, &M2, &CT, &RT);
+          v[SC_BIGA] = (int64_t)(c.n_sets + 1) * (M2 / CT);
+          v[SC_BIGB] = (int64_t)c.n_sets * (M1 / RT);
+          v[SC_BIGC] = (int64_t)c.n_sets * (M2 / CT);
+        }
+        v[kNumScans] = (int64_t)r.splits * c.n_sets * r.p;
+      }
+    }
+    int64_t tot[kNumScans + 1];
+    block_scan_excl<kNumScans + 1>(v, tot);
+    if (s < n) {
+      for (int q = 0; q < kNumScans; ++q) sc.v[q][s] = carry[q] + v[q];
+      if (r.active) {
+        r.part_off = part_carry + v[kNumScans];
+        run[s] = r;
+      }
+    }
+    for (int q = 0; q < kNumScans; ++q) carry[q] += tot[q];
+    part_carry += tot[kNumScans];
+  }
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kNumScans; ++q) sc.v[q][n] = carry[q];
+    RoundCtl c;
+    c.active = (int)tot_active;
+    c.round = ctl->round + 1;
+    c.splits = S;
+    c.pad = 0;
+    c.n_tab = carry[SC_TAB];
+    c.n_mode = carry[SC_MODE];
+    for (int q = 0; q < kMaxSetGroup; ++q) {
+      c.n_samp[q] = carry[SC_SAMP0 + q];
+      c.ctr_samp[q] = 0ull;
+    }
+    c.n_rows = carry[SC_ROWS];
+    c.n_filt = carry[SC_FILT];
+    c.n_bins = carry[SC_BINS];
+    c.n_bigA = carry[SC_BIGA];
+    c.n_bigB = carry[SC_BIGB];
+    c.n_bigC = carry[SC_BIGC];
+    c.ctr_rows = c.ctr_filt = 0ull;
+    *ctl = c;
+    if (a.use_cond) cudaGraphSetConditional(a.cond, tot_active > 0 ? 1u : 0u);
+  }
+}
+
+// ------------------------------------------------------------------ tables
+
+// Per-prime tables (W, chirp) and the round's mode projections: for every mode j of f (+a)
+// and of the registry (-a): alpha_j = (w_j . u) mod p, ga_j = 32 alpha_j mod p and
+// C[n][j] = a_j e^{2 pi i w_{j,n} / N} (n >= 1), C[0][j] = a_j.
+template <typename T>
+__global__ void k_tables(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run,
+                         const RoundCtl* __restrict__ ctl, Scans sc, c2<T>* __restrict__ tab,
+                         const int64_t* __restrict__ ubuf, const int32_t* const* __restrict__ sig_w,
+                         const double2* const* __restrict__ sig_a, const c2<T>* __restrict__ tw,
+                         const int32_t* __restrict__ regw, const double2* __restrict__ rega,
+                         const c2<T>* __restrict__ regtw, int32_t* __restrict__ alpha, int32_t* __restrict__ gam,
+                         c2<T>* __restrict__ Cm) {
+  const int64_t ntab = ctl->n_tab;
+  const int64_t total = ntab + ctl->n_mode;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < ntab) {
+      const int s = find_slot(sc.v[SC_TAB], n, e);
+      const int64_t m = e - sc.v[SC_TAB][s];
+      const int64_t p = run[s].p;
+      c2<T>* t = tab + cfg[s].tab_off;
+      t[m] = unit_root<T>(m, p);
+      // x^2 mod 2p from x^2 mod p: of r and r + p the one with the parity of x (p odd)
+      uint64_t r2;
+      if (p == 2) {
+        r2 = ((uint64_t)m * (uint64_t)m) % 4u;
+      } else {
+        const uint64_t r = mod_barrett((uint64_t)m * (uint64_t)m, (uint64_t)p, run[s].mod_m);
+        r2 = ((r ^ (uint64_t)m) & 1u) ? r + (uint64_t)p : r;
+      }
+      t[p + m] = cconj(unit_root<T>((int64_t)r2, 2 * p));
+      continue;
+    }
+    const int64_t em = e - ntab;
+    const int s = find_slot(sc.v[SC_MODE], n, em);
+    const int j = (int)(em - sc.v[SC_MODE][s]);
+    const SigCfg& c = cfg[s];
+    const SigRun& r = run[s];
+    const uint64_t up = (uint64_t)r.p, mm = r.mod_m;
+    const int64_t* u = ubuf + c.u_off;
+    const int d = c.d;
+    const int32_t* w;
+    double2 a;
+    const c2<T>* twr;
+    if (j < r.k_sig) {
+      w = sig_w[s] + (int64_t)j * d;
+      a = sig_a[s][j];
+      twr = tw + c.tw_off + (int64_t)j * d;
+    } else {
+      const int jr = j - r.k_sig;
+      w = regw + c.regw_off + (int64_t)jr * d;
+      a = rega[c.rega_off + jr];
+      a.x = -a.x;   // registry modes: f - g
+      a.y = -a.y;
+      twr = regtw + c.regtw_off + (int64_t)jr * d;
+    }
+    // (w . u) = sum (w_l - box_lo) u_l + box_lo sum u_l, all reduced mod p
+    uint64_t acc = 0, usum = 0;
+    for (int l = 0; l < d; ++l) {
+      acc = mod_barrett((uint64_t)(int64_t)(w[l] - c.box_lo) * (uint64_t)u[l] + acc, up, mm);
+      usum += (uint64_t)u[l];
+    }
+    const int64_t blm = ((int64_t)c.box_lo % r.p + r.p) % r.p;
+    acc = mod_barrett(acc + mod_barrett((uint64_t)blm * mod_barrett(usum, up, mm), up, mm), up, mm);
+    alpha[c.mode_off + j] = (int32_t)acc;
+    gam[c.mode_off + j] = (int32_t)mod_barrett(acc * 32u, up, mm);
+    const c2<T> a0 = mk2((T)a.x, (T)a.y);
+    c2<T>* crow = Cm + c.C_off + j;
+    crow[0] = a0;
+    for (int nn = 1; nn < c.n_sets; ++nn) crow[(int64_t)nn * c.Kmax] = cmul(a0, twr[nn - 1]);
+  }
+}
+
+// ------------------------------------------------------------------ sampling
+
+template <typename T, int NS>
+struct SampleSmem {
+  c2<T> Ls[kSampleChunk][32];
+  c2<T> Us[kSampleChunk][4 * rows_per_warp(NS)];
+  c2<T> Cs[kSampleChunk][NS];
+  int al[kSampleChunk], be[kSampleChunk], ga[kSampleChunk];
+  int64_t item;
+};
+
+// One tile: 32 * 4 * RW samples x the sets of one group x the modes of one split.
+// Each 32-mode chunk is summed into fresh accumulators that are then added to the
+// running totals (blocked summation), which keeps the float rounding of long mode
+// sums near that of the individual terms.
+template <typename T, int NS>
+__device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun& r, int xt, int g, int split,
+                            const int32_t* __restrict__ alpha, const int32_t* __restrict__ gam,
+                            const c2<T>* __restrict__ Cm, const c2<T>* __restrict__ W, c2<T>* __restrict__ part) {
+  using C2 = c2<T>;
+  constexpr int RW = rows_per_warp(NS);
+  constexpr int TX = tile_x(NS);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int p = (int)r.p;
+  const float inv_p = 1.0f / (float)p;
+  const int n0 = g * r.gsize;
+  const int ns_valid = min(r.gsize, c.n_sets - n0);
+  const int K = r.k_sig + min(r.K_reg, c.reg_cap);
+  const int x0 = xt * TX;
+  const int j_begin = split * r.jper;
+  const int j_end = min(K, j_begin + r.jper);
+  const C2 zero = mk2((T)0, (T)0);
+
+  T tot[RW][NS][2];
+#pragma unroll
+  for (int q = 0; q < RW; ++q)
+#pragma unroll
+    for (int nn = 0; nn < NS; ++nn) tot[q][nn][0] = tot[q][nn][1] = (T)0;
+
+  for (int jc = j_begin; jc < j_end; jc += kSampleChunk) {
+    const int nj = min(kSampleChunk, j_end - jc);
+    if (tid < kSampleChunk) {
+      const int al = (tid < nj) ? alpha[jc + tid] : 0;
+      sm.al[tid] = al;
+      sm.ga[tid] = (tid < nj) ? gam[jc + tid] : 0;
+      sm.be[tid] = (int)mod_barrett((uint64_t)al * (uint64_t)x0, (uint64_t)p, r.mod_m);
+    }
+    for (int e = tid; e < kSampleChunk * NS; e += kSampleThreads) {
+      const int jj = e / NS, nn = e - jj * NS;
+      sm.Cs[jj][nn] = (jj < nj && nn < ns_valid) ? Cm[(int64_t)(n0 + nn) * c.Kmax + jc + jj] : zero;
+    }
+    __syncthreads();
+    for (int e = tid; e < kSampleChunk * 32; e += kSampleThreads) {
+      const int jj = e >> 5, ln = e & 31;
+      sm.Ls[jj][ln] = W[mod_small((unsigned)sm.al[jj] * (unsigned)ln, p, inv_p)];
+    }
+    for (int e = tid; e < kSampleChunk * 4 * RW; e += kSampleThreads) {
+      const int jj = e / (4 * RW), row = e - jj * (4 * RW);
+      sm.Us[jj][row] = W[mod_small((unsigned)sm.be[jj] + (unsigned)row * (unsigned)sm.ga[jj], p, inv_p)];
+    }
+    __syncthreads();
+    T acc[RW][NS][2];
+#pragma unroll
+    for (int q = 0; q < RW; ++q)
+#pragma unroll
+      for (int nn = 0; nn < NS; ++nn) acc[q][nn][0] = acc[q][nn][1] = (T)0;
+#pragma unroll 2
+    for (int jj = 0; jj < kSampleChunk; ++jj) {
+      const C2 L = sm.Ls[jj][lane];
+      C2 E[RW];
+#pragma unroll
+      for (int q = 0; q < RW; ++q) E[q] = cmul(sm.Us[jj][warp * RW + q], L);
+#pragma unroll
+      for (int nn = 0; nn < NS; ++nn) {
+        const C2 cc = sm.Cs[jj][nn];
+#pragma unroll
+        for (int q = 0; q < RW; ++q) {
+          acc[q][nn][0] = fma(cc.x, E[q].x, acc[q][nn][0]);
+          acc[q][nn][0] = fma(-cc.y, E[q].y, acc[q][nn][0]);
+          acc[q][nn][1] = fma(cc.x, E[q].y, acc[q][nn][1]);
+          acc[q][nn][1] = fma(cc.y, E[q].x, acc[q][nn][1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RW; ++q)
+#pragma unroll
+      for (int nn = 0; nn < NS; ++nn) {
+        tot[q][nn][0] += acc[q][nn][0];
+        tot[q][nn][1] += acc[q][nn][1];
+      }
+    __syncthreads();
+  }
+  C2* out = part + r.part_off;
+#pragma unroll
+  for (int q = 0; q < RW; ++q) {
+    const int x = x0 + (warp * RW + q) * 32 + lane;
+    if (x < p) {
+#pragma unroll
+      for (int nn = 0; nn < NS; ++nn)
+        if (nn < ns_valid) out[((int64_t)split * c.n_sets + n0 + nn) * p + x] = mk2(tot[q][nn][0], tot[q][nn][1]);
+    }
+  }
+}
+
+// Persistent sampling kernel for the signals whose set groups hold NS sets.
+template <typename T, int NS>
+__global__ void __launch_bounds__(kSampleThreads, 4) k_sample(int n, const SigCfg* __restrict__ cfg,
+                                                           const SigRun* __restrict__ run, RoundCtl* ctl, Scans sc,
+                                                           const int32_t* __restrict__ alpha,
+                                                           const int32_t* __restrict__ gam,
+                                                           const c2<T>* __restrict__ Cm,
+                                                           const c2<T>* __restrict__ tab, c2<T>* __restrict__ part) {
+  __shared__ SampleSmem<T, NS> sm;
+  const int64_t total = ctl->n_samp[NS - 1];
+  const int64_t* scan = sc.v[SC_SAMP0 + NS - 1];
+  for (;;) {
+    if (threadIdx.x == 0) sm.item = (int64_t)atomicAdd(&ctl->ctr_samp[NS - 1], 1ull);
+    __syncthreads();
+    const int64_t item = sm.item;
+    __syncthreads();
+    if (item >= total) break;
+    const int s = find_slot(scan, n, item);
+    const int64_t local = item - scan[s];
+    const SigCfg& c = cfg[s];
+    const SigRun r = run[s];
+    const int xt = (int)(local % r.n_xt);
+    const int64_t rest = local / r.n_xt;
+    const int g = (int)(rest % r.groups);
+    const int split = (int)(rest / r.groups);
+    sample_tile<T, NS>(sm, c, r, xt, g, split, alpha + c.mode_off, gam + c.mode_off, Cm + c.C_off,
+                      tab + c.tab_off, part);
+  }
+}
+
+// sum of the split partials into y (step calls)
+template <typename T>
+__global__ void k_reduce(const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run, int n_rows,
+                         const c2<T>* __restrict__ part, c2<T>* __restrict__ y) {
+  const SigRun& r = run[0];
+  const int ns = cfg[0].n_sets;
+  const int64_t total = (int64_t)n_rows * r.p;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    c2<T> acc = part[r.part_off + e];
+    for (int q = 1; q < r.splits; ++q) acc = cadd(acc, part[r.part_off + (int64_t)q * ns * r.p + e]);
+    y[e] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ DFT, one block per row
+
+template <typename T>
+__device__ __forceinline__ c2<T> filter_value(int64_t x, int64_t p, int64_t L, const c2<T>* chirp) {
+  if (x < p) return cconj(chirp[x]);
+  if (x > L - p) return cconj(chirp[L - x]);
+  return mk2((T)0, (T)0);
+}
+
+template <typename T>
+__device__ __forceinline__ c2<T> sum_splits(const c2<T>* __restrict__ part, const SigRun& r, int n_sets, int row,
+                                            int64_t x) {
+  c2<T> acc = part[r.part_off + (int64_t)row * r.p + x];
+  for (int q = 1; q < r.splits; ++q) acc = cadd(acc, part[r.part_off + ((int64_t)q * n_sets + row) * r.p + x]);
+  return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ void max_abs_to(unsigned long long* dst, double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v > 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(v));
+}
+
+// spectrum of the Bluestein filter b[m] = conj(chirp[|m|]), |m| < p, one block per signal
+template <typename T>
+__global__ void k_filter(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run, RoundCtl* ctl,
+                         Scans sc, const c2<T>* __restrict__ tab, const c2<T>* __restrict__ twG, int64_t Lmax,
+                         c2<T>* __restrict__ bhat) {
+  using C2 = c2<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int64_t s_item;
+  C2* buf = reinterpret_cast<C2*>(smem_raw);
+  const int64_t total = ctl->n_filt;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(&ctl->ctr_filt, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    __syncthreads();
+    if (item >= total) break;
+    const int s = find_slot(sc.v[SC_FILT], n, item);
+    const SigCfg& c = cfg[s];
+    const SigRun& r = run[s];
+    const int logL = r.logL, L = 1 << logL;
+    C2* tw = buf + L;
+    const C2* chirp = tab + c.tab_off + r.p;
+    for (int j = threadIdx.x; j < L / 2; j += blockDim.x) tw[j] = twG[(int64_t)j * (Lmax >> logL)];
+    for (int x = threadIdx.x; x < L; x += blockDim.x) buf[brev_bits(x, logL)] = filter_value<T>(x, r.p, L, chirp);
+    __syncthreads();
+    fft_dit(buf, L, logL, 1, tw, false);
+    C2* out = bhat + c.bhat_off;
+    for (int x = threadIdx.x; x < L; x += blockDim.x) out[x] = buf[x];
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_dft(int n, const SigCfg* __restrict__ cfg, SigRun* run, RoundCtl* ctl, Scans sc,
+                      const c2<T>* __restrict__ part, const c2<T>* __restrict__ tab,
+                      const c2<T>* __restrict__ bhat, const c2<T>* __restrict__ twG, int64_t Lmax,
+                      c2<T>* __restrict__ Y) {
+  using C2 = c2<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int64_t s_item;
+  C2* buf = reinterpret_cast<C2*>(smem_raw);
+  const int64_t total = ctl->n_rows;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(&ctl->ctr_rows, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    __syncthreads();
+    if (item >= total) break;
+    const int s = find_slot(sc.v[SC_ROWS], n, item);
+    const int row = (int)(item - sc.v[SC_ROWS][s]);
+    const SigCfg& c = cfg[s];
+    const SigRun r = run[s];
+    const int logL = r.logL, L = 1 << logL;
+    const int64_t p = r.p;
+    C2* tw = buf + L;
+    const C2* chirp = tab + c.tab_off + p;
+    const C2* B = bhat + c.bhat_off;
+    for (int j = threadIdx.x; j < L / 2; j += blockDim.x) tw[j] = twG[(int64_t)j * (Lmax >> logL)];
+    for (int x = threadIdx.x; x < L; x += blockDim.x) {
+      C2 v = mk2((T)0, (T)0);
+      if (x < p) v = cmul(chirp[x], sum_splits<T>(part, r, c.n_sets, row, x));
+      buf[brev_bits(x, logL)] = v;
+    }
+    __syncthreads();
+    fft_dit(buf, L, logL, 1, tw, false);
+    for (int k = threadIdx.x; k < L; k += blockDim.x) buf[k] = cmul(buf[k], B[k]);
+    __syncthreads();
+    fft_dif(buf, L, logL, 1, tw, true);
+    const T invL = (T)1 / (T)L;
+    C2* out = Y + c.Y_off + (int64_t)row * p;
+    for (int64_t h0 = 0; h0 < p; h0 += blockDim.x) {
+      const int64_t h = h0 + threadIdx.x;
+      double m = 0.0;
+      if (h < p) {
+        const C2 v = cmul(chirp[h], cscale(buf[brev_bits((int)h, logL)], invL));
+        out[h] = v;
+        m = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+      }
+      if (row == 0) max_abs_to<T>(&run[s].maxy0_bits, sqrt(m));
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ DFT, four-step passes for long lengths
+
+template <typename T>
+__global__ void k_bigA(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run,
+                       const RoundCtl* __restrict__ ctl, Scans sc, const c2<T>* __restrict__ part,
+                       const c2<T>* __restrict__ tab, const c2<T>* __restrict__ twG, int64_t Lmax,
+                       c2<T>* __restrict__ Z) {
+  using C2 = c2<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* buf = reinterpret_cast<C2*>(smem_raw);
+  const int64_t total = ctl->n_bigA;
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    const int s = find_slot(sc.v[SC_BIGA], n, item);
+    const int64_t local = item - sc.v[SC_BIGA][s];
+    const SigCfg& c = cfg[s];
+    const SigRun r = run[s];
+    int M1, M2, CT, RT;
+    big_geom(r.logL, &M1, &M2, &CT, &RT);
+    const int logM1 = r.logL / 2;
+    const int64_t L = 1LL << r.logL;
+    const int ntile = M2 / CT;
+    const int row = (int)(local / ntile);
+    const int x2_0 = (int)(local % ntile) * CT;
+    const int ls = M1 + 1;
+    C2* tw = buf + CT * ls;
+    const C2* chirp = tab + c.tab_off + r.p;
+    for (int j = threadIdx.x; j < M1 / 2; j += blockDim.x) tw[j] = twG[(int64_t)j * (Lmax >> logM1)];
+    for (int e = threadIdx.x; e < CT * M1; e += blockDim.x) {
+      const int x1 = e / CT, cc = e - x1 * CT;
+      const int64_t x = (int64_t)x1 * M2 + x2_0 + cc;
+      C2 v;
+      if (row < c.n_sets) {
+        v = mk2((T)0, (T)0);
+        if (x < r.p) v = cmul(chirp[x], sum_splits<T>(part, r, c.n_sets, row, x));
+      } else {
+        v = filter_value<T>(x, r.p, L, chirp);
+      }
+      buf[cc * ls + brev_bits(x1, logM1)] = v;
+    }
+    __syncthreads();
+    fft_dit(buf, ls, logM1, CT, tw, false);
+    C2* z = Z + c.z_off + (int64_t)row * L;
+    const int64_t tstep = Lmax >> r.logL;
+    for (int e = threadIdx.x; e < CT * M1; e += blockDim.x) {
+      const int k1 = e / CT, cc = e - k1 * CT;
+      const int64_t x2 = x2_0 + cc;
+      const int64_t m = (x2 * k1) & (L - 1);
+      z[(int64_t)k1 * M2 + x2] = cmul(buf[cc * ls + k1], twG[m * tstep]);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_bigB(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run,
+                       const RoundCtl* __restrict__ ctl, Scans sc, const c2<T>* __restrict__ twG, int64_t Lmax,
+                       c2<T>* __restrict__ Z) {
+  using C2 = c2<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* buf = reinterpret_cast<C2*>(smem_raw);
+  const int64_t total = ctl->n_bigB;
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    const int s = find_slot(sc.v[SC_BIGB], n, item);
+    const int64_t local = item - sc.v[SC_BIGB][s];
+    const SigCfg& c = cfg[s];
+    const SigRun r = run[s];
+    int M1, M2, CT, RT;
+    big_geom(r.logL, &M1, &M2, &CT, &RT);
+    const int logM2 = r.logL - r.logL / 2;
+    const int64_t L = 1LL << r.logL;
+    const int ntile = M1 / RT;
+    const int row = (int)(local / ntile);
+    const int k1_0 = (int)(local % ntile) * RT;
+    const int ls = M2 + 1;
+    C2* bufF = buf + RT * ls;
+    C2* tw = buf + 2 * RT * ls;
+    for (int j = threadIdx.x; j < M2 / 2; j += blockDim.x) tw[j] = twG[(int64_t)j * (Lmax >> logM2)];
+    C2* zr = Z + c.z_off + (int64_t)row * L;
+    const C2* zf = Z + c.z_off + (int64_t)c.n_sets * L;
+    for (int e = threadIdx.x; e < RT * M2; e += blockDim.x) {
+      const int rr = e / M2, x2 = e - rr * M2;
+      const int64_t off = (int64_t)(k1_0 + rr) * M2 + x2;
+      buf[rr * ls + brev_bits(x2, logM2)] = zr[off];
+      bufF[rr * ls + brev_bits(x2, logM2)] = zf[off];
+    }
+    __syncthreads();
+    fft_dit(buf, ls, logM2, 2 * RT, tw, false);
+    for (int e = threadIdx.x; e < RT * M2; e += blockDim.x) {
+      const int rr = e / M2, k2 = e - rr * M2;
+      buf[rr * ls + k2] = cmul(buf[rr * ls + k2], bufF[rr * ls + k2]);
+    }
+    __syncthreads();
+    fft_dif(buf, ls, logM2, RT, tw, true);
+    const int64_t tstep = Lmax >> r.logL;
+    for (int e = threadIdx.x; e < RT * M2; e += blockDim.x) {
+      const int rr = e / M2, x2 = e - rr * M2;
+      const int64_t k1 = k1_0 + rr;
+      const int64_t m = ((int64_t)x2 * k1) & (L - 1);
+      zr[k1 * M2 + x2] = cmul(buf[rr * ls + brev_bits(x2, logM2)], cconj(twG[m * tstep]));
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_bigC(int n, const SigCfg* __restrict__ cfg, SigRun* run, const RoundCtl* __restrict__ ctl, Scans sc,
+                       const c2<T>* __restrict__ tab, const c2<T>* __restrict__ twG, int64_t Lmax,
+                       const c2<T>* __restrict__ Z, c2<T>* __restrict__ Y) {
+  using C2 = c2<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* buf = reinterpret_cast<C2*>(smem_raw);
+  const int64_t total = ctl->n_bigC;
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    const int s = find_slot(sc.v[SC_BIGC], n, item);
+    const int64_t local = item - sc.v[SC_BIGC][s];
+    const SigCfg& c = cfg[s];
+    const SigRun r = run[s];
+    int M1, M2, CT, RT;
+    big_geom(r.logL, &M1, &M2, &CT, &RT);
+    const int logM1 = r.logL / 2;
+    const int64_t L = 1LL << r.logL;
+    const int ntile = M2 / CT;
+    const int row = (int)(local / ntile);
+    const int x2_0 = (int)(local % ntile) * CT;
+    const int ls = M1 + 1;
+    C2* tw = buf + CT * ls;
+    const C2* chirp = tab + c.tab_off + r.p;
+    for (int j = threadIdx.x; j < M1 / 2; j += blockDim.x) tw[j] = twG[(int64_t)j * (Lmax >> logM1)];
+    const C2* z = Z + c.z_off + (int64_t)row * L;
+    for (int e = threadIdx.x; e < CT * M1; e += blockDim.x) {
+      const int k1 = e / CT, cc = e - k1 * CT;
+      buf[cc * ls + k1] = z[(int64_t)k1 * M2 + x2_0 + cc];
+    }
+    __syncthreads();
+    fft_dif(buf, ls, logM1, CT, tw, true);
+    const T invL = (T)1 / (T)L;
+    C2* out = Y + c.Y_off + (int64_t)row * r.p;
+    const int tot = CT * M1;
+    for (int e0 = 0; e0 < tot; e0 += blockDim.x) {
+      const int e = e0 + threadIdx.x;
+      double m = 0.0;
+      if (e < tot) {
+        const int x1 = e / CT, cc = e - x1 * CT;
+        const int64_t x = (int64_t)x1 * M2 + x2_0 + cc;
+        if (x < r.p) {
+          const C2 v = cmul(chirp[x], cscale(buf[cc * ls + brev_bits(x1, logM1)], invL));
+          out[x] = v;
+          m = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        }
+      }
+      if (row == 0) max_abs_to<T>(&run[s].maxy0_bits, sqrt(m));
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ classification and registry merge
+
+__device__ __forceinline__ unsigned long long hash_key(const int32_t* w, int d) {
+  unsigned long long h = 0x9E3779B97F4A7C15ull ^ (unsigned long long)d;
+  for (int l = 0; l < d; ++l) {
+    h ^= (unsigned long long)(uint32_t)w[l];
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 32;
+  }
+  h ^= h >> 29;
+  h *= 0xc4ceb9fe1a85ec53ull;
+  h ^= h >> 32;
+  return h;
+}
+
+// Arg(Y_n / Y_0) in [-pi, pi) read as N Arg / (2 pi); false when farther than delta from an integer.
+template <typename R>
+__device__ __forceinline__ bool read_coord(R ynx, R yny, R y0x, R y0y, int64_t N, int box_lo, R delta,
+                                           int64_t* w_out) {
+  const R re = ynx * y0x + yny * y0y;   // Y_n conj(Y_0)
+  const R im = yny * y0x - ynx * y0y;
+  const R pi = (R)3.14159265358979323846;
+  R phi = atan2(im, re);
+  if (phi >= pi) phi -= (R)2 * pi;
+  const R v = (R)N * phi / ((R)2 * pi);
+  const R rr = rint(v);
+  if (!(fabs(v - rr) <= delta)) return false;
+  int64_t wn = ((int64_t)rr - box_lo) % N;
+  if (wn < 0) wn += N;
+  *w_out = wn + box_lo;
+  return true;
+}
+
+struct ClassifyOut {   // step calls: accepted bins are appended here instead of merged
+  int32_t* h;
+  int32_t* w;
+  double2* a;
+  int cap;
+  int* count;
+  int* err;
+  double eta_override;
+};
+
+template <typename T, typename R>
+__device__ bool decode_bin(const SigCfg& c, const SigRun& r, const c2<T>* Y, const int64_t* u, int64_t h, R y0x,
+                           R y0y, R m0) {
+  const int64_t p = r.p;
+  const uint64_t up = (uint64_t)p;
+  uint64_t bin = 0;
+  uint64_t usum = 0;
+  for (int n = 1; n <= c.d; ++n) {
+    const c2<T> yn = Y[(int64_t)n * p + h];
+    const R ynx = (R)yn.x, yny = (R)yn.y;
+    const R mn = sqrt(ynx * ynx + yny * yny);
+    if (!(fabs(mn / m0 - (R)1) < (R)c.tau)) return false;   // Eq. 42
+    int64_t wn;
+    if (!read_coord<R>(ynx, yny, y0x, y0y, c.N, c.box_lo, (R)c.delta, &wn)) return false;
+    bin = mod_barrett((uint64_t)(wn - c.box_lo) * (uint64_t)u[n - 1] + bin, up, r.mod_m);
+    usum += (uint64_t)u[n - 1];
+  }
+  const int64_t blm = ((int64_t)c.box_lo % p + p) % p;
+  bin = mod_barrett(bin + mod_barrett((uint64_t)blm * mod_barrett(usum, up, r.mod_m), up, r.mod_m), up, r.mod_m);
+  return (int64_t)bin == h;
+}
+
+// Writes the read-out vector of an accepted bin and returns its coefficient estimate
+// (Eq. 41).  With coef_mean the estimate is the mean over the d + 1 sets of
+// Y_n[h] e^{-2 pi i w_n / N} / p: for a bin holding one mode every term equals a
+// exactly, and the mean averages the sets' independent rounding (and the leakage
+// of other modes' residuals, whose phases differ across the sets).
+template <typename T, typename R>
+__device__ double2 read_out(const SigCfg& c, const SigRun& r, const c2<T>* Y, int64_t h, R y0x, R y0y,
+                            int32_t* w_out) {
+  R ax = y0x, ay = y0y;
+  for (int n = 1; n <= c.d; ++n) {
+    const c2<T> yn = Y[(int64_t)n * r.p + h];
+    int64_t wn = 0;
+    read_coord<R>((R)yn.x, (R)yn.y, y0x, y0y, c.N, c.box_lo, (R)c.delta, &wn);
+    w_out[n - 1] = (int32_t)wn;
+    if (c.coef_mean) {
+      int64_t m = wn % c.N;
+      if (m < 0) m += c.N;
+      const c2<R> t = unit_root<R>(m, c.N);   // e^{2 pi i w_n / N}
+      ax += (R)yn.x * t.x + (R)yn.y * t.y;     // Y_n conj(t)
+      ay += (R)yn.y * t.x - (R)yn.x * t.y;
+    }
+  }
+  const double scale = c.coef_mean ? 1.0 / ((double)r.p * (double)c.n_sets) : 1.0 / (double)r.p;
+  if (!c.coef_mean) {
+    ax = y0x;
+    ay = y0y;
+  }
+  return make_double2((double)ax * scale, (double)ay * scale);
+}
+
+template <typename T>
+__global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, const RoundCtl* __restrict__ ctl,
+                           Scans sc, const c2<T>* __restrict__ Ybuf, const int64_t* __restrict__ ubuf,
+                           int32_t* regw, double2* rega, c2<T>* regtw, int32_t* hash, ClassifyOut co) {
+  const int64_t total = ctl->n_bins;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = find_slot(sc.v[SC_BINS], n, e);
+    const int64_t h = e - sc.v[SC_BINS][s];
+    const SigCfg& c = cfg[s];
+    SigRun* rp = run + s;
+    const SigRun& r = *rp;
+    const int64_t p = r.p;
+    double a_ref;
+    if (r.round == 1) {
+      a_ref = __longlong_as_double((long long)r.maxy0_bits) / (double)p;
+      if (h == 0) rp->a_ref = a_ref;
+    } else {
+      a_ref = r.a_ref;
+    }
+    const double eta = co.eta_override >= 0.0 ? co.eta_override
+                                              : fmax(c.rho * (double)p * a_ref, 6.0 * c.sigma * sqrt((double)p));
+    const c2<T>* Y = Ybuf + c.Y_off;
+    const c2<T> y0 = Y[h];
+    const double m0d = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y);
+    if (!(m0d > eta)) continue;
+    if (!r.any_occupied) rp->any_occupied = 1;
+    const int64_t* u = ubuf + c.u_off;
+    bool ok;
+    if (c.ratio64) ok = decode_bin<T, double>(c, r, Y, u, h, (double)y0.x, (double)y0.y, m0d);
+    else ok = decode_bin<T, T>(c, r, Y, u, h, (T)y0.x, (T)y0.y, (T)m0d);
+    if (!ok) continue;
+    atomicAdd(&rp->n_acc, 1);
+    if (co.count != nullptr) {
+      const int idx = atomicAdd(co.count, 1);
+      if (idx >= co.cap) {
+        atomicOr(co.err, 1);
+        continue;
+      }
+      co.h[idx] = (int32_t)h;
+      if (c.ratio64) co.a[idx] = read_out<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, co.w + (int64_t)idx * c.d);
+      else co.a[idx] = read_out<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, co.w + (int64_t)idx * c.d);
+      continue;
+    }
+    // ---- merge into the registry: keys accepted in one round are distinct (each lands in its
+    // own bin) and the table never deletes, so a key is present iff met before the first
+    // empty slot of its probe sequence; one writer per key per round.
+    int32_t wk[64];
+    const int dd = c.d;
+    int32_t* rw = regw + c.regw_off;
+    double2* ra = rega + c.rega_off;
+    c2<T>* rt = regtw + c.regtw_off;
+    int32_t* hs = hash + c.hash_off;
+    const double eta_prune = fmax(c.rho * a_ref, 6.0 * c.sigma / sqrt((double)p));
+    // decoded vector: up to 64 coordinates in registers, else read back from the registry slot
+    int32_t* wv = wk;
+    int scratch_idx = -1;
+    if (dd > 64) {
+      scratch_idx = atomicAdd(&rp->K_reg, 1);
+      if (scratch_idx >= c.reg_cap) {
+        atomicOr(&rp->err, 1);
+        continue;
+      }
+      wv = rw + (int64_t)scratch_idx * dd;
+    }
+    double2 a;
+    if (c.ratio64) a = read_out<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wv);
+    else a = read_out<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wv);
+    int slot = (int)(hash_key(wv, dd) & (unsigned long long)c.hash_mask);
+    int mine = scratch_idx;
+    bool placed = false, merged = false, past_empty = false;
+    for (int probe = 0; probe <= c.hash_mask; ++probe, slot = (slot + 1) & c.hash_mask) {
+      int cur = atomicAdd(&hs[slot], 0);
+      if (cur < 0) {
+        past_empty = true;   // the key is not in the table
+        if (mine < 0) {
+          mine = atomicAdd(&rp->K_reg, 1);
+          if (mine >= c.reg_cap) {
+            atomicOr(&rp->err, 1);
+            break;
+          }
+          for (int l = 0; l < dd; ++l) rw[(int64_t)mine * dd + l] = wv[l];
+        }
+        ra[mine] = a;
+        for (int l = 0; l < dd; ++l) {
+          int64_t m = (int64_t)wv[l] % c.N;
+          if (m < 0) m += c.N;
+          rt[(int64_t)mine * dd + l] = unit_root<T>(m, c.N);
+        }
+        __threadfence();
+        cur = atomicCAS(&hs[slot], -1, mine);
+        if (cur < 0) {
+          placed = true;
+          break;
+        }
+        continue;   // slot taken by another new key of this round
+      }
+      if (past_empty) continue;   // only new keys of this round lie beyond an empty slot
+      __threadfence();
+      const volatile int32_t* ow = rw + (int64_t)cur * dd;
+      bool same = true;
+      for (int l = 0; l < dd && same; ++l) same = (ow[l] == wv[l]);
+      if (same) {
+        const double2 old = ra[cur];
+        double2 nw = make_double2(old.x + a.x, old.y + a.y);   // duplicate key: a_R += a
+        const bool was_live = (old.x != 0.0 || old.y != 0.0);
+        const bool live = sqrt(nw.x * nw.x + nw.y * nw.y) >= eta_prune;   // prune small coefficients
+        if (!live) nw = make_double2(0.0, 0.0);
+        ra[cur] = nw;
+        if (was_live && !live) atomicSub(&rp->n_live, 1);
+        if (!was_live && live) atomicAdd(&rp->n_live, 1);
+        merged = true;
+        break;
+      }
+    }
+    if (merged && scratch_idx >= 0) {
+      // the slot that held the decoded vector stays a zero mode
+      ra[scratch_idx] = make_double2(0.0, 0.0);
+      for (int l = 0; l < dd; ++l) rt[(int64_t)scratch_idx * dd + l] = mk2((T)0, (T)0);
+    }
+    if (placed) atomicAdd(&rp->n_live, 1);
+    else if (!merged && mine >= 0 && mine < c.reg_cap) atomicOr(&rp->err, 2);   // table full
+  }
+}
+
+// ------------------------------------------------------------------ outputs
+
+__global__ void k_output(int n, const SigCfg* __restrict__ cfg, SigRun* run, const int32_t* __restrict__ regw,
+                         const double2* __restrict__ rega, const int64_t* __restrict__ bindv, int32_t* out_w,
+                         double2* out_a, int64_t* n_found, int* status, HistRec* hist) {
+  __shared__ int warp_sums[32];
+  __shared__ int64_t base_s;
+  const int s = blockIdx.x;
+  if (s >= n) return;
+  const SigCfg& c = cfg[s];
+  SigRun* rp = run + s;
+  const int nr = min(rp->K_reg, c.reg_cap);
+  if (threadIdx.x == 0) base_s = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int32_t* rw = regw + c.regw_off;
+  const double2* ra = rega + c.rega_off;
+  const int64_t cap = bindv[3 * n + s];
+  int32_t* ow = out_w + bindv[5 * n + s];
+  double2* oa = out_a + bindv[4 * n + s];
+  for (int c0 = 0; c0 < nr; c0 += blockDim.x) {
+    const int i = c0 + threadIdx.x;
+    const bool live = i < nr && (ra[i].x != 0.0 || ra[i].y != 0.0);
+    const unsigned bal = __ballot_sync(0xffffffffu, live);
+    const int before = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) warp_sums[wid] = __popc(bal);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int q = 0; q < nw; ++q) {
+      if (q < wid) off += warp_sums[q];
+      tot += warp_sums[q];
+    }
+    const int64_t pos = base_s + off + before;
+    if (live && pos < cap) {
+      for (int l = 0; l < c.d; ++l) ow[pos * c.d + l] = rw[(int64_t)i * c.d + l];
+      oa[pos] = ra[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base_s += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    n_found[s] = base_s;
+    int st = rp->active ? (int)SFFT_ERR_NOT_CONVERGED : rp->status;
+    if (rp->err) st = SFFT_ERR_CAPACITY;
+    if (st == SFFT_OK && base_s > cap) st = SFFT_ERR_CAPACITY;
+    if (st == SFFT_OK && base_s > c.k) st = SFFT_ERR_INCONSISTENT;
+    status[s] = st;
+    if (s == 0 && hist != nullptr && rp->round >= 1 && rp->round <= SFFT_STATS_MAX_ROUNDS) {
+      hist[rp->round - 1].accepted = rp->n_acc;
+      hist[rp->round - 1].live = rp->n_live;
+    }
+  }
+}
+
+__global__ void k_twiddles(int64_t Lmax, void* twG, int fp64) {
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < Lmax; m += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t mm = (2 * m > Lmax) ? m - Lmax : m;
+    double s, c;
+    sincospi(-2.0 * (double)mm / (double)Lmax, &s, &c);
+    if (fp64) reinterpret_cast<double2*>(twG)[m] = make_double2(c, s);
+    else reinterpret_cast<float2*>(twG)[m] = make_float2((float)c, (float)s);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+std::vector<int32_t> sieve_primes(int64_t lim) {
+  std::vector<char> comp((size_t)lim + 1, 0);
+  std::vector<int32_t> out;
+  for (int64_t q = 2; q <= lim; ++q) {
+    if (comp[q]) continue;
+    out.push_back((int32_t)q);
+    for (int64_t m = q * q; m <= lim; m += q) comp[m] = 1;
+  }
+  return out;
+}
+
+int64_t next_pow2(int64_t v) {
+  int64_t r = 1;
+  while (r < v) r <<= 1;
+  return r;
+}
+
+int log2i(int64_t v) {
+  int r = 0;
+  while ((1LL << r) < v) ++r;
+  return r;
+}
+
+#define ECHK(x)                          \
+  do {                                   \
+    cudaError_t _e = (x);                \
+    if (_e != cudaSuccess) return _e;    \
+  } while (0)
+
+template <typename T>
+class Engine final : public EngineBase {
+ public:
+  using C2 = c2<T>;
+
+  ~Engine() override {
+    if (graph_exec_) cudaGraphExecDestroy(graph_exec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    for (cudaEvent_t e : events_) cudaEventDestroy(e);
+    for (void* q : allocs_) cudaFree(q);
+    if (host_stage_) cudaFreeHost(host_stage_);
+  }
+
+  cudaError_t init(const std::vector<SlotDesc>& slots, cudaStream_t st, bool profile, bool use_graph) {
+    n_ = (int)slots.size();
+    st_ = st;
+    profile_ = profile;
+    use_graph_ = use_graph;
+    ECHK(cudaGetDevice(&dev_));
+    ECHK(cudaDeviceGetAttribute(&n_sm_, cudaDevAttrMultiProcessorCount, dev_));
+    std::vector<SigCfg> cfg(n_);
+    std::vector<int64_t> dirs, plist;
+    int64_t tw = 0, regw = 0, rega = 0, hashn = 0, tab = 0, bhat = 0, Y = 0, z = 0, u = 0, part_min = 0;
+    int64_t modes = 0, cm = 0;
+    int64_t pmax_all = 2;
+    const int single_logL = log2i(single_max_L<T>());
+    for (int s = 0; s < n_; ++s) {
+      const SlotDesc& d = slots[s];
+      SigCfg& c = cfg[s];
+      std::memset(&c, 0, sizeof(c));
+      c.d = d.d;
+      c.n_sets = d.d + 1;
+      c.k = (int)d.k;
+      c.c = d.c;
+      c.max_rounds = d.max_rounds;
+      c.n_dirs = d.n_dirs;
+      c.n_primes = (int)d.primes.size();
+      c.box_lo = d.box_lo;
+      c.ratio64 = d.ratio64;
+      c.coef_mean = d.coef_mean;
+      c.N = d.N;
+      c.p_max = d.p_max;
+      c.tau = d.tau;
+      c.rho = d.rho;
+      c.delta = d.delta;
+      c.sigma = d.sigma;
+      c.reg_cap = (int)std::min<int64_t>(2 * d.k + 256, 1LL << 30);
+      c.hash_mask = (int)next_pow2(2 * (int64_t)c.reg_cap) - 1;
+      const int64_t Lmax = next_pow2(2 * d.p_max - 1);
+      c.logL_max = log2i(Lmax);
+      c.dirs_off = (int64_t)dirs.size();
+      dirs.insert(dirs.end(), d.dirs.begin(), d.dirs.end());
+      c.primes_off = (int64_t)plist.size();
+      plist.insert(plist.end(), d.primes.begin(), d.primes.end());
+      c.tw_off = tw;
+      tw += std::max<int64_t>(d.k, 1) * d.d;
+      c.regw_off = regw;
+      c.regtw_off = regw;
+      regw += (int64_t)c.reg_cap * d.d;
+      c.rega_off = rega;
+      rega += c.reg_cap;
+      c.hash_off = hashn;
+      hashn += (int64_t)c.hash_mask + 1;
+      c.tab_off = tab;
+      tab += 2 * d.p_max;
+      c.bhat_off = bhat;
+      bhat += std::min<int64_t>(Lmax, single_max_L<T>());
+      c.Y_off = Y;
+      Y += (int64_t)c.n_sets * d.p_max;
+      if (c.logL_max > single_logL) {
+        c.z_off = z;
+        z += (int64_t)(c.n_sets + 1) * Lmax;
+        any_big_ = true;
+        logL_big_max_ = std::max(logL_big_max_, c.logL_max);
+      } else {
+        c.z_off = -1;
+      }
+      c.u_off = u;
+      u += d.d;
+      c.Kmax = (int)(d.k + c.reg_cap);
+      c.mode_off = modes;
+      modes += c.Kmax;
+      c.C_off = cm;
+      cm += (int64_t)c.n_sets * c.Kmax;
+      {
+        const int groups = (c.n_sets + kMaxSetGroup - 1) / kMaxSetGroup;
+        const int gsize = (c.n_sets + groups - 1) / groups;
+        ns_mask_ |= 1u << (gsize - 1);
+      }
+      part_min += (int64_t)c.n_sets * d.p_max;
+      pmax_all = std::max(pmax_all, d.p_max);
+      small_logL_max_ = std::max(small_logL_max_, std::min(c.logL_max, single_logL));
+      k_max_ = std::max<int64_t>(k_max_, d.k);
+      kd_max_ = std::max<int64_t>(kd_max_, d.k * d.d);
+      reg_cap_max_ = std::max<int64_t>(reg_cap_max_, c.reg_cap);
+    }
+    cfg_host_ = cfg;
+    Lmax_ = next_pow2(2 * pmax_all - 1);
+    p_max_ = pmax_all;
+    part_cap_ = std::max<int64_t>(part_min, (int64_t)(128ll << 20) / (int64_t)sizeof(C2));
+    hash_total_ = hashn;
+    // prime table up to the largest p any slot can reach
+    std::vector<int32_t> ptab = sieve_primes(pmax_all + 2);
+    n_ptab_ = (int)ptab.size();
+
+    ECHK(alloc(&cfg_, cfg.size() * sizeof(SigCfg)));
+    ECHK(alloc(&run_, n_ * sizeof(SigRun)));
+    ECHK(alloc(&ctl_, sizeof(RoundCtl)));
+    for (int q = 0; q < kNumScans; ++q) ECHK(alloc(&scans_.v[q], (size_t)(n_ + 1) * sizeof(int64_t)));
+    ECHK(alloc(&ptab_, ptab.size() * sizeof(int32_t)));
+    ECHK(alloc(&dirs_, std::max<size_t>(dirs.size(), 1) * sizeof(int64_t)));
+    ECHK(alloc(&plist_, std::max<size_t>(plist.size(), 1) * sizeof(int64_t)));
+    ECHK(alloc(&tw_, (size_t)tw * sizeof(C2)));
+    ECHK(alloc(&regw_, (size_t)regw * sizeof(int32_t)));
+    ECHK(alloc(&regtw_, (size_t)regw * sizeof(C2)));
+    ECHK(alloc(&rega_, (size_t)rega * sizeof(double2)));
+    ECHK(alloc(&hash_, (size_t)hashn * sizeof(int32_t)));
+    ECHK(alloc(&tab_, (size_t)tab * sizeof(C2)));
+    ECHK(alloc(&bhat_, (size_t)bhat * sizeof(C2)));
+    ECHK(alloc(&Y_, (size_t)Y * sizeof(C2)));
+    if (z > 0) ECHK(alloc(&Z_, (size_t)z * sizeof(C2)));
+    ECHK(alloc(&u_, (size_t)u * sizeof(int64_t)));
+    ECHK(alloc(&alpha_, (size_t)modes * sizeof(int32_t)));
+    ECHK(alloc(&gam_, (size_t)modes * sizeof(int32_t)));
+    ECHK(alloc(&Cm_, (size_t)cm * sizeof(C2)));
+    ECHK(alloc(&part_, (size_t)part_cap_ * sizeof(C2)));
+    ECHK(alloc(&twG_, (size_t)Lmax_ * sizeof(C2)));
+    ECHK(alloc(&hist_, SFFT_STATS_MAX_ROUNDS * sizeof(HistRec)));
+    ECHK(alloc(&bind_, (size_t)n_ * kBindArrays * sizeof(int64_t)));
+    ECHK(alloc(&outn_, (size_t)n_ * sizeof(int64_t)));
+    ECHK(alloc(&outst_, (size_t)n_ * sizeof(int)));
+    ECHK(alloc(&stepc_, 2 * sizeof(int)));
+    stage_ctl_ = align16((size_t)n_ * kBindArrays * sizeof(int64_t) + (size_t)64 * sizeof(int64_t));
+    stage_n_ = align16(stage_ctl_ + sizeof(RoundCtl));
+    stage_st_ = align16(stage_n_ + (size_t)n_ * sizeof(int64_t));
+    stage_hist_ = align16(stage_st_ + (size_t)n_ * sizeof(int));
+    host_stage_bytes_ = stage_hist_ + SFFT_STATS_MAX_ROUNDS * sizeof(HistRec);
+    ECHK(cudaMallocHost(&host_stage_, host_stage_bytes_));
+    ECHK(cudaMemcpyAsync(cfg_, cfg.data(), cfg.size() * sizeof(SigCfg), cudaMemcpyHostToDevice, st_));
+    ECHK(cudaMemcpyAsync(ptab_, ptab.data(), ptab.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
+    if (!dirs.empty())
+      ECHK(cudaMemcpyAsync(dirs_, dirs.data(), dirs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st_));
+    if (!plist.empty())
+      ECHK(cudaMemcpyAsync(plist_, plist.data(), plist.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st_));
+    k_twiddles<<<(int)std::min<int64_t>((Lmax_ + 255) / 256, 4096), 256, 0, st_>>>(Lmax_, twG_, sizeof(T) == 8);
+    ECHK(cudaGetLastError());
+    // launch shapes
+    small_threads_ = small_logL_max_ >= 12 ? 512 : 256;
+    smem_small_ = (size_t)((1 << small_logL_max_) + (1 << small_logL_max_) / 2) * sizeof(C2);
+    ECHK(cudaFuncSetAttribute(k_filter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_small_));
+    ECHK(cudaFuncSetAttribute(k_dft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_small_));
+    if (any_big_) {
+      size_t sa = 0, sb = 0;
+      for (int lg = single_logL + 1; lg <= logL_big_max_; ++lg) {
+        const int l1 = lg / 2, l2 = lg - l1, M1 = 1 << l1, M2 = 1 << l2;
+        const int CT = std::min(M2, std::max(1, kBigColElems / M1));
+        const int RT = std::min(M1, std::max(1, kBigRowElems / M2));
+        sa = std::max(sa, (size_t)(CT * (M1 + 1) + M1 / 2) * sizeof(C2));
+        sb = std::max(sb, (size_t)(2 * RT * (M2 + 1) + M2 / 2) * sizeof(C2));
+      }
+      smem_bigA_ = sa;
+      smem_bigB_ = sb;
+      ECHK(cudaFuncSetAttribute(k_bigA<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
+      ECHK(cudaFuncSetAttribute(k_bigB<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+      ECHK(cudaFuncSetAttribute(k_bigC<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
+    }
+    if (profile_) {
+      events_.resize((size_t)(SFFT_STATS_MAX_ROUNDS + 4) * 8);
+      for (auto& e : events_) ECHK(cudaEventCreate(&e));
+    }
+    ECHK(cudaStreamSynchronize(st_));
+    return cudaSuccess;
+  }
+
+  size_t device_bytes() const override { return bytes_; }
+  int64_t max_prime() const override { return p_max_; }
+  int64_t mode_capacity() const override { return k_max_ + reg_cap_max_; }
+
+  cudaError_t launch_tables() {
+    k_tables<T><<<4 * n_sm_, 256, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, u_, sig_w_, sig_a_, (C2*)tw_,
+                                            regw_, rega_, (C2*)regtw_, alpha_, gam_, (C2*)Cm_);
+    return cudaGetLastError();
+  }
+
+  // one persistent sampling launch per set-group size present in the batch
+  cudaError_t launch_samples(int64_t* launches) {
+    for (int ns = 1; ns <= kMaxSetGroup; ++ns) {
+      if (!(ns_mask_ & (1u << (ns - 1)))) continue;
+#define SFFT_SAMPLE(NSV)                                                                                        \
+  case NSV:                                                                                                     \
+    k_sample<T, NSV><<<4 * n_sm_, kSampleThreads, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, alpha_, gam_, (C2*)Cm_, \
+                                                            (C2*)tab_, (C2*)part_);                             \
+    break;
+      switch (ns) {
+        SFFT_SAMPLE(1)
+        SFFT_SAMPLE(2)
+        SFFT_SAMPLE(3)
+        SFFT_SAMPLE(4)
+        SFFT_SAMPLE(5)
+        SFFT_SAMPLE(6)
+        SFFT_SAMPLE(7)
+        SFFT_SAMPLE(8)
+        default: break;
+      }
+#undef SFFT_SAMPLE
+      ECHK(cudaGetLastError());
+      if (launches) launches[2] += 1;
+    }
+    return cudaSuccess;
+  }
+
+  // ---------------------------------------------------------------- one round
+  cudaError_t enqueue_round(const PlanArgs& pa, int64_t* launches, int round_idx, bool record) {
+    auto mark = [&](int q) -> cudaError_t {
+      if (!record) return cudaSuccess;
+      return cudaEventRecord(events_[(size_t)round_idx * 8 + q], st_);
+    };
+    ECHK(mark(0));
+    k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, dirs_, plist_, u_, hist_);
+    ECHK(cudaGetLastError());
+    ECHK(launch_tables());
+    launches[0] += 2;
+    ECHK(mark(1));
+    ECHK(mark(2));
+    ECHK(launch_samples(launches));
+    ECHK(mark(3));
+    k_filter<T><<<n_sm_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_,
+                                                            Lmax_, (C2*)bhat_);
+    ECHK(cudaGetLastError());
+    k_dft<T><<<n_sm_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_,
+                                                         (C2*)bhat_, (C2*)twG_, Lmax_, (C2*)Y_);
+    ECHK(cudaGetLastError());
+    launches[3] += 2;
+    if (any_big_) {
+      k_bigA<T><<<4 * n_sm_, 256, smem_bigA_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_, (C2*)twG_,
+                                                     Lmax_, (C2*)Z_);
+      ECHK(cudaGetLastError());
+      k_bigB<T><<<4 * n_sm_, 256, smem_bigB_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)twG_, Lmax_, (C2*)Z_);
+      ECHK(cudaGetLastError());
+      k_bigC<T><<<4 * n_sm_, 256, smem_bigA_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_, Lmax_,
+                                                     (C2*)Z_, (C2*)Y_);
+      ECHK(cudaGetLastError());
+      launches[3] += 3;
+    }
+    ECHK(mark(4));
+    ClassifyOut co{nullptr, nullptr, nullptr, 0, nullptr, nullptr, -1.0};
+    k_classify<T><<<4 * n_sm_, 128, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)Y_, u_, regw_, rega_, (C2*)regtw_,
+                                              hash_, co);
+    ECHK(cudaGetLastError());
+    launches[4] += 1;
+    ECHK(mark(5));
+    return cudaSuccess;
+  }
+
+  cudaError_t bind(const int32_t* const* sig_w, const double2* const* sig_a, const int64_t* k_sig,
+                   const int64_t* caps) {
+    // pinned staging: sig_w pointers, sig_a pointers, k_sig, capacities, output row offsets,
+    // output element offsets (rows of d_s ints)
+    int64_t* h = reinterpret_cast<int64_t*>(host_stage_);
+    int64_t rows = 0, elems = 0;
+    for (int s = 0; s < n_; ++s) {
+      const int64_t cap = caps ? caps[s] : 0;
+      h[s] = (int64_t)(uintptr_t)sig_w[s];
+      h[n_ + s] = (int64_t)(uintptr_t)sig_a[s];
+      h[2 * n_ + s] = k_sig[s];
+      h[3 * n_ + s] = cap;
+      h[4 * n_ + s] = rows;
+      h[5 * n_ + s] = elems;
+      rows += cap;
+      elems += cap * cfg_host_[s].d;
+    }
+    ECHK(cudaMemcpyAsync(bind_, h, (size_t)n_ * kBindArrays * sizeof(int64_t), cudaMemcpyHostToDevice, st_));
+    sig_w_ = reinterpret_cast<const int32_t* const*>(bind_);
+    sig_a_ = reinterpret_cast<const double2* const*>(reinterpret_cast<int64_t*>(bind_) + n_);
+    ksig_dev_ = reinterpret_cast<int64_t*>(bind_) + 2 * n_;
+    k_init<<<(n_ + 255) / 256, 256, 0, st_>>>(n_, run_, ksig_dev_);
+    ECHK(cudaGetLastError());
+    ECHK(cudaMemsetAsync(hash_, 0xFF, (size_t)hash_total_ * sizeof(int32_t), st_));
+    ECHK(cudaMemsetAsync(ctl_, 0, sizeof(RoundCtl), st_));
+    const int gx = (int)std::min<int64_t>(std::max<int64_t>((kd_max_ + 255) / 256, 1), 64);
+    k_bind_tw<T><<<dim3(gx, n_), 256, 0, st_>>>(n_, cfg_, run_, sig_w_, (C2*)tw_);
+    return cudaGetLastError();
+  }
+
+  cudaError_t build_graph(int hard_rounds) {
+    // while (plan says some signal is active) { one round }
+    cudaGraph_t g;
+    ECHK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle handle;
+    ECHK(cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault));
+    // the parameter block has union members without default constructors: zeroed raw storage
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    std::memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams* cp = reinterpret_cast<cudaGraphNodeParams*>(raw);
+    cp->type = cudaGraphNodeTypeConditional;
+    cp->conditional.handle = handle;
+    cp->conditional.type = cudaGraphCondTypeWhile;
+    cp->conditional.size = 1;
+    cudaGraphNode_t node;
+    ECHK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, cp));
+    cudaGraph_t body = cp->conditional.phGraph_out[0];
+    cudaStream_t cs;
+    ECHK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t saved = st_;
+    st_ = cs;
+    ECHK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    PlanArgs pa = plan_args(hard_rounds);
+    pa.use_cond = 1;
+    pa.cond = handle;
+    int64_t dummy[SFFT_NKCLASS] = {0, 0, 0, 0, 0, 0};
+    cudaError_t e = enqueue_round(pa, dummy, 0, false);
+    cudaGraph_t captured;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+    st_ = saved;
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return e;
+    if (e2 != cudaSuccess) return e2;
+    ECHK(cudaGraphInstantiate(&graph_exec_, g, 0));
+    graph_ = g;
+    launches_per_round_ = dummy[0] + dummy[2] + dummy[3] + dummy[4];
+    for (int q = 0; q < SFFT_NKCLASS; ++q) launch_class_per_round_[q] = dummy[q];
+    return cudaSuccess;
+  }
+
+  PlanArgs plan_args(int hard_rounds) const {
+    PlanArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.n = n_;
+    pa.part_cap = part_cap_;
+    pa.n_sm = n_sm_;
+    pa.single_max_logL = log2i(single_max_L<T>());
+    pa.hard_rounds = hard_rounds;
+    return pa;
+  }
+
+  int hard_rounds() const {
+    int m = 1;
+    for (const SigCfg& c : cfg_host_) m = std::max(m, c.max_rounds);
+    return std::min(m, SFFT_STATS_MAX_ROUNDS);
+  }
+
+  // ---------------------------------------------------------------- execute
+  cudaError_t run(const int32_t* const* sig_w, const double2* const* sig_a, const int64_t* k_sig, const int64_t* caps,
+                  int32_t* out_w, double2* out_a, int64_t* n_found, int* status, sfft_stats* stats) override {
+    int64_t launches[SFFT_NKCLASS] = {0, 0, 0, 0, 0, 0};
+    const int hard = hard_rounds();
+    ECHK(bind(sig_w, sig_a, k_sig, caps));
+    launches[5] += 2;
+    int rounds_enqueued = 0;
+    const bool record = profile_ && stats != nullptr;
+    if (use_graph_ && !record) {
+      if (!graph_exec_) ECHK(build_graph(hard));
+      ECHK(cudaGraphLaunch(graph_exec_, st_));
+    } else {
+      RoundCtl* hctl = reinterpret_cast<RoundCtl*>(reinterpret_cast<char*>(host_stage_) + stage_ctl_);
+      const PlanArgs pa = plan_args(hard);
+      for (;;) {
+        const int G = rounds_enqueued < 4 ? 4 : 2;
+        for (int q = 0; q < G && rounds_enqueued <= hard; ++q) {
+          ECHK(enqueue_round(pa, launches, rounds_enqueued, record));
+          ++rounds_enqueued;
+        }
+        ECHK(cudaMemcpyAsync(hctl, ctl_, sizeof(RoundCtl), cudaMemcpyDeviceToHost, st_));
+        ECHK(cudaStreamSynchronize(st_));
+        if (hctl->active == 0 || rounds_enqueued > hard) break;
+      }
+    }
+    k_output<<<n_, 1024, 0, st_>>>(n_, cfg_, run_, regw_, rega_, reinterpret_cast<const int64_t*>(bind_), out_w,
+                                   out_a, outn_, outst_, stats ? hist_ : nullptr);
+    ECHK(cudaGetLastError());
+    launches[5] += 1;
+    char* hb = reinterpret_cast<char*>(host_stage_);
+    int64_t* hn = reinterpret_cast<int64_t*>(hb + stage_n_);
+    int* hst = reinterpret_cast<int*>(hb + stage_st_);
+    ECHK(cudaMemcpyAsync(hn, outn_, n_ * sizeof(int64_t), cudaMemcpyDeviceToHost, st_));
+    ECHK(cudaMemcpyAsync(hst, outst_, n_ * sizeof(int), cudaMemcpyDeviceToHost, st_));
+    HistRec* hh = nullptr;
+    std::vector<SigRun> runs;
+    if (stats) {
+      hh = reinterpret_cast<HistRec*>(hb + stage_hist_);
+      ECHK(cudaMemcpyAsync(hh, hist_, SFFT_STATS_MAX_ROUNDS * sizeof(HistRec), cudaMemcpyDeviceToHost, st_));
+      runs.resize(n_);
+      ECHK(cudaMemcpyAsync(runs.data(), run_, n_ * sizeof(SigRun), cudaMemcpyDeviceToHost, st_));
+    }
+    ECHK(cudaStreamSynchronize(st_));
+    for (int s = 0; s < n_; ++s) {
+      n_found[s] = hn[s];
+      status[s] = hst[s];
+    }
+    if (stats) {
+      std::memset(stats, 0, sizeof(*stats));
+      int rounds = 0;
+      bool conv = true;
+      for (int s = 0; s < n_; ++s) {
+        rounds = std::max(rounds, runs[s].round);
+        stats->samples += runs[s].samples;
+        stats->terms += runs[s].terms;
+        conv = conv && (hst[s] == SFFT_OK || hst[s] == SFFT_ERR_INCONSISTENT || hst[s] == SFFT_ERR_CAPACITY) &&
+               !runs[s].active;
+      }
+      stats->rounds = rounds;
+      stats->converged = conv ? 1 : 0;
+      const int r0 = std::min(runs[0].round, SFFT_STATS_MAX_ROUNDS);
+      for (int i = 0; i < r0; ++i) {
+        stats->p[i] = hh[i].p;
+        stats->K[i] = hh[i].K;
+        stats->accepted[i] = hh[i].accepted;
+        stats->registry[i] = hh[i].live;
+      }
+      if (use_graph_ && !record) {
+        // rounds of the device loop: the plan of each round plus one that found nothing left
+        const int64_t loops = rounds + 1;
+        for (int q = 0; q < SFFT_NKCLASS; ++q) launches[q] += launch_class_per_round_[q] * loops;
+      }
+      for (int q = 0; q < SFFT_NKCLASS; ++q) stats->kernel_launches[q] = launches[q];
+      if (record) {
+        for (int i = 0; i < rounds_enqueued; ++i) {
+          float ms;
+          const size_t b = (size_t)i * 8;
+          ECHK(cudaEventElapsedTime(&ms, events_[b + 0], events_[b + 1]));
+          stats->kernel_ms[0] += ms;
+          ECHK(cudaEventElapsedTime(&ms, events_[b + 2], events_[b + 3]));
+          stats->kernel_ms[2] += ms;
+          ECHK(cudaEventElapsedTime(&ms, events_[b + 3], events_[b + 4]));
+          stats->kernel_ms[3] += ms;
+          ECHK(cudaEventElapsedTime(&ms, events_[b + 4], events_[b + 5]));
+          stats->kernel_ms[4] += ms;
+        }
+      }
+    }
+    return cudaSuccess;
+  }
+
+  // ---------------------------------------------------------------- step calls (slot 0)
+  cudaError_t prepare_step(int64_t p, const int64_t* u, int K, const int32_t* w, const double2* a) {
+    if (u) {
+      std::vector<int64_t> um((size_t)cfg_host_[0].d);
+      for (int l = 0; l < cfg_host_[0].d; ++l) {
+        int64_t v = u[l] % p;
+        um[l] = v < 0 ? v + p : v;
+      }
+      ECHK(cudaMemcpyAsync(u_ + cfg_host_[0].u_off, um.data(), um.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                           st_));
+      ECHK(cudaStreamSynchronize(st_));
+    }
+    const int32_t* wp[1] = {w};
+    const double2* ap[1] = {a};
+    int64_t ks[1] = {K};
+    int64_t cp[1] = {0};
+    ECHK(bind(wp, ap, ks, cp));
+    PlanArgs pa = plan_args(1 << 20);
+    pa.force = 1;
+    pa.force_p = p;
+    pa.force_K = K;
+    k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, dirs_, plist_, u_, nullptr);
+    ECHK(cudaGetLastError());
+    return launch_tables();
+  }
+
+  cudaError_t step_sample(int64_t p, const int64_t* u, int64_t K, const int32_t* w, const double2* a,
+                          void* y_out) override {
+    ECHK(prepare_step(p, u, (int)K, w, a));
+    ECHK(launch_samples(nullptr));
+    k_reduce<T><<<2 * n_sm_, 256, 0, st_>>>(cfg_, run_, cfg_host_[0].n_sets, (C2*)part_, (C2*)y_out);
+    ECHK(cudaGetLastError());
+    return cudaStreamSynchronize(st_);
+  }
+
+  cudaError_t step_dft(int64_t p, int n_rows, const void* y, void* Y_out) override {
+    ECHK(prepare_step(p, nullptr, 0, nullptr, nullptr));
+    // the rows enter as a single split at the start of the partial arena
+    const int ns = cfg_host_[0].n_sets;
+    ECHK(cudaMemsetAsync(part_, 0, (size_t)ns * p * sizeof(C2), st_));
+    ECHK(cudaMemcpyAsync(part_, y, (size_t)n_rows * p * sizeof(C2), cudaMemcpyDeviceToDevice, st_));
+    k_filter<T><<<n_sm_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_,
+                                                            Lmax_, (C2*)bhat_);
+    ECHK(cudaGetLastError());
+    k_dft<T><<<n_sm_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_,
+                                                         (C2*)bhat_, (C2*)twG_, Lmax_, (C2*)Y_);
+    ECHK(cudaGetLastError());
+    if (any_big_) {
+      k_bigA<T><<<4 * n_sm_, 256, smem_bigA_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_, (C2*)twG_,
+                                                     Lmax_, (C2*)Z_);
+      k_bigB<T><<<4 * n_sm_, 256, smem_bigB_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)twG_, Lmax_, (C2*)Z_);
+      k_bigC<T><<<4 * n_sm_, 256, smem_bigA_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_, Lmax_,
+                                                     (C2*)Z_, (C2*)Y_);
+      ECHK(cudaGetLastError());
+    }
+    ECHK(cudaMemcpyAsync(Y_out, (C2*)Y_ + cfg_host_[0].Y_off, (size_t)n_rows * p * sizeof(C2),
+                         cudaMemcpyDeviceToDevice, st_));
+    return cudaStreamSynchronize(st_);
+  }
+
+  cudaError_t step_classify(int64_t p, const int64_t* u, const void* Y, double eta, int64_t cap, int32_t* h_out,
+                            int32_t* w_out, double2* a_out, int64_t* n_out, int* err) override {
+    ECHK(prepare_step(p, u, 0, nullptr, nullptr));
+    const int ns = cfg_host_[0].n_sets;
+    ECHK(cudaMemcpyAsync((C2*)Y_ + cfg_host_[0].Y_off, Y, (size_t)ns * p * sizeof(C2), cudaMemcpyDeviceToDevice, st_));
+    ECHK(cudaMemsetAsync(stepc_, 0, 2 * sizeof(int), st_));
+    int* cnt = reinterpret_cast<int*>(stepc_);
+    ClassifyOut co{h_out, w_out, a_out, (int)cap, cnt, cnt + 1, eta};
+    k_classify<T><<<4 * n_sm_, 128, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)Y_, u_, regw_, rega_, (C2*)regtw_,
+                                              hash_, co);
+    ECHK(cudaGetLastError());
+    int* h = reinterpret_cast<int*>(reinterpret_cast<char*>(host_stage_) + stage_st_);
+    ECHK(cudaMemcpyAsync(h, stepc_, 2 * sizeof(int), cudaMemcpyDeviceToHost, st_));
+    ECHK(cudaStreamSynchronize(st_));
+    *n_out = h[0];
+    *err = h[1];
+    return cudaSuccess;
+  }
+
+ private:
+  template <typename P>
+  cudaError_t alloc(P** out, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes == 0 ? 16 : bytes);
+    if (e == cudaSuccess) {
+      allocs_.push_back(q);
+      bytes_ += bytes;
+      *out = reinterpret_cast<P*>(q);
+    }
+    return e;
+  }
+
+  static size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+  int n_ = 0, dev_ = 0, n_sm_ = 148;
+  cudaStream_t st_ = nullptr;
+  bool profile_ = false, use_graph_ = false, any_big_ = false;
+  int logL_big_max_ = 0, small_logL_max_ = 1, small_threads_ = 256, n_ptab_ = 0;
+  size_t smem_small_ = 0, smem_bigA_ = 0, smem_bigB_ = 0, bytes_ = 0, host_stage_bytes_ = 0;
+  int64_t Lmax_ = 2, p_max_ = 2, part_cap_ = 0, hash_total_ = 0, k_max_ = 0, kd_max_ = 0, reg_cap_max_ = 0;
+  std::vector<SigCfg> cfg_host_;
+  std::vector<void*> allocs_;
+  std::vector<cudaEvent_t> events_;
+  void* host_stage_ = nullptr;
+  SigCfg* cfg_ = nullptr;
+  SigRun* run_ = nullptr;
+  RoundCtl* ctl_ = nullptr;
+  Scans scans_;
+  int32_t* ptab_ = nullptr;
+  int64_t* dirs_ = nullptr;
+  int64_t* plist_ = nullptr;
+  void* tw_ = nullptr;
+  int32_t* regw_ = nullptr;
+  void* regtw_ = nullptr;
+  double2* rega_ = nullptr;
+  int32_t* hash_ = nullptr;
+  void* tab_ = nullptr;
+  void* bhat_ = nullptr;
+  void* Y_ = nullptr;
+  void* Z_ = nullptr;
+  int64_t* u_ = nullptr;
+  int32_t* alpha_ = nullptr;
+  int32_t* gam_ = nullptr;
+  void* Cm_ = nullptr;
+  unsigned ns_mask_ = 0;   // set-group sizes present among the slots
+  void* part_ = nullptr;
+  void* twG_ = nullptr;
+  HistRec* hist_ = nullptr;
+  void* bind_ = nullptr;
+  int64_t* outn_ = nullptr;
+  int* outst_ = nullptr;
+  void* stepc_ = nullptr;
+  const int32_t* const* sig_w_ = nullptr;
+  const double2* const* sig_a_ = nullptr;
+  int64_t* ksig_dev_ = nullptr;
+  size_t stage_ctl_ = 0, stage_n_ = 0, stage_st_ = 0, stage_hist_ = 0;
+  cudaGraph_t graph_ = nullptr;
+  cudaGraphExec_t graph_exec_ = nullptr;
+  int64_t launches_per_round_ = 0;
+  int64_t launch_class_per_round_[SFFT_NKCLASS] = {0, 0, 0, 0, 0, 0};
+};
+
+}  // namespace
+
+cudaError_t engine_create(bool fp64, const std::vector<SlotDesc>& slots, cudaStream_t st, bool profile,
+                          bool use_graph, EngineBase** out) {
+  *out = nullptr;
+  if (fp64) {
+    auto* e = new Engine<double>();
+    cudaError_t r = e->init(slots, st, profile, use_graph);
+    if (r != cudaSuccess) {
+      delete e;
+      return r;
+    }
+    *out = e;
+  } else {
+    auto* e = new Engine<float>();
+    cudaError_t r = e->init(slots, st, profile, use_graph);
+    if (r != cudaSuccess) {
+      delete e;
+      return r;
+    }
+    *out = e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace sfft

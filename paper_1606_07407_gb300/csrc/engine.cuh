@@ -1,0 +1,130 @@
+// Batched round engine: per-signal configuration and round state live on the
+// device, so every kernel of a round serves all signals of a batch and the
+// host only launches rounds (or one CUDA graph whose loop the device ends).
+#pragma once
+
+#include <vector>
+
+#include "sfft_internal.cuh"
+
+namespace sfft {
+
+constexpr int kPlanThreads = 1024;
+constexpr int kSingleMaxLf = 16384;   // one-block Bluestein length, FP32 (data + twiddles in shared memory)
+constexpr int kSingleMaxLd = 8192;    // same for FP64
+constexpr int kBigColElems = 4096;    // elements of one column tile of the four-step passes
+constexpr int kBigRowElems = 2048;    // elements of one row tile
+
+template <typename T> constexpr int single_max_L() { return sizeof(T) == 4 ? kSingleMaxLf : kSingleMaxLd; }
+
+// Rows of 32 samples per warp for a set group of ns sets: chunk and running accumulators
+// (4 rows x ns sets x 2 reals each) stay within about 80 registers.
+__host__ __device__ constexpr int rows_per_warp(int ns) {
+  return ns <= 2 ? 8 : ns == 3 ? 6 : ns == 4 ? 5 : ns == 5 ? 4 : ns == 6 ? 3 : 2;
+}
+__host__ __device__ constexpr int tile_x(int ns) { return 32 * 4 * rows_per_warp(ns); }   // 4 warps per block
+
+// Static description of one signal slot of a batch.
+struct SigCfg {
+  int d, n_sets, k, c, max_rounds, n_dirs, n_primes, box_lo;
+  int ratio64;        // phase ratio and coefficient in double
+  int coef_mean;      // coefficient = mean over the d + 1 sets (else Y_0[h] / p)
+  int reg_cap, hash_mask, logL_max;
+  int64_t N, p_max;
+  double tau, rho, delta, sigma;
+  int64_t dirs_off, primes_off;  // into the direction / prime-list arrays
+  int64_t tw_off;     // T2 [k * d]        unit twiddles e^{2 pi i w_n / N} of the signal's modes
+  int64_t regw_off;   // int32 [reg_cap * d]
+  int64_t rega_off;   // double2 [reg_cap]
+  int64_t regtw_off;  // T2 [reg_cap * d]
+  int64_t hash_off;   // int32 [hash_mask + 1]
+  int64_t tab_off;    // T2 [2 * p_max]     W[m] = e^{2 pi i m / p}, then chirp[x] = e^{-pi i x^2 / p}
+  int64_t bhat_off;   // T2 [L_max]         spectrum of the Bluestein filter
+  int64_t Y_off;      // T2 [n_sets * p_max]
+  int64_t z_off;      // T2 [(n_sets + 1) * L_max] four-step work space, -1 if never needed
+  int64_t u_off;      // int64 [d]           direction of the round, reduced mod p
+  int64_t mode_off;   // int32 [Kmax]        alpha_j = (w_j . u) mod p and 32 alpha_j mod p of the round
+  int64_t C_off;      // T2 [n_sets * Kmax]  a_j e^{2 pi i w_{j,n} / N} of the round (registry: -a)
+  int Kmax;           // k + reg_cap
+  int pad2;
+};
+
+// Dynamic state of one signal, updated by the kernels of each round.
+struct SigRun {
+  int active, round, status, err;
+  int K_reg;          // registry entries ever created (pruned ones have a = 0)
+  int n_live;         // entries with a != 0
+  int any_occupied;   // some bin above the empty-bin level this round
+  int n_acc;          // bins accepted this round
+  int k_sig;          // modes of the bound black box
+  int logL, big;      // Bluestein length of the round; big = four-step path
+  int n_xt, groups, gsize, chunks, jper, splits;
+  int64_t p;
+  unsigned long long mod_m;   // floor((2^64 - 1) / p), Barrett reduction
+  int64_t part_off;
+  unsigned long long maxy0_bits;
+  double a_ref;
+  int64_t samples, terms;
+  int64_t n_out;
+};
+
+// Work totals of the round (exclusive scans over signals are in Scans).
+struct RoundCtl {
+  int active, round, splits, pad;
+  int64_t n_tab, n_mode, n_rows, n_filt, n_bins, n_bigA, n_bigB, n_bigC;
+  int64_t n_samp[kMaxSetGroup];               // sampling tiles, per set-group size
+  unsigned long long ctr_samp[kMaxSetGroup], ctr_rows, ctr_filt;
+};
+
+// exclusive scans over signals: tables, modes, DFT rows, filters, bins, four-step passes,
+// then sampling tiles for each set-group size 1..kMaxSetGroup
+constexpr int kNumScans = 8 + kMaxSetGroup;
+struct Scans {
+  int64_t* v[kNumScans];       // each [n + 1]
+};
+enum { SC_TAB = 0, SC_MODE, SC_ROWS, SC_FILT, SC_BINS, SC_BIGA, SC_BIGB, SC_BIGC, SC_SAMP0 };
+
+struct HistRec {
+  int64_t p;
+  int32_t K, accepted, live, pad;
+};
+
+// Host-side description of one signal slot.
+struct SlotDesc {
+  int d;
+  int64_t N;
+  int64_t k;
+  int c;
+  int box_lo;
+  int ratio64;
+  int coef_mean;
+  double tau, rho, delta, sigma;
+  int max_rounds;
+  std::vector<int64_t> dirs;     // n_dirs x d
+  int n_dirs;
+  std::vector<int64_t> primes;   // prime-list override (empty: rule)
+  int64_t p_max;
+};
+
+// Engine interface, instantiated for float (FP32 bulk) and double (FP64).
+class EngineBase {
+ public:
+  virtual ~EngineBase() {}
+  virtual cudaError_t run(const int32_t* const* sig_w, const double2* const* sig_a, const int64_t* k_sig,
+                          const int64_t* caps, int32_t* out_w, double2* out_a, int64_t* n_found, int* status,
+                          sfft_stats* stats) = 0;
+  virtual cudaError_t step_sample(int64_t p, const int64_t* u, int64_t K, const int32_t* w, const double2* a,
+                                  void* y_out) = 0;
+  virtual cudaError_t step_dft(int64_t p, int n_rows, const void* y, void* Y_out) = 0;
+  virtual cudaError_t step_classify(int64_t p, const int64_t* u, const void* Y, double eta, int64_t cap,
+                                    int32_t* h_out, int32_t* w_out, double2* a_out, int64_t* n_out, int* err) = 0;
+  virtual size_t device_bytes() const = 0;
+  virtual int64_t max_prime() const = 0;
+  virtual int64_t mode_capacity() const = 0;
+};
+
+// Creates an engine for the slots (all slots share T).  profile: CUDA-event timing per kernel class.
+cudaError_t engine_create(bool fp64, const std::vector<SlotDesc>& slots, cudaStream_t st, bool profile,
+                          bool use_graph, EngineBase** out);
+
+}  // namespace sfft

@@ -1,0 +1,115 @@
+// Device helpers of the batched round engine: modular arithmetic, unit roots,
+// block scans and work-item lookup.
+#pragma once
+
+#include "engine.cuh"
+
+namespace sfft {
+
+// x mod p for x < 2^64 by Barrett reduction with m = floor((2^64 - 1) / p):
+// q = floor(x m / 2^64) is floor(x / p) or one less, so one correction suffices.
+__device__ __forceinline__ uint64_t mod_barrett(uint64_t x, uint64_t p, uint64_t m) {
+  const uint64_t q = __umul64hi(x, m);
+  uint64_t r = x - q * p;
+  return r >= p ? r - p : r;
+}
+
+// a mod p for 0 <= a < 64 p < 2^31, via a float reciprocal and one correction.
+__device__ __forceinline__ int mod_small(unsigned a, int p, float inv_p) {
+  int q = __float2int_rz(__uint2float_rn(a) * inv_p);
+  int r = (int)a - q * p;
+  if (r < 0) r += p;
+  else if (r >= p) r -= p;
+  return r;
+}
+
+// e^{2 pi i m / q} for integers 0 <= m < q.  The angle is folded to (-pi, pi]
+// as 2 (m - q [2m > q]) / q half-turns; in float the half-turn count is split
+// into a rounded head and an exactly computed tail, and the tail enters by a
+// first-order rotation, so the only rounding left is that of sincospif itself.
+template <typename T> __device__ __forceinline__ c2<T> unit_root(int64_t m, int64_t q);
+template <> __device__ __forceinline__ float2 unit_root<float>(int64_t m, int64_t q) {
+  const int64_t mm = (2 * m > q) ? m - q : m;
+  const float num = (float)(2 * mm);   // exact: |2 mm| <= q < 2^24
+  const float qf = (float)q;
+  const float xh = num / qf;
+  const float xl = fmaf(-xh, qf, num) / qf;
+  float s, c;
+  sincospif(xh, &s, &c);
+  const float dl = 3.14159265358979f * xl;
+  return make_float2(fmaf(-s, dl, c), fmaf(c, dl, s));
+}
+template <> __device__ __forceinline__ double2 unit_root<double>(int64_t m, int64_t q) {
+  const int64_t mm = (2 * m > q) ? m - q : m;
+  double s, c;
+  sincospi(2.0 * (double)mm / (double)q, &s, &c);
+  return make_double2(c, s);
+}
+
+// chirp[x] = e^{-pi i x^2 / p} = conj(e^{2 pi i (x^2 mod 2p) / (2p)})
+template <typename T>
+__device__ __forceinline__ c2<T> chirp_at(int64_t x, int64_t p) {
+  const uint64_t q = ((uint64_t)x * (uint64_t)x) % (uint64_t)(2 * p);
+  return cconj(unit_root<T>((int64_t)q, 2 * p));
+}
+
+// index s with scan[s] <= item < scan[s + 1] (scan non-decreasing, scan[0] = 0)
+__device__ __forceinline__ int find_slot(const int64_t* __restrict__ scan, int n, int64_t item) {
+  int lo = 0, hi = n;   // invariant scan[lo] <= item < scan[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(scan + mid) <= item) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Exclusive scan of V values per thread over a block of kPlanThreads threads.
+template <int V>
+__device__ void block_scan_excl(int64_t (&v)[V], int64_t (&tot)[V]) {
+  __shared__ int64_t ws[32][V];
+  __shared__ int64_t wt[V];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t incl[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) {
+    int64_t x = v[q];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    incl[q] = x;
+    if (lane == 31) ws[wid][q] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      int64_t x = ws[lane][q];
+      const int64_t own = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      ws[lane][q] = x - own;
+      if (lane == 31) wt[q] = x;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < V; ++q) {
+    v[q] = incl[q] - v[q] + ws[wid][q];
+    tot[q] = wt[q];
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int64_t block_sum(int64_t x) {
+  int64_t v[1] = {x}, t[1];
+  block_scan_excl<1>(v, t);
+  return t[0];
+}
+
+}  // namespace sfft

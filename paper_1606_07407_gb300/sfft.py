@@ -15,10 +15,12 @@ import torch
 
 from . import build as _build
 
-PREC = {"fp32": 0, "fp32_fp64ratio": 0, "fp32_only": 1, "fp64": 2}
+PREC = {"fp32": 0, "auto": 0, "fp32_fp64ratio": 1, "fp32_only": 2, "fp64": 3}
 STATUS = {0: "ok", 1: "invalid argument", 2: "not converged", 3: "capacity exceeded",
           4: "beyond phase resolution", 5: "more modes than k", 6: "cuda error", 7: "device wait timed out"}
 MAX_ROUNDS = 256
+NKCLASS = 6
+KCLASSES = ("setup", "project", "sample", "dft", "classify", "merge")
 
 
 class SfftError(RuntimeError):
@@ -38,17 +40,21 @@ class _Tilts(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("box_lo", C.c_int), ("tau", C.c_double), ("rho", C.c_double),
-                ("delta", C.c_double), ("noise_sigma", C.c_double), ("max_rounds", C.c_int)]
+                ("delta", C.c_double), ("noise_sigma", C.c_double), ("max_rounds", C.c_int),
+                ("profile", C.c_int), ("graph", C.c_int), ("coef_set0", C.c_int)]
 
 
 class _Stats(C.Structure):
     _fields_ = [("rounds", C.c_int), ("converged", C.c_int), ("samples", C.c_int64), ("terms", C.c_int64),
                 ("p", C.c_int64 * MAX_ROUNDS), ("K", C.c_int32 * MAX_ROUNDS),
-                ("accepted", C.c_int32 * MAX_ROUNDS), ("registry", C.c_int32 * MAX_ROUNDS)]
+                ("accepted", C.c_int32 * MAX_ROUNDS), ("registry", C.c_int32 * MAX_ROUNDS),
+                ("kernel_launches", C.c_int64 * NKCLASS), ("kernel_ms", C.c_double * NKCLASS)]
 
 
 EXPORTS = ["sfft_plan_create", "sfft_plan_destroy", "sfft_signal_synthetic", "sfft_signal_destroy",
-           "sfft_execute", "sfft_sample", "sfft_dft", "sfft_classify", "sfft_plan_max_prime",
+           "sfft_signal_assign",
+           "sfft_execute", "sfft_batch_create", "sfft_batch_destroy", "sfft_batch_device_bytes",
+           "sfft_batch_execute", "sfft_sample", "sfft_dft", "sfft_classify", "sfft_plan_max_prime",
            "sfft_plan_mode_capacity", "sfft_plan_device_bytes", "sfft_last_cuda_error", "sfft_status_string"]
 
 _lib = None
@@ -77,8 +83,19 @@ def load(path: str | None = None) -> C.CDLL:
     L.sfft_signal_synthetic.restype = C.c_int
     L.sfft_signal_destroy.argtypes = [vp]
     L.sfft_signal_destroy.restype = None
+    L.sfft_signal_assign.argtypes = [vp, i64, vp, vp]
+    L.sfft_signal_assign.restype = C.c_int
     L.sfft_execute.argtypes = [vp, vp, i64, vp, vp, C.POINTER(i64), C.POINTER(_Stats)]
     L.sfft_execute.restype = C.c_int
+    L.sfft_batch_create.argtypes = [C.c_int, C.POINTER(vp), vp, C.c_int, C.POINTER(vp)]
+    L.sfft_batch_create.restype = C.c_int
+    L.sfft_batch_destroy.argtypes = [vp]
+    L.sfft_batch_destroy.restype = None
+    L.sfft_batch_device_bytes.argtypes = [vp]
+    L.sfft_batch_device_bytes.restype = i64
+    L.sfft_batch_execute.argtypes = [vp, C.POINTER(vp), C.POINTER(i64), vp, vp, C.POINTER(i64),
+                                     C.POINTER(C.c_int32), C.POINTER(_Stats)]
+    L.sfft_batch_execute.restype = C.c_int
     L.sfft_sample.argtypes = [vp, i64, C.POINTER(i64), i64, vp, vp, vp]
     L.sfft_sample.restype = C.c_int
     L.sfft_dft.argtypes = [vp, i64, C.c_int, vp, vp]
@@ -133,6 +150,12 @@ class Signal:
                "sfft_signal_synthetic")
         self._h = h
 
+    def assign(self, freqs: torch.Tensor, coeffs: torch.Tensor):
+        """Replaces the modes in place (device tensors int32 [k, d] and complex128 [k])."""
+        _check(load().sfft_signal_assign(self._h, int(freqs.shape[0]), _ptr(freqs), _ptr(coeffs)),
+               "sfft_signal_assign")
+        self.k = int(freqs.shape[0])
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value and _lib is not None:
@@ -145,7 +168,8 @@ class Plan:
 
     def __init__(self, d: int, N: int, k: int, blocks=None, dirs=None, primes=None, c: int = 5,
                  precision: str = "fp32", box_lo: int = 0, tau: float = 0.0, rho: float = 0.0,
-                 delta: float = 0.0, noise_sigma: float = 0.0, max_rounds: int = 0, stream=None):
+                 delta: float = 0.0, noise_sigma: float = 0.0, max_rounds: int = 0, stream=None,
+                 profile: bool = False, graph: bool = False, coef: str = "mean"):
         L = load()
         self.d, self.N, self.k = int(d), int(N), int(k)
         self.precision = precision
@@ -167,7 +191,7 @@ class Plan:
             self._keep.append(arr)
             tl.n_blocks, tl.block_sizes = len(blocks), arr
         op = _Opts(PREC[precision], int(box_lo), float(tau), float(rho), float(delta), float(noise_sigma),
-                   int(max_rounds))
+                   int(max_rounds), 1 if profile else 0, 1 if graph else 0, 1 if coef == "set0" else 0)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -204,11 +228,7 @@ class Plan:
         status = L.sfft_execute(self._h, signal._h, cap, _ptr(fo), _ptr(co), C.byref(n), C.byref(st))
         _check(status, "sfft_execute", ok=allow)
         m = min(int(n.value), cap)
-        r = st.rounds
-        stats = {"rounds": r, "converged": bool(st.converged), "samples": int(st.samples),
-                 "terms": int(st.terms), "p": list(st.p[:r]), "K": list(st.K[:r]),
-                 "accepted": list(st.accepted[:r]), "registry": list(st.registry[:r])}
-        return fo[:m], co[:m], status, stats
+        return fo[:m], co[:m], status, _stats_dict(st)
 
     def sample(self, p: int, u, freqs: torch.Tensor, coeffs: torch.Tensor) -> torch.Tensor:
         L = load()
@@ -239,6 +259,70 @@ class Plan:
                                C.byref(n)), "sfft_classify")
         m = int(n.value)
         return h[:m], w[:m], a[:m]
+
+
+def _stats_dict(st: _Stats) -> dict:
+    r = min(st.rounds, MAX_ROUNDS)
+    return {"rounds": st.rounds, "converged": bool(st.converged), "samples": int(st.samples),
+            "terms": int(st.terms), "p": list(st.p[:r]), "K": list(st.K[:r]),
+            "accepted": list(st.accepted[:r]), "registry": list(st.registry[:r]),
+            "launches": dict(zip(KCLASSES, list(st.kernel_launches))),
+            "kernel_ms": dict(zip(KCLASSES, list(st.kernel_ms)))}
+
+
+class Batch:
+    """Many independent signals recovered together: every kernel launch serves all slots."""
+
+    def __init__(self, plans, stream=None, graph: bool = False):
+        L = load()
+        self.plans = list(plans)
+        self.n = len(self.plans)
+        arr = (C.c_void_p * self.n)(*[p._h.value for p in self.plans])
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        _check(L.sfft_batch_create(self.n, arr, C.c_void_p(stream.cuda_stream), 1 if graph else 0, C.byref(h)),
+               "sfft_batch_create")
+        self._h = h
+        self.d = [p.d for p in self.plans]
+        self.k = [p.k for p in self.plans]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sfft_batch_destroy(h)
+            self._h = None
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load().sfft_batch_device_bytes(self._h))
+
+    def outputs(self, caps=None):
+        caps = [2 * k + 16 for k in self.k] if caps is None else [int(c) for c in caps]
+        fo = torch.empty((sum(c * d for c, d in zip(caps, self.d)),), dtype=torch.int32, device="cuda")
+        co = torch.empty((sum(caps),), dtype=torch.complex128, device="cuda")
+        return caps, fo, co
+
+    def execute(self, signals, out=None, allow=(0,)):
+        """Returns ([(freqs [n_s, d_s], coeffs [n_s])...], statuses, stats) with device tensors."""
+        L = load()
+        caps, fo, co = out if out is not None else self.outputs()
+        sig = (C.c_void_p * self.n)(*[s._h.value for s in signals])
+        capa = (C.c_int64 * self.n)(*caps)
+        nf = (C.c_int64 * self.n)()
+        sts = (C.c_int32 * self.n)()
+        st = _Stats()
+        status = L.sfft_batch_execute(self._h, sig, capa, _ptr(fo), _ptr(co), nf, sts, C.byref(st))
+        _check(status, "sfft_batch_execute", ok=allow)
+        res = []
+        r0 = e0 = 0
+        for s in range(self.n):
+            m = min(int(nf[s]), caps[s])
+            res.append((fo[e0:e0 + m * self.d[s]].view(m, self.d[s]), co[r0:r0 + m]))
+            r0 += caps[s]
+            e0 += caps[s] * self.d[s]
+        return res, list(sts), _stats_dict(st)
 
 
 def sort_result(freqs: np.ndarray, coeffs: np.ndarray):

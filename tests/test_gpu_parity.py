@@ -83,9 +83,10 @@ def test_samples_sampled_at_large_size(sfft):
 # ------------------------------------------------------------------ kernel (b)
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-@pytest.mark.parametrize("p", [2, 5, 83, 911, 2039, 2053, 5003, 50021])
+@pytest.mark.parametrize("p", [2, 5, 83, 911, 2039, 4099, 5003, 8191, 8209, 50021])
 def test_dft_matches_definition(sfft, prec, p):
-    # 2039 is the largest single-block length (L = 4096); 2053 the first four-step one.
+    # one-block Bluestein up to L = 16384 in float (p = 8191) and L = 8192 in double (p = 4099);
+    # p = 8209 and 50021 take the four-step passes.
     rows = 3
     plan = sfft.Plan(2, 1 << 16, 12000, blocks=(1, 1), precision=prec)
     st = Stream(p)
@@ -147,11 +148,11 @@ def test_classify_matches_oracle(sfft, prec):
     w = [[5, 10, 7], [5, 40, 7], [20, 3, 60], [40, 33, 1], [12, 0, 0], [43, 0, 0]]
     a = [1.0 + 0.2j, 0.8 - 0.5j, -1.1 + 0.3j, 0.6 + 0.6j, 1.0, 0.7j]
     Y = _designed_transforms(d, N, p, u, w, a)
-    plan = sfft.Plan(d, N, 16, blocks=(1, 1, 1), precision=prec)
+    plan = sfft.Plan(d, N, 16, blocks=(1, 1, 1), precision="fp32_fp64ratio" if prec == "fp32" else prec)
     Yc = Y.astype(np.complex64 if prec == "fp32" else np.complex128)
     h, gw, ga = plan.classify(p, u, torch.tensor(Yc), 1e-3)
     th = O.Thresholds(tau=plan_tau(prec), delta=plan_delta(prec))
-    ref = O.classify(Yc.astype(np.complex128), p, u, N, 1e-3, th)
+    ref = O.classify(Yc.astype(np.complex128), p, u, N, 1e-3, th, estimator="mean")
     got = sorted(zip(_np(h).tolist(), map(tuple, _np(gw).tolist()), _np(ga).tolist()))
     assert [(x[0], x[1]) for x in got] == [(r[0], r[1]) for r in ref] == [(9, (40, 33, 1)), (20, (20, 3, 60))]
     for g, r in zip(got, ref):
@@ -172,7 +173,8 @@ def test_classify_random_round_matches_oracle(sfft):
     sig = wl.signal()
     p = 5003
     u = [int(v) for v in O.unwrap_vector(5, 1024, wl.blocks, 1)]
-    plan = sfft.Plan(5, 1024, 1000, blocks=wl.blocks)
+    # read-out decisions in double on both sides (the oracle's precision)
+    plan = sfft.Plan(5, 1024, 1000, blocks=wl.blocks, precision="fp32_fp64ratio")
     Y = _np(plan.dft(p, plan.sample(p, u, torch.tensor(sig.freqs), torch.tensor(sig.coeffs))))
     eta = 2.0 ** -17 * np.max(np.abs(Y[0]))
     h, gw, ga = plan.classify(p, u, torch.tensor(Y), eta)
@@ -192,7 +194,7 @@ def _run_both(sfft, sig, blocks=None, prec="fp32", dirs=None, primes=None, box_l
     gf, ga = sfft.sort_result(_np(f), _np(a))
     th = O.Thresholds() if prec == "fp64" else O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
     ref = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, blocks, th=th, dirs=dirs,
-                             primes=primes, box_lo=box_lo)
+                             primes=primes, box_lo=box_lo, estimator="mean")
     return gf, ga, status, stats, ref
 
 
@@ -299,3 +301,87 @@ def test_repeated_execute_is_stable(sfft):
             first = (gf, ga)
         assert status == 0 and np.array_equal(gf, first[0])
         assert np.max(np.abs(ga - first[1]) / np.abs(first[1])) < 1e-5
+
+
+# ------------------------------------------------------------------ batches and graph mode
+
+def _mixed_signals(n, seed):
+    from paper_1606_07407_gb300.inputs import default_blocks
+    st = Stream(seed)
+    ks = st.integers(n, 8, 97)
+    ds = st.integers(n, 2, 7)
+    ls = st.integers(n, 10, 17)
+    out = []
+    for s in range(n):
+        d, N, k = int(ds[s]), 1 << int(ls[s]), int(ks[s])
+        out.append((draw_signal(d, N, k, seed=seed * 1000 + s, r_lo=1.0, r_hi=10.0), default_blocks(d, N, k)))
+    return out
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_mixed_matches_oracle(sfft, graph):
+    sigs = _mixed_signals(24, 44)
+    plans = [sfft.Plan(s.d, s.N, s.k, blocks=b) for s, b in sigs]
+    batch = sfft.Batch(plans, graph=graph)
+    res, sts, stats = batch.execute([sfft.Signal(s.freqs, s.coeffs, s.N) for s, _ in sigs])
+    assert all(x == 0 for x in sts)
+    th = O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
+    for (sig, blocks), (f, a) in zip(sigs, res):
+        gf, ga = sfft.sort_result(_np(f), _np(a))
+        ref = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, blocks, th=th, estimator="mean")
+        planted = sig.freqs[np.lexsort(sig.freqs.T[::-1])].astype(np.int64)
+        assert np.array_equal(gf, ref.freqs) and np.array_equal(gf, planted)
+        assert np.max(np.abs(ga - ref.coeffs) / np.abs(ref.coeffs)) < FP32_COEFF_TOL
+
+
+def test_batch_equals_one_at_a_time(sfft):
+    sigs = _mixed_signals(8, 45)
+    plans = [sfft.Plan(s.d, s.N, s.k, blocks=b) for s, b in sigs]
+    dev = [sfft.Signal(s.freqs, s.coeffs, s.N) for s, _ in sigs]
+    res, sts, _ = sfft.Batch(plans).execute(dev)
+    for plan, sg, (f, a) in zip(plans, dev, res):
+        f1, a1, st1, _ = plan.execute(sg)
+        g1 = sfft.sort_result(_np(f1), _np(a1))
+        gb = sfft.sort_result(_np(f), _np(a))
+        assert st1 == 0 and np.array_equal(g1[0], gb[0])
+        # the mode splits of the sampling grid depend on the batch, so the float sums differ
+        # in order: both are float estimates, compared at the float coefficient tolerance
+        assert np.max(np.abs(g1[1] - gb[1]) / np.abs(g1[1])) < FP32_COEFF_TOL
+
+
+def test_batch_of_d5_workload(sfft):
+    wl = WORKLOADS["d5_N1024_k1000"]
+    sigs = [wl.signal(seed_offset=s) for s in range(4)]
+    plan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks)
+    res, sts, stats = sfft.Batch([plan] * 4, graph=True).execute(
+        [sfft.Signal(s.freqs, s.coeffs, s.N) for s in sigs])
+    assert sts == [0, 0, 0, 0]
+    for sig, (f, a) in zip(sigs, res):
+        gf, ga = sfft.sort_result(_np(f), _np(a))
+        order = np.lexsort(sig.freqs.T[::-1])
+        assert np.array_equal(gf, sig.freqs[order])
+        assert np.max(np.abs(ga - sig.coeffs[order]) / np.abs(sig.coeffs[order])) < FP32_COEFF_TOL
+
+
+def test_graph_single_signal(sfft):
+    wl = WORKLOADS["d5_N1024_k1000"]
+    sig = wl.signal(seed_offset=9)
+    plan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, graph=True)
+    s = sfft.Signal(sig.freqs, sig.coeffs, sig.N)
+    for _ in range(2):
+        f, a, status, stats = plan.execute(s)
+        gf, ga = sfft.sort_result(_np(f), _np(a))
+        order = np.lexsort(sig.freqs.T[::-1])
+        assert status == 0 and np.array_equal(gf, sig.freqs[order])
+
+
+def test_paper_estimator_option(sfft):
+    # coefficient a = Y_0[h] / p exactly as printed in Eq. 41, against the oracle with the same estimator
+    wl = WORKLOADS["d2_N1024_k16"]
+    sig = wl.signal(seed_offset=3)
+    plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=wl.blocks, coef="set0")
+    f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N))
+    gf, ga = sfft.sort_result(_np(f), _np(a))
+    ref = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, wl.blocks,
+                             th=O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25), estimator="set0")
+    _assert_parity(sig, gf, ga, status, stats, ref, FP32_COEFF_TOL)

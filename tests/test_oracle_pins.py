@@ -162,6 +162,23 @@ def test_collision_is_rejected_and_lone_mode_read_off():
     _check_collision_rejected(O.classify)
 
 
+def test_mean_estimator_equals_eq41_on_single_mode_bins():
+    # Every shifted set of a lone mode gives Y_n = p a e^{2 pi i w_n / N}: the mean estimator
+    # returns a, and on whole recoveries both estimators agree to round-off.
+    d, N, p = 3, 64, 31
+    w = np.array([[20, 3, 60], [40, 33, 1]])
+    a = np.array([-1.1 + 0.3j, 0.6 + 0.6j])
+    Y = O.dft(O.sample_sets(w, a, p, [1, 0, 0], N))
+    for est in ("set0", "mean"):
+        acc = O.classify(Y, p, [1, 0, 0], N, 1e-6, O.Thresholds(), estimator=est)
+        got = {wv: av for _, wv, av in acc}
+        assert abs(got[(20, 3, 60)] - a[0]) < 1e-13 and abs(got[(40, 33, 1)] - a[1]) < 1e-13
+    sig = draw_signal(3, 256, 60, seed=21)
+    r0 = _recover(sig, (2, 1))
+    r1 = _recover(sig, (2, 1), estimator="mean")
+    assert np.array_equal(r0.freqs, r1.freqs) and np.max(np.abs(r0.coeffs - r1.coeffs)) < 1e-12
+
+
 def test_arg_range_is_half_open():
     z = np.array([-1 + 0j, -1 - 1e-300j, 1j, -1j])
     a = O.arg(z)
