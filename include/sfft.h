@@ -203,6 +203,32 @@ sfft_status sfft_classify(sfft_plan plan, int64_t p, const int64_t* u, const voi
                           double eta_bin, int64_t capacity, int32_t* h_out_dev,
                           int32_t* freqs_out_dev, double* coeffs_out_dev, int64_t* n_out);
 
+/* Allocation-free sampling (kernel (a) without a plan).  The paper has no
+ * counterpart: this serves callers that may not allocate device memory at the
+ * point where they need samples (a fixed memory pool that must not grow, a
+ * process that forbids cudaMalloc after start-up, code that cannot own a plan).
+ * Writes the same samples as sfft_sample,
+ *     y[n][x] = sum_j coeffs_j exp(2 pi i w_j . (x u / p + s_n)),  s_0 = 0, s_n = e_n / N,
+ * complex64 [(d+1) x p] to y_out_dev, for K modes (freqs_dev int32 [K x d],
+ * coeffs_dev complex128 [K], frequencies in [box_lo, box_lo + N)), u host int64 [d].
+ * Work is enqueued on `stream` (a cudaStream_t, NULL = default) and the call
+ * returns without waiting; y_out_dev is complete when the stream reaches it.
+ * Scratch: one 8 MiB device array inside the library, present on every GPU
+ * that loads it until the process exits; it must hold p complex64 entries, two
+ * int32 arrays and (d+1) complex64 arrays of K rounded up to 32, each padded to
+ * 256 bytes (for d = 5: p + 7 K' complex64-sized entries up to 8 MiB).  Larger
+ * requests return SFFT_ERR_CAPACITY; d > 32, N > 2^23 or p >= 2^22 return
+ * SFFT_ERR_INVALID_ARG.  The first call on each device looks the array's
+ * device address up (cudaGetSymbolAddress) with that device current, so make
+ * that first call before any stream capture.  All calls share the array, and
+ * each overwrites every scratch entry it reads, so nothing needs clearing; calls
+ * whose work overlaps on the GPU (other streams, other threads) race on it and
+ * must be serialised by the caller.  No cudaMalloc, cudaFree or allocating
+ * library routine is called. */
+sfft_status sfft_sample_noalloc(int d, int64_t N, int64_t p, const int64_t* u, int64_t K,
+                                const int32_t* freqs_dev, const double* coeffs_dev, void* y_out_dev,
+                                int box_lo, void* stream);
+
 /* Plan facts: largest prime any round can use, mode capacity (k + registry),
  * bytes of device memory the plan holds. */
 int64_t sfft_plan_max_prime(sfft_plan plan);

@@ -49,6 +49,8 @@ __global__ void k_signal_copy(int64_t nw, const int32_t* w_src, int32_t* w_dst, 
 
 }  // namespace
 
+void sfft::sfft_record_cuda_error(int e) { g_last_cuda_error = e; }
+
 struct sfft_signal_s {
   int d = 0;
   int64_t N = 0;

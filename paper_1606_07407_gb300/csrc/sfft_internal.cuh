@@ -9,6 +9,9 @@
 
 namespace sfft {
 
+// Stores a cudaError_t for sfft_last_cuda_error() of the calling thread.
+void sfft_record_cuda_error(int e);
+
 // ---------------------------------------------------------------- complex types
 template <typename T> struct V2;
 template <> struct V2<float> { using t = float2; };

@@ -54,7 +54,8 @@ class _Stats(C.Structure):
 EXPORTS = ["sfft_plan_create", "sfft_plan_destroy", "sfft_signal_synthetic", "sfft_signal_destroy",
            "sfft_signal_assign",
            "sfft_execute", "sfft_batch_create", "sfft_batch_destroy", "sfft_batch_device_bytes",
-           "sfft_batch_execute", "sfft_sample", "sfft_dft", "sfft_classify", "sfft_plan_max_prime",
+           "sfft_batch_execute", "sfft_sample", "sfft_sample_noalloc", "sfft_dft", "sfft_classify",
+           "sfft_plan_max_prime",
            "sfft_plan_mode_capacity", "sfft_plan_device_bytes", "sfft_last_cuda_error", "sfft_status_string"]
 
 _lib = None
@@ -98,6 +99,8 @@ def load(path: str | None = None) -> C.CDLL:
     L.sfft_batch_execute.restype = C.c_int
     L.sfft_sample.argtypes = [vp, i64, C.POINTER(i64), i64, vp, vp, vp]
     L.sfft_sample.restype = C.c_int
+    L.sfft_sample_noalloc.argtypes = [C.c_int, i64, i64, C.POINTER(i64), i64, vp, vp, vp, C.c_int, vp]
+    L.sfft_sample_noalloc.restype = C.c_int
     L.sfft_dft.argtypes = [vp, i64, C.c_int, vp, vp]
     L.sfft_dft.restype = C.c_int
     L.sfft_classify.argtypes = [vp, i64, C.POINTER(i64), vp, C.c_double, i64, vp, vp, vp, C.POINTER(i64)]
@@ -259,6 +262,23 @@ class Plan:
                                C.byref(n)), "sfft_classify")
         m = int(n.value)
         return h[:m], w[:m], a[:m]
+
+
+def sample_noalloc(d: int, N: int, p: int, u, freqs: torch.Tensor, coeffs: torch.Tensor, box_lo: int = 0,
+                   stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Samples of kernel (a) through the allocation-free entry point (the library allocates
+    nothing; `out`, if given, receives the complex64 [d+1, p] samples).  Waits for the stream."""
+    L = load()
+    fw = freqs.to(device="cuda", dtype=torch.int32).contiguous()
+    ca = coeffs.to(device="cuda", dtype=torch.complex128).contiguous()
+    y = out if out is not None else torch.empty((d + 1, int(p)), dtype=torch.complex64, device="cuda")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    ua = _i64_array(u)
+    _check(L.sfft_sample_noalloc(int(d), int(N), int(p), ua, int(fw.shape[0]), _ptr(fw), _ptr(ca), _ptr(y),
+                                 int(box_lo), C.c_void_p(stream.cuda_stream)), "sfft_sample_noalloc")
+    stream.synchronize()
+    return y
 
 
 def _stats_dict(st: _Stats) -> dict:
