@@ -19,6 +19,7 @@
 #include <memory>
 
 #include "engine_kernels.cuh"
+#include "fft_reg.cuh"
 #include "fft_smem.cuh"
 #include "sample_tile.cuh"
 
@@ -148,8 +149,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
           }
         }
         const int K = a.force ? a.force_K : r.k_sig + min(r.K_reg, c.reg_cap);
-        r.logL = ceil_log2(2 * p - 1);
-        if (r.logL < 1) r.logL = 1;
+        r.logL = max(ceil_log2(2 * p - 1), 5);   // at least 32 points: one radix-32 pass
         r.big = r.logL > a.single_max_logL;
         r.groups = (c.n_sets + kMaxSetGroup - 1) / kMaxSetGroup;
         r.gsize = (c.n_sets + r.groups - 1) / r.groups;
@@ -414,85 +414,71 @@ __device__ __forceinline__ void max_abs_to(unsigned long long* dst, double v) {
 
 // spectrum of the Bluestein filter b[m] = conj(chirp[|m|]), |m| < p, one block per signal
 template <typename T>
-__global__ void k_filter(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run, RoundCtl* ctl,
+__global__ void __launch_bounds__(kFftThreads, 1) k_filter(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run, RoundCtl* ctl,
                          Scans sc, const c2<T>* __restrict__ tab, const c2<T>* __restrict__ twG, int64_t Lmax,
                          c2<T>* __restrict__ bhat) {
   using C2 = c2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int64_t s_item;
+  __shared__ C2 tw_lo[kTwLo], tw_hi[kSingleMaxLf / kTwLo];
   C2* buf = reinterpret_cast<C2*>(smem_raw);
-  const int64_t total = ctl->n_filt;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(&ctl->ctr_filt, 1ull);
-    __syncthreads();
-    const int64_t item = s_item;
-    __syncthreads();
-    if (item >= total) break;
-    const int s = find_slot(sc.v[SC_FILT], n, item);
-    const SigCfg& c = cfg[s];
-    const SigRun& r = run[s];
-    const int logL = r.logL, L = 1 << logL;
-    C2* tw = buf + L;
-    const C2* chirp = tab + c.tab_off + r.p;
-    for (int j = threadIdx.x; j < L / 2; j += blockDim.x) tw[j] = twG[(int64_t)j * (Lmax >> logL)];
-    for (int x = threadIdx.x; x < L; x += blockDim.x) buf[brev_bits(x, logL)] = filter_value<T>(x, r.p, L, chirp);
-    __syncthreads();
-    fft_dit(buf, L, logL, 1, tw, false);
-    C2* out = bhat + c.bhat_off;
-    for (int x = threadIdx.x; x < L; x += blockDim.x) out[x] = buf[x];
-    __syncthreads();
-  }
+  // one block per item (a loop around the unrolled passes would make them spill)
+  const int64_t item = blockIdx.x;
+  if (item >= ctl->n_filt) return;
+  const int s = find_slot(sc.v[SC_FILT], n, item);
+  const SigCfg& c = cfg[s];
+  const SigRun& r = run[s];
+  const int logL = r.logL, L = 1 << logL;
+  const C2* chirp = tab + c.tab_off + r.p;
+  fft_tables(tw_hi, tw_lo, logL, twG, Lmax);
+  for (int x = threadIdx.x; x < L; x += blockDim.x) buf[fpad(x)] = filter_value<T>(x, r.p, L, chirp);
+  __syncthreads();
+  fft_row<C2, false>(buf, logL, tw_hi, tw_lo);
+  C2* out = bhat + c.bhat_off;
+  for (int x = threadIdx.x; x < L; x += blockDim.x) out[x] = buf[fpad(x)];
 }
 
 template <typename T>
-__global__ void k_dft(int n, const SigCfg* __restrict__ cfg, SigRun* run, RoundCtl* ctl, Scans sc,
+__global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __restrict__ cfg, SigRun* run, RoundCtl* ctl, Scans sc,
                       const c2<T>* __restrict__ part, const c2<T>* __restrict__ tab,
                       const c2<T>* __restrict__ bhat, const c2<T>* __restrict__ twG, int64_t Lmax,
                       c2<T>* __restrict__ Y) {
   using C2 = c2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int64_t s_item;
+  __shared__ C2 tw_lo[kTwLo], tw_hi[kSingleMaxLf / kTwLo];
   C2* buf = reinterpret_cast<C2*>(smem_raw);
-  const int64_t total = ctl->n_rows;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(&ctl->ctr_rows, 1ull);
-    __syncthreads();
-    const int64_t item = s_item;
-    __syncthreads();
-    if (item >= total) break;
-    const int s = find_slot(sc.v[SC_ROWS], n, item);
-    const int row = (int)(item - sc.v[SC_ROWS][s]);
-    const SigCfg& c = cfg[s];
-    const SigRun r = run[s];
-    const int logL = r.logL, L = 1 << logL;
-    const int64_t p = r.p;
-    C2* tw = buf + L;
-    const C2* chirp = tab + c.tab_off + p;
-    const C2* B = bhat + c.bhat_off;
-    for (int j = threadIdx.x; j < L / 2; j += blockDim.x) tw[j] = twG[(int64_t)j * (Lmax >> logL)];
-    for (int x = threadIdx.x; x < L; x += blockDim.x) {
-      C2 v = mk2((T)0, (T)0);
-      if (x < p) v = cmul(chirp[x], sum_splits<T>(part, r, c.n_sets, row, x));
-      buf[brev_bits(x, logL)] = v;
+  // one block per row (a loop around the unrolled passes would make them spill)
+  const int64_t item = blockIdx.x;
+  if (item >= ctl->n_rows) return;
+  const int s = find_slot(sc.v[SC_ROWS], n, item);
+  const int row = (int)(item - sc.v[SC_ROWS][s]);
+  const SigCfg& c = cfg[s];
+  const SigRun r = run[s];
+  const int logL = r.logL, L = 1 << logL;
+  const int64_t p = r.p;
+  const C2* chirp = tab + c.tab_off + p;
+  const C2* B = bhat + c.bhat_off;
+  fft_tables(tw_hi, tw_lo, logL, twG, Lmax);
+  for (int x = threadIdx.x; x < L; x += blockDim.x) {
+    C2 v = mk2((T)0, (T)0);
+    if (x < p) v = cmul(chirp[x], sum_splits<T>(part, r, c.n_sets, row, x));
+    buf[fpad(x)] = v;
+  }
+  __syncthreads();
+  fft_row<C2, false>(buf, logL, tw_hi, tw_lo);
+  for (int k = threadIdx.x; k < L; k += blockDim.x) buf[fpad(k)] = cmul(buf[fpad(k)], B[k]);
+  __syncthreads();
+  fft_row<C2, true>(buf, logL, tw_hi, tw_lo);
+  const T invL = (T)1 / (T)L;
+  C2* out = Y + c.Y_off + (int64_t)row * p;
+  for (int64_t h0 = 0; h0 < p; h0 += blockDim.x) {
+    const int64_t h = h0 + threadIdx.x;
+    double m = 0.0;
+    if (h < p) {
+      const C2 v = cmul(chirp[h], cscale(buf[fpad((int)h)], invL));
+      out[h] = v;
+      m = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
     }
-    __syncthreads();
-    fft_dit(buf, L, logL, 1, tw, false);
-    for (int k = threadIdx.x; k < L; k += blockDim.x) buf[k] = cmul(buf[k], B[k]);
-    __syncthreads();
-    fft_dif(buf, L, logL, 1, tw, true);
-    const T invL = (T)1 / (T)L;
-    C2* out = Y + c.Y_off + (int64_t)row * p;
-    for (int64_t h0 = 0; h0 < p; h0 += blockDim.x) {
-      const int64_t h = h0 + threadIdx.x;
-      double m = 0.0;
-      if (h < p) {
-        const C2 v = cmul(chirp[h], cscale(buf[brev_bits((int)h, logL)], invL));
-        out[h] = v;
-        m = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
-      }
-      if (row == 0) max_abs_to<T>(&run[s].maxy0_bits, sqrt(m));
-    }
-    __syncthreads();
+    if (row == 0) max_abs_to<T>(&run[s].maxy0_bits, sqrt(m));
   }
 }
 
@@ -1015,7 +1001,7 @@ class Engine final : public EngineBase {
       c.sigma = d.sigma;
       c.reg_cap = (int)std::min<int64_t>(2 * d.k + 256, 1LL << 30);
       c.hash_mask = (int)next_pow2(2 * (int64_t)c.reg_cap) - 1;
-      const int64_t Lmax = next_pow2(2 * d.p_max - 1);
+      const int64_t Lmax = std::max<int64_t>(next_pow2(2 * d.p_max - 1), 32);
       c.logL_max = log2i(Lmax);
       c.dirs_off = (int64_t)dirs.size();
       dirs.insert(dirs.end(), d.dirs.begin(), d.dirs.end());
@@ -1057,6 +1043,7 @@ class Engine final : public EngineBase {
         ns_mask_ |= 1u << (gsize - 1);
       }
       part_min += (int64_t)c.n_sets * d.p_max;
+      rows_max_ += c.n_sets;
       pmax_all = std::max(pmax_all, d.p_max);
       small_logL_max_ = std::max(small_logL_max_, std::min(c.logL_max, single_logL));
       k_max_ = std::max<int64_t>(k_max_, d.k);
@@ -1064,7 +1051,7 @@ class Engine final : public EngineBase {
       reg_cap_max_ = std::max<int64_t>(reg_cap_max_, c.reg_cap);
     }
     cfg_host_ = cfg;
-    Lmax_ = next_pow2(2 * pmax_all - 1);
+    Lmax_ = std::max<int64_t>(next_pow2(2 * pmax_all - 1), 32);
     p_max_ = pmax_all;
     part_cap_ = std::max<int64_t>(part_min, (int64_t)(128ll << 20) / (int64_t)sizeof(C2));
     hash_total_ = hashn;
@@ -1114,8 +1101,8 @@ class Engine final : public EngineBase {
     k_twiddles<<<(int)std::min<int64_t>((Lmax_ + 255) / 256, 4096), 256, 0, st_>>>(Lmax_, twG_, sizeof(T) == 8);
     ECHK(cudaGetLastError());
     // launch shapes
-    small_threads_ = small_logL_max_ >= 12 ? 512 : 256;
-    smem_small_ = (size_t)((1 << small_logL_max_) + (1 << small_logL_max_) / 2) * sizeof(C2);
+    small_threads_ = std::max(32, (1 << small_logL_max_) / fft_per_thread<C2>());
+    smem_small_ = (size_t)((1 << small_logL_max_) + (1 << small_logL_max_) / 32) * sizeof(C2);
     ECHK(cudaFuncSetAttribute(k_filter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_small_));
     ECHK(cudaFuncSetAttribute(k_dft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_small_));
     if (any_big_) {
@@ -1193,11 +1180,12 @@ class Engine final : public EngineBase {
     ECHK(mark(2));
     ECHK(launch_samples(launches));
     ECHK(mark(3));
-    k_filter<T><<<n_sm_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_,
-                                                            Lmax_, (C2*)bhat_);
+    k_filter<T><<<n_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_, Lmax_,
+                                                         (C2*)bhat_);
     ECHK(cudaGetLastError());
-    k_dft<T><<<n_sm_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_,
-                                                         (C2*)bhat_, (C2*)twG_, Lmax_, (C2*)Y_);
+    k_dft<T><<<(unsigned)rows_max_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
+                                                                         (C2*)tab_, (C2*)bhat_, (C2*)twG_, Lmax_,
+                                                                         (C2*)Y_);
     ECHK(cudaGetLastError());
     launches[3] += 2;
     if (any_big_) {
@@ -1441,11 +1429,12 @@ class Engine final : public EngineBase {
     const int ns = cfg_host_[0].n_sets;
     ECHK(cudaMemsetAsync(part_, 0, (size_t)ns * p * sizeof(C2), st_));
     ECHK(cudaMemcpyAsync(part_, y, (size_t)n_rows * p * sizeof(C2), cudaMemcpyDeviceToDevice, st_));
-    k_filter<T><<<n_sm_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_,
-                                                            Lmax_, (C2*)bhat_);
+    k_filter<T><<<n_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_, Lmax_,
+                                                         (C2*)bhat_);
     ECHK(cudaGetLastError());
-    k_dft<T><<<n_sm_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_,
-                                                         (C2*)bhat_, (C2*)twG_, Lmax_, (C2*)Y_);
+    k_dft<T><<<(unsigned)rows_max_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
+                                                                         (C2*)tab_, (C2*)bhat_, (C2*)twG_, Lmax_,
+                                                                         (C2*)Y_);
     ECHK(cudaGetLastError());
     if (any_big_) {
       k_bigA<T><<<4 * n_sm_, 256, smem_bigA_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_, (C2*)twG_,
@@ -1499,6 +1488,7 @@ class Engine final : public EngineBase {
   bool profile_ = false, use_graph_ = false, any_big_ = false;
   int logL_big_max_ = 0, small_logL_max_ = 1, small_threads_ = 256, n_ptab_ = 0;
   size_t smem_small_ = 0, smem_bigA_ = 0, smem_bigB_ = 0, bytes_ = 0, host_stage_bytes_ = 0;
+  int64_t rows_max_ = 0;
   int64_t Lmax_ = 2, p_max_ = 2, part_cap_ = 0, hash_total_ = 0, k_max_ = 0, kd_max_ = 0, reg_cap_max_ = 0;
   std::vector<SigCfg> cfg_host_;
   std::vector<void*> allocs_;
