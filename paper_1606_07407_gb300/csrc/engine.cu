@@ -89,7 +89,8 @@ __device__ __forceinline__ void big_geom(int logL, int* M1, int* M2, int* CT, in
 template <typename T>
 __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg* __restrict__ cfg, SigRun* run,
                                                        RoundCtl* ctl, Scans sc, const int32_t* __restrict__ ptab,
-                                                       int n_ptab, const int64_t* __restrict__ dirs,
+                                                       int n_ptab, const int32_t* __restrict__ pfirst, int64_t pfirst_n,
+                                                       const int64_t* __restrict__ dirs,
                                                        const int64_t* __restrict__ plist, int64_t* ubuf,
                                                        HistRec* hist) {
   __shared__ int s_S;
@@ -125,13 +126,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
       } else {
         const int64_t kstar = max((int64_t)c.k - r.n_live, (int64_t)1);
         const int64_t lo = max((int64_t)c.c * kstar, (int64_t)2);
-        int L0 = 0, H0 = n_ptab;   // first prime >= lo
-        while (L0 < H0) {
-          const int mid = (L0 + H0) >> 1;
-          if (ptab[mid] < lo) L0 = mid + 1;
-          else H0 = mid;
-        }
-        const int idx = L0 + i - 1;
+        // pfirst[v] = index of the smallest prime >= v, so the i-th prime >= lo is one lookup away
+        const int64_t idx = lo < pfirst_n ? (int64_t)pfirst[lo] + i - 1 : (int64_t)n_ptab;
         p = idx < n_ptab ? ptab[idx] : -1;
       }
       if (p < 2 || p > c.p_max) {
@@ -1058,12 +1054,23 @@ class Engine final : public EngineBase {
     // prime table up to the largest p any slot can reach
     std::vector<int32_t> ptab = sieve_primes(pmax_all + 2);
     n_ptab_ = (int)ptab.size();
+    // pfirst[v]: index in ptab of the smallest prime >= v, for v <= pmax_all + 1
+    std::vector<int32_t> pfirst((size_t)pmax_all + 2);
+    {
+      size_t q = 0;
+      for (int64_t v = 0; v <= pmax_all + 1; ++v) {
+        while (q < ptab.size() && ptab[q] < v) ++q;
+        pfirst[(size_t)v] = (int32_t)q;
+      }
+    }
+    pfirst_n_ = (int64_t)pfirst.size();
 
     ECHK(alloc(&cfg_, cfg.size() * sizeof(SigCfg)));
     ECHK(alloc(&run_, n_ * sizeof(SigRun)));
     ECHK(alloc(&ctl_, sizeof(RoundCtl)));
     for (int q = 0; q < kNumScans; ++q) ECHK(alloc(&scans_.v[q], (size_t)(n_ + 1) * sizeof(int64_t)));
     ECHK(alloc(&ptab_, ptab.size() * sizeof(int32_t)));
+    ECHK(alloc(&pfirst_, pfirst.size() * sizeof(int32_t)));
     ECHK(alloc(&dirs_, std::max<size_t>(dirs.size(), 1) * sizeof(int64_t)));
     ECHK(alloc(&plist_, std::max<size_t>(plist.size(), 1) * sizeof(int64_t)));
     ECHK(alloc(&tw_, (size_t)tw * sizeof(C2)));
@@ -1094,6 +1101,8 @@ class Engine final : public EngineBase {
     ECHK(cudaMallocHost(&host_stage_, host_stage_bytes_));
     ECHK(cudaMemcpyAsync(cfg_, cfg.data(), cfg.size() * sizeof(SigCfg), cudaMemcpyHostToDevice, st_));
     ECHK(cudaMemcpyAsync(ptab_, ptab.data(), ptab.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
+    ECHK(cudaMemcpyAsync(pfirst_, pfirst.data(), pfirst.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
+    ECHK(cudaStreamSynchronize(st_));   // host vectors go out of scope
     if (!dirs.empty())
       ECHK(cudaMemcpyAsync(dirs_, dirs.data(), dirs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st_));
     if (!plist.empty())
@@ -1172,7 +1181,8 @@ class Engine final : public EngineBase {
       return cudaEventRecord(events_[(size_t)round_idx * 8 + q], st_);
     };
     ECHK(mark(0));
-    k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, dirs_, plist_, u_, hist_);
+    k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_, plist_, u_,
+                                            hist_);
     ECHK(cudaGetLastError());
     ECHK(launch_tables());
     launches[0] += 2;
@@ -1409,7 +1419,8 @@ class Engine final : public EngineBase {
     pa.force = 1;
     pa.force_p = p;
     pa.force_K = K;
-    k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, dirs_, plist_, u_, nullptr);
+    k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_, plist_, u_,
+                                            nullptr);
     ECHK(cudaGetLastError());
     return launch_tables();
   }
@@ -1499,6 +1510,8 @@ class Engine final : public EngineBase {
   RoundCtl* ctl_ = nullptr;
   Scans scans_;
   int32_t* ptab_ = nullptr;
+  int32_t* pfirst_ = nullptr;
+  int64_t pfirst_n_ = 0;
   int64_t* dirs_ = nullptr;
   int64_t* plist_ = nullptr;
   void* tw_ = nullptr;

@@ -13,12 +13,27 @@ namespace sfft {
 
 constexpr int kSampleThreads = kSampleWarps * 32;
 
+// Asynchronous global -> shared copies (cp.async): the gathers of the next chunk's unit
+// roots land in shared memory while the current chunk is being accumulated.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (BYTES == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// staging buffers: two in float (the next chunk is gathered during the current one), one in double
+template <typename T> constexpr int sample_stages() { return sizeof(T) == 4 ? 2 : 1; }
+
 template <typename T, int NS>
 struct SampleSmem {
-  c2<T> Ls[kSampleChunk][32];
-  c2<T> Us[kSampleChunk][4 * rows_per_warp(NS)];
-  c2<T> Cs[kSampleChunk][NS];
-  int al[kSampleChunk], be[kSampleChunk], ga[kSampleChunk];
+  static constexpr int S = sample_stages<T>();
+  c2<T> Ls[S][kSampleChunk][32];
+  c2<T> Us[S][kSampleChunk][4 * rows_per_warp(NS)];
+  c2<T> Cs[S][kSampleChunk][NS];
+  int al[S][kSampleChunk], be[S][kSampleChunk], ga[S][kSampleChunk];
   int64_t item;
 };
 
@@ -32,7 +47,9 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
                             const c2<T>* __restrict__ Cm, const c2<T>* __restrict__ W, c2<T>* __restrict__ part) {
   using C2 = c2<T>;
   constexpr int RW = rows_per_warp(NS);
+  constexpr int ROWS = 4 * RW;
   constexpr int TX = tile_x(NS);
+  constexpr int S = sample_stages<T>();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int p = (int)r.p;
   const float inv_p = 1.0f / (float)p;
@@ -42,7 +59,40 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
   const int x0 = xt * TX;
   const int j_begin = split * r.jper;
   const int j_end = min(K, j_begin + r.jper);
+  const int nchunks = j_end > j_begin ? (j_end - j_begin + kSampleChunk - 1) / kSampleChunk : 0;
   const C2 zero = mk2((T)0, (T)0);
+
+  // mode indices of chunk q into stage b (threads < 32)
+  auto put_index = [&](int b, int al, int ga) {
+    sm.al[b][tid] = al;
+    sm.ga[b][tid] = ga;
+    sm.be[b][tid] = (int)mod_barrett((uint64_t)al * (uint64_t)x0, (uint64_t)p, r.mod_m);
+  };
+  auto load_index = [&](int q, int* al, int* ga) {
+    const int j = j_begin + q * kSampleChunk + tid;
+    *al = (j < j_end) ? alpha[j] : 0;
+    *ga = (j < j_end) ? gam[j] : 0;
+  };
+  // unit roots and per-set coefficients of chunk q into stage b (all threads)
+  auto issue_data = [&](int q, int b) {
+    const int jc = j_begin + q * kSampleChunk;
+    const int nj = min(kSampleChunk, j_end - jc);
+    for (int e = tid; e < kSampleChunk * 32; e += kSampleThreads) {
+      const int jj = e >> 5, ln = e & 31;
+      cp_async<sizeof(C2)>(&sm.Ls[b][jj][ln], W + mod_small((unsigned)sm.al[b][jj] * (unsigned)ln, p, inv_p));
+    }
+    for (int e = tid; e < kSampleChunk * ROWS; e += kSampleThreads) {
+      const int jj = e / ROWS, row = e - jj * ROWS;
+      cp_async<sizeof(C2)>(&sm.Us[b][jj][row],
+                           W + mod_small((unsigned)sm.be[b][jj] + (unsigned)row * (unsigned)sm.ga[b][jj], p, inv_p));
+    }
+    for (int e = tid; e < kSampleChunk * NS; e += kSampleThreads) {
+      const int jj = e / NS, nn = e - jj * NS;
+      if (jj < nj && nn < ns_valid) cp_async<sizeof(C2)>(&sm.Cs[b][jj][nn], Cm + (int64_t)(n0 + nn) * c.Kmax + jc + jj);
+      else sm.Cs[b][jj][nn] = zero;
+    }
+    cp_async_commit();
+  };
 
   T tot[RW][NS][2];
 #pragma unroll
@@ -50,59 +100,75 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
 #pragma unroll
     for (int nn = 0; nn < NS; ++nn) tot[q][nn][0] = tot[q][nn][1] = (T)0;
 
-  for (int jc = j_begin; jc < j_end; jc += kSampleChunk) {
-    const int nj = min(kSampleChunk, j_end - jc);
+  if (nchunks > 0) {
     if (tid < kSampleChunk) {
-      const int al = (tid < nj) ? alpha[jc + tid] : 0;
-      sm.al[tid] = al;
-      sm.ga[tid] = (tid < nj) ? gam[jc + tid] : 0;
-      sm.be[tid] = (int)mod_barrett((uint64_t)al * (uint64_t)x0, (uint64_t)p, r.mod_m);
-    }
-    for (int e = tid; e < kSampleChunk * NS; e += kSampleThreads) {
-      const int jj = e / NS, nn = e - jj * NS;
-      sm.Cs[jj][nn] = (jj < nj && nn < ns_valid) ? Cm[(int64_t)(n0 + nn) * c.Kmax + jc + jj] : zero;
-    }
-    __syncthreads();
-    for (int e = tid; e < kSampleChunk * 32; e += kSampleThreads) {
-      const int jj = e >> 5, ln = e & 31;
-      sm.Ls[jj][ln] = W[mod_small((unsigned)sm.al[jj] * (unsigned)ln, p, inv_p)];
-    }
-    for (int e = tid; e < kSampleChunk * 4 * RW; e += kSampleThreads) {
-      const int jj = e / (4 * RW), row = e - jj * (4 * RW);
-      sm.Us[jj][row] = W[mod_small((unsigned)sm.be[jj] + (unsigned)row * (unsigned)sm.ga[jj], p, inv_p)];
+      int al, ga;
+      load_index(0, &al, &ga);
+      put_index(0, al, ga);
+      if (S == 2 && nchunks > 1) {
+        load_index(1, &al, &ga);
+        put_index(1, al, ga);
+      }
     }
     __syncthreads();
+    issue_data(0, 0);
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  for (int q = 0; q < nchunks; ++q) {
+    const int b = (S == 2) ? (q & 1) : 0;
+    int al_n = 0, ga_n = 0;
+    if (S == 2) {
+      if (q + 1 < nchunks) issue_data(q + 1, b ^ 1);                     // gathers of the next chunk
+      if (tid < kSampleChunk && q + 2 < nchunks) load_index(q + 2, &al_n, &ga_n);   // indices two ahead
+    }
     T acc[RW][NS][2];
 #pragma unroll
-    for (int q = 0; q < RW; ++q)
+    for (int qq = 0; qq < RW; ++qq)
 #pragma unroll
-      for (int nn = 0; nn < NS; ++nn) acc[q][nn][0] = acc[q][nn][1] = (T)0;
+      for (int nn = 0; nn < NS; ++nn) acc[qq][nn][0] = acc[qq][nn][1] = (T)0;
 #pragma unroll 2
     for (int jj = 0; jj < kSampleChunk; ++jj) {
-      const C2 L = sm.Ls[jj][lane];
+      const C2 L = sm.Ls[b][jj][lane];
       C2 E[RW];
 #pragma unroll
-      for (int q = 0; q < RW; ++q) E[q] = cmul(sm.Us[jj][warp * RW + q], L);
+      for (int qq = 0; qq < RW; ++qq) E[qq] = cmul(sm.Us[b][jj][warp * RW + qq], L);
 #pragma unroll
       for (int nn = 0; nn < NS; ++nn) {
-        const C2 cc = sm.Cs[jj][nn];
+        const C2 cc = sm.Cs[b][jj][nn];
 #pragma unroll
-        for (int q = 0; q < RW; ++q) {
-          acc[q][nn][0] = fma(cc.x, E[q].x, acc[q][nn][0]);
-          acc[q][nn][0] = fma(-cc.y, E[q].y, acc[q][nn][0]);
-          acc[q][nn][1] = fma(cc.x, E[q].y, acc[q][nn][1]);
-          acc[q][nn][1] = fma(cc.y, E[q].x, acc[q][nn][1]);
+        for (int qq = 0; qq < RW; ++qq) {
+          acc[qq][nn][0] = fma(cc.x, E[qq].x, acc[qq][nn][0]);
+          acc[qq][nn][0] = fma(-cc.y, E[qq].y, acc[qq][nn][0]);
+          acc[qq][nn][1] = fma(cc.x, E[qq].y, acc[qq][nn][1]);
+          acc[qq][nn][1] = fma(cc.y, E[qq].x, acc[qq][nn][1]);
         }
       }
     }
 #pragma unroll
-    for (int q = 0; q < RW; ++q)
+    for (int qq = 0; qq < RW; ++qq)
 #pragma unroll
       for (int nn = 0; nn < NS; ++nn) {
-        tot[q][nn][0] += acc[q][nn][0];
-        tot[q][nn][1] += acc[q][nn][1];
+        tot[qq][nn][0] += acc[qq][nn][0];
+        tot[qq][nn][1] += acc[qq][nn][1];
       }
-    __syncthreads();
+    if (S == 2) {
+      // stage b is free again: it takes the indices of chunk q + 2
+      if (tid < kSampleChunk && q + 2 < nchunks) put_index(b, al_n, ga_n);
+      cp_async_wait_all();
+      __syncthreads();
+    } else if (q + 1 < nchunks) {
+      __syncthreads();   // every thread is done with the single stage
+      if (tid < kSampleChunk) {
+        int al, ga;
+        load_index(q + 1, &al, &ga);
+        put_index(0, al, ga);
+      }
+      __syncthreads();
+      issue_data(q + 1, 0);
+      cp_async_wait_all();
+      __syncthreads();
+    }
   }
   C2* out = part + r.part_off;
 #pragma unroll
