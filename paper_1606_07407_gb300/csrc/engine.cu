@@ -149,7 +149,13 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
         r.big = r.logL > a.single_max_logL;
         r.groups = (c.n_sets + kMaxSetGroup - 1) / kMaxSetGroup;
         r.gsize = (c.n_sets + r.groups - 1) / r.groups;
-        r.n_xt = (int)((p + tile_x(r.gsize) - 1) / tile_x(r.gsize));
+        {
+          // a tile's four warps split into mode groups when p is shorter than the tile
+          const int rowx = 32 * rows_per_warp(r.gsize);
+          r.mgroups = (sizeof(T) != 4) ? 1 : (p <= rowx ? 4 : (p <= 2 * rowx ? 2 : 1));
+          const int tx = tile_x(r.gsize) / r.mgroups;
+          r.n_xt = (int)((p + tx - 1) / tx);
+        }
         r.chunks = K > 0 ? (K + kSampleChunk - 1) / kSampleChunk : 1;
         r.any_occupied = 0;
         r.n_acc = 0;
@@ -217,8 +223,9 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
         v[SC_SAMP0 + r.gsize - 1] = (int64_t)r.n_xt * r.groups * r.splits;
         v[SC_BINS] = r.p;
         if (!r.big) {
-          v[SC_ROWS] = c.n_sets;
-          v[SC_FILT] = 1;
+          const bool sm = r.logL <= kSmallFftLog;
+          v[sm ? SC_ROWS_S : SC_ROWS] = c.n_sets;
+          v[sm ? SC_FILT_S : SC_FILT] = 1;
         } else {
           int M1, M2, CT, RT;
           big_geom(r.logL, &M1, &M2, &CT, &RT);
@@ -260,6 +267,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     c.n_bigA = carry[SC_BIGA];
     c.n_bigB = carry[SC_BIGB];
     c.n_bigC = carry[SC_BIGC];
+    c.n_rows_s = carry[SC_ROWS_S];
+    c.n_filt_s = carry[SC_FILT_S];
     c.ctr_rows = c.ctr_filt = 0ull;
     *ctl = c;
     if (a.use_cond) cudaGraphSetConditional(a.cond, tot_active > 0 ? 1u : 0u);
@@ -412,15 +421,15 @@ __device__ __forceinline__ void max_abs_to(unsigned long long* dst, double v) {
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, 1) k_filter(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run, RoundCtl* ctl,
                          Scans sc, const c2<T>* __restrict__ tab, const c2<T>* __restrict__ twG, int64_t Lmax,
-                         c2<T>* __restrict__ bhat) {
+                         c2<T>* __restrict__ bhat, int small) {
   using C2 = c2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ C2 tw_lo[kTwLo], tw_hi[kSingleMaxLf / kTwLo];
   C2* buf = reinterpret_cast<C2*>(smem_raw);
   // one block per item (a loop around the unrolled passes would make them spill)
   const int64_t item = blockIdx.x;
-  if (item >= ctl->n_filt) return;
-  const int s = find_slot(sc.v[SC_FILT], n, item);
+  if (item >= (small ? ctl->n_filt_s : ctl->n_filt)) return;
+  const int s = find_slot(sc.v[small ? SC_FILT_S : SC_FILT], n, item);
   const SigCfg& c = cfg[s];
   const SigRun& r = run[s];
   const int logL = r.logL, L = 1 << logL;
@@ -437,16 +446,17 @@ template <typename T>
 __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __restrict__ cfg, SigRun* run, RoundCtl* ctl, Scans sc,
                       const c2<T>* __restrict__ part, const c2<T>* __restrict__ tab,
                       const c2<T>* __restrict__ bhat, const c2<T>* __restrict__ twG, int64_t Lmax,
-                      c2<T>* __restrict__ Y) {
+                      c2<T>* __restrict__ Y, int small) {
   using C2 = c2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ C2 tw_lo[kTwLo], tw_hi[kSingleMaxLf / kTwLo];
   C2* buf = reinterpret_cast<C2*>(smem_raw);
   // one block per row (a loop around the unrolled passes would make them spill)
   const int64_t item = blockIdx.x;
-  if (item >= ctl->n_rows) return;
-  const int s = find_slot(sc.v[SC_ROWS], n, item);
-  const int row = (int)(item - sc.v[SC_ROWS][s]);
+  if (item >= (small ? ctl->n_rows_s : ctl->n_rows)) return;
+  const int64_t* scan = sc.v[small ? SC_ROWS_S : SC_ROWS];
+  const int s = find_slot(scan, n, item);
+  const int row = (int)(item - scan[s]);
   const SigCfg& c = cfg[s];
   const SigRun r = run[s];
   const int logL = r.logL, L = 1 << logL;
@@ -1147,6 +1157,29 @@ class Engine final : public EngineBase {
     return cudaGetLastError();
   }
 
+  // Bluestein rows of one block each, in two classes: short rows (L <= 2^kSmallFftLog) in
+  // small-memory blocks, so many fit on an SM, and the longer rows
+  cudaError_t launch_dft_rows() {
+    const int ls = std::min(small_logL_max_, kSmallFftLog);
+    const int thr_s = std::max(32, (1 << ls) / fft_per_thread<C2>());
+    const size_t smem_s = (size_t)((1 << ls) + (1 << ls) / 32) * sizeof(C2);
+    k_filter<T><<<n_, thr_s, smem_s, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_, Lmax_, (C2*)bhat_, 1);
+    ECHK(cudaGetLastError());
+    k_dft<T><<<(unsigned)rows_max_, thr_s, smem_s, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_,
+                                                          (C2*)bhat_, (C2*)twG_, Lmax_, (C2*)Y_, 1);
+    ECHK(cudaGetLastError());
+    if (small_logL_max_ > kSmallFftLog) {
+      k_filter<T><<<n_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_,
+                                                           Lmax_, (C2*)bhat_, 0);
+      ECHK(cudaGetLastError());
+      k_dft<T><<<(unsigned)rows_max_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
+                                                                           (C2*)tab_, (C2*)bhat_, (C2*)twG_, Lmax_,
+                                                                           (C2*)Y_, 0);
+      ECHK(cudaGetLastError());
+    }
+    return cudaSuccess;
+  }
+
   // one persistent sampling launch per set-group size present in the batch
   cudaError_t launch_samples(int64_t* launches) {
     for (int ns = 1; ns <= kMaxSetGroup; ++ns) {
@@ -1190,14 +1223,8 @@ class Engine final : public EngineBase {
     ECHK(mark(2));
     ECHK(launch_samples(launches));
     ECHK(mark(3));
-    k_filter<T><<<n_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_, Lmax_,
-                                                         (C2*)bhat_);
-    ECHK(cudaGetLastError());
-    k_dft<T><<<(unsigned)rows_max_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
-                                                                         (C2*)tab_, (C2*)bhat_, (C2*)twG_, Lmax_,
-                                                                         (C2*)Y_);
-    ECHK(cudaGetLastError());
-    launches[3] += 2;
+    ECHK(launch_dft_rows());
+    launches[3] += small_logL_max_ > kSmallFftLog ? 4 : 2;
     if (any_big_) {
       k_bigA<T><<<4 * n_sm_, 256, smem_bigA_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_, (C2*)twG_,
                                                      Lmax_, (C2*)Z_);
@@ -1440,13 +1467,7 @@ class Engine final : public EngineBase {
     const int ns = cfg_host_[0].n_sets;
     ECHK(cudaMemsetAsync(part_, 0, (size_t)ns * p * sizeof(C2), st_));
     ECHK(cudaMemcpyAsync(part_, y, (size_t)n_rows * p * sizeof(C2), cudaMemcpyDeviceToDevice, st_));
-    k_filter<T><<<n_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_, Lmax_,
-                                                         (C2*)bhat_);
-    ECHK(cudaGetLastError());
-    k_dft<T><<<(unsigned)rows_max_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
-                                                                         (C2*)tab_, (C2*)bhat_, (C2*)twG_, Lmax_,
-                                                                         (C2*)Y_);
-    ECHK(cudaGetLastError());
+    ECHK(launch_dft_rows());
     if (any_big_) {
       k_bigA<T><<<4 * n_sm_, 256, smem_bigA_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_, (C2*)twG_,
                                                      Lmax_, (C2*)Z_);

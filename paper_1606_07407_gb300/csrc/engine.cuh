@@ -59,6 +59,8 @@ struct SigRun {
   int k_sig;          // modes of the bound black box
   int logL, big;      // Bluestein length of the round; big = four-step path
   int n_xt, groups, gsize, chunks, jper, splits;
+  int mgroups;        // mode groups per sampling tile (warps sharing rows when p is small)
+  int pad3;
   int64_t p;
   unsigned long long mod_m;   // floor((2^64 - 1) / p), Barrett reduction
   int64_t part_off;
@@ -71,18 +73,20 @@ struct SigRun {
 // Work totals of the round (exclusive scans over signals are in Scans).
 struct RoundCtl {
   int active, round, splits, pad;
-  int64_t n_tab, n_mode, n_rows, n_filt, n_bins, n_bigA, n_bigB, n_bigC;
+  int64_t n_tab, n_mode, n_rows, n_filt, n_bins, n_bigA, n_bigB, n_bigC, n_rows_s, n_filt_s;
   int64_t n_samp[kMaxSetGroup];               // sampling tiles, per set-group size
   unsigned long long ctr_samp[kMaxSetGroup], ctr_rows, ctr_filt;
 };
 
-// exclusive scans over signals: tables, modes, DFT rows, filters, bins, four-step passes,
-// then sampling tiles for each set-group size 1..kMaxSetGroup
-constexpr int kNumScans = 8 + kMaxSetGroup;
+// exclusive scans over signals: tables, modes, DFT rows, filters, bins, four-step passes, DFT
+// rows and filters of short lengths, then sampling tiles for each set-group size 1..kMaxSetGroup
+constexpr int kNumScans = 10 + kMaxSetGroup;
 struct Scans {
   int64_t* v[kNumScans];       // each [n + 1]
 };
-enum { SC_TAB = 0, SC_MODE, SC_ROWS, SC_FILT, SC_BINS, SC_BIGA, SC_BIGB, SC_BIGC, SC_SAMP0 };
+enum { SC_TAB = 0, SC_MODE, SC_ROWS, SC_FILT, SC_BINS, SC_BIGA, SC_BIGB, SC_BIGC, SC_ROWS_S, SC_FILT_S, SC_SAMP0 };
+
+constexpr int kSmallFftLog = 11;   // Bluestein rows up to 2048 points run in small-memory blocks
 
 struct HistRec {
   int64_t p;

@@ -88,6 +88,7 @@ k_na_sample(NoAllocArgs a, const int32_t* __restrict__ alpha, const int32_t* __r
   r.groups = a.groups;
   r.n_xt = a.n_xt;
   r.splits = 1;
+  r.mgroups = 1;
   r.jper = a.Kpad > 0 ? a.Kpad : kSampleChunk;
   const int xt = blockIdx.x, g = blockIdx.y;
   sample_tile<float, NS>(sm, c, r, xt, g, 0, alpha, gam, Cm, W, y);

@@ -48,9 +48,13 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
   using C2 = c2<T>;
   constexpr int RW = rows_per_warp(NS);
   constexpr int ROWS = 4 * RW;
-  constexpr int TX = tile_x(NS);
   constexpr int S = sample_stages<T>();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // G mode groups of 4 / G warps: a group covers all rows of the tile and takes every G-th mode
+  const int G = r.mgroups;
+  const int wpg = 4 / G;
+  const int grp = warp / wpg, wrow = warp - grp * wpg;
+  const int TX = 32 * RW * wpg;
   const int p = (int)r.p;
   const float inv_p = 1.0f / (float)p;
   const int n0 = g * r.gsize;
@@ -128,11 +132,11 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
 #pragma unroll
       for (int nn = 0; nn < NS; ++nn) acc[qq][nn][0] = acc[qq][nn][1] = (T)0;
 #pragma unroll 2
-    for (int jj = 0; jj < kSampleChunk; ++jj) {
+    for (int jj = grp; jj < kSampleChunk; jj += G) {
       const C2 L = sm.Ls[b][jj][lane];
       C2 E[RW];
 #pragma unroll
-      for (int qq = 0; qq < RW; ++qq) E[qq] = cmul(sm.Us[b][jj][warp * RW + qq], L);
+      for (int qq = 0; qq < RW; ++qq) E[qq] = cmul(sm.Us[b][jj][wrow * RW + qq], L);
 #pragma unroll
       for (int nn = 0; nn < NS; ++nn) {
         const C2 cc = sm.Cs[b][jj][nn];
@@ -170,10 +174,37 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
       __syncthreads();
     }
   }
+  if (G > 1) {
+    // add the other mode groups' totals into group 0 through the (now free) staging memory
+    constexpr int KK = RW * NS * 2;
+    T* red = reinterpret_cast<T*>(&sm.Ls[0][0][0]);
+    __syncthreads();
+    if (grp > 0) {
+#pragma unroll
+      for (int q = 0; q < RW; ++q)
+#pragma unroll
+        for (int nn = 0; nn < NS; ++nn)
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) red[((warp - wpg) * KK + (q * NS + nn) * 2 + cc) * 32 + lane] = tot[q][nn][cc];
+    }
+    __syncthreads();
+    if (grp == 0) {
+      for (int gg = 1; gg < G; ++gg) {
+        const int w2 = wrow + gg * wpg - wpg;
+#pragma unroll
+        for (int q = 0; q < RW; ++q)
+#pragma unroll
+          for (int nn = 0; nn < NS; ++nn)
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) tot[q][nn][cc] += red[(w2 * KK + (q * NS + nn) * 2 + cc) * 32 + lane];
+      }
+    }
+    if (grp > 0) return;
+  }
   C2* out = part + r.part_off;
 #pragma unroll
   for (int q = 0; q < RW; ++q) {
-    const int x = x0 + (warp * RW + q) * 32 + lane;
+    const int x = x0 + (wrow * RW + q) * 32 + lane;
     if (x < p) {
 #pragma unroll
       for (int nn = 0; nn < NS; ++nn)
