@@ -435,10 +435,12 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_filter(int n, const SigCfg* 
   const int logL = r.logL, L = 1 << logL;
   const C2* chirp = tab + c.tab_off + r.p;
   fft_tables(tw_hi, tw_lo, logL, twG, Lmax);
+#pragma unroll 8
   for (int x = threadIdx.x; x < L; x += blockDim.x) buf[fpad(x)] = filter_value<T>(x, r.p, L, chirp);
   __syncthreads();
   fft_row<C2, false>(buf, logL, tw_hi, tw_lo);
   C2* out = bhat + c.bhat_off;
+#pragma unroll 8
   for (int x = threadIdx.x; x < L; x += blockDim.x) out[x] = buf[fpad(x)];
 }
 
@@ -464,6 +466,8 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   const C2* chirp = tab + c.tab_off + p;
   const C2* B = bhat + c.bhat_off;
   fft_tables(tw_hi, tw_lo, logL, twG, Lmax);
+  // loops unrolled so that each thread's global loads are in flight together
+#pragma unroll 8
   for (int x = threadIdx.x; x < L; x += blockDim.x) {
     C2 v = mk2((T)0, (T)0);
     if (x < p) v = cmul(chirp[x], sum_splits<T>(part, r, c.n_sets, row, x));
@@ -471,11 +475,13 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   }
   __syncthreads();
   fft_row<C2, false>(buf, logL, tw_hi, tw_lo);
+#pragma unroll 8
   for (int k = threadIdx.x; k < L; k += blockDim.x) buf[fpad(k)] = cmul(buf[fpad(k)], B[k]);
   __syncthreads();
   fft_row<C2, true>(buf, logL, tw_hi, tw_lo);
   const T invL = (T)1 / (T)L;
   C2* out = Y + c.Y_off + (int64_t)row * p;
+#pragma unroll 4
   for (int64_t h0 = 0; h0 < p; h0 += blockDim.x) {
     const int64_t h = h0 + threadIdx.x;
     double m = 0.0;
@@ -1238,7 +1244,7 @@ class Engine final : public EngineBase {
     }
     ECHK(mark(4));
     ClassifyOut co{nullptr, nullptr, nullptr, 0, nullptr, nullptr, -1.0};
-    k_classify<T><<<4 * n_sm_, 128, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)Y_, u_, regw_, rega_, (C2*)regtw_,
+    k_classify<T><<<16 * n_sm_, 256, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)Y_, u_, regw_, rega_, (C2*)regtw_,
                                               hash_, co);
     ECHK(cudaGetLastError());
     launches[4] += 1;
@@ -1489,7 +1495,7 @@ class Engine final : public EngineBase {
     ECHK(cudaMemsetAsync(stepc_, 0, 2 * sizeof(int), st_));
     int* cnt = reinterpret_cast<int*>(stepc_);
     ClassifyOut co{h_out, w_out, a_out, (int)cap, cnt, cnt + 1, eta};
-    k_classify<T><<<4 * n_sm_, 128, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)Y_, u_, regw_, rega_, (C2*)regtw_,
+    k_classify<T><<<16 * n_sm_, 256, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)Y_, u_, regw_, rega_, (C2*)regtw_,
                                               hash_, co);
     ECHK(cudaGetLastError());
     int* h = reinterpret_cast<int*>(reinterpret_cast<char*>(host_stage_) + stage_st_);

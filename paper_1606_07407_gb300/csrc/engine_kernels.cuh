@@ -64,12 +64,12 @@ __device__ __forceinline__ int find_slot(const int64_t* __restrict__ scan, int n
   return lo;
 }
 
-// Exclusive scan of V values per thread over a block of kPlanThreads threads.
+// Exclusive scan of V values per thread over the block (a multiple of 32 threads, at most 1024).
 template <int V>
 __device__ void block_scan_excl(int64_t (&v)[V], int64_t (&tot)[V]) {
   __shared__ int64_t ws[32][V];
   __shared__ int64_t wt[V];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   int64_t incl[V];
 #pragma unroll
   for (int q = 0; q < V; ++q) {
@@ -86,7 +86,7 @@ __device__ void block_scan_excl(int64_t (&v)[V], int64_t (&tot)[V]) {
   if (wid == 0) {
 #pragma unroll
     for (int q = 0; q < V; ++q) {
-      int64_t x = ws[lane][q];
+      int64_t x = lane < nwarps ? ws[lane][q] : 0;
       const int64_t own = x;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
