@@ -325,24 +325,56 @@ class Batch:
         return caps, fo, co
 
     def execute(self, signals, out=None, allow=(0,)):
-        """Returns ([(freqs [n_s, d_s], coeffs [n_s])...], statuses, stats) with device tensors."""
+        """Returns (results, statuses, stats); results[s] is (freqs [n_s, d_s], coeffs [n_s]) as
+        device tensors, sliced from the flat outputs when it is indexed."""
         L = load()
         caps, fo, co = out if out is not None else self.outputs()
-        sig = (C.c_void_p * self.n)(*[s._h.value for s in signals])
-        capa = (C.c_int64 * self.n)(*caps)
+        handles = tuple(s._h.value for s in signals)
+        if handles != getattr(self, "_sig_key", None):       # the handle array is kept between calls
+            self._sig_key = handles
+            self._sig_arr = (C.c_void_p * self.n)(*handles)
+        if getattr(self, "_caps_key", None) != tuple(caps):
+            self._caps_key = tuple(caps)
+            self._caps_arr = (C.c_int64 * self.n)(*caps)
         nf = (C.c_int64 * self.n)()
         sts = (C.c_int32 * self.n)()
         st = _Stats()
-        status = L.sfft_batch_execute(self._h, sig, capa, _ptr(fo), _ptr(co), nf, sts, C.byref(st))
+        status = L.sfft_batch_execute(self._h, self._sig_arr, self._caps_arr, _ptr(fo), _ptr(co), nf, sts,
+                                      C.byref(st))
         _check(status, "sfft_batch_execute", ok=allow)
-        res = []
-        r0 = e0 = 0
-        for s in range(self.n):
-            m = min(int(nf[s]), caps[s])
-            res.append((fo[e0:e0 + m * self.d[s]].view(m, self.d[s]), co[r0:r0 + m]))
-            r0 += caps[s]
-            e0 += caps[s] * self.d[s]
-        return res, list(sts), _stats_dict(st)
+        return BatchResults(self.d, caps, fo, co, list(nf)), list(sts), _stats_dict(st)
+
+
+class BatchResults:
+    """Per-signal results of one batched execution.  Building hundreds of tensor views costs
+    milliseconds of host time, so an entry is sliced from the flat outputs only when asked for."""
+
+    def __init__(self, d, caps, fo, co, n_found):
+        self.n_found = n_found
+        self._d, self._fo, self._co = d, fo, co
+        self._caps = caps
+        self._r0 = self._e0 = None
+
+    def __len__(self):
+        return len(self._caps)
+
+    def __getitem__(self, s):
+        if isinstance(s, slice):
+            return [self[i] for i in range(*s.indices(len(self)))]
+        if s < 0:
+            s += len(self)
+        if not 0 <= s < len(self):
+            raise IndexError(s)
+        if self._r0 is None:
+            self._r0 = np.concatenate([[0], np.cumsum(self._caps)]).tolist()
+            self._e0 = np.concatenate([[0], np.cumsum([c * d for c, d in zip(self._caps, self._d)])]).tolist()
+        m = min(int(self.n_found[s]), self._caps[s])
+        r0, e0, d = self._r0[s], self._e0[s], self._d[s]
+        return self._fo[e0:e0 + m * d].view(m, d), self._co[r0:r0 + m]
+
+    def __iter__(self):
+        for s in range(len(self)):
+            yield self[s]
 
 
 def sort_result(freqs: np.ndarray, coeffs: np.ndarray):

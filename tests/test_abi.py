@@ -57,3 +57,22 @@ def test_invalid_arguments_rejected_without_gpu(lib):
 
 def test_library_is_built_for_sm103a():
     assert "arch=compute_103a,code=sm_103a" in " ".join(B.ARCH)
+
+
+def test_batch_results_slice_each_signal_from_the_flat_outputs():
+    torch = pytest.importorskip("torch")
+    from paper_1606_07407_gb300.sfft import BatchResults
+    d, caps, found = [2, 3, 1], [4, 2, 5], [3, 7, 0]      # the second signal overflowed its capacity
+    fo = torch.arange(sum(c * k for c, k in zip(caps, d)), dtype=torch.int32)
+    co = torch.arange(sum(caps), dtype=torch.float64).to(torch.complex128)
+    res = BatchResults(d, caps, fo, co, found)
+    assert len(res) == 3
+    f0, a0 = res[0]
+    assert f0.shape == (3, 2) and f0.flatten().tolist() == list(range(6)) and a0.real.tolist() == [0, 1, 2]
+    f1, a1 = res[1]
+    assert f1.shape == (2, 3) and f1.flatten().tolist() == list(range(8, 14)) and a1.real.tolist() == [4, 5]
+    f2, a2 = res[-1]
+    assert f2.shape == (0, 1) and a2.numel() == 0
+    assert [f.shape[0] for f, _ in res] == [3, 2, 0] and len(res[1:]) == 2
+    with pytest.raises(IndexError):
+        res[3]
