@@ -145,6 +145,28 @@ def sample_sets(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int,
     return y
 
 
+def registry_bins(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int) -> np.ndarray:
+    """The DFT of the samples of g = sum_j coeffs_j e^{2 pi i w_j . t}, written without sampling:
+    sample set n of one mode is a_j e^{2 pi i w_{j,n} / N} W^{alpha_j x} with alpha_j = (w_j . u)
+    mod p (see sample_sets), and sum_x W^{(alpha_j - h) x} is p when h = alpha_j and 0 otherwise
+    (the DFT of Sec. 2.1), so G[n, h] = p sum_{j : alpha_j = h} a_j e^{2 pi i w_{j,n} / N}
+    (the factor is 1 for n = 0).  Removing g from the transform instead of from the samples
+    is the adaptive step of Alg. 2 (Sec. 5, "Algorithm") by the linearity of the DFT."""
+    freqs = np.asarray(freqs, dtype=np.int64)
+    coeffs = np.asarray(coeffs, dtype=np.complex128)
+    K, d = freqs.shape
+    G = np.zeros((d + 1, p), dtype=np.complex128)
+    if K == 0:
+        return G
+    u_mod = np.array([int(v) % p for v in u], dtype=np.int64)
+    alpha = (freqs @ u_mod) % p
+    for j in range(K):
+        G[0, alpha[j]] += p * coeffs[j]
+        for n in range(1, d + 1):
+            G[n, alpha[j]] += p * coeffs[j] * np.exp(2j * np.pi * (int(freqs[j, n - 1]) % N) / N)
+    return G
+
+
 def dft(y: np.ndarray) -> np.ndarray:
     """Y[h] = sum_x y[x] exp(-2 pi i h x / p) along the last axis (the DFT defined in Sec. 2.1)."""
     return np.fft.fft(y, axis=-1)
@@ -226,12 +248,16 @@ class Result:
 def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int = 5,
                      th: Thresholds | None = None, max_rounds: int | None = None,
                      box_lo: int = 0, primes=None, dirs=None, noise=None,
-                     estimator: str = "set0") -> Result:
+                     estimator: str = "set0", residual: str = "samples") -> Result:
     """Algorithm 2 (MultiPhaseshift) on the black box f = sum_j coeffs_j e^{2 pi i freqs_j . t}.
 
     ``primes``, if given, overrides the prime rule (round i uses primes[(i-1) mod len]).
     ``noise``, if given, is a callable (i, p, d) -> complex array [d+1, p] added to the
-    black-box samples of round i."""
+    black-box samples of round i.  ``residual`` says where g (built from the registry) leaves
+    f: "samples" evaluates f - g at every sample point, as Alg. 2 writes it; "bins" samples f
+    alone and subtracts the transform of g bin by bin (registry_bins)."""
+    if residual not in ("samples", "bins"):
+        raise ValueError(residual)
     th = th or Thresholds()
     freqs = np.asarray(freqs, dtype=np.int64).reshape(-1, d)
     coeffs = np.asarray(coeffs, dtype=np.complex128).reshape(-1)
@@ -249,7 +275,7 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
              else ith_prime_at_least(i, c * k_star))
         u = line_direction(d, N, blocks, i, dirs)
         # f - g: black-box modes with +a, registry modes with -a (Alg. 2: g is built from R)
-        if R:
+        if R and residual == "samples":
             reg_w = np.array(list(R.keys()), dtype=np.int64).reshape(-1, d)
             reg_a = -np.array(list(R.values()), dtype=np.complex128)
             all_w = np.concatenate([freqs, reg_w])
@@ -260,6 +286,9 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
         if noise is not None:
             y = y + noise(i, p, d)
         Y = dft(y)
+        if R and residual == "bins":
+            reg_w = np.array(list(R.keys()), dtype=np.int64).reshape(-1, d)
+            Y = Y - registry_bins(reg_w, np.array(list(R.values()), dtype=np.complex128), p, u, N)
         if a_ref is None:
             a_ref = float(np.max(np.abs(Y[0]))) / p if p > 0 else 0.0
         eta_bin = max(th.rho * p * a_ref, 6.0 * th.sigma * math.sqrt(p))

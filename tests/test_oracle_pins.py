@@ -143,6 +143,57 @@ def test_parseval_on_samples():
     assert np.allclose(lhs, rhs, rtol=1e-12)
 
 
+# ---------------------------------------------------------------- registry in the bin domain
+
+def _check_registry_bins(bins_fn):
+    # (1) one mode: a delta at alpha = (w . u) mod p holding p a e^{2 pi i w_n / N} (closed form);
+    # (2) modes sharing a bin add; (3) many modes: equal to the transform of their samples,
+    # both pinned on their own above (brute-force rational points, the DFT definition).
+    d, N, p = 4, 1024, 211
+    u = [1, N, 0, 0]
+    w = np.array([[700, 13, 1000, 512]])
+    a = np.array([1.5 - 0.25j])
+    h = (700 + 13 * N) % p
+    G = bins_fn(w, a, p, u, N)
+    assert G.shape == (d + 1, p)
+    assert abs(G[0, h] - p * a[0]) < 1e-9
+    for n in range(1, d + 1):
+        assert abs(G[n, h] - p * a[0] * np.exp(2j * np.pi * w[0, n - 1] / N)) < 1e-9
+    G[:, h] = 0
+    assert np.max(np.abs(G)) == 0.0
+    w2 = np.array([[3, 5, 0, 9], [3 + p, 5, 0, 9], [3, 5, 7, 9]])   # first two share a bin (and w_2..)
+    a2 = np.array([1.0 + 1.0j, -0.5 + 2.0j, 0.25j])
+    G2 = bins_fn(w2, a2, p, u, N)
+    h2 = (3 + 5 * N) % p
+    assert abs(G2[0, h2] - p * np.sum(a2)) < 1e-9
+    assert abs(G2[1, h2] - p * (a2[0] * np.exp(2j * np.pi * 3 / N) + a2[1] * np.exp(2j * np.pi * (3 + p) / N)
+                                + a2[2] * np.exp(2j * np.pi * 3 / N))) < 1e-9
+    sig = draw_signal(d, N, 300, seed=77)
+    G3 = bins_fn(sig.freqs, sig.coeffs, p, u, N)
+    Y3 = O.dft(O.sample_sets(sig.freqs, sig.coeffs, p, u, N))
+    assert np.max(np.abs(G3 - Y3)) < 1e-9 * p * np.sum(np.abs(sig.coeffs))
+
+
+def test_registry_bins_equal_transform_of_registry_samples():
+    _check_registry_bins(O.registry_bins)
+
+
+def test_bin_domain_residual_recovers_the_same_result():
+    # subtracting g after the transform (linearity) gives the same sets and, in FP64, the same
+    # coefficients as subtracting it from the samples
+    for d, N, k, blocks, seed in ((2, 1024, 16, (1, 1), 3), (5, 1024, 200, (3, 2), 4), (3, 256, 60, (3,), 5)):
+        sig = draw_signal(d, N, k, seed=seed, r_lo=1.0, r_hi=10.0)
+        th = O.Thresholds(tau=1e-7, rho=2.0 ** -40, delta=0.1)
+        lit = O.multi_phaseshift(sig.freqs, sig.coeffs, d, N, k, blocks, th=th)
+        bins = O.multi_phaseshift(sig.freqs, sig.coeffs, d, N, k, blocks, th=th, residual="bins")
+        planted = sig.freqs[np.lexsort(sig.freqs.T[::-1])]
+        assert lit.converged and bins.converged
+        assert np.array_equal(bins.freqs, planted) and np.array_equal(lit.freqs, planted)
+        assert np.max(np.abs(bins.coeffs - lit.coeffs) / np.abs(lit.coeffs)) < 1e-12
+        assert [r["p"] for r in bins.rounds] == [r["p"] for r in lit.rounds]
+        assert all(rb["terms"] == k for rb in bins.rounds)
+
+
 # ---------------------------------------------------------------- bin test and decode
 
 def _check_collision_rejected(classify_fn):
@@ -334,3 +385,18 @@ def test_planted_mistakes_are_caught(monkeypatch):
 
     with pytest.raises(AssertionError):
         _check_full_grid(coeff_conj)
+
+    real_bins = O.registry_bins
+
+    def bins_no_p(freqs, coeffs, p, u, N):          # the factor p of the DFT dropped
+        return real_bins(freqs, coeffs, p, u, N) / p
+
+    def bins_conj_phase(freqs, coeffs, p, u, N):    # e^{-2 pi i w_n / N} on the shifted sets
+        return np.conj(real_bins(freqs, np.conj(coeffs), p, u, N))
+
+    def bins_wrong_bin(freqs, coeffs, p, u, N):     # off-by-one bin index
+        return np.roll(real_bins(freqs, coeffs, p, u, N), 1, axis=1)
+
+    for bad in (bins_no_p, bins_conj_phase, bins_wrong_bin):
+        with pytest.raises(AssertionError):
+            _check_registry_bins(bad)
