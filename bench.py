@@ -47,9 +47,11 @@ def _peaks():
 
 # ------------------------------------------------------------------ CPU oracle timing
 
-def oracle_throughput(workload: str, min_seconds: float, max_recoveries: int, seed_base: int):
+def oracle_throughput(workload: str, min_seconds: float, max_recoveries: int, seed_base: int,
+                      residual: str = "bins"):
     """Runs the FP64 oracle on successive signals of the workload until min_seconds of CPU
-    work (or max_recoveries).  Returns (modes/s, recoveries, seconds, exact)."""
+    work (or max_recoveries), with the registry removed in the same form as the GPU arm.
+    Returns (modes/s, recoveries, seconds, exact)."""
     import oracle.sfft_oracle as O
     wl = WORKLOADS[workload]
     th = O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
@@ -57,7 +59,7 @@ def oracle_throughput(workload: str, min_seconds: float, max_recoveries: int, se
     while n < max_recoveries and (t_total < min_seconds or n == 0):
         sig = wl.signal(seed_offset=seed_base + n)
         t0 = time.perf_counter()
-        res = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, wl.blocks, th=th)
+        res = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, wl.blocks, th=th, residual=residual)
         t_total += time.perf_counter() - t0
         planted = sig.freqs[np.lexsort(sig.freqs.T[::-1])].astype(np.int64)
         exact = exact and res.converged and np.array_equal(res.freqs, planted)
@@ -155,12 +157,12 @@ def run_reference(args):
         return 0
     wl = WORKLOADS[args.workload]
     for w in range(args.warmup):
-        oracle_throughput(args.workload, 0.0, 1, seed_base=10_000 + w)
+        oracle_throughput(args.workload, 0.0, 1, seed_base=10_000 + w, residual=args.residual)
     t = 0.0
     modes = 0
     exact = True
     for s in range(args.steps):
-        v, n, secs, ok = oracle_throughput(args.workload, 0.0, 1, seed_base=s)
+        v, n, secs, ok = oracle_throughput(args.workload, 0.0, 1, seed_base=s, residual=args.residual)
         t += secs
         modes += n * wl.k
         exact = exact and ok
@@ -171,7 +173,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded planted sparse signals)",
         "config": {"workload": args.workload, "d": wl.d, "N": wl.N, "k": wl.k, "blocks": list(wl.blocks),
-                   "signals_per_step": 1, "form": "FP64 CPU oracle, one recovery per step"},
+                   "signals_per_step": 1, "form": "FP64 CPU oracle, one recovery per step",
+                   "residual": args.residual},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} full recoveries, one per step, single thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -218,7 +221,8 @@ def run_ours(args):
     dev = [sfft.Signal(s.freqs, s.coeffs, s.N) for s in sigs]
     planted = [s.freqs[np.lexsort(s.freqs.T[::-1])].astype(np.int64) for s in sigs]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    plan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, precision=args.precision, graph=True, stream=stream)
+    plan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, precision=args.precision, graph=True, stream=stream,
+                     residual=args.residual)
     batch = sfft.Batch([plan] * nb, graph=True, stream=stream)
     bout = batch.outputs()
     allow = (0, 2, 3, 5)
@@ -287,7 +291,8 @@ def run_ours(args):
 
     # profiled pass (same batch, rounds enqueued from the host with CUDA events around each
     # kernel class on the launch stream): kernel shares and the sampling kernel's roofline
-    pplan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, precision=args.precision, profile=True, stream=stream)
+    pplan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, precision=args.precision, profile=True, stream=stream,
+                      residual=args.residual)
     pbatch = sfft.Batch([pplan] * nb, graph=False, stream=stream)
     pout = pbatch.outputs()
     pbatch.execute(dev, out=pout, allow=allow)
@@ -347,6 +352,8 @@ def run_ours(args):
                             if args.form == "batched" else "plain: one signal per execute, CUDA-graph round loop"),
                    "precision": "FP32 sampling, DFT and phase ratio (N <= 2^14)" if args.precision == "fp32"
                    else args.precision,
+                   "residual": ("registry removed bin by bin after the DFT" if args.residual == "bins"
+                                else "registry sampled with the black box (f - g)"),
                    "l2": "flushed between timed steps (256 MiB write)", "exact_recovery": bool(ok_all)},
         "other_form": {"form": "plain" if args.form == "batched" else "batched", "value": other_value,
                        "unit": UNIT, "steps": args.other_steps,
@@ -380,7 +387,7 @@ def run_ours(args):
 def cpu_baseline(args):
     """The oracle, single-threaded, in a child process on a bounded sample of the workload."""
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-only", "--workload", args.workload,
-           "--cpu-seconds", str(args.cpu_seconds)]
+           "--cpu-seconds", str(args.cpu_seconds), "--residual", args.residual]
     try:
         r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
         return json.loads(r.stdout.strip().splitlines()[-1])
@@ -404,11 +411,15 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-baseline-only", action="store_true")
+    ap.add_argument("--residual", default="bins", choices=["bins", "samples"],
+                    help="registry removed from the transform bin by bin, or sampled with the black box")
     args = ap.parse_args(argv)
     if args.cpu_baseline_only:
-        v, n, secs, exact = oracle_throughput(args.workload, args.cpu_seconds, 1000, seed_base=0)
+        v, n, secs, exact = oracle_throughput(args.workload, args.cpu_seconds, 1000, seed_base=0,
+                                              residual=args.residual)
         print(json.dumps({"value": v if exact else 0.0, "unit": UNIT, "cores": 1, "kind": "oracle",
-                          "sample": f"{n} full recoveries of the workload ({secs:.1f} s, single thread)"}))
+                          "sample": f"{n} full recoveries of the workload ({secs:.1f} s, single thread, "
+                                    f"residual {args.residual})"}))
         return 0
     if args.impl == "reference":
         return run_reference(args)

@@ -94,7 +94,17 @@ typedef struct {
   int coef_set0;     /* 1: coefficient a = Y_0[h] / p as printed in Eq. 41; 0 (default): the mean
                         over the d + 1 sets of Y_n[h] e^{-2 pi i w_n / N} / p, equal to it for a
                         single-mode bin and less affected by rounding */
+  int residual;      /* sfft_residual: where g, built from the registry, leaves f each round */
 } sfft_opts;
+
+/* Alg. 2 removes g (the function of the registry's modes) from f before each round's
+ * test (Sec. 5, "Algorithm").  SAMPLES evaluates f - g at every sample point, as the
+ * algorithm writes it: the sampling kernel sums k + |R| modes.  BINS (default) samples
+ * f alone and, by the linearity of the DFT, subtracts g's transform bin by bin: mode
+ * (w, a) of the registry removes p a e^{2 pi i w_n / N} from bin (w . u) mod p of set n,
+ * O(|R| (d + 1)) work instead of O(p |R| (d + 1)).  Both give the same sets; the
+ * coefficients agree to the policy's rounding. */
+typedef enum { SFFT_RESIDUAL_BINS = 0, SFFT_RESIDUAL_SAMPLES = 1 } sfft_residual;
 
 #define SFFT_STATS_MAX_ROUNDS 256
 /* kernel classes of sfft_stats.kernel_ms / kernel_launches: round setup and
@@ -105,9 +115,9 @@ typedef struct {
   int rounds;                     /* rounds run, including the final empty one  */
   int converged;                  /* 1 when the last round found no occupied bin */
   int64_t samples;                /* black-box samples, sum over rounds of (d+1) p */
-  int64_t terms;                  /* sample terms, sum over rounds of (d+1) p K */
+  int64_t terms;                  /* sample terms, sum over rounds of (d+1) p K  */
   int64_t p[SFFT_STATS_MAX_ROUNDS];
-  int32_t K[SFFT_STATS_MAX_ROUNDS];        /* modes evaluated per sample (k + |R|) */
+  int32_t K[SFFT_STATS_MAX_ROUNDS];        /* modes summed per sample: k, or k + |R| under SAMPLES */
   int32_t accepted[SFFT_STATS_MAX_ROUNDS]; /* bins accepted in the round */
   int32_t registry[SFFT_STATS_MAX_ROUNDS]; /* live registry entries after the round */
   int64_t kernel_launches[SFFT_NKCLASS];   /* kernels launched, per class */

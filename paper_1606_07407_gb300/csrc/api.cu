@@ -109,6 +109,7 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
   if (!fp64 && N > (1LL << 23)) return SFFT_ERR_PRECISION;
   if (o.tau < 0 || o.rho < 0 || o.delta < 0 || o.delta >= 0.5 || o.noise_sigma < 0 || o.max_rounds < 0)
     return SFFT_ERR_INVALID_ARG;
+  if (o.residual != SFFT_RESIDUAL_BINS && o.residual != SFFT_RESIDUAL_SAMPLES) return SFFT_ERR_INVALID_ARG;
   if (o.noise_sigma != 0.0) return SFFT_ERR_INVALID_ARG;   // noisy black boxes: not yet supported
 
   std::unique_ptr<sfft_plan_s> P(new sfft_plan_s());
@@ -124,6 +125,7 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
                   ? 1
                   : 0;
   D.coef_mean = o.coef_set0 ? 0 : 1;
+  D.peel_bins = o.residual == SFFT_RESIDUAL_BINS ? 1 : 0;
   D.tau = o.tau > 0 ? o.tau : (fp64 ? 1e-7 : 1e-3);
   D.rho = o.rho > 0 ? o.rho : (fp64 ? std::ldexp(1.0, -40) : std::ldexp(1.0, -17));
   D.delta = o.delta > 0 ? o.delta : (fp64 ? 0.1 : 0.25);

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
             ubuf[c.u_off + l] = v < 0 ? v + p : v;
           }
         }
-        const int K = a.force ? a.force_K : r.k_sig + min(r.K_reg, c.reg_cap);
+        const int K = a.force ? a.force_K : sampled_modes(c, r);
         r.logL = max(ceil_log2(2 * p - 1), 5);   // at least 32 points: one radix-32 pass
         r.big = r.logL > a.single_max_logL;
         r.groups = (c.n_sets + kMaxSetGroup - 1) / kMaxSetGroup;
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
       r = run[s];
       if (r.active) {
         const SigCfg& c = cfg[s];
-        const int K = a.force ? a.force_K : r.k_sig + min(r.K_reg, c.reg_cap);
+        const int K = a.force ? a.force_K : sampled_modes(c, r);
         int sp = min(S, r.chunks);
         r.jper = ((r.chunks + sp - 1) / sp) * kSampleChunk;
         r.splits = K > 0 ? (K + r.jper - 1) / r.jper : 1;
@@ -331,14 +331,7 @@ __global__ void k_tables(int n, const SigCfg* __restrict__ cfg, const SigRun* __
       a.y = -a.y;
       twr = regtw + c.regtw_off + (int64_t)jr * d;
     }
-    // (w . u) = sum (w_l - box_lo) u_l + box_lo sum u_l, all reduced mod p
-    uint64_t acc = 0, usum = 0;
-    for (int l = 0; l < d; ++l) {
-      acc = mod_barrett((uint64_t)(int64_t)(w[l] - c.box_lo) * (uint64_t)u[l] + acc, up, mm);
-      usum += (uint64_t)u[l];
-    }
-    const int64_t blm = ((int64_t)c.box_lo % r.p + r.p) % r.p;
-    acc = mod_barrett(acc + mod_barrett((uint64_t)blm * mod_barrett(usum, up, mm), up, mm), up, mm);
+    const uint64_t acc = project_mod(w, d, u, c.box_lo, r.p, mm);
     alpha[c.mode_off + j] = (int32_t)acc;
     gam[c.mode_off + j] = (int32_t)mod_barrett(acc * 32u, up, mm);
     const c2<T> a0 = mk2((T)a.x, (T)a.y);
@@ -647,6 +640,43 @@ __global__ void k_bigC(int n, const SigCfg* __restrict__ cfg, SigRun* run, const
       if (row == 0) max_abs_to<T>(&run[s].maxy0_bits, sqrt(m));
     }
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ registry removed in the bin domain
+
+// Residual BINS: each live registry mode (w, a) of an active signal takes p a e^{2 pi i w_n / N}
+// off bin (w . u) mod p of set n (p a off set 0).  That is the transform of the mode's samples
+// (sum over x of W^{(alpha - h) x} is p at h = alpha and 0 elsewhere), so f's transform minus
+// these is the transform of f - g (Alg. 2, by linearity).  Products in double, one rounding to T;
+// modes sharing a bin add in any order.
+template <typename T>
+__global__ void k_peel(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run,
+                       const int64_t* __restrict__ ubuf, const int32_t* __restrict__ regw,
+                       const double2* __restrict__ rega, const c2<T>* __restrict__ regtw, c2<T>* __restrict__ Ybuf) {
+  const int s = blockIdx.y;
+  if (s >= n) return;
+  const SigCfg& c = cfg[s];
+  const SigRun& r = run[s];
+  if (!r.active || !c.peel_bins) return;
+  const int nr = min(r.K_reg, c.reg_cap);
+  const int64_t p = r.p;
+  const int64_t* u = ubuf + c.u_off;
+  T* Y = reinterpret_cast<T*>(Ybuf + c.Y_off);
+  for (int jr = blockIdx.x * blockDim.x + threadIdx.x; jr < nr; jr += gridDim.x * blockDim.x) {
+    const double2 a = rega[c.rega_off + jr];
+    if (a.x == 0.0 && a.y == 0.0) continue;   // pruned
+    const int64_t h = (int64_t)project_mod(regw + c.regw_off + (int64_t)jr * c.d, c.d, u, c.box_lo, p, r.mod_m);
+    const double px = (double)p * a.x, py = (double)p * a.y;
+    atomicAdd(Y + 2 * h, (T)-px);
+    atomicAdd(Y + 2 * h + 1, (T)-py);
+    const c2<T>* tw = regtw + c.regtw_off + (int64_t)jr * c.d;
+    for (int nn = 1; nn < c.n_sets; ++nn) {
+      const c2<T> t = tw[nn - 1];   // e^{2 pi i w_n / N}
+      T* yn = Y + 2 * ((int64_t)nn * p + h);
+      atomicAdd(yn, (T)-(px * (double)t.x - py * (double)t.y));
+      atomicAdd(yn + 1, (T)-(px * (double)t.y + py * (double)t.x));
+    }
   }
 }
 
@@ -1005,6 +1035,7 @@ class Engine final : public EngineBase {
       c.box_lo = d.box_lo;
       c.ratio64 = d.ratio64;
       c.coef_mean = d.coef_mean;
+      c.peel_bins = d.peel_bins;
       c.N = d.N;
       c.p_max = d.p_max;
       c.tau = d.tau;
@@ -1044,7 +1075,11 @@ class Engine final : public EngineBase {
       }
       c.u_off = u;
       u += d.d;
-      c.Kmax = (int)(d.k + c.reg_cap);
+      c.Kmax = (int)(d.k + (c.peel_bins ? 0 : c.reg_cap));   // modes the round's tables hold
+      if (c.peel_bins) {
+        any_peel_ = true;
+        peel_gx_ = std::max(peel_gx_, (int)std::min<int64_t>((c.reg_cap + 255) / 256, 32));
+      }
       c.mode_off = modes;
       modes += c.Kmax;
       c.C_off = cm;
@@ -1243,6 +1278,12 @@ class Engine final : public EngineBase {
       launches[3] += 3;
     }
     ECHK(mark(4));
+    if (any_peel_) {
+      k_peel<T><<<dim3(peel_gx_, n_), 256, 0, st_>>>(n_, cfg_, run_, u_, regw_, rega_, (const C2*)regtw_, (C2*)Y_);
+      ECHK(cudaGetLastError());
+      launches[5] += 1;
+    }
+    ECHK(mark(6));
     ClassifyOut co{nullptr, nullptr, nullptr, 0, nullptr, nullptr, -1.0};
     k_classify<T><<<16 * n_sm_, 256, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)Y_, u_, regw_, rega_, (C2*)regtw_,
                                               hash_, co);
@@ -1423,7 +1464,9 @@ class Engine final : public EngineBase {
           stats->kernel_ms[2] += ms;
           ECHK(cudaEventElapsedTime(&ms, events_[b + 3], events_[b + 4]));
           stats->kernel_ms[3] += ms;
-          ECHK(cudaEventElapsedTime(&ms, events_[b + 4], events_[b + 5]));
+          ECHK(cudaEventElapsedTime(&ms, events_[b + 4], events_[b + 6]));
+          stats->kernel_ms[5] += ms;
+          ECHK(cudaEventElapsedTime(&ms, events_[b + 6], events_[b + 5]));
           stats->kernel_ms[4] += ms;
         }
       }
@@ -1524,6 +1567,8 @@ class Engine final : public EngineBase {
   int n_ = 0, dev_ = 0, n_sm_ = 148;
   cudaStream_t st_ = nullptr;
   bool profile_ = false, use_graph_ = false, any_big_ = false;
+  bool any_peel_ = false;   // some slot removes its registry in the bin domain
+  int peel_gx_ = 1;         // k_peel blocks per signal
   int logL_big_max_ = 0, small_logL_max_ = 1, small_threads_ = 256, n_ptab_ = 0;
   size_t smem_small_ = 0, smem_bigA_ = 0, smem_bigB_ = 0, bytes_ = 0, host_stage_bytes_ = 0;
   int64_t rows_max_ = 0;

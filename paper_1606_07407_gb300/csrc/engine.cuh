@@ -29,6 +29,7 @@ struct SigCfg {
   int d, n_sets, k, c, max_rounds, n_dirs, n_primes, box_lo;
   int ratio64;        // phase ratio and coefficient in double
   int coef_mean;      // coefficient = mean over the d + 1 sets (else Y_0[h] / p)
+  int peel_bins;      // the registry leaves the transform bin by bin (else it is sampled with f)
   int reg_cap, hash_mask, logL_max;
   int64_t N, p_max;
   double tau, rho, delta, sigma;
@@ -45,8 +46,7 @@ struct SigCfg {
   int64_t u_off;      // int64 [d]           direction of the round, reduced mod p
   int64_t mode_off;   // int32 [Kmax]        alpha_j = (w_j . u) mod p and 32 alpha_j mod p of the round
   int64_t C_off;      // T2 [n_sets * Kmax]  a_j e^{2 pi i w_{j,n} / N} of the round (registry: -a)
-  int Kmax;           // k + reg_cap
-  int pad2;
+  int Kmax;           // k, plus reg_cap when the registry is sampled
 };
 
 // Dynamic state of one signal, updated by the kernels of each round.
@@ -94,6 +94,13 @@ struct HistRec {
 };
 
 // Host-side description of one signal slot.
+// Modes the sampling kernel sums for a signal this round: the black box's, plus the
+// registry's when the residual is sampled rather than removed in the bin domain.
+__host__ __device__ inline int sampled_modes(const SigCfg& c, const SigRun& r) {
+  const int reg = r.K_reg < c.reg_cap ? r.K_reg : c.reg_cap;
+  return r.k_sig + (c.peel_bins ? 0 : reg);
+}
+
 struct SlotDesc {
   int d;
   int64_t N;
@@ -102,6 +109,7 @@ struct SlotDesc {
   int box_lo;
   int ratio64;
   int coef_mean;
+  int peel_bins;
   double tau, rho, delta, sigma;
   int max_rounds;
   std::vector<int64_t> dirs;     // n_dirs x d

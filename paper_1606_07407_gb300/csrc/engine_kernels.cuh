@@ -14,6 +14,20 @@ __device__ __forceinline__ uint64_t mod_barrett(uint64_t x, uint64_t p, uint64_t
   return r >= p ? r - p : r;
 }
 
+// (w . u) mod p for w in the box [box_lo, box_lo + N)^d and u reduced mod p, as
+// sum_l (w_l - box_lo) u_l + box_lo sum_l u_l with every step reduced (w_l - box_lo < 2^31, u_l < p).
+__device__ __forceinline__ uint64_t project_mod(const int32_t* w, int d, const int64_t* u, int box_lo, int64_t p,
+                                                uint64_t mm) {
+  const uint64_t up = (uint64_t)p;
+  uint64_t acc = 0, usum = 0;
+  for (int l = 0; l < d; ++l) {
+    acc = mod_barrett((uint64_t)(int64_t)(w[l] - box_lo) * (uint64_t)u[l] + acc, up, mm);
+    usum += (uint64_t)u[l];
+  }
+  const int64_t blm = ((int64_t)box_lo % p + p) % p;
+  return mod_barrett(acc + mod_barrett((uint64_t)blm * mod_barrett(usum, up, mm), up, mm), up, mm);
+}
+
 // a mod p for 0 <= a < 64 p < 2^31, via a float reciprocal and one correction.
 __device__ __forceinline__ int mod_small(unsigned a, int p, float inv_p) {
   int q = __float2int_rz(__uint2float_rn(a) * inv_p);

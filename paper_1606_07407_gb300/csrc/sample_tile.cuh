@@ -59,7 +59,7 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
   const float inv_p = 1.0f / (float)p;
   const int n0 = g * r.gsize;
   const int ns_valid = min(r.gsize, c.n_sets - n0);
-  const int K = r.k_sig + min(r.K_reg, c.reg_cap);
+  const int K = sampled_modes(c, r);
   const int x0 = xt * TX;
   const int j_begin = split * r.jper;
   const int j_end = min(K, j_begin + r.jper);

@@ -38,10 +38,15 @@ class _Tilts(C.Structure):
                 ("block_sizes", C.POINTER(C.c_int))]
 
 
+# where g (the registry's function) leaves f: its transform subtracted bin by bin, or its
+# samples subtracted at every sample point
+RESIDUAL = {"bins": 0, "samples": 1}
+
+
 class _Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("box_lo", C.c_int), ("tau", C.c_double), ("rho", C.c_double),
                 ("delta", C.c_double), ("noise_sigma", C.c_double), ("max_rounds", C.c_int),
-                ("profile", C.c_int), ("graph", C.c_int), ("coef_set0", C.c_int)]
+                ("profile", C.c_int), ("graph", C.c_int), ("coef_set0", C.c_int), ("residual", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -172,8 +177,10 @@ class Plan:
     def __init__(self, d: int, N: int, k: int, blocks=None, dirs=None, primes=None, c: int = 5,
                  precision: str = "fp32", box_lo: int = 0, tau: float = 0.0, rho: float = 0.0,
                  delta: float = 0.0, noise_sigma: float = 0.0, max_rounds: int = 0, stream=None,
-                 profile: bool = False, graph: bool = False, coef: str = "mean"):
+                 profile: bool = False, graph: bool = False, coef: str = "mean", residual: str = "bins"):
         L = load()
+        if residual not in RESIDUAL:
+            raise ValueError(f"residual must be one of {sorted(RESIDUAL)}")
         self.d, self.N, self.k = int(d), int(N), int(k)
         self.precision = precision
         self.cdtype = torch.complex128 if precision == "fp64" else torch.complex64
@@ -194,7 +201,8 @@ class Plan:
             self._keep.append(arr)
             tl.n_blocks, tl.block_sizes = len(blocks), arr
         op = _Opts(PREC[precision], int(box_lo), float(tau), float(rho), float(delta), float(noise_sigma),
-                   int(max_rounds), 1 if profile else 0, 1 if graph else 0, 1 if coef == "set0" else 0)
+                   int(max_rounds), 1 if profile else 0, 1 if graph else 0, 1 if coef == "set0" else 0,
+                   RESIDUAL[residual])
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

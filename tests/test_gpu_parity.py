@@ -188,13 +188,14 @@ def test_classify_random_round_matches_oracle(sfft):
 
 # ------------------------------------------------------------------ whole recovery
 
-def _run_both(sfft, sig, blocks=None, prec="fp32", dirs=None, primes=None, box_lo=0):
-    plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=blocks, dirs=dirs, primes=primes, precision=prec, box_lo=box_lo)
+def _run_both(sfft, sig, blocks=None, prec="fp32", dirs=None, primes=None, box_lo=0, residual="bins"):
+    plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=blocks, dirs=dirs, primes=primes, precision=prec, box_lo=box_lo,
+                     residual=residual)
     f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N))
     gf, ga = sfft.sort_result(_np(f), _np(a))
     th = O.Thresholds() if prec == "fp64" else O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
     ref = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, blocks, th=th, dirs=dirs,
-                             primes=primes, box_lo=box_lo, estimator="mean")
+                             primes=primes, box_lo=box_lo, estimator="mean", residual=residual)
     return gf, ga, status, stats, ref
 
 
@@ -215,10 +216,33 @@ def test_recovery_d2_workload(sfft, seed):
     _assert_parity(sig, *_run_both(sfft, sig, wl.blocks), FP32_COEFF_TOL)
 
 
-def test_recovery_d5_workload_full_size(sfft):
+@pytest.mark.parametrize("residual", ["bins", "samples"])
+def test_recovery_d5_workload_full_size(sfft, residual):
     wl = WORKLOADS["d5_N1024_k1000"]
     sig = wl.signal()
-    _assert_parity(sig, *_run_both(sfft, sig, wl.blocks), FP32_COEFF_TOL)
+    _assert_parity(sig, *_run_both(sfft, sig, wl.blocks, residual=residual), FP32_COEFF_TOL)
+
+
+def test_residual_forms_count_their_sample_terms(sfft):
+    # bins: every round sums the black box's k modes; samples: k plus every registry entry
+    # made so far (pruned ones included), so from round 2 on more than k + the live count
+    wl = WORKLOADS["d5_N1024_k1000"]
+    sig = wl.signal(seed_offset=3)
+    out = {}
+    for residual in ("bins", "samples"):
+        plan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, residual=residual)
+        f, a, status, st = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N))
+        assert status == 0
+        R = st["rounds"]
+        assert st["samples"] == sum((wl.d + 1) * p for p in st["p"][:R])
+        assert st["terms"] == sum((wl.d + 1) * p * K for p, K in zip(st["p"][:R], st["K"][:R]))
+        out[residual] = st
+    b, s_ = out["bins"], out["samples"]
+    assert b["p"] == s_["p"] and b["accepted"] == s_["accepted"]
+    assert all(K == wl.k for K in b["K"][:b["rounds"]])
+    assert s_["K"][0] == wl.k
+    assert all(K >= wl.k + live for K, live in zip(s_["K"][1:s_["rounds"]], s_["registry"]))
+    assert b["terms"] < s_["terms"]
 
 
 @pytest.mark.parametrize("case", ["d1", "d4_2x2", "d3_full_unwrap", "d6_tilted", "signed_box", "d12"])
@@ -242,10 +266,11 @@ def test_recovery_shapes(sfft, case):
     _assert_parity(sig, *_run_both(sfft, sig, blocks, dirs=dirs, box_lo=sig.box_lo), FP32_COEFF_TOL)
 
 
-def test_recovery_fp64_policy(sfft):
+@pytest.mark.parametrize("residual", ["bins", "samples"])
+def test_recovery_fp64_policy(sfft, residual):
     wl = WORKLOADS["d5_N1024_k1000"]
     sig = draw_signal(5, 1024, 300, seed=31, r_lo=1.0, r_hi=10.0)
-    _assert_parity(sig, *_run_both(sfft, sig, wl.blocks, prec="fp64"), FP64_COEFF_TOL)
+    _assert_parity(sig, *_run_both(sfft, sig, wl.blocks, prec="fp64", residual=residual), FP64_COEFF_TOL)
 
 
 def test_fig2_collision_story_on_gpu(sfft):
