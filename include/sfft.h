@@ -153,6 +153,17 @@ void sfft_signal_destroy(sfft_signal signal);
 sfft_status sfft_signal_assign(sfft_signal signal, int64_t k, const int32_t* freqs_dev,
                                const double* coeffs_dev);
 
+/* Refill n black boxes at once, each as sfft_signal_assign would, from one packed
+ * pair of device arrays: signal s takes ks[s] modes (ks: host), its frequency rows
+ * (d_s int32 each) following those of signals 0..s-1 in freqs_dev and its
+ * coefficients (complex128) following theirs in coeffs_dev.  The copies are
+ * enqueued on `stream` (a cudaStream_t, NULL for the legacy default stream) and
+ * nothing waits for them: work enqueued later on the same stream sees the new
+ * modes.  Allocates nothing.  INVALID_ARG, with nothing changed, if n < 0, a
+ * handle is NULL or some ks[s] is negative or above the handle's capacity. */
+sfft_status sfft_signal_assign_many(int n, const sfft_signal* signals, const int64_t* ks,
+                                    const int32_t* freqs_dev, const double* coeffs_dev, void* stream);
+
 /* Run Algorithm 2 on the signal until a round finds no occupied bin.
  * Writes the live registry (unordered) to freqs_out_dev (int32 [capacity x d])
  * and coeffs_out_dev (complex128 [capacity]); *n_found = number of entries.

@@ -47,6 +47,29 @@ __global__ void k_signal_copy(int64_t nw, const int32_t* w_src, int32_t* w_dst, 
     a_dst[e] = a_src[e];
 }
 
+// Copies for sfft_signal_assign_many, passed by value: block row y copies signal y's modes.
+constexpr int kAssignPerLaunch = 256;
+struct AssignDesc {
+  int32_t* w_dst;
+  double2* a_dst;
+  int64_t w_src, a_src;   // offsets into the packed arrays
+  int64_t nw, na;         // int32 frequency entries and coefficients to copy
+};
+struct AssignArgs {
+  AssignDesc d[kAssignPerLaunch];
+};
+
+__global__ void k_signal_copy_many(AssignArgs args, int count, const int32_t* __restrict__ w_src,
+                                   const double2* __restrict__ a_src) {
+  const int y = blockIdx.y;
+  if (y >= count) return;
+  const AssignDesc& c = args.d[y];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < c.nw; e += (int64_t)gridDim.x * blockDim.x)
+    c.w_dst[e] = w_src[c.w_src + e];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < c.na; e += (int64_t)gridDim.x * blockDim.x)
+    c.a_dst[e] = a_src[c.a_src + e];
+}
+
 }  // namespace
 
 void sfft::sfft_record_cuda_error(int e) { g_last_cuda_error = e; }
@@ -280,6 +303,39 @@ sfft_status sfft_signal_assign(sfft_signal S, int64_t k, const int32_t* freqs_de
     if (e != cudaSuccess) return cuda_status(e);
   }
   S->k = k;
+  return SFFT_OK;
+}
+
+sfft_status sfft_signal_assign_many(int n, const sfft_signal* signals, const int64_t* ks, const int32_t* freqs_dev,
+                                    const double* coeffs_dev, void* stream) {
+  if (n < 0 || (n > 0 && (!signals || !ks))) return SFFT_ERR_INVALID_ARG;
+  int64_t tot_w = 0, tot_a = 0, max_w = 0;
+  for (int s = 0; s < n; ++s) {
+    const sfft_signal_s* S = signals[s];
+    if (!S || ks[s] < 0 || ks[s] > S->k_cap) return SFFT_ERR_INVALID_ARG;
+    tot_w += ks[s] * S->d;
+    tot_a += ks[s];
+    max_w = std::max(max_w, ks[s] * S->d);
+  }
+  if (tot_a > 0 && (!freqs_dev || !coeffs_dev)) return SFFT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int gx = (int)std::min<int64_t>(std::max<int64_t>((max_w + 255) / 256, 1), 16);
+  int64_t w_off = 0, a_off = 0;
+  for (int s0 = 0; s0 < n; s0 += kAssignPerLaunch) {
+    const int cnt = std::min(kAssignPerLaunch, n - s0);
+    AssignArgs args;
+    std::memset(&args, 0, sizeof(args));
+    for (int i = 0; i < cnt; ++i) {
+      sfft_signal_s* S = signals[s0 + i];
+      args.d[i] = AssignDesc{S->w, S->a, w_off, a_off, ks[s0 + i] * S->d, ks[s0 + i]};
+      w_off += ks[s0 + i] * S->d;
+      a_off += ks[s0 + i];
+    }
+    k_signal_copy_many<<<dim3(gx, cnt), 256, 0, st>>>(args, cnt, freqs_dev, (const double2*)coeffs_dev);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  for (int s = 0; s < n; ++s) signals[s]->k = ks[s];
   return SFFT_OK;
 }
 

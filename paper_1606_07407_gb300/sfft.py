@@ -57,7 +57,7 @@ class _Stats(C.Structure):
 
 
 EXPORTS = ["sfft_plan_create", "sfft_plan_destroy", "sfft_signal_synthetic", "sfft_signal_destroy",
-           "sfft_signal_assign",
+           "sfft_signal_assign", "sfft_signal_assign_many",
            "sfft_execute", "sfft_batch_create", "sfft_batch_destroy", "sfft_batch_device_bytes",
            "sfft_batch_execute", "sfft_sample", "sfft_sample_noalloc", "sfft_dft", "sfft_classify",
            "sfft_plan_max_prime",
@@ -91,6 +91,8 @@ def load(path: str | None = None) -> C.CDLL:
     L.sfft_signal_destroy.restype = None
     L.sfft_signal_assign.argtypes = [vp, i64, vp, vp]
     L.sfft_signal_assign.restype = C.c_int
+    L.sfft_signal_assign_many.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(i64), vp, vp, vp]
+    L.sfft_signal_assign_many.restype = C.c_int
     L.sfft_execute.argtypes = [vp, vp, i64, vp, vp, C.POINTER(i64), C.POINTER(_Stats)]
     L.sfft_execute.restype = C.c_int
     L.sfft_batch_create.argtypes = [C.c_int, C.POINTER(vp), vp, C.c_int, C.POINTER(vp)]
@@ -169,6 +171,21 @@ class Signal:
         if h is not None and h.value and _lib is not None:
             _lib.sfft_signal_destroy(h)
             self._h = None
+
+
+def assign_many(signals, freqs: torch.Tensor, coeffs: torch.Tensor, ks, stream=None):
+    """Refills the handles from packed device tensors: signal s takes ks[s] modes, its rows of
+    freqs (int32 [sum ks, d]) and entries of coeffs (complex128 [sum ks]) following those of the
+    signals before it.  Enqueued on the stream (default: torch's current one), not waited for."""
+    n = len(signals)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    karr = (C.c_int64 * n)(*[int(k) for k in ks])
+    harr = (C.c_void_p * n)(*[s._h.value for s in signals])
+    _check(load().sfft_signal_assign_many(n, harr, karr, _ptr(freqs), _ptr(coeffs), C.c_void_p(stream.cuda_stream)),
+           "sfft_signal_assign_many")
+    for s, k in zip(signals, ks):
+        s.k = int(k)
 
 
 class Plan:

@@ -53,6 +53,15 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.sfft_plan_create(2, ctypes.c_int64(1), ctypes.c_int64(4), None, None, None, None,
                                 ctypes.byref(h)) == 1
     assert lib.sfft_execute(None, None, ctypes.c_int64(0), None, None, None, None) == 1
+    assert lib.sfft_signal_assign_many(-1, None, None, None, None, None) == 1
+    handles = (ctypes.c_void_p * 2)(None, None)
+    ks = (ctypes.c_int64 * 2)(3, 4)
+    assert lib.sfft_signal_assign_many(2, handles, ks, None, None, None) == 1
+    assert lib.sfft_signal_assign_many(0, None, None, None, None, None) == 0   # nothing to do
+    from paper_1606_07407_gb300.sfft import _Opts
+    bad = _Opts(0, 0, 0.0, 0.0, 0.0, 0.0, 0, 0, 0, 0, 7)                          # unknown residual form
+    assert lib.sfft_plan_create(2, ctypes.c_int64(16), ctypes.c_int64(4), None, None, ctypes.byref(bad), None,
+                                ctypes.byref(h)) == 1
 
 
 def test_library_is_built_for_sm103a():

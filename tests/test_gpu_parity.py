@@ -410,3 +410,26 @@ def test_paper_estimator_option(sfft):
     ref = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, wl.blocks,
                              th=O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25), estimator="set0")
     _assert_parity(sig, gf, ga, status, stats, ref, FP32_COEFF_TOL)
+
+
+def test_assign_many_refills_like_fresh_handles(sfft):
+    # mixed d in one packed buffer; one handle refilled with fewer modes than it holds, one emptied
+    sigs = _mixed_signals(6, 46)
+    handles = [sfft.Signal(np.zeros((s.k, s.d), np.int32), np.zeros(s.k, np.complex128), s.N) for s, _ in sigs]
+    ks = [s.k for s, _ in sigs]
+    ks[2] -= 3
+    ks[4] = 0
+    fw = torch.tensor(np.concatenate([s.freqs[:k].reshape(-1) for (s, _), k in zip(sigs, ks)]).astype(np.int32),
+                      device="cuda")
+    ca = torch.tensor(np.concatenate([s.coeffs[:k] for (s, _), k in zip(sigs, ks)]), dtype=torch.complex128,
+                      device="cuda")
+    sfft.assign_many(handles, fw, ca, ks)
+    for (sig, blocks), h, k in zip(sigs, handles, ks):
+        plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=blocks)
+        f, a, status, _ = plan.execute(h)
+        f1, a1, status1, _ = plan.execute(sfft.Signal(sig.freqs[:k], sig.coeffs[:k], sig.N))
+        assert h.k == k and status == 0 and status1 == 0
+        g, g1 = sfft.sort_result(_np(f), _np(a)), sfft.sort_result(_np(f1), _np(a1))
+        assert g[0].shape[0] == k and np.array_equal(g[0], g1[0])
+        if k:
+            assert np.max(np.abs(g[1] - g1[1]) / np.abs(g1[1])) < FP32_COEFF_TOL
