@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     c.n_rows_s = carry[SC_ROWS_S];
     c.n_filt_s = carry[SC_FILT_S];
     c.ctr_rows = c.ctr_filt = 0ull;
+    c.n_cand = 0ull;
     *ctl = c;
     if (a.use_cond) cudaGraphSetConditional(a.cond, tot_active > 0 ? 1u : 0u);
   }
@@ -723,88 +724,145 @@ struct ClassifyOut {   // step calls: accepted bins are appended here instead of
   double eta_override;
 };
 
+// Eq. 42 ratio test and Eq. 7 read-out of sets 1..d of an occupied bin.  The sets' values are
+// fetched eight at a time so that their loads overlap.  Writes w_n to w_out (if not null) and
+// returns whether every set passes and (w . u) mod p is the bin itself.
 template <typename T, typename R>
 __device__ bool decode_bin(const SigCfg& c, const SigRun& r, const c2<T>* Y, const int64_t* u, int64_t h, R y0x,
-                           R y0y, R m0) {
+                           R y0y, R m0, int32_t* w_out) {
+  constexpr int kB = 8;
   const int64_t p = r.p;
   const uint64_t up = (uint64_t)p;
   uint64_t bin = 0;
   uint64_t usum = 0;
-  for (int n = 1; n <= c.d; ++n) {
-    const c2<T> yn = Y[(int64_t)n * p + h];
-    const R ynx = (R)yn.x, yny = (R)yn.y;
-    const R mn = sqrt(ynx * ynx + yny * yny);
-    if (!(fabs(mn / m0 - (R)1) < (R)c.tau)) return false;   // Eq. 42
-    int64_t wn;
-    if (!read_coord<R>(ynx, yny, y0x, y0y, c.N, c.box_lo, (R)c.delta, &wn)) return false;
-    bin = mod_barrett((uint64_t)(wn - c.box_lo) * (uint64_t)u[n - 1] + bin, up, r.mod_m);
-    usum += (uint64_t)u[n - 1];
+  for (int n0 = 1; n0 <= c.d; n0 += kB) {
+    c2<T> yv[kB];
+#pragma unroll
+    for (int i = 0; i < kB; ++i) yv[i] = n0 + i <= c.d ? Y[(int64_t)(n0 + i) * p + h] : mk2((T)0, (T)0);
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+      const int n = n0 + i;
+      if (n > c.d) break;
+      const R ynx = (R)yv[i].x, yny = (R)yv[i].y;
+      const R mn = sqrt(ynx * ynx + yny * yny);
+      if (!(fabs(mn / m0 - (R)1) < (R)c.tau)) return false;   // Eq. 42
+      int64_t wn;
+      if (!read_coord<R>(ynx, yny, y0x, y0y, c.N, c.box_lo, (R)c.delta, &wn)) return false;
+      if (w_out) w_out[n - 1] = (int32_t)wn;
+      bin = mod_barrett((uint64_t)(wn - c.box_lo) * (uint64_t)u[n - 1] + bin, up, r.mod_m);
+      usum += (uint64_t)u[n - 1];
+    }
   }
   const int64_t blm = ((int64_t)c.box_lo % p + p) % p;
   bin = mod_barrett(bin + mod_barrett((uint64_t)blm * mod_barrett(usum, up, r.mod_m), up, r.mod_m), up, r.mod_m);
   return (int64_t)bin == h;
 }
 
-// Writes the read-out vector of an accepted bin and returns its coefficient estimate
-// (Eq. 41).  With coef_mean the estimate is the mean over the d + 1 sets of
-// Y_n[h] e^{-2 pi i w_n / N} / p: for a bin holding one mode every term equals a
-// exactly, and the mean averages the sets' independent rounding (and the leakage
-// of other modes' residuals, whose phases differ across the sets).
+// The read-out vector of an accepted bin, computed again (for vectors longer than the
+// decoder's register copy).
 template <typename T, typename R>
-__device__ double2 read_out(const SigCfg& c, const SigRun& r, const c2<T>* Y, int64_t h, R y0x, R y0y,
+__device__ void read_coords(const SigCfg& c, const SigRun& r, const c2<T>* Y, int64_t h, R y0x, R y0y,
                             int32_t* w_out) {
-  R ax = y0x, ay = y0y;
   for (int n = 1; n <= c.d; ++n) {
     const c2<T> yn = Y[(int64_t)n * r.p + h];
     int64_t wn = 0;
     read_coord<R>((R)yn.x, (R)yn.y, y0x, y0y, c.N, c.box_lo, (R)c.delta, &wn);
     w_out[n - 1] = (int32_t)wn;
-    if (c.coef_mean) {
-      int64_t m = wn % c.N;
-      if (m < 0) m += c.N;
-      const c2<R> t = unit_root<R>(m, c.N);   // e^{2 pi i w_n / N}
-      ax += (R)yn.x * t.x + (R)yn.y * t.y;     // Y_n conj(t)
-      ay += (R)yn.y * t.x - (R)yn.x * t.y;
+  }
+}
+
+// Coefficient estimate of an accepted bin with read-out vector w (Eq. 41).  With coef_mean
+// the estimate is the mean over the d + 1 sets of Y_n[h] e^{-2 pi i w_n / N} / p: for a bin
+// holding one mode every term equals a exactly, and the mean averages the sets' independent
+// rounding (and the leakage of other modes' residuals, whose phases differ across the sets).
+template <typename T, typename R>
+__device__ double2 coefficient(const SigCfg& c, const SigRun& r, const c2<T>* Y, int64_t h, R y0x, R y0y,
+                               const int32_t* w) {
+  if (!c.coef_mean) {
+    const double scale = 1.0 / (double)r.p;
+    return make_double2((double)y0x * scale, (double)y0y * scale);
+  }
+  R ax = y0x, ay = y0y;
+  for (int n = 1; n <= c.d; ++n) {
+    const c2<T> yn = Y[(int64_t)n * r.p + h];
+    int64_t m = (int64_t)w[n - 1] % c.N;
+    if (m < 0) m += c.N;
+    const c2<R> t = unit_root<R>(m, c.N);   // e^{2 pi i w_n / N}
+    ax += (R)yn.x * t.x + (R)yn.y * t.y;     // Y_n conj(t)
+    ay += (R)yn.y * t.x - (R)yn.x * t.y;
+  }
+  const double scale = 1.0 / ((double)r.p * (double)c.n_sets);
+  return make_double2((double)ax * scale, (double)ay * scale);
+}
+
+// Bins of the round whose set-0 magnitude is above the empty-bin level, appended to the
+// candidate list (warp-aggregated); also the first round's reference amplitude A_ref and the
+// flag that some bin is occupied (the stop rule reads it).
+template <typename T>
+__global__ void k_occupied(int n, const SigCfg* __restrict__ cfg, SigRun* run, RoundCtl* ctl, Scans sc,
+                           const c2<T>* __restrict__ Ybuf, int2* __restrict__ cand, double eta_override) {
+  const int64_t total = ctl->n_bins;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = base + threadIdx.x;
+    bool occ = false;
+    int s = 0;
+    int64_t h = 0;
+    if (e < total) {
+      s = find_slot(sc.v[SC_BINS], n, e);
+      h = e - sc.v[SC_BINS][s];
+      const SigCfg& c = cfg[s];
+      SigRun* rp = run + s;
+      const int64_t p = rp->p;
+      double a_ref;
+      if (rp->round == 1) {
+        a_ref = __longlong_as_double((long long)rp->maxy0_bits) / (double)p;
+        if (h == 0) rp->a_ref = a_ref;
+      } else {
+        a_ref = rp->a_ref;
+      }
+      const double eta = eta_override >= 0.0 ? eta_override
+                                             : fmax(c.rho * (double)p * a_ref, 6.0 * c.sigma * sqrt((double)p));
+      const c2<T> y0 = Ybuf[c.Y_off + h];
+      const double m0d = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y);
+      occ = m0d > eta;
+      if (occ && !rp->any_occupied) rp->any_occupied = 1;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, occ);
+    if (mask) {
+      const int leader = __ffs(mask) - 1;
+      unsigned long long b0 = 0;
+      if (lane == leader) b0 = atomicAdd(&ctl->n_cand, (unsigned long long)__popc(mask));
+      b0 = __shfl_sync(0xffffffffu, b0, leader);
+      if (occ) cand[b0 + __popc(mask & ((1u << lane) - 1u))] = make_int2(s, (int)h);
     }
   }
-  const double scale = c.coef_mean ? 1.0 / ((double)r.p * (double)c.n_sets) : 1.0 / (double)r.p;
-  if (!c.coef_mean) {
-    ax = y0x;
-    ay = y0y;
-  }
-  return make_double2((double)ax * scale, (double)ay * scale);
 }
 
 template <typename T>
 __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, const RoundCtl* __restrict__ ctl,
-                           Scans sc, const c2<T>* __restrict__ Ybuf, const int64_t* __restrict__ ubuf,
-                           int32_t* regw, double2* rega, c2<T>* regtw, int32_t* hash, ClassifyOut co) {
-  const int64_t total = ctl->n_bins;
+                           const int2* __restrict__ cand, const c2<T>* __restrict__ Ybuf,
+                           const int64_t* __restrict__ ubuf, int32_t* regw, double2* rega, c2<T>* regtw,
+                           int32_t* hash, ClassifyOut co) {
+  const int64_t total = (int64_t)ctl->n_cand;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int s = find_slot(sc.v[SC_BINS], n, e);
-    const int64_t h = e - sc.v[SC_BINS][s];
+    const int2 sh = cand[e];
+    const int s = sh.x;
+    const int64_t h = sh.y;
     const SigCfg& c = cfg[s];
     SigRun* rp = run + s;
     const SigRun& r = *rp;
     const int64_t p = r.p;
-    double a_ref;
-    if (r.round == 1) {
-      a_ref = __longlong_as_double((long long)r.maxy0_bits) / (double)p;
-      if (h == 0) rp->a_ref = a_ref;
-    } else {
-      a_ref = r.a_ref;
-    }
-    const double eta = co.eta_override >= 0.0 ? co.eta_override
-                                              : fmax(c.rho * (double)p * a_ref, 6.0 * c.sigma * sqrt((double)p));
     const c2<T>* Y = Ybuf + c.Y_off;
     const c2<T> y0 = Y[h];
     const double m0d = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y);
-    if (!(m0d > eta)) continue;
-    if (!r.any_occupied) rp->any_occupied = 1;
     const int64_t* u = ubuf + c.u_off;
+    const int dd = c.d;
+    int32_t wk[64];
+    int32_t* wreg = dd <= 64 ? wk : nullptr;   // decoded vector kept for the read-out
     bool ok;
-    if (c.ratio64) ok = decode_bin<T, double>(c, r, Y, u, h, (double)y0.x, (double)y0.y, m0d);
-    else ok = decode_bin<T, T>(c, r, Y, u, h, (T)y0.x, (T)y0.y, (T)m0d);
+    if (c.ratio64) ok = decode_bin<T, double>(c, r, Y, u, h, (double)y0.x, (double)y0.y, m0d, wreg);
+    else ok = decode_bin<T, T>(c, r, Y, u, h, (T)y0.x, (T)y0.y, (T)m0d, wreg);
     if (!ok) continue;
     atomicAdd(&rp->n_acc, 1);
     if (co.count != nullptr) {
@@ -814,20 +872,26 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
         continue;
       }
       co.h[idx] = (int32_t)h;
-      if (c.ratio64) co.a[idx] = read_out<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, co.w + (int64_t)idx * c.d);
-      else co.a[idx] = read_out<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, co.w + (int64_t)idx * c.d);
+      int32_t* wo = co.w + (int64_t)idx * dd;
+      if (wreg) {
+        for (int l = 0; l < dd; ++l) wo[l] = wk[l];
+      } else if (c.ratio64) {
+        read_coords<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wo);
+      } else {
+        read_coords<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wo);
+      }
+      if (c.ratio64) co.a[idx] = coefficient<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wo);
+      else co.a[idx] = coefficient<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wo);
       continue;
     }
     // ---- merge into the registry: keys accepted in one round are distinct (each lands in its
     // own bin) and the table never deletes, so a key is present iff met before the first
     // empty slot of its probe sequence; one writer per key per round.
-    int32_t wk[64];
-    const int dd = c.d;
     int32_t* rw = regw + c.regw_off;
     double2* ra = rega + c.rega_off;
     c2<T>* rt = regtw + c.regtw_off;
     int32_t* hs = hash + c.hash_off;
-    const double eta_prune = fmax(c.rho * a_ref, 6.0 * c.sigma / sqrt((double)p));
+    const double eta_prune = fmax(c.rho * r.a_ref, 6.0 * c.sigma / sqrt((double)p));
     // decoded vector: up to 64 coordinates in registers, else read back from the registry slot
     int32_t* wv = wk;
     int scratch_idx = -1;
@@ -839,9 +903,13 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
       }
       wv = rw + (int64_t)scratch_idx * dd;
     }
+    if (!wreg) {
+      if (c.ratio64) read_coords<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wv);
+      else read_coords<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wv);
+    }
     double2 a;
-    if (c.ratio64) a = read_out<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wv);
-    else a = read_out<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wv);
+    if (c.ratio64) a = coefficient<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wv);
+    else a = coefficient<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wv);
     int slot = (int)(hash_key(wv, dd) & (unsigned long long)c.hash_mask);
     int mine = scratch_idx;
     bool placed = false, merged = false, past_empty = false;
@@ -1018,6 +1086,7 @@ class Engine final : public EngineBase {
     std::vector<SigCfg> cfg(n_);
     std::vector<int64_t> dirs, plist;
     int64_t tw = 0, regw = 0, rega = 0, hashn = 0, tab = 0, bhat = 0, Y = 0, z = 0, u = 0, part_min = 0;
+    int64_t bins = 0;   // candidate-list entries: every bin of every slot at its largest prime
     int64_t modes = 0, cm = 0;
     int64_t pmax_all = 2;
     const int single_logL = log2i(single_max_L<T>());
@@ -1065,6 +1134,7 @@ class Engine final : public EngineBase {
       bhat += std::min<int64_t>(Lmax, single_max_L<T>());
       c.Y_off = Y;
       Y += (int64_t)c.n_sets * d.p_max;
+      bins += d.p_max;
       if (c.logL_max > single_logL) {
         c.z_off = z;
         z += (int64_t)(c.n_sets + 1) * Lmax;
@@ -1132,6 +1202,7 @@ class Engine final : public EngineBase {
     ECHK(alloc(&tab_, (size_t)tab * sizeof(C2)));
     ECHK(alloc(&bhat_, (size_t)bhat * sizeof(C2)));
     ECHK(alloc(&Y_, (size_t)Y * sizeof(C2)));
+    ECHK(alloc(&cand_, (size_t)bins * sizeof(int2)));
     if (z > 0) ECHK(alloc(&Z_, (size_t)z * sizeof(C2)));
     ECHK(alloc(&u_, (size_t)u * sizeof(int64_t)));
     ECHK(alloc(&alpha_, (size_t)modes * sizeof(int32_t)));
@@ -1249,6 +1320,15 @@ class Engine final : public EngineBase {
   }
 
   // ---------------------------------------------------------------- one round
+  // occupied bins into the candidate list, then the ratio test, read-out and merge over it
+  cudaError_t launch_classify(const ClassifyOut& co) {
+    k_occupied<T><<<8 * n_sm_, 256, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, (const C2*)Y_, cand_, co.eta_override);
+    ECHK(cudaGetLastError());
+    k_classify<T><<<8 * n_sm_, 256, 0, st_>>>(n_, cfg_, run_, ctl_, cand_, (const C2*)Y_, u_, regw_, rega_,
+                                             (C2*)regtw_, hash_, co);
+    return cudaGetLastError();
+  }
+
   cudaError_t enqueue_round(const PlanArgs& pa, int64_t* launches, int round_idx, bool record) {
     auto mark = [&](int q) -> cudaError_t {
       if (!record) return cudaSuccess;
@@ -1285,10 +1365,8 @@ class Engine final : public EngineBase {
     }
     ECHK(mark(6));
     ClassifyOut co{nullptr, nullptr, nullptr, 0, nullptr, nullptr, -1.0};
-    k_classify<T><<<16 * n_sm_, 256, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)Y_, u_, regw_, rega_, (C2*)regtw_,
-                                              hash_, co);
-    ECHK(cudaGetLastError());
-    launches[4] += 1;
+    ECHK(launch_classify(co));
+    launches[4] += 2;
     ECHK(mark(5));
     return cudaSuccess;
   }
@@ -1538,9 +1616,7 @@ class Engine final : public EngineBase {
     ECHK(cudaMemsetAsync(stepc_, 0, 2 * sizeof(int), st_));
     int* cnt = reinterpret_cast<int*>(stepc_);
     ClassifyOut co{h_out, w_out, a_out, (int)cap, cnt, cnt + 1, eta};
-    k_classify<T><<<16 * n_sm_, 256, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)Y_, u_, regw_, rega_, (C2*)regtw_,
-                                              hash_, co);
-    ECHK(cudaGetLastError());
+    ECHK(launch_classify(co));
     int* h = reinterpret_cast<int*>(reinterpret_cast<char*>(host_stage_) + stage_st_);
     ECHK(cudaMemcpyAsync(h, stepc_, 2 * sizeof(int), cudaMemcpyDeviceToHost, st_));
     ECHK(cudaStreamSynchronize(st_));
@@ -1568,6 +1644,7 @@ class Engine final : public EngineBase {
   cudaStream_t st_ = nullptr;
   bool profile_ = false, use_graph_ = false, any_big_ = false;
   bool any_peel_ = false;   // some slot removes its registry in the bin domain
+  int2* cand_ = nullptr;    // (slot, bin) of the round's occupied bins, sum of p_max entries
   int peel_gx_ = 1;         // k_peel blocks per signal
   int logL_big_max_ = 0, small_logL_max_ = 1, small_threads_ = 256, n_ptab_ = 0;
   size_t smem_small_ = 0, smem_bigA_ = 0, smem_bigB_ = 0, bytes_ = 0, host_stage_bytes_ = 0;

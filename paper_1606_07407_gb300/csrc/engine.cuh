@@ -76,6 +76,7 @@ struct RoundCtl {
   int64_t n_tab, n_mode, n_rows, n_filt, n_bins, n_bigA, n_bigB, n_bigC, n_rows_s, n_filt_s;
   int64_t n_samp[kMaxSetGroup];               // sampling tiles, per set-group size
   unsigned long long ctr_samp[kMaxSetGroup], ctr_rows, ctr_filt;
+  unsigned long long n_cand;                  // occupied bins found this round (classification)
 };
 
 // exclusive scans over signals: tables, modes, DFT rows, filters, bins, four-step passes, DFT
