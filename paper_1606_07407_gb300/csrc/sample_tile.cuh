@@ -37,6 +37,60 @@ struct SampleSmem {
   int64_t item;
 };
 
+// Sums one staged 32-mode chunk (modes grp, grp + G, ...) into the first Q rows of the totals:
+// E = U_row L_lane, then every set's coefficient times E.
+template <typename T, int NS, int RW, int Q>
+__device__ __forceinline__ void accumulate_chunk(const SampleSmem<T, NS>& sm, int b, int grp, int G, int lane,
+                                                 int wrow, T (&tot)[RW][NS][2]) {
+  using C2 = c2<T>;
+  T acc[Q][NS][2];
+#pragma unroll
+  for (int qq = 0; qq < Q; ++qq)
+#pragma unroll
+    for (int nn = 0; nn < NS; ++nn) acc[qq][nn][0] = acc[qq][nn][1] = (T)0;
+#pragma unroll 2
+  for (int jj = grp; jj < kSampleChunk; jj += G) {
+    const C2 L = sm.Ls[b][jj][lane];
+    C2 E[Q];
+#pragma unroll
+    for (int qq = 0; qq < Q; ++qq) E[qq] = cmul(sm.Us[b][jj][wrow * RW + qq], L);
+#pragma unroll
+    for (int nn = 0; nn < NS; ++nn) {
+      const C2 cc = sm.Cs[b][jj][nn];
+#pragma unroll
+      for (int qq = 0; qq < Q; ++qq) {
+        acc[qq][nn][0] = fma(cc.x, E[qq].x, acc[qq][nn][0]);
+        acc[qq][nn][0] = fma(-cc.y, E[qq].y, acc[qq][nn][0]);
+        acc[qq][nn][1] = fma(cc.x, E[qq].y, acc[qq][nn][1]);
+        acc[qq][nn][1] = fma(cc.y, E[qq].x, acc[qq][nn][1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int qq = 0; qq < Q; ++qq)
+#pragma unroll
+    for (int nn = 0; nn < NS; ++nn) {
+      tot[qq][nn][0] += acc[qq][nn][0];
+      tot[qq][nn][1] += acc[qq][nn][1];
+    }
+}
+
+// The same for 1 <= nq < RW rows (the rows of a warp that reach past p are skipped).
+template <typename T, int NS, int RW>
+__device__ __forceinline__ void accumulate_rows(const SampleSmem<T, NS>& sm, int b, int grp, int G, int lane,
+                                                int wrow, int nq, T (&tot)[RW][NS][2]) {
+  switch (nq) {
+    case 1: if constexpr (RW > 1) accumulate_chunk<T, NS, RW, 1>(sm, b, grp, G, lane, wrow, tot); break;
+    case 2: if constexpr (RW > 2) accumulate_chunk<T, NS, RW, 2>(sm, b, grp, G, lane, wrow, tot); break;
+    case 3: if constexpr (RW > 3) accumulate_chunk<T, NS, RW, 3>(sm, b, grp, G, lane, wrow, tot); break;
+    case 4: if constexpr (RW > 4) accumulate_chunk<T, NS, RW, 4>(sm, b, grp, G, lane, wrow, tot); break;
+    case 5: if constexpr (RW > 5) accumulate_chunk<T, NS, RW, 5>(sm, b, grp, G, lane, wrow, tot); break;
+    case 6: if constexpr (RW > 6) accumulate_chunk<T, NS, RW, 6>(sm, b, grp, G, lane, wrow, tot); break;
+    case 7: if constexpr (RW > 7) accumulate_chunk<T, NS, RW, 7>(sm, b, grp, G, lane, wrow, tot); break;
+    default: break;
+  }
+}
+
 // One tile: 32 * 4 * RW samples x the sets of one group x the modes of one split.
 // Each 32-mode chunk is summed into fresh accumulators that are then added to the
 // running totals (blocked summation), which keeps the float rounding of long mode
@@ -61,6 +115,7 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
   const int ns_valid = min(r.gsize, c.n_sets - n0);
   const int K = sampled_modes(c, r);
   const int x0 = xt * TX;
+  const int nq = min(RW, max(0, (p - (x0 + wrow * RW * 32) + 31) / 32));   // valid rows of this warp
   const int j_begin = split * r.jper;
   const int j_end = min(K, j_begin + r.jper);
   const int nchunks = j_end > j_begin ? (j_end - j_begin + kSampleChunk - 1) / kSampleChunk : 0;
@@ -126,36 +181,9 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
       if (q + 1 < nchunks) issue_data(q + 1, b ^ 1);                     // gathers of the next chunk
       if (tid < kSampleChunk && q + 2 < nchunks) load_index(q + 2, &al_n, &ga_n);   // indices two ahead
     }
-    T acc[RW][NS][2];
-#pragma unroll
-    for (int qq = 0; qq < RW; ++qq)
-#pragma unroll
-      for (int nn = 0; nn < NS; ++nn) acc[qq][nn][0] = acc[qq][nn][1] = (T)0;
-#pragma unroll 2
-    for (int jj = grp; jj < kSampleChunk; jj += G) {
-      const C2 L = sm.Ls[b][jj][lane];
-      C2 E[RW];
-#pragma unroll
-      for (int qq = 0; qq < RW; ++qq) E[qq] = cmul(sm.Us[b][jj][wrow * RW + qq], L);
-#pragma unroll
-      for (int nn = 0; nn < NS; ++nn) {
-        const C2 cc = sm.Cs[b][jj][nn];
-#pragma unroll
-        for (int qq = 0; qq < RW; ++qq) {
-          acc[qq][nn][0] = fma(cc.x, E[qq].x, acc[qq][nn][0]);
-          acc[qq][nn][0] = fma(-cc.y, E[qq].y, acc[qq][nn][0]);
-          acc[qq][nn][1] = fma(cc.x, E[qq].y, acc[qq][nn][1]);
-          acc[qq][nn][1] = fma(cc.y, E[qq].x, acc[qq][nn][1]);
-        }
-      }
-    }
-#pragma unroll
-    for (int qq = 0; qq < RW; ++qq)
-#pragma unroll
-      for (int nn = 0; nn < NS; ++nn) {
-        tot[qq][nn][0] += acc[qq][nn][0];
-        tot[qq][nn][1] += acc[qq][nn][1];
-      }
+    // rows of this warp that lie below p (warp-uniform): a tile's last warps may have fewer
+    if (nq == RW) accumulate_chunk<T, NS, RW, RW>(sm, b, grp, G, lane, wrow, tot);
+    else if (nq > 0) accumulate_rows<T, NS, RW>(sm, b, grp, G, lane, wrow, nq, tot);
     if (S == 2) {
       // stage b is free again: it takes the indices of chunk q + 2
       if (tid < kSampleChunk && q + 2 < nchunks) put_index(b, al_n, ga_n);
