@@ -78,6 +78,18 @@ __device__ __forceinline__ int ceil_log2(int64_t v) {
   return r;
 }
 
+// Smallest length m 2^a >= max(n, 32) with m in {1, 3, 5}: the cyclic convolution of Bluestein's
+// DFT only needs n = 2p - 1 points, and these lengths factor into the FFT's radices.
+__device__ __forceinline__ int bluestein_length(int64_t n) {
+  n = max(n, (int64_t)32);
+  int64_t best = (int64_t)1 << ceil_log2(n);
+  for (int m = 3; m <= 5; m += 2) {
+    const int64_t L = (int64_t)m << ceil_log2((n + m - 1) / m);
+    if (L < best) best = L;
+  }
+  return (int)best;
+}
+
 __device__ __forceinline__ void big_geom(int logL, int* M1, int* M2, int* CT, int* RT) {
   const int l1 = logL / 2, l2 = logL - l1;
   *M1 = 1 << l1;
@@ -145,8 +157,9 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
           }
         }
         const int K = a.force ? a.force_K : sampled_modes(c, r);
-        r.logL = max(ceil_log2(2 * p - 1), 5);   // at least 32 points: one radix-32 pass
-        r.big = r.logL > a.single_max_logL;
+        r.logL = max(ceil_log2(2 * p - 1), 5);   // at least 32 points
+        r.L = bluestein_length(2 * p - 1);
+        r.big = r.L > (1 << a.single_max_logL);
         r.groups = (c.n_sets + kMaxSetGroup - 1) / kMaxSetGroup;
         r.gsize = (c.n_sets + r.groups - 1) / r.groups;
         {
@@ -159,6 +172,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
         r.chunks = K > 0 ? (K + kSampleChunk - 1) / kSampleChunk : 1;
         r.any_occupied = 0;
         r.n_acc = 0;
+        r.reg_start = r.K_reg;
         r.maxy0_bits = 0ull;
         r.samples += (int64_t)c.n_sets * p;
         r.terms += (int64_t)c.n_sets * p * K;
@@ -223,7 +237,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
         v[SC_SAMP0 + r.gsize - 1] = (int64_t)r.n_xt * r.groups * r.splits;
         v[SC_BINS] = r.p;
         if (!r.big) {
-          const bool sm = r.logL <= kSmallFftLog;
+          const bool sm = r.L <= (1 << kSmallFftLog);
           v[sm ? SC_ROWS_S : SC_ROWS] = c.n_sets;
           v[sm ? SC_FILT_S : SC_FILT] = 1;
         } else {
@@ -414,8 +428,8 @@ __device__ __forceinline__ void max_abs_to(unsigned long long* dst, double v) {
 // spectrum of the Bluestein filter b[m] = conj(chirp[|m|]), |m| < p, one block per signal
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, 1) k_filter(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run, RoundCtl* ctl,
-                         Scans sc, const c2<T>* __restrict__ tab, const c2<T>* __restrict__ twG, int64_t Lmax,
-                         c2<T>* __restrict__ bhat, int small) {
+                         Scans sc, const c2<T>* __restrict__ tab, TwSrc<c2<T>> tws, c2<T>* __restrict__ bhat,
+                         int small) {
   using C2 = c2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ C2 tw_lo[kTwLo], tw_hi[kSingleMaxLf / kTwLo];
@@ -426,13 +440,13 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_filter(int n, const SigCfg* 
   const int s = find_slot(sc.v[small ? SC_FILT_S : SC_FILT], n, item);
   const SigCfg& c = cfg[s];
   const SigRun& r = run[s];
-  const int logL = r.logL, L = 1 << logL;
+  const int L = r.L;
   const C2* chirp = tab + c.tab_off + r.p;
-  fft_tables(tw_hi, tw_lo, logL, twG, Lmax);
+  fft_tables(tw_hi, tw_lo, L, tws);
 #pragma unroll 8
   for (int x = threadIdx.x; x < L; x += blockDim.x) buf[fpad(x)] = filter_value<T>(x, r.p, L, chirp);
   __syncthreads();
-  fft_row<C2, false>(buf, logL, tw_hi, tw_lo);
+  fft_row<C2, false>(buf, L, tw_hi, tw_lo);
   C2* out = bhat + c.bhat_off;
 #pragma unroll 8
   for (int x = threadIdx.x; x < L; x += blockDim.x) out[x] = buf[fpad(x)];
@@ -441,8 +455,7 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_filter(int n, const SigCfg* 
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __restrict__ cfg, SigRun* run, RoundCtl* ctl, Scans sc,
                       const c2<T>* __restrict__ part, const c2<T>* __restrict__ tab,
-                      const c2<T>* __restrict__ bhat, const c2<T>* __restrict__ twG, int64_t Lmax,
-                      c2<T>* __restrict__ Y, int small) {
+                      const c2<T>* __restrict__ bhat, TwSrc<c2<T>> tws, c2<T>* __restrict__ Y, int small) {
   using C2 = c2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ C2 tw_lo[kTwLo], tw_hi[kSingleMaxLf / kTwLo];
@@ -455,11 +468,11 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   const int row = (int)(item - scan[s]);
   const SigCfg& c = cfg[s];
   const SigRun r = run[s];
-  const int logL = r.logL, L = 1 << logL;
+  const int L = r.L;
   const int64_t p = r.p;
   const C2* chirp = tab + c.tab_off + p;
   const C2* B = bhat + c.bhat_off;
-  fft_tables(tw_hi, tw_lo, logL, twG, Lmax);
+  fft_tables(tw_hi, tw_lo, L, tws);
   // loops unrolled so that each thread's global loads are in flight together
 #pragma unroll 8
   for (int x = threadIdx.x; x < L; x += blockDim.x) {
@@ -468,24 +481,24 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
     buf[fpad(x)] = v;
   }
   __syncthreads();
-  fft_row<C2, false>(buf, logL, tw_hi, tw_lo);
+  fft_row<C2, false>(buf, L, tw_hi, tw_lo);
 #pragma unroll 8
   for (int k = threadIdx.x; k < L; k += blockDim.x) buf[fpad(k)] = cmul(buf[fpad(k)], B[k]);
   __syncthreads();
-  fft_row<C2, true>(buf, logL, tw_hi, tw_lo);
+  fft_row<C2, true>(buf, L, tw_hi, tw_lo);
   const T invL = (T)1 / (T)L;
   C2* out = Y + c.Y_off + (int64_t)row * p;
+  T m2 = (T)0;   // largest |Y_0|^2 of this thread (set 0 only), in the transform's precision
 #pragma unroll 4
   for (int64_t h0 = 0; h0 < p; h0 += blockDim.x) {
     const int64_t h = h0 + threadIdx.x;
-    double m = 0.0;
     if (h < p) {
       const C2 v = cmul(chirp[h], cscale(buf[fpad((int)h)], invL));
       out[h] = v;
-      m = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+      m2 = fmax(m2, v.x * v.x + v.y * v.y);
     }
-    if (row == 0) max_abs_to<T>(&run[s].maxy0_bits, sqrt(m));
   }
+  if (row == 0) max_abs_to<T>(&run[s].maxy0_bits, sqrt((double)m2));
 }
 
 // ------------------------------------------------------------------ DFT, four-step passes for long lengths
@@ -626,20 +639,20 @@ __global__ void k_bigC(int n, const SigCfg* __restrict__ cfg, SigRun* run, const
     const T invL = (T)1 / (T)L;
     C2* out = Y + c.Y_off + (int64_t)row * r.p;
     const int tot = CT * M1;
+    T m2 = (T)0;
     for (int e0 = 0; e0 < tot; e0 += blockDim.x) {
       const int e = e0 + threadIdx.x;
-      double m = 0.0;
       if (e < tot) {
         const int x1 = e / CT, cc = e - x1 * CT;
         const int64_t x = (int64_t)x1 * M2 + x2_0 + cc;
         if (x < r.p) {
           const C2 v = cmul(chirp[x], cscale(buf[cc * ls + brev_bits(x1, logM1)], invL));
           out[x] = v;
-          m = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+          m2 = fmax(m2, v.x * v.x + v.y * v.y);
         }
       }
-      if (row == 0) max_abs_to<T>(&run[s].maxy0_bits, sqrt(m));
     }
+    if (row == 0) max_abs_to<T>(&run[s].maxy0_bits, sqrt((double)m2));
     __syncthreads();
   }
 }
@@ -649,8 +662,16 @@ __global__ void k_bigC(int n, const SigCfg* __restrict__ cfg, SigRun* run, const
 // Residual BINS: each live registry mode (w, a) of an active signal takes p a e^{2 pi i w_n / N}
 // off bin (w . u) mod p of set n (p a off set 0).  That is the transform of the mode's samples
 // (sum over x of W^{(alpha - h) x} is p at h = alpha and 0 elsewhere), so f's transform minus
-// these is the transform of f - g (Alg. 2, by linearity).  Products in double, one rounding to T;
-// modes sharing a bin add in any order.
+// these is the transform of f - g (Alg. 2, by linearity).  Modes sharing a bin add in any order.
+// y += (gx, gy) atomically: one 64-bit vector atomic in float, two in double
+__device__ __forceinline__ void peel_add(float* y, float gx, float gy) {
+  atomicAdd(reinterpret_cast<float2*>(y), make_float2(gx, gy));
+}
+__device__ __forceinline__ void peel_add(double* y, double gx, double gy) {
+  atomicAdd(y, gx);
+  atomicAdd(y + 1, gy);
+}
+
 template <typename T>
 __global__ void k_peel(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run,
                        const int64_t* __restrict__ ubuf, const int32_t* __restrict__ regw,
@@ -668,15 +689,13 @@ __global__ void k_peel(int n, const SigCfg* __restrict__ cfg, const SigRun* __re
     const double2 a = rega[c.rega_off + jr];
     if (a.x == 0.0 && a.y == 0.0) continue;   // pruned
     const int64_t h = (int64_t)project_mod(regw + c.regw_off + (int64_t)jr * c.d, c.d, u, c.box_lo, p, r.mod_m);
-    const double px = (double)p * a.x, py = (double)p * a.y;
-    atomicAdd(Y + 2 * h, (T)-px);
-    atomicAdd(Y + 2 * h + 1, (T)-py);
+    // -p a, then -p a e^{2 pi i w_n / N} for n >= 1, in T (float policy: the double pipe is narrow)
+    const T px = (T)(-(double)p * a.x), py = (T)(-(double)p * a.y);
+    peel_add(Y + 2 * h, px, py);
     const c2<T>* tw = regtw + c.regtw_off + (int64_t)jr * c.d;
     for (int nn = 1; nn < c.n_sets; ++nn) {
       const c2<T> t = tw[nn - 1];   // e^{2 pi i w_n / N}
-      T* yn = Y + 2 * ((int64_t)nn * p + h);
-      atomicAdd(yn, (T)-(px * (double)t.x - py * (double)t.y));
-      atomicAdd(yn + 1, (T)-(px * (double)t.y + py * (double)t.x));
+      peel_add(Y + 2 * ((int64_t)nn * p + h), px * t.x - py * t.y, px * t.y + py * t.x);
     }
   }
 }
@@ -708,8 +727,10 @@ __device__ __forceinline__ bool read_coord(R ynx, R yny, R y0x, R y0y, int64_t N
   const R v = (R)N * phi / ((R)2 * pi);
   const R rr = rint(v);
   if (!(fabs(v - rr) <= delta)) return false;
-  int64_t wn = ((int64_t)rr - box_lo) % N;
+  // |rr| <= N / 2 and -N <= box_lo <= 0, so rr - box_lo lies in [-N/2, 3N/2]: one wrap
+  int64_t wn = (int64_t)rr - box_lo;
   if (wn < 0) wn += N;
+  else if (wn >= N) wn -= N;
   *w_out = wn + box_lo;
   return true;
 }
@@ -777,19 +798,31 @@ __device__ void read_coords(const SigCfg& c, const SigRun& r, const c2<T>* Y, in
 // rounding (and the leakage of other modes' residuals, whose phases differ across the sets).
 template <typename T, typename R>
 __device__ double2 coefficient(const SigCfg& c, const SigRun& r, const c2<T>* Y, int64_t h, R y0x, R y0y,
-                               const int32_t* w) {
+                               const int32_t* w, const c2<T>* tn) {
   if (!c.coef_mean) {
+    if (sizeof(R) == 4) {
+      const float scale = 1.0f / (float)r.p;
+      return make_double2((double)((float)y0x * scale), (double)((float)y0y * scale));
+    }
     const double scale = 1.0 / (double)r.p;
     return make_double2((double)y0x * scale, (double)y0y * scale);
   }
   R ax = y0x, ay = y0y;
   for (int n = 1; n <= c.d; ++n) {
     const c2<T> yn = Y[(int64_t)n * r.p + h];
-    int64_t m = (int64_t)w[n - 1] % c.N;
-    if (m < 0) m += c.N;
-    const c2<R> t = unit_root<R>(m, c.N);   // e^{2 pi i w_n / N}
+    c2<R> t;   // e^{2 pi i w_n / N}
+    if (sizeof(R) == sizeof(T) && tn != nullptr) {
+      t = mk2((R)tn[n - 1].x, (R)tn[n - 1].y);
+    } else {
+      const int64_t m = w[n - 1] < 0 ? (int64_t)w[n - 1] + c.N : (int64_t)w[n - 1];   // w in [box_lo, box_lo + N)
+      t = unit_root<R>(m, c.N);
+    }
     ax += (R)yn.x * t.x + (R)yn.y * t.y;     // Y_n conj(t)
     ay += (R)yn.y * t.x - (R)yn.x * t.y;
+  }
+  if (sizeof(R) == 4) {   // float read-out: scale in float (the double pipe of this GPU is narrow)
+    const float scale = 1.0f / ((float)r.p * (float)c.n_sets);
+    return make_double2((double)((float)ax * scale), (double)((float)ay * scale));
   }
   const double scale = 1.0 / ((double)r.p * (double)c.n_sets);
   return make_double2((double)ax * scale, (double)ay * scale);
@@ -799,10 +832,13 @@ __device__ double2 coefficient(const SigCfg& c, const SigRun& r, const c2<T>* Y,
 // candidate list (warp-aggregated); also the first round's reference amplitude A_ref and the
 // flag that some bin is occupied (the stop rule reads it).
 template <typename T>
-__global__ void k_occupied(int n, const SigCfg* __restrict__ cfg, SigRun* run, RoundCtl* ctl, Scans sc,
-                           const c2<T>* __restrict__ Ybuf, int2* __restrict__ cand, double eta_override) {
+__global__ void __launch_bounds__(256) k_occupied(int n, const SigCfg* __restrict__ cfg, SigRun* run, RoundCtl* ctl,
+                                                  Scans sc, const c2<T>* __restrict__ Ybuf, int2* __restrict__ cand,
+                                                  double eta_override) {
+  __shared__ int warp_cnt[8];
+  __shared__ unsigned long long tile_base;
   const int64_t total = ctl->n_bins;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = base + threadIdx.x;
     bool occ = false;
@@ -814,29 +850,57 @@ __global__ void k_occupied(int n, const SigCfg* __restrict__ cfg, SigRun* run, R
       const SigCfg& c = cfg[s];
       SigRun* rp = run + s;
       const int64_t p = rp->p;
-      double a_ref;
-      if (rp->round == 1) {
-        a_ref = __longlong_as_double((long long)rp->maxy0_bits) / (double)p;
-        if (h == 0) rp->a_ref = a_ref;
-      } else {
-        a_ref = rp->a_ref;
+      const bool first = rp->round == 1;
+      const double maxy0 = __longlong_as_double((long long)rp->maxy0_bits);
+      if (h == 0) {
+        // once per signal: A_ref (first round) and the prune level of the round's merges
+        const double a_ref = first ? maxy0 / (double)p : rp->a_ref;
+        if (first) rp->a_ref = a_ref;
+        rp->eta_prune = fmax(c.rho * a_ref, 6.0 * c.sigma / sqrt((double)p));
       }
-      const double eta = eta_override >= 0.0 ? eta_override
-                                             : fmax(c.rho * (double)p * a_ref, 6.0 * c.sigma * sqrt((double)p));
       const c2<T> y0 = Ybuf[c.Y_off + h];
-      const double m0d = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y);
-      occ = m0d > eta;
+      if (sizeof(T) == 4) {
+        // float policy: squared magnitude against the squared level, all in float (the double
+        // pipe of this GPU is narrow, and the level is a heuristic far from any mode's size)
+        const float a_ref = first ? (float)maxy0 / (float)p : (float)rp->a_ref;
+        const float eta = eta_override >= 0.0 ? (float)eta_override
+                                               : fmaxf((float)c.rho * (float)p * a_ref,
+                                                       6.0f * (float)c.sigma * sqrtf((float)p));
+        occ = (float)y0.x * (float)y0.x + (float)y0.y * (float)y0.y > eta * eta;
+      } else {
+        const double a_ref = first ? maxy0 / (double)p : rp->a_ref;
+        const double eta = eta_override >= 0.0 ? eta_override
+                                               : fmax(c.rho * (double)p * a_ref, 6.0 * c.sigma * sqrt((double)p));
+        occ = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y) > eta;
+      }
       if (occ && !rp->any_occupied) rp->any_occupied = 1;
     }
+    // one slot range of the list per tile: warp counts, their prefix, one atomic
     const unsigned mask = __ballot_sync(0xffffffffu, occ);
-    if (mask) {
-      const int leader = __ffs(mask) - 1;
-      unsigned long long b0 = 0;
-      if (lane == leader) b0 = atomicAdd(&ctl->n_cand, (unsigned long long)__popc(mask));
-      b0 = __shfl_sync(0xffffffffu, b0, leader);
-      if (occ) cand[b0 + __popc(mask & ((1u << lane) - 1u))] = make_int2(s, (int)h);
+    if (lane == 0) warp_cnt[wid] = __popc(mask);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        const int cw = warp_cnt[w];
+        warp_cnt[w] = tot;
+        tot += cw;
+      }
+      tile_base = tot > 0 ? atomicAdd(&ctl->n_cand, (unsigned long long)tot) : 0ull;
     }
+    __syncthreads();
+    if (occ) cand[tile_base + warp_cnt[wid] + __popc(mask & ((1u << lane) - 1u))] = make_int2(s, (int)h);
+    __syncthreads();   // warp_cnt and tile_base are reused by the next tile
   }
+}
+
+// *ctr += v from every active lane, one atomic per group of lanes that share key (a signal)
+__device__ __forceinline__ void warp_add(int* ctr, int v, int key) {
+  const unsigned grp = __match_any_sync(__activemask(), key);
+  const int leader = __ffs(grp) - 1;
+  int sum = 0;
+  for (unsigned m = grp; m; m &= m - 1) sum += __shfl_sync(grp, v, __ffs(m) - 1);
+  if ((threadIdx.x & 31) == leader) atomicAdd(ctr, sum);
 }
 
 template <typename T>
@@ -852,19 +916,21 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
     const SigCfg& c = cfg[s];
     SigRun* rp = run + s;
     const SigRun& r = *rp;
-    const int64_t p = r.p;
     const c2<T>* Y = Ybuf + c.Y_off;
     const c2<T> y0 = Y[h];
-    const double m0d = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y);
     const int64_t* u = ubuf + c.u_off;
     const int dd = c.d;
     int32_t wk[64];
     int32_t* wreg = dd <= 64 ? wk : nullptr;   // decoded vector kept for the read-out
     bool ok;
-    if (c.ratio64) ok = decode_bin<T, double>(c, r, Y, u, h, (double)y0.x, (double)y0.y, m0d, wreg);
-    else ok = decode_bin<T, T>(c, r, Y, u, h, (T)y0.x, (T)y0.y, (T)m0d, wreg);
+    if (c.ratio64) {
+      const double m0d = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y);
+      ok = decode_bin<T, double>(c, r, Y, u, h, (double)y0.x, (double)y0.y, m0d, wreg);
+    } else {
+      ok = decode_bin<T, T>(c, r, Y, u, h, y0.x, y0.y, sqrt(y0.x * y0.x + y0.y * y0.y), wreg);
+    }
     if (!ok) continue;
-    atomicAdd(&rp->n_acc, 1);
+    warp_add(&rp->n_acc, 1, s);
     if (co.count != nullptr) {
       const int idx = atomicAdd(co.count, 1);
       if (idx >= co.cap) {
@@ -880,8 +946,8 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
       } else {
         read_coords<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wo);
       }
-      if (c.ratio64) co.a[idx] = coefficient<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wo);
-      else co.a[idx] = coefficient<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wo);
+      if (c.ratio64) co.a[idx] = coefficient<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wo, nullptr);
+      else co.a[idx] = coefficient<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wo, nullptr);
       continue;
     }
     // ---- merge into the registry: keys accepted in one round are distinct (each lands in its
@@ -891,7 +957,7 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
     double2* ra = rega + c.rega_off;
     c2<T>* rt = regtw + c.regtw_off;
     int32_t* hs = hash + c.hash_off;
-    const double eta_prune = fmax(c.rho * r.a_ref, 6.0 * c.sigma / sqrt((double)p));
+    const double eta_prune2 = r.eta_prune * r.eta_prune;
     // decoded vector: up to 64 coordinates in registers, else read back from the registry slot
     int32_t* wv = wk;
     int scratch_idx = -1;
@@ -907,14 +973,21 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
       if (c.ratio64) read_coords<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wv);
       else read_coords<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wv);
     }
+    // e^{2 pi i w_n / N} of the decoded vector: the registry keeps them (and the float read-out
+    // uses them) so they are formed once
+    c2<T> tn[64];
+    const bool keep_tn = dd <= 64;
+    if (keep_tn) {
+      for (int l = 0; l < dd; ++l) tn[l] = unit_root<T>(wv[l] < 0 ? (int64_t)wv[l] + c.N : (int64_t)wv[l], c.N);
+    }
     double2 a;
-    if (c.ratio64) a = coefficient<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wv);
-    else a = coefficient<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wv);
+    if (c.ratio64) a = coefficient<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wv, nullptr);
+    else a = coefficient<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wv, keep_tn ? tn : nullptr);
     int slot = (int)(hash_key(wv, dd) & (unsigned long long)c.hash_mask);
     int mine = scratch_idx;
     bool placed = false, merged = false, past_empty = false;
     for (int probe = 0; probe <= c.hash_mask; ++probe, slot = (slot + 1) & c.hash_mask) {
-      int cur = atomicAdd(&hs[slot], 0);
+      int cur = __ldcg(&hs[slot]);   // a stale -1 only makes the CAS below fail
       if (cur < 0) {
         past_empty = true;   // the key is not in the table
         if (mine < 0) {
@@ -926,12 +999,10 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
           for (int l = 0; l < dd; ++l) rw[(int64_t)mine * dd + l] = wv[l];
         }
         ra[mine] = a;
-        for (int l = 0; l < dd; ++l) {
-          int64_t m = (int64_t)wv[l] % c.N;
-          if (m < 0) m += c.N;
-          rt[(int64_t)mine * dd + l] = unit_root<T>(m, c.N);
-        }
-        __threadfence();
+        for (int l = 0; l < dd; ++l)
+          rt[(int64_t)mine * dd + l] =
+              keep_tn ? tn[l] : unit_root<T>(wv[l] < 0 ? (int64_t)wv[l] + c.N : (int64_t)wv[l], c.N);
+        // no fence: nobody reads this entry before the next kernel (see the probe rule below)
         cur = atomicCAS(&hs[slot], -1, mine);
         if (cur < 0) {
           placed = true;
@@ -939,16 +1010,18 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
         }
         continue;   // slot taken by another new key of this round
       }
-      if (past_empty) continue;   // only new keys of this round lie beyond an empty slot
-      __threadfence();
-      const volatile int32_t* ow = rw + (int64_t)cur * dd;
+      // keys accepted in one round are distinct (each decodes in its own bin), so a slot claimed
+      // this round (index from the round's start on, or any slot beyond an empty one) holds
+      // another key: only keys of earlier rounds, complete since the last kernel, are compared
+      if (past_empty || cur >= r.reg_start) continue;
+      const int32_t* ow = rw + (int64_t)cur * dd;
       bool same = true;
       for (int l = 0; l < dd && same; ++l) same = (ow[l] == wv[l]);
       if (same) {
         const double2 old = ra[cur];
         double2 nw = make_double2(old.x + a.x, old.y + a.y);   // duplicate key: a_R += a
         const bool was_live = (old.x != 0.0 || old.y != 0.0);
-        const bool live = sqrt(nw.x * nw.x + nw.y * nw.y) >= eta_prune;   // prune small coefficients
+        const bool live = nw.x * nw.x + nw.y * nw.y >= eta_prune2;   // prune small coefficients
         if (!live) nw = make_double2(0.0, 0.0);
         ra[cur] = nw;
         if (was_live && !live) atomicSub(&rp->n_live, 1);
@@ -962,7 +1035,7 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
       ra[scratch_idx] = make_double2(0.0, 0.0);
       for (int l = 0; l < dd; ++l) rt[(int64_t)scratch_idx * dd + l] = mk2((T)0, (T)0);
     }
-    if (placed) atomicAdd(&rp->n_live, 1);
+    if (placed) warp_add(&rp->n_live, 1, s);
     else if (!merged && mine >= 0 && mine < c.reg_cap) atomicOr(&rp->err, 2);   // table full
   }
 }
@@ -1210,6 +1283,8 @@ class Engine final : public EngineBase {
     ECHK(alloc(&Cm_, (size_t)cm * sizeof(C2)));
     ECHK(alloc(&part_, (size_t)part_cap_ * sizeof(C2)));
     ECHK(alloc(&twG_, (size_t)Lmax_ * sizeof(C2)));
+    ECHK(alloc(&twG3_, (size_t)len3_ * sizeof(C2)));
+    ECHK(alloc(&twG5_, (size_t)len5_ * sizeof(C2)));
     ECHK(alloc(&hist_, SFFT_STATS_MAX_ROUNDS * sizeof(HistRec)));
     ECHK(alloc(&bind_, (size_t)n_ * kBindArrays * sizeof(int64_t)));
     ECHK(alloc(&outn_, (size_t)n_ * sizeof(int64_t)));
@@ -1230,6 +1305,10 @@ class Engine final : public EngineBase {
     if (!plist.empty())
       ECHK(cudaMemcpyAsync(plist_, plist.data(), plist.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st_));
     k_twiddles<<<(int)std::min<int64_t>((Lmax_ + 255) / 256, 4096), 256, 0, st_>>>(Lmax_, twG_, sizeof(T) == 8);
+    ECHK(cudaGetLastError());
+    k_twiddles<<<(int)std::min<int64_t>((len3_ + 255) / 256, 4096), 256, 0, st_>>>(len3_, twG3_, sizeof(T) == 8);
+    ECHK(cudaGetLastError());
+    k_twiddles<<<(int)std::min<int64_t>((len5_ + 255) / 256, 4096), 256, 0, st_>>>(len5_, twG5_, sizeof(T) == 8);
     ECHK(cudaGetLastError());
     // launch shapes
     small_threads_ = std::max(32, (1 << small_logL_max_) / fft_per_thread<C2>());
@@ -1275,18 +1354,18 @@ class Engine final : public EngineBase {
     const int ls = std::min(small_logL_max_, kSmallFftLog);
     const int thr_s = std::max(32, (1 << ls) / fft_per_thread<C2>());
     const size_t smem_s = (size_t)((1 << ls) + (1 << ls) / 32) * sizeof(C2);
-    k_filter<T><<<n_, thr_s, smem_s, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_, Lmax_, (C2*)bhat_, 1);
+    const TwSrc<C2> tws = tw_src();
+    k_filter<T><<<n_, thr_s, smem_s, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, tws, (C2*)bhat_, 1);
     ECHK(cudaGetLastError());
     k_dft<T><<<(unsigned)rows_max_, thr_s, smem_s, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_,
-                                                          (C2*)bhat_, (C2*)twG_, Lmax_, (C2*)Y_, 1);
+                                                          (C2*)bhat_, tws, (C2*)Y_, 1);
     ECHK(cudaGetLastError());
     if (small_logL_max_ > kSmallFftLog) {
-      k_filter<T><<<n_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, (C2*)twG_,
-                                                           Lmax_, (C2*)bhat_, 0);
+      k_filter<T><<<n_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, tws, (C2*)bhat_,
+                                                           0);
       ECHK(cudaGetLastError());
       k_dft<T><<<(unsigned)rows_max_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
-                                                                           (C2*)tab_, (C2*)bhat_, (C2*)twG_, Lmax_,
-                                                                           (C2*)Y_, 0);
+                                                                           (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 0);
       ECHK(cudaGetLastError());
     }
     return cudaSuccess;
@@ -1679,6 +1758,21 @@ class Engine final : public EngineBase {
   unsigned ns_mask_ = 0;   // set-group sizes present among the slots
   void* part_ = nullptr;
   void* twG_ = nullptr;
+  void* twG3_ = nullptr;   // e^{-2 pi i j / len3_}, len3_ = 3 2^A: lengths 3 2^a of the one-block path
+  void* twG5_ = nullptr;   // the same for 5 2^a
+  // the one-block path's largest lengths 3 2^a and 5 2^a (and a table for the power-of-two ones)
+  static constexpr int64_t len3_ = 3 * (single_max_L<T>() / 4);
+  static constexpr int64_t len5_ = 5 * (single_max_L<T>() / 8);
+  TwSrc<C2> tw_src() const {
+    TwSrc<C2> t;
+    t.t[0] = (const C2*)twG_;
+    t.t[1] = (const C2*)twG3_;
+    t.t[2] = (const C2*)twG5_;
+    t.len[0] = Lmax_;
+    t.len[1] = len3_;
+    t.len[2] = len5_;
+    return t;
+  }
   HistRec* hist_ = nullptr;
   void* bind_ = nullptr;
   int64_t* outn_ = nullptr;

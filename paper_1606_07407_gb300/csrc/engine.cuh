@@ -57,15 +57,17 @@ struct SigRun {
   int any_occupied;   // some bin above the empty-bin level this round
   int n_acc;          // bins accepted this round
   int k_sig;          // modes of the bound black box
-  int logL, big;      // Bluestein length of the round; big = four-step path
+  int logL, big;      // power-of-two Bluestein length of the round (four-step path when big)
+  int L;              // Bluestein length of the one-block path: m 2^a >= 2p - 1, m in {1, 3, 5}
   int n_xt, groups, gsize, chunks, jper, splits;
   int mgroups;        // mode groups per sampling tile (warps sharing rows when p is small)
-  int pad3;
+  int reg_start;      // registry entries at the start of the round
   int64_t p;
   unsigned long long mod_m;   // floor((2^64 - 1) / p), Barrett reduction
   int64_t part_off;
   unsigned long long maxy0_bits;
   double a_ref;
+  double eta_prune;   // the round's prune level: max(rho A_ref, 6 sigma / sqrt(p))
   int64_t samples, terms;
   int64_t n_out;
 };

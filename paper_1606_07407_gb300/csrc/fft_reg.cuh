@@ -1,18 +1,20 @@
-// Stockham auto-sort FFT of one row held in shared memory, with each pass's
-// radix-R butterflies done in registers.
+// Stockham auto-sort FFT of one row held in shared memory, with each pass's radix-R
+// butterflies done in registers, for lengths L = m 2^a with m in {1, 3, 5}.
 //
-// For a length L = 2^n (n >= 5) the passes use radix E (32 in float, 16 in
-// double) while E points remain per transform, then one smaller power of two.  Pass with
-// stride Ns (product of the earlier radices) and radix R, for j = 0..L/R-1:
+// Passes use radix E (32 in float, 16 in double) while E points remain in the power-of-two
+// part; the rest of it goes with the odd factor m into one pass of radix m 2^b when that is at
+// most E points, else into a radix-2^b pass followed by a radix-m pass.  The pass with stride Ns
+// (product of the earlier radices, always a power of two) and radix R computes, for the
+// butterflies j = 0..L/R-1:
 //     v[r] = x[j + r L/R] * w^(r k),  k = j mod Ns,  w = e^{-+2 pi i / (Ns R)}
 //     v    = DFT_R(v)
 //     x'[(j div Ns) Ns R + k + r Ns] = v[r]
-// which leaves the transform in natural order after the last pass.  Every thread
-// handles E values per pass (E / R indices j), so L / E threads take part; all
-// of a pass's values are read before the barrier and written after it, so one
-// buffer suffices.  Rows use the padded index e + e / 32: the only pass whose
-// writes stride by 32 (Ns = 1) then hits distinct banks.  Twiddles e^{-2 pi i m / L}
-// come from two 128-entry tables, e^{-2 pi i m / L} = hi[m >> 7] * lo[m & 127].
+// which leaves the transform in natural order after the last pass.  The block's threads take
+// the butterflies in turn, at most E / R each (the block sizes and lengths in use keep L / R
+// within that); all of a pass's values are read before a barrier and written after it, so one
+// buffer suffices.  Rows use the padded index e + e / 32: the only pass whose writes stride by
+// 32 (Ns = 1) then hits distinct banks.  Twiddles e^{-2 pi i m / L} come from two tables,
+// e^{-2 pi i m / L} = hi[m >> 7] * lo[m & 127], filled from a global table of a multiple of L.
 #pragma once
 
 #include "sfft_internal.cuh"
@@ -27,8 +29,8 @@ template <typename C2> __host__ __device__ constexpr int fft_per_thread() { retu
 
 __device__ __forceinline__ int fpad(int e) { return e + (e >> 5); }
 
-// cos(pi m / 16), m = 0..16: the unit roots of order 32 used inside the register DFTs
-__device__ __forceinline__ double cos_pi16(int m) {
+// cos(pi m / 16), m = 0..16: the unit roots of order 32 used inside the power-of-two register DFTs
+__host__ __device__ __forceinline__ double cos_pi16(int m) {
   constexpr double c[17] = {1.0,
                             0.98078528040323044912618223613424,
                             0.92387953251128675612818318939679,
@@ -49,13 +51,56 @@ __device__ __forceinline__ double cos_pi16(int m) {
   return c[m];
 }
 
-// In-register DFT of R points (R a power of two <= 32), forward (e^{-2 pi i}) or inverse.
+// cos(pi j / 60), j = 0..60: the unit roots of order dividing 120 used by the radix-3 and
+// radix-5 factors
+__host__ __device__ constexpr double cos_pi60(int j) {
+  constexpr double c[61] = {
+      +1.000000000000000000000, +0.998629534754573873784, +0.994521895368273336923,
+      +0.987688340595137726190, +0.978147600733805637929, +0.965925826289068286750,
+      +0.951056516295153572116, +0.933580426497201748990, +0.913545457642600895502,
+      +0.891006524188367862360, +0.866025403784438646764, +0.838670567945424029638,
+      +0.809016994374947424102, +0.777145961456970879980, +0.743144825477394235015,
+      +0.707106781186547524401, +0.669130606358858213826, +0.629320391049837452706,
+      +0.587785252292473129169, +0.544639035015027082224, +0.500000000000000000000,
+      +0.453990499739546791560, +0.406736643075800207754, +0.358367949545300273484,
+      +0.309016994374947424102, +0.258819045102520762349, +0.207911690817759337102,
+      +0.156434465040230869010, +0.104528463267653471400, +0.052335956242943832722,
+      +0.0,                     -0.052335956242943832722, -0.104528463267653471400,
+      -0.156434465040230869010, -0.207911690817759337102, -0.258819045102520762349,
+      -0.309016994374947424102, -0.358367949545300273484, -0.406736643075800207754,
+      -0.453990499739546791560, -0.500000000000000000000, -0.544639035015027082224,
+      -0.587785252292473129169, -0.629320391049837452706, -0.669130606358858213826,
+      -0.707106781186547524401, -0.743144825477394235015, -0.777145961456970879980,
+      -0.809016994374947424102, -0.838670567945424029638, -0.866025403784438646764,
+      -0.891006524188367862360, -0.913545457642600895502, -0.933580426497201748990,
+      -0.951056516295153572116, -0.965925826289068286750, -0.978147600733805637929,
+      -0.987688340595137726190, -0.994521895368273336923, -0.998629534754573873784,
+      -1.000000000000000000000};
+  return c[j];
+}
+
+// cos and sin of pi j / 60 for 0 <= j < 120
+__host__ __device__ constexpr double cos_pi60_any(int j) { return j <= 60 ? cos_pi60(j) : cos_pi60(120 - j); }
+__host__ __device__ constexpr double sin_pi60_any(int j) {
+  return j <= 60 ? cos_pi60(j <= 30 ? 30 - j : j - 30) : -cos_pi60(j <= 90 ? 90 - j : j - 90);
+}
+
+// e^{-+2 pi i e / N} (forward: minus) for N dividing 120
+template <typename C2, int N, bool INV>
+__host__ __device__ __forceinline__ C2 root_n(int e) {
+  using T = decltype(C2().x);
+  const int j = ((120 / N) * e) % 120;
+  const double s = sin_pi60_any(j);
+  return mk2((T)cos_pi60_any(j), (T)(INV ? s : -s));
+}
+
+// In-register DFT of R points, R a power of two <= 32, forward (e^{-2 pi i}) or inverse.
 // Radix-2 decimation in time on the bit-reversed register order; all indices are
 // compile-time constants, so the permutation costs nothing.
 template <typename C2, int R, bool INV>
-__device__ __forceinline__ void dft_reg(C2 (&v)[R]) {
+__host__ __device__ __forceinline__ void dft_reg(C2 (&v)[R]) {
   using T = decltype(C2().x);
-  constexpr int LG = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5;
+  constexpr int LG = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5;
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     int j = 0;
@@ -74,14 +119,13 @@ __device__ __forceinline__ void dft_reg(C2 (&v)[R]) {
 #pragma unroll
       for (int t = 0; t < s; ++t) {
         // w = e^{-+2 pi i t / (2 s)} = e^{-+ i pi (16 t / s) / 16}
-        const int m = (16 * t) / s;   // 0..31 in units of pi / 16
+        const int m = (16 * t) / s;   // 0..15 in units of pi / 16
         const C2 a = v[g + t];
         C2 b = v[g + t + s];
         if (t != 0) {
-          // m < 16: cos(pi m / 16) and sin(pi m / 16) = cos(pi |8 - m| / 16)
+          // cos(pi m / 16) and sin(pi m / 16) = cos(pi |8 - m| / 16)
           const T c = (T)cos_pi16(m);
           const T sn = (T)cos_pi16(m <= 8 ? 8 - m : m - 8);
-          // w = c - i sn (forward) or c + i sn (inverse), sn = sin(pi m / 16)
           const T wy = INV ? sn : -sn;
           b = mk2(b.x * c - b.y * wy, b.x * wy + b.y * c);
         }
@@ -90,6 +134,88 @@ __device__ __forceinline__ void dft_reg(C2 (&v)[R]) {
       }
     }
   }
+}
+
+// 3-point DFT: X0 = a + t, X1,2 = a - t / 2 -+ i sin(2 pi / 3) (b - c), t = b + c
+template <typename C2, bool INV>
+__host__ __device__ __forceinline__ void dft3(C2 (&v)[3]) {
+  using T = decltype(C2().x);
+  const T sn = (T)cos_pi60(10);   // sin(2 pi / 3)
+  const C2 t = cadd(v[1], v[2]);
+  const C2 d = csub(v[1], v[2]);
+  const C2 m = mk2(v[0].x - (T)0.5 * t.x, v[0].y - (T)0.5 * t.y);
+  const C2 q = INV ? mk2(-sn * d.y, sn * d.x) : mk2(sn * d.y, -sn * d.x);   // -+ i sn d
+  v[0] = cadd(v[0], t);
+  v[1] = cadd(m, q);
+  v[2] = csub(m, q);
+}
+
+// 5-point DFT from the symmetric pairs t1 = x1 + x4, t2 = x2 + x3, t3 = x1 - x4, t4 = x2 - x3:
+// X1,4 = x0 + c1 t1 + c2 t2 -+ i (s1 t3 + s2 t4), X2,3 = x0 + c2 t1 + c1 t2 -+ i (s2 t3 - s1 t4),
+// c_k = cos(2 pi k / 5), s_k = sin(2 pi k / 5); the inverse swaps the signs of the i terms.
+template <typename C2, bool INV>
+__host__ __device__ __forceinline__ void dft5(C2 (&v)[5]) {
+  using T = decltype(C2().x);
+  const T c1 = (T)cos_pi60(24), c2 = (T)cos_pi60(48);   // cos(2 pi / 5), cos(4 pi / 5)
+  const T s1 = (T)cos_pi60(6), s2 = (T)cos_pi60(18);    // sin(2 pi / 5), sin(4 pi / 5)
+  const C2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+  const C2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+  const C2 a1 = mk2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+  const C2 a2 = mk2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+  const C2 b1 = mk2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
+  const C2 b2 = mk2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
+  // -+ i b
+  const C2 q1 = INV ? mk2(-b1.y, b1.x) : mk2(b1.y, -b1.x);
+  const C2 q2 = INV ? mk2(-b2.y, b2.x) : mk2(b2.y, -b2.x);
+  v[0] = cadd(v[0], cadd(t1, t2));
+  v[1] = cadd(a1, q1);
+  v[4] = csub(a1, q1);
+  v[2] = cadd(a2, q2);
+  v[3] = csub(a2, q2);
+}
+
+template <typename C2, int R, bool INV>
+__host__ __device__ __forceinline__ void dft_any(C2 (&v)[R]);
+
+// DFT of N = M P points (M = 3 or 5, P a power of two) by one Cooley-Tukey step: with
+// n = P n1 + n2 and k = k1 + M k2, X[k] = sum_{n2} W_N^{n2 k1} W_P^{n2 k2} sum_{n1} x[n] W_M^{n1 k1}.
+template <typename C2, int M, int P, bool INV>
+__host__ __device__ __forceinline__ void dft_mixed(C2 (&v)[M * P]) {
+  constexpr int N = M * P;
+#pragma unroll
+  for (int n2 = 0; n2 < P; ++n2) {
+    C2 t[M];
+#pragma unroll
+    for (int n1 = 0; n1 < M; ++n1) t[n1] = v[P * n1 + n2];
+    dft_any<C2, M, INV>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < M; ++k1) v[P * k1 + n2] = t[k1];
+  }
+#pragma unroll
+  for (int k1 = 1; k1 < M; ++k1)
+#pragma unroll
+    for (int n2 = 1; n2 < P; ++n2) v[P * k1 + n2] = cmul(v[P * k1 + n2], root_n<C2, N, INV>(n2 * k1));
+  C2 out[N];
+#pragma unroll
+  for (int k1 = 0; k1 < M; ++k1) {
+    C2 t[P];
+#pragma unroll
+    for (int n2 = 0; n2 < P; ++n2) t[n2] = v[P * k1 + n2];
+    dft_reg<C2, P, INV>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) out[k1 + M * k2] = t[k2];
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = out[i];
+}
+
+template <typename C2, int R, bool INV>
+__host__ __device__ __forceinline__ void dft_any(C2 (&v)[R]) {
+  if constexpr ((R & (R - 1)) == 0) dft_reg<C2, R, INV>(v);
+  else if constexpr (R == 3) dft3<C2, INV>(v);
+  else if constexpr (R == 5) dft5<C2, INV>(v);
+  else if constexpr (R % 3 == 0) dft_mixed<C2, 3, R / 3, INV>(v);
+  else dft_mixed<C2, 5, R / 5, INV>(v);
 }
 
 // e^{-+2 pi i m / L} from the two tables (m < L)
@@ -101,43 +227,57 @@ __device__ __forceinline__ C2 tw_at(const C2* hi, const C2* lo, int m, bool inv)
   return w;
 }
 
-// Builds the twiddle tables for length L from twG (e^{-2 pi i m / Lmax}, m < Lmax).
+// Global twiddle tables e^{-2 pi i j / len} for lengths 2^A, 3 2^A3 and 5 2^A5; a length
+// m 2^a reads the table of its odd factor m with stride len / L.
 template <typename C2>
-__device__ void fft_tables(C2* hi, C2* lo, int logL, const C2* __restrict__ twG, int64_t Lmax) {
-  const int L = 1 << logL;
-  const int64_t step = Lmax >> logL;
-  for (int i = threadIdx.x; i < kTwLo; i += blockDim.x) lo[i] = twG[(int64_t)(i & (L - 1)) * step];
-  for (int i = threadIdx.x; i * kTwLo < L; i += blockDim.x) hi[i] = twG[(int64_t)i * kTwLo * step];
+struct TwSrc {
+  const C2* t[3];
+  int64_t len[3];
+};
+
+__device__ __forceinline__ int odd_slot(int L) {
+  const int m = L >> (__ffs(L) - 1);
+  return m == 1 ? 0 : (m == 3 ? 1 : 2);
+}
+
+// Fills the hi / lo tables for length L (one block, all threads).
+template <typename C2>
+__device__ void fft_tables(C2* hi, C2* lo, int L, const TwSrc<C2>& src) {
+  const int q = odd_slot(L);
+  const C2* __restrict__ tw = src.t[q];
+  const int64_t step = src.len[q] / L;
+  for (int i = threadIdx.x; i < kTwLo; i += blockDim.x) lo[i] = tw[(int64_t)(i % L) * step];
+  for (int i = threadIdx.x; i * kTwLo < L; i += blockDim.x) hi[i] = tw[(int64_t)i * kTwLo * step];
 }
 
 template <typename C2, int R, bool INV>
 __device__ __forceinline__ void stockham_pass(C2* buf, int L, int Ns, const C2* hi, const C2* lo) {
   constexpr int E = fft_per_thread<C2>();
-  constexpr int J = E / R;
-  const int nthr = L / E;
+  constexpr int J = E / R > 0 ? E / R : 1;   // butterflies per thread at most
+  const int nthr = blockDim.x;
   const int t = threadIdx.x;
-  const int LR = L / R;
-  const int tstride = L / (Ns * R);   // twiddle index scale: w^(r k) = e^{-2 pi i r k tstride / L}
+  const int B = L / R;                       // butterflies of the pass
+  const int tstride = L / (Ns * R);          // twiddle index scale: w^(r k) = e^{-2 pi i r k tstride / L}
   C2 v[J][R];
-  if (t < nthr) {
 #pragma unroll
-    for (int q = 0; q < J; ++q) {
-      const int j = t + q * nthr;
+  for (int q = 0; q < J; ++q) {
+    const int j = t + q * nthr;
+    if (j < B) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = buf[fpad(j + r * LR)];
+      for (int r = 0; r < R; ++r) v[q][r] = buf[fpad(j + r * B)];
     }
   }
   __syncthreads();
-  if (t < nthr) {
 #pragma unroll
-    for (int q = 0; q < J; ++q) {
-      const int j = t + q * nthr;
+  for (int q = 0; q < J; ++q) {
+    const int j = t + q * nthr;
+    if (j < B) {
       const int k = j & (Ns - 1);
       if (Ns > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], tw_at(hi, lo, r * k * tstride, INV));
       }
-      dft_reg<C2, R, INV>(v[q]);
+      dft_any<C2, R, INV>(v[q]);
       const int base = (j - k) * R + k;   // (j div Ns) Ns R + k
 #pragma unroll
       for (int r = 0; r < R; ++r) buf[fpad(base + r * Ns)] = v[q][r];
@@ -146,26 +286,54 @@ __device__ __forceinline__ void stockham_pass(C2* buf, int L, int Ns, const C2* 
   __syncthreads();
 }
 
-// Full transform of one row of length L = 2^logL (5 <= logL) in buf (padded layout).
+// a pass of radix 2^b (1 <= b < log2 E)
+template <typename C2, bool INV>
+__device__ __forceinline__ void pow2_pass(C2* buf, int L, int Ns, int b, const C2* hi, const C2* lo) {
+  switch (b) {
+    case 1: stockham_pass<C2, 2, INV>(buf, L, Ns, hi, lo); break;
+    case 2: stockham_pass<C2, 4, INV>(buf, L, Ns, hi, lo); break;
+    case 3: stockham_pass<C2, 8, INV>(buf, L, Ns, hi, lo); break;
+    case 4: if constexpr (fft_per_thread<C2>() > 16) stockham_pass<C2, 16, INV>(buf, L, Ns, hi, lo); break;
+    default: break;
+  }
+}
+
+// Full transform of one row of length L = m 2^a (m in {1, 3, 5}, L >= 32) in buf (padded layout).
 // (inlined: the caller must leave it about 100 registers)
 template <typename C2, bool INV>
-__device__ __forceinline__ void fft_row(C2* buf, int logL, const C2* hi, const C2* lo) {
+__device__ __forceinline__ void fft_row(C2* buf, int L, const C2* hi, const C2* lo) {
   constexpr int E = fft_per_thread<C2>();
   constexpr int LE = E == 32 ? 5 : 4;
-  const int L = 1 << logL;
-  int Ns = 1, rem = logL;
+  const int a = __ffs(L) - 1;
+  const int m = L >> a;
+  int Ns = 1, rem = a;
   while (rem >= LE) {
     stockham_pass<C2, E, INV>(buf, L, Ns, hi, lo);
     Ns <<= LE;
     rem -= LE;
   }
-  switch (rem) {
-    case 1: stockham_pass<C2, 2, INV>(buf, L, Ns, hi, lo); break;
-    case 2: stockham_pass<C2, 4, INV>(buf, L, Ns, hi, lo); break;
-    case 3: stockham_pass<C2, 8, INV>(buf, L, Ns, hi, lo); break;
-    case 4: stockham_pass<C2, 16, INV>(buf, L, Ns, hi, lo); break;
-    default: break;
+  if (m == 1) {
+    pow2_pass<C2, INV>(buf, L, Ns, rem, hi, lo);
+    return;
   }
+  const int mp = m << rem;
+  if (mp <= E) {
+    switch (mp) {
+      case 3: stockham_pass<C2, 3, INV>(buf, L, Ns, hi, lo); break;
+      case 5: stockham_pass<C2, 5, INV>(buf, L, Ns, hi, lo); break;
+      case 6: stockham_pass<C2, 6, INV>(buf, L, Ns, hi, lo); break;
+      case 10: stockham_pass<C2, 10, INV>(buf, L, Ns, hi, lo); break;
+      case 12: stockham_pass<C2, 12, INV>(buf, L, Ns, hi, lo); break;
+      case 20: if constexpr (E >= 20) stockham_pass<C2, 20, INV>(buf, L, Ns, hi, lo); break;
+      case 24: if constexpr (E >= 24) stockham_pass<C2, 24, INV>(buf, L, Ns, hi, lo); break;
+      default: break;
+    }
+    return;
+  }
+  pow2_pass<C2, INV>(buf, L, Ns, rem, hi, lo);
+  Ns <<= rem;
+  if (m == 3) stockham_pass<C2, 3, INV>(buf, L, Ns, hi, lo);
+  else stockham_pass<C2, 5, INV>(buf, L, Ns, hi, lo);
 }
 
 }  // namespace sfft

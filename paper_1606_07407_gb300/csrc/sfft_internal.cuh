@@ -21,13 +21,13 @@ template <typename T> using c2 = typename V2<T>::t;
 __host__ __device__ inline float2 mk2(float a, float b) { return make_float2(a, b); }
 __host__ __device__ inline double2 mk2(double a, double b) { return make_double2(a, b); }
 
-template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk2(a.x + b.x, a.y + b.y); }
-template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk2(a.x - b.x, a.y - b.y); }
-template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mk2(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mk2(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
   return mk2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-template <typename C> __device__ __forceinline__ C cconj(C a) { return mk2(a.x, -a.y); }
-template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s) {
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return mk2(a.x, -a.y); }
+template <typename C, typename S> __host__ __device__ __forceinline__ C cscale(C a, S s) {
   return mk2(a.x * s, a.y * s);
 }
 

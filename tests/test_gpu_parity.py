@@ -85,8 +85,9 @@ def test_samples_sampled_at_large_size(sfft):
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("p", [2, 5, 83, 911, 2039, 4099, 5003, 8191, 8209, 50021])
 def test_dft_matches_definition(sfft, prec, p):
-    # one-block Bluestein up to L = 16384 in float (p = 8191) and L = 8192 in double (p = 4099);
-    # p = 8209 and 50021 take the four-step passes.
+    # one-block Bluestein up to L = 16384 in float (p = 8191) and L = 10240 = 5 * 2^11 in double
+    # (p = 4099, beyond the one-block limit of 8192 there: four-step); p = 8209 and 50021 take the
+    # four-step passes.
     rows = 3
     plan = sfft.Plan(2, 1 << 16, 12000, blocks=(1, 1), precision=prec)
     st = Stream(p)
@@ -99,6 +100,49 @@ def test_dft_matches_definition(sfft, prec, p):
     for r in range(rows):
         tol = 16 * eps * math.log2(L) * np.linalg.norm(ycast[r])
         assert np.max(np.abs(Yg[r] - ref[r])) < tol
+
+
+def _primes_upto(n):
+    s = np.ones(n + 1, dtype=bool)
+    s[:2] = False
+    for q in range(2, int(n ** 0.5) + 1):
+        if s[q]:
+            s[q * q::q] = False
+    return np.nonzero(s)[0]
+
+
+def _length_classes(lmax):
+    # the convolution lengths m 2^a (m = 1, 3, 5; 32 <= L <= lmax) and, for each, the largest
+    # prime p whose 2p - 1 falls between it and the next smaller length: that p uses it
+    Ls = sorted({m << a for m in (1, 3, 5) for a in range(0, 15) if 32 <= (m << a) <= lmax})
+    pr = _primes_upto(lmax)
+    out, prev = [], 0
+    for L in Ls:
+        cand = [int(q) for q in pr if prev < 2 * q - 1 <= L]
+        if cand:
+            out.append((L, cand[-1]))
+        prev = L
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_dft_every_bluestein_length(sfft, prec):
+    # every pass shape of the one-block FFT: powers of two, 3 2^a and 5 2^a, with the odd factor
+    # in a combined radix-(m 2^b) pass or a separate radix-m pass, in both block classes
+    lmax = 16384 if prec == "fp32" else 8192
+    plan = sfft.Plan(2, 1 << 16, 12000, blocks=(1, 1), precision=prec)
+    eps = 2.0 ** -24 if prec == "fp32" else 2.0 ** -53
+    classes = _length_classes(lmax)
+    assert len(classes) >= 25
+    for L, p in classes:
+        st = Stream(L)
+        y = (st.uniform(2 * p) - 0.5 + 1j * (st.uniform(2 * p) - 0.5)).reshape(2, p)
+        Yg = _np(plan.dft(p, torch.tensor(y)))
+        ycast = y.astype(np.complex64).astype(np.complex128) if prec == "fp32" else y
+        ref = O.dft(ycast)
+        for r in range(2):
+            tol = 16 * eps * math.log2(L) * np.linalg.norm(ycast[r])
+            assert np.max(np.abs(Yg[r] - ref[r])) < tol, (L, p)
 
 
 def test_dft_single_mode_closed_form(sfft):
