@@ -163,11 +163,13 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
         r.groups = (c.n_sets + kMaxSetGroup - 1) / kMaxSetGroup;
         r.gsize = (c.n_sets + r.groups - 1) / r.groups;
         {
-          // a tile's four warps split into mode groups when p is shorter than the tile
-          const int rowx = 32 * rows_per_warp(r.gsize);
-          r.mgroups = (sizeof(T) != 4) ? 1 : (p <= rowx ? 4 : (p <= 2 * rowx ? 2 : 1));
+          // tiles cover the half line 0 <= x < H (each x also gives p - x); a tile's warps
+          // split into mode groups when H is shorter than the tile
+          const int64_t H = p / 2 + 1;
+          const int rowx = 32 * row_pairs(r.gsize);
+          r.mgroups = (sizeof(T) != 4) ? 1 : (H <= rowx ? 8 : H <= 2 * rowx ? 4 : H <= 4 * rowx ? 2 : 1);
           const int tx = tile_x(r.gsize) / r.mgroups;
-          r.n_xt = (int)((p + tx - 1) / tx);
+          r.n_xt = (int)((H + tx - 1) / tx);
         }
         r.chunks = K > 0 ? (K + kSampleChunk - 1) / kSampleChunk : 1;
         r.any_occupied = 0;
@@ -360,7 +362,7 @@ __global__ void k_tables(int n, const SigCfg* __restrict__ cfg, const SigRun* __
 
 // Persistent sampling kernel for the signals whose set groups hold NS sets.
 template <typename T, int NS>
-__global__ void __launch_bounds__(kSampleThreads, 4) k_sample(int n, const SigCfg* __restrict__ cfg,
+__global__ void __launch_bounds__(kSampleThreads, 2) k_sample(int n, const SigCfg* __restrict__ cfg,
                                                            const SigRun* __restrict__ run, RoundCtl* ctl, Scans sc,
                                                            const int32_t* __restrict__ alpha,
                                                            const int32_t* __restrict__ gam,
@@ -1377,7 +1379,7 @@ class Engine final : public EngineBase {
       if (!(ns_mask_ & (1u << (ns - 1)))) continue;
 #define SFFT_SAMPLE(NSV)                                                                                        \
   case NSV:                                                                                                     \
-    k_sample<T, NSV><<<4 * n_sm_, kSampleThreads, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, alpha_, gam_, (C2*)Cm_, \
+    k_sample<T, NSV><<<2 * n_sm_, kSampleThreads, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, alpha_, gam_, (C2*)Cm_, \
                                                             (C2*)tab_, (C2*)part_);                             \
     break;
       switch (ns) {

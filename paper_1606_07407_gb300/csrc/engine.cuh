@@ -17,12 +17,12 @@ constexpr int kBigRowElems = 2048;    // elements of one row tile
 
 template <typename T> constexpr int single_max_L() { return sizeof(T) == 4 ? kSingleMaxLf : kSingleMaxLd; }
 
-// Rows of 32 samples per warp for a set group of ns sets: chunk and running accumulators
-// (4 rows x ns sets x 2 reals each) stay within about 80 registers.
-__host__ __device__ constexpr int rows_per_warp(int ns) {
-  return ns <= 2 ? 8 : ns == 3 ? 6 : ns == 4 ? 5 : ns == 5 ? 4 : ns == 6 ? 3 : 2;
-}
-__host__ __device__ constexpr int tile_x(int ns) { return 32 * 4 * rows_per_warp(ns); }   // 4 warps per block
+// Row pairs per warp for a set group of ns sets: 32 positions x of the half line, each with its
+// mirror p - x.  Chunk and running sums (4 reals per position and set, twice) stay within about
+// 80 registers in float, and the staged roots within 48 KiB of shared memory.
+__host__ __device__ constexpr int row_pairs(int ns) { return ns <= 2 ? 5 : ns == 3 ? 3 : ns <= 5 ? 2 : 1; }
+// positions of the half line per sampling tile
+__host__ __device__ constexpr int tile_x(int ns) { return 32 * kSampleWarps * row_pairs(ns); }
 
 // Static description of one signal slot of a batch.
 struct SigCfg {

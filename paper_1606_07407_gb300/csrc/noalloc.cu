@@ -70,7 +70,7 @@ __global__ void k_na_tables(NoAllocArgs a, const int32_t* __restrict__ w, const 
 
 // one block per (sample tile, set group); every block sums all K modes
 template <int NS>
-__global__ void __launch_bounds__(kSampleThreads, 4)
+__global__ void __launch_bounds__(kSampleThreads, 2)
 k_na_sample(NoAllocArgs a, const int32_t* __restrict__ alpha, const int32_t* __restrict__ gam,
             const float2* __restrict__ Cm, const float2* __restrict__ W, float2* __restrict__ y) {
   __shared__ SampleSmem<float, NS> sm;
@@ -133,7 +133,7 @@ extern "C" sfft_status sfft_sample_noalloc(int d, int64_t N, int64_t p, const in
   a.mod_m = ~0ull / (uint64_t)p;
   a.groups = (a.n_sets + kMaxSetGroup - 1) / kMaxSetGroup;
   a.gsize = (a.n_sets + a.groups - 1) / a.groups;
-  a.n_xt = (int)((p + tile_x(a.gsize) - 1) / tile_x(a.gsize));
+  a.n_xt = (int)((p / 2 + 1 + tile_x(a.gsize) - 1) / tile_x(a.gsize));   // tiles of the half line
   for (int l = 0; l < d; ++l) {
     int64_t v = u[l] % p;
     a.u[l] = v < 0 ? v + p : v;

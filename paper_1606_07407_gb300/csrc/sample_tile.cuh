@@ -1,9 +1,15 @@
 // One tile of the sample-and-residual computation (Alg. 2 sampling; Eq. 41), shared
 // by the batched engine and the allocation-free sampling entry point.
 //
-//   y_n[x] = sum_j C[n][j] W[(alpha_j x) mod p],  x = x0 + 32 row + lane,
-//   W[(alpha x) mod p] = W[(alpha (x0 + 32 row)) mod p] * W[(alpha lane) mod p],
+//   y_n[x] = sum_j C[n][j] W[(alpha_j x) mod p],  W[m] = e^{2 pi i m / p}.
 //
+// The points x and p - x of the line have conjugate exponentials, W[(alpha (p - x)) mod p] =
+// conj(W[(alpha x) mod p]) = conj(E).  With C = c_r + i c_i and E = e_r + i e_i, the four sums
+//   P1 = sum c_r e_r,  P2 = sum c_i e_i,  P3 = sum c_r e_i,  P4 = sum c_i e_r
+// give both samples: y[x] = (P1 - P2, P3 + P4) and y[p - x] = (P1 + P2, P4 - P3), so every term
+// of the two samples costs four fused multiply-adds instead of eight.  A tile therefore runs
+// over the positions 0 <= x < H = floor(p / 2) + 1 (x and p - x coincide only for p = 2), and
+//   E = W[(alpha (x0 + 32 row)) mod p] * W[(alpha lane) mod p],  x = x0 + 32 row + lane,
 // the first factor shared by the 32 lanes of a row, the second by the rows of a lane.
 #pragma once
 
@@ -27,95 +33,106 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // staging buffers: two in float (the next chunk is gathered during the current one), one in double
 template <typename T> constexpr int sample_stages() { return sizeof(T) == 4 ? 2 : 1; }
 
+// Staged data of one or two 32-mode chunks, overlaid at the end of a tile by the buffer that
+// adds the mode groups' sums (half of the warps' sums at a time).
 template <typename T, int NS>
 struct SampleSmem {
   static constexpr int S = sample_stages<T>();
-  c2<T> Ls[S][kSampleChunk][32];
-  c2<T> Us[S][kSampleChunk][4 * rows_per_warp(NS)];
-  c2<T> Cs[S][kSampleChunk][NS];
+  static constexpr int RP = row_pairs(NS);
+  struct Stage {
+    c2<T> Ls[S][kSampleChunk][32];
+    c2<T> Us[S][kSampleChunk][kSampleWarps * RP];
+    c2<T> Cs[S][kSampleChunk][NS];
+  };
+  static constexpr int kRedValues = (kSampleWarps / 2) * RP * NS * 4 * 32;
+  union {
+    Stage st;
+    T red[kRedValues];
+  };
   int al[S][kSampleChunk], be[S][kSampleChunk], ga[S][kSampleChunk];
   int64_t item;
 };
 
-// Sums one staged 32-mode chunk (modes grp, grp + G, ...) into the first Q rows of the totals:
-// E = U_row L_lane, then every set's coefficient times E.
-template <typename T, int NS, int RW, int Q>
+// Sums one staged 32-mode chunk (modes grp, grp + G, ...) into the first Q row pairs of the
+// totals: E = U_row L_lane, then the four products of every set's coefficient with E.
+template <typename T, int NS, int RP, int Q>
 __device__ __forceinline__ void accumulate_chunk(const SampleSmem<T, NS>& sm, int b, int grp, int G, int lane,
-                                                 int wrow, T (&tot)[RW][NS][2]) {
+                                                 int wrow, T (&tot)[RP][NS][4]) {
   using C2 = c2<T>;
-  T acc[Q][NS][2];
+  T acc[Q][NS][4];
 #pragma unroll
   for (int qq = 0; qq < Q; ++qq)
 #pragma unroll
-    for (int nn = 0; nn < NS; ++nn) acc[qq][nn][0] = acc[qq][nn][1] = (T)0;
+    for (int nn = 0; nn < NS; ++nn) acc[qq][nn][0] = acc[qq][nn][1] = acc[qq][nn][2] = acc[qq][nn][3] = (T)0;
 #pragma unroll 2
   for (int jj = grp; jj < kSampleChunk; jj += G) {
-    const C2 L = sm.Ls[b][jj][lane];
+    const C2 L = sm.st.Ls[b][jj][lane];
     C2 E[Q];
 #pragma unroll
-    for (int qq = 0; qq < Q; ++qq) E[qq] = cmul(sm.Us[b][jj][wrow * RW + qq], L);
+    for (int qq = 0; qq < Q; ++qq) E[qq] = cmul(sm.st.Us[b][jj][wrow * RP + qq], L);
 #pragma unroll
     for (int nn = 0; nn < NS; ++nn) {
-      const C2 cc = sm.Cs[b][jj][nn];
+      const C2 cc = sm.st.Cs[b][jj][nn];
 #pragma unroll
       for (int qq = 0; qq < Q; ++qq) {
-        acc[qq][nn][0] = fma(cc.x, E[qq].x, acc[qq][nn][0]);
-        acc[qq][nn][0] = fma(-cc.y, E[qq].y, acc[qq][nn][0]);
-        acc[qq][nn][1] = fma(cc.x, E[qq].y, acc[qq][nn][1]);
-        acc[qq][nn][1] = fma(cc.y, E[qq].x, acc[qq][nn][1]);
+        acc[qq][nn][0] = fma(cc.x, E[qq].x, acc[qq][nn][0]);   // P1: c_r e_r
+        acc[qq][nn][1] = fma(cc.y, E[qq].y, acc[qq][nn][1]);   // P2: c_i e_i
+        acc[qq][nn][2] = fma(cc.x, E[qq].y, acc[qq][nn][2]);   // P3: c_r e_i
+        acc[qq][nn][3] = fma(cc.y, E[qq].x, acc[qq][nn][3]);   // P4: c_i e_r
       }
     }
   }
 #pragma unroll
   for (int qq = 0; qq < Q; ++qq)
 #pragma unroll
-    for (int nn = 0; nn < NS; ++nn) {
-      tot[qq][nn][0] += acc[qq][nn][0];
-      tot[qq][nn][1] += acc[qq][nn][1];
-    }
+    for (int nn = 0; nn < NS; ++nn)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) tot[qq][nn][k] += acc[qq][nn][k];
 }
 
-// The same for 1 <= nq < RW rows (the rows of a warp that reach past p are skipped).
-template <typename T, int NS, int RW>
+// The same for 1 <= nq < RP row pairs (the rows of a warp that reach past the half line are skipped).
+template <typename T, int NS, int RP>
 __device__ __forceinline__ void accumulate_rows(const SampleSmem<T, NS>& sm, int b, int grp, int G, int lane,
-                                                int wrow, int nq, T (&tot)[RW][NS][2]) {
+                                                int wrow, int nq, T (&tot)[RP][NS][4]) {
   switch (nq) {
-    case 1: if constexpr (RW > 1) accumulate_chunk<T, NS, RW, 1>(sm, b, grp, G, lane, wrow, tot); break;
-    case 2: if constexpr (RW > 2) accumulate_chunk<T, NS, RW, 2>(sm, b, grp, G, lane, wrow, tot); break;
-    case 3: if constexpr (RW > 3) accumulate_chunk<T, NS, RW, 3>(sm, b, grp, G, lane, wrow, tot); break;
-    case 4: if constexpr (RW > 4) accumulate_chunk<T, NS, RW, 4>(sm, b, grp, G, lane, wrow, tot); break;
-    case 5: if constexpr (RW > 5) accumulate_chunk<T, NS, RW, 5>(sm, b, grp, G, lane, wrow, tot); break;
-    case 6: if constexpr (RW > 6) accumulate_chunk<T, NS, RW, 6>(sm, b, grp, G, lane, wrow, tot); break;
-    case 7: if constexpr (RW > 7) accumulate_chunk<T, NS, RW, 7>(sm, b, grp, G, lane, wrow, tot); break;
+    case 1: if constexpr (RP > 1) accumulate_chunk<T, NS, RP, 1>(sm, b, grp, G, lane, wrow, tot); break;
+    case 2: if constexpr (RP > 2) accumulate_chunk<T, NS, RP, 2>(sm, b, grp, G, lane, wrow, tot); break;
+    case 3: if constexpr (RP > 3) accumulate_chunk<T, NS, RP, 3>(sm, b, grp, G, lane, wrow, tot); break;
+    case 4: if constexpr (RP > 4) accumulate_chunk<T, NS, RP, 4>(sm, b, grp, G, lane, wrow, tot); break;
+    case 5: if constexpr (RP > 5) accumulate_chunk<T, NS, RP, 5>(sm, b, grp, G, lane, wrow, tot); break;
+    case 6: if constexpr (RP > 6) accumulate_chunk<T, NS, RP, 6>(sm, b, grp, G, lane, wrow, tot); break;
+    case 7: if constexpr (RP > 7) accumulate_chunk<T, NS, RP, 7>(sm, b, grp, G, lane, wrow, tot); break;
     default: break;
   }
 }
 
-// One tile: 32 * 4 * RW samples x the sets of one group x the modes of one split.
-// Each 32-mode chunk is summed into fresh accumulators that are then added to the
-// running totals (blocked summation), which keeps the float rounding of long mode
-// sums near that of the individual terms.
+// One tile: 32 * kSampleWarps * RP positions of the half line (each giving the samples x and
+// p - x) x the sets of one group x the modes of one split.  Each 32-mode chunk is summed into
+// fresh accumulators that are then added to the running totals (blocked summation), which
+// keeps the float rounding of long mode sums near that of the individual terms.
 template <typename T, int NS>
 __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun& r, int xt, int g, int split,
                             const int32_t* __restrict__ alpha, const int32_t* __restrict__ gam,
                             const c2<T>* __restrict__ Cm, const c2<T>* __restrict__ W, c2<T>* __restrict__ part) {
   using C2 = c2<T>;
-  constexpr int RW = rows_per_warp(NS);
-  constexpr int ROWS = 4 * RW;
+  constexpr int RP = row_pairs(NS);
+  constexpr int ROWS = kSampleWarps * RP;
   constexpr int S = sample_stages<T>();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // G mode groups of 4 / G warps: a group covers all rows of the tile and takes every G-th mode
+  // G mode groups of kSampleWarps / G warps: a group covers all rows of the tile and takes
+  // every G-th mode
   const int G = r.mgroups;
-  const int wpg = 4 / G;
+  const int wpg = kSampleWarps / G;
   const int grp = warp / wpg, wrow = warp - grp * wpg;
-  const int TX = 32 * RW * wpg;
+  const int TX = 32 * RP * wpg;
   const int p = (int)r.p;
+  const int H = p / 2 + 1;   // positions of the half line
   const float inv_p = 1.0f / (float)p;
   const int n0 = g * r.gsize;
   const int ns_valid = min(r.gsize, c.n_sets - n0);
   const int K = sampled_modes(c, r);
   const int x0 = xt * TX;
-  const int nq = min(RW, max(0, (p - (x0 + wrow * RW * 32) + 31) / 32));   // valid rows of this warp
+  const int nq = min(RP, max(0, (H - (x0 + wrow * RP * 32) + 31) / 32));   // row pairs of this warp below H
   const int j_begin = split * r.jper;
   const int j_end = min(K, j_begin + r.jper);
   const int nchunks = j_end > j_begin ? (j_end - j_begin + kSampleChunk - 1) / kSampleChunk : 0;
@@ -138,26 +155,26 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
     const int nj = min(kSampleChunk, j_end - jc);
     for (int e = tid; e < kSampleChunk * 32; e += kSampleThreads) {
       const int jj = e >> 5, ln = e & 31;
-      cp_async<sizeof(C2)>(&sm.Ls[b][jj][ln], W + mod_small((unsigned)sm.al[b][jj] * (unsigned)ln, p, inv_p));
+      cp_async<sizeof(C2)>(&sm.st.Ls[b][jj][ln], W + mod_small((unsigned)sm.al[b][jj] * (unsigned)ln, p, inv_p));
     }
     for (int e = tid; e < kSampleChunk * ROWS; e += kSampleThreads) {
       const int jj = e / ROWS, row = e - jj * ROWS;
-      cp_async<sizeof(C2)>(&sm.Us[b][jj][row],
+      cp_async<sizeof(C2)>(&sm.st.Us[b][jj][row],
                            W + mod_small((unsigned)sm.be[b][jj] + (unsigned)row * (unsigned)sm.ga[b][jj], p, inv_p));
     }
     for (int e = tid; e < kSampleChunk * NS; e += kSampleThreads) {
       const int jj = e / NS, nn = e - jj * NS;
-      if (jj < nj && nn < ns_valid) cp_async<sizeof(C2)>(&sm.Cs[b][jj][nn], Cm + (int64_t)(n0 + nn) * c.Kmax + jc + jj);
-      else sm.Cs[b][jj][nn] = zero;
+      if (jj < nj && nn < ns_valid) cp_async<sizeof(C2)>(&sm.st.Cs[b][jj][nn], Cm + (int64_t)(n0 + nn) * c.Kmax + jc + jj);
+      else sm.st.Cs[b][jj][nn] = zero;
     }
     cp_async_commit();
   };
 
-  T tot[RW][NS][2];
+  T tot[RP][NS][4];
 #pragma unroll
-  for (int q = 0; q < RW; ++q)
+  for (int q = 0; q < RP; ++q)
 #pragma unroll
-    for (int nn = 0; nn < NS; ++nn) tot[q][nn][0] = tot[q][nn][1] = (T)0;
+    for (int nn = 0; nn < NS; ++nn) tot[q][nn][0] = tot[q][nn][1] = tot[q][nn][2] = tot[q][nn][3] = (T)0;
 
   if (nchunks > 0) {
     if (tid < kSampleChunk) {
@@ -181,9 +198,8 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
       if (q + 1 < nchunks) issue_data(q + 1, b ^ 1);                     // gathers of the next chunk
       if (tid < kSampleChunk && q + 2 < nchunks) load_index(q + 2, &al_n, &ga_n);   // indices two ahead
     }
-    // rows of this warp that lie below p (warp-uniform): a tile's last warps may have fewer
-    if (nq == RW) accumulate_chunk<T, NS, RW, RW>(sm, b, grp, G, lane, wrow, tot);
-    else if (nq > 0) accumulate_rows<T, NS, RW>(sm, b, grp, G, lane, wrow, nq, tot);
+    if (nq == RP) accumulate_chunk<T, NS, RP, RP>(sm, b, grp, G, lane, wrow, tot);
+    else if (nq > 0) accumulate_rows<T, NS, RP>(sm, b, grp, G, lane, wrow, nq, tot);
     if (S == 2) {
       // stage b is free again: it takes the indices of chunk q + 2
       if (tid < kSampleChunk && q + 2 < nchunks) put_index(b, al_n, ga_n);
@@ -203,40 +219,49 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
     }
   }
   if (G > 1) {
-    // add the other mode groups' totals into group 0 through the (now free) staging memory
-    constexpr int KK = RW * NS * 2;
-    T* red = reinterpret_cast<T*>(&sm.Ls[0][0][0]);
+    // add the mode groups' sums pairwise into group 0 through the (now free) staging memory:
+    // at each step the upper half of the remaining groups hands its sums to the lower half
+    constexpr int KK = RP * NS * 4;
     __syncthreads();
-    if (grp > 0) {
+    for (int half = G / 2; half >= 1; half /= 2) {
+      if (grp >= half && grp < 2 * half) {
+        const int slot = (grp - half) * wpg + wrow;   // < kSampleWarps / 2
 #pragma unroll
-      for (int q = 0; q < RW; ++q)
-#pragma unroll
-        for (int nn = 0; nn < NS; ++nn)
-#pragma unroll
-          for (int cc = 0; cc < 2; ++cc) red[((warp - wpg) * KK + (q * NS + nn) * 2 + cc) * 32 + lane] = tot[q][nn][cc];
-    }
-    __syncthreads();
-    if (grp == 0) {
-      for (int gg = 1; gg < G; ++gg) {
-        const int w2 = wrow + gg * wpg - wpg;
-#pragma unroll
-        for (int q = 0; q < RW; ++q)
+        for (int q = 0; q < RP; ++q)
 #pragma unroll
           for (int nn = 0; nn < NS; ++nn)
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) tot[q][nn][cc] += red[(w2 * KK + (q * NS + nn) * 2 + cc) * 32 + lane];
+            for (int k = 0; k < 4; ++k) sm.red[(slot * KK + (q * NS + nn) * 4 + k) * 32 + lane] = tot[q][nn][k];
       }
+      __syncthreads();
+      if (grp < half) {
+        const int slot = grp * wpg + wrow;
+#pragma unroll
+        for (int q = 0; q < RP; ++q)
+#pragma unroll
+          for (int nn = 0; nn < NS; ++nn)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) tot[q][nn][k] += sm.red[(slot * KK + (q * NS + nn) * 4 + k) * 32 + lane];
+      }
+      __syncthreads();
     }
     if (grp > 0) return;
   }
   C2* out = part + r.part_off;
 #pragma unroll
-  for (int q = 0; q < RW; ++q) {
-    const int x = x0 + (wrow * RW + q) * 32 + lane;
-    if (x < p) {
+  for (int q = 0; q < RP; ++q) {
+    const int x = x0 + (wrow * RP + q) * 32 + lane;
+    if (x < H) {
+      const bool mirror = x >= 1 && p - x >= H;   // p - x is a distinct sample of the other half
 #pragma unroll
-      for (int nn = 0; nn < NS; ++nn)
-        if (nn < ns_valid) out[((int64_t)split * c.n_sets + n0 + nn) * p + x] = mk2(tot[q][nn][0], tot[q][nn][1]);
+      for (int nn = 0; nn < NS; ++nn) {
+        if (nn < ns_valid) {
+          C2* row = out + ((int64_t)split * c.n_sets + n0 + nn) * p;
+          const T P1 = tot[q][nn][0], P2 = tot[q][nn][1], P3 = tot[q][nn][2], P4 = tot[q][nn][3];
+          row[x] = mk2(P1 - P2, P3 + P4);
+          if (mirror) row[p - x] = mk2(P1 + P2, P4 - P3);
+        }
+      }
     }
   }
 }

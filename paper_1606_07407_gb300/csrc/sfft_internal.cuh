@@ -33,7 +33,7 @@ template <typename C, typename S> __host__ __device__ __forceinline__ C cscale(C
 
 // ---------------------------------------------------------------- limits
 constexpr int kMaxSetGroup = 8;     // sample sets accumulated per thread (register tile)
-constexpr int kSampleWarps = 4;     // warps per sampling block
+constexpr int kSampleWarps = 8;     // warps per sampling block
 constexpr int kSampleChunk = 32;    // modes staged in shared memory per step
 
 }  // namespace sfft
