@@ -20,7 +20,7 @@ template <typename T> constexpr int single_max_L() { return sizeof(T) == 4 ? kSi
 // Row pairs per warp for a set group of ns sets: 32 positions x of the half line, each with its
 // mirror p - x.  Chunk and running sums (4 reals per position and set, twice) stay within about
 // 80 registers in float, and the staged roots within 48 KiB of shared memory.
-__host__ __device__ constexpr int row_pairs(int ns) { return ns <= 2 ? 5 : ns == 3 ? 3 : ns <= 5 ? 2 : 1; }
+__host__ __device__ constexpr int row_pairs(int ns) { return ns <= 2 ? 5 : ns <= 4 ? 3 : ns <= 6 ? 2 : 1; }
 // positions of the half line per sampling tile
 __host__ __device__ constexpr int tile_x(int ns) { return 32 * kSampleWarps * row_pairs(ns); }
 

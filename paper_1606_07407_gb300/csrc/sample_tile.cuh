@@ -116,7 +116,6 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
                             const c2<T>* __restrict__ Cm, const c2<T>* __restrict__ W, c2<T>* __restrict__ part) {
   using C2 = c2<T>;
   constexpr int RP = row_pairs(NS);
-  constexpr int ROWS = kSampleWarps * RP;
   constexpr int S = sample_stages<T>();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // G mode groups of kSampleWarps / G warps: a group covers all rows of the tile and takes
@@ -125,6 +124,7 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
   const int wpg = kSampleWarps / G;
   const int grp = warp / wpg, wrow = warp - grp * wpg;
   const int TX = 32 * RP * wpg;
+  const int rows = RP * wpg;   // rows of 32 positions in the tile
   const int p = (int)r.p;
   const int H = p / 2 + 1;   // positions of the half line
   const float inv_p = 1.0f / (float)p;
@@ -157,8 +157,8 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
       const int jj = e >> 5, ln = e & 31;
       cp_async<sizeof(C2)>(&sm.st.Ls[b][jj][ln], W + mod_small((unsigned)sm.al[b][jj] * (unsigned)ln, p, inv_p));
     }
-    for (int e = tid; e < kSampleChunk * ROWS; e += kSampleThreads) {
-      const int jj = e / ROWS, row = e - jj * ROWS;
+    for (int e = tid; e < kSampleChunk * rows; e += kSampleThreads) {   // the rows a mode group covers
+      const int jj = e / rows, row = e - jj * rows;
       cp_async<sizeof(C2)>(&sm.st.Us[b][jj][row],
                            W + mod_small((unsigned)sm.be[b][jj] + (unsigned)row * (unsigned)sm.ga[b][jj], p, inv_p));
     }
