@@ -14,6 +14,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -43,6 +44,35 @@ def _peaks():
             return json.load(fh)
     except OSError:
         return {}
+
+
+# DRAM traffic per sampling launch, from the committed ncu summary of this workload, valid while
+# the sampling sources are the ones that summary was taken from
+SAMPLE_PROFILE = os.path.join(ROOT, "profiles", "k_sample_d5_N1024_k1000_batch256.md")
+SAMPLE_SOURCES = ["sample_tile.cuh", "engine_kernels.cuh", "engine.cuh", "sfft_internal.cuh"]
+
+
+def sampling_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in SAMPLE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1606_07407_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def sample_traffic(workload: str):
+    if workload != "d5_N1024_k1000":
+        return None
+    try:
+        text = open(SAMPLE_PROFILE).read()
+    except OSError:
+        return None
+    sha = re.search(r"sources_sha256:\s*([0-9a-f]{64})", text)
+    val = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not sha or not val or sha.group(1) != sampling_sources_sha256():
+        return None
+    return float(val.group(1))
 
 
 # ------------------------------------------------------------------ CPU oracle timing
@@ -361,7 +391,8 @@ def run_ours(args):
                        "unit": UNIT, "steps": args.other_steps,
                        "ms_per_step": sum(other_ms) / max(len(other_ms), 1)},
         "roofline": {"bound": "alu", "kernel": "k_sample", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
+                     "traffic": sample_traffic(args.workload),
                      "peak_basis": f"{props.multi_processor_count} SMs x {FP32_ALU_LANES_PER_SM} FP32 FMA lanes x 2 "
                                    f"x {sm_max:.0f} MHz",
                      "measured": f"CUDA events around each sampling launch, {args.profile_steps} profiled steps "
