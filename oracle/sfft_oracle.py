@@ -173,6 +173,52 @@ def dft(y: np.ndarray) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Noise of the black box: the Philox4x32-10 counter-based generator
+# --------------------------------------------------------------------------
+
+_PHILOX_M0, _PHILOX_M1 = 0xD2511F53, 0xCD9E8D57   # round multipliers
+_PHILOX_W0, _PHILOX_W1 = 0x9E3779B9, 0xBB67AE85   # key increments between rounds
+_M32 = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+    as 1, 2, 3", SC 2011), vectorised over arrays of 32-bit values.  One round multiplies c0 by
+    M0 and c2 by M1 into 64-bit products (hi, lo) and sets
+        c <- (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0));
+    the key (k0, k1) advances by the two increments between rounds."""
+    c0, c1, c2, c3 = (np.asarray(v, dtype=np.uint64) & _M32 for v in (c0, c1, c2, c3))
+    k0 = np.uint64(int(k0) & 0xFFFFFFFF)
+    k1 = np.uint64(int(k1) & 0xFFFFFFFF)
+    for rnd in range(10):
+        if rnd > 0:
+            k0 = (k0 + np.uint64(_PHILOX_W0)) & _M32
+            k1 = (k1 + np.uint64(_PHILOX_W1)) & _M32
+        p0 = c0 * np.uint64(_PHILOX_M0)   # < 2^64: exact in uint64
+        p1 = c2 * np.uint64(_PHILOX_M1)
+        hi0, lo0 = p0 >> np.uint64(32), p0 & _M32
+        hi1, lo1 = p1 >> np.uint64(32), p1 & _M32
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+    return c0, c1, c2, c3
+
+
+def black_box_noise(seed: int, round_i: int, p: int, d: int, sigma: float) -> np.ndarray:
+    """Noise added to the black box's samples of round i (complex [d + 1, p]), Re and Im each
+    N(0, sigma^2 / 2).  Sample (set n, point x) takes Philox4x32-10 of the counter
+    (x, n, i, 0) under the key (seed mod 2^32, seed div 2^32); its first two words give
+    u1 = (w0 + 1/2) / 2^32 in (0, 1) and u2 = w1 / 2^32, and the Box-Muller transform gives
+    sqrt(-2 ln u1) e^{2 pi i u2} sigma / sqrt(2)."""
+    x = np.tile(np.arange(p, dtype=np.uint64), d + 1)
+    n = np.repeat(np.arange(d + 1, dtype=np.uint64), p)
+    w0, w1, _, _ = philox4x32_10(x, n, np.full(x.shape, round_i, dtype=np.uint64), np.zeros_like(x),
+                                 seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    u1 = (w0.astype(np.float64) + 0.5) / 2.0 ** 32
+    u2 = w1.astype(np.float64) / 2.0 ** 32
+    z = np.sqrt(-2.0 * np.log(u1)) * np.exp(2j * np.pi * u2) * (sigma / math.sqrt(2.0))
+    return z.reshape(d + 1, p)
+
+
+# --------------------------------------------------------------------------
 # Bin test, frequency and coefficient read-out (Eq. 7-8, Eq. 41-42)
 # --------------------------------------------------------------------------
 

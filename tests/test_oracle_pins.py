@@ -194,6 +194,73 @@ def test_bin_domain_residual_recovers_the_same_result():
         assert all(rb["terms"] == k for rb in bins.rounds)
 
 
+# ---------------------------------------------------------------- noise of the black box
+
+def test_philox_is_a_bijection_with_full_avalanche():
+    # for one key the 128-bit output of distinct counters never repeats; flipping one counter
+    # bit flips about half of the 128 output bits (a dropped round, word or xor breaks one of these)
+    n = 1 << 17
+    c0 = np.arange(n, dtype=np.uint64)
+    c1 = (np.arange(n, dtype=np.uint64) * np.uint64(7)) & np.uint64(0xFF)
+    out = O.philox4x32_10(c0, c1, np.full(n, 5, np.uint64), np.zeros(n, np.uint64), 0x1234, 0xABCD)
+    words = np.stack(out, axis=1).astype(np.uint64)
+    assert np.unique(words, axis=0).shape[0] == n
+    base = np.stack(O.philox4x32_10(c0[:4096], c1[:4096], 5, 0, 0x1234, 0xABCD), axis=1)
+    for bit in (0, 13, 31):
+        for word in range(4):
+            cs = [c0[:4096], c1[:4096], np.full(4096, 5, np.uint64), np.zeros(4096, np.uint64)]
+            cs[word] = cs[word] ^ np.uint64(1 << bit)
+            flip = np.stack(O.philox4x32_10(*cs, 0x1234, 0xABCD), axis=1) ^ base
+            bits = sum(bin(int(v)).count("1") for v in flip.reshape(-1)) / 4096.0
+            assert abs(bits - 64.0) < 1.5
+    assert np.array_equal(np.stack(O.philox4x32_10(c0[:64], c1[:64], 5, 0, 0x1234, 0xABCD)), base[:64].T)
+
+
+def test_philox_words_are_uniform():
+    n = 1 << 16
+    out = O.philox4x32_10(np.arange(n, dtype=np.uint64), 3, 1, 0, 99, 7)
+    for w in out:
+        counts = np.bincount((w >> np.uint64(28)).astype(np.int64), minlength=16)
+        chi2 = float(np.sum((counts - n / 16.0) ** 2 / (n / 16.0)))
+        assert chi2 < 45.0          # 15 degrees of freedom: p < 2e-4 above this
+
+
+def test_noise_is_complex_gaussian_with_the_stated_variance():
+    sigma = 2e-3
+    z = O.black_box_noise(0x9E3779B97F4A7C15, 3, 20011, 4, sigma)     # 100 055 samples
+    assert z.shape == (5, 20011)
+    re, im = z.real.reshape(-1), z.imag.reshape(-1)
+    var = sigma ** 2 / 2
+    sd_mean = math.sqrt(var / re.size)
+    assert abs(re.mean()) < 5 * sd_mean and abs(im.mean()) < 5 * sd_mean
+    assert abs(re.var() / var - 1) < 0.03 and abs(im.var() / var - 1) < 0.03
+    assert abs(np.mean(re * im)) / var < 0.02                          # Re and Im independent
+    assert abs(np.mean(re ** 4) / var ** 2 - 3.0) < 0.1                # Gaussian kurtosis
+    # sets, points and rounds draw independent values
+    assert abs(np.mean(z[0] * np.conj(z[1]))) / sigma ** 2 < 0.02
+    assert abs(np.mean(z[:, 1:] * np.conj(z[:, :-1]))) / sigma ** 2 < 0.02
+    z2 = O.black_box_noise(0x9E3779B97F4A7C15, 4, 20011, 4, sigma)
+    assert abs(np.mean(z * np.conj(z2))) / sigma ** 2 < 0.02
+    assert np.array_equal(z, O.black_box_noise(0x9E3779B97F4A7C15, 3, 20011, 4, sigma))
+
+
+def test_noisy_recovery_errors_scale_like_sigma_over_root_p():
+    # sigma = 1e-3 on modes of |a| in [1, 10]: the planted set is recovered and each coefficient
+    # is off by about the noise of its bin, sigma / sqrt(p (d + 1)) for the mean over the sets
+    d, N, k, sigma = 3, 256, 120, 1e-3
+    sig = draw_signal(d, N, k, seed=41, r_lo=1.0, r_hi=10.0, noise_sigma=sigma)
+    th = O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25, sigma=sigma)
+    res = O.multi_phaseshift(sig.freqs, sig.coeffs, d, N, k, (2, 1), th=th, estimator="mean",
+                             residual="bins",
+                             noise=lambda i, p, dd: O.black_box_noise(sig.noise_seed, i, p, dd, sigma))
+    order = np.lexsort(sig.freqs.T[::-1])
+    assert res.converged and np.array_equal(res.freqs, sig.freqs[order])
+    err = np.abs(res.coeffs - sig.coeffs[order])
+    ps = [r["p"] for r in res.rounds]
+    assert np.max(err) < 8 * sigma / math.sqrt(min(ps) * (d + 1))
+    assert np.sqrt(np.mean(err ** 2)) > 0.2 * sigma / math.sqrt(max(ps) * (d + 1))   # the noise is there
+
+
 # ---------------------------------------------------------------- bin test and decode
 
 def _check_collision_rejected(classify_fn):
@@ -400,3 +467,26 @@ def test_planted_mistakes_are_caught(monkeypatch):
     for bad in (bins_no_p, bins_conj_phase, bins_wrong_bin):
         with pytest.raises(AssertionError):
             _check_registry_bins(bad)
+
+    real_philox = O.philox4x32_10
+
+    def philox_2_rounds(c0, c1, c2, c3, k0, k1):       # two rounds, no key schedule: weak mixing
+        c0, c1, c2, c3 = (np.asarray(v, dtype=np.uint64) & np.uint64(0xFFFFFFFF) for v in (c0, c1, c2, c3))
+        out = (c0, c1, c2, c3)
+        k0, k1 = np.uint64(k0), np.uint64(k1)
+        for rnd in range(2):
+            p0, p1 = out[0] * np.uint64(0xD2511F53), out[2] * np.uint64(0xCD9E8D57)
+            out = ((p1 >> np.uint64(32)) ^ out[1] ^ k0, p1 & np.uint64(0xFFFFFFFF),
+                   (p0 >> np.uint64(32)) ^ out[3] ^ k1, p0 & np.uint64(0xFFFFFFFF))
+        return out
+
+    monkeypatch.setattr(O, "philox4x32_10", philox_2_rounds)
+    with pytest.raises(AssertionError):
+        test_philox_is_a_bijection_with_full_avalanche()
+    monkeypatch.setattr(O, "philox4x32_10", real_philox)
+
+    real_noise = O.black_box_noise
+    monkeypatch.setattr(O, "black_box_noise", lambda seed, i, p, d, sigma: real_noise(seed, i, p, d, sigma * 2 ** 0.5))
+    with pytest.raises(AssertionError):                 # sigma per component instead of sigma / sqrt 2
+        test_noise_is_complex_gaussian_with_the_stated_variance()
+    monkeypatch.setattr(O, "black_box_noise", real_noise)
