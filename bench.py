@@ -84,12 +84,16 @@ def oracle_throughput(workload: str, min_seconds: float, max_recoveries: int, se
     Returns (modes/s, recoveries, seconds, exact)."""
     import oracle.sfft_oracle as O
     wl = WORKLOADS[workload]
-    th = O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
+    th = O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25, sigma=wl.noise_sigma)
     n, modes, t_total, exact = 0, 0, 0.0, True
     while n < max_recoveries and (t_total < min_seconds or n == 0):
         sig = wl.signal(seed_offset=seed_base + n)
         t0 = time.perf_counter()
-        res = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, wl.blocks, th=th, residual=residual)
+        noise = None
+        if wl.noise_sigma > 0:
+            noise = lambda i, p, d, s=sig: O.black_box_noise(s.noise_seed, i, p, d, wl.noise_sigma)  # noqa: E731
+        res = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, wl.blocks, th=th, residual=residual,
+                                 noise=noise, p_min=wl.p_min)
         t_total += time.perf_counter() - t0
         planted = sig.freqs[np.lexsort(sig.freqs.T[::-1])].astype(np.int64)
         exact = exact and res.converged and np.array_equal(res.freqs, planted)
@@ -248,11 +252,11 @@ def run_ours(args):
     # inputs resident in HBM before timing: distinct signals per rank and batch slot
     from paper_1606_07407_gb300 import dist as D
     sigs = [wl.signal(seed_offset=o) for o in D.rank_seed_offsets(rank, nb)]
-    dev = [sfft.Signal(s.freqs, s.coeffs, s.N) for s in sigs]
+    dev = [sfft.Signal(s.freqs, s.coeffs, s.N, noise_sigma=s.noise_sigma, noise_seed=s.noise_seed) for s in sigs]
     planted = [s.freqs[np.lexsort(s.freqs.T[::-1])].astype(np.int64) for s in sigs]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     plan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, precision=args.precision, graph=True, stream=stream,
-                     residual=args.residual)
+                     residual=args.residual, noise_sigma=wl.noise_sigma, p_min=wl.p_min)
     batch = sfft.Batch([plan] * nb, graph=True, stream=stream)
     bout = batch.outputs(caps=[wl.k + 16] * nb)   # room for the recovered set (overflow: CAPACITY)
     allow = (0, 2, 3, 5)
@@ -322,7 +326,7 @@ def run_ours(args):
     # profiled pass (same batch, rounds enqueued from the host with CUDA events around each
     # kernel class on the launch stream): kernel shares and the sampling kernel's roofline
     pplan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, precision=args.precision, profile=True, stream=stream,
-                      residual=args.residual)
+                      residual=args.residual, noise_sigma=wl.noise_sigma, p_min=wl.p_min)
     pbatch = sfft.Batch([pplan] * nb, graph=False, stream=stream)
     pout = pbatch.outputs(caps=[wl.k + 16] * nb)
     pbatch.execute(dev, out=pout, allow=allow)

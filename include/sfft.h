@@ -60,11 +60,17 @@ typedef struct sfft_signal_s* sfft_signal;
 typedef struct sfft_batch_s* sfft_batch;
 
 /* Prime schedule (Alg. 1 and Alg. 2: p = i-th prime >= c k*, c = 5 in Sec. 5).
- * primes != NULL overrides the rule: round i uses primes[(i-1) mod n_primes]. */
+ * primes != NULL overrides the rule: round i uses primes[(i-1) mod n_primes].
+ * p_min > 0 floors the rule: round i uses the i-th prime >= max(c k*, p_min).
+ * With noisy samples the phase read-out w_n = N Arg(Y_n / Y_0) / (2 pi) of a
+ * mode a varies by about N sigma / (2 pi sqrt(p) |a|), so reading modes down
+ * to |a| reliably needs p of order (4 N sigma / (2 pi delta |a|))^2, which the
+ * noiseless rule c k* does not give once k* is small. */
 typedef struct {
   int c_prime;            /* c; 0 means 5 */
   int n_primes;
   const int64_t* primes;  /* host, n_primes entries, each prime and >= 5 */
+  int64_t p_min;          /* 0: no floor */
 } sfft_pschedule;
 
 /* Line directions (Sec. 3.2, 3.3, 4.1).  Either n_dirs explicit integer
@@ -140,7 +146,13 @@ void sfft_plan_destroy(sfft_plan plan);
 /* A synthetic black box f(t) = sum_j coeffs_j exp(2 pi i freqs_j . t) with k
  * modes.  freqs_dev: int32 [k x d] device; coeffs_dev: complex128 [k] device.
  * Both are copied; the handle owns its copy until sfft_signal_destroy.
- * noise_sigma > 0 is reserved (INVALID_ARG for now). */
+ * noise_sigma >= 0: every sample the method takes carries complex Gaussian
+ * noise, Re and Im each N(0, sigma^2 / 2).  Sample (set n, point x) of round i
+ * draws Philox4x32-10 (Salmon et al., SC 2011) of the counter (x, n, i, 0)
+ * under the key (noise_seed mod 2^32, noise_seed div 2^32), and its first two
+ * words w0, w1 give sqrt(-2 ln((w0 + 1/2) / 2^32)) e^{2 pi i w1 / 2^32}
+ * sigma / sqrt(2) (Box-Muller).  The plan's opts.noise_sigma is the level the
+ * thresholds assume.  INVALID_ARG for a negative or non-finite noise_sigma. */
 sfft_status sfft_signal_synthetic(int d, int64_t N, int64_t k, const int32_t* freqs_dev,
                                   const double* coeffs_dev, double noise_sigma,
                                   uint64_t noise_seed, sfft_signal* signal_out);

@@ -294,14 +294,15 @@ class Result:
 def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int = 5,
                      th: Thresholds | None = None, max_rounds: int | None = None,
                      box_lo: int = 0, primes=None, dirs=None, noise=None,
-                     estimator: str = "set0", residual: str = "samples") -> Result:
+                     estimator: str = "set0", residual: str = "samples", p_min: int = 0) -> Result:
     """Algorithm 2 (MultiPhaseshift) on the black box f = sum_j coeffs_j e^{2 pi i freqs_j . t}.
 
     ``primes``, if given, overrides the prime rule (round i uses primes[(i-1) mod len]).
     ``noise``, if given, is a callable (i, p, d) -> complex array [d+1, p] added to the
     black-box samples of round i.  ``residual`` says where g (built from the registry) leaves
     f: "samples" evaluates f - g at every sample point, as Alg. 2 writes it; "bins" samples f
-    alone and subtracts the transform of g bin by bin (registry_bins)."""
+    alone and subtracts the transform of g bin by bin (registry_bins).  ``p_min`` floors the
+    prime rule: round i uses the i-th prime >= max(c k*, p_min)."""
     if residual not in ("samples", "bins"):
         raise ValueError(residual)
     th = th or Thresholds()
@@ -318,7 +319,7 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
     for i in range(1, max_rounds + 1):
         k_star = max(k - len(R), 1)
         p = (int(primes[(i - 1) % len(primes)]) if primes is not None
-             else ith_prime_at_least(i, c * k_star))
+             else ith_prime_at_least(i, max(c * k_star, p_min)))
         u = line_direction(d, N, blocks, i, dirs)
         # f - g: black-box modes with +a, registry modes with -a (Alg. 2: g is built from R)
         if R and residual == "samples":

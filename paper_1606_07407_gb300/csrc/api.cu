@@ -79,6 +79,8 @@ struct sfft_signal_s {
   int64_t N = 0;
   int64_t k = 0;
   int64_t k_cap = 0;
+  double noise_sigma = 0.0;    // complex Gaussian noise of every sample (E|z|^2 = sigma^2)
+  uint64_t noise_seed = 0;
   int32_t* w = nullptr;   // device [k x d]
   double2* a = nullptr;   // device [k]
 };
@@ -133,7 +135,6 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
   if (o.tau < 0 || o.rho < 0 || o.delta < 0 || o.delta >= 0.5 || o.noise_sigma < 0 || o.max_rounds < 0)
     return SFFT_ERR_INVALID_ARG;
   if (o.residual != SFFT_RESIDUAL_BINS && o.residual != SFFT_RESIDUAL_SAMPLES) return SFFT_ERR_INVALID_ARG;
-  if (o.noise_sigma != 0.0) return SFFT_ERR_INVALID_ARG;   // noisy black boxes: not yet supported
 
   std::unique_ptr<sfft_plan_s> P(new sfft_plan_s());
   SlotDesc& D = P->desc;
@@ -163,8 +164,9 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
 
   // ---- prime schedule
   if (ps) {
-    if (ps->c_prime < 0 || ps->n_primes < 0) return SFFT_ERR_INVALID_ARG;
+    if (ps->c_prime < 0 || ps->n_primes < 0 || ps->p_min < 0 || ps->p_min > (1LL << 26)) return SFFT_ERR_INVALID_ARG;
     if (ps->c_prime > 0) D.c = ps->c_prime;
+    D.p_min = ps->p_min;
     if (ps->n_primes > 0) {
       if (!ps->primes) return SFFT_ERR_INVALID_ARG;
       for (int i = 0; i < ps->n_primes; ++i) {
@@ -177,7 +179,7 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
     }
   }
   if (D.primes.empty()) {
-    const int64_t lo = (int64_t)D.c * std::max<int64_t>(k, 1);
+    const int64_t lo = std::max<int64_t>((int64_t)D.c * std::max<int64_t>(k, 1), D.p_min);
     int64_t lim = lo + 64LL * D.max_rounds + 1000;
     for (;;) {
       std::vector<int64_t> pr = primes_up_to(lim);
@@ -257,12 +259,13 @@ int64_t sfft_plan_device_bytes(sfft_plan plan) { return plan ? (int64_t)plan->en
 
 sfft_status sfft_signal_synthetic(int d, int64_t N, int64_t k, const int32_t* freqs_dev, const double* coeffs_dev,
                                   double noise_sigma, uint64_t noise_seed, sfft_signal* signal_out) {
-  (void)noise_seed;
   if (!signal_out) return SFFT_ERR_INVALID_ARG;
   *signal_out = nullptr;
   if (d < 1 || N < 2 || k < 0 || (k > 0 && (!freqs_dev || !coeffs_dev))) return SFFT_ERR_INVALID_ARG;
-  if (noise_sigma != 0.0) return SFFT_ERR_INVALID_ARG;
+  if (!(noise_sigma >= 0.0) || !std::isfinite(noise_sigma)) return SFFT_ERR_INVALID_ARG;
   std::unique_ptr<sfft_signal_s> S(new sfft_signal_s());
+  S->noise_sigma = noise_sigma;
+  S->noise_seed = noise_seed;
   S->d = d;
   S->N = N;
   S->k = k;
@@ -350,9 +353,11 @@ sfft_status sfft_execute(sfft_plan plan, sfft_signal signal, int64_t capacity, i
   const double2* a[1] = {signal->a};
   int64_t ks[1] = {signal->k};
   int64_t caps[1] = {capacity};
+  const double ns[1] = {signal->noise_sigma};
+  const uint64_t nseed[1] = {signal->noise_seed};
   int st = 0;
   sfft_status cs = cuda_status(
-      plan->eng->run(w, a, ks, caps, freqs_out_dev, (double2*)coeffs_out_dev, n_found, &st, stats));
+      plan->eng->run(w, a, ks, caps, ns, nseed, freqs_out_dev, (double2*)coeffs_out_dev, n_found, &st, stats));
   if (cs != SFFT_OK) return cs;
   return (sfft_status)st;
 }
@@ -397,6 +402,8 @@ sfft_status sfft_batch_execute(sfft_batch batch, const sfft_signal* signals, con
   std::vector<const int32_t*> w(n);
   std::vector<const double2*> a(n);
   std::vector<int64_t> ks(n);
+  std::vector<double> nsig(n);
+  std::vector<uint64_t> nseed(n);
   int64_t total_cap = 0;
   for (int s = 0; s < n; ++s) {
     const sfft_signal_s* S = signals[s];
@@ -405,11 +412,14 @@ sfft_status sfft_batch_execute(sfft_batch batch, const sfft_signal* signals, con
     w[s] = S->w;
     a[s] = S->a;
     ks[s] = S->k;
+    nsig[s] = S->noise_sigma;
+    nseed[s] = S->noise_seed;
     total_cap += capacities[s];
   }
   if (total_cap > 0 && (!freqs_out_dev || !coeffs_out_dev)) return SFFT_ERR_INVALID_ARG;
   std::vector<int> st(n, 0);
-  sfft_status cs = cuda_status(batch->eng->run(w.data(), a.data(), ks.data(), capacities, freqs_out_dev,
+  sfft_status cs = cuda_status(batch->eng->run(w.data(), a.data(), ks.data(), capacities, nsig.data(), nseed.data(),
+                                               freqs_out_dev,
                                                (double2*)coeffs_out_dev, n_found, st.data(), stats));
   if (cs != SFFT_OK) return cs;
   int worst = SFFT_OK;

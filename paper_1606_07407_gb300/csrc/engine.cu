@@ -21,22 +21,32 @@
 #include "engine_kernels.cuh"
 #include "fft_reg.cuh"
 #include "fft_smem.cuh"
+#include "noise.cuh"
 #include "sample_tile.cuh"
 
 namespace sfft {
 
 namespace {
 
-constexpr int kBindArrays = 6;   // per-signal arrays staged by bind()
+constexpr int kBindArrays = 8;   // per-signal arrays staged by bind()
+
+inline unsigned long long double_bits(double v) {
+  unsigned long long u;
+  std::memcpy(&u, &v, sizeof(u));
+  return u;
+}
 
 // ------------------------------------------------------------------ init / bind
 
-__global__ void k_init(int n, SigRun* run, const int64_t* __restrict__ k_sig) {
+// bindv: the staged per-signal arrays (k at [2n, 3n), noise sigma bits at [6n, 7n), seed at [7n, 8n))
+__global__ void k_init(int n, SigRun* run, const int64_t* __restrict__ bindv) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     SigRun r;
     memset(&r, 0, sizeof(r));
     r.active = 1;
-    r.k_sig = (int)k_sig[s];
+    r.k_sig = (int)bindv[2 * n + s];
+    r.noise_sigma = __longlong_as_double((long long)bindv[6 * n + s]);
+    r.noise_seed = (unsigned long long)bindv[7 * n + s];
     run[s] = r;
   }
 }
@@ -137,7 +147,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
         p = plist[c.primes_off + (i - 1) % c.n_primes];
       } else {
         const int64_t kstar = max((int64_t)c.k - r.n_live, (int64_t)1);
-        const int64_t lo = max((int64_t)c.c * kstar, (int64_t)2);
+        const int64_t lo = max(max((int64_t)c.c * kstar, c.p_min), (int64_t)2);
         // pfirst[v] = index of the smallest prime >= v, so the i-th prime >= lo is one lookup away
         const int64_t idx = lo < pfirst_n ? (int64_t)pfirst[lo] + i - 1 : (int64_t)n_ptab;
         p = idx < n_ptab ? ptab[idx] : -1;
@@ -479,7 +489,11 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
 #pragma unroll 8
   for (int x = threadIdx.x; x < L; x += blockDim.x) {
     C2 v = mk2((T)0, (T)0);
-    if (x < p) v = cmul(chirp[x], sum_splits<T>(part, r, c.n_sets, row, x));
+    if (x < p) {
+      C2 y = sum_splits<T>(part, r, c.n_sets, row, x);
+      if (r.noise_sigma > 0.0) y = cadd(y, black_box_noise<T>(r.noise_seed, r.round, row, x, r.noise_sigma));
+      v = cmul(chirp[x], y);
+    }
     buf[fpad(x)] = v;
   }
   __syncthreads();
@@ -536,7 +550,11 @@ __global__ void k_bigA(int n, const SigCfg* __restrict__ cfg, const SigRun* __re
       C2 v;
       if (row < c.n_sets) {
         v = mk2((T)0, (T)0);
-        if (x < r.p) v = cmul(chirp[x], sum_splits<T>(part, r, c.n_sets, row, x));
+        if (x < r.p) {
+          C2 y = sum_splits<T>(part, r, c.n_sets, row, x);
+          if (r.noise_sigma > 0.0) y = cadd(y, black_box_noise<T>(r.noise_seed, r.round, row, x, r.noise_sigma));
+          v = cmul(chirp[x], y);
+        }
       } else {
         v = filter_value<T>(x, r.p, L, chirp);
       }
@@ -1182,6 +1200,7 @@ class Engine final : public EngineBase {
       c.peel_bins = d.peel_bins;
       c.N = d.N;
       c.p_max = d.p_max;
+      c.p_min = d.p_min;
       c.tau = d.tau;
       c.rho = d.rho;
       c.delta = d.delta;
@@ -1453,7 +1472,7 @@ class Engine final : public EngineBase {
   }
 
   cudaError_t bind(const int32_t* const* sig_w, const double2* const* sig_a, const int64_t* k_sig,
-                   const int64_t* caps) {
+                   const int64_t* caps, const double* noise_sigma = nullptr, const uint64_t* noise_seed = nullptr) {
     // pinned staging: sig_w pointers, sig_a pointers, k_sig, capacities, output row offsets,
     // output element offsets (rows of d_s ints)
     int64_t* h = reinterpret_cast<int64_t*>(host_stage_);
@@ -1466,6 +1485,8 @@ class Engine final : public EngineBase {
       h[3 * n_ + s] = cap;
       h[4 * n_ + s] = rows;
       h[5 * n_ + s] = elems;
+      h[6 * n_ + s] = noise_sigma ? (int64_t)double_bits(noise_sigma[s]) : 0;
+      h[7 * n_ + s] = noise_seed ? (int64_t)noise_seed[s] : 0;
       rows += cap;
       elems += cap * cfg_host_[s].d;
     }
@@ -1473,7 +1494,7 @@ class Engine final : public EngineBase {
     sig_w_ = reinterpret_cast<const int32_t* const*>(bind_);
     sig_a_ = reinterpret_cast<const double2* const*>(reinterpret_cast<int64_t*>(bind_) + n_);
     ksig_dev_ = reinterpret_cast<int64_t*>(bind_) + 2 * n_;
-    k_init<<<(n_ + 255) / 256, 256, 0, st_>>>(n_, run_, ksig_dev_);
+    k_init<<<(n_ + 255) / 256, 256, 0, st_>>>(n_, run_, reinterpret_cast<const int64_t*>(bind_));
     ECHK(cudaGetLastError());
     ECHK(cudaMemsetAsync(hash_, 0xFF, (size_t)hash_total_ * sizeof(int32_t), st_));
     ECHK(cudaMemsetAsync(ctl_, 0, sizeof(RoundCtl), st_));
@@ -1541,10 +1562,11 @@ class Engine final : public EngineBase {
 
   // ---------------------------------------------------------------- execute
   cudaError_t run(const int32_t* const* sig_w, const double2* const* sig_a, const int64_t* k_sig, const int64_t* caps,
-                  int32_t* out_w, double2* out_a, int64_t* n_found, int* status, sfft_stats* stats) override {
+                  const double* noise_sigma, const uint64_t* noise_seed, int32_t* out_w, double2* out_a,
+                  int64_t* n_found, int* status, sfft_stats* stats) override {
     int64_t launches[SFFT_NKCLASS] = {0, 0, 0, 0, 0, 0};
     const int hard = hard_rounds();
-    ECHK(bind(sig_w, sig_a, k_sig, caps));
+    ECHK(bind(sig_w, sig_a, k_sig, caps, noise_sigma, noise_seed));
     launches[5] += 2;
     int rounds_enqueued = 0;
     const bool record = profile_ && stats != nullptr;

@@ -32,6 +32,7 @@ struct SigCfg {
   int peel_bins;      // the registry leaves the transform bin by bin (else it is sampled with f)
   int reg_cap, hash_mask, logL_max;
   int64_t N, p_max;
+  int64_t p_min;      // floor of the prime rule: the i-th prime >= max(c k*, p_min)
   double tau, rho, delta, sigma;
   int64_t dirs_off, primes_off;  // into the direction / prime-list arrays
   int64_t tw_off;     // T2 [k * d]        unit twiddles e^{2 pi i w_n / N} of the signal's modes
@@ -68,6 +69,8 @@ struct SigRun {
   unsigned long long maxy0_bits;
   double a_ref;
   double eta_prune;   // the round's prune level: max(rho A_ref, 6 sigma / sqrt(p))
+  double noise_sigma;              // noise of the bound black box (0: none)
+  unsigned long long noise_seed;
   int64_t samples, terms;
   int64_t n_out;
 };
@@ -118,6 +121,7 @@ struct SlotDesc {
   std::vector<int64_t> dirs;     // n_dirs x d
   int n_dirs;
   std::vector<int64_t> primes;   // prime-list override (empty: rule)
+  int64_t p_min = 0;             // floor of the rule
   int64_t p_max;
 };
 
@@ -125,9 +129,10 @@ struct SlotDesc {
 class EngineBase {
  public:
   virtual ~EngineBase() {}
+  // noise_sigma / noise_seed: per-signal noise of the black boxes (null: none)
   virtual cudaError_t run(const int32_t* const* sig_w, const double2* const* sig_a, const int64_t* k_sig,
-                          const int64_t* caps, int32_t* out_w, double2* out_a, int64_t* n_found, int* status,
-                          sfft_stats* stats) = 0;
+                          const int64_t* caps, const double* noise_sigma, const uint64_t* noise_seed,
+                          int32_t* out_w, double2* out_a, int64_t* n_found, int* status, sfft_stats* stats) = 0;
   virtual cudaError_t step_sample(int64_t p, const int64_t* u, int64_t K, const int32_t* w, const double2* a,
                                   void* y_out) = 0;
   virtual cudaError_t step_dft(int64_t p, int n_rows, const void* y, void* Y_out) = 0;

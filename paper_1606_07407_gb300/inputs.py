@@ -125,6 +125,7 @@ class Workload:
     r_hi: float = 10.0
     noise_sigma: float = 0.0
     seed: int = BASE_SEED
+    p_min: int = 0          # floor of the prime schedule the workload is run with (0: none)
     extra: dict = field(default_factory=dict)
 
     def signal(self, seed_offset: int = 0) -> Signal:
@@ -139,8 +140,10 @@ class Workload:
 WORKLOADS = {
     "d2_N1024_k16": Workload("d2_N1024_k16", 2, 1024, 16, (1, 1), r_lo=1.0, r_hi=2.0, seed=BASE_SEED + 1),
     "d5_N1024_k1000": Workload("d5_N1024_k1000", 5, 1024, 1000, (3, 2), seed=BASE_SEED + 2),
+    # noisy: a prime floor keeps the read-out noise N sigma / (2 pi sqrt(p) |a|) of |a| = 1 modes
+    # four standard deviations inside delta = 0.25
     "d10_N65536_k10000_noisy": Workload("d10_N65536_k10000_noisy", 10, 1 << 16, 10000, (2,) * 5,
-                                        noise_sigma=1e-3, seed=BASE_SEED + 3),
+                                        noise_sigma=1e-3, seed=BASE_SEED + 3, p_min=30000),
     "d20_N1048576_k100000": Workload("d20_N1048576_k100000", 20, 1 << 20, 100000, (2,) * 10,
                                      r_dist="loguniform", r_lo=1e-2, r_hi=1e2, seed=BASE_SEED + 5),
 }

@@ -30,7 +30,8 @@ class SfftError(RuntimeError):
 
 
 class _PSchedule(C.Structure):
-    _fields_ = [("c_prime", C.c_int), ("n_primes", C.c_int), ("primes", C.POINTER(C.c_int64))]
+    _fields_ = [("c_prime", C.c_int), ("n_primes", C.c_int), ("primes", C.POINTER(C.c_int64)),
+                ("p_min", C.c_int64)]
 
 
 class _Tilts(C.Structure):
@@ -145,9 +146,10 @@ def _i64_array(vals):
 
 
 class Signal:
-    """Synthetic black box f(t) = sum_j coeffs_j e^{2 pi i freqs_j . t} held on the device."""
+    """Synthetic black box f(t) = sum_j coeffs_j e^{2 pi i freqs_j . t} held on the device; with
+    noise_sigma > 0 every sample carries complex Gaussian noise drawn from noise_seed."""
 
-    def __init__(self, freqs, coeffs, N: int):
+    def __init__(self, freqs, coeffs, N: int, noise_sigma: float = 0.0, noise_seed: int = 0):
         L = load()
         freqs = torch.as_tensor(np.asarray(freqs) if not torch.is_tensor(freqs) else freqs)
         coeffs = torch.as_tensor(np.asarray(coeffs) if not torch.is_tensor(coeffs) else coeffs)
@@ -156,8 +158,9 @@ class Signal:
         fw = freqs.to(device="cuda", dtype=torch.int32).contiguous()
         ca = coeffs.to(device="cuda", dtype=torch.complex128).contiguous()
         h = C.c_void_p()
-        _check(L.sfft_signal_synthetic(self.d, self.N, self.k, _ptr(fw), _ptr(ca), 0.0, 0, C.byref(h)),
-               "sfft_signal_synthetic")
+        self.noise_sigma, self.noise_seed = float(noise_sigma), int(noise_seed)
+        _check(L.sfft_signal_synthetic(self.d, self.N, self.k, _ptr(fw), _ptr(ca), self.noise_sigma,
+                                       self.noise_seed & 0xFFFFFFFFFFFFFFFF, C.byref(h)), "sfft_signal_synthetic")
         self._h = h
 
     def assign(self, freqs: torch.Tensor, coeffs: torch.Tensor):
@@ -194,7 +197,8 @@ class Plan:
     def __init__(self, d: int, N: int, k: int, blocks=None, dirs=None, primes=None, c: int = 5,
                  precision: str = "fp32", box_lo: int = 0, tau: float = 0.0, rho: float = 0.0,
                  delta: float = 0.0, noise_sigma: float = 0.0, max_rounds: int = 0, stream=None,
-                 profile: bool = False, graph: bool = False, coef: str = "mean", residual: str = "bins"):
+                 profile: bool = False, graph: bool = False, coef: str = "mean", residual: str = "bins",
+                 p_min: int = 0):
         L = load()
         if residual not in RESIDUAL:
             raise ValueError(f"residual must be one of {sorted(RESIDUAL)}")
@@ -202,7 +206,7 @@ class Plan:
         self.precision = precision
         self.cdtype = torch.complex128 if precision == "fp64" else torch.complex64
         self._keep = []
-        ps = _PSchedule(int(c), 0, None)
+        ps = _PSchedule(int(c), 0, None, int(p_min))
         if primes is not None and len(primes):
             arr = _i64_array(primes)
             self._keep.append(arr)

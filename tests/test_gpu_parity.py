@@ -477,3 +477,46 @@ def test_assign_many_refills_like_fresh_handles(sfft):
         assert g[0].shape[0] == k and np.array_equal(g[0], g1[0])
         if k:
             assert np.max(np.abs(g[1] - g1[1]) / np.abs(g1[1])) < FP32_COEFF_TOL
+
+
+# ------------------------------------------------------------------ noisy black boxes
+
+def test_noisy_recovery_matches_oracle_noise_for_noise(sfft):
+    # sigma = 0.01 moves the coefficients by a few 1e-5 relative (the noise of a bin over p), a
+    # multiple of the float tolerance, so agreement with the oracle shows that both draw the
+    # same noise for every sample
+    d, N, k, sigma = 3, 256, 120, 1e-2
+    sig = draw_signal(d, N, k, seed=43, r_lo=1.0, r_hi=10.0, noise_sigma=sigma)
+    plan = sfft.Plan(d, N, k, blocks=(2, 1), tau=2e-2, noise_sigma=sigma, p_min=700)
+    f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, N, noise_sigma=sigma,
+                                                   noise_seed=sig.noise_seed))
+    gf, ga = sfft.sort_result(_np(f), _np(a))
+    th = O.Thresholds(tau=2e-2, rho=2.0 ** -17, delta=0.25, sigma=sigma)
+    ref = O.multi_phaseshift(sig.freqs, sig.coeffs, d, N, k, (2, 1), th=th, estimator="mean", residual="bins",
+                             noise=lambda i, p, dd: O.black_box_noise(sig.noise_seed, i, p, dd, sigma), p_min=700)
+    order = np.lexsort(sig.freqs.T[::-1])
+    assert status == 0 and ref.converged and min(stats["p"]) >= 700
+    assert np.array_equal(gf, ref.freqs) and np.array_equal(gf, sig.freqs[order])
+    assert stats["p"] == [r["p"] for r in ref.rounds]
+    moved = np.abs(ref.coeffs - sig.coeffs[order]) / np.abs(sig.coeffs[order])
+    assert np.median(moved) > 2 * FP32_COEFF_TOL                   # the noise is visible ...
+    assert np.max(np.abs(ga - ref.coeffs) / np.abs(ref.coeffs)) < FP32_COEFF_TOL   # ... and the same
+
+
+def test_noisy_d10_workload_full_size(sfft):
+    # d = 10, N = 2^16, k = 10^4, sigma = 1e-3 (FP64 phase ratio, four-step DFT), primes floored
+    # at 30000 so that the read-out noise of |a| = 1 modes stays inside delta: the planted set,
+    # and coefficient errors on the scale of the noise in a bin
+    wl = WORKLOADS["d10_N65536_k10000_noisy"]
+    sig = wl.signal()
+    plan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, noise_sigma=wl.noise_sigma, p_min=wl.p_min)
+    f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N, noise_sigma=wl.noise_sigma,
+                                                   noise_seed=sig.noise_seed))
+    gf, ga = sfft.sort_result(_np(f), _np(a))
+    order = np.lexsort(sig.freqs.T[::-1])
+    assert status == 0 and stats["converged"]
+    assert np.array_equal(gf, sig.freqs[order])
+    err = np.abs(ga - sig.coeffs[order])
+    ps, ns = stats["p"], wl.d + 1
+    assert np.max(err) < 8 * wl.noise_sigma / math.sqrt(min(ps) * ns)
+    assert np.sqrt(np.mean(err ** 2)) > 0.2 * wl.noise_sigma / math.sqrt(max(ps) * ns)

@@ -196,6 +196,17 @@ def test_bin_domain_residual_recovers_the_same_result():
 
 # ---------------------------------------------------------------- noise of the black box
 
+def test_prime_floor_takes_the_ith_prime_above_the_floor():
+    wl_sig = draw_signal(2, 1024, 16, seed=5, r_lo=1.0, r_hi=2.0)
+    th = O.Thresholds(tau=1e-7, rho=2.0 ** -40, delta=0.1)
+    res = O.multi_phaseshift(wl_sig.freqs, wl_sig.coeffs, 2, 1024, 16, (1, 1), th=th, p_min=1000)
+    assert res.converged and np.array_equal(res.freqs, wl_sig.freqs[np.lexsort(wl_sig.freqs.T[::-1])])
+    pr = _sieve(4000)
+    for r in res.rounds:
+        lo = max(5 * r["k_star"], 1000)
+        assert r["p"] == int(pr[np.searchsorted(pr, lo) + r["round"] - 1])
+
+
 def test_philox_is_a_bijection_with_full_avalanche():
     # for one key the 128-bit output of distinct counters never repeats; flipping one counter
     # bit flips about half of the 128 output bits (a dropped round, word or xor breaks one of these)
