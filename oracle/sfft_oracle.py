@@ -116,8 +116,32 @@ def line_direction(d: int, N: int, blocks, i: int, dirs=None) -> np.ndarray:
 # --------------------------------------------------------------------------
 
 
+def shift_phases(freqs: np.ndarray, N: int, shift: str = "coord", blocks=None):
+    """Exact phases of the shifted sets: (num, q) with w_j . s_n = num[j, n] / q[n] mod 1.
+
+    shift "coord" (the general form): s_n = e_n / N, so the phase of set n is w_n mod N over N.
+    shift "block" (Alg. 2 as printed, reading A5): set n moves along the unwrap vector v_n of
+    block n (N^r on its r-th coordinate, Eq. 35) by eps_n = 1 / (2 N^{d1_n}), d1_n its size, so
+    the phase is w~_n / (2 N^{d1_n}) with w~_n = sum_r w_{b_n + r} N^r the block's unwrapped
+    frequency (Eq. 35-36)."""
+    freqs = np.asarray(freqs, dtype=np.int64)
+    K, d = freqs.shape
+    if shift == "coord":
+        return np.mod(freqs, N), np.full(d, N, dtype=np.int64)
+    starts = block_starts(blocks)
+    num = np.zeros((K, len(blocks)), dtype=np.int64)
+    q = np.zeros(len(blocks), dtype=np.int64)
+    for n, (b, size) in enumerate(zip(starts, blocks)):
+        wt = np.zeros(K, dtype=np.int64)
+        for r in range(size):
+            wt += freqs[:, b + r] * N ** r
+        q[n] = 2 * N ** size
+        num[:, n] = np.mod(wt, q[n])
+    return num, q
+
+
 def sample_sets(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int,
-                chunk: int = 4096, x_values=None) -> np.ndarray:
+                chunk: int = 4096, x_values=None, shift: str = "coord", blocks=None) -> np.ndarray:
     """y[n, x] = sum_j coeffs_j exp(2 pi i w_j . t_{n,x}),  t_{n,x} = x u / p + s_n,
     s_0 = 0 and s_n = e_n / N, for x = 0..p-1 and n = 0..d.
 
@@ -125,27 +149,31 @@ def sample_sets(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int,
     exactly: w . (x u / p) = x (w . u) / p, whose fractional part is ((x (w . u)) mod p) / p,
     and w . s_n = w_n / N, whose fractional part is (w_n mod N) / N.  Registry modes enter
     with negated coefficients, so the same call evaluates f - g.  ``x_values``, if given,
-    restricts the evaluation to those sample indices (columns in the given order)."""
+    restricts the evaluation to those sample indices (columns in the given order).  With
+    shift "block" the shifted sets are those of shift_phases (one per block)."""
     freqs = np.asarray(freqs, dtype=np.int64)
     coeffs = np.asarray(coeffs, dtype=np.complex128)
     K, d = freqs.shape
+    S = d if shift == "coord" else len(blocks)
     xs = np.arange(p, dtype=np.int64) if x_values is None else np.asarray(x_values, dtype=np.int64)
-    y = np.zeros((d + 1, xs.size), dtype=np.complex128)
+    y = np.zeros((S + 1, xs.size), dtype=np.complex128)
     if K == 0:
         return y
     u_mod = np.array([int(v) % p for v in u], dtype=np.int64)
     alpha = (freqs @ u_mod) % p                       # (w . u) mod p, exact
-    shift_frac = np.mod(freqs, N) / N                 # frac(w . s_n) for n = 1..d
+    num, q = shift_phases(freqs, N, shift, blocks)
+    shift_frac = num / q[None, :]                     # frac(w . s_n) for n = 1..S
     for x0 in range(0, xs.size, chunk):
         x = xs[x0:x0 + chunk]
         line_frac = ((alpha[:, None] * x[None, :]) % p) / p
-        for n in range(d + 1):
+        for n in range(S + 1):
             frac = line_frac if n == 0 else line_frac + shift_frac[:, n - 1][:, None]
             y[n, x0:x0 + x.size] = coeffs @ np.exp(2j * np.pi * frac)
     return y
 
 
-def registry_bins(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int) -> np.ndarray:
+def registry_bins(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int, shift: str = "coord",
+                  blocks=None) -> np.ndarray:
     """The DFT of the samples of g = sum_j coeffs_j e^{2 pi i w_j . t}, written without sampling:
     sample set n of one mode is a_j e^{2 pi i w_{j,n} / N} W^{alpha_j x} with alpha_j = (w_j . u)
     mod p (see sample_sets), and sum_x W^{(alpha_j - h) x} is p when h = alpha_j and 0 otherwise
@@ -155,15 +183,17 @@ def registry_bins(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int) -> n
     freqs = np.asarray(freqs, dtype=np.int64)
     coeffs = np.asarray(coeffs, dtype=np.complex128)
     K, d = freqs.shape
-    G = np.zeros((d + 1, p), dtype=np.complex128)
+    S = d if shift == "coord" else len(blocks)
+    G = np.zeros((S + 1, p), dtype=np.complex128)
     if K == 0:
         return G
     u_mod = np.array([int(v) % p for v in u], dtype=np.int64)
     alpha = (freqs @ u_mod) % p
+    num, q = shift_phases(freqs, N, shift, blocks)
     for j in range(K):
         G[0, alpha[j]] += p * coeffs[j]
-        for n in range(1, d + 1):
-            G[n, alpha[j]] += p * coeffs[j] * np.exp(2j * np.pi * (int(freqs[j, n - 1]) % N) / N)
+        for n in range(1, S + 1):
+            G[n, alpha[j]] += p * coeffs[j] * np.exp(2j * np.pi * int(num[j, n - 1]) / int(q[n - 1]))
     return G
 
 
@@ -237,32 +267,62 @@ class Thresholds:
     sigma: float = 0.0       # noise level of the samples (adds 6 sigma sqrt(p) to the level)
 
 
+def _decode_blocks(ratio: np.ndarray, N: int, blocks, box_lo: int, delta: float, d: int):
+    """Frequency vector from the block read-outs, or None when a read-out is farther than delta
+    from an integer or falls outside the box's window of unwrapped values."""
+    w = np.zeros(d, dtype=np.int64)
+    for n, (b, size) in enumerate(zip(block_starts(blocks), blocks)):
+        q = 2 * N ** size
+        v = q * float(arg(ratio[n])) / (2 * np.pi)
+        r = round(v)
+        if abs(v - r) > delta:
+            return None
+        lo = box_lo * sum(N ** t for t in range(size))              # unwrapped value of (box_lo, ...)
+        t = (r - lo) % q
+        if t >= N ** size:
+            return None
+        for pos in range(size):                                      # base-N digits, lowest first
+            w[b + pos] = t % N + box_lo
+            t //= N
+    return w
+
+
 def classify(Y: np.ndarray, p: int, u, N: int, eta_bin: float, th: Thresholds,
-             box_lo: int = 0, estimator: str = "set0"):
+             box_lo: int = 0, estimator: str = "set0", shift: str = "coord", blocks=None):
     """All bins h = 0..p-1 that hold exactly one mode, with the mode read off.
 
     The coefficient is a = Y_0[h] / p (Eq. 41, estimator "set0") or, with estimator
     "mean", the mean over n = 0..d of Y_n[h] exp(-2 pi i w_n / N) / p, which for a bin
     holding one mode has every term equal to a (Eq. 41 applied to each shifted set).
-    Returns a list of (h, w, a), w a tuple of d ints, in increasing h."""
-    D = Y.shape[0] - 1
+    Returns a list of (h, w, a), w a tuple of d ints, in increasing h.
+
+    With shift "block" set n reads the unwrapped frequency of block n,
+    w~_n = 2 N^{d1} Arg(Y_n / Y_0) / (2 pi) (Alg. 2 read-out with eps = 1 / (2 N^{d1})), taken in
+    the window of the box's unwrapped values and split into its d1 base-N digits (Alg. 2 wrap-back)."""
     Y0 = Y[0]
     occupied = np.abs(Y0) > eta_bin
     out = []
     u_mod = np.array([int(v) % p for v in u], dtype=np.int64)
+    d = len(u_mod)
     for h in np.nonzero(occupied)[0]:
         ratio = np.abs(Y[1:, h]) / np.abs(Y0[h])                    # Eq. 42, every n
         if not np.all(np.abs(ratio - 1.0) < th.tau):
             continue
-        v = N * arg(Y[1:, h] / Y0[h]) / (2 * np.pi)                 # Eq. 41 with eps = 1/N
-        r = np.round(v)
-        if not np.all(np.abs(v - r) <= th.delta):
-            continue
-        w = (np.mod(r.astype(np.int64) - box_lo, N) + box_lo).astype(np.int64)
+        if shift == "coord":
+            v = N * arg(Y[1:, h] / Y0[h]) / (2 * np.pi)             # Eq. 41 with eps = 1/N
+            r = np.round(v)
+            if not np.all(np.abs(v - r) <= th.delta):
+                continue
+            w = (np.mod(r.astype(np.int64) - box_lo, N) + box_lo).astype(np.int64)
+        else:
+            w = _decode_blocks(Y[1:, h] / Y0[h], N, blocks, box_lo, th.delta, d)
+            if w is None:
+                continue
         if int(w @ u_mod) % p != h:                                  # lands in its own bin
             continue
         if estimator == "mean":
-            rot = np.concatenate([[1.0 + 0j], np.exp(-2j * np.pi * np.mod(w, N) / N)])
+            num, q = shift_phases(w[None, :], N, shift, blocks)
+            rot = np.concatenate([[1.0 + 0j], np.exp(-2j * np.pi * num[0] / q)])
             a = complex(np.mean(Y[:, h] * rot) / p)
         else:
             a = complex(Y0[h] / p)                                   # Eq. 41: a = Y_0 / p
@@ -294,7 +354,8 @@ class Result:
 def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int = 5,
                      th: Thresholds | None = None, max_rounds: int | None = None,
                      box_lo: int = 0, primes=None, dirs=None, noise=None,
-                     estimator: str = "set0", residual: str = "samples", p_min: int = 0) -> Result:
+                     estimator: str = "set0", residual: str = "samples", p_min: int = 0,
+                     shift: str = "coord") -> Result:
     """Algorithm 2 (MultiPhaseshift) on the black box f = sum_j coeffs_j e^{2 pi i freqs_j . t}.
 
     ``primes``, if given, overrides the prime rule (round i uses primes[(i-1) mod len]).
@@ -302,7 +363,8 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
     black-box samples of round i.  ``residual`` says where g (built from the registry) leaves
     f: "samples" evaluates f - g at every sample point, as Alg. 2 writes it; "bins" samples f
     alone and subtracts the transform of g bin by bin (registry_bins).  ``p_min`` floors the
-    prime rule: round i uses the i-th prime >= max(c k*, p_min)."""
+    prime rule: round i uses the i-th prime >= max(c k*, p_min).  ``shift`` is "coord" (one
+    shifted set per coordinate, s_n = e_n / N) or "block" (one per block, Alg. 2 as printed)."""
     if residual not in ("samples", "bins"):
         raise ValueError(residual)
     th = th or Thresholds()
@@ -329,24 +391,25 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
             all_a = np.concatenate([coeffs, reg_a])
         else:
             all_w, all_a = freqs, coeffs
-        y = sample_sets(all_w, all_a, p, u, N)
+        y = sample_sets(all_w, all_a, p, u, N, shift=shift, blocks=blocks)
         if noise is not None:
-            y = y + noise(i, p, d)
+            y = y + noise(i, p, y.shape[0] - 1)
         Y = dft(y)
         if R and residual == "bins":
             reg_w = np.array(list(R.keys()), dtype=np.int64).reshape(-1, d)
-            Y = Y - registry_bins(reg_w, np.array(list(R.values()), dtype=np.complex128), p, u, N)
+            Y = Y - registry_bins(reg_w, np.array(list(R.values()), dtype=np.complex128), p, u, N,
+                                  shift=shift, blocks=blocks)
         if a_ref is None:
             a_ref = float(np.max(np.abs(Y[0]))) / p if p > 0 else 0.0
         eta_bin = max(th.rho * p * a_ref, 6.0 * th.sigma * math.sqrt(p))
         stat = {"round": i, "p": p, "k_star": k_star, "terms": int(all_w.shape[0]),
-                "samples": (d + 1) * p, "eta_bin": eta_bin}
+                "samples": int(Y.shape[0]) * p, "eta_bin": eta_bin}
         if not np.any(np.abs(Y[0]) > eta_bin):
             stat.update(accepted=0, registry=len(R))
             rounds.append(stat)
             converged = True
             break
-        acc = classify(Y, p, u, N, eta_bin, th, box_lo, estimator)
+        acc = classify(Y, p, u, N, eta_bin, th, box_lo, estimator, shift=shift, blocks=blocks)
         for _, w, a in acc:                                    # R <- R u (w, a)
             R[w] = R.get(w, 0j) + a
         eta_prune = max(th.rho * a_ref, 6.0 * th.sigma / math.sqrt(p))

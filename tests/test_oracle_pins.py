@@ -89,6 +89,67 @@ def test_samples_equal_exact_rational_evaluation():
     _check_samples_against_rationals(O.sample_sets)
 
 
+def _check_block_samples_against_rationals(sample_fn):
+    # Alg. 2 as printed: set n moves along the unwrap vector v_n of block n (N^r on its r-th
+    # coordinate) by eps_n = 1 / (2 N^{d1}); exact rational phases, then cos / sin
+    rng = Stream(12)
+    d, N, p, blocks = 5, 6, 11, (2, 3)
+    freqs = rng.integers(4 * d, -3, 3).reshape(4, d)
+    coeffs = rng.uniform(4) + 1j * rng.uniform(4)
+    u = [1, N, 0, 0, 0]
+    y = sample_fn(freqs, coeffs, p, u, N)
+    starts = [0, 2]
+    assert y.shape == (3, p)
+    for n in range(3):
+        shift = [Fraction(0)] * d
+        if n:
+            b, size = starts[n - 1], blocks[n - 1]
+            for r in range(size):
+                shift[b + r] = Fraction(N ** r, 2 * N ** size)
+        for x in range(p):
+            t = [Fraction(x * u[l], p) + shift[l] for l in range(d)]
+            want = 0j
+            for w, a in zip(freqs, coeffs):
+                ph = sum(int(w[l]) * t[l] for l in range(d))
+                ph -= math.floor(ph)
+                want += a * complex(math.cos(2 * math.pi * ph), math.sin(2 * math.pi * ph))
+            assert abs(y[n, x] - want) < 1e-12
+
+
+def test_block_shift_samples_equal_exact_rational_evaluation():
+    _check_block_samples_against_rationals(
+        lambda f, a, p, u, N: O.sample_sets(f, a, p, u, N, shift="block", blocks=(2, 3)))
+
+
+def test_block_readout_decodes_every_vector_of_a_box():
+    # every vector of the box [-2, 2)^3 (N = 4, one block of 3): its set-1 ratio e^{2 pi i w~ / (2 N^3)}
+    # reads back exactly, and a read-out outside the box's window is rejected
+    N, blocks, box_lo = 4, (3,), -2
+    for w in np.stack(np.meshgrid(*[np.arange(-2, 2)] * 3, indexing="ij"), -1).reshape(-1, 3):
+        num, q = O.shift_phases(w[None, :], N, "block", blocks)
+        ratio = np.array([np.exp(2j * np.pi * num[0, 0] / q[0])])
+        assert np.array_equal(O._decode_blocks(ratio, N, blocks, box_lo, 0.1, 3), w)
+    lo = box_lo * (1 + N + N * N)
+    outside = np.array([np.exp(2j * np.pi * (lo + N ** 3 + 5) / (2 * N ** 3))])
+    assert O._decode_blocks(outside, N, blocks, box_lo, 0.1, 3) is None
+
+
+def test_block_shift_recovery_equals_coordinate_shift_recovery():
+    # the two shift forms read the same modes (the paper's shape included: d = 100, N = 20,
+    # d1 = 5, |a| = 1, signed box) with FP64 coefficients at round-off
+    for d, N, k, blocks, box, seed, unit in ((4, 8, 20, (2, 2), 0, 1, False), (6, 16, 40, (3, 3), -8, 2, False),
+                                             (100, 20, 16, (5,) * 20, -10, 3, True)):
+        sig = draw_signal(d, N, k, seed=seed, box_lo=box, unit_modulus=unit)
+        th = O.Thresholds()
+        rb = O.multi_phaseshift(sig.freqs, sig.coeffs, d, N, k, blocks, th=th, box_lo=box, shift="block")
+        rc = O.multi_phaseshift(sig.freqs, sig.coeffs, d, N, k, blocks, th=th, box_lo=box)
+        o = np.lexsort(sig.freqs.T[::-1])
+        assert rb.converged and np.array_equal(rb.freqs, sig.freqs[o].astype(np.int64))
+        assert np.array_equal(rb.freqs, rc.freqs)
+        assert np.linalg.norm(rb.coeffs - sig.coeffs[o]) < 16 * 2.0 ** -52 * math.sqrt(k) * 10
+        assert sum(r["samples"] for r in rb.rounds) < sum(r["samples"] for r in rc.rounds)
+
+
 def test_samples_equal_direct_real_point_evaluation():
     # f evaluated at the real point t = x u / p + s_n without any reduction (small numbers).
     sig = draw_signal(2, 16, 5, seed=3)
@@ -478,6 +539,23 @@ def test_planted_mistakes_are_caught(monkeypatch):
     for bad in (bins_no_p, bins_conj_phase, bins_wrong_bin):
         with pytest.raises(AssertionError):
             _check_registry_bins(bad)
+
+    real_phases = O.shift_phases
+
+    def eps_not_halved(freqs, N, shift="coord", blocks=None):   # eps = 1 / N^{d1}: read-out wraps
+        num, q = real_phases(freqs, N, shift, blocks)
+        if shift == "block":
+            q = q // 2
+            num = np.mod(num, q[None, :])
+        return num, q
+
+    monkeypatch.setattr(O, "shift_phases", eps_not_halved)
+    with pytest.raises(AssertionError):
+        test_block_readout_decodes_every_vector_of_a_box()
+    with pytest.raises(AssertionError):
+        _check_block_samples_against_rationals(
+            lambda f, a, p, u, N: O.sample_sets(f, a, p, u, N, shift="block", blocks=(2, 3)))
+    monkeypatch.setattr(O, "shift_phases", real_phases)
 
     real_philox = O.philox4x32_10
 
