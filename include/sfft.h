@@ -101,7 +101,17 @@ typedef struct {
                         over the d + 1 sets of Y_n[h] e^{-2 pi i w_n / N} / p, equal to it for a
                         single-mode bin and less affected by rounding */
   int residual;      /* sfft_residual: where g, built from the registry, leaves f each round */
+  int shift;         /* sfft_shift: which shifted copies of the line are sampled */
 } sfft_opts;
+
+/* The shifted sample sets (Alg. 2).  COORD (default): one set per coordinate, shifted by e_n / N,
+ * reads w_n = N Arg(Y_n / Y_0) / (2 pi); d + 1 sets.  BLOCK (Alg. 2 as printed): one set per
+ * block of the partial unwrapping (tilts.block_sizes, or the default rule), shifted by
+ * v_n / (2 N^{d1}) along the block's unwrap vector (N^r on its r-th coordinate, Eq. 35); it reads
+ * the block's unwrapped frequency 2 N^{d1} Arg(Y_n / Y_0) / (2 pi) and splits it into d1 base-N
+ * digits; 1 + (number of blocks) sets.  With BLOCK the precision policy follows N^{d1}: AUTO
+ * reads phases in double above 2^14, and the float policies return PRECISION above 2^20. */
+typedef enum { SFFT_SHIFT_COORD = 0, SFFT_SHIFT_BLOCK = 1 } sfft_shift;
 
 /* Alg. 2 removes g (the function of the registry's modes) from f before each round's
  * test (Sec. 5, "Algorithm").  SAMPLES evaluates f - g at every sample point, as the
@@ -266,6 +276,8 @@ sfft_status sfft_sample_noalloc(int d, int64_t N, int64_t p, const int64_t* u, i
  * bytes of device memory the plan holds. */
 int64_t sfft_plan_max_prime(sfft_plan plan);
 int64_t sfft_plan_mode_capacity(sfft_plan plan);
+/* Sample sets per round: d + 1 (coordinate shifts) or 1 + blocks (block shifts); -1 for NULL. */
+int sfft_plan_sets(sfft_plan plan);
 int64_t sfft_plan_device_bytes(sfft_plan plan);
 
 /* The last cudaError_t seen by any call of this thread (0 if none). */

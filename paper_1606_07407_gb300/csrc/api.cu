@@ -135,6 +135,7 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
   if (o.tau < 0 || o.rho < 0 || o.delta < 0 || o.delta >= 0.5 || o.noise_sigma < 0 || o.max_rounds < 0)
     return SFFT_ERR_INVALID_ARG;
   if (o.residual != SFFT_RESIDUAL_BINS && o.residual != SFFT_RESIDUAL_SAMPLES) return SFFT_ERR_INVALID_ARG;
+  if (o.shift != SFFT_SHIFT_COORD && o.shift != SFFT_SHIFT_BLOCK) return SFFT_ERR_INVALID_ARG;
 
   std::unique_ptr<sfft_plan_s> P(new sfft_plan_s());
   SlotDesc& D = P->desc;
@@ -195,33 +196,35 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
   }
   if (D.p_max > (1LL << 26) || (!fp64 && D.p_max >= (1LL << 22))) return SFFT_ERR_INVALID_ARG;
 
+  // ---- blocks (partial unwrapping, Sec. 4.1; also the shifted sets of the block form)
+  std::vector<int> blocks;
+  if (tilts && tilts->n_blocks > 0) {
+    if (!tilts->block_sizes) return SFFT_ERR_INVALID_ARG;
+    int tot = 0;
+    for (int q = 0; q < tilts->n_blocks; ++q) {
+      if (tilts->block_sizes[q] < 1) return SFFT_ERR_INVALID_ARG;
+      blocks.push_back(tilts->block_sizes[q]);
+      tot += tilts->block_sizes[q];
+    }
+    if (tot != d) return SFFT_ERR_INVALID_ARG;
+  } else {
+    // default: smallest b with N^b >= 4 c k, d / b blocks, earlier blocks take the remainder
+    int b = 1;
+    double range = (double)N;
+    while (range < 4.0 * D.c * std::max<int64_t>(k, 1) && b < d) {
+      ++b;
+      range *= (double)N;
+    }
+    const int nb = std::max(1, d / b);
+    for (int q = 0; q < nb; ++q) blocks.push_back(d / nb + (q < d % nb ? 1 : 0));
+  }
+
   // ---- line directions
   if (tilts && tilts->n_dirs > 0) {
     if (!tilts->dirs) return SFFT_ERR_INVALID_ARG;
     D.dirs.assign(tilts->dirs, tilts->dirs + (size_t)tilts->n_dirs * d);
     D.n_dirs = tilts->n_dirs;
   } else {
-    std::vector<int> blocks;
-    if (tilts && tilts->n_blocks > 0) {
-      if (!tilts->block_sizes) return SFFT_ERR_INVALID_ARG;
-      int tot = 0;
-      for (int q = 0; q < tilts->n_blocks; ++q) {
-        if (tilts->block_sizes[q] < 1) return SFFT_ERR_INVALID_ARG;
-        blocks.push_back(tilts->block_sizes[q]);
-        tot += tilts->block_sizes[q];
-      }
-      if (tot != d) return SFFT_ERR_INVALID_ARG;
-    } else {
-      // default: smallest b with N^b >= 4 c k, d / b blocks, earlier blocks take the remainder
-      int b = 1;
-      double range = (double)N;
-      while (range < 4.0 * D.c * std::max<int64_t>(k, 1) && b < d) {
-        ++b;
-        range *= (double)N;
-      }
-      const int nb = std::max(1, d / b);
-      for (int q = 0; q < nb; ++q) blocks.push_back(d / nb + (q < d % nb ? 1 : 0));
-    }
     D.n_dirs = (int)blocks.size();
     D.dirs.assign((size_t)D.n_dirs * d, 0);
     int start = 0;
@@ -236,6 +239,23 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
       }
       start += blocks[q];
     }
+  }
+
+  // ---- shifted sets: e_n / N per coordinate, or v_n / (2 N^{d1}) per block (Alg. 2 as printed).
+  // The block form reads a block's unwrapped frequency (up to N^{d1}) from one phase, so the
+  // precision policy follows N^{d1}: float ratio up to 2^14, float samples up to 2^20, FP64 beyond.
+  D.shift_block = o.shift == SFFT_SHIFT_BLOCK ? 1 : 0;
+  if (D.shift_block) {
+    double span_max = 0.0;
+    for (int size : blocks) {
+      if (size > 32) return SFFT_ERR_INVALID_ARG;
+      const double span = std::pow((double)N, (double)size);
+      if (span > std::ldexp(1.0, 40)) return SFFT_ERR_INVALID_ARG;
+      span_max = std::max(span_max, span);
+    }
+    if (!fp64 && span_max > std::ldexp(1.0, 20)) return SFFT_ERR_PRECISION;
+    if (o.precision == SFFT_PREC_AUTO) D.ratio64 = span_max > std::ldexp(1.0, 14) ? 1 : 0;
+    D.shift_blocks = blocks;
   }
 
   std::vector<SlotDesc> slots(1, D);
@@ -255,6 +275,10 @@ void sfft_plan_destroy(sfft_plan plan) {
 
 int64_t sfft_plan_max_prime(sfft_plan plan) { return plan ? plan->eng->max_prime() : -1; }
 int64_t sfft_plan_mode_capacity(sfft_plan plan) { return plan ? plan->eng->mode_capacity() : -1; }
+int sfft_plan_sets(sfft_plan plan) {
+  if (!plan) return -1;
+  return plan->desc.shift_block ? 1 + (int)plan->desc.shift_blocks.size() : plan->desc.d + 1;
+}
 int64_t sfft_plan_device_bytes(sfft_plan plan) { return plan ? (int64_t)plan->eng->device_bytes() : -1; }
 
 sfft_status sfft_signal_synthetic(int d, int64_t N, int64_t k, const int32_t* freqs_dev, const double* coeffs_dev,

@@ -51,19 +51,21 @@ __global__ void k_init(int n, SigRun* run, const int64_t* __restrict__ bindv) {
   }
 }
 
-// unit twiddles e^{2 pi i w_{j,l} / N} of the bound signals' modes
+// twiddles e^{2 pi i w_j . s_n} of the bound signals' modes, one per shifted set (shift_root)
 template <typename T>
 __global__ void k_bind_tw(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run,
-                          const int32_t* const* __restrict__ sig_w, c2<T>* __restrict__ tw) {
+                          const int32_t* const* __restrict__ sig_w, const int32_t* __restrict__ shblk,
+                          c2<T>* __restrict__ tw) {
   const int s = blockIdx.y;
   if (s >= n) return;
   const SigCfg& c = cfg[s];
-  const int64_t total = (int64_t)run[s].k_sig * c.d;
+  const int S = c.n_sets - 1;
+  const int64_t total = (int64_t)run[s].k_sig * S;
   const int32_t* w = sig_w[s];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t m = (int64_t)w[e] % c.N;
-    if (m < 0) m += c.N;
-    tw[c.tw_off + e] = unit_root<T>(m, c.N);
+    const int64_t j = e / S;
+    const int nn = (int)(e - j * S) + 1;
+    tw[c.tw_off + e] = shift_root<T>(c, shblk + c.blk_off, w + j * c.d, nn, false);
   }
 }
 
@@ -346,17 +348,18 @@ __global__ void k_tables(int n, const SigCfg* __restrict__ cfg, const SigRun* __
     const int32_t* w;
     double2 a;
     const c2<T>* twr;
+    const int S = c.n_sets - 1;   // twiddles per mode: one per shifted set
     if (j < r.k_sig) {
       w = sig_w[s] + (int64_t)j * d;
       a = sig_a[s][j];
-      twr = tw + c.tw_off + (int64_t)j * d;
+      twr = tw + c.tw_off + (int64_t)j * S;
     } else {
       const int jr = j - r.k_sig;
       w = regw + c.regw_off + (int64_t)jr * d;
       a = rega[c.rega_off + jr];
       a.x = -a.x;   // registry modes: f - g
       a.y = -a.y;
-      twr = regtw + c.regtw_off + (int64_t)jr * d;
+      twr = regtw + c.regtw_off + (int64_t)jr * S;
     }
     const uint64_t acc = project_mod(w, d, u, c.box_lo, r.p, mm);
     alpha[c.mode_off + j] = (int32_t)acc;
@@ -712,7 +715,7 @@ __global__ void k_peel(int n, const SigCfg* __restrict__ cfg, const SigRun* __re
     // -p a, then -p a e^{2 pi i w_n / N} for n >= 1, in T (float policy: the double pipe is narrow)
     const T px = (T)(-(double)p * a.x), py = (T)(-(double)p * a.y);
     peel_add(Y + 2 * h, px, py);
-    const c2<T>* tw = regtw + c.regtw_off + (int64_t)jr * c.d;
+    const c2<T>* tw = regtw + c.regtw_off + (int64_t)jr * (c.n_sets - 1);
     for (int nn = 1; nn < c.n_sets; ++nn) {
       const c2<T> t = tw[nn - 1];   // e^{2 pi i w_n / N}
       peel_add(Y + 2 * ((int64_t)nn * p + h), px * t.x - py * t.y, px * t.y + py * t.x);
@@ -755,6 +758,61 @@ __device__ __forceinline__ bool read_coord(R ynx, R yny, R y0x, R y0y, int64_t N
   return true;
 }
 
+// Block form: Arg(Y_n / Y_0) read as the block's unwrapped frequency w~ = 2 N^{d1} Arg / (2 pi),
+// taken in the window [W_lo, W_lo + N^{d1}) of the box's unwrapped values (W_lo that of
+// (box_lo, ..., box_lo)) and split into its d1 base-N digits, lowest first; false when farther
+// than delta from an integer or outside the window.
+template <typename R>
+__device__ __forceinline__ bool read_block(R ynx, R yny, R y0x, R y0y, int64_t N, int size, int box_lo, R delta,
+                                           int32_t* digits) {
+  const R re = ynx * y0x + yny * y0y;
+  const R im = yny * y0x - ynx * y0y;
+  const R pi = (R)3.14159265358979323846;
+  R phi = atan2(im, re);
+  if (phi >= pi) phi -= (R)2 * pi;
+  int64_t span = 1, ones = 0;   // N^{d1} and 1 + N + ... + N^{d1-1}
+  for (int r = 0; r < size; ++r) {
+    ones += span;
+    span *= N;
+  }
+  const int64_t q = 2 * span;
+  const R v = (R)q * phi / ((R)2 * pi);
+  const R rr = rint(v);
+  if (!(fabs(v - rr) <= delta)) return false;
+  int64_t t = ((int64_t)rr - (int64_t)box_lo * ones) % q;
+  if (t < 0) t += q;
+  if (t >= span) return false;
+  for (int r = 0; r < size; ++r) {
+    digits[r] = (int32_t)(t % N) + box_lo;
+    t /= N;
+  }
+  return true;
+}
+
+// Read-out of shifted set n (1-based) of an occupied bin: the coordinate it fixes (coordinate
+// form) or the d1 coordinates of block n (block form) go to w (if not null), and their
+// (w_l - box_lo) u_l are added to *bin mod p.
+template <typename R>
+__device__ __forceinline__ bool read_set(const SigCfg& c, const SigRun& r, const int32_t* __restrict__ blk, int n,
+                                         R ynx, R yny, R y0x, R y0y, const int64_t* u, uint64_t* bin, int32_t* w) {
+  const uint64_t up = (uint64_t)r.p;
+  if (!c.shift_block) {
+    int64_t wn;
+    if (!read_coord<R>(ynx, yny, y0x, y0y, c.N, c.box_lo, (R)c.delta, &wn)) return false;
+    if (w) w[n - 1] = (int32_t)wn;
+    *bin = mod_barrett((uint64_t)(wn - c.box_lo) * (uint64_t)u[n - 1] + *bin, up, r.mod_m);
+    return true;
+  }
+  const int b = blk[2 * (n - 1)], size = blk[2 * (n - 1) + 1];
+  int32_t dg[32];
+  if (size > 32 || !read_block<R>(ynx, yny, y0x, y0y, c.N, size, c.box_lo, (R)c.delta, dg)) return false;
+  for (int t = 0; t < size; ++t) {
+    if (w) w[b + t] = dg[t];
+    *bin = mod_barrett((uint64_t)(dg[t] - c.box_lo) * (uint64_t)u[b + t] + *bin, up, r.mod_m);
+  }
+  return true;
+}
+
 struct ClassifyOut {   // step calls: accepted bins are appended here instead of merged
   int32_t* h;
   int32_t* w;
@@ -769,31 +827,29 @@ struct ClassifyOut {   // step calls: accepted bins are appended here instead of
 // fetched eight at a time so that their loads overlap.  Writes w_n to w_out (if not null) and
 // returns whether every set passes and (w . u) mod p is the bin itself.
 template <typename T, typename R>
-__device__ bool decode_bin(const SigCfg& c, const SigRun& r, const c2<T>* Y, const int64_t* u, int64_t h, R y0x,
-                           R y0y, R m0, int32_t* w_out) {
+__device__ bool decode_bin(const SigCfg& c, const SigRun& r, const int32_t* __restrict__ blk, const c2<T>* Y,
+                           const int64_t* u, int64_t h, R y0x, R y0y, R m0, int32_t* w_out) {
   constexpr int kB = 8;
   const int64_t p = r.p;
   const uint64_t up = (uint64_t)p;
+  const int S = c.n_sets - 1;
   uint64_t bin = 0;
-  uint64_t usum = 0;
-  for (int n0 = 1; n0 <= c.d; n0 += kB) {
+  for (int n0 = 1; n0 <= S; n0 += kB) {
     c2<T> yv[kB];
 #pragma unroll
-    for (int i = 0; i < kB; ++i) yv[i] = n0 + i <= c.d ? Y[(int64_t)(n0 + i) * p + h] : mk2((T)0, (T)0);
+    for (int i = 0; i < kB; ++i) yv[i] = n0 + i <= S ? Y[(int64_t)(n0 + i) * p + h] : mk2((T)0, (T)0);
 #pragma unroll
     for (int i = 0; i < kB; ++i) {
       const int n = n0 + i;
-      if (n > c.d) break;
+      if (n > S) break;
       const R ynx = (R)yv[i].x, yny = (R)yv[i].y;
       const R mn = sqrt(ynx * ynx + yny * yny);
       if (!(fabs(mn / m0 - (R)1) < (R)c.tau)) return false;   // Eq. 42
-      int64_t wn;
-      if (!read_coord<R>(ynx, yny, y0x, y0y, c.N, c.box_lo, (R)c.delta, &wn)) return false;
-      if (w_out) w_out[n - 1] = (int32_t)wn;
-      bin = mod_barrett((uint64_t)(wn - c.box_lo) * (uint64_t)u[n - 1] + bin, up, r.mod_m);
-      usum += (uint64_t)u[n - 1];
+      if (!read_set<R>(c, r, blk, n, ynx, yny, y0x, y0y, u, &bin, w_out)) return false;
     }
   }
+  uint64_t usum = 0;
+  for (int l = 0; l < c.d; ++l) usum += (uint64_t)u[l];
   const int64_t blm = ((int64_t)c.box_lo % p + p) % p;
   bin = mod_barrett(bin + mod_barrett((uint64_t)blm * mod_barrett(usum, up, r.mod_m), up, r.mod_m), up, r.mod_m);
   return (int64_t)bin == h;
@@ -802,23 +858,22 @@ __device__ bool decode_bin(const SigCfg& c, const SigRun& r, const c2<T>* Y, con
 // The read-out vector of an accepted bin, computed again (for vectors longer than the
 // decoder's register copy).
 template <typename T, typename R>
-__device__ void read_coords(const SigCfg& c, const SigRun& r, const c2<T>* Y, int64_t h, R y0x, R y0y,
-                            int32_t* w_out) {
-  for (int n = 1; n <= c.d; ++n) {
+__device__ void read_coords(const SigCfg& c, const SigRun& r, const int32_t* __restrict__ blk, const c2<T>* Y,
+                            const int64_t* u, int64_t h, R y0x, R y0y, int32_t* w_out) {
+  uint64_t bin = 0;
+  for (int n = 1; n < c.n_sets; ++n) {
     const c2<T> yn = Y[(int64_t)n * r.p + h];
-    int64_t wn = 0;
-    read_coord<R>((R)yn.x, (R)yn.y, y0x, y0y, c.N, c.box_lo, (R)c.delta, &wn);
-    w_out[n - 1] = (int32_t)wn;
+    read_set<R>(c, r, blk, n, (R)yn.x, (R)yn.y, y0x, y0y, u, &bin, w_out);
   }
 }
 
 // Coefficient estimate of an accepted bin with read-out vector w (Eq. 41).  With coef_mean
-// the estimate is the mean over the d + 1 sets of Y_n[h] e^{-2 pi i w_n / N} / p: for a bin
+// the estimate is the mean over the sets of Y_n[h] e^{-2 pi i w . s_n} / p: for a bin
 // holding one mode every term equals a exactly, and the mean averages the sets' independent
 // rounding (and the leakage of other modes' residuals, whose phases differ across the sets).
 template <typename T, typename R>
-__device__ double2 coefficient(const SigCfg& c, const SigRun& r, const c2<T>* Y, int64_t h, R y0x, R y0y,
-                               const int32_t* w, const c2<T>* tn) {
+__device__ double2 coefficient(const SigCfg& c, const SigRun& r, const int32_t* __restrict__ blk, const c2<T>* Y,
+                               int64_t h, R y0x, R y0y, const int32_t* w, const c2<T>* tn) {
   if (!c.coef_mean) {
     if (sizeof(R) == 4) {
       const float scale = 1.0f / (float)r.p;
@@ -828,15 +883,11 @@ __device__ double2 coefficient(const SigCfg& c, const SigRun& r, const c2<T>* Y,
     return make_double2((double)y0x * scale, (double)y0y * scale);
   }
   R ax = y0x, ay = y0y;
-  for (int n = 1; n <= c.d; ++n) {
+  for (int n = 1; n < c.n_sets; ++n) {
     const c2<T> yn = Y[(int64_t)n * r.p + h];
-    c2<R> t;   // e^{2 pi i w_n / N}
-    if (sizeof(R) == sizeof(T) && tn != nullptr) {
-      t = mk2((R)tn[n - 1].x, (R)tn[n - 1].y);
-    } else {
-      const int64_t m = w[n - 1] < 0 ? (int64_t)w[n - 1] + c.N : (int64_t)w[n - 1];   // w in [box_lo, box_lo + N)
-      t = unit_root<R>(m, c.N);
-    }
+    c2<R> t;   // e^{2 pi i w . s_n}
+    if (sizeof(R) == sizeof(T) && tn != nullptr) t = mk2((R)tn[n - 1].x, (R)tn[n - 1].y);
+    else t = shift_root<R>(c, blk, w, n, true);
     ax += (R)yn.x * t.x + (R)yn.y * t.y;     // Y_n conj(t)
     ay += (R)yn.y * t.x - (R)yn.x * t.y;
   }
@@ -926,8 +977,8 @@ __device__ __forceinline__ void warp_add(int* ctr, int v, int key) {
 template <typename T>
 __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, const RoundCtl* __restrict__ ctl,
                            const int2* __restrict__ cand, const c2<T>* __restrict__ Ybuf,
-                           const int64_t* __restrict__ ubuf, int32_t* regw, double2* rega, c2<T>* regtw,
-                           int32_t* hash, ClassifyOut co) {
+                           const int64_t* __restrict__ ubuf, const int32_t* __restrict__ shblk, int32_t* regw,
+                           double2* rega, c2<T>* regtw, int32_t* hash, ClassifyOut co) {
   const int64_t total = (int64_t)ctl->n_cand;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int2 sh = cand[e];
@@ -939,15 +990,17 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
     const c2<T>* Y = Ybuf + c.Y_off;
     const c2<T> y0 = Y[h];
     const int64_t* u = ubuf + c.u_off;
+    const int32_t* blk = shblk + c.blk_off;
     const int dd = c.d;
+    const int S = c.n_sets - 1;   // shifted sets: twiddles per set
     int32_t wk[64];
     int32_t* wreg = dd <= 64 ? wk : nullptr;   // decoded vector kept for the read-out
     bool ok;
     if (c.ratio64) {
       const double m0d = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y);
-      ok = decode_bin<T, double>(c, r, Y, u, h, (double)y0.x, (double)y0.y, m0d, wreg);
+      ok = decode_bin<T, double>(c, r, blk, Y, u, h, (double)y0.x, (double)y0.y, m0d, wreg);
     } else {
-      ok = decode_bin<T, T>(c, r, Y, u, h, y0.x, y0.y, sqrt(y0.x * y0.x + y0.y * y0.y), wreg);
+      ok = decode_bin<T, T>(c, r, blk, Y, u, h, y0.x, y0.y, sqrt(y0.x * y0.x + y0.y * y0.y), wreg);
     }
     if (!ok) continue;
     warp_add(&rp->n_acc, 1, s);
@@ -962,12 +1015,12 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
       if (wreg) {
         for (int l = 0; l < dd; ++l) wo[l] = wk[l];
       } else if (c.ratio64) {
-        read_coords<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wo);
+        read_coords<T, double>(c, r, blk, Y, u, h, (double)y0.x, (double)y0.y, wo);
       } else {
-        read_coords<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wo);
+        read_coords<T, T>(c, r, blk, Y, u, h, (T)y0.x, (T)y0.y, wo);
       }
-      if (c.ratio64) co.a[idx] = coefficient<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wo, nullptr);
-      else co.a[idx] = coefficient<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wo, nullptr);
+      if (c.ratio64) co.a[idx] = coefficient<T, double>(c, r, blk, Y, h, (double)y0.x, (double)y0.y, wo, nullptr);
+      else co.a[idx] = coefficient<T, T>(c, r, blk, Y, h, (T)y0.x, (T)y0.y, wo, nullptr);
       continue;
     }
     // ---- merge into the registry: keys accepted in one round are distinct (each lands in its
@@ -990,19 +1043,19 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
       wv = rw + (int64_t)scratch_idx * dd;
     }
     if (!wreg) {
-      if (c.ratio64) read_coords<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wv);
-      else read_coords<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wv);
+      if (c.ratio64) read_coords<T, double>(c, r, blk, Y, u, h, (double)y0.x, (double)y0.y, wv);
+      else read_coords<T, T>(c, r, blk, Y, u, h, (T)y0.x, (T)y0.y, wv);
     }
-    // e^{2 pi i w_n / N} of the decoded vector: the registry keeps them (and the float read-out
+    // e^{2 pi i w . s_n} of the decoded vector: the registry keeps them (and the float read-out
     // uses them) so they are formed once
     c2<T> tn[64];
-    const bool keep_tn = dd <= 64;
+    const bool keep_tn = S <= 64;
     if (keep_tn) {
-      for (int l = 0; l < dd; ++l) tn[l] = unit_root<T>(wv[l] < 0 ? (int64_t)wv[l] + c.N : (int64_t)wv[l], c.N);
+      for (int n = 1; n <= S; ++n) tn[n - 1] = shift_root<T>(c, blk, wv, n, true);
     }
     double2 a;
-    if (c.ratio64) a = coefficient<T, double>(c, r, Y, h, (double)y0.x, (double)y0.y, wv, nullptr);
-    else a = coefficient<T, T>(c, r, Y, h, (T)y0.x, (T)y0.y, wv, keep_tn ? tn : nullptr);
+    if (c.ratio64) a = coefficient<T, double>(c, r, blk, Y, h, (double)y0.x, (double)y0.y, wv, nullptr);
+    else a = coefficient<T, T>(c, r, blk, Y, h, (T)y0.x, (T)y0.y, wv, keep_tn ? tn : nullptr);
     int slot = (int)(hash_key(wv, dd) & (unsigned long long)c.hash_mask);
     int mine = scratch_idx;
     bool placed = false, merged = false, past_empty = false;
@@ -1019,9 +1072,8 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
           for (int l = 0; l < dd; ++l) rw[(int64_t)mine * dd + l] = wv[l];
         }
         ra[mine] = a;
-        for (int l = 0; l < dd; ++l)
-          rt[(int64_t)mine * dd + l] =
-              keep_tn ? tn[l] : unit_root<T>(wv[l] < 0 ? (int64_t)wv[l] + c.N : (int64_t)wv[l], c.N);
+        for (int n = 1; n <= S; ++n)
+          rt[(int64_t)mine * S + n - 1] = keep_tn ? tn[n - 1] : shift_root<T>(c, blk, wv, n, true);
         // no fence: nobody reads this entry before the next kernel (see the probe rule below)
         cur = atomicCAS(&hs[slot], -1, mine);
         if (cur < 0) {
@@ -1053,7 +1105,7 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
     if (merged && scratch_idx >= 0) {
       // the slot that held the decoded vector stays a zero mode
       ra[scratch_idx] = make_double2(0.0, 0.0);
-      for (int l = 0; l < dd; ++l) rt[(int64_t)scratch_idx * dd + l] = mk2((T)0, (T)0);
+      for (int l = 0; l < S; ++l) rt[(int64_t)scratch_idx * S + l] = mk2((T)0, (T)0);
     }
     if (placed) warp_add(&rp->n_live, 1, s);
     else if (!merged && mine >= 0 && mine < c.reg_cap) atomicOr(&rp->err, 2);   // table full
@@ -1178,6 +1230,7 @@ class Engine final : public EngineBase {
     ECHK(cudaDeviceGetAttribute(&n_sm_, cudaDevAttrMultiProcessorCount, dev_));
     std::vector<SigCfg> cfg(n_);
     std::vector<int64_t> dirs, plist;
+    std::vector<int32_t> shblk;   // (start, size) of every shift block, block form
     int64_t tw = 0, regw = 0, rega = 0, hashn = 0, tab = 0, bhat = 0, Y = 0, z = 0, u = 0, part_min = 0;
     int64_t bins = 0;   // candidate-list entries: every bin of every slot at its largest prime
     int64_t modes = 0, cm = 0;
@@ -1188,7 +1241,17 @@ class Engine final : public EngineBase {
       SigCfg& c = cfg[s];
       std::memset(&c, 0, sizeof(c));
       c.d = d.d;
-      c.n_sets = d.d + 1;
+      c.shift_block = d.shift_block;
+      c.n_sets = d.shift_block ? 1 + (int)d.shift_blocks.size() : d.d + 1;
+      c.blk_off = (int64_t)shblk.size();
+      if (d.shift_block) {
+        int start = 0;
+        for (int size : d.shift_blocks) {
+          shblk.push_back(start);
+          shblk.push_back(size);
+          start += size;
+        }
+      }
       c.k = (int)d.k;
       c.c = d.c;
       c.max_rounds = d.max_rounds;
@@ -1287,6 +1350,7 @@ class Engine final : public EngineBase {
     ECHK(alloc(&ptab_, ptab.size() * sizeof(int32_t)));
     ECHK(alloc(&pfirst_, pfirst.size() * sizeof(int32_t)));
     ECHK(alloc(&dirs_, std::max<size_t>(dirs.size(), 1) * sizeof(int64_t)));
+    ECHK(alloc(&shblk_, std::max<size_t>(shblk.size(), 1) * sizeof(int32_t)));
     ECHK(alloc(&plist_, std::max<size_t>(plist.size(), 1) * sizeof(int64_t)));
     ECHK(alloc(&tw_, (size_t)tw * sizeof(C2)));
     ECHK(alloc(&regw_, (size_t)regw * sizeof(int32_t)));
@@ -1325,6 +1389,8 @@ class Engine final : public EngineBase {
       ECHK(cudaMemcpyAsync(dirs_, dirs.data(), dirs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st_));
     if (!plist.empty())
       ECHK(cudaMemcpyAsync(plist_, plist.data(), plist.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st_));
+    if (!shblk.empty())
+      ECHK(cudaMemcpyAsync(shblk_, shblk.data(), shblk.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
     k_twiddles<<<(int)std::min<int64_t>((Lmax_ + 255) / 256, 4096), 256, 0, st_>>>(Lmax_, twG_, sizeof(T) == 8);
     ECHK(cudaGetLastError());
     k_twiddles<<<(int)std::min<int64_t>((len3_ + 255) / 256, 4096), 256, 0, st_>>>(len3_, twG3_, sizeof(T) == 8);
@@ -1424,7 +1490,7 @@ class Engine final : public EngineBase {
   cudaError_t launch_classify(const ClassifyOut& co) {
     k_occupied<T><<<8 * n_sm_, 256, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, (const C2*)Y_, cand_, co.eta_override);
     ECHK(cudaGetLastError());
-    k_classify<T><<<8 * n_sm_, 256, 0, st_>>>(n_, cfg_, run_, ctl_, cand_, (const C2*)Y_, u_, regw_, rega_,
+    k_classify<T><<<8 * n_sm_, 256, 0, st_>>>(n_, cfg_, run_, ctl_, cand_, (const C2*)Y_, u_, shblk_, regw_, rega_,
                                              (C2*)regtw_, hash_, co);
     return cudaGetLastError();
   }
@@ -1499,7 +1565,7 @@ class Engine final : public EngineBase {
     ECHK(cudaMemsetAsync(hash_, 0xFF, (size_t)hash_total_ * sizeof(int32_t), st_));
     ECHK(cudaMemsetAsync(ctl_, 0, sizeof(RoundCtl), st_));
     const int gx = (int)std::min<int64_t>(std::max<int64_t>((kd_max_ + 255) / 256, 1), 64);
-    k_bind_tw<T><<<dim3(gx, n_), 256, 0, st_>>>(n_, cfg_, run_, sig_w_, (C2*)tw_);
+    k_bind_tw<T><<<dim3(gx, n_), 256, 0, st_>>>(n_, cfg_, run_, sig_w_, shblk_, (C2*)tw_);
     return cudaGetLastError();
   }
 
@@ -1765,6 +1831,7 @@ class Engine final : public EngineBase {
   int32_t* pfirst_ = nullptr;
   int64_t pfirst_n_ = 0;
   int64_t* dirs_ = nullptr;
+  int32_t* shblk_ = nullptr;   // (start, size) per shift block of every slot (block form)
   int64_t* plist_ = nullptr;
   void* tw_ = nullptr;
   int32_t* regw_ = nullptr;

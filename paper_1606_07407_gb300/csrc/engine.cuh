@@ -30,11 +30,13 @@ struct SigCfg {
   int ratio64;        // phase ratio and coefficient in double
   int coef_mean;      // coefficient = mean over the d + 1 sets (else Y_0[h] / p)
   int peel_bins;      // the registry leaves the transform bin by bin (else it is sampled with f)
+  int shift_block;    // shifted sets move along block unwrap vectors (Alg. 2 as printed), else e_n / N
   int reg_cap, hash_mask, logL_max;
   int64_t N, p_max;
   int64_t p_min;      // floor of the prime rule: the i-th prime >= max(c k*, p_min)
   double tau, rho, delta, sigma;
   int64_t dirs_off, primes_off;  // into the direction / prime-list arrays
+  int64_t blk_off;    // int32 [2 (n_sets - 1)]: start and size of each shift block (block form)
   int64_t tw_off;     // T2 [k * d]        unit twiddles e^{2 pi i w_n / N} of the signal's modes
   int64_t regw_off;   // int32 [reg_cap * d]
   int64_t rega_off;   // double2 [reg_cap]
@@ -116,6 +118,8 @@ struct SlotDesc {
   int ratio64;
   int coef_mean;
   int peel_bins;
+  int shift_block;
+  std::vector<int> shift_blocks;   // block sizes of the shifted sets (block form)
   double tau, rho, delta, sigma;
   int max_rounds;
   std::vector<int64_t> dirs;     // n_dirs x d

@@ -60,6 +60,35 @@ template <> __device__ __forceinline__ double2 unit_root<double>(int64_t m, int6
   return make_double2(c, s);
 }
 
+// e^{2 pi i w . s_n} of shifted set n (1-based).  Coordinate form: s_n = e_n / N, the root of
+// w_n mod N of order N.  Block form: s_n = v_n / (2 N^{d1}) along the unwrap vector of block n
+// (start blk[2n - 2], size d1 = blk[2n - 1]), the root of w~_n mod 2 N^{d1} of order 2 N^{d1},
+// w~_n = sum_r w_{start + r} N^r.  in_box: w lies in the box (one conditional wrap suffices).
+template <typename T>
+__device__ __forceinline__ c2<T> shift_root(const SigCfg& c, const int32_t* __restrict__ blk, const int32_t* w,
+                                            int n, bool in_box) {
+  if (!c.shift_block) {
+    int64_t m = w[n - 1];
+    if (in_box) {
+      if (m < 0) m += c.N;
+    } else {
+      m %= c.N;
+      if (m < 0) m += c.N;
+    }
+    return unit_root<T>(m, c.N);
+  }
+  const int b = blk[2 * (n - 1)], size = blk[2 * (n - 1) + 1];
+  int64_t wt = 0, pw = 1;
+  for (int r = 0; r < size; ++r) {
+    wt += (int64_t)w[b + r] * pw;
+    pw *= c.N;
+  }
+  const int64_t q = 2 * pw;
+  int64_t m = in_box ? wt : wt % q;
+  if (m < 0) m += q;
+  return unit_root<T>(m, q);
+}
+
 // chirp[x] = e^{-pi i x^2 / p} = conj(e^{2 pi i (x^2 mod 2p) / (2p)})
 template <typename T>
 __device__ __forceinline__ c2<T> chirp_at(int64_t x, int64_t p) {

@@ -42,12 +42,15 @@ class _Tilts(C.Structure):
 # where g (the registry's function) leaves f: its transform subtracted bin by bin, or its
 # samples subtracted at every sample point
 RESIDUAL = {"bins": 0, "samples": 1}
+# shifted sets: one per coordinate (e_n / N), or one per unwrapping block (Alg. 2 as printed)
+SHIFT = {"coord": 0, "block": 1}
 
 
 class _Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("box_lo", C.c_int), ("tau", C.c_double), ("rho", C.c_double),
                 ("delta", C.c_double), ("noise_sigma", C.c_double), ("max_rounds", C.c_int),
-                ("profile", C.c_int), ("graph", C.c_int), ("coef_set0", C.c_int), ("residual", C.c_int)]
+                ("profile", C.c_int), ("graph", C.c_int), ("coef_set0", C.c_int), ("residual", C.c_int),
+                ("shift", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -62,7 +65,8 @@ EXPORTS = ["sfft_plan_create", "sfft_plan_destroy", "sfft_signal_synthetic", "sf
            "sfft_execute", "sfft_batch_create", "sfft_batch_destroy", "sfft_batch_device_bytes",
            "sfft_batch_execute", "sfft_sample", "sfft_sample_noalloc", "sfft_dft", "sfft_classify",
            "sfft_plan_max_prime",
-           "sfft_plan_mode_capacity", "sfft_plan_device_bytes", "sfft_last_cuda_error", "sfft_status_string"]
+           "sfft_plan_mode_capacity", "sfft_plan_sets", "sfft_plan_device_bytes", "sfft_last_cuda_error",
+           "sfft_status_string"]
 
 _lib = None
 
@@ -116,6 +120,8 @@ def load(path: str | None = None) -> C.CDLL:
     for f in ("sfft_plan_max_prime", "sfft_plan_mode_capacity", "sfft_plan_device_bytes"):
         getattr(L, f).argtypes = [vp]
         getattr(L, f).restype = i64
+    L.sfft_plan_sets.argtypes = [vp]
+    L.sfft_plan_sets.restype = C.c_int
     L.sfft_last_cuda_error.argtypes = []
     L.sfft_last_cuda_error.restype = C.c_int
     L.sfft_status_string.argtypes = [C.c_int]
@@ -198,7 +204,7 @@ class Plan:
                  precision: str = "fp32", box_lo: int = 0, tau: float = 0.0, rho: float = 0.0,
                  delta: float = 0.0, noise_sigma: float = 0.0, max_rounds: int = 0, stream=None,
                  profile: bool = False, graph: bool = False, coef: str = "mean", residual: str = "bins",
-                 p_min: int = 0):
+                 p_min: int = 0, shift: str = "coord"):
         L = load()
         if residual not in RESIDUAL:
             raise ValueError(f"residual must be one of {sorted(RESIDUAL)}")
@@ -223,7 +229,7 @@ class Plan:
             tl.n_blocks, tl.block_sizes = len(blocks), arr
         op = _Opts(PREC[precision], int(box_lo), float(tau), float(rho), float(delta), float(noise_sigma),
                    int(max_rounds), 1 if profile else 0, 1 if graph else 0, 1 if coef == "set0" else 0,
-                   RESIDUAL[residual])
+                   RESIDUAL[residual], SHIFT[shift])
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -237,6 +243,11 @@ class Plan:
         if h is not None and h.value and _lib is not None:
             _lib.sfft_plan_destroy(h)
             self._h = None
+
+    @property
+    def n_sets(self) -> int:
+        """Sample sets per round: d + 1 (coordinate shifts) or 1 + blocks (block shifts)."""
+        return int(load().sfft_plan_sets(self._h))
 
     @property
     def max_prime(self) -> int:
@@ -266,7 +277,7 @@ class Plan:
         L = load()
         fw = freqs.to(device="cuda", dtype=torch.int32).contiguous()
         ca = coeffs.to(device="cuda", dtype=torch.complex128).contiguous()
-        y = torch.empty((self.d + 1, int(p)), dtype=self.cdtype, device="cuda")
+        y = torch.empty((self.n_sets, int(p)), dtype=self.cdtype, device="cuda")
         ua = _i64_array(u)
         _check(L.sfft_sample(self._h, int(p), ua, int(fw.shape[0]), _ptr(fw), _ptr(ca), _ptr(y)), "sfft_sample")
         return y

@@ -59,9 +59,17 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.sfft_signal_assign_many(2, handles, ks, None, None, None) == 1
     assert lib.sfft_signal_assign_many(0, None, None, None, None, None) == 0   # nothing to do
     from paper_1606_07407_gb300.sfft import _Opts
-    bad = _Opts(0, 0, 0.0, 0.0, 0.0, 0.0, 0, 0, 0, 0, 7)                          # unknown residual form
+    bad = _Opts(0, 0, 0.0, 0.0, 0.0, 0.0, 0, 0, 0, 0, 7, 0)                       # unknown residual form
     assert lib.sfft_plan_create(2, ctypes.c_int64(16), ctypes.c_int64(4), None, None, ctypes.byref(bad), None,
                                 ctypes.byref(h)) == 1
+    # block shifts read N^{d1} values from one phase: beyond 2^20 only the FP64 policy may (PRECISION = 4)
+    from paper_1606_07407_gb300.sfft import _Tilts
+    blk = (ctypes.c_int * 20)(*([5] * 20))
+    tl = _Tilts(0, None, 20, blk)
+    block = _Opts(0, -10, 0.0, 0.0, 0.0, 0.0, 0, 0, 0, 0, 0, 1)
+    assert lib.sfft_plan_create(100, ctypes.c_int64(20), ctypes.c_int64(16), None, ctypes.byref(tl),
+                                ctypes.byref(block), None, ctypes.byref(h)) == 4
+    assert lib.sfft_plan_sets(None) == -1
 
 
 def test_library_is_built_for_sm103a():

@@ -520,3 +520,51 @@ def test_noisy_d10_workload_full_size(sfft):
     ps, ns = stats["p"], wl.d + 1
     assert np.max(err) < 8 * wl.noise_sigma / math.sqrt(min(ps) * ns)
     assert np.sqrt(np.mean(err ** 2)) > 0.2 * wl.noise_sigma / math.sqrt(max(ps) * ns)
+
+
+# ------------------------------------------------------------------ block shifts (Alg. 2 as printed)
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_block_shift_samples_match_oracle(sfft, prec):
+    d, N, K, p, blocks = 5, 6, 300, 1031, (2, 3)
+    sig = draw_signal(d, N, K, seed=71, r_lo=1.0, r_hi=10.0, box_lo=-3)
+    plan = sfft.Plan(d, N, K, blocks=blocks, precision=prec, shift="block", box_lo=-3)
+    assert plan.n_sets == 3
+    u = [int(v) for v in O.unwrap_vector(d, N, blocks, 1)]
+    y = _np(plan.sample(p, u, torch.tensor(sig.freqs), torch.tensor(sig.coeffs)))
+    ref = O.sample_sets(sig.freqs, sig.coeffs, p, u, N, shift="block", blocks=blocks)
+    tol = (2.0 ** -20 if prec == "fp32" else 2.0 ** -48) * np.sum(np.abs(sig.coeffs))
+    assert y.shape == ref.shape and np.max(np.abs(y - ref)) < tol
+
+
+@pytest.mark.parametrize("case", ["d6_auto", "d6_fp64", "paper_d100_fp64"])
+def test_block_shift_recovery_matches_oracle(sfft, case):
+    if case.startswith("d6"):
+        d, N, k, blocks, box, unit, seed = 6, 16, 40, (3, 3), -8, False, 72
+    else:
+        d, N, k, blocks, box, unit, seed = 100, 20, 64, (5,) * 20, -10, True, 73
+    prec = "fp64" if case.endswith("fp64") else "fp32"
+    sig = draw_signal(d, N, k, seed=seed, box_lo=box, unit_modulus=unit, r_lo=1.0, r_hi=10.0)
+    plan = sfft.Plan(d, N, k, blocks=blocks, precision=prec, shift="block", box_lo=box)
+    f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, N))
+    gf, ga = sfft.sort_result(_np(f), _np(a))
+    th = O.Thresholds() if prec == "fp64" else O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
+    ref = O.multi_phaseshift(sig.freqs, sig.coeffs, d, N, k, blocks, th=th, box_lo=box, estimator="mean",
+                             residual="bins", shift="block")
+    _assert_parity(sig, gf, ga, status, stats, ref, FP64_COEFF_TOL if prec == "fp64" else FP32_COEFF_TOL)
+    assert stats["samples"] == sum(r["samples"] for r in ref.rounds)
+
+
+@pytest.mark.parametrize("d", [100, 1000])
+def test_paper_experiment_exact_with_round_off_error(sfft, d):
+    # Sec. 5: d = 100 and 1000, d1 = 5 (d2 = 20 and 200 blocks), N = 20, |a| = 1, box
+    # [-N/2, N/2)^d, eps = 1 / (2 N^5): every frequency exact and the l2 coefficient error at
+    # double round-off (the paper reports averages below 2^-52; a few ulps per mode here)
+    for k, seed in ((1, 1), (32, 2), (1024, 3)):
+        sig = draw_signal(d, 20, k, seed=seed * 100 + d, box_lo=-10, unit_modulus=True)
+        plan = sfft.Plan(d, 20, k, blocks=(5,) * (d // 5), precision="fp64", shift="block", box_lo=-10)
+        f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, 20))
+        gf, ga = sfft.sort_result(_np(f), _np(a))
+        order = np.lexsort(sig.freqs.T[::-1])
+        assert status == 0 and np.array_equal(gf, sig.freqs[order])
+        assert np.linalg.norm(ga - sig.coeffs[order]) < 16 * 2.0 ** -52 * math.sqrt(k) * 10
