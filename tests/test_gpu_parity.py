@@ -568,3 +568,17 @@ def test_paper_experiment_exact_with_round_off_error(sfft, d):
         order = np.lexsort(sig.freqs.T[::-1])
         assert status == 0 and np.array_equal(gf, sig.freqs[order])
         assert np.linalg.norm(ga - sig.coeffs[order]) < 16 * 2.0 ** -52 * math.sqrt(k) * 10
+
+
+def test_precision_stress_d20_fp64_recovers_every_mode(sfft):
+    # d = 20, N = 2^20, k = 10^5, |a| log-uniform in [1e-2, 1e2]: the all-FP64 policy reads every
+    # mode (the float policies cannot: float sampling error over 10^5 modes with a 1e4 dynamic range
+    # puts the small modes' phase read-out N Arg / (2 pi) far beyond delta at N = 2^20)
+    wl = WORKLOADS["d20_N1048576_k100000"]
+    sig = wl.signal()
+    plan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, precision="fp64")
+    f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N))
+    gf, ga = sfft.sort_result(_np(f), _np(a))
+    order = np.lexsort(sig.freqs.T[::-1])
+    assert status == 0 and np.array_equal(gf, sig.freqs[order])
+    assert np.max(np.abs(ga - sig.coeffs[order]) / np.abs(sig.coeffs[order])) < 1e-9
