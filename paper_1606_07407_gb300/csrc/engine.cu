@@ -110,6 +110,98 @@ __device__ __forceinline__ void big_geom(int logL, int* M1, int* M2, int* CT, in
   *RT = min(*M1, max(1, kBigRowElems / *M2));
 }
 
+// Tables of the prime rule and the line directions.
+struct PrimeTables {
+  const int32_t* ptab;
+  int n_ptab;
+  const int32_t* pfirst;
+  int64_t pfirst_n;
+  const int64_t* dirs;
+  const int64_t* plist;
+};
+
+// Round setup of one signal (Alg. 2): the stop rule, then for an active signal the next round's
+// prime, line direction (written to its u slot), Bluestein lengths and sampling geometry, and
+// the statistics of the round just finished (first slot only).
+template <typename T>
+__device__ void plan_signal(const PlanArgs& a, const SigCfg& c, SigRun& r, const PrimeTables& pt, int64_t* ubuf,
+                            HistRec* hist, bool first_slot) {
+  if (first_slot && hist != nullptr && r.round >= 1 && r.round <= SFFT_STATS_MAX_ROUNDS) {
+    hist[r.round - 1].accepted = r.n_acc;
+    hist[r.round - 1].live = r.n_live;
+  }
+  if (r.active && !a.force) {
+    if (r.round > 0 && !r.any_occupied) {
+      r.active = 0;                        // the residual is empty: done
+      r.status = SFFT_OK;
+    } else if (r.err) {
+      r.active = 0;
+      r.status = SFFT_ERR_CAPACITY;
+    } else if (r.round >= c.max_rounds || r.round >= a.hard_rounds) {
+      r.active = 0;
+      r.status = SFFT_ERR_NOT_CONVERGED;
+    }
+  }
+  if (r.active) {
+    const int i = r.round + 1;
+    int64_t p;
+    if (a.force) {
+      p = a.force_p;
+    } else if (c.n_primes > 0) {
+      p = pt.plist[c.primes_off + (i - 1) % c.n_primes];
+    } else {
+      const int64_t kstar = max((int64_t)c.k - r.n_live, (int64_t)1);
+      const int64_t lo = max(max((int64_t)c.c * kstar, c.p_min), (int64_t)2);
+      // pfirst[v] = index of the smallest prime >= v, so the i-th prime >= lo is one lookup away
+      const int64_t idx = lo < pt.pfirst_n ? (int64_t)pt.pfirst[lo] + i - 1 : (int64_t)pt.n_ptab;
+      p = idx < pt.n_ptab ? pt.ptab[idx] : -1;
+    }
+    if (p < 2 || p > c.p_max) {
+      r.active = 0;
+      r.status = SFFT_ERR_INVALID_ARG;
+    } else {
+      r.p = p;
+      r.mod_m = ~0ull / (uint64_t)p;
+      r.round = i;
+      if (!a.force) {
+        const int di = i % c.n_dirs;
+        for (int l = 0; l < c.d; ++l) {
+          int64_t v = pt.dirs[c.dirs_off + (int64_t)di * c.d + l] % p;
+          ubuf[c.u_off + l] = v < 0 ? v + p : v;
+        }
+      }
+      const int K = a.force ? a.force_K : sampled_modes(c, r);
+      r.logL = max(ceil_log2(2 * p - 1), 5);   // at least 32 points
+      r.L = bluestein_length(2 * p - 1);
+      r.big = r.L > (1 << a.single_max_logL);
+      r.groups = (c.n_sets + kMaxSetGroup - 1) / kMaxSetGroup;
+      r.gsize = (c.n_sets + r.groups - 1) / r.groups;
+      {
+        // tiles cover the half line 0 <= x < H (each x also gives p - x); a tile's warps
+        // split into mode groups when H is shorter than the tile
+        const int64_t H = p / 2 + 1;
+        const int rowx = 32 * row_pairs(r.gsize);
+        r.mgroups = (sizeof(T) != 4) ? 1 : (H <= rowx ? 8 : H <= 2 * rowx ? 4 : H <= 4 * rowx ? 2 : 1);
+        const int tx = tile_x(r.gsize) / r.mgroups;
+        r.n_xt = (int)((H + tx - 1) / tx);
+      }
+      r.chunks = K > 0 ? (K + kSampleChunk - 1) / kSampleChunk : 1;
+      r.any_occupied = 0;
+      r.n_acc = 0;
+      r.reg_start = r.K_reg;
+      r.maxy0_bits = 0ull;
+      r.samples += (int64_t)c.n_sets * p;
+      r.terms += (int64_t)c.n_sets * p * K;
+      if (first_slot && hist != nullptr && i <= SFFT_STATS_MAX_ROUNDS) {
+        hist[i - 1].p = p;
+        hist[i - 1].K = K;
+        hist[i - 1].accepted = 0;
+        hist[i - 1].live = r.n_live;
+      }
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg* __restrict__ cfg, SigRun* run,
                                                        RoundCtl* ctl, Scans sc, const int32_t* __restrict__ ptab,
@@ -121,83 +213,10 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
   const int n = a.n;
   int64_t tiles = 0, active = 0;
   // pass 1: stop rule and round parameters of every signal
+  const PrimeTables pt{ptab, n_ptab, pfirst, pfirst_n, dirs, plist};
   for (int s = threadIdx.x; s < n; s += blockDim.x) {
     SigRun r = run[s];
-    const SigCfg& c = cfg[s];
-    if (s == 0 && hist != nullptr && r.round >= 1 && r.round <= SFFT_STATS_MAX_ROUNDS) {
-      hist[r.round - 1].accepted = r.n_acc;
-      hist[r.round - 1].live = r.n_live;
-    }
-    if (r.active && !a.force) {
-      if (r.round > 0 && !r.any_occupied) {
-        r.active = 0;                        // the residual is empty: done
-        r.status = SFFT_OK;
-      } else if (r.err) {
-        r.active = 0;
-        r.status = SFFT_ERR_CAPACITY;
-      } else if (r.round >= c.max_rounds || r.round >= a.hard_rounds) {
-        r.active = 0;
-        r.status = SFFT_ERR_NOT_CONVERGED;
-      }
-    }
-    if (r.active) {
-      const int i = r.round + 1;
-      int64_t p;
-      if (a.force) {
-        p = a.force_p;
-      } else if (c.n_primes > 0) {
-        p = plist[c.primes_off + (i - 1) % c.n_primes];
-      } else {
-        const int64_t kstar = max((int64_t)c.k - r.n_live, (int64_t)1);
-        const int64_t lo = max(max((int64_t)c.c * kstar, c.p_min), (int64_t)2);
-        // pfirst[v] = index of the smallest prime >= v, so the i-th prime >= lo is one lookup away
-        const int64_t idx = lo < pfirst_n ? (int64_t)pfirst[lo] + i - 1 : (int64_t)n_ptab;
-        p = idx < n_ptab ? ptab[idx] : -1;
-      }
-      if (p < 2 || p > c.p_max) {
-        r.active = 0;
-        r.status = SFFT_ERR_INVALID_ARG;
-      } else {
-        r.p = p;
-        r.mod_m = ~0ull / (uint64_t)p;
-        r.round = i;
-        if (!a.force) {
-          const int di = i % c.n_dirs;
-          for (int l = 0; l < c.d; ++l) {
-            int64_t v = dirs[c.dirs_off + (int64_t)di * c.d + l] % p;
-            ubuf[c.u_off + l] = v < 0 ? v + p : v;
-          }
-        }
-        const int K = a.force ? a.force_K : sampled_modes(c, r);
-        r.logL = max(ceil_log2(2 * p - 1), 5);   // at least 32 points
-        r.L = bluestein_length(2 * p - 1);
-        r.big = r.L > (1 << a.single_max_logL);
-        r.groups = (c.n_sets + kMaxSetGroup - 1) / kMaxSetGroup;
-        r.gsize = (c.n_sets + r.groups - 1) / r.groups;
-        {
-          // tiles cover the half line 0 <= x < H (each x also gives p - x); a tile's warps
-          // split into mode groups when H is shorter than the tile
-          const int64_t H = p / 2 + 1;
-          const int rowx = 32 * row_pairs(r.gsize);
-          r.mgroups = (sizeof(T) != 4) ? 1 : (H <= rowx ? 8 : H <= 2 * rowx ? 4 : H <= 4 * rowx ? 2 : 1);
-          const int tx = tile_x(r.gsize) / r.mgroups;
-          r.n_xt = (int)((H + tx - 1) / tx);
-        }
-        r.chunks = K > 0 ? (K + kSampleChunk - 1) / kSampleChunk : 1;
-        r.any_occupied = 0;
-        r.n_acc = 0;
-        r.reg_start = r.K_reg;
-        r.maxy0_bits = 0ull;
-        r.samples += (int64_t)c.n_sets * p;
-        r.terms += (int64_t)c.n_sets * p * K;
-        if (s == 0 && hist != nullptr && i <= SFFT_STATS_MAX_ROUNDS) {
-          hist[i - 1].p = p;
-          hist[i - 1].K = K;
-          hist[i - 1].accepted = 0;
-          hist[i - 1].live = r.n_live;
-        }
-      }
-    }
+    plan_signal<T>(a, cfg[s], r, pt, ubuf, hist, s == 0);
     run[s] = r;
     if (r.active) {
       tiles += (int64_t)r.n_xt * r.groups;
@@ -309,6 +328,58 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
 // Per-prime tables (W, chirp) and the round's mode projections: for every mode j of f (+a)
 // and of the registry (-a): alpha_j = (w_j . u) mod p, ga_j = 32 alpha_j mod p and
 // C[n][j] = a_j e^{2 pi i w_{j,n} / N} (n >= 1), C[0][j] = a_j.
+// W[m] = e^{2 pi i m / p} and chirp[m] = e^{-pi i m^2 / p} of one index m < p of a signal's tables
+template <typename T>
+__device__ __forceinline__ void table_entry(int64_t p, unsigned long long mod_m, int64_t m, c2<T>* t) {
+  t[m] = unit_root<T>(m, p);
+  // x^2 mod 2p from x^2 mod p: of r and r + p the one with the parity of x (p odd)
+  uint64_t r2;
+  if (p == 2) {
+    r2 = ((uint64_t)m * (uint64_t)m) % 4u;
+  } else {
+    const uint64_t r = mod_barrett((uint64_t)m * (uint64_t)m, (uint64_t)p, mod_m);
+    r2 = ((r ^ (uint64_t)m) & 1u) ? r + (uint64_t)p : r;
+  }
+  t[p + m] = cconj(unit_root<T>((int64_t)r2, 2 * p));
+}
+
+// The round's projection of mode j of a signal (black box for j < k, registry with -a after):
+// alpha_j = (w_j . u) mod p, ga_j = 32 alpha_j mod p and C[n][j] = a_j e^{2 pi i w_j . s_n}.
+template <typename T>
+__device__ __forceinline__ void mode_entry(const SigCfg& c, const SigRun& r, int s, int j, const int64_t* __restrict__ ubuf,
+                                           const int32_t* const* __restrict__ sig_w,
+                                           const double2* const* __restrict__ sig_a, const c2<T>* __restrict__ tw,
+                                           const int32_t* __restrict__ regw, const double2* __restrict__ rega,
+                                           const c2<T>* __restrict__ regtw, int32_t* __restrict__ alpha,
+                                           int32_t* __restrict__ gam, c2<T>* __restrict__ Cm) {
+  const uint64_t up = (uint64_t)r.p, mm = r.mod_m;
+  const int64_t* u = ubuf + c.u_off;
+  const int d = c.d;
+  const int32_t* w;
+  double2 a;
+  const c2<T>* twr;
+  const int S = c.n_sets - 1;   // twiddles per mode: one per shifted set
+  if (j < r.k_sig) {
+    w = sig_w[s] + (int64_t)j * d;
+    a = sig_a[s][j];
+    twr = tw + c.tw_off + (int64_t)j * S;
+  } else {
+    const int jr = j - r.k_sig;
+    w = regw + c.regw_off + (int64_t)jr * d;
+    a = rega[c.rega_off + jr];
+    a.x = -a.x;   // registry modes: f - g
+    a.y = -a.y;
+    twr = regtw + c.regtw_off + (int64_t)jr * S;
+  }
+  const uint64_t acc = project_mod(w, d, u, c.box_lo, r.p, mm);
+  alpha[c.mode_off + j] = (int32_t)acc;
+  gam[c.mode_off + j] = (int32_t)mod_barrett(acc * 32u, up, mm);
+  const c2<T> a0 = mk2((T)a.x, (T)a.y);
+  c2<T>* crow = Cm + c.C_off + j;
+  crow[0] = a0;
+  for (int nn = 1; nn < c.n_sets; ++nn) crow[(int64_t)nn * c.Kmax] = cmul(a0, twr[nn - 1]);
+}
+
 template <typename T>
 __global__ void k_tables(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run,
                          const RoundCtl* __restrict__ ctl, Scans sc, c2<T>* __restrict__ tab,
@@ -322,52 +393,13 @@ __global__ void k_tables(int n, const SigCfg* __restrict__ cfg, const SigRun* __
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     if (e < ntab) {
       const int s = find_slot(sc.v[SC_TAB], n, e);
-      const int64_t m = e - sc.v[SC_TAB][s];
-      const int64_t p = run[s].p;
-      c2<T>* t = tab + cfg[s].tab_off;
-      t[m] = unit_root<T>(m, p);
-      // x^2 mod 2p from x^2 mod p: of r and r + p the one with the parity of x (p odd)
-      uint64_t r2;
-      if (p == 2) {
-        r2 = ((uint64_t)m * (uint64_t)m) % 4u;
-      } else {
-        const uint64_t r = mod_barrett((uint64_t)m * (uint64_t)m, (uint64_t)p, run[s].mod_m);
-        r2 = ((r ^ (uint64_t)m) & 1u) ? r + (uint64_t)p : r;
-      }
-      t[p + m] = cconj(unit_root<T>((int64_t)r2, 2 * p));
+      table_entry<T>(run[s].p, run[s].mod_m, e - sc.v[SC_TAB][s], tab + cfg[s].tab_off);
       continue;
     }
     const int64_t em = e - ntab;
     const int s = find_slot(sc.v[SC_MODE], n, em);
-    const int j = (int)(em - sc.v[SC_MODE][s]);
-    const SigCfg& c = cfg[s];
-    const SigRun& r = run[s];
-    const uint64_t up = (uint64_t)r.p, mm = r.mod_m;
-    const int64_t* u = ubuf + c.u_off;
-    const int d = c.d;
-    const int32_t* w;
-    double2 a;
-    const c2<T>* twr;
-    const int S = c.n_sets - 1;   // twiddles per mode: one per shifted set
-    if (j < r.k_sig) {
-      w = sig_w[s] + (int64_t)j * d;
-      a = sig_a[s][j];
-      twr = tw + c.tw_off + (int64_t)j * S;
-    } else {
-      const int jr = j - r.k_sig;
-      w = regw + c.regw_off + (int64_t)jr * d;
-      a = rega[c.rega_off + jr];
-      a.x = -a.x;   // registry modes: f - g
-      a.y = -a.y;
-      twr = regtw + c.regtw_off + (int64_t)jr * S;
-    }
-    const uint64_t acc = project_mod(w, d, u, c.box_lo, r.p, mm);
-    alpha[c.mode_off + j] = (int32_t)acc;
-    gam[c.mode_off + j] = (int32_t)mod_barrett(acc * 32u, up, mm);
-    const c2<T> a0 = mk2((T)a.x, (T)a.y);
-    c2<T>* crow = Cm + c.C_off + j;
-    crow[0] = a0;
-    for (int nn = 1; nn < c.n_sets; ++nn) crow[(int64_t)nn * c.Kmax] = cmul(a0, twr[nn - 1]);
+    mode_entry<T>(cfg[s], run[s], s, (int)(em - sc.v[SC_MODE][s]), ubuf, sig_w, sig_a, tw, regw, rega, regtw, alpha,
+                  gam, Cm);
   }
 }
 
@@ -695,6 +727,26 @@ __device__ __forceinline__ void peel_add(double* y, double gx, double gy) {
   atomicAdd(y + 1, gy);
 }
 
+// Registry mode jr of a signal: add(e, gx, gy) receives -p a e^{2 pi i w . s_n} for bin
+// e = n p + (w . u) mod p of every set n (pruned modes add nothing).
+template <typename T, class Add>
+__device__ __forceinline__ void peel_entry(const SigCfg& c, const SigRun& r, int jr, const int64_t* u,
+                                           const int32_t* __restrict__ regw, const double2* __restrict__ rega,
+                                           const c2<T>* __restrict__ regtw, Add add) {
+  const double2 a = rega[c.rega_off + jr];
+  if (a.x == 0.0 && a.y == 0.0) return;   // pruned
+  const int64_t p = r.p;
+  const int64_t h = (int64_t)project_mod(regw + c.regw_off + (int64_t)jr * c.d, c.d, u, c.box_lo, p, r.mod_m);
+  // -p a, then -p a e^{2 pi i w . s_n} for n >= 1, in T (float policy: the double pipe is narrow)
+  const T px = (T)(-(double)p * a.x), py = (T)(-(double)p * a.y);
+  add(h, px, py);
+  const c2<T>* tw = regtw + c.regtw_off + (int64_t)jr * (c.n_sets - 1);
+  for (int nn = 1; nn < c.n_sets; ++nn) {
+    const c2<T> t = tw[nn - 1];
+    add((int64_t)nn * p + h, px * t.x - py * t.y, px * t.y + py * t.x);
+  }
+}
+
 template <typename T>
 __global__ void k_peel(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run,
                        const int64_t* __restrict__ ubuf, const int32_t* __restrict__ regw,
@@ -705,22 +757,10 @@ __global__ void k_peel(int n, const SigCfg* __restrict__ cfg, const SigRun* __re
   const SigRun& r = run[s];
   if (!r.active || !c.peel_bins) return;
   const int nr = min(r.K_reg, c.reg_cap);
-  const int64_t p = r.p;
   const int64_t* u = ubuf + c.u_off;
   T* Y = reinterpret_cast<T*>(Ybuf + c.Y_off);
-  for (int jr = blockIdx.x * blockDim.x + threadIdx.x; jr < nr; jr += gridDim.x * blockDim.x) {
-    const double2 a = rega[c.rega_off + jr];
-    if (a.x == 0.0 && a.y == 0.0) continue;   // pruned
-    const int64_t h = (int64_t)project_mod(regw + c.regw_off + (int64_t)jr * c.d, c.d, u, c.box_lo, p, r.mod_m);
-    // -p a, then -p a e^{2 pi i w_n / N} for n >= 1, in T (float policy: the double pipe is narrow)
-    const T px = (T)(-(double)p * a.x), py = (T)(-(double)p * a.y);
-    peel_add(Y + 2 * h, px, py);
-    const c2<T>* tw = regtw + c.regtw_off + (int64_t)jr * (c.n_sets - 1);
-    for (int nn = 1; nn < c.n_sets; ++nn) {
-      const c2<T> t = tw[nn - 1];   // e^{2 pi i w_n / N}
-      peel_add(Y + 2 * ((int64_t)nn * p + h), px * t.x - py * t.y, px * t.y + py * t.x);
-    }
-  }
+  for (int jr = blockIdx.x * blockDim.x + threadIdx.x; jr < nr; jr += gridDim.x * blockDim.x)
+    peel_entry<T>(c, r, jr, u, regw, rega, regtw, [&](int64_t e, T gx, T gy) { peel_add(Y + 2 * e, gx, gy); });
 }
 
 // ------------------------------------------------------------------ classification and registry merge
@@ -974,6 +1014,137 @@ __device__ __forceinline__ void warp_add(int* ctr, int v, int key) {
   if ((threadIdx.x & 31) == leader) atomicAdd(ctr, sum);
 }
 
+// Ratio test, read-out, own-bin check and registry merge of one occupied bin h of signal s
+// (Eq. 41-42, Alg. 2 registry update); Y holds the signal's d + 1 transforms (global memory or
+// the fused kernel's shared copy).
+template <typename T>
+__device__ void classify_candidate(const SigCfg& c, SigRun* rp, int s, int64_t h, const c2<T>* Y,
+                                   const int64_t* __restrict__ ubuf, const int32_t* __restrict__ shblk,
+                                   int32_t* regw, double2* rega, c2<T>* regtw, int32_t* hash, const ClassifyOut& co) {
+  const SigRun& r = *rp;
+  const c2<T> y0 = Y[h];
+  const int64_t* u = ubuf + c.u_off;
+  const int32_t* blk = shblk + c.blk_off;
+  const int dd = c.d;
+  const int S = c.n_sets - 1;   // shifted sets: twiddles per set
+  int32_t wk[64];
+  int32_t* wreg = dd <= 64 ? wk : nullptr;   // decoded vector kept for the read-out
+  bool ok;
+  if (c.ratio64) {
+    const double m0d = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y);
+    ok = decode_bin<T, double>(c, r, blk, Y, u, h, (double)y0.x, (double)y0.y, m0d, wreg);
+  } else {
+    ok = decode_bin<T, T>(c, r, blk, Y, u, h, y0.x, y0.y, sqrt(y0.x * y0.x + y0.y * y0.y), wreg);
+  }
+  if (!ok) return;
+  warp_add(&rp->n_acc, 1, s);
+  if (co.count != nullptr) {
+    const int idx = atomicAdd(co.count, 1);
+    if (idx >= co.cap) {
+      atomicOr(co.err, 1);
+      return;
+    }
+    co.h[idx] = (int32_t)h;
+    int32_t* wo = co.w + (int64_t)idx * dd;
+    if (wreg) {
+      for (int l = 0; l < dd; ++l) wo[l] = wk[l];
+    } else if (c.ratio64) {
+      read_coords<T, double>(c, r, blk, Y, u, h, (double)y0.x, (double)y0.y, wo);
+    } else {
+      read_coords<T, T>(c, r, blk, Y, u, h, (T)y0.x, (T)y0.y, wo);
+    }
+    if (c.ratio64) co.a[idx] = coefficient<T, double>(c, r, blk, Y, h, (double)y0.x, (double)y0.y, wo, nullptr);
+    else co.a[idx] = coefficient<T, T>(c, r, blk, Y, h, (T)y0.x, (T)y0.y, wo, nullptr);
+    return;
+  }
+  // ---- merge into the registry: keys accepted in one round are distinct (each lands in its
+  // own bin) and the table never deletes, so a key is present iff met before the first
+  // empty slot of its probe sequence; one writer per key per round.
+  int32_t* rw = regw + c.regw_off;
+  double2* ra = rega + c.rega_off;
+  c2<T>* rt = regtw + c.regtw_off;
+  int32_t* hs = hash + c.hash_off;
+  const double eta_prune2 = r.eta_prune * r.eta_prune;
+  // decoded vector: up to 64 coordinates in registers, else read back from the registry slot
+  int32_t* wv = wk;
+  int scratch_idx = -1;
+  if (dd > 64) {
+    scratch_idx = atomicAdd(&rp->K_reg, 1);
+    if (scratch_idx >= c.reg_cap) {
+      atomicOr(&rp->err, 1);
+      return;
+    }
+    wv = rw + (int64_t)scratch_idx * dd;
+  }
+  if (!wreg) {
+    if (c.ratio64) read_coords<T, double>(c, r, blk, Y, u, h, (double)y0.x, (double)y0.y, wv);
+    else read_coords<T, T>(c, r, blk, Y, u, h, (T)y0.x, (T)y0.y, wv);
+  }
+  // e^{2 pi i w . s_n} of the decoded vector: the registry keeps them (and the float read-out
+  // uses them) so they are formed once
+  c2<T> tn[64];
+  const bool keep_tn = S <= 64;
+  if (keep_tn) {
+    for (int n = 1; n <= S; ++n) tn[n - 1] = shift_root<T>(c, blk, wv, n, true);
+  }
+  double2 a;
+  if (c.ratio64) a = coefficient<T, double>(c, r, blk, Y, h, (double)y0.x, (double)y0.y, wv, nullptr);
+  else a = coefficient<T, T>(c, r, blk, Y, h, (T)y0.x, (T)y0.y, wv, keep_tn ? tn : nullptr);
+  int slot = (int)(hash_key(wv, dd) & (unsigned long long)c.hash_mask);
+  int mine = scratch_idx;
+  bool placed = false, merged = false, past_empty = false;
+  for (int probe = 0; probe <= c.hash_mask; ++probe, slot = (slot + 1) & c.hash_mask) {
+    int cur = __ldcg(&hs[slot]);   // a stale -1 only makes the CAS below fail
+    if (cur < 0) {
+      past_empty = true;   // the key is not in the table
+      if (mine < 0) {
+        mine = atomicAdd(&rp->K_reg, 1);
+        if (mine >= c.reg_cap) {
+          atomicOr(&rp->err, 1);
+          break;
+        }
+        for (int l = 0; l < dd; ++l) rw[(int64_t)mine * dd + l] = wv[l];
+      }
+      ra[mine] = a;
+      for (int n = 1; n <= S; ++n)
+        rt[(int64_t)mine * S + n - 1] = keep_tn ? tn[n - 1] : shift_root<T>(c, blk, wv, n, true);
+      // no fence: nobody reads this entry before the next kernel (see the probe rule below)
+      cur = atomicCAS(&hs[slot], -1, mine);
+      if (cur < 0) {
+        placed = true;
+        break;
+      }
+      continue;   // slot taken by another new key of this round
+    }
+    // keys accepted in one round are distinct (each decodes in its own bin), so a slot claimed
+    // this round (index from the round's start on, or any slot beyond an empty one) holds
+    // another key: only keys of earlier rounds, complete since the last kernel, are compared
+    if (past_empty || cur >= r.reg_start) continue;
+    const int32_t* ow = rw + (int64_t)cur * dd;
+    bool same = true;
+    for (int l = 0; l < dd && same; ++l) same = (ow[l] == wv[l]);
+    if (same) {
+      const double2 old = ra[cur];
+      double2 nw = make_double2(old.x + a.x, old.y + a.y);   // duplicate key: a_R += a
+      const bool was_live = (old.x != 0.0 || old.y != 0.0);
+      const bool live = nw.x * nw.x + nw.y * nw.y >= eta_prune2;   // prune small coefficients
+      if (!live) nw = make_double2(0.0, 0.0);
+      ra[cur] = nw;
+      if (was_live && !live) atomicSub(&rp->n_live, 1);
+      if (!was_live && live) atomicAdd(&rp->n_live, 1);
+      merged = true;
+      break;
+    }
+  }
+  if (merged && scratch_idx >= 0) {
+    // the slot that held the decoded vector stays a zero mode
+    ra[scratch_idx] = make_double2(0.0, 0.0);
+    for (int l = 0; l < S; ++l) rt[(int64_t)scratch_idx * S + l] = mk2((T)0, (T)0);
+  }
+  if (placed) warp_add(&rp->n_live, 1, s);
+  else if (!merged && mine >= 0 && mine < c.reg_cap) atomicOr(&rp->err, 2);   // table full
+}
+
 template <typename T>
 __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, const RoundCtl* __restrict__ ctl,
                            const int2* __restrict__ cand, const c2<T>* __restrict__ Ybuf,
@@ -983,132 +1154,7 @@ __global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, c
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int2 sh = cand[e];
     const int s = sh.x;
-    const int64_t h = sh.y;
-    const SigCfg& c = cfg[s];
-    SigRun* rp = run + s;
-    const SigRun& r = *rp;
-    const c2<T>* Y = Ybuf + c.Y_off;
-    const c2<T> y0 = Y[h];
-    const int64_t* u = ubuf + c.u_off;
-    const int32_t* blk = shblk + c.blk_off;
-    const int dd = c.d;
-    const int S = c.n_sets - 1;   // shifted sets: twiddles per set
-    int32_t wk[64];
-    int32_t* wreg = dd <= 64 ? wk : nullptr;   // decoded vector kept for the read-out
-    bool ok;
-    if (c.ratio64) {
-      const double m0d = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y);
-      ok = decode_bin<T, double>(c, r, blk, Y, u, h, (double)y0.x, (double)y0.y, m0d, wreg);
-    } else {
-      ok = decode_bin<T, T>(c, r, blk, Y, u, h, y0.x, y0.y, sqrt(y0.x * y0.x + y0.y * y0.y), wreg);
-    }
-    if (!ok) continue;
-    warp_add(&rp->n_acc, 1, s);
-    if (co.count != nullptr) {
-      const int idx = atomicAdd(co.count, 1);
-      if (idx >= co.cap) {
-        atomicOr(co.err, 1);
-        continue;
-      }
-      co.h[idx] = (int32_t)h;
-      int32_t* wo = co.w + (int64_t)idx * dd;
-      if (wreg) {
-        for (int l = 0; l < dd; ++l) wo[l] = wk[l];
-      } else if (c.ratio64) {
-        read_coords<T, double>(c, r, blk, Y, u, h, (double)y0.x, (double)y0.y, wo);
-      } else {
-        read_coords<T, T>(c, r, blk, Y, u, h, (T)y0.x, (T)y0.y, wo);
-      }
-      if (c.ratio64) co.a[idx] = coefficient<T, double>(c, r, blk, Y, h, (double)y0.x, (double)y0.y, wo, nullptr);
-      else co.a[idx] = coefficient<T, T>(c, r, blk, Y, h, (T)y0.x, (T)y0.y, wo, nullptr);
-      continue;
-    }
-    // ---- merge into the registry: keys accepted in one round are distinct (each lands in its
-    // own bin) and the table never deletes, so a key is present iff met before the first
-    // empty slot of its probe sequence; one writer per key per round.
-    int32_t* rw = regw + c.regw_off;
-    double2* ra = rega + c.rega_off;
-    c2<T>* rt = regtw + c.regtw_off;
-    int32_t* hs = hash + c.hash_off;
-    const double eta_prune2 = r.eta_prune * r.eta_prune;
-    // decoded vector: up to 64 coordinates in registers, else read back from the registry slot
-    int32_t* wv = wk;
-    int scratch_idx = -1;
-    if (dd > 64) {
-      scratch_idx = atomicAdd(&rp->K_reg, 1);
-      if (scratch_idx >= c.reg_cap) {
-        atomicOr(&rp->err, 1);
-        continue;
-      }
-      wv = rw + (int64_t)scratch_idx * dd;
-    }
-    if (!wreg) {
-      if (c.ratio64) read_coords<T, double>(c, r, blk, Y, u, h, (double)y0.x, (double)y0.y, wv);
-      else read_coords<T, T>(c, r, blk, Y, u, h, (T)y0.x, (T)y0.y, wv);
-    }
-    // e^{2 pi i w . s_n} of the decoded vector: the registry keeps them (and the float read-out
-    // uses them) so they are formed once
-    c2<T> tn[64];
-    const bool keep_tn = S <= 64;
-    if (keep_tn) {
-      for (int n = 1; n <= S; ++n) tn[n - 1] = shift_root<T>(c, blk, wv, n, true);
-    }
-    double2 a;
-    if (c.ratio64) a = coefficient<T, double>(c, r, blk, Y, h, (double)y0.x, (double)y0.y, wv, nullptr);
-    else a = coefficient<T, T>(c, r, blk, Y, h, (T)y0.x, (T)y0.y, wv, keep_tn ? tn : nullptr);
-    int slot = (int)(hash_key(wv, dd) & (unsigned long long)c.hash_mask);
-    int mine = scratch_idx;
-    bool placed = false, merged = false, past_empty = false;
-    for (int probe = 0; probe <= c.hash_mask; ++probe, slot = (slot + 1) & c.hash_mask) {
-      int cur = __ldcg(&hs[slot]);   // a stale -1 only makes the CAS below fail
-      if (cur < 0) {
-        past_empty = true;   // the key is not in the table
-        if (mine < 0) {
-          mine = atomicAdd(&rp->K_reg, 1);
-          if (mine >= c.reg_cap) {
-            atomicOr(&rp->err, 1);
-            break;
-          }
-          for (int l = 0; l < dd; ++l) rw[(int64_t)mine * dd + l] = wv[l];
-        }
-        ra[mine] = a;
-        for (int n = 1; n <= S; ++n)
-          rt[(int64_t)mine * S + n - 1] = keep_tn ? tn[n - 1] : shift_root<T>(c, blk, wv, n, true);
-        // no fence: nobody reads this entry before the next kernel (see the probe rule below)
-        cur = atomicCAS(&hs[slot], -1, mine);
-        if (cur < 0) {
-          placed = true;
-          break;
-        }
-        continue;   // slot taken by another new key of this round
-      }
-      // keys accepted in one round are distinct (each decodes in its own bin), so a slot claimed
-      // this round (index from the round's start on, or any slot beyond an empty one) holds
-      // another key: only keys of earlier rounds, complete since the last kernel, are compared
-      if (past_empty || cur >= r.reg_start) continue;
-      const int32_t* ow = rw + (int64_t)cur * dd;
-      bool same = true;
-      for (int l = 0; l < dd && same; ++l) same = (ow[l] == wv[l]);
-      if (same) {
-        const double2 old = ra[cur];
-        double2 nw = make_double2(old.x + a.x, old.y + a.y);   // duplicate key: a_R += a
-        const bool was_live = (old.x != 0.0 || old.y != 0.0);
-        const bool live = nw.x * nw.x + nw.y * nw.y >= eta_prune2;   // prune small coefficients
-        if (!live) nw = make_double2(0.0, 0.0);
-        ra[cur] = nw;
-        if (was_live && !live) atomicSub(&rp->n_live, 1);
-        if (!was_live && live) atomicAdd(&rp->n_live, 1);
-        merged = true;
-        break;
-      }
-    }
-    if (merged && scratch_idx >= 0) {
-      // the slot that held the decoded vector stays a zero mode
-      ra[scratch_idx] = make_double2(0.0, 0.0);
-      for (int l = 0; l < S; ++l) rt[(int64_t)scratch_idx * S + l] = mk2((T)0, (T)0);
-    }
-    if (placed) warp_add(&rp->n_live, 1, s);
-    else if (!merged && mine >= 0 && mine < c.reg_cap) atomicOr(&rp->err, 2);   // table full
+    classify_candidate<T>(cfg[s], run + s, s, sh.y, Ybuf + cfg[s].Y_off, ubuf, shblk, regw, rega, regtw, hash, co);
   }
 }
 
