@@ -102,6 +102,9 @@ typedef struct {
                         single-mode bin and less affected by rounding */
   int residual;      /* sfft_residual: where g, built from the registry, leaves f each round */
   int shift;         /* sfft_shift: which shifted copies of the line are sampled */
+  int unfused;       /* FP32 policies run each signal's rounds of Bluestein length <= 2048 in one
+                        fused kernel, one block per signal; 1: every round through the batched
+                        kernels (same arithmetic, other summation order of the samples) */
 } sfft_opts;
 
 /* The shifted sample sets (Alg. 2).  COORD (default): one set per coordinate, shifted by e_n / N,
@@ -125,13 +128,14 @@ typedef enum { SFFT_RESIDUAL_BINS = 0, SFFT_RESIDUAL_SAMPLES = 1 } sfft_residual
 #define SFFT_STATS_MAX_ROUNDS 256
 /* kernel classes of sfft_stats.kernel_ms / kernel_launches: round setup and
  * per-prime tables, mode projection, sampling, DFT, classification, registry
- * merge + prune + output */
-#define SFFT_NKCLASS 6
+ * merge + prune + output, and the fused kernel that runs whole rounds on short lines */
+#define SFFT_NKCLASS 7
 typedef struct {
   int rounds;                     /* rounds run, including the final empty one  */
   int converged;                  /* 1 when the last round found no occupied bin */
   int64_t samples;                /* black-box samples, sum over rounds of (d+1) p */
   int64_t terms;                  /* sample terms, sum over rounds of (d+1) p K  */
+  int64_t terms_fused;            /* of these, the terms of rounds run by the fused kernel */
   int64_t p[SFFT_STATS_MAX_ROUNDS];
   int32_t K[SFFT_STATS_MAX_ROUNDS];        /* modes summed per sample: k, or k + |R| under SAMPLES */
   int32_t accepted[SFFT_STATS_MAX_ROUNDS]; /* bins accepted in the round */

@@ -162,6 +162,7 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
   P->stream = (cudaStream_t)stream;
   P->profile = o.profile != 0;
   P->graph = o.graph != 0;
+  D.fuse = o.unfused ? 0 : 1;
 
   // ---- prime schedule
   if (ps) {

@@ -21,7 +21,9 @@
 #include "engine_kernels.cuh"
 #include "fft_reg.cuh"
 #include "fft_smem.cuh"
+#include "fused.cuh"
 #include "noise.cuh"
+#include "round_steps.cuh"
 #include "sample_tile.cuh"
 
 namespace sfft {
@@ -71,137 +73,10 @@ __global__ void k_bind_tw(int n, const SigCfg* __restrict__ cfg, const SigRun* _
 
 // ------------------------------------------------------------------ plan
 
-struct PlanArgs {
-  int n;
-  int64_t part_cap;
-  int n_sm;
-  int single_max_logL;
-  int force;            // step calls: slot 0 uses force_p and the direction already in its u slot
-  int64_t force_p;
-  int force_K;          // modes bound for the step call
-  int use_cond;
-  cudaGraphConditionalHandle cond;
-  int hard_rounds;      // stop the device loop after this many rounds
-};
-
-__device__ __forceinline__ int ceil_log2(int64_t v) {
-  int r = 0;
-  while ((1LL << r) < v) ++r;
-  return r;
-}
-
-// Smallest length m 2^a >= max(n, 32) with m in {1, 3, 5}: the cyclic convolution of Bluestein's
-// DFT only needs n = 2p - 1 points, and these lengths factor into the FFT's radices.
-__device__ __forceinline__ int bluestein_length(int64_t n) {
-  n = max(n, (int64_t)32);
-  int64_t best = (int64_t)1 << ceil_log2(n);
-  for (int m = 3; m <= 5; m += 2) {
-    const int64_t L = (int64_t)m << ceil_log2((n + m - 1) / m);
-    if (L < best) best = L;
-  }
-  return (int)best;
-}
-
-__device__ __forceinline__ void big_geom(int logL, int* M1, int* M2, int* CT, int* RT) {
-  const int l1 = logL / 2, l2 = logL - l1;
-  *M1 = 1 << l1;
-  *M2 = 1 << l2;
-  *CT = min(*M2, max(1, kBigColElems / *M1));
-  *RT = min(*M1, max(1, kBigRowElems / *M2));
-}
-
-// Tables of the prime rule and the line directions.
-struct PrimeTables {
-  const int32_t* ptab;
-  int n_ptab;
-  const int32_t* pfirst;
-  int64_t pfirst_n;
-  const int64_t* dirs;
-  const int64_t* plist;
-};
-
-// Round setup of one signal (Alg. 2): the stop rule, then for an active signal the next round's
-// prime, line direction (written to its u slot), Bluestein lengths and sampling geometry, and
-// the statistics of the round just finished (first slot only).
-template <typename T>
-__device__ void plan_signal(const PlanArgs& a, const SigCfg& c, SigRun& r, const PrimeTables& pt, int64_t* ubuf,
-                            HistRec* hist, bool first_slot) {
-  if (first_slot && hist != nullptr && r.round >= 1 && r.round <= SFFT_STATS_MAX_ROUNDS) {
-    hist[r.round - 1].accepted = r.n_acc;
-    hist[r.round - 1].live = r.n_live;
-  }
-  if (r.active && !a.force) {
-    if (r.round > 0 && !r.any_occupied) {
-      r.active = 0;                        // the residual is empty: done
-      r.status = SFFT_OK;
-    } else if (r.err) {
-      r.active = 0;
-      r.status = SFFT_ERR_CAPACITY;
-    } else if (r.round >= c.max_rounds || r.round >= a.hard_rounds) {
-      r.active = 0;
-      r.status = SFFT_ERR_NOT_CONVERGED;
-    }
-  }
-  if (r.active) {
-    const int i = r.round + 1;
-    int64_t p;
-    if (a.force) {
-      p = a.force_p;
-    } else if (c.n_primes > 0) {
-      p = pt.plist[c.primes_off + (i - 1) % c.n_primes];
-    } else {
-      const int64_t kstar = max((int64_t)c.k - r.n_live, (int64_t)1);
-      const int64_t lo = max(max((int64_t)c.c * kstar, c.p_min), (int64_t)2);
-      // pfirst[v] = index of the smallest prime >= v, so the i-th prime >= lo is one lookup away
-      const int64_t idx = lo < pt.pfirst_n ? (int64_t)pt.pfirst[lo] + i - 1 : (int64_t)pt.n_ptab;
-      p = idx < pt.n_ptab ? pt.ptab[idx] : -1;
-    }
-    if (p < 2 || p > c.p_max) {
-      r.active = 0;
-      r.status = SFFT_ERR_INVALID_ARG;
-    } else {
-      r.p = p;
-      r.mod_m = ~0ull / (uint64_t)p;
-      r.round = i;
-      if (!a.force) {
-        const int di = i % c.n_dirs;
-        for (int l = 0; l < c.d; ++l) {
-          int64_t v = pt.dirs[c.dirs_off + (int64_t)di * c.d + l] % p;
-          ubuf[c.u_off + l] = v < 0 ? v + p : v;
-        }
-      }
-      const int K = a.force ? a.force_K : sampled_modes(c, r);
-      r.logL = max(ceil_log2(2 * p - 1), 5);   // at least 32 points
-      r.L = bluestein_length(2 * p - 1);
-      r.big = r.L > (1 << a.single_max_logL);
-      r.groups = (c.n_sets + kMaxSetGroup - 1) / kMaxSetGroup;
-      r.gsize = (c.n_sets + r.groups - 1) / r.groups;
-      {
-        // tiles cover the half line 0 <= x < H (each x also gives p - x); a tile's warps
-        // split into mode groups when H is shorter than the tile
-        const int64_t H = p / 2 + 1;
-        const int rowx = 32 * row_pairs(r.gsize);
-        r.mgroups = (sizeof(T) != 4) ? 1 : (H <= rowx ? 8 : H <= 2 * rowx ? 4 : H <= 4 * rowx ? 2 : 1);
-        const int tx = tile_x(r.gsize) / r.mgroups;
-        r.n_xt = (int)((H + tx - 1) / tx);
-      }
-      r.chunks = K > 0 ? (K + kSampleChunk - 1) / kSampleChunk : 1;
-      r.any_occupied = 0;
-      r.n_acc = 0;
-      r.reg_start = r.K_reg;
-      r.maxy0_bits = 0ull;
-      r.samples += (int64_t)c.n_sets * p;
-      r.terms += (int64_t)c.n_sets * p * K;
-      if (first_slot && hist != nullptr && i <= SFFT_STATS_MAX_ROUNDS) {
-        hist[i - 1].p = p;
-        hist[i - 1].K = K;
-        hist[i - 1].accepted = 0;
-        hist[i - 1].live = r.n_live;
-      }
-    }
-  }
-}
-
+// Plans the round of every signal (plan_signal; a signal whose next round the fused kernel
+// has planned keeps it), then the work counts of the batched kernels and their exclusive
+// scans over the signals.  Sets the graph conditions: some signal active (the round loop),
+// some batched work, some fused round planned.
 template <typename T>
 __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg* __restrict__ cfg, SigRun* run,
                                                        RoundCtl* ctl, Scans sc, const int32_t* __restrict__ ptab,
@@ -211,21 +86,25 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
                                                        HistRec* hist) {
   __shared__ int s_S;
   const int n = a.n;
-  int64_t tiles = 0, active = 0;
+  int64_t tiles = 0, active = 0, fused = 0;
   // pass 1: stop rule and round parameters of every signal
   const PrimeTables pt{ptab, n_ptab, pfirst, pfirst_n, dirs, plist};
   for (int s = threadIdx.x; s < n; s += blockDim.x) {
     SigRun r = run[s];
-    plan_signal<T>(a, cfg[s], r, pt, ubuf, hist, s == 0);
-    run[s] = r;
+    if (!(r.active && r.fused)) {
+      plan_signal<T>(a, cfg[s], r, pt, ubuf, hist, s == 0);
+      run[s] = r;
+    }
     if (r.active) {
-      tiles += (int64_t)r.n_xt * r.groups;
       active += 1;
+      if (r.fused) fused += 1;
+      else tiles += (int64_t)r.n_xt * r.groups;
     }
   }
   __syncthreads();
   const int64_t tot_tiles = block_sum(tiles);
   const int64_t tot_active = block_sum(active);
+  const int64_t tot_fused = block_sum(fused);
   // mode splits: enough sampling items to fill the GPU, within the partial-sum arena
   if (threadIdx.x == 0) {
     const int64_t target = 8LL * a.n_sm;
@@ -238,7 +117,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     int64_t part = 0;
     for (int s = threadIdx.x; s < n; s += blockDim.x) {
       const SigRun& r = run[s];
-      if (!r.active) continue;
+      if (!r.active || r.fused) continue;
       part += (int64_t)min(S, r.chunks) * cfg[s].n_sets * r.p;
     }
     const int64_t tot = block_sum(part);
@@ -257,9 +136,11 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     int64_t v[kNumScans + 1];
     for (int q = 0; q <= kNumScans; ++q) v[q] = 0;
     SigRun r;
+    bool batched = false;   // active and not left to the fused kernel
     if (s < n) {
       r = run[s];
-      if (r.active) {
+      batched = r.active && !r.fused;
+      if (batched) {
         const SigCfg& c = cfg[s];
         const int K = a.force ? a.force_K : sampled_modes(c, r);
         int sp = min(S, r.chunks);
@@ -287,7 +168,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     block_scan_excl<kNumScans + 1>(v, tot);
     if (s < n) {
       for (int q = 0; q < kNumScans; ++q) sc.v[q][s] = carry[q] + v[q];
-      if (r.active) {
+      if (batched) {
         r.part_off = part_carry + v[kNumScans];
         run[s] = r;
       }
@@ -318,8 +199,16 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     c.n_filt_s = carry[SC_FILT_S];
     c.ctr_rows = c.ctr_filt = 0ull;
     c.n_cand = 0ull;
+    c.n_fused_next = 0ull;
+    const bool batched = tot_active > tot_fused;
+    c.bodies_batched = ctl->bodies_batched + (batched ? 1 : 0);
+    c.fused_iters = ctl->fused_iters;
     *ctl = c;
-    if (a.use_cond) cudaGraphSetConditional(a.cond, tot_active > 0 ? 1u : 0u);
+    if (a.use_cond) {
+      cudaGraphSetConditional(a.cond, tot_active > 0 ? 1u : 0u);
+      cudaGraphSetConditional(a.cond_batch, batched ? 1u : 0u);
+      if (a.fuse) cudaGraphSetConditional(a.cond_fused, tot_fused > 0 ? 1u : 0u);   // handle exists
+    }
   }
 }
 
@@ -328,58 +217,6 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
 // Per-prime tables (W, chirp) and the round's mode projections: for every mode j of f (+a)
 // and of the registry (-a): alpha_j = (w_j . u) mod p, ga_j = 32 alpha_j mod p and
 // C[n][j] = a_j e^{2 pi i w_{j,n} / N} (n >= 1), C[0][j] = a_j.
-// W[m] = e^{2 pi i m / p} and chirp[m] = e^{-pi i m^2 / p} of one index m < p of a signal's tables
-template <typename T>
-__device__ __forceinline__ void table_entry(int64_t p, unsigned long long mod_m, int64_t m, c2<T>* t) {
-  t[m] = unit_root<T>(m, p);
-  // x^2 mod 2p from x^2 mod p: of r and r + p the one with the parity of x (p odd)
-  uint64_t r2;
-  if (p == 2) {
-    r2 = ((uint64_t)m * (uint64_t)m) % 4u;
-  } else {
-    const uint64_t r = mod_barrett((uint64_t)m * (uint64_t)m, (uint64_t)p, mod_m);
-    r2 = ((r ^ (uint64_t)m) & 1u) ? r + (uint64_t)p : r;
-  }
-  t[p + m] = cconj(unit_root<T>((int64_t)r2, 2 * p));
-}
-
-// The round's projection of mode j of a signal (black box for j < k, registry with -a after):
-// alpha_j = (w_j . u) mod p, ga_j = 32 alpha_j mod p and C[n][j] = a_j e^{2 pi i w_j . s_n}.
-template <typename T>
-__device__ __forceinline__ void mode_entry(const SigCfg& c, const SigRun& r, int s, int j, const int64_t* __restrict__ ubuf,
-                                           const int32_t* const* __restrict__ sig_w,
-                                           const double2* const* __restrict__ sig_a, const c2<T>* __restrict__ tw,
-                                           const int32_t* __restrict__ regw, const double2* __restrict__ rega,
-                                           const c2<T>* __restrict__ regtw, int32_t* __restrict__ alpha,
-                                           int32_t* __restrict__ gam, c2<T>* __restrict__ Cm) {
-  const uint64_t up = (uint64_t)r.p, mm = r.mod_m;
-  const int64_t* u = ubuf + c.u_off;
-  const int d = c.d;
-  const int32_t* w;
-  double2 a;
-  const c2<T>* twr;
-  const int S = c.n_sets - 1;   // twiddles per mode: one per shifted set
-  if (j < r.k_sig) {
-    w = sig_w[s] + (int64_t)j * d;
-    a = sig_a[s][j];
-    twr = tw + c.tw_off + (int64_t)j * S;
-  } else {
-    const int jr = j - r.k_sig;
-    w = regw + c.regw_off + (int64_t)jr * d;
-    a = rega[c.rega_off + jr];
-    a.x = -a.x;   // registry modes: f - g
-    a.y = -a.y;
-    twr = regtw + c.regtw_off + (int64_t)jr * S;
-  }
-  const uint64_t acc = project_mod(w, d, u, c.box_lo, r.p, mm);
-  alpha[c.mode_off + j] = (int32_t)acc;
-  gam[c.mode_off + j] = (int32_t)mod_barrett(acc * 32u, up, mm);
-  const c2<T> a0 = mk2((T)a.x, (T)a.y);
-  c2<T>* crow = Cm + c.C_off + j;
-  crow[0] = a0;
-  for (int nn = 1; nn < c.n_sets; ++nn) crow[(int64_t)nn * c.Kmax] = cmul(a0, twr[nn - 1]);
-}
-
 template <typename T>
 __global__ void k_tables(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run,
                          const RoundCtl* __restrict__ ctl, Scans sc, c2<T>* __restrict__ tab,
@@ -450,27 +287,6 @@ __global__ void k_reduce(const SigCfg* __restrict__ cfg, const SigRun* __restric
 }
 
 // ------------------------------------------------------------------ DFT, one block per row
-
-template <typename T>
-__device__ __forceinline__ c2<T> filter_value(int64_t x, int64_t p, int64_t L, const c2<T>* chirp) {
-  if (x < p) return cconj(chirp[x]);
-  if (x > L - p) return cconj(chirp[L - x]);
-  return mk2((T)0, (T)0);
-}
-
-template <typename T>
-__device__ __forceinline__ c2<T> sum_splits(const c2<T>* __restrict__ part, const SigRun& r, int n_sets, int row,
-                                            int64_t x) {
-  c2<T> acc = part[r.part_off + (int64_t)row * r.p + x];
-  for (int q = 1; q < r.splits; ++q) acc = cadd(acc, part[r.part_off + ((int64_t)q * n_sets + row) * r.p + x]);
-  return acc;
-}
-
-template <typename T>
-__device__ __forceinline__ void max_abs_to(unsigned long long* dst, double v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0 && v > 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(v));
-}
 
 // spectrum of the Bluestein filter b[m] = conj(chirp[|m|]), |m| < p, one block per signal
 template <typename T>
@@ -714,39 +530,8 @@ __global__ void k_bigC(int n, const SigCfg* __restrict__ cfg, SigRun* run, const
 
 // ------------------------------------------------------------------ registry removed in the bin domain
 
-// Residual BINS: each live registry mode (w, a) of an active signal takes p a e^{2 pi i w_n / N}
-// off bin (w . u) mod p of set n (p a off set 0).  That is the transform of the mode's samples
-// (sum over x of W^{(alpha - h) x} is p at h = alpha and 0 elsewhere), so f's transform minus
-// these is the transform of f - g (Alg. 2, by linearity).  Modes sharing a bin add in any order.
-// y += (gx, gy) atomically: one 64-bit vector atomic in float, two in double
-__device__ __forceinline__ void peel_add(float* y, float gx, float gy) {
-  atomicAdd(reinterpret_cast<float2*>(y), make_float2(gx, gy));
-}
-__device__ __forceinline__ void peel_add(double* y, double gx, double gy) {
-  atomicAdd(y, gx);
-  atomicAdd(y + 1, gy);
-}
-
-// Registry mode jr of a signal: add(e, gx, gy) receives -p a e^{2 pi i w . s_n} for bin
-// e = n p + (w . u) mod p of every set n (pruned modes add nothing).
-template <typename T, class Add>
-__device__ __forceinline__ void peel_entry(const SigCfg& c, const SigRun& r, int jr, const int64_t* u,
-                                           const int32_t* __restrict__ regw, const double2* __restrict__ rega,
-                                           const c2<T>* __restrict__ regtw, Add add) {
-  const double2 a = rega[c.rega_off + jr];
-  if (a.x == 0.0 && a.y == 0.0) return;   // pruned
-  const int64_t p = r.p;
-  const int64_t h = (int64_t)project_mod(regw + c.regw_off + (int64_t)jr * c.d, c.d, u, c.box_lo, p, r.mod_m);
-  // -p a, then -p a e^{2 pi i w . s_n} for n >= 1, in T (float policy: the double pipe is narrow)
-  const T px = (T)(-(double)p * a.x), py = (T)(-(double)p * a.y);
-  add(h, px, py);
-  const c2<T>* tw = regtw + c.regtw_off + (int64_t)jr * (c.n_sets - 1);
-  for (int nn = 1; nn < c.n_sets; ++nn) {
-    const c2<T> t = tw[nn - 1];
-    add((int64_t)nn * p + h, px * t.x - py * t.y, px * t.y + py * t.x);
-  }
-}
-
+// Residual BINS (peel_entry): every live registry mode of an active signal leaves its bin of
+// each set, one thread per mode.
 template <typename T>
 __global__ void k_peel(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run,
                        const int64_t* __restrict__ ubuf, const int32_t* __restrict__ regw,
@@ -755,7 +540,7 @@ __global__ void k_peel(int n, const SigCfg* __restrict__ cfg, const SigRun* __re
   if (s >= n) return;
   const SigCfg& c = cfg[s];
   const SigRun& r = run[s];
-  if (!r.active || !c.peel_bins) return;
+  if (!r.active || r.fused || !c.peel_bins) return;
   const int nr = min(r.K_reg, c.reg_cap);
   const int64_t* u = ubuf + c.u_off;
   T* Y = reinterpret_cast<T*>(Ybuf + c.Y_off);
@@ -764,180 +549,6 @@ __global__ void k_peel(int n, const SigCfg* __restrict__ cfg, const SigRun* __re
 }
 
 // ------------------------------------------------------------------ classification and registry merge
-
-__device__ __forceinline__ unsigned long long hash_key(const int32_t* w, int d) {
-  unsigned long long h = 0x9E3779B97F4A7C15ull ^ (unsigned long long)d;
-  for (int l = 0; l < d; ++l) {
-    h ^= (unsigned long long)(uint32_t)w[l];
-    h *= 0xff51afd7ed558ccdull;
-    h ^= h >> 32;
-  }
-  h ^= h >> 29;
-  h *= 0xc4ceb9fe1a85ec53ull;
-  h ^= h >> 32;
-  return h;
-}
-
-// Arg(Y_n / Y_0) in [-pi, pi) read as N Arg / (2 pi); false when farther than delta from an integer.
-template <typename R>
-__device__ __forceinline__ bool read_coord(R ynx, R yny, R y0x, R y0y, int64_t N, int box_lo, R delta,
-                                           int64_t* w_out) {
-  const R re = ynx * y0x + yny * y0y;   // Y_n conj(Y_0)
-  const R im = yny * y0x - ynx * y0y;
-  const R pi = (R)3.14159265358979323846;
-  R phi = atan2(im, re);
-  if (phi >= pi) phi -= (R)2 * pi;
-  const R v = (R)N * phi / ((R)2 * pi);
-  const R rr = rint(v);
-  if (!(fabs(v - rr) <= delta)) return false;
-  // |rr| <= N / 2 and -N <= box_lo <= 0, so rr - box_lo lies in [-N/2, 3N/2]: one wrap
-  int64_t wn = (int64_t)rr - box_lo;
-  if (wn < 0) wn += N;
-  else if (wn >= N) wn -= N;
-  *w_out = wn + box_lo;
-  return true;
-}
-
-// Block form: Arg(Y_n / Y_0) read as the block's unwrapped frequency w~ = 2 N^{d1} Arg / (2 pi),
-// taken in the window [W_lo, W_lo + N^{d1}) of the box's unwrapped values (W_lo that of
-// (box_lo, ..., box_lo)) and split into its d1 base-N digits, lowest first; false when farther
-// than delta from an integer or outside the window.
-template <typename R>
-__device__ __forceinline__ bool read_block(R ynx, R yny, R y0x, R y0y, int64_t N, int size, int box_lo, R delta,
-                                           int32_t* digits) {
-  const R re = ynx * y0x + yny * y0y;
-  const R im = yny * y0x - ynx * y0y;
-  const R pi = (R)3.14159265358979323846;
-  R phi = atan2(im, re);
-  if (phi >= pi) phi -= (R)2 * pi;
-  int64_t span = 1, ones = 0;   // N^{d1} and 1 + N + ... + N^{d1-1}
-  for (int r = 0; r < size; ++r) {
-    ones += span;
-    span *= N;
-  }
-  const int64_t q = 2 * span;
-  const R v = (R)q * phi / ((R)2 * pi);
-  const R rr = rint(v);
-  if (!(fabs(v - rr) <= delta)) return false;
-  int64_t t = ((int64_t)rr - (int64_t)box_lo * ones) % q;
-  if (t < 0) t += q;
-  if (t >= span) return false;
-  for (int r = 0; r < size; ++r) {
-    digits[r] = (int32_t)(t % N) + box_lo;
-    t /= N;
-  }
-  return true;
-}
-
-// Read-out of shifted set n (1-based) of an occupied bin: the coordinate it fixes (coordinate
-// form) or the d1 coordinates of block n (block form) go to w (if not null), and their
-// (w_l - box_lo) u_l are added to *bin mod p.
-template <typename R>
-__device__ __forceinline__ bool read_set(const SigCfg& c, const SigRun& r, const int32_t* __restrict__ blk, int n,
-                                         R ynx, R yny, R y0x, R y0y, const int64_t* u, uint64_t* bin, int32_t* w) {
-  const uint64_t up = (uint64_t)r.p;
-  if (!c.shift_block) {
-    int64_t wn;
-    if (!read_coord<R>(ynx, yny, y0x, y0y, c.N, c.box_lo, (R)c.delta, &wn)) return false;
-    if (w) w[n - 1] = (int32_t)wn;
-    *bin = mod_barrett((uint64_t)(wn - c.box_lo) * (uint64_t)u[n - 1] + *bin, up, r.mod_m);
-    return true;
-  }
-  const int b = blk[2 * (n - 1)], size = blk[2 * (n - 1) + 1];
-  int32_t dg[32];
-  if (size > 32 || !read_block<R>(ynx, yny, y0x, y0y, c.N, size, c.box_lo, (R)c.delta, dg)) return false;
-  for (int t = 0; t < size; ++t) {
-    if (w) w[b + t] = dg[t];
-    *bin = mod_barrett((uint64_t)(dg[t] - c.box_lo) * (uint64_t)u[b + t] + *bin, up, r.mod_m);
-  }
-  return true;
-}
-
-struct ClassifyOut {   // step calls: accepted bins are appended here instead of merged
-  int32_t* h;
-  int32_t* w;
-  double2* a;
-  int cap;
-  int* count;
-  int* err;
-  double eta_override;
-};
-
-// Eq. 42 ratio test and Eq. 7 read-out of sets 1..d of an occupied bin.  The sets' values are
-// fetched eight at a time so that their loads overlap.  Writes w_n to w_out (if not null) and
-// returns whether every set passes and (w . u) mod p is the bin itself.
-template <typename T, typename R>
-__device__ bool decode_bin(const SigCfg& c, const SigRun& r, const int32_t* __restrict__ blk, const c2<T>* Y,
-                           const int64_t* u, int64_t h, R y0x, R y0y, R m0, int32_t* w_out) {
-  constexpr int kB = 8;
-  const int64_t p = r.p;
-  const uint64_t up = (uint64_t)p;
-  const int S = c.n_sets - 1;
-  uint64_t bin = 0;
-  for (int n0 = 1; n0 <= S; n0 += kB) {
-    c2<T> yv[kB];
-#pragma unroll
-    for (int i = 0; i < kB; ++i) yv[i] = n0 + i <= S ? Y[(int64_t)(n0 + i) * p + h] : mk2((T)0, (T)0);
-#pragma unroll
-    for (int i = 0; i < kB; ++i) {
-      const int n = n0 + i;
-      if (n > S) break;
-      const R ynx = (R)yv[i].x, yny = (R)yv[i].y;
-      const R mn = sqrt(ynx * ynx + yny * yny);
-      if (!(fabs(mn / m0 - (R)1) < (R)c.tau)) return false;   // Eq. 42
-      if (!read_set<R>(c, r, blk, n, ynx, yny, y0x, y0y, u, &bin, w_out)) return false;
-    }
-  }
-  uint64_t usum = 0;
-  for (int l = 0; l < c.d; ++l) usum += (uint64_t)u[l];
-  const int64_t blm = ((int64_t)c.box_lo % p + p) % p;
-  bin = mod_barrett(bin + mod_barrett((uint64_t)blm * mod_barrett(usum, up, r.mod_m), up, r.mod_m), up, r.mod_m);
-  return (int64_t)bin == h;
-}
-
-// The read-out vector of an accepted bin, computed again (for vectors longer than the
-// decoder's register copy).
-template <typename T, typename R>
-__device__ void read_coords(const SigCfg& c, const SigRun& r, const int32_t* __restrict__ blk, const c2<T>* Y,
-                            const int64_t* u, int64_t h, R y0x, R y0y, int32_t* w_out) {
-  uint64_t bin = 0;
-  for (int n = 1; n < c.n_sets; ++n) {
-    const c2<T> yn = Y[(int64_t)n * r.p + h];
-    read_set<R>(c, r, blk, n, (R)yn.x, (R)yn.y, y0x, y0y, u, &bin, w_out);
-  }
-}
-
-// Coefficient estimate of an accepted bin with read-out vector w (Eq. 41).  With coef_mean
-// the estimate is the mean over the sets of Y_n[h] e^{-2 pi i w . s_n} / p: for a bin
-// holding one mode every term equals a exactly, and the mean averages the sets' independent
-// rounding (and the leakage of other modes' residuals, whose phases differ across the sets).
-template <typename T, typename R>
-__device__ double2 coefficient(const SigCfg& c, const SigRun& r, const int32_t* __restrict__ blk, const c2<T>* Y,
-                               int64_t h, R y0x, R y0y, const int32_t* w, const c2<T>* tn) {
-  if (!c.coef_mean) {
-    if (sizeof(R) == 4) {
-      const float scale = 1.0f / (float)r.p;
-      return make_double2((double)((float)y0x * scale), (double)((float)y0y * scale));
-    }
-    const double scale = 1.0 / (double)r.p;
-    return make_double2((double)y0x * scale, (double)y0y * scale);
-  }
-  R ax = y0x, ay = y0y;
-  for (int n = 1; n < c.n_sets; ++n) {
-    const c2<T> yn = Y[(int64_t)n * r.p + h];
-    c2<R> t;   // e^{2 pi i w . s_n}
-    if (sizeof(R) == sizeof(T) && tn != nullptr) t = mk2((R)tn[n - 1].x, (R)tn[n - 1].y);
-    else t = shift_root<R>(c, blk, w, n, true);
-    ax += (R)yn.x * t.x + (R)yn.y * t.y;     // Y_n conj(t)
-    ay += (R)yn.y * t.x - (R)yn.x * t.y;
-  }
-  if (sizeof(R) == 4) {   // float read-out: scale in float (the double pipe of this GPU is narrow)
-    const float scale = 1.0f / ((float)r.p * (float)c.n_sets);
-    return make_double2((double)((float)ax * scale), (double)((float)ay * scale));
-  }
-  const double scale = 1.0 / ((double)r.p * (double)c.n_sets);
-  return make_double2((double)ax * scale, (double)ay * scale);
-}
 
 // Bins of the round whose set-0 magnitude is above the empty-bin level, appended to the
 // candidate list (warp-aggregated); also the first round's reference amplitude A_ref and the
@@ -1003,146 +614,6 @@ __global__ void __launch_bounds__(256) k_occupied(int n, const SigCfg* __restric
     if (occ) cand[tile_base + warp_cnt[wid] + __popc(mask & ((1u << lane) - 1u))] = make_int2(s, (int)h);
     __syncthreads();   // warp_cnt and tile_base are reused by the next tile
   }
-}
-
-// *ctr += v from every active lane, one atomic per group of lanes that share key (a signal)
-__device__ __forceinline__ void warp_add(int* ctr, int v, int key) {
-  const unsigned grp = __match_any_sync(__activemask(), key);
-  const int leader = __ffs(grp) - 1;
-  int sum = 0;
-  for (unsigned m = grp; m; m &= m - 1) sum += __shfl_sync(grp, v, __ffs(m) - 1);
-  if ((threadIdx.x & 31) == leader) atomicAdd(ctr, sum);
-}
-
-// Ratio test, read-out, own-bin check and registry merge of one occupied bin h of signal s
-// (Eq. 41-42, Alg. 2 registry update); Y holds the signal's d + 1 transforms (global memory or
-// the fused kernel's shared copy).
-template <typename T>
-__device__ void classify_candidate(const SigCfg& c, SigRun* rp, int s, int64_t h, const c2<T>* Y,
-                                   const int64_t* __restrict__ ubuf, const int32_t* __restrict__ shblk,
-                                   int32_t* regw, double2* rega, c2<T>* regtw, int32_t* hash, const ClassifyOut& co) {
-  const SigRun& r = *rp;
-  const c2<T> y0 = Y[h];
-  const int64_t* u = ubuf + c.u_off;
-  const int32_t* blk = shblk + c.blk_off;
-  const int dd = c.d;
-  const int S = c.n_sets - 1;   // shifted sets: twiddles per set
-  int32_t wk[64];
-  int32_t* wreg = dd <= 64 ? wk : nullptr;   // decoded vector kept for the read-out
-  bool ok;
-  if (c.ratio64) {
-    const double m0d = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y);
-    ok = decode_bin<T, double>(c, r, blk, Y, u, h, (double)y0.x, (double)y0.y, m0d, wreg);
-  } else {
-    ok = decode_bin<T, T>(c, r, blk, Y, u, h, y0.x, y0.y, sqrt(y0.x * y0.x + y0.y * y0.y), wreg);
-  }
-  if (!ok) return;
-  warp_add(&rp->n_acc, 1, s);
-  if (co.count != nullptr) {
-    const int idx = atomicAdd(co.count, 1);
-    if (idx >= co.cap) {
-      atomicOr(co.err, 1);
-      return;
-    }
-    co.h[idx] = (int32_t)h;
-    int32_t* wo = co.w + (int64_t)idx * dd;
-    if (wreg) {
-      for (int l = 0; l < dd; ++l) wo[l] = wk[l];
-    } else if (c.ratio64) {
-      read_coords<T, double>(c, r, blk, Y, u, h, (double)y0.x, (double)y0.y, wo);
-    } else {
-      read_coords<T, T>(c, r, blk, Y, u, h, (T)y0.x, (T)y0.y, wo);
-    }
-    if (c.ratio64) co.a[idx] = coefficient<T, double>(c, r, blk, Y, h, (double)y0.x, (double)y0.y, wo, nullptr);
-    else co.a[idx] = coefficient<T, T>(c, r, blk, Y, h, (T)y0.x, (T)y0.y, wo, nullptr);
-    return;
-  }
-  // ---- merge into the registry: keys accepted in one round are distinct (each lands in its
-  // own bin) and the table never deletes, so a key is present iff met before the first
-  // empty slot of its probe sequence; one writer per key per round.
-  int32_t* rw = regw + c.regw_off;
-  double2* ra = rega + c.rega_off;
-  c2<T>* rt = regtw + c.regtw_off;
-  int32_t* hs = hash + c.hash_off;
-  const double eta_prune2 = r.eta_prune * r.eta_prune;
-  // decoded vector: up to 64 coordinates in registers, else read back from the registry slot
-  int32_t* wv = wk;
-  int scratch_idx = -1;
-  if (dd > 64) {
-    scratch_idx = atomicAdd(&rp->K_reg, 1);
-    if (scratch_idx >= c.reg_cap) {
-      atomicOr(&rp->err, 1);
-      return;
-    }
-    wv = rw + (int64_t)scratch_idx * dd;
-  }
-  if (!wreg) {
-    if (c.ratio64) read_coords<T, double>(c, r, blk, Y, u, h, (double)y0.x, (double)y0.y, wv);
-    else read_coords<T, T>(c, r, blk, Y, u, h, (T)y0.x, (T)y0.y, wv);
-  }
-  // e^{2 pi i w . s_n} of the decoded vector: the registry keeps them (and the float read-out
-  // uses them) so they are formed once
-  c2<T> tn[64];
-  const bool keep_tn = S <= 64;
-  if (keep_tn) {
-    for (int n = 1; n <= S; ++n) tn[n - 1] = shift_root<T>(c, blk, wv, n, true);
-  }
-  double2 a;
-  if (c.ratio64) a = coefficient<T, double>(c, r, blk, Y, h, (double)y0.x, (double)y0.y, wv, nullptr);
-  else a = coefficient<T, T>(c, r, blk, Y, h, (T)y0.x, (T)y0.y, wv, keep_tn ? tn : nullptr);
-  int slot = (int)(hash_key(wv, dd) & (unsigned long long)c.hash_mask);
-  int mine = scratch_idx;
-  bool placed = false, merged = false, past_empty = false;
-  for (int probe = 0; probe <= c.hash_mask; ++probe, slot = (slot + 1) & c.hash_mask) {
-    int cur = __ldcg(&hs[slot]);   // a stale -1 only makes the CAS below fail
-    if (cur < 0) {
-      past_empty = true;   // the key is not in the table
-      if (mine < 0) {
-        mine = atomicAdd(&rp->K_reg, 1);
-        if (mine >= c.reg_cap) {
-          atomicOr(&rp->err, 1);
-          break;
-        }
-        for (int l = 0; l < dd; ++l) rw[(int64_t)mine * dd + l] = wv[l];
-      }
-      ra[mine] = a;
-      for (int n = 1; n <= S; ++n)
-        rt[(int64_t)mine * S + n - 1] = keep_tn ? tn[n - 1] : shift_root<T>(c, blk, wv, n, true);
-      // no fence: nobody reads this entry before the next kernel (see the probe rule below)
-      cur = atomicCAS(&hs[slot], -1, mine);
-      if (cur < 0) {
-        placed = true;
-        break;
-      }
-      continue;   // slot taken by another new key of this round
-    }
-    // keys accepted in one round are distinct (each decodes in its own bin), so a slot claimed
-    // this round (index from the round's start on, or any slot beyond an empty one) holds
-    // another key: only keys of earlier rounds, complete since the last kernel, are compared
-    if (past_empty || cur >= r.reg_start) continue;
-    const int32_t* ow = rw + (int64_t)cur * dd;
-    bool same = true;
-    for (int l = 0; l < dd && same; ++l) same = (ow[l] == wv[l]);
-    if (same) {
-      const double2 old = ra[cur];
-      double2 nw = make_double2(old.x + a.x, old.y + a.y);   // duplicate key: a_R += a
-      const bool was_live = (old.x != 0.0 || old.y != 0.0);
-      const bool live = nw.x * nw.x + nw.y * nw.y >= eta_prune2;   // prune small coefficients
-      if (!live) nw = make_double2(0.0, 0.0);
-      ra[cur] = nw;
-      if (was_live && !live) atomicSub(&rp->n_live, 1);
-      if (!was_live && live) atomicAdd(&rp->n_live, 1);
-      merged = true;
-      break;
-    }
-  }
-  if (merged && scratch_idx >= 0) {
-    // the slot that held the decoded vector stays a zero mode
-    ra[scratch_idx] = make_double2(0.0, 0.0);
-    for (int l = 0; l < S; ++l) rt[(int64_t)scratch_idx * S + l] = mk2((T)0, (T)0);
-  }
-  if (placed) warp_add(&rp->n_live, 1, s);
-  else if (!merged && mine >= 0 && mine < c.reg_cap) atomicOr(&rp->err, 2);   // table full
 }
 
 template <typename T>
@@ -1289,6 +760,7 @@ class Engine final : public EngineBase {
       c.d = d.d;
       c.shift_block = d.shift_block;
       c.n_sets = d.shift_block ? 1 + (int)d.shift_blocks.size() : d.d + 1;
+      c.fuse_L = (sizeof(T) == 4 && d.fuse) ? fused_max_length(c.n_sets) : 0;
       c.blk_off = (int64_t)shblk.size();
       if (d.shift_block) {
         int start = 0;
@@ -1365,6 +837,12 @@ class Engine final : public EngineBase {
       part_min += (int64_t)c.n_sets * d.p_max;
       rows_max_ += c.n_sets;
       pmax_all = std::max(pmax_all, d.p_max);
+      if (c.fuse_L > 0) {
+        any_fuse_ = true;
+        fuse_ns_mask_ |= 1u << (c.n_sets - 1);
+        fuse_sets_max_ = std::max(fuse_sets_max_, c.n_sets);
+        fuse_L_max_ = std::max(fuse_L_max_, c.fuse_L);
+      }
       small_logL_max_ = std::max(small_logL_max_, std::min(c.logL_max, single_logL));
       k_max_ = std::max<int64_t>(k_max_, d.k);
       kd_max_ = std::max<int64_t>(kd_max_, d.k * d.d);
@@ -1463,6 +941,10 @@ class Engine final : public EngineBase {
       ECHK(cudaFuncSetAttribute(k_bigB<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
       ECHK(cudaFuncSetAttribute(k_bigC<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
     }
+    if (any_fuse_) {
+      smem_fused_ = fused_smem_bytes(fuse_sets_max_, fuse_L_max_);
+      ECHK(fused_setup(smem_fused_));
+    }
     if (profile_) {
       events_.resize((size_t)(SFFT_STATS_MAX_ROUNDS + 4) * 8);
       for (auto& e : events_) ECHK(cudaEventCreate(&e));
@@ -1531,6 +1013,38 @@ class Engine final : public EngineBase {
     return cudaSuccess;
   }
 
+  // One fused round: a launch per set count present (the signals whose round is marked
+  // fused run it and plan the next), then the tail that counts it and sets the loop condition.
+  cudaError_t launch_fused(const PlanArgs& pa, int64_t* launches) {
+    if constexpr (sizeof(T) == 4) {
+      FusedArgs fa;
+      fa.pa = pa;
+      fa.pt = PrimeTables{ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_, plist_};
+      fa.cfg = cfg_;
+      fa.run = run_;
+      fa.ctl = ctl_;
+      fa.hist = hist_;
+      fa.ubuf = u_;
+      fa.sig_w = sig_w_;
+      fa.sig_a = sig_a_;
+      fa.tw = (const float2*)tw_;
+      fa.shblk = shblk_;
+      fa.regw = regw_;
+      fa.rega = rega_;
+      fa.regtw = (float2*)regtw_;
+      fa.hash = hash_;
+      fa.tws = tw_src();
+      for (int ns = 1; ns <= kFusedMaxSets; ++ns) {
+        if (!(fuse_ns_mask_ & (1u << (ns - 1)))) continue;
+        ECHK(fused_launch(ns, n_, smem_fused_, st_, fa));
+        launches[6] += 1;
+      }
+      ECHK(fused_tail(st_, ctl_, pa.use_cond, pa.cond_fused));
+      launches[6] += 1;
+    }
+    return cudaSuccess;
+  }
+
   // ---------------------------------------------------------------- one round
   // occupied bins into the candidate list, then the ratio test, read-out and merge over it
   cudaError_t launch_classify(const ClassifyOut& co) {
@@ -1541,17 +1055,20 @@ class Engine final : public EngineBase {
     return cudaGetLastError();
   }
 
-  cudaError_t enqueue_round(const PlanArgs& pa, int64_t* launches, int round_idx, bool record) {
-    auto mark = [&](int q) -> cudaError_t {
-      if (!record) return cudaSuccess;
-      return cudaEventRecord(events_[(size_t)round_idx * 8 + q], st_);
-    };
-    ECHK(mark(0));
-    k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_, plist_, u_,
-                                            hist_);
-    ECHK(cudaGetLastError());
+  // the round's plan (one launch)
+  cudaError_t launch_plan(const PlanArgs& pa, int64_t* launches) {
+    k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_,
+                                            plist_, u_, hist_);
+    launches[0] += 1;
+    return cudaGetLastError();
+  }
+
+  // The batched kernels of a round, over the signals not left to the fused kernel; mark(q)
+  // records the profile events between the kernel classes.
+  template <class Mark>
+  cudaError_t enqueue_batched(int64_t* launches, Mark mark) {
     ECHK(launch_tables());
-    launches[0] += 2;
+    launches[0] += 1;
     ECHK(mark(1));
     ECHK(mark(2));
     ECHK(launch_samples(launches));
@@ -1580,6 +1097,22 @@ class Engine final : public EngineBase {
     ECHK(launch_classify(co));
     launches[4] += 2;
     ECHK(mark(5));
+    return cudaSuccess;
+  }
+
+  // One round enqueued from the host: plan, batched kernels, then kFusedHostRounds fused rounds
+  // (launches without work return at once).
+  cudaError_t enqueue_round(const PlanArgs& pa, int64_t* launches, int round_idx, bool record) {
+    auto mark = [&](int q) -> cudaError_t {
+      if (!record) return cudaSuccess;
+      return cudaEventRecord(events_[(size_t)round_idx * 8 + q], st_);
+    };
+    ECHK(mark(0));
+    ECHK(launch_plan(pa, launches));
+    ECHK(enqueue_batched(launches, mark));
+    if (any_fuse_)
+      for (int q = 0; q < kFusedHostRounds; ++q) ECHK(launch_fused(pa, launches));
+    ECHK(mark(7));
     return cudaSuccess;
   }
 
@@ -1615,8 +1148,49 @@ class Engine final : public EngineBase {
     return cudaGetLastError();
   }
 
+  // Adds a conditional node of the given type after the work captured so far on cs, and
+  // captures fill() (launches on st_) into its body.
+  template <class Fill>
+  cudaError_t capture_conditional(cudaStream_t cs, cudaGraphConditionalNodeType type,
+                                  cudaGraphConditionalHandle handle, Fill fill) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    ECHK(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd));
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    std::memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams* cp = reinterpret_cast<cudaGraphNodeParams*>(raw);
+    cp->type = cudaGraphNodeTypeConditional;
+    cp->conditional.handle = handle;
+    cp->conditional.type = type;
+    cp->conditional.size = 1;
+    cudaGraphNode_t node;
+    ECHK(cudaGraphAddNode(&node, cg, deps, nullptr, nd, cp));
+    ECHK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaStream_t inner;
+    ECHK(cudaStreamCreateWithFlags(&inner, cudaStreamNonBlocking));
+    cudaStream_t saved = st_;
+    st_ = inner;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(inner, cp->conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      e = fill();
+      cudaGraph_t captured;
+      const cudaError_t e2 = cudaStreamEndCapture(inner, &captured);
+      if (e == cudaSuccess) e = e2;
+    }
+    st_ = saved;
+    cudaStreamDestroy(inner);
+    return e;
+  }
+
   cudaError_t build_graph(int hard_rounds) {
-    // while (plan says some signal is active) { one round }
+    // while (some signal active) {
+    //   plan;
+    //   if (some signal has batched work) { the batched kernels }
+    //   while (some signal has a fused round planned) { fused round }
+    // }
     cudaGraph_t g;
     ECHK(cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle handle;
@@ -1632,26 +1206,38 @@ class Engine final : public EngineBase {
     cudaGraphNode_t node;
     ECHK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, cp));
     cudaGraph_t body = cp->conditional.phGraph_out[0];
+    PlanArgs pa = plan_args(hard_rounds);
+    pa.use_cond = 1;
+    pa.cond = handle;
+    ECHK(cudaGraphConditionalHandleCreate(&pa.cond_batch, body, 0, cudaGraphCondAssignDefault));
+    if (any_fuse_) ECHK(cudaGraphConditionalHandleCreate(&pa.cond_fused, body, 0, cudaGraphCondAssignDefault));
     cudaStream_t cs;
     ECHK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaStream_t saved = st_;
     st_ = cs;
-    ECHK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    PlanArgs pa = plan_args(hard_rounds);
-    pa.use_cond = 1;
-    pa.cond = handle;
-    int64_t dummy[SFFT_NKCLASS] = {0, 0, 0, 0, 0, 0};
-    cudaError_t e = enqueue_round(pa, dummy, 0, false);
-    cudaGraph_t captured;
-    cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+    int64_t dplan[SFFT_NKCLASS] = {};
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      e = launch_plan(pa, dplan);
+      if (e == cudaSuccess)
+        e = capture_conditional(cs, cudaGraphCondTypeIf, pa.cond_batch, [&]() {
+          return enqueue_batched(launch_batched_, [](int) { return cudaSuccess; });
+        });
+      if (e == cudaSuccess && any_fuse_)
+        e = capture_conditional(cs, cudaGraphCondTypeWhile, pa.cond_fused,
+                                [&]() { return launch_fused(pa, launch_fused_); });
+      cudaGraph_t captured;
+      const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+      if (e == cudaSuccess) e = e2;
+    }
     st_ = saved;
     cudaStreamDestroy(cs);
-    if (e != cudaSuccess) return e;
-    if (e2 != cudaSuccess) return e2;
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return e;
+    }
     ECHK(cudaGraphInstantiate(&graph_exec_, g, 0));
     graph_ = g;
-    launches_per_round_ = dummy[0] + dummy[2] + dummy[3] + dummy[4];
-    for (int q = 0; q < SFFT_NKCLASS; ++q) launch_class_per_round_[q] = dummy[q];
     return cudaSuccess;
   }
 
@@ -1663,6 +1249,7 @@ class Engine final : public EngineBase {
     pa.n_sm = n_sm_;
     pa.single_max_logL = log2i(single_max_L<T>());
     pa.hard_rounds = hard_rounds;
+    pa.fuse = any_fuse_ ? 1 : 0;
     return pa;
   }
 
@@ -1676,7 +1263,7 @@ class Engine final : public EngineBase {
   cudaError_t run(const int32_t* const* sig_w, const double2* const* sig_a, const int64_t* k_sig, const int64_t* caps,
                   const double* noise_sigma, const uint64_t* noise_seed, int32_t* out_w, double2* out_a,
                   int64_t* n_found, int* status, sfft_stats* stats) override {
-    int64_t launches[SFFT_NKCLASS] = {0, 0, 0, 0, 0, 0};
+    int64_t launches[SFFT_NKCLASS] = {};
     const int hard = hard_rounds();
     ECHK(bind(sig_w, sig_a, k_sig, caps, noise_sigma, noise_seed));
     launches[5] += 2;
@@ -1708,6 +1295,8 @@ class Engine final : public EngineBase {
     int* hst = reinterpret_cast<int*>(hb + stage_st_);
     ECHK(cudaMemcpyAsync(hn, outn_, n_ * sizeof(int64_t), cudaMemcpyDeviceToHost, st_));
     ECHK(cudaMemcpyAsync(hst, outst_, n_ * sizeof(int), cudaMemcpyDeviceToHost, st_));
+    RoundCtl* hctl_end = reinterpret_cast<RoundCtl*>(hb + stage_ctl_);
+    if (stats) ECHK(cudaMemcpyAsync(hctl_end, ctl_, sizeof(RoundCtl), cudaMemcpyDeviceToHost, st_));
     HistRec* hh = nullptr;
     std::vector<SigRun> runs;
     if (stats) {
@@ -1729,6 +1318,7 @@ class Engine final : public EngineBase {
         rounds = std::max(rounds, runs[s].round);
         stats->samples += runs[s].samples;
         stats->terms += runs[s].terms;
+        stats->terms_fused += runs[s].terms_fused;
         conv = conv && (hst[s] == SFFT_OK || hst[s] == SFFT_ERR_INCONSISTENT || hst[s] == SFFT_ERR_CAPACITY) &&
                !runs[s].active;
       }
@@ -1742,9 +1332,10 @@ class Engine final : public EngineBase {
         stats->registry[i] = hh[i].live;
       }
       if (use_graph_ && !record) {
-        // rounds of the device loop: the plan of each round plus one that found nothing left
-        const int64_t loops = rounds + 1;
-        for (int q = 0; q < SFFT_NKCLASS; ++q) launches[q] += launch_class_per_round_[q] * loops;
+        // bodies of the device loop (one plan each), those with batched work, and fused rounds
+        launches[0] += hctl_end->round;
+        for (int q = 0; q < SFFT_NKCLASS; ++q)
+          launches[q] += launch_batched_[q] * hctl_end->bodies_batched + launch_fused_[q] * hctl_end->fused_iters;
       }
       for (int q = 0; q < SFFT_NKCLASS; ++q) stats->kernel_launches[q] = launches[q];
       if (record) {
@@ -1761,6 +1352,8 @@ class Engine final : public EngineBase {
           stats->kernel_ms[5] += ms;
           ECHK(cudaEventElapsedTime(&ms, events_[b + 6], events_[b + 5]));
           stats->kernel_ms[4] += ms;
+          ECHK(cudaEventElapsedTime(&ms, events_[b + 5], events_[b + 7]));
+          stats->kernel_ms[6] += ms;
         }
       }
     }
@@ -1785,6 +1378,7 @@ class Engine final : public EngineBase {
     int64_t cp[1] = {0};
     ECHK(bind(wp, ap, ks, cp));
     PlanArgs pa = plan_args(1 << 20);
+    pa.fuse = 0;   // a step call runs its stage in the batched kernels
     pa.force = 1;
     pa.force_p = p;
     pa.force_K = K;
@@ -1859,6 +1453,11 @@ class Engine final : public EngineBase {
   cudaStream_t st_ = nullptr;
   bool profile_ = false, use_graph_ = false, any_big_ = false;
   bool any_peel_ = false;   // some slot removes its registry in the bin domain
+  bool any_fuse_ = false;   // some slot may run short rounds in the fused kernel (FP32 engines)
+  int fuse_sets_max_ = 0;   // most sample sets of such a slot
+  unsigned fuse_ns_mask_ = 0;   // set counts of such slots
+  int fuse_L_max_ = 0;      // and its longest fused Bluestein length
+  size_t smem_fused_ = 0;   // dynamic shared memory of the fused kernel
   int2* cand_ = nullptr;    // (slot, bin) of the round's occupied bins, sum of p_max entries
   int peel_gx_ = 1;         // k_peel blocks per signal
   int logL_big_max_ = 0, small_logL_max_ = 1, small_threads_ = 256, n_ptab_ = 0;
@@ -1921,8 +1520,9 @@ class Engine final : public EngineBase {
   size_t stage_ctl_ = 0, stage_n_ = 0, stage_st_ = 0, stage_hist_ = 0;
   cudaGraph_t graph_ = nullptr;
   cudaGraphExec_t graph_exec_ = nullptr;
-  int64_t launches_per_round_ = 0;
-  int64_t launch_class_per_round_[SFFT_NKCLASS] = {0, 0, 0, 0, 0, 0};
+  // launches per class of one batched round body and of one fused round (graph mode counts)
+  int64_t launch_batched_[SFFT_NKCLASS] = {};
+  int64_t launch_fused_[SFFT_NKCLASS] = {};
 };
 
 }  // namespace

@@ -31,6 +31,7 @@ struct SigCfg {
   int coef_mean;      // coefficient = mean over the d + 1 sets (else Y_0[h] / p)
   int peel_bins;      // the registry leaves the transform bin by bin (else it is sampled with f)
   int shift_block;    // shifted sets move along block unwrap vectors (Alg. 2 as printed), else e_n / N
+  int fuse_L;         // rounds of Bluestein length up to this run in the fused kernel (0: none)
   int reg_cap, hash_mask, logL_max;
   int64_t N, p_max;
   int64_t p_min;      // floor of the prime rule: the i-th prime >= max(c k*, p_min)
@@ -62,11 +63,13 @@ struct SigRun {
   int k_sig;          // modes of the bound black box
   int logL, big;      // power-of-two Bluestein length of the round (four-step path when big)
   int L;              // Bluestein length of the one-block path: m 2^a >= 2p - 1, m in {1, 3, 5}
+  int fused;          // the round runs in the fused small-round kernel (one block for the signal)
   int n_xt, groups, gsize, chunks, jper, splits;
   int mgroups;        // mode groups per sampling tile (warps sharing rows when p is small)
   int reg_start;      // registry entries at the start of the round
   int64_t p;
   unsigned long long mod_m;   // floor((2^64 - 1) / p), Barrett reduction
+  unsigned long long proj_off;   // (box_lo mod p)(sum of u mod p) mod p, for project_mod
   int64_t part_off;
   unsigned long long maxy0_bits;
   double a_ref;
@@ -74,6 +77,7 @@ struct SigRun {
   double noise_sigma;              // noise of the bound black box (0: none)
   unsigned long long noise_seed;
   int64_t samples, terms;
+  int64_t terms_fused;  // of the terms, those of fused rounds
   int64_t n_out;
 };
 
@@ -84,6 +88,9 @@ struct RoundCtl {
   int64_t n_samp[kMaxSetGroup];               // sampling tiles, per set-group size
   unsigned long long ctr_samp[kMaxSetGroup], ctr_rows, ctr_filt;
   unsigned long long n_cand;                  // occupied bins found this round (classification)
+  unsigned long long n_fused_next;            // signals with another fused round planned
+  int64_t bodies_batched;                     // round bodies that had batched work (whole run)
+  int64_t fused_iters;                        // fused rounds launched (whole run)
 };
 
 // exclusive scans over signals: tables, modes, DFT rows, filters, bins, four-step passes, DFT
@@ -119,6 +126,7 @@ struct SlotDesc {
   int coef_mean;
   int peel_bins;
   int shift_block;
+  int fuse = 1;                    // short rounds may run in the fused kernel
   std::vector<int> shift_blocks;   // block sizes of the shifted sets (block form)
   double tau, rho, delta, sigma;
   int max_rounds;

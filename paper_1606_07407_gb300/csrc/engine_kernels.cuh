@@ -16,16 +16,24 @@ __device__ __forceinline__ uint64_t mod_barrett(uint64_t x, uint64_t p, uint64_t
 
 // (w . u) mod p for w in the box [box_lo, box_lo + N)^d and u reduced mod p, as
 // sum_l (w_l - box_lo) u_l + box_lo sum_l u_l with every step reduced (w_l - box_lo < 2^31, u_l < p).
+// off = (box_lo mod p) (sum_l u_l mod p) mod p, a constant of the round (proj_offset)
 __device__ __forceinline__ uint64_t project_mod(const int32_t* w, int d, const int64_t* u, int box_lo, int64_t p,
-                                                uint64_t mm) {
+                                                uint64_t mm, uint64_t off) {
   const uint64_t up = (uint64_t)p;
-  uint64_t acc = 0, usum = 0;
-  for (int l = 0; l < d; ++l) {
-    acc = mod_barrett((uint64_t)(int64_t)(w[l] - box_lo) * (uint64_t)u[l] + acc, up, mm);
-    usum += (uint64_t)u[l];
-  }
+  uint64_t acc = 0;
+  for (int l = 0; l < d; ++l) acc = mod_barrett((uint64_t)(int64_t)(w[l] - box_lo) * (uint64_t)u[l] + acc, up, mm);
+  acc += off;   // < 2p
+  return acc >= up ? acc - up : acc;
+}
+
+// The offset of project_mod for the direction u (reduced mod p) of a round: w . u = sum_l
+// (w_l - box_lo) u_l + box_lo sum_l u_l, the first sum over non-negative terms.
+__device__ __forceinline__ uint64_t proj_offset(int d, const int64_t* u, int box_lo, int64_t p, uint64_t mm) {
+  const uint64_t up = (uint64_t)p;
+  uint64_t usum = 0;
+  for (int l = 0; l < d; ++l) usum = mod_barrett(usum + (uint64_t)u[l], up, mm);
   const int64_t blm = ((int64_t)box_lo % p + p) % p;
-  return mod_barrett(acc + mod_barrett((uint64_t)blm * mod_barrett(usum, up, mm), up, mm), up, mm);
+  return mod_barrett((uint64_t)blm * usum, up, mm);
 }
 
 // a mod p for 0 <= a < 64 p < 2^31, via a float reciprocal and one correction.

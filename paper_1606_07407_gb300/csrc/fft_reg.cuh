@@ -250,13 +250,13 @@ __device__ void fft_tables(C2* hi, C2* lo, int L, const TwSrc<C2>& src) {
   for (int i = threadIdx.x; i * kTwLo < L; i += blockDim.x) hi[i] = tw[(int64_t)i * kTwLo * step];
 }
 
-template <typename C2, int R, bool INV>
-__device__ __forceinline__ void stockham_pass(C2* buf, int L, int Ns, const C2* hi, const C2* lo) {
-  constexpr int E = fft_per_thread<C2>();
+// One pass over a row by the nthr threads t = 0..nthr-1 given to it (act false: the thread has
+// no row this time and only takes part in the barriers); E bounds the values a thread holds.
+template <typename C2, int R, bool INV, int E = fft_per_thread<C2>()>
+__device__ __forceinline__ void stockham_pass(C2* buf, int L, int Ns, const C2* hi, const C2* lo, int t, int nthr,
+                                              bool act) {
   constexpr int J = E / R > 0 ? E / R : 1;   // butterflies per thread at most
-  const int nthr = blockDim.x;
-  const int t = threadIdx.x;
-  const int B = L / R;                       // butterflies of the pass
+  const int B = act ? L / R : 0;             // butterflies of the pass
   const int tstride = L / (Ns * R);          // twiddle index scale: w^(r k) = e^{-2 pi i r k tstride / L}
   C2 v[J][R];
 #pragma unroll
@@ -287,53 +287,101 @@ __device__ __forceinline__ void stockham_pass(C2* buf, int L, int Ns, const C2* 
 }
 
 // a pass of radix 2^b (1 <= b < log2 E)
-template <typename C2, bool INV>
-__device__ __forceinline__ void pow2_pass(C2* buf, int L, int Ns, int b, const C2* hi, const C2* lo) {
+template <typename C2, bool INV, int E = fft_per_thread<C2>()>
+__device__ __forceinline__ void pow2_pass(C2* buf, int L, int Ns, int b, const C2* hi, const C2* lo, int t, int nthr,
+                                          bool act) {
   switch (b) {
-    case 1: stockham_pass<C2, 2, INV>(buf, L, Ns, hi, lo); break;
-    case 2: stockham_pass<C2, 4, INV>(buf, L, Ns, hi, lo); break;
-    case 3: stockham_pass<C2, 8, INV>(buf, L, Ns, hi, lo); break;
-    case 4: if constexpr (fft_per_thread<C2>() > 16) stockham_pass<C2, 16, INV>(buf, L, Ns, hi, lo); break;
+    case 1: stockham_pass<C2, 2, INV, E>(buf, L, Ns, hi, lo, t, nthr, act); break;
+    case 2: stockham_pass<C2, 4, INV, E>(buf, L, Ns, hi, lo, t, nthr, act); break;
+    case 3: stockham_pass<C2, 8, INV, E>(buf, L, Ns, hi, lo, t, nthr, act); break;
+    case 4:
+      if constexpr (E > 16) stockham_pass<C2, 16, INV, E>(buf, L, Ns, hi, lo, t, nthr, act);
+      break;
     default: break;
   }
 }
 
-// Full transform of one row of length L = m 2^a (m in {1, 3, 5}, L >= 32) in buf (padded layout).
-// (inlined: the caller must leave it about 100 registers)
-template <typename C2, bool INV>
-__device__ __forceinline__ void fft_row(C2* buf, int L, const C2* hi, const C2* lo) {
-  constexpr int E = fft_per_thread<C2>();
-  constexpr int LE = E == 32 ? 5 : 4;
+// Radix plan of a row of length L = m 2^a (m in {1, 3, 5}, L >= 32): `pass(R)` for each pass in
+// order.  Radix E while E points remain in the power-of-two part, then the rest of it with m in
+// one pass of radix m 2^b if that is at most E points, else a radix-2^b pass and a radix-m pass.
+template <int E, class F>
+__host__ __device__ __forceinline__ void fft_plan(int L, F pass) {
+  constexpr int LE = E == 32 ? 5 : E == 16 ? 4 : 3;
+  int a = 0;
+  while (((L >> a) & 1) == 0) ++a;
+  const int m = L >> a;
+  int rem = a;
+  while (rem >= LE) {
+    pass(E);
+    rem -= LE;
+  }
+  if (m == 1) {
+    if (rem > 0) pass(1 << rem);
+    return;
+  }
+  if ((m << rem) <= E) {
+    pass(m << rem);
+    return;
+  }
+  if (rem > 0) pass(1 << rem);
+  pass(m);
+}
+
+// Threads one row of length L needs so that no thread has more than E / R butterflies of a
+// radix-R pass, rounded up to whole warps.
+template <typename C2, int E = fft_per_thread<C2>()>
+__host__ __device__ inline int fft_threads(int L) {
+  int need = 32;
+  fft_plan<E>(L, [&](int R) {
+    const int J = E / R > 0 ? E / R : 1;
+    const int q = (L / R + J - 1) / J;
+    if (q > need) need = q;
+  });
+  return (need + 31) / 32 * 32;
+}
+
+// Full transform of one row of length L = m 2^a (m in {1, 3, 5}, L >= 32) in buf (padded
+// layout) by threads t = 0..nthr-1, nthr >= fft_threads(L); threads with act false take part
+// in the barriers only.  (inlined: the caller must leave it about 100 registers)
+template <typename C2, bool INV, int E = fft_per_thread<C2>()>
+__device__ __forceinline__ void fft_row(C2* buf, int L, const C2* hi, const C2* lo, int t, int nthr, bool act) {
+  constexpr int LE = E == 32 ? 5 : E == 16 ? 4 : 3;
   const int a = __ffs(L) - 1;
   const int m = L >> a;
   int Ns = 1, rem = a;
   while (rem >= LE) {
-    stockham_pass<C2, E, INV>(buf, L, Ns, hi, lo);
+    stockham_pass<C2, E, INV, E>(buf, L, Ns, hi, lo, t, nthr, act);
     Ns <<= LE;
     rem -= LE;
   }
   if (m == 1) {
-    pow2_pass<C2, INV>(buf, L, Ns, rem, hi, lo);
+    pow2_pass<C2, INV, E>(buf, L, Ns, rem, hi, lo, t, nthr, act);
     return;
   }
   const int mp = m << rem;
   if (mp <= E) {
     switch (mp) {
-      case 3: stockham_pass<C2, 3, INV>(buf, L, Ns, hi, lo); break;
-      case 5: stockham_pass<C2, 5, INV>(buf, L, Ns, hi, lo); break;
-      case 6: stockham_pass<C2, 6, INV>(buf, L, Ns, hi, lo); break;
-      case 10: stockham_pass<C2, 10, INV>(buf, L, Ns, hi, lo); break;
-      case 12: stockham_pass<C2, 12, INV>(buf, L, Ns, hi, lo); break;
-      case 20: if constexpr (E >= 20) stockham_pass<C2, 20, INV>(buf, L, Ns, hi, lo); break;
-      case 24: if constexpr (E >= 24) stockham_pass<C2, 24, INV>(buf, L, Ns, hi, lo); break;
+      case 3: stockham_pass<C2, 3, INV, E>(buf, L, Ns, hi, lo, t, nthr, act); break;
+      case 5: stockham_pass<C2, 5, INV, E>(buf, L, Ns, hi, lo, t, nthr, act); break;
+      case 6: stockham_pass<C2, 6, INV, E>(buf, L, Ns, hi, lo, t, nthr, act); break;
+      case 10: stockham_pass<C2, 10, INV, E>(buf, L, Ns, hi, lo, t, nthr, act); break;
+      case 12: stockham_pass<C2, 12, INV, E>(buf, L, Ns, hi, lo, t, nthr, act); break;
+      case 20: if constexpr (E >= 20) stockham_pass<C2, 20, INV, E>(buf, L, Ns, hi, lo, t, nthr, act); break;
+      case 24: if constexpr (E >= 24) stockham_pass<C2, 24, INV, E>(buf, L, Ns, hi, lo, t, nthr, act); break;
       default: break;
     }
     return;
   }
-  pow2_pass<C2, INV>(buf, L, Ns, rem, hi, lo);
+  pow2_pass<C2, INV, E>(buf, L, Ns, rem, hi, lo, t, nthr, act);
   Ns <<= rem;
-  if (m == 3) stockham_pass<C2, 3, INV>(buf, L, Ns, hi, lo);
-  else stockham_pass<C2, 5, INV>(buf, L, Ns, hi, lo);
+  if (m == 3) stockham_pass<C2, 3, INV, E>(buf, L, Ns, hi, lo, t, nthr, act);
+  else stockham_pass<C2, 5, INV, E>(buf, L, Ns, hi, lo, t, nthr, act);
+}
+
+// the same by the whole block
+template <typename C2, bool INV>
+__device__ __forceinline__ void fft_row(C2* buf, int L, const C2* hi, const C2* lo) {
+  fft_row<C2, INV>(buf, L, hi, lo, (int)threadIdx.x, (int)blockDim.x, true);
 }
 
 }  // namespace sfft

@@ -1,0 +1,332 @@
+// Fused small-round kernel (see fused.cuh).  Each launch runs one round of Algorithm 2 for
+// every signal whose plan marks it fused, one block of kSampleThreads threads per signal, with
+// the round's data in shared memory:
+//
+//   tables      W[m] = e^{2 pi i m / p} and chirp[m] = e^{-pi i m^2 / p} (table_entry)
+//   samples     y_n[x] = sum_j C[n][j] W[(alpha_j x) mod p] for every set n (Eq. 41), thread
+//               x of the half line taking x and p - x (their exponentials are conjugate), the
+//               modes staged kFusedChunk at a time (mode_source) and split over G groups of
+//               threads when the half line is short; written times the chirp into the rows
+//   DFT         Bluestein (Eq. 3) of the n_sets rows and the filter at once, one row per
+//               fft_threads(L) threads, out into the transforms Y_n
+//   residual    the registry taken off its bins (peel_entry), when it is removed in the bin domain
+//   classify    empty-bin test, then the ratio test, read-out and registry merge of every
+//               occupied bin (classify_candidate)
+//   plan        the next round (plan_signal): the next launch runs it while it stays short,
+//               else the batched kernels plan it again the same way
+//
+// Shared memory (offsets from fused_layout): the tables (2p), the n_sets + 1 rows of the DFT
+// (padded), and a work area that holds in turn a chunk of modes, the groups' partial sums and
+// the transforms Y_n.  The registry's probe rule (entries of earlier rounds are complete) holds
+// as in the batched path, since each round is a launch of its own.
+//
+// Included by the translation units that instantiate the kernel for a few set counts each
+// (they compile in parallel).
+#pragma once
+
+#include "fused.cuh"
+#include "noise.cuh"
+#include "sample_tile.cuh"
+
+namespace sfft {
+
+namespace {
+
+// Samples of every set into the DFT rows: slot n + 1 gets chirp[x] y_n[x] at x < p.
+template <int NS>
+__device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c, const SigRun& r, int s,
+                                             const float2* tab_s, float2* slots, int ls, unsigned char* work) {
+  using C2 = float2;
+  const int tid = threadIdx.x;
+  const int p = (int)r.p;
+  const int H = p / 2 + 1;                        // positions of the half line (<= 256)
+  const int G = max(1, (int)blockDim.x / H);      // mode groups
+  const int g = tid / H, x = tid - g * H;
+  const bool on = g < G;
+  const float inv_p = 1.0f / (float)p;
+  const int32_t* sw = a.sig_w[s];   // the black box's modes
+  const double2* sa = a.sig_a[s];
+  int* m_al = reinterpret_cast<int*>(work);
+  C2* m_C = reinterpret_cast<C2*>(work + kFusedChunk * sizeof(int));
+  float acc[NS][4];
+#pragma unroll
+  for (int n = 0; n < NS; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.0f;
+  const int K = sampled_modes(c, r);
+  for (int j0 = 0; j0 < K; j0 += kFusedChunk) {
+    const int cnt = min(kFusedChunk, K - j0);
+    if (j0 > 0) __syncthreads();   // every thread is done with the previous chunk
+    for (int jj = tid; jj < cnt; jj += blockDim.x) {
+      C2 a0;
+      const C2* twr;
+      m_al[jj] = (int)mode_source<float>(c, r, j0 + jj, a.ubuf, sw, sa, a.tw, a.regw, a.rega, a.regtw, &a0, &twr);
+      m_C[jj * NS] = a0;
+#pragma unroll
+      for (int n = 1; n < NS; ++n) m_C[jj * NS + n] = cmul(a0, twr[n - 1]);
+    }
+    __syncthreads();
+    if (on) {
+      for (int jj = g; jj < cnt; jj += G) {
+        const C2 E = tab_s[mod_small((unsigned)m_al[jj] * (unsigned)x, p, inv_p)];
+#pragma unroll
+        for (int n = 0; n < NS; ++n) {
+          const C2 cc = m_C[jj * NS + n];
+          acc[n][0] = fmaf(cc.x, E.x, acc[n][0]);   // P1: c_r e_r
+          acc[n][1] = fmaf(cc.y, E.y, acc[n][1]);   // P2: c_i e_i
+          acc[n][2] = fmaf(cc.x, E.y, acc[n][2]);   // P3: c_r e_i
+          acc[n][3] = fmaf(cc.y, E.x, acc[n][3]);   // P4: c_i e_r
+        }
+      }
+    }
+  }
+  if (G > 1) {
+    // groups 1..G-1 hand their sums to group 0 through the work area
+    float* red = reinterpret_cast<float*>(work);
+    __syncthreads();   // the last chunk is consumed
+    if (on && g > 0) {
+#pragma unroll
+      for (int n = 0; n < NS; ++n)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) red[(((g - 1) * H + x) * NS + n) * 4 + k] = acc[n][k];
+    }
+    __syncthreads();
+    if (g == 0) {
+      for (int gg = 1; gg < G; ++gg)
+#pragma unroll
+        for (int n = 0; n < NS; ++n)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc[n][k] += red[(((gg - 1) * H + x) * NS + n) * 4 + k];
+    }
+  }
+  if (g == 0) {
+    const C2* chirp = tab_s + p;
+    const bool mirror = x >= 1 && p - x >= H;   // p - x is a distinct sample of the other half
+    const bool noisy = r.noise_sigma > 0.0;
+#pragma unroll
+    for (int n = 0; n < NS; ++n) {
+      const float P1 = acc[n][0], P2 = acc[n][1], P3 = acc[n][2], P4 = acc[n][3];
+      C2* rb = slots + (n + 1) * ls;
+      C2 y = mk2(P1 - P2, P3 + P4);
+      if (noisy) y = cadd(y, black_box_noise<float>(r.noise_seed, r.round, n, x, r.noise_sigma));
+      rb[fpad(x)] = cmul(chirp[x], y);
+      if (mirror) {
+        C2 ym = mk2(P1 + P2, P4 - P3);
+        if (noisy) ym = cadd(ym, black_box_noise<float>(r.noise_seed, r.round, n, p - x, r.noise_sigma));
+        rb[fpad(p - x)] = cmul(chirp[p - x], ym);
+      }
+    }
+  }
+}
+
+// Bluestein DFT (Eq. 3) of the rows in the slots, all at once: the forward transforms of slot
+// 0 (the filter) and slots 1..n_sets (the rows, times the chirp), the products with the
+// filter's spectrum, the inverse transforms, and Y_n[h] = chirp[h] (...)[h] / L into Ys.  The
+// largest |Y_0| goes to *maxy0 (the first round's A_ref).  A function of its own, called once:
+// the compiler keeps the unrolled passes in registers only where they are neither in a loop
+// nor at several call sites.
+__device__ __noinline__ void fused_convolve(const SigCfg& c, const SigRun& r, const float2* tab_s, float2* slots,
+                                            int ls, float2* tw_hi, float2* tw_lo, float2* Ys,
+                                            unsigned long long* maxy0) {
+  using C2 = float2;
+  const int p = (int)r.p;
+  const int L = r.L;
+  const int nthr = fft_threads<C2>(L);
+  const int slot = threadIdx.x / nthr, lt = threadIdx.x - slot * nthr;
+  const int row = slot - 1;
+  const bool data = slot >= 1 && row < c.n_sets;
+  const bool act = slot == 0 || data;
+  C2* rb = slots + slot * ls;
+  fft_row<C2, false>(rb, L, tw_hi, tw_lo, lt, nthr, act);
+  if (data)
+    for (int k = lt; k < L; k += nthr) rb[fpad(k)] = cmul(rb[fpad(k)], slots[fpad(k)]);
+  __syncthreads();
+  fft_row<C2, true>(rb, L, tw_hi, tw_lo, lt, nthr, data);
+  float m2 = 0.0f;   // largest |Y_0|^2 seen by this thread
+  if (data) {
+    const C2* chirp = tab_s + p;
+    const float invL = 1.0f / (float)L;
+    for (int h = lt; h < p; h += nthr) {
+      const C2 v = cmul(chirp[h], cscale(rb[fpad(h)], invL));
+      Ys[row * p + h] = v;
+      m2 = fmaxf(m2, v.x * v.x + v.y * v.y);
+    }
+  }
+  // row 0 is slot 1: whole warps, as nthr is a multiple of 32
+  if (slot == 1) max_abs_to<float>(maxy0, sqrt((double)m2));
+}
+
+// The registry of the round's start off its bins of Ys (residual in the bin domain, as
+// peel_entry): -p a e^{2 pi i w . s_n} to bin (w . u) mod p of set n.  Each thread takes four
+// entries at a time and loads all of them before its shared-memory atomics, so that the loads
+// overlap; the products are formed in float (the double pipe of this GPU is narrow).
+template <int NS>
+__device__ __forceinline__ void fused_peel(const SigCfg& c, const SigRun& r, float2* Ys, const int64_t* u,
+                                           const int32_t* regw, const double2* rega, const float2* regtw) {
+  constexpr int U = 4;
+  constexpr int S = NS - 1 > 0 ? NS - 1 : 1;
+  const int nr = min(r.K_reg, c.reg_cap);
+  const int p = (int)r.p;
+  const float pf = (float)p;
+  float* Yt = reinterpret_cast<float*>(Ys);
+  const int32_t* rw = regw + c.regw_off;
+  const double2* ra = rega + c.rega_off;
+  const float2* rt = regtw + c.regtw_off;
+  for (int j0 = threadIdx.x; j0 < nr; j0 += U * blockDim.x) {
+    double2 av[U];
+    float2 tv[U][S];
+    int h[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int jr = j0 + q * blockDim.x;
+      av[q] = jr < nr ? ra[jr] : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int n = 0; n < NS - 1; ++n) tv[q][n] = jr < nr ? rt[(int64_t)jr * (NS - 1) + n] : make_float2(0.f, 0.f);
+      h[q] = jr < nr ? (int)project_mod(rw + (int64_t)jr * c.d, c.d, u, c.box_lo, r.p, r.mod_m, r.proj_off) : -1;
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      if (h[q] < 0 || (av[q].x == 0.0 && av[q].y == 0.0)) continue;   // past the end, or pruned
+      const float px = -pf * (float)av[q].x, py = -pf * (float)av[q].y;
+      atomicAdd(Yt + 2 * h[q], px);
+      atomicAdd(Yt + 2 * h[q] + 1, py);
+#pragma unroll
+      for (int n = 1; n < NS; ++n) {
+        const float2 t = tv[q][n - 1];
+        const int e = n * p + h[q];
+        atomicAdd(Yt + 2 * e, px * t.x - py * t.y);
+        atomicAdd(Yt + 2 * e + 1, px * t.y + py * t.x);
+      }
+    }
+  }
+}
+
+// ratio test, read-out and registry merge of the occupied bins cand[0..n_cand)
+__device__ __noinline__ void fused_classify(const SigCfg& c, SigRun* rp, int s, const int* cand, int n_cand,
+                                            const float2* Ys, const int64_t* ubuf, const int32_t* shblk,
+                                            int32_t* regw, double2* rega, float2* regtw, int32_t* hash) {
+  const ClassifyOut co{nullptr, nullptr, nullptr, 0, nullptr, nullptr, -1.0};
+  for (int e = threadIdx.x; e < n_cand; e += blockDim.x)
+    classify_candidate<float>(c, rp, s, cand[e], Ys, ubuf, shblk, regw, rega, regtw, hash, co);
+}
+
+// Plans the signal's next round (one thread); returns 1 when it runs fused too.  A round left
+// to the batched kernels is not stored: their plan kernel makes the same one.
+__device__ __noinline__ int fused_next(const PlanArgs& pa, const PrimeTables& pt, const SigCfg& c, SigRun* rp, int s,
+                                       int64_t* ubuf, HistRec* hist) {
+  SigRun nx = *rp;
+  plan_signal<float>(pa, c, nx, pt, ubuf, hist, s == 0);
+  if (!nx.active) {
+    *rp = nx;   // done, or stopped by the round limit
+    return 0;
+  }
+  if (nx.fused) {
+    *rp = nx;
+    return 1;
+  }
+  rp->fused = 0;   // the round just run is finished and the next one not yet planned
+  return 0;
+}
+
+// One round of every signal of NS sample sets whose plan marks it fused (blocks of other
+// signals return).
+template <int NS>
+__global__ void __launch_bounds__(kSampleThreads, 2) k_fused(FusedArgs a) {
+  using C2 = float2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ C2 tw_lo[kTwLo], tw_hi[kFusedMaxL / kTwLo];
+  __shared__ SigRun rs;   // the round being run
+  __shared__ int s_cnt;
+  __shared__ PlanArgs s_pa;
+  __shared__ PrimeTables s_pt;
+  const int s = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (s >= a.pa.n) return;
+  SigRun* rp = a.run + s;
+  const SigCfg& c = a.cfg[s];
+  {
+    const SigRun& r0 = *rp;   // every thread reads the same fields: a uniform exit
+    if (!r0.active || !r0.fused || c.n_sets != NS) return;
+  }
+  if (tid == 0) {
+    rs = *rp;
+    s_pa = a.pa;
+    s_pt = a.pt;
+    s_cnt = 0;
+  }
+  __syncthreads();
+  const SigRun& r = rs;
+  const int p = (int)r.p;
+  const int L = r.L;
+  const FusedLayout lay = fused_layout(L, NS);
+  C2* tab_s = reinterpret_cast<C2*>(smem_raw + lay.tab);
+  C2* slots = reinterpret_cast<C2*>(smem_raw + lay.slots);
+  unsigned char* work = smem_raw + lay.work;
+  const int ls = lay.ls;
+
+  // tables, the DFT's twiddles, then the filter (slot 0) and the rows' zero tails
+  for (int m = tid; m < p; m += blockDim.x) table_entry<float>(r.p, r.mod_m, m, tab_s);
+  fft_tables(tw_hi, tw_lo, L, a.tws);
+  __syncthreads();
+  for (int e = tid; e < L; e += blockDim.x) slots[fpad(e)] = filter_value<float>(e, p, L, tab_s + p);
+  for (int e = tid; e < NS * (L - p); e += blockDim.x) {
+    const int n = e / (L - p), x = p + (e - n * (L - p));
+    slots[(n + 1) * ls + fpad(x)] = mk2(0.0f, 0.0f);
+  }
+  fused_sample<NS>(a, c, r, s, tab_s, slots, ls, work);
+  __syncthreads();
+
+  C2* Ys = reinterpret_cast<C2*>(work);   // the modes and partial sums are consumed
+  fused_convolve(c, r, tab_s, slots, ls, tw_hi, tw_lo, Ys, &rp->maxy0_bits);
+  __syncthreads();
+  if (c.peel_bins) {
+    fused_peel<NS>(c, r, Ys, a.ubuf + c.u_off, a.regw, a.rega, a.regtw);
+    __syncthreads();
+  }
+
+  // empty-bin test, as in the batched path (A_ref from the first round's largest bin)
+  const bool first = r.round == 1;
+  const double maxy0 = __longlong_as_double((long long)rp->maxy0_bits);
+  if (tid == 0) {
+    const double a_ref = first ? maxy0 / (double)p : r.a_ref;
+    if (first) rp->a_ref = a_ref;
+    rp->eta_prune = fmax(c.rho * a_ref, 6.0 * c.sigma / sqrt((double)p));
+  }
+  const float a_ref_f = first ? (float)maxy0 / (float)p : (float)r.a_ref;
+  const float eta = fmaxf((float)c.rho * (float)p * a_ref_f, 6.0f * (float)c.sigma * sqrtf((float)p));
+  int* cand = reinterpret_cast<int*>(slots);   // the DFT rows are consumed
+  for (int h0 = 0; h0 < p; h0 += blockDim.x) {
+    const int h = h0 + tid;
+    bool occ = false;
+    if (h < p) {
+      const C2 y0 = Ys[h];
+      occ = y0.x * y0.x + y0.y * y0.y > eta * eta;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, occ);
+    int base = 0;
+    if (lane == 0 && mask != 0u) base = atomicAdd(&s_cnt, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (occ) cand[base + __popc(mask & ((1u << lane) - 1u))] = h;
+  }
+  __syncthreads();
+  const int n_cand = s_cnt;
+  if (tid == 0 && n_cand > 0) rp->any_occupied = 1;
+  fused_classify(c, rp, s, cand, n_cand, Ys, a.ubuf, a.shblk, a.regw, a.rega, a.regtw, a.hash);
+  __syncthreads();
+
+  // the next round: fused again while its line stays short
+  if (tid == 0 && fused_next(s_pa, s_pt, c, rp, s, a.ubuf, a.hist)) atomicAdd(&a.ctl->n_fused_next, 1ull);
+}
+
+}  // namespace
+
+template <int NS>
+cudaError_t fused_setup_ns(size_t smem) {
+  return cudaFuncSetAttribute(k_fused<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int NS>
+cudaError_t fused_launch_ns(int n_slots, size_t smem, cudaStream_t st, const FusedArgs& a) {
+  k_fused<NS><<<n_slots, kSampleThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace sfft

@@ -19,8 +19,8 @@ PREC = {"fp32": 0, "auto": 0, "fp32_fp64ratio": 1, "fp32_only": 2, "fp64": 3}
 STATUS = {0: "ok", 1: "invalid argument", 2: "not converged", 3: "capacity exceeded",
           4: "beyond phase resolution", 5: "more modes than k", 6: "cuda error", 7: "device wait timed out"}
 MAX_ROUNDS = 256
-NKCLASS = 6
-KCLASSES = ("setup", "project", "sample", "dft", "classify", "merge")
+NKCLASS = 7
+KCLASSES = ("setup", "project", "sample", "dft", "classify", "merge", "fused")
 
 
 class SfftError(RuntimeError):
@@ -50,11 +50,12 @@ class _Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("box_lo", C.c_int), ("tau", C.c_double), ("rho", C.c_double),
                 ("delta", C.c_double), ("noise_sigma", C.c_double), ("max_rounds", C.c_int),
                 ("profile", C.c_int), ("graph", C.c_int), ("coef_set0", C.c_int), ("residual", C.c_int),
-                ("shift", C.c_int)]
+                ("shift", C.c_int), ("unfused", C.c_int)]
 
 
 class _Stats(C.Structure):
     _fields_ = [("rounds", C.c_int), ("converged", C.c_int), ("samples", C.c_int64), ("terms", C.c_int64),
+                ("terms_fused", C.c_int64),
                 ("p", C.c_int64 * MAX_ROUNDS), ("K", C.c_int32 * MAX_ROUNDS),
                 ("accepted", C.c_int32 * MAX_ROUNDS), ("registry", C.c_int32 * MAX_ROUNDS),
                 ("kernel_launches", C.c_int64 * NKCLASS), ("kernel_ms", C.c_double * NKCLASS)]
@@ -204,7 +205,7 @@ class Plan:
                  precision: str = "fp32", box_lo: int = 0, tau: float = 0.0, rho: float = 0.0,
                  delta: float = 0.0, noise_sigma: float = 0.0, max_rounds: int = 0, stream=None,
                  profile: bool = False, graph: bool = False, coef: str = "mean", residual: str = "bins",
-                 p_min: int = 0, shift: str = "coord"):
+                 p_min: int = 0, shift: str = "coord", fuse: bool = True):
         L = load()
         if residual not in RESIDUAL:
             raise ValueError(f"residual must be one of {sorted(RESIDUAL)}")
@@ -229,7 +230,7 @@ class Plan:
             tl.n_blocks, tl.block_sizes = len(blocks), arr
         op = _Opts(PREC[precision], int(box_lo), float(tau), float(rho), float(delta), float(noise_sigma),
                    int(max_rounds), 1 if profile else 0, 1 if graph else 0, 1 if coef == "set0" else 0,
-                   RESIDUAL[residual], SHIFT[shift])
+                   RESIDUAL[residual], SHIFT[shift], 0 if fuse else 1)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -324,7 +325,7 @@ def sample_noalloc(d: int, N: int, p: int, u, freqs: torch.Tensor, coeffs: torch
 def _stats_dict(st: _Stats) -> dict:
     r = min(st.rounds, MAX_ROUNDS)
     return {"rounds": st.rounds, "converged": bool(st.converged), "samples": int(st.samples),
-            "terms": int(st.terms), "p": list(st.p[:r]), "K": list(st.K[:r]),
+            "terms": int(st.terms), "terms_fused": int(st.terms_fused), "p": list(st.p[:r]), "K": list(st.K[:r]),
             "accepted": list(st.accepted[:r]), "registry": list(st.registry[:r]),
             "launches": dict(zip(KCLASSES, list(st.kernel_launches))),
             "kernel_ms": dict(zip(KCLASSES, list(st.kernel_ms)))}

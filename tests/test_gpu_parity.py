@@ -232,9 +232,10 @@ def test_classify_random_round_matches_oracle(sfft):
 
 # ------------------------------------------------------------------ whole recovery
 
-def _run_both(sfft, sig, blocks=None, prec="fp32", dirs=None, primes=None, box_lo=0, residual="bins"):
+def _run_both(sfft, sig, blocks=None, prec="fp32", dirs=None, primes=None, box_lo=0, residual="bins", fuse=True,
+              graph=False):
     plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=blocks, dirs=dirs, primes=primes, precision=prec, box_lo=box_lo,
-                     residual=residual)
+                     residual=residual, fuse=fuse, graph=graph)
     f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N))
     gf, ga = sfft.sort_result(_np(f), _np(a))
     th = O.Thresholds() if prec == "fp64" else O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
@@ -265,6 +266,22 @@ def test_recovery_d5_workload_full_size(sfft, residual):
     wl = WORKLOADS["d5_N1024_k1000"]
     sig = wl.signal()
     _assert_parity(sig, *_run_both(sfft, sig, wl.blocks, residual=residual), FP32_COEFF_TOL)
+
+
+@pytest.mark.parametrize("residual", ["bins", "samples"])
+def test_fused_short_rounds_match_oracle_and_cut_launches(sfft, residual):
+    # rounds on short lines run one block per signal in the fused kernel (default) or through
+    # the batched kernels (fuse=False): both reach the oracle's result, the fused one in a third
+    # fewer launches or less (graph mode counts the launches its loops ran; the rounds on long
+    # lines and the launches around the loop are the same for both)
+    wl = WORKLOADS["d5_N1024_k1000"]
+    sig = wl.signal(seed_offset=5)
+    launches = {}
+    for fuse in (True, False):
+        out = _run_both(sfft, sig, wl.blocks, residual=residual, fuse=fuse, graph=True)
+        _assert_parity(sig, *out, FP32_COEFF_TOL)
+        launches[fuse] = sum(out[3]["launches"].values())
+    assert 3 * launches[True] <= 2 * launches[False]
 
 
 def test_residual_forms_count_their_sample_terms(sfft):
