@@ -318,7 +318,8 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_filter(int n, const SigCfg* 
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __restrict__ cfg, SigRun* run, RoundCtl* ctl, Scans sc,
                       const c2<T>* __restrict__ part, const c2<T>* __restrict__ tab,
-                      const c2<T>* __restrict__ bhat, TwSrc<c2<T>> tws, c2<T>* __restrict__ Y, int small) {
+                      const c2<T>* __restrict__ bhat, TwSrc<c2<T>> tws, c2<T>* __restrict__ Y, int small,
+                      int smem_bytes) {
   using C2 = c2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ C2 tw_lo[kTwLo], tw_hi[kSingleMaxLf / kTwLo];
@@ -335,6 +336,18 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   const int64_t p = r.p;
   const C2* chirp = tab + c.tab_off + p;
   const C2* B = bhat + c.bhat_off;
+  // With room for a second row of L values after the padded row, the filter spectrum is copied
+  // there asynchronously during the forward transform, and then the chirp during the inverse
+  // one, so that neither product waits on global memory.
+  const int pfo = (L + L / 32 + 1) & ~1;   // past the padded row, at an even element: 16-byte aligned
+  C2* pf = buf + pfo;
+  const bool prefetch = (int64_t)(pfo + L) * (int64_t)sizeof(C2) <= (int64_t)smem_bytes;
+  if (prefetch) {
+    const int units = L * (int)sizeof(C2) / 16;   // the spectrum's offset is even: 16-byte aligned
+    for (int i = threadIdx.x; i < units; i += blockDim.x)
+      cp_async<16>(reinterpret_cast<unsigned char*>(pf) + 16 * i, reinterpret_cast<const unsigned char*>(B) + 16 * i);
+    cp_async_commit();
+  }
   fft_tables(tw_hi, tw_lo, L, tws);
   // loops unrolled so that each thread's global loads are in flight together
 #pragma unroll 8
@@ -349,10 +362,25 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   }
   __syncthreads();
   fft_row<C2, false>(buf, L, tw_hi, tw_lo);
+  if (prefetch) {
+    cp_async_wait_all();
+    __syncthreads();
 #pragma unroll 8
-  for (int k = threadIdx.x; k < L; k += blockDim.x) buf[fpad(k)] = cmul(buf[fpad(k)], B[k]);
-  __syncthreads();
+    for (int k = threadIdx.x; k < L; k += blockDim.x) buf[fpad(k)] = cmul(buf[fpad(k)], pf[k]);
+    __syncthreads();   // the spectrum is consumed: the chirp takes its place
+    for (int x = threadIdx.x; x < p; x += blockDim.x) cp_async<sizeof(C2)>(pf + x, chirp + x);
+    cp_async_commit();
+  } else {
+#pragma unroll 8
+    for (int k = threadIdx.x; k < L; k += blockDim.x) buf[fpad(k)] = cmul(buf[fpad(k)], B[k]);
+    __syncthreads();
+  }
   fft_row<C2, true>(buf, L, tw_hi, tw_lo);
+  if (prefetch) {
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  const C2* ch = prefetch ? pf : chirp;
   const T invL = (T)1 / (T)L;
   C2* out = Y + c.Y_off + (int64_t)row * p;
   T m2 = (T)0;   // largest |Y_0|^2 of this thread (set 0 only), in the transform's precision
@@ -360,7 +388,7 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   for (int64_t h0 = 0; h0 < p; h0 += blockDim.x) {
     const int64_t h = h0 + threadIdx.x;
     if (h < p) {
-      const C2 v = cmul(chirp[h], cscale(buf[fpad((int)h)], invL));
+      const C2 v = cmul(ch[h], cscale(buf[fpad((int)h)], invL));
       out[h] = v;
       m2 = fmax(m2, v.x * v.x + v.y * v.y);
     }
@@ -925,7 +953,17 @@ class Engine final : public EngineBase {
     small_threads_ = std::max(32, (1 << small_logL_max_) / fft_per_thread<C2>());
     smem_small_ = (size_t)((1 << small_logL_max_) + (1 << small_logL_max_) / 32) * sizeof(C2);
     ECHK(cudaFuncSetAttribute(k_filter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_small_));
-    ECHK(cudaFuncSetAttribute(k_dft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_small_));
+    // the long-row DFT blocks (one per SM by registers) also take the prefetch row where it fits:
+    // a row of L <= 10240 with its spectrum, within the block's shared-memory limit
+    {
+      int optin = 0;
+      ECHK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_));
+      const size_t kStatic = (size_t)(kTwLo + kSingleMaxLf / kTwLo) * sizeof(C2);   // k_dft's static tables
+      const int Lp = std::min(1 << small_logL_max_, 10240);
+      const size_t want = (size_t)(Lp + Lp / 32 + Lp) * sizeof(C2);
+      smem_dft_ = std::max(smem_small_, want + kStatic <= (size_t)optin ? want : (size_t)0);
+    }
+    ECHK(cudaFuncSetAttribute(k_dft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dft_));
     if (any_big_) {
       size_t sa = 0, sb = 0;
       for (int lg = single_logL + 1; lg <= logL_big_max_; ++lg) {
@@ -973,14 +1011,15 @@ class Engine final : public EngineBase {
     k_filter<T><<<n_, thr_s, smem_s, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, tws, (C2*)bhat_, 1);
     ECHK(cudaGetLastError());
     k_dft<T><<<(unsigned)rows_max_, thr_s, smem_s, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_,
-                                                          (C2*)bhat_, tws, (C2*)Y_, 1);
+                                                          (C2*)bhat_, tws, (C2*)Y_, 1, (int)smem_s);
     ECHK(cudaGetLastError());
     if (small_logL_max_ > kSmallFftLog) {
       k_filter<T><<<n_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, tws, (C2*)bhat_,
                                                            0);
       ECHK(cudaGetLastError());
-      k_dft<T><<<(unsigned)rows_max_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
-                                                                           (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 0);
+      k_dft<T><<<(unsigned)rows_max_, small_threads_, smem_dft_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
+                                                                         (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 0,
+                                                                         (int)smem_dft_);
       ECHK(cudaGetLastError());
     }
     return cudaSuccess;
@@ -1462,6 +1501,7 @@ class Engine final : public EngineBase {
   int peel_gx_ = 1;         // k_peel blocks per signal
   int logL_big_max_ = 0, small_logL_max_ = 1, small_threads_ = 256, n_ptab_ = 0;
   size_t smem_small_ = 0, smem_bigA_ = 0, smem_bigB_ = 0, bytes_ = 0, host_stage_bytes_ = 0;
+  size_t smem_dft_ = 0;   // the long-row DFT kernel's dynamic shared memory (row + prefetch row)
   int64_t rows_max_ = 0;
   int64_t Lmax_ = 2, p_max_ = 2, part_cap_ = 0, hash_total_ = 0, k_max_ = 0, kd_max_ = 0, reg_cap_max_ = 0;
   std::vector<SigCfg> cfg_host_;

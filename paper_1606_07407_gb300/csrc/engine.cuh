@@ -70,6 +70,8 @@ struct SigRun {
   int64_t p;
   unsigned long long mod_m;   // floor((2^64 - 1) / p), Barrett reduction
   unsigned long long proj_off;   // (box_lo mod p)(sum of u mod p) mod p, for project_mod
+  unsigned int mod32;            // floor((2^32 - 1) / p) when (N + 1) p < 2^32, else 0
+  unsigned int pad32;
   int64_t part_off;
   unsigned long long maxy0_bits;
   double a_ref;

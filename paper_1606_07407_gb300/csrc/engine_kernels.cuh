@@ -17,11 +17,41 @@ __device__ __forceinline__ uint64_t mod_barrett(uint64_t x, uint64_t p, uint64_t
 // (w . u) mod p for w in the box [box_lo, box_lo + N)^d and u reduced mod p, as
 // sum_l (w_l - box_lo) u_l + box_lo sum_l u_l with every step reduced (w_l - box_lo < 2^31, u_l < p).
 // off = (box_lo mod p) (sum_l u_l mod p) mod p, a constant of the round (proj_offset)
+// Up to 8 coordinates are loaded together before the reduction chain (their loads overlap).
+// m32 = floor((2^32 - 1) / p) when (N + 1) p < 2^32 (every partial sum fits 32 bits: 32-bit
+// Barrett steps), else 0 (64-bit steps).
 __device__ __forceinline__ uint64_t project_mod(const int32_t* w, int d, const int64_t* u, int box_lo, int64_t p,
-                                                uint64_t mm, uint64_t off) {
+                                                uint64_t mm, uint64_t off, uint32_t m32) {
   const uint64_t up = (uint64_t)p;
   uint64_t acc = 0;
-  for (int l = 0; l < d; ++l) acc = mod_barrett((uint64_t)(int64_t)(w[l] - box_lo) * (uint64_t)u[l] + acc, up, mm);
+  if (d <= 8) {
+    int32_t wv[8];
+    int64_t uv[8];
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      wv[l] = l < d ? w[l] : box_lo;
+      uv[l] = l < d ? u[l] : 0;
+    }
+    if (m32 != 0u) {
+      const uint32_t p32 = (uint32_t)p;
+      uint32_t a32 = 0;
+#pragma unroll
+      for (int l = 0; l < 8; ++l) {
+        if (l < d) {
+          const uint32_t x = (uint32_t)(wv[l] - box_lo) * (uint32_t)uv[l] + a32;
+          const uint32_t r = x - __umulhi(x, m32) * p32;
+          a32 = r >= p32 ? r - p32 : r;
+        }
+      }
+      acc = a32;
+    } else {
+#pragma unroll
+      for (int l = 0; l < 8; ++l)
+        if (l < d) acc = mod_barrett((uint64_t)(int64_t)(wv[l] - box_lo) * (uint64_t)uv[l] + acc, up, mm);
+    }
+  } else {
+    for (int l = 0; l < d; ++l) acc = mod_barrett((uint64_t)(int64_t)(w[l] - box_lo) * (uint64_t)u[l] + acc, up, mm);
+  }
   acc += off;   // < 2p
   return acc >= up ? acc - up : acc;
 }

@@ -14,6 +14,7 @@ namespace sfft {
 constexpr int kFusedMaxL = 1024;       // longest Bluestein length of the fused path (half line <= 256)
 constexpr int kFusedMaxSets = 7;       // most sample sets: n_sets + 1 transforms of >= 32 threads each
 constexpr int kFusedChunk = 256;       // modes staged in shared memory at a time
+constexpr int kFusedMaxD = 64;         // directions up to this many coordinates are kept in shared memory
 constexpr int kFusedHostRounds = 4;    // fused rounds per round when the host enqueues rounds
 
 // Device buffers and tables of the engine, as the fused kernel reads and writes them.

@@ -35,7 +35,8 @@ namespace {
 // Samples of every set into the DFT rows: slot n + 1 gets chirp[x] y_n[x] at x < p.
 template <int NS>
 __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c, const SigRun& r, int s,
-                                             const float2* tab_s, float2* slots, int ls, unsigned char* work) {
+                                             const int64_t* u_s, const float2* tab_s, float2* slots, int ls,
+                                             unsigned char* work) {
   using C2 = float2;
   const int tid = threadIdx.x;
   const int p = (int)r.p;
@@ -58,10 +59,14 @@ __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c
     for (int jj = tid; jj < cnt; jj += blockDim.x) {
       C2 a0;
       const C2* twr;
-      m_al[jj] = (int)mode_source<float>(c, r, j0 + jj, a.ubuf, sw, sa, a.tw, a.regw, a.rega, a.regtw, &a0, &twr);
+      const int32_t* w = mode_source<float>(c, r, j0 + jj, sw, sa, a.tw, a.regw, a.rega, a.regtw, &a0, &twr);
+      C2 t[NS > 1 ? NS - 1 : 1];   // loaded with w, before the projection's chain
+#pragma unroll
+      for (int n = 1; n < NS; ++n) t[n - 1] = twr[n - 1];
+      m_al[jj] = (int)project_mod(w, c.d, u_s, c.box_lo, r.p, r.mod_m, r.proj_off, r.mod32);
       m_C[jj * NS] = a0;
 #pragma unroll
-      for (int n = 1; n < NS; ++n) m_C[jj * NS + n] = cmul(a0, twr[n - 1]);
+      for (int n = 1; n < NS; ++n) m_C[jj * NS + n] = cmul(a0, t[n - 1]);
     }
     __syncthreads();
     if (on) {
@@ -180,7 +185,7 @@ __device__ __forceinline__ void fused_peel(const SigCfg& c, const SigRun& r, flo
       av[q] = jr < nr ? ra[jr] : make_double2(0.0, 0.0);
 #pragma unroll
       for (int n = 0; n < NS - 1; ++n) tv[q][n] = jr < nr ? rt[(int64_t)jr * (NS - 1) + n] : make_float2(0.f, 0.f);
-      h[q] = jr < nr ? (int)project_mod(rw + (int64_t)jr * c.d, c.d, u, c.box_lo, r.p, r.mod_m, r.proj_off) : -1;
+      h[q] = jr < nr ? (int)project_mod(rw + (int64_t)jr * c.d, c.d, u, c.box_lo, r.p, r.mod_m, r.proj_off, r.mod32) : -1;
     }
 #pragma unroll
     for (int q = 0; q < U; ++q) {
@@ -237,6 +242,7 @@ __global__ void __launch_bounds__(kSampleThreads, 2) k_fused(FusedArgs a) {
   __shared__ int s_cnt;
   __shared__ PlanArgs s_pa;
   __shared__ PrimeTables s_pt;
+  __shared__ int64_t s_u[kFusedMaxD];   // the round's direction (d <= kFusedMaxD)
   const int s = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31;
   if (s >= a.pa.n) return;
@@ -252,6 +258,8 @@ __global__ void __launch_bounds__(kSampleThreads, 2) k_fused(FusedArgs a) {
     s_pt = a.pt;
     s_cnt = 0;
   }
+  if (c.d <= kFusedMaxD && tid < c.d) s_u[tid] = a.ubuf[c.u_off + tid];
+  const int64_t* u_s = c.d <= kFusedMaxD ? s_u : a.ubuf + c.u_off;
   __syncthreads();
   const SigRun& r = rs;
   const int p = (int)r.p;
@@ -271,14 +279,14 @@ __global__ void __launch_bounds__(kSampleThreads, 2) k_fused(FusedArgs a) {
     const int n = e / (L - p), x = p + (e - n * (L - p));
     slots[(n + 1) * ls + fpad(x)] = mk2(0.0f, 0.0f);
   }
-  fused_sample<NS>(a, c, r, s, tab_s, slots, ls, work);
+  fused_sample<NS>(a, c, r, s, u_s, tab_s, slots, ls, work);
   __syncthreads();
 
   C2* Ys = reinterpret_cast<C2*>(work);   // the modes and partial sums are consumed
   fused_convolve(c, r, tab_s, slots, ls, tw_hi, tw_lo, Ys, &rp->maxy0_bits);
   __syncthreads();
   if (c.peel_bins) {
-    fused_peel<NS>(c, r, Ys, a.ubuf + c.u_off, a.regw, a.rega, a.regtw);
+    fused_peel<NS>(c, r, Ys, u_s, a.regw, a.rega, a.regtw);
     __syncthreads();
   }
 

@@ -119,6 +119,7 @@ __device__ void plan_signal(const PlanArgs& a, const SigCfg& c, SigRun& r, const
         }
       }
       r.proj_off = proj_offset(c.d, ubuf + c.u_off, c.box_lo, p, r.mod_m);
+      r.mod32 = (uint64_t)(c.N + 1) * (uint64_t)p < (1ull << 32) ? 0xFFFFFFFFu / (uint32_t)p : 0u;
       const int K = a.force ? a.force_K : sampled_modes(c, r);
       r.logL = max(ceil_log2(2 * p - 1), 5);   // at least 32 points
       r.L = bluestein_length(2 * p - 1);
@@ -173,14 +174,14 @@ __device__ __forceinline__ void table_entry(int64_t p, unsigned long long mod_m,
 }
 
 // Mode j of a signal this round (black box for j < k, with frequencies sw and coefficients sa;
-// registry with -a after): returns its projection alpha_j = (w_j . u) mod p, with its
-// coefficient in *a0 and its row of twiddles e^{2 pi i w_j . s_n}, n = 1 .. n_sets - 1, in *twr.
+// registry with -a after): returns its frequency vector, with its coefficient in *a0 and its
+// row of twiddles e^{2 pi i w_j . s_n}, n = 1 .. n_sets - 1, in *twr.
 template <typename T>
-__device__ __forceinline__ uint64_t mode_source(const SigCfg& c, const SigRun& r, int j,
-                                                const int64_t* __restrict__ ubuf, const int32_t* __restrict__ sw,
-                                                const double2* __restrict__ sa, const c2<T>* __restrict__ tw,
-                                                const int32_t* __restrict__ regw, const double2* __restrict__ rega,
-                                                const c2<T>* __restrict__ regtw, c2<T>* a0, const c2<T>** twr) {
+__device__ __forceinline__ const int32_t* mode_source(const SigCfg& c, const SigRun& r, int j,
+                                                      const int32_t* __restrict__ sw, const double2* __restrict__ sa,
+                                                      const c2<T>* __restrict__ tw, const int32_t* __restrict__ regw,
+                                                      const double2* __restrict__ rega,
+                                                      const c2<T>* __restrict__ regtw, c2<T>* a0, const c2<T>** twr) {
   const int d = c.d;
   const int32_t* w;
   double2 a;
@@ -198,10 +199,10 @@ __device__ __forceinline__ uint64_t mode_source(const SigCfg& c, const SigRun& r
     *twr = regtw + c.regtw_off + (int64_t)jr * S;
   }
   *a0 = mk2((T)a.x, (T)a.y);
-  return project_mod(w, d, ubuf + c.u_off, c.box_lo, r.p, r.mod_m, r.proj_off);
+  return w;
 }
 
-// The round's tables entry of mode j: alpha_j, ga_j = 32 alpha_j mod p and
+// The round's tables entry of mode j: alpha_j = (w_j . u) mod p, ga_j = 32 alpha_j mod p and
 // C[n][j] = a_j e^{2 pi i w_j . s_n}.
 template <typename T>
 __device__ __forceinline__ void mode_entry(const SigCfg& c, const SigRun& r, int s, int j, const int64_t* __restrict__ ubuf,
@@ -212,7 +213,8 @@ __device__ __forceinline__ void mode_entry(const SigCfg& c, const SigRun& r, int
                                            int32_t* __restrict__ gam, c2<T>* __restrict__ Cm) {
   c2<T> a0;
   const c2<T>* twr;
-  const uint64_t acc = mode_source<T>(c, r, j, ubuf, sig_w[s], sig_a[s], tw, regw, rega, regtw, &a0, &twr);
+  const int32_t* w = mode_source<T>(c, r, j, sig_w[s], sig_a[s], tw, regw, rega, regtw, &a0, &twr);
+  const uint64_t acc = project_mod(w, c.d, ubuf + c.u_off, c.box_lo, r.p, r.mod_m, r.proj_off, r.mod32);
   alpha[c.mode_off + j] = (int32_t)acc;
   gam[c.mode_off + j] = (int32_t)mod_barrett(acc * 32u, (uint64_t)r.p, r.mod_m);
   c2<T>* crow = Cm + c.C_off + j;
@@ -271,7 +273,7 @@ __device__ __forceinline__ void peel_entry(const SigCfg& c, const SigRun& r, int
   if (a.x == 0.0 && a.y == 0.0) return;   // pruned
   const int64_t p = r.p;
   const int64_t h = (int64_t)project_mod(regw + c.regw_off + (int64_t)jr * c.d, c.d, u, c.box_lo, p, r.mod_m,
-                                         r.proj_off);
+                                         r.proj_off, r.mod32);
   // -p a, then -p a e^{2 pi i w . s_n} for n >= 1, in T (float policy: the double pipe is narrow)
   const T px = (T)(-(double)p * a.x), py = (T)(-(double)p * a.y);
   add(h, px, py);
