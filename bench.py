@@ -345,33 +345,53 @@ def run_ours(args):
     peak = props.multi_processor_count * FP32_ALU_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     tot_class = sum(class_ms.values())
 
-    # end to end through the public API with host buffers: the step's inputs (all signals' modes,
-    # packed) copied pinned host -> device, the signal handles refilled in place by one call,
-    # recovery, device -> host of the results
+    # end to end through the public API with host buffers: per step, the step's inputs (all
+    # signals' modes, packed) copied pinned host -> device, the signal handles refilled in place by
+    # one call, recovery, device -> host of the results.  The steps are pipelined over a second
+    # stream: step i + 1's inputs and step i - 1's results cross PCIe/C2C while step i recovers
+    # (double-buffered inputs and outputs); the wall clock runs from the first copy to the last.
     host_fw = torch.from_numpy(np.concatenate([s.freqs.astype(np.int32).reshape(-1) for s in sigs])).pin_memory()
     host_ca = torch.from_numpy(np.concatenate([s.coeffs.astype(np.complex128) for s in sigs])).pin_memory()
-    dev_fw = torch.empty_like(host_fw, device="cuda")
-    dev_ca = torch.empty_like(host_ca, device="cuda")
+    dev_in = [(torch.empty_like(host_fw, device="cuda"), torch.empty_like(host_ca, device="cuda")) for _ in range(2)]
     ks = [s.k for s in sigs]
     h2d = host_fw.numel() * 4 + host_ca.numel() * 16
-    host_fo = torch.empty(bout[1].shape, dtype=torch.int32).pin_memory()
-    host_co = torch.empty(bout[2].shape, dtype=torch.complex128).pin_memory()
-    d2h = host_fo.numel() * 4 + host_co.numel() * 16
-    e2e_ms = 0.0
+    outs2 = [bout, batch.outputs(caps=[wl.k + 16] * nb)]
+    host_out = [(torch.empty(o[1].shape, dtype=torch.int32).pin_memory(),
+                 torch.empty(o[2].shape, dtype=torch.complex128).pin_memory()) for o in outs2]
+    d2h = host_out[0][0].numel() * 4 + host_out[0][1].numel() * 16
+    copy_stream = torch.cuda.Stream()
+    in_ready = [torch.cuda.Event() for _ in range(2)]
+
+    def h2d_step(i):
+        with torch.cuda.stream(copy_stream):
+            fw, ca = dev_in[i % 2]
+            fw.copy_(host_fw, non_blocking=True)
+            ca.copy_(host_ca, non_blocking=True)
+            in_ready[i % 2].record(copy_stream)
+
+    def d2h_step(i):
+        copy_stream.wait_stream(stream)   # the step's results are written (execute has returned)
+        with torch.cuda.stream(copy_stream):
+            host_out[i % 2][0].copy_(outs2[i % 2][1], non_blocking=True)
+            host_out[i % 2][1].copy_(outs2[i % 2][2], non_blocking=True)
+
     e2e_ok = True
-    for _ in range(args.e2e_steps):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2d_step(0)
+    for i in range(args.e2e_steps):
+        if i + 1 < args.e2e_steps:
+            h2d_step(i + 1)
         flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        dev_fw.copy_(host_fw, non_blocking=True)
-        dev_ca.copy_(host_ca, non_blocking=True)
-        sfft.assign_many(dev, dev_fw, dev_ca, ks, stream=stream)
-        res, sts, _ = batch.execute(dev, out=bout, allow=allow)
-        host_fo.copy_(bout[1], non_blocking=True)
-        host_co.copy_(bout[2], non_blocking=True)
-        torch.cuda.synchronize()
-        e2e_ms += 1e3 * (time.perf_counter() - t0)
+        stream.wait_event(in_ready[i % 2])
+        fw, ca = dev_in[i % 2]
+        sfft.assign_many(dev, fw, ca, ks, stream=stream)
+        res, sts, _ = batch.execute(dev, out=outs2[i % 2], allow=allow)
+        d2h_step(i)
         e2e_ok = e2e_ok and all(x == 0 for x in sts) and all(int(n) == wl.k for n in res.n_found)
+    copy_stream.synchronize()
+    torch.cuda.synchronize()
+    e2e_ms = 1e3 * (time.perf_counter() - t0)
     e2e_ms = _max_over_ranks(world, e2e_ms)
     e2e_modes = _sum_over_ranks(world, float(args.e2e_steps * nb * wl.k)) if e2e_ok else 0.0
     e2e_value = e2e_modes / (e2e_ms / 1e3)
@@ -410,7 +430,9 @@ def run_ours(args):
         "gpu_launches": gpu_launches,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "steps": args.e2e_steps},
+                "steps": args.e2e_steps,
+                "form": "public API (assign_many + batch execute), host buffers, copies of step i+1 / i-1 "
+                        "overlapping step i on a second stream, L2 flushed before each step (inside the clock)"},
     }
     if launches_step is not None:
         line["launches_per_step"] = launches_step
@@ -446,7 +468,7 @@ def main(argv=None):
     ap.add_argument("--other-steps", type=int, default=3)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-baseline-only", action="store_true")

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
                                                        const int64_t* __restrict__ plist, int64_t* ubuf,
                                                        HistRec* hist) {
   __shared__ int s_S;
+  __shared__ int s_own[kPlanThreads];
   const int n = a.n;
   int64_t tiles = 0, active = 0, fused = 0;
   // pass 1: stop rule and round parameters of every signal
@@ -127,10 +128,13 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     __syncthreads();
   }
   const int S = s_S;
-  // pass 2: per-signal work counts and their exclusive scans
+  // pass 2: per-signal work counts and their exclusive scans.  Consecutive batched signals with
+  // the same prime share one copy of the tables (W, chirp) and of the filter spectrum: that of
+  // the first of them (the owner, from a running max over the chunk).
   int64_t carry[kNumScans];
   for (int q = 0; q < kNumScans; ++q) carry[q] = 0;
   int64_t part_carry = 0;
+  int owner_carry = -1;
   for (int base = 0; base < n; base += blockDim.x) {
     const int s = base + threadIdx.x;
     int64_t v[kNumScans + 1];
@@ -140,20 +144,48 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     if (s < n) {
       r = run[s];
       batched = r.active && !r.fused;
+    }
+    {
+      bool start = true;
+      if (s < n && s > 0 && batched) {
+        const SigRun& q = run[s - 1];
+        start = !(q.active && !q.fused && q.p == r.p);
+      }
+      int own = start ? s : -1;
+      s_own[threadIdx.x] = own;
+      __syncthreads();
+      for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        const int o = threadIdx.x >= off ? s_own[threadIdx.x - off] : -1;
+        __syncthreads();
+        own = max(own, o);
+        s_own[threadIdx.x] = own;
+        __syncthreads();
+      }
+      if (own < 0) own = owner_carry;
+      const int last = s_own[blockDim.x - 1];
+      owner_carry = last >= 0 ? last : owner_carry;
+      __syncthreads();
+      if (batched) {
+        r.tab_at = cfg[own].tab_off;
+        r.bhat_at = cfg[own].bhat_off;
+        r.tab_owner = own == s ? 1 : 0;
+      }
+    }
+    if (s < n) {
       if (batched) {
         const SigCfg& c = cfg[s];
         const int K = a.force ? a.force_K : sampled_modes(c, r);
         int sp = min(S, r.chunks);
         r.jper = ((r.chunks + sp - 1) / sp) * kSampleChunk;
         r.splits = K > 0 ? (K + r.jper - 1) / r.jper : 1;
-        v[SC_TAB] = r.p;
+        v[SC_TAB] = r.tab_owner ? r.p : 0;
         v[SC_MODE] = K;
         v[SC_SAMP0 + r.gsize - 1] = (int64_t)r.n_xt * r.groups * r.splits;
         v[SC_BINS] = r.p;
         if (!r.big) {
           const bool sm = r.L <= (1 << kSmallFftLog);
           v[sm ? SC_ROWS_S : SC_ROWS] = c.n_sets;
-          v[sm ? SC_FILT_S : SC_FILT] = 1;
+          v[sm ? SC_FILT_S : SC_FILT] = r.tab_owner;
         } else {
           int M1, M2, CT, RT;
           big_geom(r.logL, &M1, &M2, &CT, &RT);
@@ -268,7 +300,7 @@ __global__ void __launch_bounds__(kSampleThreads, 2) k_sample(int n, const SigCf
     const int g = (int)(rest % r.groups);
     const int split = (int)(rest / r.groups);
     sample_tile<T, NS>(sm, c, r, xt, g, split, alpha + c.mode_off, gam + c.mode_off, Cm + c.C_off,
-                      tab + c.tab_off, part);
+                      tab + r.tab_at, part);
   }
 }
 
@@ -304,7 +336,7 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_filter(int n, const SigCfg* 
   const SigCfg& c = cfg[s];
   const SigRun& r = run[s];
   const int L = r.L;
-  const C2* chirp = tab + c.tab_off + r.p;
+  const C2* chirp = tab + r.tab_at + r.p;
   fft_tables(tw_hi, tw_lo, L, tws);
 #pragma unroll 8
   for (int x = threadIdx.x; x < L; x += blockDim.x) buf[fpad(x)] = filter_value<T>(x, r.p, L, chirp);
@@ -334,8 +366,8 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   const SigRun r = run[s];
   const int L = r.L;
   const int64_t p = r.p;
-  const C2* chirp = tab + c.tab_off + p;
-  const C2* B = bhat + c.bhat_off;
+  const C2* chirp = tab + r.tab_at + p;   // the tables and filter of the first signal with this prime
+  const C2* B = bhat + r.bhat_at;
   // With room for a second row of L values after the padded row, the filter spectrum is copied
   // there asynchronously during the forward transform, and then the chirp during the inverse
   // one, so that neither product waits on global memory.
@@ -421,7 +453,7 @@ __global__ void k_bigA(int n, const SigCfg* __restrict__ cfg, const SigRun* __re
     const int x2_0 = (int)(local % ntile) * CT;
     const int ls = M1 + 1;
     C2* tw = buf + CT * ls;
-    const C2* chirp = tab + c.tab_off + r.p;
+    const C2* chirp = tab + r.tab_at + r.p;
     for (int j = threadIdx.x; j < M1 / 2; j += blockDim.x) tw[j] = twG[(int64_t)j * (Lmax >> logM1)];
     for (int e = threadIdx.x; e < CT * M1; e += blockDim.x) {
       const int x1 = e / CT, cc = e - x1 * CT;
@@ -526,7 +558,7 @@ __global__ void k_bigC(int n, const SigCfg* __restrict__ cfg, SigRun* run, const
     const int x2_0 = (int)(local % ntile) * CT;
     const int ls = M1 + 1;
     C2* tw = buf + CT * ls;
-    const C2* chirp = tab + c.tab_off + r.p;
+    const C2* chirp = tab + r.tab_at + r.p;
     for (int j = threadIdx.x; j < M1 / 2; j += blockDim.x) tw[j] = twG[(int64_t)j * (Lmax >> logM1)];
     const C2* z = Z + c.z_off + (int64_t)row * L;
     for (int e = threadIdx.x; e < CT * M1; e += blockDim.x) {

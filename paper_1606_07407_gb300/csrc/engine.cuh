@@ -73,6 +73,9 @@ struct SigRun {
   unsigned int mod32;            // floor((2^32 - 1) / p) when (N + 1) p < 2^32, else 0
   unsigned int pad32;
   int64_t part_off;
+  int64_t tab_at, bhat_at;   // this round's W / chirp table and filter spectrum (shared by equal primes)
+  int tab_owner;             // 1: this signal computes them
+  int pad_owner;
   unsigned long long maxy0_bits;
   double a_ref;
   double eta_prune;   // the round's prune level: max(rho A_ref, 6 sigma / sqrt(p))
