@@ -17,8 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libsfft.so")
-SOURCES = ["api.cu", "engine.cu", "fused.cu", "fused_ns12.cu", "fused_ns34.cu", "fused_ns56.cu", "fused_ns7.cu",
-           "noalloc.cu"]
+SOURCES = ["api.cu", "engine.cu", "fused.cu", "noalloc.cu"] + [f"fused_ns{n}.cu" for n in range(1, 8)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", INCLUDE]
 

@@ -1105,6 +1105,7 @@ class Engine final : public EngineBase {
       fa.regtw = (float2*)regtw_;
       fa.hash = hash_;
       fa.tws = tw_src();
+      fa.L_alloc = fuse_L_max_;
       for (int ns = 1; ns <= kFusedMaxSets; ++ns) {
         if (!(fuse_ns_mask_ & (1u << (ns - 1)))) continue;
         ECHK(fused_launch(ns, n_, smem_fused_, st_, fa));
@@ -1525,10 +1526,10 @@ class Engine final : public EngineBase {
   bool profile_ = false, use_graph_ = false, any_big_ = false;
   bool any_peel_ = false;   // some slot removes its registry in the bin domain
   bool any_fuse_ = false;   // some slot may run short rounds in the fused kernel (FP32 engines)
-  int fuse_sets_max_ = 0;   // most sample sets of such a slot
-  unsigned fuse_ns_mask_ = 0;   // set counts of such slots
-  int fuse_L_max_ = 0;      // and its longest fused Bluestein length
-  size_t smem_fused_ = 0;   // dynamic shared memory of the fused kernel
+  int fuse_sets_max_ = 0;      // most sample sets of such a slot
+  unsigned fuse_ns_mask_ = 0;  // set counts of such slots
+  int fuse_L_max_ = 0;         // and its longest fused Bluestein length
+  size_t smem_fused_ = 0;      // dynamic shared memory of the fused kernel
   int2* cand_ = nullptr;    // (slot, bin) of the round's occupied bins, sum of p_max entries
   int peel_gx_ = 1;         // k_peel blocks per signal
   int logL_big_max_ = 0, small_logL_max_ = 1, small_threads_ = 256, n_ptab_ = 0;

@@ -63,7 +63,7 @@ struct SigRun {
   int k_sig;          // modes of the bound black box
   int logL, big;      // power-of-two Bluestein length of the round (four-step path when big)
   int L;              // Bluestein length of the one-block path: m 2^a >= 2p - 1, m in {1, 3, 5}
-  int fused;          // the round runs in the fused small-round kernel (one block for the signal)
+  int fused;          // the round runs in the fused short-round kernel (one block for the signal)
   int n_xt, groups, gsize, chunks, jper, splits;
   int mgroups;        // mode groups per sampling tile (warps sharing rows when p is small)
   int reg_start;      // registry entries at the start of the round

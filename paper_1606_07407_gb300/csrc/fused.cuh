@@ -1,9 +1,11 @@
-// Fused small-round kernel: once a signal's line is short, one block runs a round of
+// Fused short-round kernel: once a signal's line is short, one block runs a round of
 // Algorithm 2 end to end (tables, samples, Bluestein DFT, residual, ratio test and read-out,
 // registry merge, plan of the next round), instead of a dozen batched launches per round
 // that each have little work.  A round runs fused when its Bluestein length is at most the
 // slot's limit: the largest length up to kFusedMaxL whose n_sets + 1 transforms (the rows and
-// the filter) fit the block at once.  FP32 policies only.
+// the filter) fit the block at once.  FP32 policies only.  (A 512-thread variant for lengths
+// up to 2048 measured slower than the batched kernels on round 2 of the d = 5 workload: one
+// block per SM leaves the sampling issue-bound and the batch in two waves.)
 #pragma once
 
 #include "fft_reg.cuh"
@@ -13,7 +15,7 @@ namespace sfft {
 
 constexpr int kFusedMaxL = 1024;       // longest Bluestein length of the fused path (half line <= 256)
 constexpr int kFusedMaxSets = 7;       // most sample sets: n_sets + 1 transforms of >= 32 threads each
-constexpr int kFusedChunk = 256;       // modes staged in shared memory at a time
+constexpr int kFusedChunk = 512;       // modes staged in shared memory at a time (two per thread)
 constexpr int kFusedMaxD = 64;         // directions up to this many coordinates are kept in shared memory
 constexpr int kFusedHostRounds = 4;    // fused rounds per round when the host enqueues rounds
 
@@ -35,6 +37,7 @@ struct FusedArgs {
   float2* regtw;
   int32_t* hash;
   TwSrc<float2> tws;
+  int L_alloc;            // the Bluestein length the shared memory was sized for
 };
 
 // Byte offsets of the fused kernel's shared memory for a round of Bluestein length L and
@@ -67,8 +70,8 @@ int fused_max_length(int n_sets);
 // fused lengths up to max_L.
 size_t fused_smem_bytes(int max_sets, int max_L);
 
-// Per set count ns <= kFusedMaxSets (instantiated in fused_ns*.cu): the shared-memory attribute
-// and one launch.
+// Per set count ns <= kFusedMaxSets (instantiated in fused_ns<ns>.cu): the shared-memory
+// attribute and one launch.
 template <int NS> cudaError_t fused_setup_ns(size_t smem);
 template <int NS> cudaError_t fused_launch_ns(int n_slots, size_t smem, cudaStream_t st, const FusedArgs& a);
 

@@ -20,8 +20,8 @@
 // the transforms Y_n.  The registry's probe rule (entries of earlier rounds are complete) holds
 // as in the batched path, since each round is a launch of its own.
 //
-// Included by the translation units that instantiate the kernel for a few set counts each
-// (they compile in parallel).
+// Included by the translation units that instantiate the kernel, one set count each (they
+// compile in parallel).
 #pragma once
 
 #include "fused.cuh"
@@ -56,6 +56,7 @@ __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c
   for (int j0 = 0; j0 < K; j0 += kFusedChunk) {
     const int cnt = min(kFusedChunk, K - j0);
     if (j0 > 0) __syncthreads();   // every thread is done with the previous chunk
+#pragma unroll 2
     for (int jj = tid; jj < cnt; jj += blockDim.x) {
       C2 a0;
       const C2* twr;
@@ -70,15 +71,31 @@ __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c
     }
     __syncthreads();
     if (on) {
+      // unrolled so that several modes' index chains (load, product, reduction, table load) overlap
+#pragma unroll 4
       for (int jj = g; jj < cnt; jj += G) {
         const C2 E = tab_s[mod_small((unsigned)m_al[jj] * (unsigned)x, p, inv_p)];
+        auto term = [&](int n, float cr, float ci) {
+          acc[n][0] = fmaf(cr, E.x, acc[n][0]);   // P1: c_r e_r
+          acc[n][1] = fmaf(ci, E.y, acc[n][1]);   // P2: c_i e_i
+          acc[n][2] = fmaf(cr, E.y, acc[n][2]);   // P3: c_r e_i
+          acc[n][3] = fmaf(ci, E.x, acc[n][3]);   // P4: c_i e_r
+        };
+        if constexpr (NS % 2 == 0) {
+          // two sets' coefficients per 16-byte load (jj NS is even, so the pair is aligned)
+          const float4* c4 = reinterpret_cast<const float4*>(m_C + jj * NS);
 #pragma unroll
-        for (int n = 0; n < NS; ++n) {
-          const C2 cc = m_C[jj * NS + n];
-          acc[n][0] = fmaf(cc.x, E.x, acc[n][0]);   // P1: c_r e_r
-          acc[n][1] = fmaf(cc.y, E.y, acc[n][1]);   // P2: c_i e_i
-          acc[n][2] = fmaf(cc.x, E.y, acc[n][2]);   // P3: c_r e_i
-          acc[n][3] = fmaf(cc.y, E.x, acc[n][3]);   // P4: c_i e_r
+          for (int n = 0; n < NS; n += 2) {
+            const float4 cc = c4[n / 2];
+            term(n, cc.x, cc.y);
+            term(n + 1, cc.z, cc.w);
+          }
+        } else {
+#pragma unroll
+          for (int n = 0; n < NS; ++n) {
+            const C2 cc = m_C[jj * NS + n];
+            term(n, cc.x, cc.y);
+          }
         }
       }
     }
@@ -204,6 +221,89 @@ __device__ __forceinline__ void fused_peel(const SigCfg& c, const SigRun& r, flo
   }
 }
 
+// Residual in the bin domain, set 0 only: every registry entry of the round's start gets its
+// bin h = (w . u) mod p in hreg (-1 when pruned) and takes -p a off Y_0[h].  The other sets are
+// corrected later at the occupied bins only (fused_peel_bins): the empty-bin test reads set 0
+// alone, and the ratio test and read-out read the other sets at occupied bins only.
+template <int NS>
+__device__ __forceinline__ void fused_peel_set0(const SigCfg& c, const SigRun& r, float2* Ys, const int64_t* u,
+                                                const int32_t* regw, const double2* rega, int16_t* hreg) {
+  constexpr int U = 4;
+  const int nr = min(r.K_reg, c.reg_cap);
+  const float pf = (float)r.p;
+  float* Yt = reinterpret_cast<float*>(Ys);
+  const int32_t* rw = regw + c.regw_off;
+  const double2* ra = rega + c.rega_off;
+  for (int j0 = threadIdx.x; j0 < nr; j0 += U * blockDim.x) {
+    double2 av[U];
+    int h[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int jr = j0 + q * blockDim.x;
+      av[q] = jr < nr ? ra[jr] : make_double2(0.0, 0.0);
+      h[q] = jr < nr ? (int)project_mod(rw + (int64_t)jr * c.d, c.d, u, c.box_lo, r.p, r.mod_m, r.proj_off, r.mod32)
+                     : -1;
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int jr = j0 + q * blockDim.x;
+      if (jr >= nr) continue;
+      const bool live = av[q].x != 0.0 || av[q].y != 0.0;
+      hreg[jr] = live ? (int16_t)h[q] : (int16_t)-1;
+      if (!live) continue;
+      atomicAdd(Yt + 2 * h[q], -pf * (float)av[q].x);
+      atomicAdd(Yt + 2 * h[q] + 1, -pf * (float)av[q].y);
+    }
+  }
+}
+
+// The other sets' residual at the occupied bins (occ[h] != 0): the entries whose bin is
+// occupied add -p a e^{2 pi i w . s_n} to Y_n[h], n >= 1 (four entries per thread, their loads
+// first; a few entries per occupied bin, so few atomics).
+template <int NS>
+__device__ __forceinline__ void fused_peel_bins(const SigCfg& c, const SigRun& r, float2* Ys, const uint8_t* occ,
+                                                const double2* rega, const float2* regtw, const int16_t* hreg) {
+  constexpr int U = 4;
+  constexpr int S = NS - 1 > 0 ? NS - 1 : 1;
+  const int nr = min(r.K_reg, c.reg_cap);
+  const int p = (int)r.p;
+  const float pf = (float)p;
+  float* Yt = reinterpret_cast<float*>(Ys);
+  const double2* ra = rega + c.rega_off;
+  const float2* rt = regtw + c.regtw_off;
+  for (int j0 = threadIdx.x; j0 < nr; j0 += U * blockDim.x) {
+    int h[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int jr = j0 + q * blockDim.x;
+      h[q] = jr < nr ? (int)hreg[jr] : -1;
+      if (h[q] >= 0 && !occ[h[q]]) h[q] = -1;
+    }
+    double2 av[U];
+    float2 tv[U][S];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      if (h[q] < 0) continue;
+      const int jr = j0 + q * blockDim.x;
+      av[q] = ra[jr];
+#pragma unroll
+      for (int n = 0; n < NS - 1; ++n) tv[q][n] = rt[(int64_t)jr * (NS - 1) + n];
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      if (h[q] < 0) continue;
+      const float px = -pf * (float)av[q].x, py = -pf * (float)av[q].y;
+#pragma unroll
+      for (int n = 1; n < NS; ++n) {
+        const float2 t = tv[q][n - 1];
+        const int e = n * p + h[q];
+        atomicAdd(Yt + 2 * e, px * t.x - py * t.y);
+        atomicAdd(Yt + 2 * e + 1, px * t.y + py * t.x);
+      }
+    }
+  }
+}
+
 // ratio test, read-out and registry merge of the occupied bins cand[0..n_cand)
 __device__ __noinline__ void fused_classify(const SigCfg& c, SigRun* rp, int s, const int* cand, int n_cand,
                                             const float2* Ys, const int64_t* ubuf, const int32_t* shblk,
@@ -264,7 +364,7 @@ __global__ void __launch_bounds__(kSampleThreads, 2) k_fused(FusedArgs a) {
   const SigRun& r = rs;
   const int p = (int)r.p;
   const int L = r.L;
-  const FusedLayout lay = fused_layout(L, NS);
+  const FusedLayout lay = fused_layout(a.L_alloc, NS);   // every area at its largest
   C2* tab_s = reinterpret_cast<C2*>(smem_raw + lay.tab);
   C2* slots = reinterpret_cast<C2*>(smem_raw + lay.slots);
   unsigned char* work = smem_raw + lay.work;
@@ -285,8 +385,17 @@ __global__ void __launch_bounds__(kSampleThreads, 2) k_fused(FusedArgs a) {
   C2* Ys = reinterpret_cast<C2*>(work);   // the modes and partial sums are consumed
   fused_convolve(c, r, tab_s, slots, ls, tw_hi, tw_lo, Ys, &rp->maxy0_bits);
   __syncthreads();
+  // the DFT rows are consumed: their area takes the candidate list (p <= kFusedMaxL / 2 entries),
+  // occupied-bin flags (bytes) and the registry entries' bins (int16)
+  int* cand = reinterpret_cast<int*>(slots);
+  uint8_t* occf = reinterpret_cast<uint8_t*>(slots) + 2 * kFusedMaxL;
+  int16_t* hreg = reinterpret_cast<int16_t*>(slots) + 3 * kFusedMaxL / 2;
+  const int hcap = (lay.work - lay.slots) / 2 - 3 * kFusedMaxL / 2;
+  const bool lazy = min(r.K_reg, c.reg_cap) <= hcap;
+  for (int h = tid; h < p; h += blockDim.x) occf[h] = 0;
   if (c.peel_bins) {
-    fused_peel<NS>(c, r, Ys, u_s, a.regw, a.rega, a.regtw);
+    if (lazy) fused_peel_set0<NS>(c, r, Ys, u_s, a.regw, a.rega, hreg);
+    else fused_peel<NS>(c, r, Ys, u_s, a.regw, a.rega, a.regtw);
     __syncthreads();
   }
 
@@ -300,7 +409,6 @@ __global__ void __launch_bounds__(kSampleThreads, 2) k_fused(FusedArgs a) {
   }
   const float a_ref_f = first ? (float)maxy0 / (float)p : (float)r.a_ref;
   const float eta = fmaxf((float)c.rho * (float)p * a_ref_f, 6.0f * (float)c.sigma * sqrtf((float)p));
-  int* cand = reinterpret_cast<int*>(slots);   // the DFT rows are consumed
   for (int h0 = 0; h0 < p; h0 += blockDim.x) {
     const int h = h0 + tid;
     bool occ = false;
@@ -312,11 +420,18 @@ __global__ void __launch_bounds__(kSampleThreads, 2) k_fused(FusedArgs a) {
     int base = 0;
     if (lane == 0 && mask != 0u) base = atomicAdd(&s_cnt, __popc(mask));
     base = __shfl_sync(0xffffffffu, base, 0);
-    if (occ) cand[base + __popc(mask & ((1u << lane) - 1u))] = h;
+    if (occ) {
+      cand[base + __popc(mask & ((1u << lane) - 1u))] = h;
+      occf[h] = 1;
+    }
   }
   __syncthreads();
   const int n_cand = s_cnt;
   if (tid == 0 && n_cand > 0) rp->any_occupied = 1;
+  if (c.peel_bins && lazy && n_cand > 0) {
+    fused_peel_bins<NS>(c, r, Ys, occf, a.rega, a.regtw, hreg);
+    __syncthreads();
+  }
   fused_classify(c, rp, s, cand, n_cand, Ys, a.ubuf, a.shblk, a.regw, a.rega, a.regtw, a.hash);
   __syncthreads();
 

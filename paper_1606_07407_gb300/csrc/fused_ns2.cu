@@ -1,11 +1,9 @@
-// The fused small-round kernel for signals of 1 and 2 sample sets.
+// The fused short-round kernel for signals of 2 sample sets.
 #include "fused_kernel.cuh"
 
 namespace sfft {
 
-template cudaError_t fused_setup_ns<1>(size_t);
 template cudaError_t fused_setup_ns<2>(size_t);
-template cudaError_t fused_launch_ns<1>(int, size_t, cudaStream_t, const FusedArgs&);
 template cudaError_t fused_launch_ns<2>(int, size_t, cudaStream_t, const FusedArgs&);
 
 }  // namespace sfft

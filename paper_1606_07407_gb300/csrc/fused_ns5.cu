@@ -1,11 +1,9 @@
-// The fused small-round kernel for signals of 5 and 6 sample sets.
+// The fused short-round kernel for signals of 5 sample sets.
 #include "fused_kernel.cuh"
 
 namespace sfft {
 
 template cudaError_t fused_setup_ns<5>(size_t);
-template cudaError_t fused_setup_ns<6>(size_t);
 template cudaError_t fused_launch_ns<5>(int, size_t, cudaStream_t, const FusedArgs&);
-template cudaError_t fused_launch_ns<6>(int, size_t, cudaStream_t, const FusedArgs&);
 
 }  // namespace sfft

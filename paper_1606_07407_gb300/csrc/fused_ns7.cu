@@ -1,4 +1,4 @@
-// The fused small-round kernel for signals of 7 sample sets.
+// The fused short-round kernel for signals of 7 sample sets.
 #include "fused_kernel.cuh"
 
 namespace sfft {
