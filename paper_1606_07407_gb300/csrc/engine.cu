@@ -676,8 +676,11 @@ __global__ void __launch_bounds__(256) k_occupied(int n, const SigCfg* __restric
   }
 }
 
+// three blocks per SM (80 registers): one candidate per thread is a chain of global loads and
+// atomics, so more warps hide more of it
 template <typename T>
-__global__ void k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run, const RoundCtl* __restrict__ ctl,
+__global__ void __launch_bounds__(256, 3) k_classify(int n, const SigCfg* __restrict__ cfg, SigRun* run,
+                                                     const RoundCtl* __restrict__ ctl,
                            const int2* __restrict__ cand, const c2<T>* __restrict__ Ybuf,
                            const int64_t* __restrict__ ubuf, const int32_t* __restrict__ shblk, int32_t* regw,
                            double2* rega, c2<T>* regtw, int32_t* hash, ClassifyOut co) {
@@ -1039,11 +1042,13 @@ class Engine final : public EngineBase {
     const int ls = std::min(small_logL_max_, kSmallFftLog);
     const int thr_s = std::max(32, (1 << ls) / fft_per_thread<C2>());
     const size_t smem_s = (size_t)((1 << ls) + (1 << ls) / 32) * sizeof(C2);
+    // short rows: room for the prefetch row too (six blocks per SM by shared memory, eight by registers)
+    const size_t smem_sp = (size_t)((((1 << ls) + (1 << ls) / 32 + 1) & ~1) + (1 << ls)) * sizeof(C2);
     const TwSrc<C2> tws = tw_src();
     k_filter<T><<<n_, thr_s, smem_s, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, tws, (C2*)bhat_, 1);
     ECHK(cudaGetLastError());
-    k_dft<T><<<(unsigned)rows_max_, thr_s, smem_s, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_,
-                                                          (C2*)bhat_, tws, (C2*)Y_, 1, (int)smem_s);
+    k_dft<T><<<(unsigned)rows_max_, thr_s, smem_sp, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_,
+                                                           (C2*)bhat_, tws, (C2*)Y_, 1, (int)smem_sp);
     ECHK(cudaGetLastError());
     if (small_logL_max_ > kSmallFftLog) {
       k_filter<T><<<n_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, tws, (C2*)bhat_,
