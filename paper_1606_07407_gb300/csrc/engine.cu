@@ -145,11 +145,14 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
       r = run[s];
       batched = r.active && !r.fused;
     }
+    // round 1 with the tables made with the engine
+    const bool pre = batched && !a.force && r.round == 1 && cfg[s].tab0_off >= 0 && r.p == cfg[s].p1;
     {
       bool start = true;
-      if (s < n && s > 0 && batched) {
+      if (s < n && s > 0 && batched && !pre) {
         const SigRun& q = run[s - 1];
-        start = !(q.active && !q.fused && q.p == r.p);
+        const bool q_pre = !a.force && q.round == 1 && cfg[s - 1].tab0_off >= 0 && q.p == cfg[s - 1].p1;
+        start = !(q.active && !q.fused && q.p == r.p && !q_pre);
       }
       int own = start ? s : -1;
       s_own[threadIdx.x] = own;
@@ -165,7 +168,11 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
       const int last = s_own[blockDim.x - 1];
       owner_carry = last >= 0 ? last : owner_carry;
       __syncthreads();
-      if (batched) {
+      if (pre) {
+        r.tab_at = cfg[s].tab0_off;
+        r.bhat_at = cfg[s].bhat0_off;
+        r.tab_owner = 0;
+      } else if (batched) {
         r.tab_at = cfg[own].tab_off;
         r.bhat_at = cfg[own].bhat_off;
         r.tab_owner = own == s ? 1 : 0;
@@ -320,7 +327,20 @@ __global__ void k_reduce(const SigCfg* __restrict__ cfg, const SigRun* __restric
 
 // ------------------------------------------------------------------ DFT, one block per row
 
-// spectrum of the Bluestein filter b[m] = conj(chirp[|m|]), |m| < p, one block per signal
+// Spectrum of the Bluestein filter b[m] = conj(chirp[|m|]), |m| < p, by one block into out.
+template <typename T>
+__device__ __forceinline__ void filter_spectrum(int64_t p, int L, const c2<T>* chirp, const TwSrc<c2<T>>& tws,
+                                                c2<T>* out, c2<T>* buf, c2<T>* tw_hi, c2<T>* tw_lo) {
+  fft_tables(tw_hi, tw_lo, L, tws);
+#pragma unroll 8
+  for (int x = threadIdx.x; x < L; x += blockDim.x) buf[fpad(x)] = filter_value<T>(x, p, L, chirp);
+  __syncthreads();
+  fft_row<c2<T>, false>(buf, L, tw_hi, tw_lo);
+#pragma unroll 8
+  for (int x = threadIdx.x; x < L; x += blockDim.x) out[x] = buf[fpad(x)];
+}
+
+// spectrum of the Bluestein filter of each signal that owns its round's tables, one block each
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, 1) k_filter(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run, RoundCtl* ctl,
                          Scans sc, const c2<T>* __restrict__ tab, TwSrc<c2<T>> tws, c2<T>* __restrict__ bhat,
@@ -335,16 +355,24 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_filter(int n, const SigCfg* 
   const int s = find_slot(sc.v[small ? SC_FILT_S : SC_FILT], n, item);
   const SigCfg& c = cfg[s];
   const SigRun& r = run[s];
-  const int L = r.L;
-  const C2* chirp = tab + r.tab_at + r.p;
-  fft_tables(tw_hi, tw_lo, L, tws);
-#pragma unroll 8
-  for (int x = threadIdx.x; x < L; x += blockDim.x) buf[fpad(x)] = filter_value<T>(x, r.p, L, chirp);
-  __syncthreads();
-  fft_row<C2, false>(buf, L, tw_hi, tw_lo);
-  C2* out = bhat + c.bhat_off;
-#pragma unroll 8
-  for (int x = threadIdx.x; x < L; x += blockDim.x) out[x] = buf[fpad(x)];
+  filter_spectrum<T>(r.p, r.L, tab + r.tab_at + r.p, tws, bhat + c.bhat_off, buf, tw_hi, tw_lo);
+}
+
+// The tables and filter spectrum of round 1's prime, made once when the engine is created (the
+// prime is fixed by the plan: the first prime >= max(c k, p_min), or the list's first).
+template <typename T>
+__global__ void k_tables_one(int64_t p, unsigned long long mod_m, c2<T>* __restrict__ t) {
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < p; m += (int64_t)gridDim.x * blockDim.x)
+    table_entry<T>(p, mod_m, m, t);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads, 1) k_filter_one(int64_t p, int L, const c2<T>* __restrict__ chirp,
+                                                             TwSrc<c2<T>> tws, c2<T>* __restrict__ out) {
+  using C2 = c2<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ C2 tw_lo[kTwLo], tw_hi[kSingleMaxLf / kTwLo];
+  filter_spectrum<T>(p, L, chirp, tws, out, reinterpret_cast<C2*>(smem_raw), tw_hi, tw_lo);
 }
 
 template <typename T>
@@ -929,6 +957,37 @@ class Engine final : public EngineBase {
       }
     }
     pfirst_n_ = (int64_t)pfirst.size();
+    // Round 1's prime is fixed by the plan (k* = k): the first prime >= max(c k, p_min), or the
+    // list's first.  Where its transform is one block, its tables and filter spectrum are made
+    // here once, shared by the slots with that prime, and the rounds reuse them every execute.
+    std::vector<int64_t> pre_p, pre_tab, pre_bhat;
+    for (int s = 0; s < n_; ++s) {
+      const SlotDesc& d = slots[s];
+      SigCfg& c = cfg[s];
+      c.tab0_off = c.bhat0_off = -1;
+      c.p1 = 0;
+      int64_t p1 = -1;
+      if (!d.primes.empty()) {
+        p1 = d.primes[0];
+      } else {
+        const int64_t lo = std::max<int64_t>(std::max<int64_t>((int64_t)d.c * std::max<int64_t>(d.k, 1), d.p_min), 2);
+        if (lo < (int64_t)pfirst.size() && pfirst[(size_t)lo] < (int32_t)ptab.size()) p1 = ptab[pfirst[(size_t)lo]];
+      }
+      if (p1 < 2 || p1 > d.p_max || bluestein_length(2 * p1 - 1) > single_max_L<T>()) continue;
+      size_t q = 0;
+      while (q < pre_p.size() && pre_p[q] != p1) ++q;
+      if (q == pre_p.size()) {
+        pre_p.push_back(p1);
+        pre_tab.push_back(tab);
+        pre_bhat.push_back(bhat);
+        tab += 2 * p1;
+        bhat += bluestein_length(2 * p1 - 1);
+      }
+      c.p1 = p1;
+      c.tab0_off = pre_tab[q];
+      c.bhat0_off = pre_bhat[q];
+    }
+    cfg_host_ = cfg;
 
     ECHK(alloc(&cfg_, cfg.size() * sizeof(SigCfg)));
     ECHK(alloc(&run_, n_ * sizeof(SigRun)));
@@ -988,6 +1047,17 @@ class Engine final : public EngineBase {
     small_threads_ = std::max(32, (1 << small_logL_max_) / fft_per_thread<C2>());
     smem_small_ = (size_t)((1 << small_logL_max_) + (1 << small_logL_max_) / 32) * sizeof(C2);
     ECHK(cudaFuncSetAttribute(k_filter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_small_));
+    ECHK(cudaFuncSetAttribute(k_filter_one<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_small_));
+    for (size_t q = 0; q < pre_p.size(); ++q) {
+      const int64_t p1 = pre_p[q];
+      const int L1 = bluestein_length(2 * p1 - 1);
+      C2* t0 = (C2*)tab_ + pre_tab[q];
+      k_tables_one<T><<<(int)std::min<int64_t>((p1 + 255) / 256, 1024), 256, 0, st_>>>(p1, ~0ull / (uint64_t)p1, t0);
+      ECHK(cudaGetLastError());
+      k_filter_one<T><<<1, std::max(32, fft_threads<C2>(L1)), (size_t)(L1 + L1 / 32) * sizeof(C2), st_>>>(
+          p1, L1, t0 + p1, tw_src(), (C2*)bhat_ + pre_bhat[q]);
+      ECHK(cudaGetLastError());
+    }
     // the long-row DFT blocks (one per SM by registers) also take the prefetch row where it fits:
     // a row of L <= 10240 with its spectrum, within the block's shared-memory limit
     {

@@ -45,6 +45,8 @@ struct SigCfg {
   int64_t hash_off;   // int32 [hash_mask + 1]
   int64_t tab_off;    // T2 [2 * p_max]     W[m] = e^{2 pi i m / p}, then chirp[x] = e^{-pi i x^2 / p}
   int64_t bhat_off;   // T2 [L_max]         spectrum of the Bluestein filter
+  int64_t p1;         // round 1's prime when its tables below were made with the engine (else 0)
+  int64_t tab0_off, bhat0_off;   // those tables and filter spectrum (-1: none)
   int64_t Y_off;      // T2 [n_sets * p_max]
   int64_t z_off;      // T2 [(n_sets + 1) * L_max] four-step work space, -1 if never needed
   int64_t u_off;      // int64 [d]           direction of the round, reduced mod p

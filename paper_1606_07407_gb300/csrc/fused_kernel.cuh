@@ -49,9 +49,12 @@ __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c
   const double2* sa = a.sig_a[s];
   int* m_al = reinterpret_cast<int*>(work);
   C2* m_C = reinterpret_cast<C2*>(work + kFusedChunk * sizeof(int));
-  float acc[NS][4];
+  // each chunk's sums go to fresh accumulators that are then added to the running totals
+  // (blocked summation, as in the batched kernel): with many modes a single float sum per
+  // sample would carry the rounding of all K terms
+  float acc[NS][4], tot[NS][4];
 #pragma unroll
-  for (int n = 0; n < NS; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.0f;
+  for (int n = 0; n < NS; ++n) tot[n][0] = tot[n][1] = tot[n][2] = tot[n][3] = 0.0f;
   const int K = sampled_modes(c, r);
   for (int j0 = 0; j0 < K; j0 += kFusedChunk) {
     const int cnt = min(kFusedChunk, K - j0);
@@ -70,34 +73,44 @@ __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c
       for (int n = 1; n < NS; ++n) m_C[jj * NS + n] = cmul(a0, t[n - 1]);
     }
     __syncthreads();
-    if (on) {
-      // unrolled so that several modes' index chains (load, product, reduction, table load) overlap
+    // blocks of 32 of the thread's modes (every G-th of the chunk)
+    for (int j1 = g; j1 < cnt; j1 += 32 * G) {
+#pragma unroll
+      for (int n = 0; n < NS; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.0f;
+      if (on) {
+        const int j_end = min(cnt, j1 + 32 * G);
+        // unrolled so that several modes' index chains (load, product, reduction, table load) overlap
 #pragma unroll 4
-      for (int jj = g; jj < cnt; jj += G) {
-        const C2 E = tab_s[mod_small((unsigned)m_al[jj] * (unsigned)x, p, inv_p)];
-        auto term = [&](int n, float cr, float ci) {
-          acc[n][0] = fmaf(cr, E.x, acc[n][0]);   // P1: c_r e_r
-          acc[n][1] = fmaf(ci, E.y, acc[n][1]);   // P2: c_i e_i
-          acc[n][2] = fmaf(cr, E.y, acc[n][2]);   // P3: c_r e_i
-          acc[n][3] = fmaf(ci, E.x, acc[n][3]);   // P4: c_i e_r
-        };
-        if constexpr (NS % 2 == 0) {
-          // two sets' coefficients per 16-byte load (jj NS is even, so the pair is aligned)
-          const float4* c4 = reinterpret_cast<const float4*>(m_C + jj * NS);
+        for (int jj = j1; jj < j_end; jj += G) {
+          const C2 E = tab_s[mod_small((unsigned)m_al[jj] * (unsigned)x, p, inv_p)];
+          auto term = [&](int n, float cr, float ci) {
+            acc[n][0] = fmaf(cr, E.x, acc[n][0]);   // P1: c_r e_r
+            acc[n][1] = fmaf(ci, E.y, acc[n][1]);   // P2: c_i e_i
+            acc[n][2] = fmaf(cr, E.y, acc[n][2]);   // P3: c_r e_i
+            acc[n][3] = fmaf(ci, E.x, acc[n][3]);   // P4: c_i e_r
+          };
+          if constexpr (NS % 2 == 0) {
+            // two sets' coefficients per 16-byte load (jj NS is even, so the pair is aligned)
+            const float4* c4 = reinterpret_cast<const float4*>(m_C + jj * NS);
 #pragma unroll
-          for (int n = 0; n < NS; n += 2) {
-            const float4 cc = c4[n / 2];
-            term(n, cc.x, cc.y);
-            term(n + 1, cc.z, cc.w);
-          }
-        } else {
+            for (int n = 0; n < NS; n += 2) {
+              const float4 cc = c4[n / 2];
+              term(n, cc.x, cc.y);
+              term(n + 1, cc.z, cc.w);
+            }
+          } else {
 #pragma unroll
-          for (int n = 0; n < NS; ++n) {
-            const C2 cc = m_C[jj * NS + n];
-            term(n, cc.x, cc.y);
+            for (int n = 0; n < NS; ++n) {
+              const C2 cc = m_C[jj * NS + n];
+              term(n, cc.x, cc.y);
+            }
           }
         }
       }
+#pragma unroll
+      for (int n = 0; n < NS; ++n)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) tot[n][k] += acc[n][k];
     }
   }
   if (G > 1) {
@@ -108,7 +121,7 @@ __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c
 #pragma unroll
       for (int n = 0; n < NS; ++n)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) red[(((g - 1) * H + x) * NS + n) * 4 + k] = acc[n][k];
+        for (int k = 0; k < 4; ++k) red[(((g - 1) * H + x) * NS + n) * 4 + k] = tot[n][k];
     }
     __syncthreads();
     if (g == 0) {
@@ -116,7 +129,7 @@ __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c
 #pragma unroll
         for (int n = 0; n < NS; ++n)
 #pragma unroll
-          for (int k = 0; k < 4; ++k) acc[n][k] += red[(((gg - 1) * H + x) * NS + n) * 4 + k];
+          for (int k = 0; k < 4; ++k) tot[n][k] += red[(((gg - 1) * H + x) * NS + n) * 4 + k];
     }
   }
   if (g == 0) {
@@ -125,7 +138,7 @@ __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c
     const bool noisy = r.noise_sigma > 0.0;
 #pragma unroll
     for (int n = 0; n < NS; ++n) {
-      const float P1 = acc[n][0], P2 = acc[n][1], P3 = acc[n][2], P4 = acc[n][3];
+      const float P1 = tot[n][0], P2 = tot[n][1], P3 = tot[n][2], P4 = tot[n][3];
       C2* rb = slots + (n + 1) * ls;
       C2 y = mk2(P1 - P2, P3 + P4);
       if (noisy) y = cadd(y, black_box_noise<float>(r.noise_seed, r.round, n, x, r.noise_sigma));

@@ -31,7 +31,7 @@ struct PlanArgs {
   cudaGraphConditionalHandle cond_fused;   // graph condition: some signal has a fused round planned
 };
 
-__device__ __forceinline__ int ceil_log2(int64_t v) {
+__host__ __device__ inline int ceil_log2(int64_t v) {
   int r = 0;
   while ((1LL << r) < v) ++r;
   return r;
@@ -39,8 +39,8 @@ __device__ __forceinline__ int ceil_log2(int64_t v) {
 
 // Smallest length m 2^a >= max(n, 32) with m in {1, 3, 5}: the cyclic convolution of Bluestein's
 // DFT only needs n = 2p - 1 points, and these lengths factor into the FFT's radices.
-__device__ __forceinline__ int bluestein_length(int64_t n) {
-  n = max(n, (int64_t)32);
+__host__ __device__ inline int bluestein_length(int64_t n) {
+  n = n < 32 ? 32 : n;
   int64_t best = (int64_t)1 << ceil_log2(n);
   for (int m = 3; m <= 5; m += 2) {
     const int64_t L = (int64_t)m << ceil_log2((n + m - 1) / m);

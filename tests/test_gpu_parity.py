@@ -284,6 +284,24 @@ def test_fused_short_rounds_match_oracle_and_cut_launches(sfft, residual):
     assert 3 * launches[True] <= 2 * launches[False]
 
 
+def test_fused_rounds_with_a_registry_too_large_for_shared_memory(sfft):
+    # d = 2 (3 sets), k = 20000: the fused rounds' registry (about k entries) exceeds the shared
+    # list of entry bins (15360 for 3 sets), so they take the whole registry off every set with
+    # atomics instead of set 0 first; both paths recover the planted set
+    sig = draw_signal(2, 4096, 20000, seed=20000, r_lo=1.0, r_hi=10.0)
+    order = np.lexsort(sig.freqs.T[::-1])
+    planted, a_true = sig.freqs[order].astype(np.int64), sig.coeffs[order]
+    got = {}
+    for fuse in (True, False):
+        plan = sfft.Plan(2, 4096, 20000, blocks=(2,), fuse=fuse)   # full unwrap: N^2 >= p
+        f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N))
+        gf, ga = sfft.sort_result(_np(f), _np(a))
+        assert status == 0 and np.array_equal(gf, planted)
+        assert np.max(np.abs(ga - a_true) / np.abs(a_true)) < 1e-4
+        got[fuse] = stats
+    assert got[True]["terms_fused"] > 0 and got[False]["terms_fused"] == 0
+
+
 def test_residual_forms_count_their_sample_terms(sfft):
     # bins: every round sums the black box's k modes; samples: k plus every registry entry
     # made so far (pruned ones included), so from round 2 on more than k + the live count
