@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
                                                        const int64_t* __restrict__ plist, int64_t* ubuf,
                                                        HistRec* hist) {
   __shared__ int s_S;
+  __shared__ unsigned long long s_key;
   __shared__ int s_own[kPlanThreads];
   const int n = a.n;
   int64_t tiles = 0, active = 0, fused = 0;
@@ -106,12 +107,21 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
   const int64_t tot_tiles = block_sum(tiles);
   const int64_t tot_active = block_sum(active);
   const int64_t tot_fused = block_sum(fused);
-  // mode splits: enough sampling items to fill the GPU, within the partial-sum arena
-  if (threadIdx.x == 0) {
-    const int64_t target = 8LL * a.n_sm;
-    int64_t S = tot_tiles > 0 ? (target + tot_tiles - 1) / tot_tiles : 1;
-    s_S = (int)min(max(S, (int64_t)1), (int64_t)64);
+  // mode splits S (1..64): the persistent sampling kernel's 2 n_sm blocks take tiles x S items of
+  // 1/S of the modes each; S minimises its waves per unit of work, ceil(items / blocks) / S, with
+  // 12% per extra split for the partial sums it adds and the DFT reads back (then it is halved to
+  // fit the partial-sum arena).  Thread S - 1 scores S; the smallest score wins, ties to small S.
+  if (threadIdx.x == 0) s_key = ~0ull;
+  __syncthreads();
+  if (threadIdx.x < 64 && tot_tiles > 0) {
+    const int64_t S = threadIdx.x + 1;
+    const int64_t slots = 2LL * a.n_sm;
+    const int64_t waves = (tot_tiles * S + slots - 1) / slots;
+    const unsigned long long score = (unsigned long long)((waves * (100 + 12 * (S - 1)) << 20) / S);
+    atomicMin(&s_key, (score << 6) | (unsigned long long)(S - 1));
   }
+  __syncthreads();
+  if (threadIdx.x == 0) s_S = tot_tiles > 0 ? (int)(s_key & 63ull) + 1 : 1;
   __syncthreads();
   for (;;) {
     const int S = s_S;
