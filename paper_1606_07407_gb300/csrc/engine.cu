@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
                                                        const int64_t* __restrict__ plist, int64_t* ubuf,
                                                        HistRec* hist) {
   __shared__ int s_S;
+  __shared__ int64_t s_part;   // partial-sum elements at the chosen S
   __shared__ unsigned long long s_key;
   __shared__ int s_own[kPlanThreads];
   const int n = a.n;
@@ -133,17 +134,47 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     }
     const int64_t tot = block_sum(part);
     __syncthreads();
+    if (threadIdx.x == 0) s_part = tot;
     if (tot <= a.part_cap || S == 1) break;
     if (threadIdx.x == 0) s_S = S / 2;
     __syncthreads();
   }
   const int S = s_S;
+  // Tail of the sampling queue: when the items (tiles unsplit) leave the persistent kernel's last
+  // wave mostly empty (rem of 2 n_sm blocks busy), the signals whose tiles fall in that wave split
+  // their modes q ways, so their work spreads over the idle blocks, if the partial sums still fit.
+  const int64_t slots = 2LL * a.n_sm;
+  const int64_t rem = tot_tiles % slots;
+  const int64_t tail_from = tot_tiles - rem;   // queue position (in tiles) where the last wave starts
+  int q_tail = 1;
+  if (S == 1 && rem > 0 && 5 * rem < 4 * slots) {
+    const int q = (int)min((int64_t)8, max((int64_t)2, slots / rem));
+    int64_t extra = 0, tcarry = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+      const int s = base + threadIdx.x;
+      int64_t tv[1] = {0}, tt[1];
+      SigRun r;
+      bool batched = false;
+      if (s < n) {
+        r = run[s];
+        batched = r.active && !r.fused;
+        if (batched) tv[0] = (int64_t)r.n_xt * r.groups;
+      }
+      const int64_t tiles_s = tv[0];
+      block_scan_excl<1>(tv, tt);
+      if (batched && tcarry + tv[0] + tiles_s > tail_from)
+        extra += (int64_t)(min(q, r.chunks) - 1) * cfg[s].n_sets * r.p;
+      tcarry += tt[0];
+    }
+    const int64_t tot_extra = block_sum(extra);
+    if (s_part + tot_extra <= a.part_cap) q_tail = q;
+  }
   // pass 2: per-signal work counts and their exclusive scans.  Consecutive batched signals with
   // the same prime share one copy of the tables (W, chirp) and of the filter spectrum: that of
   // the first of them (the owner, from a running max over the chunk).
   int64_t carry[kNumScans];
   for (int q = 0; q < kNumScans; ++q) carry[q] = 0;
-  int64_t part_carry = 0;
+  int64_t part_carry = 0, tile_carry = 0;
   int owner_carry = -1;
   for (int base = 0; base < n; base += blockDim.x) {
     const int s = base + threadIdx.x;
@@ -154,6 +185,14 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     if (s < n) {
       r = run[s];
       batched = r.active && !r.fused;
+    }
+    bool in_tail = false;   // the signal's tiles reach into the last wave (split q_tail ways)
+    if (q_tail > 1) {
+      int64_t tv[1] = {batched ? (int64_t)r.n_xt * r.groups : 0}, tt[1];
+      const int64_t tiles_s = tv[0];
+      block_scan_excl<1>(tv, tt);
+      in_tail = batched && tile_carry + tv[0] + tiles_s > tail_from;
+      tile_carry += tt[0];
     }
     // round 1 with the tables made with the engine
     const bool pre = batched && !a.force && r.round == 1 && cfg[s].tab0_off >= 0 && r.p == cfg[s].p1;
@@ -192,7 +231,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
       if (batched) {
         const SigCfg& c = cfg[s];
         const int K = a.force ? a.force_K : sampled_modes(c, r);
-        int sp = min(S, r.chunks);
+        int sp = min(in_tail ? q_tail : S, r.chunks);
         r.jper = ((r.chunks + sp - 1) / sp) * kSampleChunk;
         r.splits = K > 0 ? (K + r.jper - 1) / r.jper : 1;
         v[SC_TAB] = r.tab_owner ? r.p : 0;
