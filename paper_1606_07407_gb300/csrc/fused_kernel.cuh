@@ -158,23 +158,26 @@ __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c
 // largest |Y_0| goes to *maxy0 (the first round's A_ref).  A function of its own, called once:
 // the compiler keeps the unrolled passes in registers only where they are neither in a loop
 // nor at several call sites.
+// E bounds the values a thread holds per pass: 16 (shorter register chains, more passes) where
+// the rows and the filter still fit the block at fft_threads<16>(L) threads each, else 32.
+template <int E>
 __device__ __noinline__ void fused_convolve(const SigCfg& c, const SigRun& r, const float2* tab_s, float2* slots,
                                             int ls, float2* tw_hi, float2* tw_lo, float2* Ys,
                                             unsigned long long* maxy0) {
   using C2 = float2;
   const int p = (int)r.p;
   const int L = r.L;
-  const int nthr = fft_threads<C2>(L);
+  const int nthr = fft_threads<C2, E>(L);
   const int slot = threadIdx.x / nthr, lt = threadIdx.x - slot * nthr;
   const int row = slot - 1;
   const bool data = slot >= 1 && row < c.n_sets;
   const bool act = slot == 0 || data;
   C2* rb = slots + slot * ls;
-  fft_row<C2, false>(rb, L, tw_hi, tw_lo, lt, nthr, act);
+  fft_row<C2, false, E>(rb, L, tw_hi, tw_lo, lt, nthr, act);
   if (data)
     for (int k = lt; k < L; k += nthr) rb[fpad(k)] = cmul(rb[fpad(k)], slots[fpad(k)]);
   __syncthreads();
-  fft_row<C2, true>(rb, L, tw_hi, tw_lo, lt, nthr, data);
+  fft_row<C2, true, E>(rb, L, tw_hi, tw_lo, lt, nthr, data);
   float m2 = 0.0f;   // largest |Y_0|^2 seen by this thread
   if (data) {
     const C2* chirp = tab_s + p;
@@ -396,7 +399,10 @@ __global__ void __launch_bounds__(kSampleThreads, 2) k_fused(FusedArgs a) {
   __syncthreads();
 
   C2* Ys = reinterpret_cast<C2*>(work);   // the modes and partial sums are consumed
-  fused_convolve(c, r, tab_s, slots, ls, tw_hi, tw_lo, Ys, &rp->maxy0_bits);
+  if ((NS + 1) * fft_threads<C2, 16>(L) <= (int)blockDim.x)
+    fused_convolve<16>(c, r, tab_s, slots, ls, tw_hi, tw_lo, Ys, &rp->maxy0_bits);
+  else
+    fused_convolve<32>(c, r, tab_s, slots, ls, tw_hi, tw_lo, Ys, &rp->maxy0_bits);
   __syncthreads();
   // the DFT rows are consumed: their area takes the candidate list (p <= kFusedMaxL / 2 entries),
   // occupied-bin flags (bytes) and the registry entries' bins (int16)
