@@ -41,9 +41,14 @@ __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c
   const int tid = threadIdx.x;
   const int p = (int)r.p;
   const int H = p / 2 + 1;                        // positions of the half line (<= 256)
-  const int G = max(1, (int)blockDim.x / H);      // mode groups
+  // mode groups: thread (g, x) = (tid / H, tid mod H); positions x < extra have G + 1 groups, the
+  // others G, so that every thread of the block has work
+  const int G = max(1, (int)blockDim.x / H);
+  const int extra = (int)blockDim.x - G * H;
   const int g = tid / H, x = tid - g * H;
-  const bool on = g < G;
+  const int Gx = G + (x < extra ? 1 : 0);          // this position's groups
+  const bool on = g < Gx;
+  const int Gmax = G + (extra > 0 ? 1 : 0);
   const float inv_p = 1.0f / (float)p;
   const int32_t* sw = a.sig_w[s];   // the black box's modes
   const double2* sa = a.sig_a[s];
@@ -73,15 +78,15 @@ __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c
       for (int n = 1; n < NS; ++n) m_C[jj * NS + n] = cmul(a0, t[n - 1]);
     }
     __syncthreads();
-    // blocks of 32 of the thread's modes (every G-th of the chunk)
-    for (int j1 = g; j1 < cnt; j1 += 32 * G) {
+    // blocks of 32 of the thread's modes (every Gx-th of the chunk)
+    for (int j1 = g; j1 < cnt; j1 += 32 * Gx) {
 #pragma unroll
       for (int n = 0; n < NS; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.0f;
       if (on) {
-        const int j_end = min(cnt, j1 + 32 * G);
+        const int j_end = min(cnt, j1 + 32 * Gx);
         // unrolled so that several modes' index chains (load, product, reduction, table load) overlap
 #pragma unroll 4
-        for (int jj = j1; jj < j_end; jj += G) {
+        for (int jj = j1; jj < j_end; jj += Gx) {
           const C2 E = tab_s[mod_small((unsigned)m_al[jj] * (unsigned)x, p, inv_p)];
           auto term = [&](int n, float cr, float ci) {
             acc[n][0] = fmaf(cr, E.x, acc[n][0]);   // P1: c_r e_r
@@ -113,8 +118,8 @@ __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c
         for (int k = 0; k < 4; ++k) tot[n][k] += acc[n][k];
     }
   }
-  if (G > 1) {
-    // groups 1..G-1 hand their sums to group 0 through the work area
+  if (Gmax > 1) {
+    // groups 1..Gx-1 hand their sums to group 0 through the work area
     float* red = reinterpret_cast<float*>(work);
     __syncthreads();   // the last chunk is consumed
     if (on && g > 0) {
@@ -125,7 +130,7 @@ __device__ __forceinline__ void fused_sample(const FusedArgs& a, const SigCfg& c
     }
     __syncthreads();
     if (g == 0) {
-      for (int gg = 1; gg < G; ++gg)
+      for (int gg = 1; gg < Gx; ++gg)
 #pragma unroll
         for (int n = 0; n < NS; ++n)
 #pragma unroll
