@@ -433,9 +433,11 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ C2 tw_lo[kTwLo], tw_hi[kSingleMaxLf / kTwLo];
   C2* buf = reinterpret_cast<C2*>(smem_raw);
-  // one block per row (a loop around the unrolled passes would make them spill)
-  const int64_t item = blockIdx.x;
-  if (item >= (small ? ctl->n_rows_s : ctl->n_rows)) return;
+  // one block per row (a loop around the unrolled passes would make them spill), last rows first:
+  // the signals at the end of the sampling queue may carry several mode splits to add
+  const int64_t n_rows = small ? ctl->n_rows_s : ctl->n_rows;
+  if ((int64_t)blockIdx.x >= n_rows) return;
+  const int64_t item = n_rows - 1 - blockIdx.x;
   const int64_t* scan = sc.v[small ? SC_ROWS_S : SC_ROWS];
   const int s = find_slot(scan, n, item);
   const int row = (int)(item - scan[s]);
@@ -688,69 +690,108 @@ __global__ void k_peel(int n, const SigCfg* __restrict__ cfg, const SigRun* __re
 // ------------------------------------------------------------------ classification and registry merge
 
 // Bins of the round whose set-0 magnitude is above the empty-bin level, appended to the
-// candidate list (warp-aggregated); also the first round's reference amplitude A_ref and the
-// flag that some bin is occupied (the stop rule reads it).
+// candidate list; also the first round's reference amplitude A_ref and the flag that some bin is
+// occupied (the stop rule reads it).  A block takes a contiguous range of bins and gathers its
+// candidates in shared memory, with one atomic on the list's counter per kCandBuf of them; a
+// warp whose 32 bins belong to one signal reads that signal's level once.
+constexpr int kCandBuf = 2048;
 template <typename T>
 __global__ void __launch_bounds__(256) k_occupied(int n, const SigCfg* __restrict__ cfg, SigRun* run, RoundCtl* ctl,
                                                   Scans sc, const c2<T>* __restrict__ Ybuf, int2* __restrict__ cand,
                                                   double eta_override) {
-  __shared__ int warp_cnt[8];
-  __shared__ unsigned long long tile_base;
+  __shared__ int2 buf[kCandBuf];
+  __shared__ int s_cnt;
+  __shared__ unsigned long long s_base;
   const int64_t total = ctl->n_bins;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = base + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t per = (total + gridDim.x - 1) / gridDim.x;   // bins of this block
+  const int64_t lo = blockIdx.x * per, hi = min(total, lo + per);
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  auto flush = [&]() {   // all threads: copy the gathered candidates out, one atomic
+    __syncthreads();
+    const int m = min(s_cnt, kCandBuf);
+    if (threadIdx.x == 0) s_base = m > 0 ? atomicAdd(&ctl->n_cand, (unsigned long long)m) : 0ull;
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) cand[s_base + i] = buf[i];
+    __syncthreads();
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+  };
+  for (int64_t b0 = lo; b0 < hi; b0 += blockDim.x) {
+    const int64_t e = b0 + threadIdx.x;
+    const bool valid = e < hi;
+    const int s = valid ? find_slot(sc.v[SC_BINS], n, e) : -1;
+    const int s0 = __shfl_sync(0xffffffffu, s, 0);
+    const bool uni = __all_sync(0xffffffffu, !valid || s == s0);
     bool occ = false;
-    int s = 0;
     int64_t h = 0;
-    if (e < total) {
-      s = find_slot(sc.v[SC_BINS], n, e);
-      h = e - sc.v[SC_BINS][s];
-      const SigCfg& c = cfg[s];
-      SigRun* rp = run + s;
+    // the signal's level: by lane 0 for the warp when its bins share the signal, else per lane
+    T lvl = (T)0;   // squared level in float, the level itself in double
+    auto level = [&](int ss) -> T {
+      const SigCfg& c = cfg[ss];
+      SigRun* rp = run + ss;
       const int64_t p = rp->p;
       const bool first = rp->round == 1;
       const double maxy0 = __longlong_as_double((long long)rp->maxy0_bits);
+      if (sizeof(T) == 4) {
+        // float policy: the squared level in float (the double pipe of this GPU is narrow, and
+        // the level is a heuristic far from any mode's size)
+        const float a_ref = first ? (float)maxy0 / (float)p : (float)rp->a_ref;
+        const float eta = eta_override >= 0.0 ? (float)eta_override
+                                               : fmaxf((float)c.rho * (float)p * a_ref,
+                                                       6.0f * (float)c.sigma * sqrtf((float)p));
+        return (T)(eta * eta);
+      }
+      const double a_ref = first ? maxy0 / (double)p : rp->a_ref;
+      return (T)(eta_override >= 0.0 ? eta_override : fmax(c.rho * (double)p * a_ref, 6.0 * c.sigma * sqrt((double)p)));
+    };
+    if (uni) {
+      T l0 = (T)0;
+      if (lane == 0 && s0 >= 0) l0 = level(s0);
+      lvl = __shfl_sync(0xffffffffu, l0, 0);
+    } else if (valid) {
+      lvl = level(s);
+    }
+    if (valid) {
+      const SigCfg& c = cfg[s];
+      SigRun* rp = run + s;
+      h = e - sc.v[SC_BINS][s];
       if (h == 0) {
         // once per signal: A_ref (first round) and the prune level of the round's merges
+        const int64_t p = rp->p;
+        const bool first = rp->round == 1;
+        const double maxy0 = __longlong_as_double((long long)rp->maxy0_bits);
         const double a_ref = first ? maxy0 / (double)p : rp->a_ref;
         if (first) rp->a_ref = a_ref;
         rp->eta_prune = fmax(c.rho * a_ref, 6.0 * c.sigma / sqrt((double)p));
       }
       const c2<T> y0 = Ybuf[c.Y_off + h];
-      if (sizeof(T) == 4) {
-        // float policy: squared magnitude against the squared level, all in float (the double
-        // pipe of this GPU is narrow, and the level is a heuristic far from any mode's size)
-        const float a_ref = first ? (float)maxy0 / (float)p : (float)rp->a_ref;
-        const float eta = eta_override >= 0.0 ? (float)eta_override
-                                               : fmaxf((float)c.rho * (float)p * a_ref,
-                                                       6.0f * (float)c.sigma * sqrtf((float)p));
-        occ = (float)y0.x * (float)y0.x + (float)y0.y * (float)y0.y > eta * eta;
-      } else {
-        const double a_ref = first ? maxy0 / (double)p : rp->a_ref;
-        const double eta = eta_override >= 0.0 ? eta_override
-                                               : fmax(c.rho * (double)p * a_ref, 6.0 * c.sigma * sqrt((double)p));
-        occ = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y) > eta;
-      }
-      if (occ && !rp->any_occupied) rp->any_occupied = 1;
+      if (sizeof(T) == 4) occ = y0.x * y0.x + y0.y * y0.y > lvl;
+      else occ = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y) > (double)lvl;
     }
-    // one slot range of the list per tile: warp counts, their prefix, one atomic
+    // the occupied flag: once per warp for a one-signal warp
     const unsigned mask = __ballot_sync(0xffffffffu, occ);
-    if (lane == 0) warp_cnt[wid] = __popc(mask);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int tot = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        const int cw = warp_cnt[w];
-        warp_cnt[w] = tot;
-        tot += cw;
-      }
-      tile_base = tot > 0 ? atomicAdd(&ctl->n_cand, (unsigned long long)tot) : 0ull;
+    if (uni) {
+      if (lane == 0 && mask != 0u && !run[s0].any_occupied) run[s0].any_occupied = 1;
+    } else if (occ && !run[s].any_occupied) {
+      run[s].any_occupied = 1;
+    }
+    // gather: warp offsets by one shared atomic per warp
+    int wbase = 0;
+    if (lane == 0 && mask != 0u) wbase = atomicAdd(&s_cnt, __popc(mask));
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    if (occ) {
+      const int slot = wbase + __popc(mask & ((1u << lane) - 1u));
+      if (slot < kCandBuf) buf[slot] = make_int2(s, (int)h);
     }
     __syncthreads();
-    if (occ) cand[tile_base + warp_cnt[wid] + __popc(mask & ((1u << lane) - 1u))] = make_int2(s, (int)h);
-    __syncthreads();   // warp_cnt and tile_base are reused by the next tile
+    if (s_cnt > kCandBuf - (int)blockDim.x) {
+      // (kCandBuf >= 2 blockDim: the last tile always fitted)
+      flush();
+    }
   }
+  flush();
 }
 
 // three blocks per SM (80 registers): one candidate per thread is a chain of global loads and
