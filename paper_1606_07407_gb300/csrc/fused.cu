@@ -1,4 +1,4 @@
-// Host side of the fused small-round kernel: which rounds a slot runs fused, the kernel's
+// Host side of the fused short-round kernel: which rounds a slot runs fused, the kernel's
 // shared memory, and the launches (the kernel itself is in fused_kernel.cuh, instantiated by
 // fused_ns*.cu).
 #include <algorithm>

@@ -1,24 +1,28 @@
-// Fused small-round kernel (see fused.cuh).  Each launch runs one round of Algorithm 2 for
+// Fused short-round kernel (see fused.cuh).  Each launch runs one round of Algorithm 2 for
 // every signal whose plan marks it fused, one block of kSampleThreads threads per signal, with
 // the round's data in shared memory:
 //
 //   tables      W[m] = e^{2 pi i m / p} and chirp[m] = e^{-pi i m^2 / p} (table_entry)
 //   samples     y_n[x] = sum_j C[n][j] W[(alpha_j x) mod p] for every set n (Eq. 41), thread
 //               x of the half line taking x and p - x (their exponentials are conjugate), the
-//               modes staged kFusedChunk at a time (mode_source) and split over G groups of
-//               threads when the half line is short; written times the chirp into the rows
+//               modes staged kFusedChunk at a time (mode_source) and split over mode groups of
+//               threads when the half line is short, summed in blocks of 32; written times the
+//               chirp into the rows
 //   DFT         Bluestein (Eq. 3) of the n_sets rows and the filter at once, one row per
-//               fft_threads(L) threads, out into the transforms Y_n
-//   residual    the registry taken off its bins (peel_entry), when it is removed in the bin domain
+//               fft_threads(L) threads (radix-16 passes where they fit), out into Y_n
+//   residual    when the registry is removed in the bin domain: every entry's bin and its set-0
+//               term first; after the empty-bin test, the other sets' terms at the occupied bins
+//               only (or the whole peel, peel_entry's, for a registry beyond the shared list)
 //   classify    empty-bin test, then the ratio test, read-out and registry merge of every
 //               occupied bin (classify_candidate)
 //   plan        the next round (plan_signal): the next launch runs it while it stays short,
 //               else the batched kernels plan it again the same way
 //
-// Shared memory (offsets from fused_layout): the tables (2p), the n_sets + 1 rows of the DFT
-// (padded), and a work area that holds in turn a chunk of modes, the groups' partial sums and
-// the transforms Y_n.  The registry's probe rule (entries of earlier rounds are complete) holds
-// as in the batched path, since each round is a launch of its own.
+// Shared memory (offsets from fused_layout at the allocation's length): the tables (2p), the
+// n_sets + 1 rows of the DFT (padded; afterwards the candidate list, occupied-bin flags and the
+// entries' bins), and a work area that holds in turn a chunk of modes, the groups' partial sums
+// and the transforms Y_n.  The registry's probe rule (entries of earlier rounds are complete)
+// holds as in the batched path, since each round is a launch of its own.
 //
 // Included by the translation units that instantiate the kernel, one set count each (they
 // compile in parallel).

@@ -1,5 +1,5 @@
 // Per-signal steps of one round of Algorithm 2, as device functions: the batched kernels of
-// the round engine call them for many signals at once, and the fused small-round kernel calls
+// the round engine call them for many signals at once, and the fused short-round kernel calls
 // them for one signal per block.
 //
 //   plan_signal         stop rule, the round's prime (Alg. 2), line direction and geometry
