@@ -112,22 +112,64 @@ def line_direction(d: int, N: int, blocks, i: int, dirs=None) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Tilted lines in two dimensions (Sec. 3.3, Eq. 21-27, Alg. 3, Theorem 1)
+# --------------------------------------------------------------------------
+
+
+def tilt_axes(tilt) -> np.ndarray:
+    """The rotated axes of Alg. 3 in the original coordinates.  With sin = height / hypo and
+    cos = base / hypo (Eq. 25), g^(t~) = f(t~_1 base + t~_2 height, -t~_1 height + t~_2 base)
+    (Eq. 27 after the factor hypo), so t~ = e_1 is the point (base, -height) and t~ = e_2 the
+    point (height, base); a mode w is seen with the rotated frequency
+    w~ = (base w_1 - height w_2, height w_1 + base w_2) (Eq. 21 times hypo).
+    Row m - 1 is axis m; round i samples along axis (i mod 2) + 1 (Alg. 3), which line_direction
+    picks from these rows as dirs[i mod 2]."""
+    base, height, _ = (int(v) for v in tilt)
+    return np.array([[base, -height], [height, base]], dtype=np.int64)
+
+
+def tilt_window(N: int, box_lo: int, tilt):
+    """(Q, lo): the read-out modulus and the lowest value of each rotated coordinate over the box
+    [box_lo, box_lo + N)^2.  Both rotated coordinates span (base + height)(N - 1) + 1 values, so
+    the shift eps = 1 / Q with Q = (base + height) N keeps each one unambiguous modulo Q (the
+    role of eps in Alg. 3, which leaves its value open)."""
+    base, height, _ = (int(v) for v in tilt)
+    Q = (base + height) * N
+    lo = (base * box_lo - height * (box_lo + N - 1), (base + height) * box_lo)
+    return Q, lo
+
+
+def check_tilt(tilt) -> None:
+    """Theorem 1's conditions that the read-out relies on: a Pythagorean triple
+    base^2 + height^2 = hypo^2 with gcd(base, height) = 1 (Eq. 25), both legs positive."""
+    base, height, hypo = (int(v) for v in tilt)
+    if base < 1 or height < 1 or base * base + height * height != hypo * hypo or math.gcd(base, height) != 1:
+        raise ValueError("tilt must be a primitive Pythagorean triple (base, height, hypo)")
+
+
+# --------------------------------------------------------------------------
 # Sampling of f - g along the line and its shifted copies (Alg. 2 sampling lines, Eq. 41)
 # --------------------------------------------------------------------------
 
 
-def shift_phases(freqs: np.ndarray, N: int, shift: str = "coord", blocks=None):
+def shift_phases(freqs: np.ndarray, N: int, shift: str = "coord", blocks=None, tilt=None):
     """Exact phases of the shifted sets: (num, q) with w_j . s_n = num[j, n] / q[n] mod 1.
 
     shift "coord" (the general form): s_n = e_n / N, so the phase of set n is w_n mod N over N.
     shift "block" (Alg. 2 as printed, reading A5): set n moves along the unwrap vector v_n of
     block n (N^r on its r-th coordinate, Eq. 35) by eps_n = 1 / (2 N^{d1_n}), d1_n its size, so
     the phase is w~_n / (2 N^{d1_n}) with w~_n = sum_r w_{b_n + r} N^r the block's unwrapped
-    frequency (Eq. 35-36)."""
+    frequency (Eq. 35-36).
+    shift "tilt" (Alg. 3, d = 2): set n moves by eps along rotated axis n (tilt_axes), eps = 1 / Q
+    (tilt_window), so the phase is w~_n / Q with w~_n the n-th rotated frequency (Eq. 27)."""
     freqs = np.asarray(freqs, dtype=np.int64)
     K, d = freqs.shape
     if shift == "coord":
         return np.mod(freqs, N), np.full(d, N, dtype=np.int64)
+    if shift == "tilt":
+        Q, _ = tilt_window(N, 0, tilt)
+        wt = freqs @ tilt_axes(tilt).T                 # [K, 2]: w . (axis n), exact in int64
+        return np.mod(wt, Q), np.full(2, Q, dtype=np.int64)
     starts = block_starts(blocks)
     num = np.zeros((K, len(blocks)), dtype=np.int64)
     q = np.zeros(len(blocks), dtype=np.int64)
@@ -141,7 +183,8 @@ def shift_phases(freqs: np.ndarray, N: int, shift: str = "coord", blocks=None):
 
 
 def sample_sets(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int,
-                chunk: int = 4096, x_values=None, shift: str = "coord", blocks=None) -> np.ndarray:
+                chunk: int = 4096, x_values=None, shift: str = "coord", blocks=None,
+                tilt=None) -> np.ndarray:
     """y[n, x] = sum_j coeffs_j exp(2 pi i w_j . t_{n,x}),  t_{n,x} = x u / p + s_n,
     s_0 = 0 and s_n = e_n / N, for x = 0..p-1 and n = 0..d.
 
@@ -150,18 +193,19 @@ def sample_sets(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int,
     and w . s_n = w_n / N, whose fractional part is (w_n mod N) / N.  Registry modes enter
     with negated coefficients, so the same call evaluates f - g.  ``x_values``, if given,
     restricts the evaluation to those sample indices (columns in the given order).  With
-    shift "block" the shifted sets are those of shift_phases (one per block)."""
+    shift "block" or "tilt" the shifted sets are those of shift_phases (one per block, or one per
+    rotated axis)."""
     freqs = np.asarray(freqs, dtype=np.int64)
     coeffs = np.asarray(coeffs, dtype=np.complex128)
     K, d = freqs.shape
-    S = d if shift == "coord" else len(blocks)
+    S = len(blocks) if shift == "block" else d
     xs = np.arange(p, dtype=np.int64) if x_values is None else np.asarray(x_values, dtype=np.int64)
     y = np.zeros((S + 1, xs.size), dtype=np.complex128)
     if K == 0:
         return y
     u_mod = np.array([int(v) % p for v in u], dtype=np.int64)
     alpha = (freqs @ u_mod) % p                       # (w . u) mod p, exact
-    num, q = shift_phases(freqs, N, shift, blocks)
+    num, q = shift_phases(freqs, N, shift, blocks, tilt)
     shift_frac = num / q[None, :]                     # frac(w . s_n) for n = 1..S
     for x0 in range(0, xs.size, chunk):
         x = xs[x0:x0 + chunk]
@@ -173,7 +217,7 @@ def sample_sets(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int,
 
 
 def registry_bins(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int, shift: str = "coord",
-                  blocks=None) -> np.ndarray:
+                  blocks=None, tilt=None) -> np.ndarray:
     """The DFT of the samples of g = sum_j coeffs_j e^{2 pi i w_j . t}, written without sampling:
     sample set n of one mode is a_j e^{2 pi i w_{j,n} / N} W^{alpha_j x} with alpha_j = (w_j . u)
     mod p (see sample_sets), and sum_x W^{(alpha_j - h) x} is p when h = alpha_j and 0 otherwise
@@ -183,13 +227,13 @@ def registry_bins(freqs: np.ndarray, coeffs: np.ndarray, p: int, u, N: int, shif
     freqs = np.asarray(freqs, dtype=np.int64)
     coeffs = np.asarray(coeffs, dtype=np.complex128)
     K, d = freqs.shape
-    S = d if shift == "coord" else len(blocks)
+    S = len(blocks) if shift == "block" else d
     G = np.zeros((S + 1, p), dtype=np.complex128)
     if K == 0:
         return G
     u_mod = np.array([int(v) % p for v in u], dtype=np.int64)
     alpha = (freqs @ u_mod) % p
-    num, q = shift_phases(freqs, N, shift, blocks)
+    num, q = shift_phases(freqs, N, shift, blocks, tilt)
     for j in range(K):
         G[0, alpha[j]] += p * coeffs[j]
         for n in range(1, S + 1):
@@ -287,8 +331,35 @@ def _decode_blocks(ratio: np.ndarray, N: int, blocks, box_lo: int, delta: float,
     return w
 
 
+def _decode_tilt(ratio: np.ndarray, N: int, tilt, box_lo: int, delta: float):
+    """Frequency pair from the two rotated read-outs (Alg. 3), or None.  Set n gives
+    w~_n = Q Arg(Y_n / Y_0) / (2 pi) (eps = 1 / Q), taken in the window of the box's rotated
+    values; the pair is turned back with [cos sin; -sin cos] (Alg. 3, last step).  The rotated
+    frequencies carry the factor hypo (Eq. 27), so the turn gives hypo^2 w: a pair that is not
+    an exact multiple of hypo^2, or lands outside the box, is no mode's read-out and is
+    rejected."""
+    base, height, hypo = (int(v) for v in tilt)
+    Q, lo = tilt_window(N, box_lo, tilt)
+    wt = []
+    for n in range(2):
+        v = Q * float(arg(ratio[n])) / (2 * np.pi)
+        r = round(v)
+        if abs(v - r) > delta:
+            return None
+        wt.append(lo[n] + (r - lo[n]) % Q)
+    c2 = hypo * hypo
+    x1 = base * wt[0] + height * wt[1]
+    x2 = -height * wt[0] + base * wt[1]
+    if x1 % c2 or x2 % c2:
+        return None
+    w = np.array([x1 // c2, x2 // c2], dtype=np.int64)
+    if np.any(w < box_lo) or np.any(w >= box_lo + N):
+        return None
+    return w
+
+
 def classify(Y: np.ndarray, p: int, u, N: int, eta_bin: float, th: Thresholds,
-             box_lo: int = 0, estimator: str = "set0", shift: str = "coord", blocks=None):
+             box_lo: int = 0, estimator: str = "set0", shift: str = "coord", blocks=None, tilt=None):
     """All bins h = 0..p-1 that hold exactly one mode, with the mode read off.
 
     The coefficient is a = Y_0[h] / p (Eq. 41, estimator "set0") or, with estimator
@@ -298,7 +369,8 @@ def classify(Y: np.ndarray, p: int, u, N: int, eta_bin: float, th: Thresholds,
 
     With shift "block" set n reads the unwrapped frequency of block n,
     w~_n = 2 N^{d1} Arg(Y_n / Y_0) / (2 pi) (Alg. 2 read-out with eps = 1 / (2 N^{d1})), taken in
-    the window of the box's unwrapped values and split into its d1 base-N digits (Alg. 2 wrap-back)."""
+    the window of the box's unwrapped values and split into its d1 base-N digits (Alg. 2 wrap-back).
+    With shift "tilt" the two sets read the rotated pair, turned back by _decode_tilt (Alg. 3)."""
     Y0 = Y[0]
     occupied = np.abs(Y0) > eta_bin
     out = []
@@ -314,6 +386,10 @@ def classify(Y: np.ndarray, p: int, u, N: int, eta_bin: float, th: Thresholds,
             if not np.all(np.abs(v - r) <= th.delta):
                 continue
             w = (np.mod(r.astype(np.int64) - box_lo, N) + box_lo).astype(np.int64)
+        elif shift == "tilt":
+            w = _decode_tilt(Y[1:, h] / Y0[h], N, tilt, box_lo, th.delta)
+            if w is None:
+                continue
         else:
             w = _decode_blocks(Y[1:, h] / Y0[h], N, blocks, box_lo, th.delta, d)
             if w is None:
@@ -321,7 +397,7 @@ def classify(Y: np.ndarray, p: int, u, N: int, eta_bin: float, th: Thresholds,
         if int(w @ u_mod) % p != h:                                  # lands in its own bin
             continue
         if estimator == "mean":
-            num, q = shift_phases(w[None, :], N, shift, blocks)
+            num, q = shift_phases(w[None, :], N, shift, blocks, tilt)
             rot = np.concatenate([[1.0 + 0j], np.exp(-2j * np.pi * num[0] / q)])
             a = complex(np.mean(Y[:, h] * rot) / p)
         else:
@@ -355,7 +431,7 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
                      th: Thresholds | None = None, max_rounds: int | None = None,
                      box_lo: int = 0, primes=None, dirs=None, noise=None,
                      estimator: str = "set0", residual: str = "samples", p_min: int = 0,
-                     shift: str = "coord") -> Result:
+                     shift: str = "coord", tilt=None) -> Result:
     """Algorithm 2 (MultiPhaseshift) on the black box f = sum_j coeffs_j e^{2 pi i freqs_j . t}.
 
     ``primes``, if given, overrides the prime rule (round i uses primes[(i-1) mod len]).
@@ -364,9 +440,17 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
     f: "samples" evaluates f - g at every sample point, as Alg. 2 writes it; "bins" samples f
     alone and subtracts the transform of g bin by bin (registry_bins).  ``p_min`` floors the
     prime rule: round i uses the i-th prime >= max(c k*, p_min).  ``shift`` is "coord" (one
-    shifted set per coordinate, s_n = e_n / N) or "block" (one per block, Alg. 2 as printed)."""
+    shifted set per coordinate, s_n = e_n / N), "block" (one per block, Alg. 2 as printed) or
+    "tilt" (d = 2, Alg. 3: ``tilt`` = (base, height, hypo); the lines run along the rotated axes
+    in turn unless ``dirs`` is given, and the sets shift along them)."""
     if residual not in ("samples", "bins"):
         raise ValueError(residual)
+    if shift == "tilt":
+        if d != 2:
+            raise ValueError("the tilted form (Alg. 3) is two-dimensional")
+        check_tilt(tilt)
+        if dirs is None:
+            dirs = [tuple(int(v) for v in row) for row in tilt_axes(tilt)]
     th = th or Thresholds()
     freqs = np.asarray(freqs, dtype=np.int64).reshape(-1, d)
     coeffs = np.asarray(coeffs, dtype=np.complex128).reshape(-1)
@@ -391,14 +475,14 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
             all_a = np.concatenate([coeffs, reg_a])
         else:
             all_w, all_a = freqs, coeffs
-        y = sample_sets(all_w, all_a, p, u, N, shift=shift, blocks=blocks)
+        y = sample_sets(all_w, all_a, p, u, N, shift=shift, blocks=blocks, tilt=tilt)
         if noise is not None:
             y = y + noise(i, p, y.shape[0] - 1)
         Y = dft(y)
         if R and residual == "bins":
             reg_w = np.array(list(R.keys()), dtype=np.int64).reshape(-1, d)
             Y = Y - registry_bins(reg_w, np.array(list(R.values()), dtype=np.complex128), p, u, N,
-                                  shift=shift, blocks=blocks)
+                                  shift=shift, blocks=blocks, tilt=tilt)
         if a_ref is None:
             a_ref = float(np.max(np.abs(Y[0]))) / p if p > 0 else 0.0
         eta_bin = max(th.rho * p * a_ref, 6.0 * th.sigma * math.sqrt(p))
@@ -409,7 +493,7 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
             rounds.append(stat)
             converged = True
             break
-        acc = classify(Y, p, u, N, eta_bin, th, box_lo, estimator, shift=shift, blocks=blocks)
+        acc = classify(Y, p, u, N, eta_bin, th, box_lo, estimator, shift=shift, blocks=blocks, tilt=tilt)
         for _, w, a in acc:                                    # R <- R u (w, a)
             R[w] = R.get(w, 0j) + a
         eta_prune = max(th.rho * a_ref, 6.0 * th.sigma / math.sqrt(p))

@@ -134,6 +134,123 @@ def test_block_readout_decodes_every_vector_of_a_box():
     assert O._decode_blocks(outside, N, blocks, box_lo, 0.1, 3) is None
 
 
+# ---------------------------------------------------------------- tilted lines (Sec. 3.3, Alg. 3)
+
+TILT_16 = (40, 9, 41)   # base, height, hypo: 40^2 + 9^2 = 41^2, base > 2 N for N = 16 (Theorem 1)
+TILT_32 = (84, 13, 85)  # base > 2 N for N = 32
+
+
+def _box(N, lo):
+    g = np.arange(lo, lo + N)
+    return np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2)
+
+
+def test_tilt_theorem1_rotated_coordinates_separate_every_pair_of_the_box():
+    # Theorem 1: with tan(theta) = height / base, base > 2N and gcd(base, height) = 1, no two
+    # frequency pairs of the box share either rotated coordinate (brute force over all pairs);
+    # the triple (4, 3, 5) at the same N breaks the condition and has such pairs
+    for N, lo in ((16, 0), (16, -8)):
+        W = _box(N, lo)
+        for tilt, distinct in ((TILT_16, True), ((4, 3, 5), False)):
+            wt = W @ O.tilt_axes(tilt).T
+            sep = all(len(set(wt[:, m].tolist())) == len(W) for m in range(2))
+            assert sep == distinct
+
+
+def _check_tilt_samples_against_rationals(sample_fn):
+    # Eq. 27: g^(t~) = f(t~_1 base + t~_2 height, -t~_1 height + t~_2 base), sampled at
+    # t~ = (x / p) e_m + eps e_n (Alg. 3), eps = 1 / ((base + height) N); exact rational phases
+    rng = Stream(21)
+    N, p = 16, 13
+    base, height, _ = TILT_16
+    eps = Fraction(1, (base + height) * N)
+    freqs = rng.integers(8, 0, N).reshape(4, 2)
+    coeffs = rng.uniform(4) + 1j * rng.uniform(4)
+    for m in (1, 2):
+        u = [base, -height] if m == 1 else [height, base]
+        y = sample_fn(freqs, coeffs, p, u, N)
+        assert y.shape == (3, p)
+        for n in range(3):
+            for x in range(p):
+                tt = [Fraction(x, p) if m == 1 else Fraction(0), Fraction(x, p) if m == 2 else Fraction(0)]
+                if n:
+                    tt[n - 1] += eps
+                t = (tt[0] * base + tt[1] * height, -tt[0] * height + tt[1] * base)
+                want = 0j
+                for w, a in zip(freqs, coeffs):
+                    ph = int(w[0]) * t[0] + int(w[1]) * t[1]
+                    ph -= math.floor(ph)
+                    want += a * complex(math.cos(2 * math.pi * ph), math.sin(2 * math.pi * ph))
+                assert abs(y[n, x] - want) < 1e-12
+
+
+def test_tilt_samples_equal_exact_rational_evaluation():
+    _check_tilt_samples_against_rationals(
+        lambda f, a, p, u, N: O.sample_sets(f, a, p, u, N, shift="tilt", tilt=TILT_16))
+
+
+def test_tilt_readout_decodes_every_pair_of_a_box_and_rejects_the_rest():
+    # a bin holding one mode has Y_n / Y_0 = e^{2 pi i eps w~_n}, w~ = hypo (w_1 cos - w_2 sin,
+    # w_1 sin + w_2 cos) (Eq. 21 times hypo); every pair of the box must read back exactly, and
+    # a rotated pair that is no box pair's image must be rejected
+    base, height, hypo = TILT_16
+    for N, lo in ((16, 0), (16, -8)):
+        Q = (base + height) * N
+        for w in _box(N, lo):
+            wt = (base * int(w[0]) - height * int(w[1]), height * int(w[0]) + base * int(w[1]))
+            ratio = np.exp(2j * np.pi * np.array(wt, dtype=float) / Q)
+            assert np.array_equal(O._decode_tilt(ratio, N, TILT_16, lo, 0.1), w)
+            for dw in ((1, 0), (0, 1), (hypo, 0)):
+                bad = np.exp(2j * np.pi * np.array([wt[0] + dw[0], wt[1] + dw[1]], dtype=float) / Q)
+                assert O._decode_tilt(bad, N, TILT_16, lo, 0.1) is None
+
+
+def _rectangles(N):
+    # corners of two axis-aligned rectangles: every mode shares its first coordinate with one
+    # other mode and its second with another, so every parallel projection collides
+    xs, ys, xs2, ys2 = (3, N - 5), (5, N - 3), (8, N - 11), (11, N - 2)
+    return np.array([(x, y) for x in xs for y in ys] + [(x, y) for x in xs2 for y in ys2], dtype=np.int64)
+
+
+def test_tilt_recovers_the_worst_case_that_parallel_projections_cannot():
+    # Sec. 3.3: rectangle corners defeat the parallel projections (blocks of 1, lines along e_1
+    # and e_2: no mode is ever alone in its bin); Alg. 3's tilted lines recover the planted set
+    N = 32
+    freqs = _rectangles(N)
+    k = len(freqs)
+    rng = Stream(22)
+    coeffs = (1 + rng.uniform(k)) * np.exp(2j * np.pi * rng.uniform(k))
+    o = np.lexsort(freqs.T[::-1])
+    par = O.multi_phaseshift(freqs, coeffs, 2, N, k, (1, 1), max_rounds=12, residual="bins")
+    assert not par.converged and par.n_found == 0
+    for residual in ("samples", "bins"):
+        r = O.multi_phaseshift(freqs, coeffs, 2, N, k, shift="tilt", tilt=TILT_32, residual=residual)
+        assert r.converged and np.array_equal(r.freqs, freqs[o])
+        assert np.max(np.abs(r.coeffs - coeffs[o])) < 1e-13
+
+
+def test_tilt_recovery_equals_coordinate_shift_recovery():
+    # the tilted form reads the same modes as the per-coordinate form, FP64 coefficients at round-off
+    for N, k, box, seed in ((32, 24, 0, 23), (64, 60, -32, 24)):
+        tilt = TILT_32 if N == 32 else (144, 17, 145)
+        sig = draw_signal(2, N, k, seed=seed, box_lo=box)
+        o = np.lexsort(sig.freqs.T[::-1])
+        rt = O.multi_phaseshift(sig.freqs, sig.coeffs, 2, N, k, box_lo=box, shift="tilt", tilt=tilt,
+                                residual="bins")
+        rc = O.multi_phaseshift(sig.freqs, sig.coeffs, 2, N, k, (1, 1), box_lo=box, residual="bins")
+        assert rt.converged and np.array_equal(rt.freqs, sig.freqs[o].astype(np.int64))
+        assert np.array_equal(rt.freqs, rc.freqs)
+        assert np.max(np.abs(rt.coeffs - sig.coeffs[o])) < 1e-13
+
+
+def test_tilt_needs_a_primitive_pythagorean_triple_in_two_dimensions():
+    for bad in ((4, 3, 6), (6, 8, 10), (0, 1, 1)):
+        with pytest.raises(ValueError):
+            O.check_tilt(bad)
+    with pytest.raises(ValueError):
+        O.multi_phaseshift(np.zeros((1, 3), dtype=np.int64), np.ones(1), 3, 16, 1, shift="tilt", tilt=TILT_16)
+
+
 def test_block_shift_recovery_equals_coordinate_shift_recovery():
     # the two shift forms read the same modes (the paper's shape included: d = 100, N = 20,
     # d1 = 5, |a| = 1, signed box) with FP64 coefficients at round-off
@@ -542,8 +659,8 @@ def test_planted_mistakes_are_caught(monkeypatch):
 
     real_phases = O.shift_phases
 
-    def eps_not_halved(freqs, N, shift="coord", blocks=None):   # eps = 1 / N^{d1}: read-out wraps
-        num, q = real_phases(freqs, N, shift, blocks)
+    def eps_not_halved(freqs, N, shift="coord", blocks=None, tilt=None):   # eps = 1 / N^{d1}: read-out wraps
+        num, q = real_phases(freqs, N, shift, blocks, tilt)
         if shift == "block":
             q = q // 2
             num = np.mod(num, q[None, :])
@@ -556,6 +673,32 @@ def test_planted_mistakes_are_caught(monkeypatch):
         _check_block_samples_against_rationals(
             lambda f, a, p, u, N: O.sample_sets(f, a, p, u, N, shift="block", blocks=(2, 3)))
     monkeypatch.setattr(O, "shift_phases", real_phases)
+
+    real_axes = O.tilt_axes
+
+    def axes_unsigned(tilt):                       # rotated axis 1 taken as (base, height)
+        return np.abs(real_axes(tilt))
+
+    def axes_swapped(tilt):                        # the two rotated axes exchanged
+        return real_axes(tilt)[::-1].copy()
+
+    for bad in (axes_unsigned, axes_swapped):
+        monkeypatch.setattr(O, "tilt_axes", bad)
+        with pytest.raises(AssertionError):
+            _check_tilt_samples_against_rationals(
+                lambda f, a, p, u, N: O.sample_sets(f, a, p, u, N, shift="tilt", tilt=TILT_16))
+        monkeypatch.setattr(O, "tilt_axes", real_axes)
+
+    real_window = O.tilt_window
+
+    def window_unsigned(N, box_lo, tilt):          # the first rotated coordinate's window from 0
+        Q, lo = real_window(N, box_lo, tilt)
+        return Q, (0, lo[1])
+
+    monkeypatch.setattr(O, "tilt_window", window_unsigned)
+    with pytest.raises(AssertionError):
+        test_tilt_readout_decodes_every_pair_of_a_box_and_rejects_the_rest()
+    monkeypatch.setattr(O, "tilt_window", real_window)
 
     real_philox = O.philox4x32_10
 
