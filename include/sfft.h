@@ -105,6 +105,9 @@ typedef struct {
   int unfused;       /* FP32 policies run each signal's rounds of Bluestein length <= 2048 in one
                         fused kernel, one block per signal; 1: every round through the batched
                         kernels (same arithmetic, other summation order of the samples) */
+  int tilt_base;     /* shift = TILT: the rotation of Sec. 3.3, sin = tilt_height / tilt_hypo,  */
+  int tilt_height;   /* cos = tilt_base / tilt_hypo (Eq. 25): a primitive Pythagorean triple,   */
+  int tilt_hypo;     /* both legs >= 1 and <= 2^20; Theorem 1 wants tilt_base > 2 N (see below) */
 } sfft_opts;
 
 /* The shifted sample sets (Alg. 2).  COORD (default): one set per coordinate, shifted by e_n / N,
@@ -113,8 +116,21 @@ typedef struct {
  * v_n / (2 N^{d1}) along the block's unwrap vector (N^r on its r-th coordinate, Eq. 35); it reads
  * the block's unwrapped frequency 2 N^{d1} Arg(Y_n / Y_0) / (2 pi) and splits it into d1 base-N
  * digits; 1 + (number of blocks) sets.  With BLOCK the precision policy follows N^{d1}: AUTO
- * reads phases in double above 2^14, and the float policies return PRECISION above 2^20. */
-typedef enum { SFFT_SHIFT_COORD = 0, SFFT_SHIFT_BLOCK = 1 } sfft_shift;
+ * reads phases in double above 2^14, and the float policies return PRECISION above 2^20.
+ *
+ * TILT (Alg. 3, Sec. 3.3; d = 2 only): the lines run along the rotated axes in turn, axis
+ * (i mod 2) + 1 in round i, which are the integer directions (base, -height) and (height, base)
+ * (Eq. 27 after the factor hypo) unless tilts.dirs gives others; set n = 1, 2 is shifted by
+ * eps = 1 / Q along rotated axis n, Q = (base + height) N.  A mode w is seen with the rotated
+ * frequencies w~ = (base w_1 - height w_2, height w_1 + base w_2), each read as
+ * Q Arg(Y_n / Y_0) / (2 pi) within the box's window; the pair is turned back (Alg. 3, last step)
+ * to hypo^2 w and accepted only when it divides exactly and lands in the box.  With
+ * base > 2 N and gcd(base, height) = 1 no two modes of the box share a rotated coordinate
+ * (Theorem 1), which resolves configurations no parallel projection separates (the corners of
+ * axis-aligned rectangles).  Precision follows Q: AUTO reads phases in double above 2^15, the
+ * float policies return PRECISION above 2^21, and Q may not exceed 2^40.  INVALID_ARG for
+ * d != 2 or a triple that is not primitive Pythagorean. */
+typedef enum { SFFT_SHIFT_COORD = 0, SFFT_SHIFT_BLOCK = 1, SFFT_SHIFT_TILT = 2 } sfft_shift;
 
 /* Alg. 2 removes g (the function of the registry's modes) from f before each round's
  * test (Sec. 5, "Algorithm").  SAMPLES evaluates f - g at every sample point, as the
@@ -227,7 +243,8 @@ sfft_status sfft_batch_execute(sfft_batch batch, const sfft_signal* signals, con
 /* Kernel (a), sample-and-residual (Alg. 2 sampling; Eq. 41): for the K modes
  * (freqs_dev int32 [K x d], coeffs_dev complex128 [K]) writes
  *     y[n][x] = sum_j coeffs_j exp(2 pi i w_j . (x u / p + s_n)),
- * s_0 = 0, s_n = e_n / N, x < p, n <= d, to y_out_dev, row-major [(d+1) x p],
+ * s_0 = 0, s_n the plan's shifted sets (e_n / N unless opts.shift says otherwise),
+ * x < p, n <= d, to y_out_dev, row-major [(d+1) x p],
  * complex64 for float plans and complex128 for FP64 plans.  u: host int64 [d].
  * Requires 2 <= p <= the plan's largest prime; CAPACITY when K exceeds the
  * plan's k. */

@@ -135,7 +135,22 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
   if (o.tau < 0 || o.rho < 0 || o.delta < 0 || o.delta >= 0.5 || o.noise_sigma < 0 || o.max_rounds < 0)
     return SFFT_ERR_INVALID_ARG;
   if (o.residual != SFFT_RESIDUAL_BINS && o.residual != SFFT_RESIDUAL_SAMPLES) return SFFT_ERR_INVALID_ARG;
-  if (o.shift != SFFT_SHIFT_COORD && o.shift != SFFT_SHIFT_BLOCK) return SFFT_ERR_INVALID_ARG;
+  if (o.shift != SFFT_SHIFT_COORD && o.shift != SFFT_SHIFT_BLOCK && o.shift != SFFT_SHIFT_TILT)
+    return SFFT_ERR_INVALID_ARG;
+  if (o.shift == SFFT_SHIFT_TILT) {
+    // Alg. 3 is two-dimensional; sin and cos rational with one denominator (Eq. 25)
+    const int64_t b = o.tilt_base, h = o.tilt_height, hy = o.tilt_hypo;
+    if (d != 2 || b < 1 || h < 1 || b > (1 << 20) || h > (1 << 20) || b * b + h * h != hy * hy)
+      return SFFT_ERR_INVALID_ARG;
+    int64_t x = b, y = h;
+    while (y != 0) {
+      const int64_t t = x % y;
+      x = y;
+      y = t;
+    }
+    if (x != 1) return SFFT_ERR_INVALID_ARG;
+    if ((double)(b + h) * (double)N > std::ldexp(1.0, 40)) return SFFT_ERR_INVALID_ARG;
+  }
 
   std::unique_ptr<sfft_plan_s> P(new sfft_plan_s());
   SlotDesc& D = P->desc;
@@ -220,8 +235,11 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
     for (int q = 0; q < nb; ++q) blocks.push_back(d / nb + (q < d % nb ? 1 : 0));
   }
 
-  // ---- line directions
-  if (tilts && tilts->n_dirs > 0) {
+  // ---- line directions (the tilted form: its two rotated axes unless directions are given)
+  if (o.shift == SFFT_SHIFT_TILT && !(tilts && tilts->n_dirs > 0)) {
+    D.n_dirs = 2;
+    D.dirs = {(int64_t)o.tilt_base, -(int64_t)o.tilt_height, (int64_t)o.tilt_height, (int64_t)o.tilt_base};
+  } else if (tilts && tilts->n_dirs > 0) {
     if (!tilts->dirs) return SFFT_ERR_INVALID_ARG;
     D.dirs.assign(tilts->dirs, tilts->dirs + (size_t)tilts->n_dirs * d);
     D.n_dirs = tilts->n_dirs;
@@ -257,6 +275,17 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
     if (!fp64 && span_max > std::ldexp(1.0, 20)) return SFFT_ERR_PRECISION;
     if (o.precision == SFFT_PREC_AUTO) D.ratio64 = span_max > std::ldexp(1.0, 14) ? 1 : 0;
     D.shift_blocks = blocks;
+  }
+  // the tilted form reads a rotated coordinate (Q = (base + height) N values) from one phase:
+  // the same policy as the block form's 2 N^{d1}
+  D.shift_tilt = o.shift == SFFT_SHIFT_TILT ? 1 : 0;
+  if (D.shift_tilt) {
+    D.tilt_base = o.tilt_base;
+    D.tilt_height = o.tilt_height;
+    D.tilt_hypo = o.tilt_hypo;
+    const double q = (double)(o.tilt_base + o.tilt_height) * (double)N;
+    if (!fp64 && q > std::ldexp(1.0, 21)) return SFFT_ERR_PRECISION;
+    if (o.precision == SFFT_PREC_AUTO) D.ratio64 = q > std::ldexp(1.0, 15) ? 1 : 0;
   }
 
   std::vector<SlotDesc> slots(1, D);

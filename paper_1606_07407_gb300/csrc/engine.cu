@@ -940,6 +940,10 @@ class Engine final : public EngineBase {
       std::memset(&c, 0, sizeof(c));
       c.d = d.d;
       c.shift_block = d.shift_block;
+      c.shift_tilt = d.shift_tilt;
+      c.tilt_base = d.tilt_base;
+      c.tilt_height = d.tilt_height;
+      c.tilt_hypo = d.tilt_hypo;
       c.n_sets = d.shift_block ? 1 + (int)d.shift_blocks.size() : d.d + 1;
       c.fuse_L = (sizeof(T) == 4 && d.fuse) ? fused_max_length(c.n_sets) : 0;
       c.blk_off = (int64_t)shblk.size();

@@ -32,6 +32,8 @@ struct SigCfg {
   int peel_bins;      // the registry leaves the transform bin by bin (else it is sampled with f)
   int shift_block;    // shifted sets move along block unwrap vectors (Alg. 2 as printed), else e_n / N
   int fuse_L;         // rounds of Bluestein length up to this run in the fused kernel (0: none)
+  int shift_tilt;     // Alg. 3 (d = 2): set n shifted by (axis n) / Q, Q = (base + height) N, the
+  int tilt_base, tilt_height, tilt_hypo;   // axes (base, -height) and (height, base)
   int reg_cap, hash_mask, logL_max;
   int64_t N, p_max;
   int64_t p_min;      // floor of the prime rule: the i-th prime >= max(c k*, p_min)
@@ -133,6 +135,8 @@ struct SlotDesc {
   int coef_mean;
   int peel_bins;
   int shift_block;
+  int shift_tilt = 0;              // Alg. 3 (d = 2): sets shifted along the rotated axes
+  int tilt_base = 0, tilt_height = 0, tilt_hypo = 0;
   int fuse = 1;                    // short rounds may run in the fused kernel
   std::vector<int> shift_blocks;   // block sizes of the shifted sets (block form)
   double tau, rho, delta, sigma;

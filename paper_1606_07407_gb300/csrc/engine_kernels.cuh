@@ -102,9 +102,18 @@ template <> __device__ __forceinline__ double2 unit_root<double>(int64_t m, int6
 // w_n mod N of order N.  Block form: s_n = v_n / (2 N^{d1}) along the unwrap vector of block n
 // (start blk[2n - 2], size d1 = blk[2n - 1]), the root of w~_n mod 2 N^{d1} of order 2 N^{d1},
 // w~_n = sum_r w_{start + r} N^r.  in_box: w lies in the box (one conditional wrap suffices).
+// Tilted form (Alg. 3, d = 2): s_n = (axis n) / Q, the root of w~_n mod Q of order Q, with
+// w~_1 = base w_1 - height w_2, w~_2 = height w_1 + base w_2 and Q = (base + height) N.
 template <typename T>
 __device__ __forceinline__ c2<T> shift_root(const SigCfg& c, const int32_t* __restrict__ blk, const int32_t* w,
                                             int n, bool in_box) {
+  if (c.shift_tilt) {
+    const int64_t b = c.tilt_base, h = c.tilt_height, w1 = w[0], w2 = w[1];
+    const int64_t q = (b + h) * c.N;
+    int64_t m = (n == 1 ? b * w1 - h * w2 : h * w1 + b * w2) % q;
+    if (m < 0) m += q;
+    return unit_root<T>(m, q);
+  }
   if (!c.shift_block) {
     int64_t m = w[n - 1];
     if (in_box) {

@@ -350,6 +350,44 @@ __device__ __forceinline__ bool read_block(R ynx, R yny, R y0x, R y0y, int64_t N
   return true;
 }
 
+// Tilted form (Alg. 3, d = 2): sets 1 and 2 read the rotated coordinates w~_n =
+// Q Arg(Y_n / Y_0) / (2 pi), Q = (base + height) N, each in the window of the box's values
+// (lowest: base lo - height (lo + N - 1), then (base + height) lo); the pair is turned back by
+// [cos sin; -sin cos] times hypo, which gives hypo^2 w (the rotated frequencies carry the factor
+// hypo, Eq. 27).  False when a phase is farther than delta from an integer, the turned pair is
+// not a multiple of hypo^2, or w leaves the box.
+template <typename R>
+__device__ __forceinline__ bool read_tilt(const SigCfg& c, R y1x, R y1y, R y2x, R y2y, R y0x, R y0y, int32_t* w) {
+  const int64_t b = c.tilt_base, h = c.tilt_height, hy = c.tilt_hypo;
+  const int64_t N = c.N, lo = c.box_lo;
+  const int64_t q = (b + h) * N;
+  const R pi = (R)3.14159265358979323846;
+  int64_t wt[2];
+#pragma unroll
+  for (int n = 0; n < 2; ++n) {
+    const R ynx = n == 0 ? y1x : y2x, yny = n == 0 ? y1y : y2y;
+    const R re = ynx * y0x + yny * y0y;   // Y_n conj(Y_0)
+    const R im = yny * y0x - ynx * y0y;
+    R phi = atan2(im, re);
+    if (phi >= pi) phi -= (R)2 * pi;
+    const R v = (R)q * phi / ((R)2 * pi);
+    const R rr = rint(v);
+    if (!(fabs(v - rr) <= (R)c.delta)) return false;
+    const int64_t wlo = n == 0 ? b * lo - h * (lo + N - 1) : (b + h) * lo;
+    int64_t t = ((int64_t)rr - wlo) % q;
+    if (t < 0) t += q;
+    wt[n] = wlo + t;
+  }
+  const int64_t c2 = hy * hy;
+  const int64_t x1 = b * wt[0] + h * wt[1], x2 = b * wt[1] - h * wt[0];
+  if (x1 % c2 != 0 || x2 % c2 != 0) return false;
+  const int64_t w1 = x1 / c2, w2 = x2 / c2;
+  if (w1 < lo || w1 >= lo + N || w2 < lo || w2 >= lo + N) return false;
+  w[0] = (int32_t)w1;
+  w[1] = (int32_t)w2;
+  return true;
+}
+
 // Read-out of shifted set n (1-based) of an occupied bin: the coordinate it fixes (coordinate
 // form) or the d1 coordinates of block n (block form) go to w (if not null), and their
 // (w_l - box_lo) u_l are added to *bin mod p.
@@ -384,9 +422,31 @@ struct ClassifyOut {   // step calls: accepted bins are appended here instead of
   double eta_override;
 };
 
-// Eq. 42 ratio test and Eq. 7 read-out of sets 1..d of an occupied bin.  The sets' values are
-// fetched eight at a time so that their loads overlap.  Writes w_n to w_out (if not null) and
-// returns whether every set passes and (w . u) mod p is the bin itself.
+// The tilted form's ratio test (Eq. 42) and read-out of an occupied bin: both sets, then
+// read_tilt; *bin gets sum_l (w_l - box_lo) u_l mod p.
+template <typename T, typename R>
+__device__ __forceinline__ bool decode_tilt(const SigCfg& c, const SigRun& r, const c2<T>* Y, const int64_t* u,
+                                         int64_t h, R y0x, R y0y, R m0, int32_t* w_out, uint64_t* bin) {
+  const uint64_t up = (uint64_t)r.p;
+  const c2<T> y1 = Y[r.p + h], y2 = Y[2 * r.p + h];
+  const R y1x = (R)y1.x, y1y = (R)y1.y, y2x = (R)y2.x, y2y = (R)y2.y;
+  if (!(fabs(sqrt(y1x * y1x + y1y * y1y) / m0 - (R)1) < (R)c.tau)) return false;   // Eq. 42
+  if (!(fabs(sqrt(y2x * y2x + y2y * y2y) / m0 - (R)1) < (R)c.tau)) return false;
+  int32_t wt[2];
+  if (!read_tilt<R>(c, y1x, y1y, y2x, y2y, y0x, y0y, wt)) return false;
+  if (w_out) {
+    w_out[0] = wt[0];
+    w_out[1] = wt[1];
+  }
+  uint64_t b = mod_barrett((uint64_t)(wt[0] - c.box_lo) * (uint64_t)u[0], up, r.mod_m);
+  *bin = mod_barrett((uint64_t)(wt[1] - c.box_lo) * (uint64_t)u[1] + b, up, r.mod_m);
+  return true;
+}
+
+// Eq. 42 ratio test and Eq. 7 read-out of sets 1..d of an occupied bin (the tilted form:
+// decode_tilt).  The sets' values are fetched eight at a time so that their loads
+// overlap.  Writes w_n to w_out (if not null) and returns whether every set passes and
+// (w . u) mod p is the bin itself.
 template <typename T, typename R>
 __device__ bool decode_bin(const SigCfg& c, const SigRun& r, const int32_t* __restrict__ blk, const c2<T>* Y,
                            const int64_t* u, int64_t h, R y0x, R y0y, R m0, int32_t* w_out) {
@@ -395,7 +455,10 @@ __device__ bool decode_bin(const SigCfg& c, const SigRun& r, const int32_t* __re
   const uint64_t up = (uint64_t)p;
   const int S = c.n_sets - 1;
   uint64_t bin = 0;
-  for (int n0 = 1; n0 <= S; n0 += kB) {
+  if (c.shift_tilt) {
+    if (!decode_tilt<T, R>(c, r, Y, u, h, y0x, y0y, m0, w_out, &bin)) return false;
+  }
+  for (int n0 = 1; n0 <= S && !c.shift_tilt; n0 += kB) {
     c2<T> yv[kB];
 #pragma unroll
     for (int i = 0; i < kB; ++i) yv[i] = n0 + i <= S ? Y[(int64_t)(n0 + i) * p + h] : mk2((T)0, (T)0);
@@ -421,6 +484,11 @@ __device__ bool decode_bin(const SigCfg& c, const SigRun& r, const int32_t* __re
 template <typename T, typename R>
 __device__ void read_coords(const SigCfg& c, const SigRun& r, const int32_t* __restrict__ blk, const c2<T>* Y,
                             const int64_t* u, int64_t h, R y0x, R y0y, int32_t* w_out) {
+  if (c.shift_tilt) {
+    const c2<T> y1 = Y[r.p + h], y2 = Y[2 * r.p + h];
+    read_tilt<R>(c, (R)y1.x, (R)y1.y, (R)y2.x, (R)y2.y, y0x, y0y, w_out);
+    return;
+  }
   uint64_t bin = 0;
   for (int n = 1; n < c.n_sets; ++n) {
     const c2<T> yn = Y[(int64_t)n * r.p + h];

@@ -112,6 +112,38 @@ def draw_signal(d: int, N: int, k: int, seed: int, r_dist: str = "uniform",
                   noise_sigma=noise_sigma, noise_seed=(seed * 7919 + 17) & _MASK64)
 
 
+def draw_rectangle_signal(N: int, k: int, n_rect: int, seed: int, r_lo: float = 1.0, r_hi: float = 10.0) -> Signal:
+    """A two-dimensional signal of k distinct modes in [0, N)^2 whose first 4 n_rect modes are
+    the corners of n_rect axis-aligned rectangles (distinct corners; two x and two y values
+    each), the rest drawn uniformly; coefficients r exp(i theta), r ~ U[r_lo, r_hi].  Every
+    corner shares its first coordinate with one corner and its second with another, the
+    configuration that defeats the projections onto the axes (the worst case of the tilted
+    lines' section of the paper)."""
+    if 4 * n_rect > k or k > N * N or N < 2:
+        raise ValueError("bad rectangle signal shape")
+    st = Stream(seed)
+    seen: set = set()
+    rows: list = []
+    while len(rows) < 4 * n_rect:
+        x0, x1, y0, y1 = (int(v) for v in st.integers(4, 0, N))
+        if x0 == x1 or y0 == y1:
+            continue
+        corners = [(x0, y0), (x0, y1), (x1, y0), (x1, y1)]
+        if any(c in seen for c in corners):
+            continue
+        seen.update(corners)
+        rows.extend(corners)
+    while len(rows) < k:
+        x, y = (int(v) for v in st.integers(2, 0, N))
+        if (x, y) not in seen:
+            seen.add((x, y))
+            rows.append((x, y))
+    freqs = np.array(rows, dtype=np.int32).reshape(k, 2)
+    r = r_lo + (r_hi - r_lo) * st.uniform(k)
+    coeffs = r * np.exp(2j * np.pi * st.uniform(k))
+    return Signal(d=2, N=N, freqs=freqs, coeffs=coeffs.astype(np.complex128))
+
+
 @dataclass
 class Workload:
     """A workload preset: signal shape, line-direction blocks and precision policy."""

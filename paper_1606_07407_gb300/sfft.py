@@ -42,15 +42,17 @@ class _Tilts(C.Structure):
 # where g (the registry's function) leaves f: its transform subtracted bin by bin, or its
 # samples subtracted at every sample point
 RESIDUAL = {"bins": 0, "samples": 1}
-# shifted sets: one per coordinate (e_n / N), or one per unwrapping block (Alg. 2 as printed)
-SHIFT = {"coord": 0, "block": 1}
+# shifted sets: one per coordinate (e_n / N), one per unwrapping block (Alg. 2 as printed), or
+# one per rotated axis of the tilted lines (Alg. 3, d = 2)
+SHIFT = {"coord": 0, "block": 1, "tilt": 2}
 
 
 class _Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("box_lo", C.c_int), ("tau", C.c_double), ("rho", C.c_double),
                 ("delta", C.c_double), ("noise_sigma", C.c_double), ("max_rounds", C.c_int),
                 ("profile", C.c_int), ("graph", C.c_int), ("coef_set0", C.c_int), ("residual", C.c_int),
-                ("shift", C.c_int), ("unfused", C.c_int)]
+                ("shift", C.c_int), ("unfused", C.c_int),
+                ("tilt_base", C.c_int), ("tilt_height", C.c_int), ("tilt_hypo", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -205,7 +207,7 @@ class Plan:
                  precision: str = "fp32", box_lo: int = 0, tau: float = 0.0, rho: float = 0.0,
                  delta: float = 0.0, noise_sigma: float = 0.0, max_rounds: int = 0, stream=None,
                  profile: bool = False, graph: bool = False, coef: str = "mean", residual: str = "bins",
-                 p_min: int = 0, shift: str = "coord", fuse: bool = True):
+                 p_min: int = 0, shift: str = "coord", fuse: bool = True, tilt=None):
         L = load()
         if residual not in RESIDUAL:
             raise ValueError(f"residual must be one of {sorted(RESIDUAL)}")
@@ -231,6 +233,8 @@ class Plan:
         op = _Opts(PREC[precision], int(box_lo), float(tau), float(rho), float(delta), float(noise_sigma),
                    int(max_rounds), 1 if profile else 0, 1 if graph else 0, 1 if coef == "set0" else 0,
                    RESIDUAL[residual], SHIFT[shift], 0 if fuse else 1)
+        if tilt is not None:   # (base, height, hypo) of the tilted form
+            op.tilt_base, op.tilt_height, op.tilt_hypo = (int(v) for v in tilt)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

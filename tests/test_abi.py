@@ -72,6 +72,25 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.sfft_plan_sets(None) == -1
 
 
+def test_tilt_arguments_rejected_without_gpu(lib):
+    # the tilted form (Alg. 3) takes d = 2 and a primitive Pythagorean triple; its read-out
+    # resolves Q = (base + height) N values, beyond 2^21 under a float policy only in FP64
+    from paper_1606_07407_gb300.sfft import _Opts
+    h = ctypes.c_void_p()
+
+    def create(d, N, triple, precision=0):
+        o = _Opts(precision, 0, 0.0, 0.0, 0.0, 0.0, 0, 0, 0, 0, 0, 2)
+        o.tilt_base, o.tilt_height, o.tilt_hypo = triple
+        return lib.sfft_plan_create(d, ctypes.c_int64(N), ctypes.c_int64(8), None, None, ctypes.byref(o), None,
+                                    ctypes.byref(h))
+
+    assert create(3, 32, (84, 13, 85)) == 1          # not two-dimensional
+    assert create(2, 32, (84, 13, 86)) == 1          # not Pythagorean
+    assert create(2, 32, (8, 6, 10)) == 1            # not primitive
+    assert create(2, 32, (0, 1, 1)) == 1             # a leg of zero
+    assert create(2, 1024, (2112, 65, 2113), precision=1) == 4   # Q = 2.2e6 > 2^21 in float (PRECISION)
+
+
 def test_library_is_built_for_sm103a():
     assert "arch=compute_103a,code=sm_103a" in " ".join(B.ARCH)
 

@@ -13,7 +13,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle.sfft_oracle as O
-from paper_1606_07407_gb300.inputs import WORKLOADS, Stream, draw_signal
+from paper_1606_07407_gb300.inputs import WORKLOADS, Stream, draw_rectangle_signal, draw_signal
 
 pytestmark = pytest.mark.gpu
 
@@ -588,6 +588,92 @@ def test_block_shift_recovery_matches_oracle(sfft, case):
                              residual="bins", shift="block")
     _assert_parity(sig, gf, ga, status, stats, ref, FP64_COEFF_TOL if prec == "fp64" else FP32_COEFF_TOL)
     assert stats["samples"] == sum(r["samples"] for r in ref.rounds)
+
+
+TILT_32 = (84, 13, 85)        # base, height, hypo: base > 2 N for N = 32 (Theorem 1)
+TILT_1024 = (2112, 65, 2113)  # base > 2 N for N = 1024
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_tilt_samples_match_oracle(sfft, prec):
+    N, K, p = 32, 300, 1031
+    sig = draw_signal(2, N, K, seed=81, r_lo=1.0, r_hi=10.0)
+    plan = sfft.Plan(2, N, K, precision=prec, shift="tilt", tilt=TILT_32)
+    assert plan.n_sets == 3
+    for u in O.tilt_axes(TILT_32):
+        u = [int(v) for v in u]
+        y = _np(plan.sample(p, u, torch.tensor(sig.freqs), torch.tensor(sig.coeffs)))
+        ref = O.sample_sets(sig.freqs, sig.coeffs, p, u, N, shift="tilt", tilt=TILT_32)
+        tol = (2.0 ** -20 if prec == "fp32" else 2.0 ** -48) * np.sum(np.abs(sig.coeffs))
+        assert y.shape == ref.shape and np.max(np.abs(y - ref)) < tol
+
+
+@pytest.mark.parametrize("case", ["N32_fp32", "N32_fp32_unfused", "N32_signed_fp32", "N1024_signed_fp64",
+                                  "N1024_fp64_samples"])
+def test_tilt_recovery_matches_oracle(sfft, case):
+    # Alg. 3: lines along the rotated axes in turn, sets shifted along them by 1 / ((base + height) N),
+    # read-out turned back; same sets, primes and coefficients as the oracle's tilted form
+    if case.startswith("N32"):
+        N, k, tilt, prec = 32, 40, TILT_32, "fp32"
+    else:
+        N, k, tilt, prec = 1024, 300, TILT_1024, "fp64"
+    box = -N // 2 if "signed" in case else 0
+    residual = "samples" if case.endswith("samples") else "bins"
+    sig = draw_signal(2, N, k, seed=82 + len(case), box_lo=box, r_lo=1.0, r_hi=10.0)
+    plan = sfft.Plan(2, N, k, precision=prec, shift="tilt", tilt=tilt, box_lo=box, residual=residual,
+                     fuse="unfused" not in case)
+    f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, N))
+    gf, ga = sfft.sort_result(_np(f), _np(a))
+    th = O.Thresholds() if prec == "fp64" else O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
+    ref = O.multi_phaseshift(sig.freqs, sig.coeffs, 2, N, k, th=th, box_lo=box, estimator="mean",
+                             residual=residual, shift="tilt", tilt=tilt)
+    _assert_parity(sig, gf, ga, status, stats, ref, FP64_COEFF_TOL if prec == "fp64" else FP32_COEFF_TOL)
+    assert stats["samples"] == sum(r["samples"] for r in ref.rounds)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_tilt_resolves_rectangle_corners_that_parallel_projections_cannot(sfft, prec):
+    # the worst case of Sec. 3.3: with lines along e_1 and e_2 every corner shares its bin with
+    # another corner in every round (NOT_CONVERGED, nothing found); the tilted lines of Alg. 3
+    # recover every corner (Theorem 1), as the oracle does
+    N, tilt = (32, TILT_32) if prec == "fp32" else (1024, TILT_1024)
+    sig = draw_rectangle_signal(N, 24, 6, seed=83)
+    freqs, coeffs, k = sig.freqs, sig.coeffs, 24
+    par = sfft.Plan(2, N, k, blocks=(1, 1), precision=prec, max_rounds=24)
+    f, a, status, stats = par.execute(sfft.Signal(freqs, coeffs, N), allow=(0, 2))
+    assert status == 2 and f.shape[0] < k
+    plan = sfft.Plan(2, N, k, precision=prec, shift="tilt", tilt=tilt)
+    f, a, status, stats = plan.execute(sfft.Signal(freqs, coeffs, N))
+    gf, ga = sfft.sort_result(_np(f), _np(a))
+    order = np.lexsort(freqs.T[::-1])
+    assert status == 0 and np.array_equal(gf, freqs[order].astype(np.int64))
+    th = O.Thresholds() if prec == "fp64" else O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
+    ref = O.multi_phaseshift(freqs, coeffs, 2, N, k, th=th, estimator="mean", residual="bins", shift="tilt",
+                             tilt=tilt)
+    assert np.array_equal(gf, ref.freqs)
+    tol = FP64_COEFF_TOL if prec == "fp64" else FP32_COEFF_TOL
+    assert np.max(np.abs(ga - ref.coeffs) / np.abs(ref.coeffs)) < tol
+
+
+def test_tilt_in_a_batch_with_other_forms(sfft):
+    # per-slot shift forms: tilted, per-coordinate and block slots share the batched kernels
+    N = 32
+    specs = [("tilt", 2, None), ("coord", 2, (1, 1)), ("tilt", 2, None), ("block", 4, (2, 2))]
+    sigs, plans, refs = [], [], []
+    th = O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
+    for i, (shift, d, blocks) in enumerate(specs):
+        sig = draw_signal(d, N, 24, seed=90 + i, r_lo=1.0, r_hi=10.0)
+        kw = {"tilt": TILT_32} if shift == "tilt" else {"blocks": blocks}
+        plans.append(sfft.Plan(d, N, 24, shift=shift, **kw))
+        sigs.append(sig)
+        refs.append(O.multi_phaseshift(sig.freqs, sig.coeffs, d, N, 24, blocks, th=th, estimator="mean",
+                                       residual="bins", shift=shift, tilt=TILT_32 if shift == "tilt" else None))
+    batch = sfft.Batch(plans)
+    res, sts, stats = batch.execute([sfft.Signal(s.freqs, s.coeffs, N) for s in sigs])
+    for (f, a), st, ref in zip(res, sts, refs):
+        gf, ga = sfft.sort_result(_np(f), _np(a))
+        assert st == 0 and np.array_equal(gf, ref.freqs)
+        assert np.max(np.abs(ga - ref.coeffs) / np.abs(ref.coeffs)) < FP32_COEFF_TOL
 
 
 @pytest.mark.parametrize("d", [100, 1000])
