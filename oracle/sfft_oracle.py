@@ -407,6 +407,64 @@ def classify(Y: np.ndarray, p: int, u, N: int, eta_bin: float, th: Thresholds,
 
 
 # --------------------------------------------------------------------------
+# Worst case of the parallel projections (Sec. 2.2, Sec. 4.2)
+# --------------------------------------------------------------------------
+
+
+def unwrapped_coordinates(freqs: np.ndarray, N: int, blocks, box_lo: int = 0) -> np.ndarray:
+    """[K, B] the block-unwrapped coordinates w~_q = sum_r (w_{b_q + r} - box_lo) N^r (Eq. 35),
+    the values the line of block q separates the modes by (Python ints: N^{d1} may pass 2^63)."""
+    freqs = np.asarray(freqs, dtype=np.int64)
+    out = np.empty((freqs.shape[0], len(blocks)), dtype=object)
+    for q, (b, size) in enumerate(zip(block_starts(blocks), blocks)):
+        for j in range(freqs.shape[0]):
+            out[j, q] = sum((int(freqs[j, b + r]) - box_lo) * N ** r for r in range(size))
+    return out
+
+
+def projection_core(freqs: np.ndarray, N: int, blocks, box_lo: int = 0) -> np.ndarray:
+    """Indices of the modes that the parallel projections never isolate (the worst case of
+    Sec. 2.2 and 3.3): two modes with the same unwrapped coordinate q share a bin on every line of
+    block q whatever the prime, while modes whose coordinates differ are apart for all but the
+    primes dividing the difference.  A mode whose coordinate q no other remaining mode shares is
+    found on block q's lines and leaves the residual; removing those repeatedly leaves the modes
+    that every projection keeps in a bin with another (the rectangle corners of two dimensions)."""
+    wt = unwrapped_coordinates(freqs, N, blocks, box_lo)
+    alive = set(range(wt.shape[0]))
+    changed = True
+    while changed:
+        changed = False
+        for q in range(wt.shape[1]):
+            count: dict = {}
+            for j in alive:
+                count[wt[j, q]] = count.get(wt[j, q], 0) + 1
+            lone = {j for j in alive if count[wt[j, q]] == 1}
+            if lone:
+                alive -= lone
+                changed = True
+    return np.array(sorted(alive), dtype=np.int64)
+
+
+def worst_case_bound(N: int, blocks, k: int) -> float:
+    """Sec. 4.2's upper bound on the probability that the parallel projections fail for k modes
+    drawn uniformly from N^d vectors with the blocks' unwrapping: 1 - prod_{j=1..k} P(A_j), where
+    A_j is the j-th vector avoiding the axis-parallel lines (in the unwrapped coordinates) through
+    the earlier ones, P(A_j) >= (N^d - (j - 1) sum_q N^{d_q}) / N^d.  Evaluated exactly, clipped
+    at 1."""
+    from fractions import Fraction
+    d = sum(blocks)
+    total = N ** d
+    line = sum(N ** b for b in blocks)
+    prod = Fraction(1)
+    for j in range(1, k + 1):
+        f = Fraction(total - (j - 1) * line, total)
+        if f <= 0:
+            return 1.0
+        prod *= f
+    return float(1 - prod)
+
+
+# --------------------------------------------------------------------------
 # Algorithm 2 driver
 # --------------------------------------------------------------------------
 

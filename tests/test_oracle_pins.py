@@ -251,6 +251,64 @@ def test_tilt_needs_a_primitive_pythagorean_triple_in_two_dimensions():
         O.multi_phaseshift(np.zeros((1, 3), dtype=np.int64), np.ones(1), 3, 16, 1, shift="tilt", tilt=TILT_16)
 
 
+# ---------------------------------------------------------------- worst case of the parallel projections (Sec. 4.2)
+
+def test_projection_core_in_two_dimensions_is_the_two_core_of_the_row_column_graph():
+    # in two dimensions a mode is an edge between its x value and its y value; a mode with a
+    # coordinate no other mode shares hangs off a degree-1 vertex, so peeling leaves exactly the
+    # edges of the graph's 2-core (networkx's k_core, a library routine)
+    nx = pytest.importorskip("networkx")
+    for seed in range(40):
+        sig = draw_signal(2, 12, 10 + seed % 20, seed=500 + seed)
+        G = nx.Graph()
+        G.add_edges_from((("x", int(w[0])), ("y", int(w[1]))) for w in sig.freqs)
+        core_nodes = set(nx.k_core(G, 2).nodes)
+        want = sorted(j for j, w in enumerate(sig.freqs)
+                      if ("x", int(w[0])) in core_nodes and ("y", int(w[1])) in core_nodes)
+        assert O.projection_core(sig.freqs, 12, (1, 1)).tolist() == want
+    corners = np.array([(1, 2), (1, 7), (5, 2), (5, 7), (9, 9)])
+    assert O.projection_core(corners, 12, (1, 1)).tolist() == [0, 1, 2, 3]
+
+
+def test_parallel_projections_fail_exactly_on_the_projection_core():
+    # Alg. 2 with parallel projections leaves out the core's modes and no other, and stops
+    # unconverged exactly when the core is not empty (d = 2, blocks of 1; d = 3 with a block of 2)
+    n_fail = 0
+    for d, N, k, blocks, seeds in ((2, 16, 12, (1, 1), range(40)), (3, 6, 24, (2, 1), range(20))):
+        for seed in seeds:
+            sig = draw_signal(d, N, k, seed=600 + seed)
+            core = set(O.projection_core(sig.freqs, N, blocks).tolist())
+            r = O.multi_phaseshift(sig.freqs, sig.coeffs, d, N, k, blocks, residual="bins", max_rounds=40)
+            found = {tuple(int(v) for v in w) for w in r.freqs}
+            missing = {j for j in range(k) if tuple(int(v) for v in sig.freqs[j]) not in found}
+            assert missing == core and r.converged == (not core) and r.n_found == k - len(core)
+            n_fail += bool(core)
+    assert n_fail >= 3   # the cases include failures
+
+
+def test_worst_case_bound_closed_form_and_monte_carlo():
+    # Sec. 4.2: with tau = N^d / sum_q N^{d_q} an integer the product is tau! / ((tau - k)! tau^k);
+    # the bound covers the probability of a pair on a common axis-parallel line (event A's
+    # complement) and, in two dimensions, the failure probability itself
+    for N, blocks, k in ((32, (1, 1), 8), (16, (1, 1), 5), (8, (2, 2), 10)):
+        d = sum(blocks)
+        tau = N ** d // sum(N ** b for b in blocks)
+        exact = 1 - math.factorial(tau) / (math.factorial(tau - k) * tau ** k)
+        assert abs(O.worst_case_bound(N, blocks, k) - exact) < 1e-12
+    assert O.worst_case_bound(8, (1, 1), 9) == 1.0   # j - 1 >= tau: a factor reaches 0
+    N, blocks, k, T = 16, (1, 1), 6, 3000
+    pair = fail = 0
+    for t in range(T):
+        sig = draw_signal(2, N, k, seed=10_000 + t)
+        w = sig.freqs
+        shared = any(w[i, 0] == w[j, 0] or w[i, 1] == w[j, 1] for i in range(k) for j in range(i))
+        pair += shared
+        fail += len(O.projection_core(w, N, blocks)) > 0
+    bound = O.worst_case_bound(N, blocks, k)
+    se = math.sqrt(bound * (1 - bound) / T)
+    assert fail <= pair and pair / T < bound + 4 * se
+
+
 def test_block_shift_recovery_equals_coordinate_shift_recovery():
     # the two shift forms read the same modes (the paper's shape included: d = 100, N = 20,
     # d1 = 5, |a| = 1, signed box) with FP64 coefficients at round-off
