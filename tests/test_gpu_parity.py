@@ -676,6 +676,30 @@ def test_tilt_in_a_batch_with_other_forms(sfft):
         assert np.max(np.abs(ga - ref.coeffs) / np.abs(ref.coeffs)) < FP32_COEFF_TOL
 
 
+@pytest.mark.parametrize("case", ["d2_blocks11", "d3_blocks21"])
+def test_parallel_projection_failures_match_the_projection_core(sfft, case):
+    # Sec. 2.2 / 4.2: the parallel projections never isolate the oracle's projection core; a batch
+    # of random small signals recovers every other mode (FP64: exact set per signal) and stops
+    # unconverged exactly where the core is not empty (float: the status per signal)
+    d, N, k, blocks, n = (2, 16, 12, (1, 1), 96) if case == "d2_blocks11" else (3, 6, 24, (2, 1), 48)
+    sigs = [draw_signal(d, N, k, seed=700 + t) for t in range(n)]
+    cores = [set(O.projection_core(s.freqs, N, blocks).tolist()) for s in sigs]
+    handles = [sfft.Signal(s.freqs, s.coeffs, N) for s in sigs]
+    for prec in ("fp64", "fp32"):
+        batch = sfft.Batch([sfft.Plan(d, N, k, blocks=blocks, precision=prec, max_rounds=40)] * n)
+        res, sts, stats = batch.execute(handles, allow=(0, 2))
+        for s, core, (f, a), st in zip(sigs, cores, res, sts):
+            assert st == (2 if core else 0)
+            if prec == "fp64":
+                gf, ga = sfft.sort_result(_np(f), _np(a))
+                keep = np.array([j for j in range(k) if j not in core], dtype=np.int64)
+                want = s.freqs[keep][np.lexsort(s.freqs[keep].T[::-1])].astype(np.int64)
+                wa = s.coeffs[keep][np.lexsort(s.freqs[keep].T[::-1])]
+                assert np.array_equal(gf, want)
+                assert np.max(np.abs(ga - wa) / np.abs(wa)) < 1e-9
+    assert sum(bool(c) for c in cores) >= 3   # the batch includes failures
+
+
 @pytest.mark.parametrize("d", [100, 1000])
 def test_paper_experiment_exact_with_round_off_error(sfft, d):
     # Sec. 5: d = 100 and 1000, d1 = 5 (d2 = 20 and 200 blocks), N = 20, |a| = 1, box
