@@ -31,6 +31,9 @@ namespace sfft {
 namespace {
 
 constexpr int kBindArrays = 8;   // per-signal arrays staged by bind()
+// powner[p] between k_plan launches: above every signal index (the byte of a memset fill)
+constexpr int kNoOwnerByte = 0x7F;
+constexpr int32_t kNoOwner = 0x7F7F7F7F;
 
 inline unsigned long long double_bits(double v) {
   unsigned long long u;
@@ -83,11 +86,10 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
                                                        int n_ptab, const int32_t* __restrict__ pfirst, int64_t pfirst_n,
                                                        const int64_t* __restrict__ dirs,
                                                        const int64_t* __restrict__ plist, int64_t* ubuf,
-                                                       HistRec* hist) {
+                                                       HistRec* hist, int32_t* __restrict__ powner) {
   __shared__ int s_S;
   __shared__ int64_t s_part;   // partial-sum elements at the chosen S
   __shared__ unsigned long long s_key;
-  __shared__ int s_own[kPlanThreads];
   const int n = a.n;
   int64_t tiles = 0, active = 0, fused = 0;
   // pass 1: stop rule and round parameters of every signal
@@ -169,13 +171,22 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     const int64_t tot_extra = block_sum(extra);
     if (s_part + tot_extra <= a.part_cap) q_tail = q;
   }
-  // pass 2: per-signal work counts and their exclusive scans.  Consecutive batched signals with
-  // the same prime share one copy of the tables (W, chirp) and of the filter spectrum: that of
-  // the first of them (the owner, from a running max over the chunk).
+  // Batched signals with the same prime share one copy of the tables (W, chirp) and of the filter
+  // spectrum: that of the first of them, the owner, found through powner[p] (kept at kNoOwner
+  // between launches; set here, read in pass 2, reset after it).  Round 1 with the tables made
+  // with the engine needs no owner.
+  auto uses_engine_tables = [&](const SigRun& r, int s) {
+    return !a.force && r.round == 1 && cfg[s].tab0_off >= 0 && r.p == cfg[s].p1;
+  };
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    const SigRun& r = run[s];
+    if (r.active && !r.fused && !uses_engine_tables(r, s)) atomicMin(&powner[r.p], s);
+  }
+  __syncthreads();
+  // pass 2: per-signal work counts and their exclusive scans
   int64_t carry[kNumScans];
   for (int q = 0; q < kNumScans; ++q) carry[q] = 0;
   int64_t part_carry = 0, tile_carry = 0;
-  int owner_carry = -1;
   for (int base = 0; base < n; base += blockDim.x) {
     const int s = base + threadIdx.x;
     int64_t v[kNumScans + 1];
@@ -194,38 +205,15 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
       in_tail = batched && tile_carry + tv[0] + tiles_s > tail_from;
       tile_carry += tt[0];
     }
-    // round 1 with the tables made with the engine
-    const bool pre = batched && !a.force && r.round == 1 && cfg[s].tab0_off >= 0 && r.p == cfg[s].p1;
-    {
-      bool start = true;
-      if (s < n && s > 0 && batched && !pre) {
-        const SigRun& q = run[s - 1];
-        const bool q_pre = !a.force && q.round == 1 && cfg[s - 1].tab0_off >= 0 && q.p == cfg[s - 1].p1;
-        start = !(q.active && !q.fused && q.p == r.p && !q_pre);
-      }
-      int own = start ? s : -1;
-      s_own[threadIdx.x] = own;
-      __syncthreads();
-      for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        const int o = threadIdx.x >= off ? s_own[threadIdx.x - off] : -1;
-        __syncthreads();
-        own = max(own, o);
-        s_own[threadIdx.x] = own;
-        __syncthreads();
-      }
-      if (own < 0) own = owner_carry;
-      const int last = s_own[blockDim.x - 1];
-      owner_carry = last >= 0 ? last : owner_carry;
-      __syncthreads();
-      if (pre) {
-        r.tab_at = cfg[s].tab0_off;
-        r.bhat_at = cfg[s].bhat0_off;
-        r.tab_owner = 0;
-      } else if (batched) {
-        r.tab_at = cfg[own].tab_off;
-        r.bhat_at = cfg[own].bhat_off;
-        r.tab_owner = own == s ? 1 : 0;
-      }
+    if (batched && uses_engine_tables(r, s)) {
+      r.tab_at = cfg[s].tab0_off;
+      r.bhat_at = cfg[s].bhat0_off;
+      r.tab_owner = 0;
+    } else if (batched) {
+      const int own = powner[r.p];
+      r.tab_at = cfg[own].tab_off;
+      r.bhat_at = cfg[own].bhat_off;
+      r.tab_owner = own == s ? 1 : 0;
     }
     if (s < n) {
       if (batched) {
@@ -263,6 +251,11 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     }
     for (int q = 0; q < kNumScans; ++q) carry[q] += tot[q];
     part_carry += tot[kNumScans];
+  }
+  __syncthreads();   // every owner has been read
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    const SigRun& r = run[s];
+    if (r.active && !r.fused) powner[r.p] = kNoOwner;
   }
   if (threadIdx.x == 0) {
     for (int q = 0; q < kNumScans; ++q) sc.v[q][n] = carry[q];
@@ -915,6 +908,9 @@ class Engine final : public EngineBase {
     if (graph_exec_) cudaGraphExecDestroy(graph_exec_);
     if (graph_) cudaGraphDestroy(graph_);
     for (cudaEvent_t e : events_) cudaEventDestroy(e);
+    if (fork_ev_) cudaEventDestroy(fork_ev_);
+    if (join_ev_) cudaEventDestroy(join_ev_);
+    if (side_) cudaStreamDestroy(side_);
     for (void* q : allocs_) cudaFree(q);
     if (host_stage_) cudaFreeHost(host_stage_);
   }
@@ -1089,6 +1085,8 @@ class Engine final : public EngineBase {
     for (int q = 0; q < kNumScans; ++q) ECHK(alloc(&scans_.v[q], (size_t)(n_ + 1) * sizeof(int64_t)));
     ECHK(alloc(&ptab_, ptab.size() * sizeof(int32_t)));
     ECHK(alloc(&pfirst_, pfirst.size() * sizeof(int32_t)));
+    ECHK(alloc(&powner_, (size_t)(pmax_all + 1) * sizeof(int32_t)));
+    ECHK(cudaMemsetAsync(powner_, kNoOwnerByte, (size_t)(pmax_all + 1) * sizeof(int32_t), st_));
     ECHK(alloc(&dirs_, std::max<size_t>(dirs.size(), 1) * sizeof(int64_t)));
     ECHK(alloc(&shblk_, std::max<size_t>(shblk.size(), 1) * sizeof(int32_t)));
     ECHK(alloc(&plist_, std::max<size_t>(plist.size(), 1) * sizeof(int64_t)));
@@ -1186,6 +1184,9 @@ class Engine final : public EngineBase {
       events_.resize((size_t)(SFFT_STATS_MAX_ROUNDS + 4) * 8);
       for (auto& e : events_) ECHK(cudaEventCreate(&e));
     }
+    ECHK(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking));
+    ECHK(cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming));
+    ECHK(cudaEventCreateWithFlags(&join_ev_, cudaEventDisableTiming));
     ECHK(cudaStreamSynchronize(st_));
     return cudaSuccess;
   }
@@ -1202,22 +1203,34 @@ class Engine final : public EngineBase {
 
   // Bluestein rows of one block each, in two classes: short rows (L <= 2^kSmallFftLog) in
   // small-memory blocks, so many fit on an SM, and the longer rows
-  cudaError_t launch_dft_rows() {
+  // The Bluestein filter spectra of the round's owners (short and long class) on stream s.
+  cudaError_t launch_filters(cudaStream_t s) {
     const int ls = std::min(small_logL_max_, kSmallFftLog);
     const int thr_s = std::max(32, (1 << ls) / fft_per_thread<C2>());
     const size_t smem_s = (size_t)((1 << ls) + (1 << ls) / 32) * sizeof(C2);
+    const TwSrc<C2> tws = tw_src();
+    k_filter<T><<<n_, thr_s, smem_s, s>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, tws, (C2*)bhat_, 1);
+    ECHK(cudaGetLastError());
+    if (small_logL_max_ > kSmallFftLog) {
+      k_filter<T><<<n_, small_threads_, smem_small_, s>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, tws, (C2*)bhat_, 0);
+      ECHK(cudaGetLastError());
+    }
+    return cudaSuccess;
+  }
+
+  // with_filters: the filter spectra first, on the same stream (else they were made beside the
+  // sampling, see enqueue_batched)
+  cudaError_t launch_dft_rows(bool with_filters = true) {
+    const int ls = std::min(small_logL_max_, kSmallFftLog);
+    const int thr_s = std::max(32, (1 << ls) / fft_per_thread<C2>());
     // short rows: room for the prefetch row too (six blocks per SM by shared memory, eight by registers)
     const size_t smem_sp = (size_t)((((1 << ls) + (1 << ls) / 32 + 1) & ~1) + (1 << ls)) * sizeof(C2);
     const TwSrc<C2> tws = tw_src();
-    k_filter<T><<<n_, thr_s, smem_s, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, tws, (C2*)bhat_, 1);
-    ECHK(cudaGetLastError());
+    if (with_filters) ECHK(launch_filters(st_));
     k_dft<T><<<(unsigned)rows_max_, thr_s, smem_sp, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_,
                                                            (C2*)bhat_, tws, (C2*)Y_, 1, (int)smem_sp);
     ECHK(cudaGetLastError());
     if (small_logL_max_ > kSmallFftLog) {
-      k_filter<T><<<n_, small_threads_, smem_small_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)tab_, tws, (C2*)bhat_,
-                                                           0);
-      ECHK(cudaGetLastError());
       k_dft<T><<<(unsigned)rows_max_, small_threads_, smem_dft_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
                                                                          (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 0,
                                                                          (int)smem_dft_);
@@ -1299,7 +1312,7 @@ class Engine final : public EngineBase {
   // the round's plan (one launch)
   cudaError_t launch_plan(const PlanArgs& pa, int64_t* launches) {
     k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_,
-                                            plist_, u_, hist_);
+                                            plist_, u_, hist_, powner_);
     launches[0] += 1;
     return cudaGetLastError();
   }
@@ -1312,9 +1325,17 @@ class Engine final : public EngineBase {
     launches[0] += 1;
     ECHK(mark(1));
     ECHK(mark(2));
+    // the filter spectra depend only on the round's primes: they are made on a side stream beside
+    // the sampling, whose persistent blocks take their tiles from a queue and so absorb the SMs
+    // the filters hold for a while
+    ECHK(cudaEventRecord(fork_ev_, st_));
+    ECHK(cudaStreamWaitEvent(side_, fork_ev_, 0));
+    ECHK(launch_filters(side_));
+    ECHK(cudaEventRecord(join_ev_, side_));
     ECHK(launch_samples(launches));
+    ECHK(cudaStreamWaitEvent(st_, join_ev_, 0));
     ECHK(mark(3));
-    ECHK(launch_dft_rows());
+    ECHK(launch_dft_rows(false));
     launches[3] += small_logL_max_ > kSmallFftLog ? 4 : 2;
     if (any_big_) {
       k_bigA<T><<<4 * n_sm_, 256, smem_bigA_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_, (C2*)twG_,
@@ -1624,7 +1645,7 @@ class Engine final : public EngineBase {
     pa.force_p = p;
     pa.force_K = K;
     k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_, plist_, u_,
-                                            nullptr);
+                                            nullptr, powner_);
     ECHK(cudaGetLastError());
     return launch_tables();
   }
@@ -1709,6 +1730,8 @@ class Engine final : public EngineBase {
   std::vector<SigCfg> cfg_host_;
   std::vector<void*> allocs_;
   std::vector<cudaEvent_t> events_;
+  cudaStream_t side_ = nullptr;                            // filter spectra beside the sampling
+  cudaEvent_t fork_ev_ = nullptr, join_ev_ = nullptr;
   void* host_stage_ = nullptr;
   SigCfg* cfg_ = nullptr;
   SigRun* run_ = nullptr;
@@ -1716,6 +1739,7 @@ class Engine final : public EngineBase {
   Scans scans_;
   int32_t* ptab_ = nullptr;
   int32_t* pfirst_ = nullptr;
+  int32_t* powner_ = nullptr;   // [p_max + 1] first batched signal of each prime in k_plan (kNoOwner between)
   int64_t pfirst_n_ = 0;
   int64_t* dirs_ = nullptr;
   int32_t* shblk_ = nullptr;   // (start, size) per shift block of every slot (block form)
