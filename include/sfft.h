@@ -256,12 +256,14 @@ sfft_status sfft_sample(sfft_plan plan, int64_t p, const int64_t* u, int64_t K,
  * [n_rows x p] in the plan's complex type; n_rows <= d + 1. */
 sfft_status sfft_dft(sfft_plan plan, int64_t p, int n_rows, const void* y_dev, void* Y_out_dev);
 
-/* Kernel (c), bin classification and read-out (Eq. 41-42): for the (d+1) x p
- * transforms Y_dev (plan's complex type) of the line with direction u (host
- * int64 [d]) returns every bin h with |Y_0[h]| > eta_bin that passes the ratio
- * test for all n, whose read-out rounds to integers within delta and lands in
- * its own bin.  Outputs (device): h_out int32 [capacity], freqs_out int32
- * [capacity x d], coeffs_out complex128 [capacity] (a = Y_0[h] / p);
+/* Kernel (c), bin classification and read-out (Eq. 41-42): for the
+ * sfft_plan_sets(plan) x p transforms Y_dev (plan's complex type; d + 1 rows in
+ * the coordinate and tilted forms) of the line with direction u (host int64 [d])
+ * returns every bin h with |Y_0[h]| > eta_bin that passes the ratio test for all
+ * n, whose read-out (the plan's shift form) rounds to integers within delta and
+ * lands in its own bin.  Outputs (device): h_out int32 [capacity], freqs_out
+ * int32 [capacity x d], coeffs_out complex128 [capacity] (the plan's coefficient
+ * estimator: Y_0[h] / p with opts.coef_set0, else the mean over the sets);
  * *n_out = count (order unspecified).  CAPACITY if more bins pass than fit. */
 sfft_status sfft_classify(sfft_plan plan, int64_t p, const int64_t* u, const void* Y_dev,
                           double eta_bin, int64_t capacity, int32_t* h_out_dev,

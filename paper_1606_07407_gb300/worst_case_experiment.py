@@ -64,7 +64,8 @@ def wilson(x: int, n: int, z: float = 1.96):
     den = 1 + z * z / n
     c = (ph + z * z / (2 * n)) / den
     h = z * math.sqrt(ph * (1 - ph) / n + z * z / (4 * n * n)) / den
-    return (max(0.0, c - h), min(1.0, c + h))
+    # the interval reaches 0 at x = 0 and 1 at x = n exactly (set them: rounding misses by an ulp)
+    return (0.0 if x == 0 else max(0.0, c - h), 1.0 if x == n else min(1.0, c + h))
 
 
 def run(trials=4096, seed=1606074072, max_rounds=40):
