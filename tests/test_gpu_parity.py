@@ -676,6 +676,29 @@ def test_tilt_in_a_batch_with_other_forms(sfft):
         assert np.max(np.abs(ga - ref.coeffs) / np.abs(ref.coeffs)) < FP32_COEFF_TOL
 
 
+def test_batch_beyond_one_plan_block_shares_tables_across_chunks(sfft):
+    # more signals than the plan kernel's threads (its scans run in chunks of 256): sparsities
+    # repeat across the chunks, so signals of one prime in different chunks share the tables
+    # and filter of the first of them; every signal recovers its planted set, and a sample of
+    # them matches the oracle coefficient by coefficient
+    n, N = 320, 64
+    ks = [8 + (t * 7) % 33 for t in range(n)]
+    sigs = [draw_signal(2, N, k, seed=1200 + t, r_lo=1.0, r_hi=10.0) for t, k in enumerate(ks)]
+    plans = {k: sfft.Plan(2, N, k, blocks=(2,)) for k in set(ks)}
+    batch = sfft.Batch([plans[k] for k in ks])
+    res, sts, stats = batch.execute([sfft.Signal(s.freqs, s.coeffs, N) for s in sigs])
+    th = O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
+    for t, (s, (f, a), st) in enumerate(zip(sigs, res, sts)):
+        gf, ga = sfft.sort_result(_np(f), _np(a))
+        order = np.lexsort(s.freqs.T[::-1])
+        assert st == 0 and np.array_equal(gf, s.freqs[order].astype(np.int64))
+        assert np.max(np.abs(ga - s.coeffs[order]) / np.abs(s.coeffs[order])) < 1e-4
+        if t % 20 == 0:
+            ref = O.multi_phaseshift(s.freqs, s.coeffs, 2, N, ks[t], (2,), th=th, estimator="mean", residual="bins")
+            assert np.array_equal(gf, ref.freqs)
+            assert np.max(np.abs(ga - ref.coeffs) / np.abs(ref.coeffs)) < FP32_COEFF_TOL
+
+
 @pytest.mark.parametrize("case", ["d2_blocks11", "d3_blocks21"])
 def test_parallel_projection_failures_match_the_projection_core(sfft, case):
     # Sec. 2.2 / 4.2: the parallel projections never isolate the oracle's projection core; a batch
