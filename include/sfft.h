@@ -79,7 +79,8 @@ typedef struct {
  * consecutive coordinates, whose direction has N^r on the block's r-th
  * coordinate (Eq. 35-38).  Round i uses direction / block (i mod count), the
  * paper's m = (i mod d2) + 1 in 1-based numbering.  Both empty means one block
- * per the default rule: the smallest b with N^b >= 4 c k, d / b blocks. */
+ * per the default rule: the smallest b with N^b >= 4 c k, d / b blocks; with
+ * opts.shift = TILT, both empty means Alg. 3's two rotated axes. */
 typedef struct {
   int n_dirs;
   const int64_t* dirs;      /* host */
@@ -166,8 +167,11 @@ typedef struct {
  * during execute.  stream: a cudaStream_t, or NULL for the default stream.
  * pschedule, tilts, opts may be NULL (defaults).  Errors: INVALID_ARG for
  * d < 1, N < 2, k < 0, a direction that overflows int64, a largest prime at or
- * above 2^22 under a float policy, or bad options; PRECISION when N exceeds
- * 2^23 under a float policy; CUDA when an allocation fails. */
+ * above 2^22 under a float policy, or bad options (including a tilted form that
+ * is not two-dimensional or whose triple is not primitive Pythagorean);
+ * PRECISION when N exceeds 2^23 under a float policy, or when the block or
+ * tilted read-out resolves more values than the policy's phase precision;
+ * CUDA when an allocation fails. */
 sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* pschedule,
                              const sfft_tilts* tilts, const sfft_opts* opts, void* stream,
                              sfft_plan* plan_out);
