@@ -758,6 +758,42 @@ def test_planted_mistakes_are_caught(monkeypatch):
         test_tilt_readout_decodes_every_pair_of_a_box_and_rejects_the_rest()
     monkeypatch.setattr(O, "tilt_window", real_window)
 
+    real_core = O.projection_core
+
+    def core_one_pass(freqs, N, blocks, box_lo=0):   # each block peeled once, no repeat
+        wt = O.unwrapped_coordinates(freqs, N, blocks, box_lo)
+        alive = set(range(wt.shape[0]))
+        for q in range(wt.shape[1]):
+            count = {}
+            for j in alive:
+                count[wt[j, q]] = count.get(wt[j, q], 0) + 1
+            alive -= {j for j in alive if count[wt[j, q]] == 1}
+        return np.array(sorted(alive), dtype=np.int64)
+
+    def core_counts_once(freqs, N, blocks, box_lo=0):   # shared values counted over all modes only
+        wt = O.unwrapped_coordinates(freqs, N, blocks, box_lo)
+        K, B = wt.shape
+        keep = [j for j in range(K) if all(sum(wt[i, q] == wt[j, q] for i in range(K)) > 1 for q in range(B))]
+        return np.array(keep, dtype=np.int64)
+
+    for bad in (core_one_pass, core_counts_once):
+        monkeypatch.setattr(O, "projection_core", bad)
+        with pytest.raises(AssertionError):
+            test_projection_core_in_two_dimensions_is_the_two_core_of_the_row_column_graph()
+        with pytest.raises(AssertionError):
+            test_parallel_projections_fail_exactly_on_the_projection_core()
+        monkeypatch.setattr(O, "projection_core", real_core)
+
+    real_decode_tilt = O._decode_tilt
+
+    def tilt_turned_the_wrong_way(ratio, N, tilt, box_lo, delta):   # [cos -sin; sin cos] back
+        return real_decode_tilt(ratio, N, (tilt[0], -tilt[1], tilt[2]), box_lo, delta)
+
+    monkeypatch.setattr(O, "_decode_tilt", tilt_turned_the_wrong_way)
+    with pytest.raises(AssertionError):
+        test_tilt_readout_decodes_every_pair_of_a_box_and_rejects_the_rest()
+    monkeypatch.setattr(O, "_decode_tilt", real_decode_tilt)
+
     real_philox = O.philox4x32_10
 
     def philox_2_rounds(c0, c1, c2, c3, k0, k1):       # two rounds, no key schedule: weak mixing
