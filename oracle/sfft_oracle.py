@@ -33,6 +33,12 @@ adds its coefficient to the registry entry; the empty-bin level is rho p A_ref
 with A_ref the largest first-round bin divided by p, plus 6 sigma sqrt(p) when
 the samples carry noise.
 
+Also here: the block shifts of Alg. 2 as printed (shift "block"), the tilted
+lines of Alg. 3 in two dimensions (shift "tilt": rotated axes, rotated shifts,
+read-out turned back, Sec. 3.3 and Theorem 1), Alg. 1 in one dimension, and the
+worst case of the parallel projections (projection_core: the modes no axis line
+ever isolates; worst_case_bound: Sec. 4.2's bound on its probability).
+
 Arithmetic is float64 / complex128 throughout; integer phase indices are
 reduced exactly in int64 before any floating point is applied.
 """
