@@ -426,7 +426,7 @@ struct ClassifyOut {   // step calls: accepted bins are appended here instead of
 // read_tilt; *bin gets sum_l (w_l - box_lo) u_l mod p.
 template <typename T, typename R>
 __device__ __forceinline__ bool decode_tilt(const SigCfg& c, const SigRun& r, const c2<T>* Y, const int64_t* u,
-                                         int64_t h, R y0x, R y0y, R m0, int32_t* w_out, uint64_t* bin) {
+                                            int64_t h, R y0x, R y0y, R m0, int32_t* w_out, uint64_t* bin) {
   const uint64_t up = (uint64_t)r.p;
   const c2<T> y1 = Y[r.p + h], y2 = Y[2 * r.p + h];
   const R y1x = (R)y1.x, y1y = (R)y1.y, y2x = (R)y2.x, y2y = (R)y2.y;
