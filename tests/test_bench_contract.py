@@ -36,3 +36,14 @@ def test_reference_arm_prints_one_contract_line():
 def test_reference_arm_other_ranks_exit_quietly():
     rc, lines = _run({"RANK": "1", "WORLD_SIZE": "2"}, "--steps", "1", "--warmup", "3", "--gpus", "2")
     assert rc == 0 and lines == []
+
+
+def test_cpu_baseline_reports_one_core_and_all_cores():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-baseline-only", "--workload",
+                        "d2_N1024_k16", "--cpu-seconds", "0.5", "--cpu-all-cores"], capture_output=True, text=True,
+                       cwd=ROOT, timeout=300)
+    assert r.returncode == 0
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["kind"] == "oracle" and d["cores"] == 1 and d["value"] > 0
+    ac = d["all_cores"]
+    assert ac["cores"] >= 1 and ac["value"] > 0 and ac["unit"] == d["unit"]
