@@ -72,6 +72,31 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.sfft_plan_sets(None) == -1
 
 
+def test_more_plan_arguments_rejected_without_gpu(lib):
+    # every check of sfft_plan_create runs before the engine touches the device
+    from paper_1606_07407_gb300.sfft import _Opts, _PSchedule, _Tilts
+    h = ctypes.c_void_p()
+
+    def create(d=2, N=64, k=8, ps=None, tl=None, **opt):
+        o = _Opts(0, 0, 0.0, 0.0, 0.0, 0.0, 0, 0, 0, 0, 0, 0)
+        for key, v in opt.items():
+            setattr(o, key, v)
+        return lib.sfft_plan_create(d, ctypes.c_int64(N), ctypes.c_int64(k), ctypes.byref(ps) if ps else None,
+                                    ctypes.byref(tl) if tl else None, ctypes.byref(o), None, ctypes.byref(h))
+
+    assert create(shift=3) == 1                       # unknown shift form
+    assert create(precision=9) == 1                   # unknown precision policy
+    assert create(box_lo=1) == 1                      # the box starts at most at 0
+    assert create(delta=0.5) == 1                     # read-out tolerance below half an integer
+    assert create(max_rounds=-1) == 1
+    assert create(N=1 << 24) == 4                     # a float policy reads N values from a phase
+    primes = (ctypes.c_int64 * 2)(101, 91)            # 91 = 7 * 13
+    assert create(ps=_PSchedule(0, 2, primes, 0)) == 1
+    assert create(ps=_PSchedule(0, 0, None, 1 << 27)) == 1   # prime floor beyond the tables
+    blocks = (ctypes.c_int * 2)(2, 2)                 # block sizes must add up to d
+    assert create(tl=_Tilts(0, None, 2, blocks)) == 1
+
+
 def test_tilt_arguments_rejected_without_gpu(lib):
     # the tilted form (Alg. 3) takes d = 2 and a primitive Pythagorean triple; its read-out
     # resolves Q = (base + height) N values, beyond 2^21 under a float policy only in FP64
