@@ -40,3 +40,15 @@ def test_rectangle_signal_puts_every_corner_in_the_projection_core():
         assert len({tuple(w) for w in sig.freqs.tolist()}) == 60
         core = set(O.projection_core(sig.freqs, 64, (1, 1)).tolist())
         assert set(range(40)) <= core
+
+
+def test_tilt_experiment_triples_meet_theorem_1():
+    # each case's triple is primitive Pythagorean with base > 2N, so the rotated coordinates of
+    # the box are distinct (Theorem 1), and its read-out fits the case's precision policy
+    from paper_1606_07407_gb300.tilt_experiment import CASES as TILT_CASES
+    for N, prec, tilt, k, n_rect, div in TILT_CASES:
+        O.check_tilt(tilt)
+        base, height, _ = tilt
+        assert base > 2 * N and 4 * n_rect <= k
+        Q, _ = O.tilt_window(N, 0, tilt)
+        assert prec == "fp64" or Q <= 2 ** 21
