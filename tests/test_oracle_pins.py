@@ -443,6 +443,60 @@ def test_prime_floor_takes_the_ith_prime_above_the_floor():
         assert r["p"] == int(pr[np.searchsorted(pr, lo) + r["round"] - 1])
 
 
+STOP_RULE_W = np.array([[3, 5], [7, 5], [20, 30]], dtype=np.int64)
+STOP_RULE_A = np.array([1.5 - 0.5j, -1.5 + 0.5j, 2.0 + 0.0j])
+
+
+def _check_stop_rule(recover):
+    # Modes 0 and 1 have opposite coefficients and differ only in coordinate 1, which lines along
+    # e_2 do not see: on such a line they share a bin and cancel in set 0, while set 1 (shifted
+    # along e_1) holds p a (e^{2 pi i 3/N} - e^{2 pi i 7/N}).  With every line along e_2 the pair
+    # can never be separated: after mode 2 is found, set 0 is empty but the residual is not, so
+    # the run must end unconverged instead of returning {mode 2} as the whole set.  Lines along
+    # e_2 and e_1 in turn recover all three.
+    N = 64
+    conv, fw, fa = recover(STOP_RULE_W, STOP_RULE_A, N, dirs=[(0, 1)], max_rounds=8)
+    assert not conv
+    assert np.array_equal(fw, STOP_RULE_W[2:])
+    conv, fw, fa = recover(STOP_RULE_W, STOP_RULE_A, N, dirs=None, max_rounds=0)
+    order = np.lexsort(STOP_RULE_W.T[::-1])
+    assert conv and np.array_equal(fw, STOP_RULE_W[order])
+    return fa, STOP_RULE_A[order]
+
+
+def test_stop_rule_reads_every_set():
+    def recover(w, a, N, dirs, max_rounds):
+        res = O.multi_phaseshift(w, a, 2, N, len(w), (1, 1), dirs=dirs, max_rounds=max_rounds or None,
+                                 residual="bins")
+        return res.converged, res.freqs, res.coeffs
+    fa, ref = _check_stop_rule(recover)
+    assert np.max(np.abs(fa - ref)) < 1e-12
+
+
+def test_prime_rule_with_a_fractional_factor():
+    # c = 5/2 and c = 3/8: round i takes the i-th prime at or above ceil(c k*), found by a sieve
+    pr = _sieve(6000)
+    for c, k, seed in ((2.5, 300, 7), (0.375, 40, 8)):
+        sig = draw_signal(2, 1 << 12, k, seed=seed, r_lo=1.0, r_hi=10.0)
+        res = O.multi_phaseshift(sig.freqs, sig.coeffs, 2, sig.N, k, (1, 1), c=c,
+                                 th=O.Thresholds(tau=1e-7, rho=2.0 ** -40, delta=0.1), residual="bins")
+        assert res.converged and np.array_equal(res.freqs, sig.freqs[np.lexsort(sig.freqs.T[::-1])])
+        for r in res.rounds:
+            lo = -(-int(c * 8) * r["k_star"] // 8)                 # ceil(c k*) in integers
+            assert r["p"] == int(pr[np.searchsorted(pr, max(lo, 2)) + r["round"] - 1])
+
+
+def test_philox_matches_the_published_known_answer_vectors():
+    # the generator's authors' own test vectors: a swapped multiplier or key increment, a
+    # permuted output word or a dropped round changes every one of them
+    rows = _rows("philox4x32_10_kat.txt")
+    assert len(rows) == 3
+    for row in rows:
+        v = [int(x, 16) for x in row]
+        out = O.philox4x32_10(*[np.array([c], dtype=np.uint64) for c in v[:4]], v[4], v[5])
+        assert [int(np.asarray(w).ravel()[0]) for w in out] == v[6:10]
+
+
 def test_philox_is_a_bijection_with_full_avalanche():
     # for one key the 128-bit output of distinct counters never repeats; flipping one counter
     # bit flips about half of the 128 output bits (a dropped round, word or xor breaks one of these)
@@ -809,6 +863,33 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(O, "philox4x32_10", philox_2_rounds)
     with pytest.raises(AssertionError):
         test_philox_is_a_bijection_with_full_avalanche()
+    monkeypatch.setattr(O, "philox4x32_10", real_philox)
+
+    def philox_variant(m0, m1, w0, w1, perm):
+        # Philox4x32-10 with its constants or output order changed: each of these still mixes
+        # fully, so only the published vectors tell it from the generator
+        def gen(c0, c1, c2, c3, k0, k1):
+            m32 = np.uint64(0xFFFFFFFF)
+            c = [np.asarray(v, dtype=np.uint64) & m32 for v in (c0, c1, c2, c3)]
+            ka, kb = np.uint64(int(k0) & 0xFFFFFFFF), np.uint64(int(k1) & 0xFFFFFFFF)
+            for rnd in range(10):
+                if rnd:
+                    ka, kb = (ka + np.uint64(w0)) & m32, (kb + np.uint64(w1)) & m32
+                p0, p1 = c[0] * np.uint64(m0), c[2] * np.uint64(m1)
+                c = [(p1 >> np.uint64(32)) ^ c[1] ^ ka, p1 & m32, (p0 >> np.uint64(32)) ^ c[3] ^ kb, p0 & m32]
+            return tuple(c[i] for i in perm)
+        return gen
+
+    M0, M1, W0, W1 = 0xD2511F53, 0xCD9E8D57, 0x9E3779B9, 0xBB67AE85
+    monkeypatch.setattr(O, "philox4x32_10", philox_variant(M0, M1, W0, W1, (0, 1, 2, 3)))
+    test_philox_matches_the_published_known_answer_vectors()       # the restatement itself passes
+    for bad in (philox_variant(M1, M0, W0, W1, (0, 1, 2, 3)),      # multipliers swapped
+                philox_variant(M0, M1, W1, W0, (0, 1, 2, 3)),      # key increments swapped
+                philox_variant(M0, M1, W0, W1, (1, 0, 3, 2))):     # output words permuted
+        monkeypatch.setattr(O, "philox4x32_10", bad)
+        test_philox_is_a_bijection_with_full_avalanche()           # the statistical pins miss it
+        with pytest.raises(AssertionError):
+            test_philox_matches_the_published_known_answer_vectors()
     monkeypatch.setattr(O, "philox4x32_10", real_philox)
 
     real_noise = O.black_box_noise
