@@ -21,7 +21,7 @@ What it computes (Algorithm 2, MultiPhaseshift, in its general form):
          w_n = N Arg(Y_n[h] / Y_0[h]) / (2 pi), rounded            (Eq. 7, Eq. 41 with eps = 1/N)
          a   = Y_0[h] / p                                         (Eq. 7, Eq. 41)
     R <- R merged with the accepted (w, a); prune small |a|       (Alg. 2 registry update)
-  until a round finds no bin above the empty-bin level (the residual is empty).
+  until a round finds no bin of any set above the empty-bin level (the residual is empty).
 
 Readings of the paper taken here (each is listed with its reason in the design
 notes): per-coordinate shifts e_n / N instead of eps times a block vector; the
@@ -45,6 +45,7 @@ reduced exactly in int64 before any floating point is applied.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
+from fractions import Fraction
 import math
 
 import numpy as np
@@ -491,7 +492,7 @@ class Result:
         return int(sum(r["samples"] for r in self.rounds))
 
 
-def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int = 5,
+def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: float = 5,
                      th: Thresholds | None = None, max_rounds: int | None = None,
                      box_lo: int = 0, primes=None, dirs=None, noise=None,
                      estimator: str = "set0", residual: str = "samples", p_min: int = 0,
@@ -528,8 +529,10 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
     converged = False
     for i in range(1, max_rounds + 1):
         k_star = max(k - len(R), 1)
+        # "p <- i-th prime >= c k*": the smallest integer at or above c k* is ceil(c k*), taken
+        # exactly (c may be a fraction such as 5/2; Alg. 2 leaves c to the caller)
         p = (int(primes[(i - 1) % len(primes)]) if primes is not None
-             else ith_prime_at_least(i, max(c * k_star, p_min)))
+             else ith_prime_at_least(i, max(math.ceil(Fraction(c) * k_star), p_min)))
         u = line_direction(d, N, blocks, i, dirs)
         # f - g: black-box modes with +a, registry modes with -a (Alg. 2: g is built from R)
         if R and residual == "samples":
@@ -552,7 +555,9 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: int 
         eta_bin = max(th.rho * p * a_ref, 6.0 * th.sigma * math.sqrt(p))
         stat = {"round": i, "p": p, "k_star": k_star, "terms": int(all_w.shape[0]),
                 "samples": int(Y.shape[0]) * p, "eta_bin": eta_bin}
-        if not np.any(np.abs(Y[0]) > eta_bin):
+        # the residual is empty when no bin of any set is above the level: a registry pair of
+        # opposite coefficients that the line does not separate cancels in set 0 alone
+        if not np.any(np.abs(Y) > eta_bin):
             stat.update(accepted=0, registry=len(R))
             rounds.append(stat)
             converged = True
