@@ -1,11 +1,16 @@
 #!/usr/bin/env python
 """Benchmark of the sparse-FFT hot path: modes recovered per second at exact frequency recovery.
 
-Workload (default): d = 5, N = 1024, k = 1000 planted modes per signal, r ~ U[1, 10],
-noiseless, line directions from partial unwrapping with blocks (3, 2), FP32 sampling and
-DFT with an FP64 phase-ratio step.  One step recovers a batch of independent signals
-(--batch, all resident in HBM before timing) by full runs of Algorithm 2; a step counts
-only if every recovered frequency set equals the planted one.
+Default workload (mix4096): 4096 independent signals with k ~ U{8..512}, d ~ U{2..8},
+N = 2^U{10..20}, r ~ U[1, 10], noiseless, each with its own plan (partial-unwrap blocks by the
+default rule, prime schedule from the tuned table), float sampling and DFT with the phase ratio
+in double above N = 2^14.  One step recovers all of them in one batched execute whose rounds run
+as a CUDA graph with a device-ended while loop (the batched form); the plain form, one execute
+per signal, is timed beside it on the same signals.  A step counts only if every recovered
+frequency set equals the planted one.
+
+Other workloads: the single-shape presets of paper_1606_07407_gb300.inputs.WORKLOADS, recovered
+--batch signals at a time (batched) or one at a time (--form plain).
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead.
 """
@@ -17,6 +22,7 @@ import os
 import re
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -30,12 +36,15 @@ if "--impl" in sys.argv and "reference" in sys.argv or "--cpu-baseline-only" in 
 
 import numpy as np  # noqa: E402
 
-from paper_1606_07407_gb300.inputs import WORKLOADS  # noqa: E402
+from paper_1606_07407_gb300.inputs import BASE_SEED, WORKLOADS, batched_mix  # noqa: E402
 
 METRIC = "modes recovered/s at exact freq recovery"
 UNIT = "modes/s"
-DEFAULT_WORKLOAD = "d5_N1024_k1000"
+MIX = "mix4096"
+MIX_SIGNALS = 4096
+DEFAULT_WORKLOAD = MIX
 FP32_ALU_LANES_PER_SM = 128      # FP32 FMA lanes per SM (Blackwell)
+ORACLE_TH = dict(tau=1e-3, rho=2.0 ** -17, delta=0.25)   # the float policies' default thresholds
 
 
 def _peaks():
@@ -46,8 +55,8 @@ def _peaks():
         return {}
 
 
-# DRAM traffic per sampling launch, from the committed ncu summary of this workload, valid while
-# the sampling sources are the ones that summary was taken from
+# DRAM traffic per sampling launch, from the committed ncu summary of the d = 5 workload, valid
+# while the sampling sources are the ones that summary was taken from
 SAMPLE_PROFILE = os.path.join(ROOT, "profiles", "k_sample_d5_N1024_k1000_batch256.md")
 SAMPLE_SOURCES = ["sample_tile.cuh", "engine_kernels.cuh", "engine.cuh", "sfft_internal.cuh"]
 
@@ -75,31 +84,100 @@ def sample_traffic(workload: str):
     return float(val.group(1))
 
 
-# ------------------------------------------------------------------ CPU oracle timing
+# ------------------------------------------------------------------ workloads
+
+class Job:
+    """The signals one rank recovers per step, with each signal's plan arguments."""
+
+    def __init__(self, name: str, rank: int, batch: int):
+        from paper_1606_07407_gb300 import tuning
+        self.name = name
+        if name == MIX:
+            mix = batched_mix(MIX_SIGNALS, seed=BASE_SEED + 4 + 1000 * rank)
+            self.sigs = [s for s, _ in mix]
+            self.blocks = [b for _, b in mix]
+            self.sched = [tuning.schedule(s.d, s.N, s.k) for s in self.sigs]
+            self.homogeneous = False
+            self.noise = 0.0
+            self.table_sha = tuning.table_sha256()
+        else:
+            from paper_1606_07407_gb300 import dist as D
+            wl = WORKLOADS[name]
+            self.sigs = [wl.signal(seed_offset=o) for o in D.rank_seed_offsets(rank, batch)]
+            self.blocks = [wl.blocks] * len(self.sigs)
+            self.sched = [{"c": 5, "p_min": wl.p_min, "fuse_max_len": 0}] * len(self.sigs)
+            self.homogeneous = True
+            self.noise = wl.noise_sigma
+            self.table_sha = None
+        self.ks = [s.k for s in self.sigs]
+        self.modes = int(sum(self.ks))
+
+    def config(self) -> dict:
+        if self.homogeneous:
+            s = self.sigs[0]
+            return {"workload": self.name, "d": s.d, "N": s.N, "k": s.k, "blocks": list(self.blocks[0]),
+                    "signals_per_step": len(self.sigs), "p_min": self.sched[0]["p_min"]}
+        ds = [s.d for s in self.sigs]
+        ns = [s.N for s in self.sigs]
+        cs = sorted({sc["c"] for sc in self.sched})
+        pm = sorted({sc["p_min"] for sc in self.sched})
+        return {"workload": self.name, "signals_per_step": len(self.sigs), "modes_per_step": self.modes,
+                "k": [min(self.ks), max(self.ks)], "d": [min(ds), max(ds)], "N": [min(ns), max(ns)],
+                "r": [1.0, 10.0], "blocks": "default rule per signal (smallest b with N^b >= 4 c k)",
+                "schedule": f"per (N, k) class from the tuned table: prime factor c in {cs}, prime floor in {pm}",
+                "tuned_table_sha256": self.table_sha}
+
+    def make_plans(self, sfft, precision, residual, stream, graph=True):
+        if self.homogeneous:
+            s, sc = self.sigs[0], self.sched[0]
+            plan = sfft.Plan(s.d, s.N, s.k, blocks=self.blocks[0], precision=precision, graph=graph, stream=stream,
+                             residual=residual, noise_sigma=self.noise, p_min=sc["p_min"], c=sc["c"],
+                             fuse_max_len=sc["fuse_max_len"])
+            return [plan] * len(self.sigs)
+        return [sfft.Plan(s.d, s.N, s.k, blocks=b, precision=precision, graph=graph, stream=stream,
+                          residual=residual, p_min=sc["p_min"], c=sc["c"], fuse_max_len=sc["fuse_max_len"])
+                for s, b, sc in zip(self.sigs, self.blocks, self.sched)]
+
+
+def oracle_recover(sig, blocks, sched, residual):
+    import oracle.sfft_oracle as O
+    th = O.Thresholds(sigma=sig.noise_sigma, **ORACLE_TH)
+    noise = None
+    if sig.noise_sigma > 0:
+        noise = lambda i, p, d, s=sig: O.black_box_noise(s.noise_seed, i, p, d, s.noise_sigma)  # noqa: E731
+    return O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, blocks, th=th, residual=residual,
+                              noise=noise, p_min=sched["p_min"], c=sched["c"], estimator="mean")
+
 
 def oracle_throughput(workload: str, min_seconds: float, max_recoveries: int, seed_base: int,
-                      residual: str = "bins"):
-    """Runs the FP64 oracle on successive signals of the workload until min_seconds of CPU
-    work (or max_recoveries), with the registry removed in the same form as the GPU arm.
-    Returns (modes/s, recoveries, seconds, exact)."""
-    import oracle.sfft_oracle as O
-    wl = WORKLOADS[workload]
-    th = O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25, sigma=wl.noise_sigma)
+                      residual: str = "bins", keep=None):
+    """Runs the FP64 oracle on successive signals of the workload until min_seconds of CPU work
+    (or max_recoveries), with the registry removed in the same form as the GPU arm and the same
+    prime schedule.  For the mix, signal seed_base + n of rank 0's mix; else the preset's signal
+    of that seed offset.  keep (a list), if given, receives (index, freqs, coeffs) of each.
+    Returns (modes/s, recoveries, seconds, exact, modes)."""
+    if workload == MIX:
+        from paper_1606_07407_gb300 import tuning
+        mix = batched_mix(MIX_SIGNALS, seed=BASE_SEED + 4)
     n, modes, t_total, exact = 0, 0, 0.0, True
     while n < max_recoveries and (t_total < min_seconds or n == 0):
-        sig = wl.signal(seed_offset=seed_base + n)
+        if workload == MIX:
+            sig, blocks = mix[(seed_base + n) % MIX_SIGNALS]
+            sched = tuning.schedule(sig.d, sig.N, sig.k)
+        else:
+            wl = WORKLOADS[workload]
+            sig, blocks, sched = (wl.signal(seed_offset=seed_base + n), wl.blocks,
+                                  {"c": 5, "p_min": wl.p_min, "fuse_max_len": 0})
         t0 = time.perf_counter()
-        noise = None
-        if wl.noise_sigma > 0:
-            noise = lambda i, p, d, s=sig: O.black_box_noise(s.noise_seed, i, p, d, wl.noise_sigma)  # noqa: E731
-        res = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, wl.blocks, th=th, residual=residual,
-                                 noise=noise, p_min=wl.p_min)
+        res = oracle_recover(sig, blocks, sched, residual)
         t_total += time.perf_counter() - t0
         planted = sig.freqs[np.lexsort(sig.freqs.T[::-1])].astype(np.int64)
         exact = exact and res.converged and np.array_equal(res.freqs, planted)
+        if keep is not None:
+            keep.append((seed_base + n, res.freqs, res.coeffs))
         n += 1
         modes += sig.k
-    return modes / t_total, n, t_total, exact
+    return modes / t_total, n, t_total, exact, modes
 
 
 # ------------------------------------------------------------------ clocks
@@ -145,6 +223,7 @@ class ClockSampler:
             inside = [min(self.samples, key=lambda ts: abs(ts[0] - mid))[1]]
         if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
         def num(x):
             try:
                 return float(x)
@@ -186,29 +265,32 @@ def _sum_over_ranks(world, value: float) -> float:
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args):
-    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    """The FP64 oracle on the host, as it stands: each step recovers one signal of the workload
+    (the mix: the next signal of rank 0's mix), single-threaded."""
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    wl = WORKLOADS[args.workload]
     for w in range(args.warmup):
         oracle_throughput(args.workload, 0.0, 1, seed_base=10_000 + w, residual=args.residual)
-    t = 0.0
-    modes = 0
-    exact = True
+    t, modes, exact = 0.0, 0, True
     for s in range(args.steps):
-        v, n, secs, ok = oracle_throughput(args.workload, 0.0, 1, seed_base=s, residual=args.residual)
+        _, n, secs, ok, m = oracle_throughput(args.workload, 0.0, 1, seed_base=s, residual=args.residual)
         t += secs
-        modes += n * wl.k
+        modes += m
         exact = exact and ok
     value = modes / t if exact else 0.0
+    cfg = {"workload": args.workload, "signals_per_step": 1, "form": "FP64 CPU oracle, one recovery per step",
+           "residual": args.residual}
+    if args.workload != MIX:
+        wl = WORKLOADS[args.workload]
+        cfg.update(d=wl.d, N=wl.N, k=wl.k, blocks=list(wl.blocks))
+    else:
+        cfg["sample"] = f"signals 0..{args.steps - 1} of the {MIX_SIGNALS}-signal mix, one per step"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded planted sparse signals)",
-        "config": {"workload": args.workload, "d": wl.d, "N": wl.N, "k": wl.k, "blocks": list(wl.blocks),
-                   "signals_per_step": 1, "form": "FP64 CPU oracle, one recovery per step",
-                   "residual": args.residual},
+        "data": "synthetic (seeded planted sparse signals)", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} full recoveries, one per step, single thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -236,6 +318,13 @@ def _timed_steps(torch, stream, flush, steps, step_fn):
     return ms, outs
 
 
+def _precision_name(prec: str) -> str:
+    return {"fp32": "AUTO: float sampling and DFT; phase ratio, read-out and coefficient in double above N = 2^14",
+            "fp32_fp64ratio": "float sampling and DFT; phase ratio, read-out and coefficient in double",
+            "fp32_only": "every step in float",
+            "fp64": "every step in double"}[prec]
+
+
 def run_ours(args):
     import torch
     world, rank, local = _dist_setup(args.gpus)
@@ -246,33 +335,33 @@ def run_ours(args):
     _barrier(world)
     from paper_1606_07407_gb300 import sfft
 
-    wl = WORKLOADS[args.workload]
+    job = Job(args.workload, rank, args.batch)
     stream = torch.cuda.current_stream()
-    nb = args.batch
-    # inputs resident in HBM before timing: distinct signals per rank and batch slot
-    from paper_1606_07407_gb300 import dist as D
-    sigs = [wl.signal(seed_offset=o) for o in D.rank_seed_offsets(rank, nb)]
-    dev = [sfft.Signal(s.freqs, s.coeffs, s.N, noise_sigma=s.noise_sigma, noise_seed=s.noise_seed) for s in sigs]
-    planted = [s.freqs[np.lexsort(s.freqs.T[::-1])].astype(np.int64) for s in sigs]
+    nb = len(job.sigs)
+    # inputs resident in HBM before timing
+    dev = [sfft.Signal(s.freqs, s.coeffs, s.N, noise_sigma=s.noise_sigma, noise_seed=s.noise_seed) for s in job.sigs]
+    planted = [s.freqs[np.lexsort(s.freqs.T[::-1])].astype(np.int64) for s in job.sigs]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    plan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, precision=args.precision, graph=True, stream=stream,
-                     residual=args.residual, noise_sigma=wl.noise_sigma, p_min=wl.p_min)
-    batch = sfft.Batch([plan] * nb, graph=True, stream=stream)
-    bout = batch.outputs(caps=[wl.k + 16] * nb)   # room for the recovered set (overflow: CAPACITY)
+    t_plan0 = time.perf_counter()
+    plans = job.make_plans(sfft, args.precision, args.residual, stream)
+    batch = sfft.Batch(plans, graph=True, stream=stream)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t_plan0
+    caps = [k + 16 for k in job.ks]
+    bout = batch.outputs(caps=caps)   # room for the recovered set (overflow: CAPACITY)
     allow = (0, 2, 3, 5)
 
     def step_batched():
         res, sts, st = batch.execute(dev, out=bout, allow=allow)
         return sts, st, res
 
-    cap = 2 * wl.k + 16
-    pouts = [(torch.empty((cap, wl.d), dtype=torch.int32, device="cuda"),
-              torch.empty((cap,), dtype=torch.complex128, device="cuda")) for _ in range(nb)]
+    pouts = [(torch.empty((2 * k + 16, s.d), dtype=torch.int32, device="cuda"),
+              torch.empty((2 * k + 16,), dtype=torch.complex128, device="cuda")) for k, s in zip(job.ks, job.sigs)]
 
     def step_plain():
         sts, res, st = [], [], None
         for b in range(nb):
-            f, a, status, st = plan.execute(dev[b], capacity=cap, out=pouts[b], allow=allow)
+            f, a, status, st = plans[b].execute(dev[b], capacity=2 * job.ks[b] + 16, out=pouts[b], allow=allow)
             sts.append(status)
             res.append((f, a))
         return sts, st, res
@@ -304,15 +393,16 @@ def run_ours(args):
 
     # every step's statuses, and the last step's sets element by element against the planted ones
     ok_all = all(all(x == 0 for x in sts) for sts, _, _ in outs)
-    for b, (f, a) in enumerate(outs[-1][2]):
-        gf, _ = sfft.sort_result(f.cpu().numpy(), a.cpu().numpy())
-        ok_all = ok_all and np.array_equal(gf, planted[b])
+    last = [sfft.sort_result(f.cpu().numpy(), a.cpu().numpy()) for f, a in outs[-1][2]]
+    exact_slots = sum(1 for b, (gf, _) in enumerate(last) if np.array_equal(gf, planted[b]))
+    ok_all = ok_all and exact_slots == nb
     total_ms = _max_over_ranks(world, float(sum(step_ms)))
-    modes = _sum_over_ranks(world, float(args.steps * nb * wl.k)) if ok_all else 0.0
+    modes = _sum_over_ranks(world, float(args.steps * job.modes)) if ok_all else 0.0
     value = modes / (total_ms / 1e3)
     launches_step = outs[-1][1]["launches"] if args.form == "batched" else None
     gpu_launches = int(sum(sum(st["launches"].values()) for _, st, _ in outs)) if args.form == "batched" else \
         int(args.steps * nb * sum(outs[-1][1]["launches"].values()))
+    rounds_step = outs[-1][1]["rounds"] if args.form == "batched" else None
 
     # the other form, on the same signals, for comparison
     other_fn = step_plain if args.form == "batched" else step_batched
@@ -321,14 +411,12 @@ def run_ours(args):
         other_fn()
         other_ms, other_outs = _timed_steps(torch, stream, flush, args.other_steps, other_fn)
         other_ok = all(all(x == 0 for x in sts) for sts, _, _ in other_outs)
-        other_value = (args.other_steps * nb * wl.k) / (sum(other_ms) / 1e3) if other_ok else 0.0
+        other_value = (args.other_steps * job.modes) / (sum(other_ms) / 1e3) if other_ok else 0.0
 
     # profiled pass (same batch, rounds enqueued from the host with CUDA events around each
     # kernel class on the launch stream): kernel shares and the sampling kernel's roofline
-    pplan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, precision=args.precision, profile=True, stream=stream,
-                      residual=args.residual, noise_sigma=wl.noise_sigma, p_min=wl.p_min)
-    pbatch = sfft.Batch([pplan] * nb, graph=False, stream=stream)
-    pout = pbatch.outputs(caps=[wl.k + 16] * nb)
+    pbatch = sfft.Batch(plans, graph=False, profile=True, stream=stream)
+    pout = pbatch.outputs(caps=caps)
     pbatch.execute(dev, out=pout, allow=allow)
     prof_ms, prof = _timed_steps(torch, stream, flush, args.profile_steps,
                                  lambda: pbatch.execute(dev, out=pout, allow=allow))
@@ -344,18 +432,18 @@ def run_ours(args):
     sm_max = (clocks or {}).get("sm_max_mhz") or _peaks().get("sm_max_mhz", 2070.0)
     peak = props.multi_processor_count * FP32_ALU_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     tot_class = sum(class_ms.values())
+    del pbatch, pout
 
     # end to end through the public API with host buffers: per step, the step's inputs (all
     # signals' modes, packed) copied pinned host -> device, the signal handles refilled in place by
     # one call, recovery, device -> host of the results.  The steps are pipelined over a second
     # stream: step i + 1's inputs and step i - 1's results cross PCIe/C2C while step i recovers
     # (double-buffered inputs and outputs); the wall clock runs from the first copy to the last.
-    host_fw = torch.from_numpy(np.concatenate([s.freqs.astype(np.int32).reshape(-1) for s in sigs])).pin_memory()
-    host_ca = torch.from_numpy(np.concatenate([s.coeffs.astype(np.complex128) for s in sigs])).pin_memory()
+    host_fw = torch.from_numpy(np.concatenate([s.freqs.astype(np.int32).reshape(-1) for s in job.sigs])).pin_memory()
+    host_ca = torch.from_numpy(np.concatenate([s.coeffs.astype(np.complex128) for s in job.sigs])).pin_memory()
     dev_in = [(torch.empty_like(host_fw, device="cuda"), torch.empty_like(host_ca, device="cuda")) for _ in range(2)]
-    ks = [s.k for s in sigs]
     h2d = host_fw.numel() * 4 + host_ca.numel() * 16
-    outs2 = [bout, batch.outputs(caps=[wl.k + 16] * nb)]
+    outs2 = [bout, batch.outputs(caps=caps)]
     host_out = [(torch.empty(o[1].shape, dtype=torch.int32).pin_memory(),
                  torch.empty(o[2].shape, dtype=torch.complex128).pin_memory()) for o in outs2]
     d2h = host_out[0][0].numel() * 4 + host_out[0][1].numel() * 16
@@ -385,36 +473,44 @@ def run_ours(args):
         flush.zero_()
         stream.wait_event(in_ready[i % 2])
         fw, ca = dev_in[i % 2]
-        sfft.assign_many(dev, fw, ca, ks, stream=stream)
+        sfft.assign_many(dev, fw, ca, job.ks, stream=stream)
         res, sts, _ = batch.execute(dev, out=outs2[i % 2], allow=allow)
         d2h_step(i)
-        e2e_ok = e2e_ok and all(x == 0 for x in sts) and all(int(n) == wl.k for n in res.n_found)
+        e2e_ok = e2e_ok and all(x == 0 for x in sts) and all(int(n) == k for n, k in zip(res.n_found, job.ks))
     copy_stream.synchronize()
     torch.cuda.synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - t0)
     e2e_ms = _max_over_ranks(world, e2e_ms)
-    e2e_modes = _sum_over_ranks(world, float(args.e2e_steps * nb * wl.k)) if e2e_ok else 0.0
+    e2e_modes = _sum_over_ranks(world, float(args.e2e_steps * job.modes)) if e2e_ok else 0.0
     e2e_value = e2e_modes / (e2e_ms / 1e3)
 
     if rank != 0:
         return 0
+    cfg = job.config()
+    cfg.update({
+        "form": ("batched: all signals in every launch, device-ended CUDA-graph round loop"
+                 if args.form == "batched" else "plain: one signal per execute, CUDA-graph round loop"),
+        "precision": _precision_name(args.precision),
+        "residual": ("registry removed bin by bin after the DFT" if args.residual == "bins"
+                     else "registry sampled with the black box (f - g)"),
+        "l2": "flushed between timed steps (256 MiB write)", "exact_recovery": bool(ok_all),
+        "exact_slots": f"{exact_slots}/{nb}",
+        "plan_time_s": round(plan_s, 3),
+        "plan_time_note": "plans and the batch are made before timing: device buffers, prime tables, and "
+                          "round 1's root tables and Bluestein filter spectra (fixed by k) live with them"})
+    if rounds_step is not None:
+        cfg["rounds_last_step"] = rounds_step
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "fp32" if args.precision != "fp64" else "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "fp32",
         "data": "synthetic (seeded planted sparse signals, resident in HBM)",
-        "config": {"workload": args.workload, "d": wl.d, "N": wl.N, "k": wl.k, "blocks": list(wl.blocks),
-                   "signals_per_step": nb,
-                   "form": ("batched: all signals in every launch, device-ended CUDA-graph round loop"
-                            if args.form == "batched" else "plain: one signal per execute, CUDA-graph round loop"),
-                   "precision": "FP32 sampling, DFT and phase ratio (N <= 2^14)" if args.precision == "fp32"
-                   else args.precision,
-                   "residual": ("registry removed bin by bin after the DFT" if args.residual == "bins"
-                                else "registry sampled with the black box (f - g)"),
-                   "l2": "flushed between timed steps (256 MiB write)", "exact_recovery": bool(ok_all)},
+        "config": cfg,
         "other_form": {"form": "plain" if args.form == "batched" else "batched", "value": other_value,
                        "unit": UNIT, "steps": args.other_steps,
-                       "ms_per_step": sum(other_ms) / max(len(other_ms), 1)},
+                       "ms_per_step": sum(other_ms) / max(len(other_ms), 1),
+                       "batched_over_plain": (value / other_value if other_value else None)
+                       if args.form == "batched" else None},
         "roofline": {"bound": "alu", "kernel": "k_sample", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
                      "traffic": sample_traffic(args.workload),
@@ -422,7 +518,7 @@ def run_ours(args):
                                    f"x {sm_max:.0f} MHz",
                      "measured": f"CUDA events around each sampling launch, {args.profile_steps} profiled steps "
                                  "of the same batch (rounds enqueued from the host); terms of the rounds "
-                                 "the batched kernels ran",
+                                 "the batched kernels ran, 8 flops each",
                      "launches": sample_launches,
                      "avg_launch_us": 1e3 * sample_ms / max(sample_launches, 1),
                      "profiled_ms_per_step": sum(prof_ms) / max(len(prof_ms), 1)},
@@ -437,7 +533,9 @@ def run_ours(args):
     if launches_step is not None:
         line["launches_per_step"] = launches_step
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args)
+        cb, ref = cpu_baseline(args)
+        line["cpu_baseline"] = cb
+        line["precision_report"] = precision_report(ref, last, planted, job)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -445,17 +543,46 @@ def run_ours(args):
     return 0
 
 
+def precision_report(ref, last, planted, job):
+    """Every recovered set against the planted one, and the coefficients of the signals the
+    oracle recovered (the cpu_baseline sample) against the FP64 oracle's."""
+    rel = []
+    same = 0
+    ref = [(idx, rf, ra) for idx, rf, ra in ref if idx < len(last)]
+    for idx, rf, ra in ref:
+        gf, ga = last[idx]
+        if np.array_equal(gf, rf):
+            same += 1
+            rel.append(np.abs(ga - ra) / np.abs(ra))
+    rel = np.concatenate(rel) if rel else np.zeros(0)
+    return {"exact_sets_vs_planted": f"{sum(1 for b, (gf, _) in enumerate(last) if np.array_equal(gf, planted[b]))}"
+                                     f"/{len(last)}",
+            "oracle_signals": len(ref), "sets_equal_oracle": f"{same}/{len(ref)}",
+            "coeff_rel_err_vs_oracle": {"max": float(rel.max()) if rel.size else None,
+                                        "median": float(np.median(rel)) if rel.size else None,
+                                        "modes": int(rel.size)}}
+
+
 def cpu_baseline(args):
     """The oracle, single-threaded, in a child process on a bounded sample of the workload; then
     one oracle process per host core on independent signals (their summed rates under
-    all_cores)."""
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-only", "--workload", args.workload,
-           "--cpu-seconds", str(args.cpu_seconds), "--residual", args.residual, "--cpu-all-cores"]
-    try:
-        r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
-        return json.loads(r.stdout.strip().splitlines()[-1])
-    except Exception as exc:  # noqa: BLE001
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+    all_cores).  Also returns the sample's oracle results [(index, freqs, coeffs)]."""
+    with tempfile.TemporaryDirectory() as tmp:
+        out = os.path.join(tmp, "oracle.npz")
+        cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-only", "--workload", args.workload,
+               "--cpu-seconds", str(args.cpu_seconds), "--residual", args.residual, "--cpu-all-cores",
+               "--oracle-out", out]
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+            cb = json.loads(r.stdout.strip().splitlines()[-1])
+        except Exception as exc:  # noqa: BLE001
+            return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}, []
+        ref = []
+        if os.path.exists(out):
+            z = np.load(out)
+            for i in range(int(z["n"])):
+                ref.append((int(z[f"idx{i}"]), z[f"w{i}"], z[f"a{i}"]))
+        return cb, ref
 
 
 def _oracle_worker(workload, seconds, seed_base, residual):
@@ -468,8 +595,10 @@ def oracle_all_cores(workload, seconds, residual):
     rates, each over its own recoveries' time (process start-up is not counted)."""
     import multiprocessing as mp
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    stride = 7 if workload == MIX else 100_000
     with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.starmap(_oracle_worker, [(workload, seconds, 100_000 * (i + 1), residual) for i in range(cores)])
+        res = pool.starmap(_oracle_worker, [(workload, seconds, stride * (i + 1) + (50 if workload == MIX else 0),
+                                             residual) for i in range(cores)])
     exact = all(r[3] for r in res)
     return {"value": sum(r[0] for r in res) if exact else 0.0, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{cores} processes x {min(r[1] for r in res)}-{max(r[1] for r in res)} full recoveries "
@@ -479,30 +608,39 @@ def oracle_all_cores(workload, seconds, residual):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--batch", type=int, default=256, help="signals recovered per step")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + [MIX])
+    ap.add_argument("--batch", type=int, default=256, help="signals recovered per step (single-shape presets)")
     ap.add_argument("--form", default="batched", choices=["batched", "plain"])
-    ap.add_argument("--other-steps", type=int, default=3)
-    ap.add_argument("--profile-steps", type=int, default=3)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--other-steps", type=int, default=1)
+    ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_fp64ratio", "fp32_only", "fp64"],
+                    help="fp32: AUTO (ratio in double above N = 2^14); fp32_fp64ratio: ratio always in double")
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-baseline-only", action="store_true")
     ap.add_argument("--cpu-all-cores", action="store_true",
                     help="with --cpu-baseline-only: also time one oracle process per host core")
+    ap.add_argument("--oracle-out", default=None, help="with --cpu-baseline-only: save the oracle's results (npz)")
     ap.add_argument("--residual", default="bins", choices=["bins", "samples"],
                     help="registry removed from the transform bin by bin, or sampled with the black box")
     args = ap.parse_args(argv)
     if args.cpu_baseline_only:
-        v, n, secs, exact = oracle_throughput(args.workload, args.cpu_seconds, 1000, seed_base=0,
-                                              residual=args.residual)
+        keep = []
+        v, n, secs, exact, modes = oracle_throughput(args.workload, args.cpu_seconds, 1000, seed_base=0,
+                                                     residual=args.residual, keep=keep)
+        what = f"signals 0..{n - 1} of the mix" if args.workload == MIX else f"{n} signals of the workload"
         out = {"value": v if exact else 0.0, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{n} full recoveries of the workload ({secs:.1f} s, single thread, "
+               "sample": f"{n} full recoveries ({what}, {modes} modes, {secs:.1f} s, single thread, "
                          f"residual {args.residual})"}
+        if args.oracle_out:
+            arrs = {"n": np.array(len(keep))}
+            for i, (idx, w, a) in enumerate(keep):
+                arrs[f"idx{i}"], arrs[f"w{i}"], arrs[f"a{i}"] = np.array(idx), w, a
+            np.savez(args.oracle_out, **arrs)
         if args.cpu_all_cores:
             try:
                 out["all_cores"] = oracle_all_cores(args.workload, max(1.0, args.cpu_seconds * 2 / 3), args.residual)

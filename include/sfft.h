@@ -47,12 +47,19 @@ typedef enum {
  * ratio, frequency read-out and coefficient estimate in double when N > 2^14
  * (where float's phase resolution starts to matter against pi / N), else in
  * float.  FP32_FP64RATIO: the same with the ratio step always in double.
- * FP32: every step in float.  FP64: every step in double. */
+ * FP32: every step in float.  FP64: every step in double.
+ * FP32_BF16DFT: as AUTO, except that a round whose prime is at most 8191 takes
+ * its DFT (Eq. 3) as a dense contraction with the DFT matrix on the tensor
+ * cores: operands split into two BF16 terms each (hi = bf16(v), lo = bf16(v -
+ * hi)), three products per pair, FP32 accumulation; longer rounds use the float
+ * Bluestein DFT, and no round is fused.  Its DFT carries about 2^-16 of each
+ * operand's size instead of float's 2^-24 (at most 64 sample sets). */
 typedef enum {
   SFFT_PREC_AUTO = 0,
   SFFT_PREC_FP32_FP64RATIO = 1,
   SFFT_PREC_FP32 = 2,
-  SFFT_PREC_FP64 = 3
+  SFFT_PREC_FP64 = 3,
+  SFFT_PREC_FP32_BF16DFT = 4
 } sfft_precision;
 
 typedef struct sfft_plan_s* sfft_plan;
@@ -60,8 +67,12 @@ typedef struct sfft_signal_s* sfft_signal;
 typedef struct sfft_batch_s* sfft_batch;
 
 /* Prime schedule (Alg. 1 and Alg. 2: p = i-th prime >= c k*, c = 5 in Sec. 5).
+ * c is an input of both algorithms; c_eighths > 0 gives it in eighths (c = c_eighths / 8, so
+ * 2.5 is 20), overriding c_prime, and the rule takes the i-th prime >= ceil(c k*).  A smaller c
+ * samples fewer points per round (about c k* per set) at the price of more collisions (a mode
+ * is alone in its bin with probability about e^{-1/c}) and so more rounds.
  * primes != NULL overrides the rule: round i uses primes[(i-1) mod n_primes].
- * p_min > 0 floors the rule: round i uses the i-th prime >= max(c k*, p_min).
+ * p_min > 0 floors the rule: round i uses the i-th prime >= max(ceil(c k*), p_min).
  * With noisy samples the phase read-out w_n = N Arg(Y_n / Y_0) / (2 pi) of a
  * mode a varies by about N sigma / (2 pi sqrt(p) |a|), so reading modes down
  * to |a| reliably needs p of order (4 N sigma / (2 pi delta |a|))^2, which the
@@ -71,10 +82,11 @@ typedef struct sfft_batch_s* sfft_batch;
  * bins p |a| large against it (N = 512, Q = 5.9e5: the slowest of 256 signals
  * needs 39 rounds without a floor, 7 with p_min = 1024). */
 typedef struct {
-  int c_prime;            /* c; 0 means 5 */
+  int c_prime;            /* c; 0 means 5 (1 .. 4096) */
   int n_primes;
   const int64_t* primes;  /* host, n_primes entries, each prime and >= 5 */
   int64_t p_min;          /* 0: no floor */
+  int c_eighths;          /* 0: c = c_prime; else c = c_eighths / 8 (1 .. 32768) */
 } sfft_pschedule;
 
 /* Line directions (Sec. 3.2, 3.3, 4.1).  Either n_dirs explicit integer
@@ -113,7 +125,24 @@ typedef struct {
   int tilt_base;     /* shift = TILT: the rotation of Sec. 3.3, sin = tilt_height / tilt_hypo,  */
   int tilt_height;   /* cos = tilt_base / tilt_hypo (Eq. 25): a primitive Pythagorean triple,   */
   int tilt_hypo;     /* both legs >= 1 and <= 2^20; Theorem 1 wants tilt_base > 2 N (see below) */
+  int fuse_max_len;  /* FP32 policies: rounds whose Bluestein length is at most this (and at most the
+                        fused kernel's limit for the slot's set count) run fused; 0: that limit */
+  int empty_rounds;  /* rounds in a row with no bin of any set above the empty-bin level that end the
+                        recovery; 0: the number of line directions under the float policies, 1
+                        under FP64 (see the stop rule below) */
 } sfft_opts;
+
+/* Stop rule.  The recovery ends when empty_rounds rounds in a row, on successive line directions,
+ * find no bin of any set above the empty-bin level (the residual is empty).  A read-out that is
+ * wrong in a coordinate outside its round's block passes the own-bin check (w . u) mod p = h,
+ * since u is zero there, and one wrong by a multiple of p inside the block passes it too (a
+ * collision that slipped through the ratio test reads such values).  The registry then holds w'
+ * instead of w, and the pair shares a bin on every line that does not separate them, where set
+ * 0 cancels and the shifted sets differ by a phase of only 2 pi |w_n - w'_n| / N, below the level
+ * at large N.  A later line of the block where they differ, with another prime, separates them:
+ * so the float policies wait for an empty round on every direction.  The FP64 policy's ratio
+ * test (tau = 1e-7) lets a collision through with negligible probability, and its read-outs do
+ * not slip, so one empty round ends it. */
 
 /* The shifted sample sets (Alg. 2).  COORD (default): one set per coordinate, shifted by e_n / N,
  * reads w_n = N Arg(Y_n / Y_0) / (2 pi); d + 1 sets.  BLOCK (Alg. 2 as printed): one set per
@@ -229,8 +258,14 @@ sfft_status sfft_execute(sfft_plan plan, sfft_signal signal, int64_t capacity,
 /* A batch of n signal slots; slot s takes d, N, k, schedule, directions and
  * thresholds from plans[s] (the same plan may appear many times).  All plans
  * must share the float-or-double choice of their precision.  The batch owns
- * its own device buffers; the plans may be destroyed afterwards.  graph = 1
- * runs the rounds as one CUDA graph with a device-ended while-loop. */
+ * its own device buffers; the plans may be destroyed afterwards.  graph is a
+ * set of flags: SFFT_BATCH_GRAPH runs the rounds as one CUDA graph with a
+ * device-ended while-loop; SFFT_BATCH_PROFILE (also on when some plan has
+ * opts.profile) enqueues the rounds from the host with CUDA events between
+ * the kernel classes and fills sfft_stats.kernel_ms.  INVALID_ARG for other
+ * bits. */
+#define SFFT_BATCH_GRAPH 1
+#define SFFT_BATCH_PROFILE 2
 sfft_status sfft_batch_create(int n, const sfft_plan* plans, void* stream, int graph, sfft_batch* batch_out);
 void sfft_batch_destroy(sfft_batch batch);
 int64_t sfft_batch_device_bytes(sfft_batch batch);

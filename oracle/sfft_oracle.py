@@ -21,7 +21,8 @@ What it computes (Algorithm 2, MultiPhaseshift, in its general form):
          w_n = N Arg(Y_n[h] / Y_0[h]) / (2 pi), rounded            (Eq. 7, Eq. 41 with eps = 1/N)
          a   = Y_0[h] / p                                         (Eq. 7, Eq. 41)
     R <- R merged with the accepted (w, a); prune small |a|       (Alg. 2 registry update)
-  until a round finds no bin of any set above the empty-bin level (the residual is empty).
+  until empty_rounds rounds in a row (successive line directions; by default one per
+  direction) find no bin of any set above the empty-bin level (the residual is empty).
 
 Readings of the paper taken here (each is listed with its reason in the design
 notes): per-coordinate shifts e_n / N instead of eps times a block vector; the
@@ -496,7 +497,7 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: floa
                      th: Thresholds | None = None, max_rounds: int | None = None,
                      box_lo: int = 0, primes=None, dirs=None, noise=None,
                      estimator: str = "set0", residual: str = "samples", p_min: int = 0,
-                     shift: str = "coord", tilt=None) -> Result:
+                     shift: str = "coord", tilt=None, empty_rounds: int | None = None) -> Result:
     """Algorithm 2 (MultiPhaseshift) on the black box f = sum_j coeffs_j e^{2 pi i freqs_j . t}.
 
     ``primes``, if given, overrides the prime rule (round i uses primes[(i-1) mod len]).
@@ -507,7 +508,9 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: floa
     prime rule: round i uses the i-th prime >= max(c k*, p_min).  ``shift`` is "coord" (one
     shifted set per coordinate, s_n = e_n / N), "block" (one per block, Alg. 2 as printed) or
     "tilt" (d = 2, Alg. 3: ``tilt`` = (base, height, hypo); the lines run along the rotated axes
-    in turn unless ``dirs`` is given, and the sets shift along them)."""
+    in turn unless ``dirs`` is given, and the sets shift along them).  ``empty_rounds`` rounds in a
+    row with no bin of any set above the empty-bin level end the run (default: the number of line
+    directions)."""
     if residual not in ("samples", "bins"):
         raise ValueError(residual)
     if shift == "tilt":
@@ -525,6 +528,10 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: floa
         max_rounds = 64 + 4 * max(1, math.ceil(math.log2(max(k, 2))))
     R: dict = {}                       # registry: w -> a, in insertion order
     a_ref = None
+    n_dirs = len(dirs) if dirs is not None and len(dirs) > 0 else len(blocks)
+    if empty_rounds is None:
+        empty_rounds = n_dirs
+    empty_streak = 0
     rounds = []
     converged = False
     for i in range(1, max_rounds + 1):
@@ -555,13 +562,20 @@ def multi_phaseshift(freqs, coeffs, d: int, N: int, k: int, blocks=None, c: floa
         eta_bin = max(th.rho * p * a_ref, 6.0 * th.sigma * math.sqrt(p))
         stat = {"round": i, "p": p, "k_star": k_star, "terms": int(all_w.shape[0]),
                 "samples": int(Y.shape[0]) * p, "eta_bin": eta_bin}
-        # the residual is empty when no bin of any set is above the level: a registry pair of
-        # opposite coefficients that the line does not separate cancels in set 0 alone
+        # the residual is empty when no bin of any set is above the level, in empty_rounds rounds
+        # in a row (successive line directions): a registry pair of opposite coefficients that a
+        # line does not separate cancels in set 0, and when the pair differs by a few units in
+        # one coordinate its shifted sets differ by a phase of only 2 pi (w_n - w'_n) / N; a line
+        # of the block where they differ, with another prime, puts the two in different bins
         if not np.any(np.abs(Y) > eta_bin):
+            empty_streak += 1
             stat.update(accepted=0, registry=len(R))
             rounds.append(stat)
-            converged = True
-            break
+            if empty_streak >= empty_rounds:
+                converged = True
+                break
+            continue
+        empty_streak = 0
         acc = classify(Y, p, u, N, eta_bin, th, box_lo, estimator, shift=shift, blocks=blocks, tilt=tilt)
         for _, w, a in acc:                                    # R <- R u (w, a)
             R[w] = R.get(w, 0j) + a

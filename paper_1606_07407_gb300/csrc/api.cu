@@ -128,7 +128,7 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
   sfft_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  if (o.precision < SFFT_PREC_AUTO || o.precision > SFFT_PREC_FP64) return SFFT_ERR_INVALID_ARG;
+  if (o.precision < SFFT_PREC_AUTO || o.precision > SFFT_PREC_FP32_BF16DFT) return SFFT_ERR_INVALID_ARG;
   if (o.box_lo > 0 || o.box_lo < -N) return SFFT_ERR_INVALID_ARG;
   const bool fp64 = o.precision == SFFT_PREC_FP64;
   if (!fp64 && N > (1LL << 23)) return SFFT_ERR_PRECISION;
@@ -157,13 +157,12 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
   D.d = d;
   D.N = N;
   D.k = k;
-  D.c = 5;
+  D.c8 = 40;   // c = 5 (Sec. 5)
   D.box_lo = o.box_lo;
   P->prec = o.precision;
-  D.ratio64 = (o.precision == SFFT_PREC_FP32_FP64RATIO || fp64 ||
-               (o.precision == SFFT_PREC_AUTO && N > (1LL << 14)))
-                  ? 1
-                  : 0;
+  const bool auto_ratio = o.precision == SFFT_PREC_AUTO || o.precision == SFFT_PREC_FP32_BF16DFT;
+  D.ratio64 = (o.precision == SFFT_PREC_FP32_FP64RATIO || fp64 || (auto_ratio && N > (1LL << 14))) ? 1 : 0;
+  D.dense_dft = o.precision == SFFT_PREC_FP32_BF16DFT ? 1 : 0;
   D.coef_mean = o.coef_set0 ? 0 : 1;
   D.peel_bins = o.residual == SFFT_RESIDUAL_BINS ? 1 : 0;
   D.tau = o.tau > 0 ? o.tau : (fp64 ? 1e-7 : 1e-3);
@@ -177,12 +176,17 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
   P->stream = (cudaStream_t)stream;
   P->profile = o.profile != 0;
   P->graph = o.graph != 0;
-  D.fuse = o.unfused ? 0 : 1;
+  D.fuse = (o.unfused || D.dense_dft) ? 0 : 1;   // the fused kernel has its own (Bluestein) DFT
+  if (o.fuse_max_len < 0 || o.empty_rounds < 0) return SFFT_ERR_INVALID_ARG;
+  D.fuse_max_len = o.fuse_max_len;
 
   // ---- prime schedule
   if (ps) {
-    if (ps->c_prime < 0 || ps->n_primes < 0 || ps->p_min < 0 || ps->p_min > (1LL << 26)) return SFFT_ERR_INVALID_ARG;
-    if (ps->c_prime > 0) D.c = ps->c_prime;
+    if (ps->c_prime < 0 || ps->c_prime > 4096 || ps->c_eighths < 0 || ps->c_eighths > 8 * 4096 || ps->n_primes < 0 ||
+        ps->p_min < 0 || ps->p_min > (1LL << 26))
+      return SFFT_ERR_INVALID_ARG;
+    if (ps->c_prime > 0) D.c8 = 8 * ps->c_prime;
+    if (ps->c_eighths > 0) D.c8 = ps->c_eighths;
     D.p_min = ps->p_min;
     if (ps->n_primes > 0) {
       if (!ps->primes) return SFFT_ERR_INVALID_ARG;
@@ -196,7 +200,7 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
     }
   }
   if (D.primes.empty()) {
-    const int64_t lo = std::max<int64_t>((int64_t)D.c * std::max<int64_t>(k, 1), D.p_min);
+    const int64_t lo = std::max<int64_t>(prime_floor_ck(D.c8, std::max<int64_t>(k, 1)), D.p_min);
     int64_t lim = lo + 64LL * D.max_rounds + 1000;
     for (;;) {
       std::vector<int64_t> pr = primes_up_to(lim);
@@ -227,7 +231,7 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
     // default: smallest b with N^b >= 4 c k, d / b blocks, earlier blocks take the remainder
     int b = 1;
     double range = (double)N;
-    while (range < 4.0 * D.c * std::max<int64_t>(k, 1) && b < d) {
+    while (range < 4.0 * (D.c8 / 8.0) * std::max<int64_t>(k, 1) && b < d) {
       ++b;
       range *= (double)N;
     }
@@ -260,6 +264,9 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
     }
   }
 
+  // ---- stop rule: empty rounds in a row that end the recovery (see sfft.h)
+  D.empty_rounds = o.empty_rounds > 0 ? o.empty_rounds : (fp64 ? 1 : D.n_dirs);
+
   // ---- shifted sets: e_n / N per coordinate, or v_n / (2 N^{d1}) per block (Alg. 2 as printed).
   // The block form reads a block's unwrapped frequency (up to N^{d1}) from one phase, so the
   // precision policy follows N^{d1}: float ratio up to 2^14, float samples up to 2^20, FP64 beyond.
@@ -273,7 +280,7 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
       span_max = std::max(span_max, span);
     }
     if (!fp64 && span_max > std::ldexp(1.0, 20)) return SFFT_ERR_PRECISION;
-    if (o.precision == SFFT_PREC_AUTO) D.ratio64 = span_max > std::ldexp(1.0, 14) ? 1 : 0;
+    if (auto_ratio) D.ratio64 = span_max > std::ldexp(1.0, 14) ? 1 : 0;
     D.shift_blocks = blocks;
   }
   // the tilted form reads a rotated coordinate (Q = (base + height) N values) from one phase:
@@ -285,9 +292,11 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
     D.tilt_hypo = o.tilt_hypo;
     const double q = (double)(o.tilt_base + o.tilt_height) * (double)N;
     if (!fp64 && q > std::ldexp(1.0, 21)) return SFFT_ERR_PRECISION;
-    if (o.precision == SFFT_PREC_AUTO) D.ratio64 = q > std::ldexp(1.0, 15) ? 1 : 0;
+    if (auto_ratio) D.ratio64 = q > std::ldexp(1.0, 15) ? 1 : 0;
   }
 
+  // the dense DFT takes every sample set of a signal as the N of one MMA (at most 64)
+  if (D.dense_dft && (D.shift_block ? 1 + (int)D.shift_blocks.size() : d + 1) > 64) return SFFT_ERR_INVALID_ARG;
   std::vector<SlotDesc> slots(1, D);
   EngineBase* e = nullptr;
   sfft_status st = cuda_status(engine_create(fp64, slots, P->stream, P->profile, P->graph, &e));
@@ -417,13 +426,14 @@ sfft_status sfft_execute(sfft_plan plan, sfft_signal signal, int64_t capacity, i
 }
 
 sfft_status sfft_batch_create(int n, const sfft_plan* plans, void* stream, int graph, sfft_batch* batch_out) {
-  if (!batch_out || n < 1 || !plans) return SFFT_ERR_INVALID_ARG;
+  if (!batch_out || n < 1 || !plans || graph < 0 || graph > (SFFT_BATCH_GRAPH | SFFT_BATCH_PROFILE))
+    return SFFT_ERR_INVALID_ARG;
   *batch_out = nullptr;
   std::unique_ptr<sfft_batch_s> B(new sfft_batch_s());
   B->n = n;
   std::vector<SlotDesc> slots;
   slots.reserve(n);
-  bool profile = false;
+  bool profile = (graph & SFFT_BATCH_PROFILE) != 0;
   for (int s = 0; s < n; ++s) {
     if (!plans[s]) return SFFT_ERR_INVALID_ARG;
     const bool fp64 = plans[s]->prec == SFFT_PREC_FP64;
@@ -437,7 +447,8 @@ sfft_status sfft_batch_create(int n, const sfft_plan* plans, void* stream, int g
   }
   EngineBase* e = nullptr;
   sfft_status st = cuda_status(
-      engine_create(B->prec == SFFT_PREC_FP64, slots, (cudaStream_t)stream, profile, graph != 0, &e));
+      engine_create(B->prec == SFFT_PREC_FP64, slots, (cudaStream_t)stream, profile, (graph & SFFT_BATCH_GRAPH) != 0,
+                    &e));
   if (st != SFFT_OK) return st;
   B->eng.reset(e);
   *batch_out = B.release();

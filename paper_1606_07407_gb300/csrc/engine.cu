@@ -25,6 +25,7 @@
 #include "noise.cuh"
 #include "round_steps.cuh"
 #include "sample_tile.cuh"
+#include "dense_dft.cuh"
 
 namespace sfft {
 
@@ -226,7 +227,9 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
         v[SC_MODE] = K;
         v[SC_SAMP0 + r.gsize - 1] = (int64_t)r.n_xt * r.groups * r.splits;
         v[SC_BINS] = r.p;
-        if (!r.big) {
+        if (r.dense) {
+          // the dense tensor-core kernel takes the signal's rows (no Bluestein row or filter)
+        } else if (!r.big) {
           const bool sm = r.L <= (1 << kSmallFftLog);
           v[sm ? SC_ROWS_S : SC_ROWS] = c.n_sets;
           v[sm ? SC_FILT_S : SC_FILT] = r.tab_owner;
@@ -683,8 +686,8 @@ __global__ void k_peel(int n, const SigCfg* __restrict__ cfg, const SigRun* __re
 // ------------------------------------------------------------------ classification and registry merge
 
 // Bins of the round whose set-0 magnitude is above the empty-bin level, appended to the
-// candidate list; also the first round's reference amplitude A_ref and the flag that some bin is
-// occupied (the stop rule reads it).  A block takes a contiguous range of bins and gathers its
+// candidate list; also the first round's reference amplitude A_ref and the flag that some bin of
+// some set is above that level (the stop rule reads it).  A block takes a contiguous range of bins and gathers its
 // candidates in shared memory, with one atomic on the list's counter per kCandBuf of them; a
 // warp whose 32 bins belong to one signal reads that signal's level once.
 constexpr int kCandBuf = 2048;
@@ -717,7 +720,8 @@ __global__ void __launch_bounds__(256) k_occupied(int n, const SigCfg* __restric
     const int s = valid ? find_slot(sc.v[SC_BINS], n, e) : -1;
     const int s0 = __shfl_sync(0xffffffffu, s, 0);
     const bool uni = __all_sync(0xffffffffu, !valid || s == s0);
-    bool occ = false;
+    bool occ = false;     // set 0 above the level: a candidate for the ratio test
+    bool resid = false;   // some set above the level: the residual is not empty
     int64_t h = 0;
     // the signal's level: by lane 0 for the warp when its bins share the signal, else per lane
     T lvl = (T)0;   // squared level in float, the level itself in double
@@ -759,15 +763,27 @@ __global__ void __launch_bounds__(256) k_occupied(int n, const SigCfg* __restric
         if (first) rp->a_ref = a_ref;
         rp->eta_prune = fmax(c.rho * a_ref, 6.0 * c.sigma / sqrt((double)p));
       }
-      const c2<T> y0 = Ybuf[c.Y_off + h];
-      if (sizeof(T) == 4) occ = y0.x * y0.x + y0.y * y0.y > lvl;
-      else occ = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y) > (double)lvl;
+      auto above = [&](const c2<T> y) -> bool {
+        if (sizeof(T) == 4) return y.x * y.x + y.y * y.y > lvl;
+        return sqrt((double)y.x * (double)y.x + (double)y.y * (double)y.y) > (double)lvl;
+      };
+      occ = above(Ybuf[c.Y_off + h]);
+      // The residual is empty only when every set is: two modes w, w' of opposite coefficients
+      // whose difference the line does not see ((w - w') . u = 0 mod p; a read-out that
+      // slipped in a coordinate outside the round's block leaves such a pair in the registry)
+      // cancel in set 0 but not in the set of that coordinate.  Such a bin is no candidate (no
+      // single mode passes the ratio test there), but it keeps the signal's rounds going.
+      // (skipped once the signal is known to be occupied this round)
+      resid = occ;
+      if (!resid && !rp->any_occupied)
+        for (int n = 1; n < c.n_sets && !resid; ++n) resid = above(Ybuf[c.Y_off + (int64_t)n * rp->p + h]);
     }
     // the occupied flag: once per warp for a one-signal warp
     const unsigned mask = __ballot_sync(0xffffffffu, occ);
+    const unsigned rmask = __ballot_sync(0xffffffffu, resid);
     if (uni) {
-      if (lane == 0 && mask != 0u && !run[s0].any_occupied) run[s0].any_occupied = 1;
-    } else if (occ && !run[s].any_occupied) {
+      if (lane == 0 && rmask != 0u && !run[s0].any_occupied) run[s0].any_occupied = 1;
+    } else if (resid && !run[s].any_occupied) {
       run[s].any_occupied = 1;
     }
     // gather: warp offsets by one shared atomic per warp
@@ -847,7 +863,7 @@ __global__ void k_output(int n, const SigCfg* __restrict__ cfg, SigRun* run, con
   if (threadIdx.x == 0) {
     n_found[s] = base_s;
     int st = rp->active ? (int)SFFT_ERR_NOT_CONVERGED : rp->status;
-    if (rp->err) st = SFFT_ERR_CAPACITY;
+    if (rp->err) st = (rp->err & kErrTimeout) ? SFFT_ERR_TIMEOUT : SFFT_ERR_CAPACITY;
     if (st == SFFT_OK && base_s > cap) st = SFFT_ERR_CAPACITY;
     if (st == SFFT_OK && base_s > c.k) st = SFFT_ERR_INCONSISTENT;
     status[s] = st;
@@ -942,6 +958,8 @@ class Engine final : public EngineBase {
       c.tilt_hypo = d.tilt_hypo;
       c.n_sets = d.shift_block ? 1 + (int)d.shift_blocks.size() : d.d + 1;
       c.fuse_L = (sizeof(T) == 4 && d.fuse) ? fused_max_length(c.n_sets) : 0;
+      if (d.fuse_max_len > 0) c.fuse_L = std::min(c.fuse_L, d.fuse_max_len);
+      if (c.fuse_L < 32) c.fuse_L = 0;   // below the shortest Bluestein length: nothing is fused
       c.blk_off = (int64_t)shblk.size();
       if (d.shift_block) {
         int start = 0;
@@ -952,7 +970,10 @@ class Engine final : public EngineBase {
         }
       }
       c.k = (int)d.k;
-      c.c = d.c;
+      c.c8 = d.c8;
+      c.empty_rounds = std::max(1, d.empty_rounds);
+      c.dense_dft = (sizeof(T) == 4 && d.dense_dft) ? 1 : 0;
+      if (c.dense_dft) any_dense_ = true;
       c.max_rounds = d.max_rounds;
       c.n_dirs = d.n_dirs;
       c.n_primes = (int)d.primes.size();
@@ -1032,7 +1053,10 @@ class Engine final : public EngineBase {
     cfg_host_ = cfg;
     Lmax_ = std::max<int64_t>(next_pow2(2 * pmax_all - 1), 32);
     p_max_ = pmax_all;
-    part_cap_ = std::max<int64_t>(part_min, (int64_t)(128ll << 20) / (int64_t)sizeof(C2));
+    // a signal takes at most 64 mode splits (k_plan's S), so 64 part_min holds any split choice;
+    // small engines (one short signal) stay small, large batches stop at 128 MiB
+    part_cap_ = std::max<int64_t>(part_min, std::min<int64_t>((int64_t)(128ll << 20) / (int64_t)sizeof(C2),
+                                                              64 * part_min));
     hash_total_ = hashn;
     // prime table up to the largest p any slot can reach
     std::vector<int32_t> ptab = sieve_primes(pmax_all + 2);
@@ -1060,7 +1084,7 @@ class Engine final : public EngineBase {
       if (!d.primes.empty()) {
         p1 = d.primes[0];
       } else {
-        const int64_t lo = std::max<int64_t>(std::max<int64_t>((int64_t)d.c * std::max<int64_t>(d.k, 1), d.p_min), 2);
+        const int64_t lo = std::max<int64_t>(std::max<int64_t>(prime_floor_ck(d.c8, std::max<int64_t>(d.k, 1)), d.p_min), 2);
         if (lo < (int64_t)pfirst.size() && pfirst[(size_t)lo] < (int32_t)ptab.size()) p1 = ptab[pfirst[(size_t)lo]];
       }
       if (p1 < 2 || p1 > d.p_max || bluestein_length(2 * p1 - 1) > single_max_L<T>()) continue;
@@ -1180,6 +1204,7 @@ class Engine final : public EngineBase {
       smem_fused_ = fused_smem_bytes(fuse_sets_max_, fuse_L_max_);
       ECHK(fused_setup(smem_fused_));
     }
+    if (any_dense_) ECHK(cudaFuncSetAttribute(k_dft_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmem));
     if (profile_) {
       events_.resize((size_t)(SFFT_STATS_MAX_ROUNDS + 4) * 8);
       for (auto& e : events_) ECHK(cudaEventCreate(&e));
@@ -1235,6 +1260,19 @@ class Engine final : public EngineBase {
                                                                          (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 0,
                                                                          (int)smem_dft_);
       ECHK(cudaGetLastError());
+    }
+    return cudaSuccess;
+  }
+
+  // the dense tensor-core DFT of the rounds that take it: a block per 64 bins of each such signal
+  cudaError_t launch_dense() {
+    if constexpr (sizeof(T) == 4) {
+      if (!any_dense_) return cudaSuccess;
+      const int64_t pm = std::min<int64_t>(p_max_, kDenseMaxP);
+      const dim3 grid((unsigned)((pm + kDenseBins - 1) / kDenseBins), (unsigned)n_);
+      k_dft_dense<<<grid, kDenseThreads, kDenseSmem, st_>>>(n_, cfg_, run_, (const float2*)part_, (const float2*)tab_,
+                                                           (float2*)Y_);
+      return cudaGetLastError();
     }
     return cudaSuccess;
   }
@@ -1337,6 +1375,10 @@ class Engine final : public EngineBase {
     ECHK(mark(3));
     ECHK(launch_dft_rows(false));
     launches[3] += small_logL_max_ > kSmallFftLog ? 4 : 2;
+    if (any_dense_) {
+      ECHK(launch_dense());
+      launches[3] += 1;
+    }
     if (any_big_) {
       k_bigA<T><<<4 * n_sm_, 256, smem_bigA_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_, (C2*)twG_,
                                                      Lmax_, (C2*)Z_);
@@ -1666,6 +1708,7 @@ class Engine final : public EngineBase {
     ECHK(cudaMemsetAsync(part_, 0, (size_t)ns * p * sizeof(C2), st_));
     ECHK(cudaMemcpyAsync(part_, y, (size_t)n_rows * p * sizeof(C2), cudaMemcpyDeviceToDevice, st_));
     ECHK(launch_dft_rows());
+    ECHK(launch_dense());
     if (any_big_) {
       k_bigA<T><<<4 * n_sm_, 256, smem_bigA_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_, (C2*)twG_,
                                                      Lmax_, (C2*)Z_);
@@ -1727,6 +1770,7 @@ class Engine final : public EngineBase {
   size_t smem_dft_ = 0;   // the long-row DFT kernel's dynamic shared memory (row + prefetch row)
   int64_t rows_max_ = 0;
   int64_t Lmax_ = 2, p_max_ = 2, part_cap_ = 0, hash_total_ = 0, k_max_ = 0, kd_max_ = 0, reg_cap_max_ = 0;
+  bool any_dense_ = false;   // some slot takes short rounds' DFT on the tensor cores
   std::vector<SigCfg> cfg_host_;
   std::vector<void*> allocs_;
   std::vector<cudaEvent_t> events_;

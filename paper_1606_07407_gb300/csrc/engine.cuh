@@ -26,7 +26,7 @@ __host__ __device__ constexpr int tile_x(int ns) { return 32 * kSampleWarps * ro
 
 // Static description of one signal slot of a batch.
 struct SigCfg {
-  int d, n_sets, k, c, max_rounds, n_dirs, n_primes, box_lo;
+  int d, n_sets, k, c8, max_rounds, n_dirs, n_primes, box_lo;   // c8: the prime factor c in eighths
   int ratio64;        // phase ratio and coefficient in double
   int coef_mean;      // coefficient = mean over the d + 1 sets (else Y_0[h] / p)
   int peel_bins;      // the registry leaves the transform bin by bin (else it is sampled with f)
@@ -35,8 +35,10 @@ struct SigCfg {
   int shift_tilt;     // Alg. 3 (d = 2): set n shifted by (axis n) / Q, Q = (base + height) N, the
   int tilt_base, tilt_height, tilt_hypo;   // axes (base, -height) and (height, base)
   int reg_cap, hash_mask, logL_max;
+  int empty_rounds;   // rounds in a row with no bin of any set occupied that end the recovery
+  int dense_dft;      // rounds of primes up to kDenseMaxP take the tensor-core dense DFT
   int64_t N, p_max;
-  int64_t p_min;      // floor of the prime rule: the i-th prime >= max(c k*, p_min)
+  int64_t p_min;      // floor of the prime rule: the i-th prime >= max(ceil(c k*), p_min)
   double tau, rho, delta, sigma;
   int64_t dirs_off, primes_off;  // into the direction / prime-list arrays
   int64_t blk_off;    // int32 [2 (n_sets - 1)]: start and size of each shift block (block form)
@@ -68,6 +70,7 @@ struct SigRun {
   int logL, big;      // power-of-two Bluestein length of the round (four-step path when big)
   int L;              // Bluestein length of the one-block path: m 2^a >= 2p - 1, m in {1, 3, 5}
   int fused;          // the round runs in the fused short-round kernel (one block for the signal)
+  int dense;          // the round's DFT is the dense tensor-core contraction (k_dft_dense)
   int n_xt, groups, gsize, chunks, jper, splits;
   int mgroups;        // mode groups per sampling tile (warps sharing rows when p is small)
   int reg_start;      // registry entries at the start of the round
@@ -79,7 +82,7 @@ struct SigRun {
   int64_t part_off;
   int64_t tab_at, bhat_at;   // this round's W / chirp table and filter spectrum (shared by equal primes)
   int tab_owner;             // 1: this signal computes them
-  int pad_owner;
+  int empty_streak;   // rounds in a row, up to the last one run, with no bin of any set occupied
   unsigned long long maxy0_bits;
   double a_ref;
   double eta_prune;   // the round's prune level: max(rho A_ref, 6 sigma / sqrt(p))
@@ -111,6 +114,8 @@ struct Scans {
 enum { SC_TAB = 0, SC_MODE, SC_ROWS, SC_FILT, SC_BINS, SC_BIGA, SC_BIGB, SC_BIGC, SC_ROWS_S, SC_FILT_S, SC_SAMP0 };
 
 constexpr int kSmallFftLog = 11;   // Bluestein rows up to 2048 points run in small-memory blocks
+constexpr int kDenseMaxP = 8191;   // longest prime whose DFT the dense tensor-core kernel takes
+constexpr int kErrTimeout = 4;     // SigRun::err bit: a bounded device wait ran out (1, 2: capacity)
 
 struct HistRec {
   int64_t p;
@@ -129,7 +134,7 @@ struct SlotDesc {
   int d;
   int64_t N;
   int64_t k;
-  int c;
+  int c8;                          // prime factor c of the rule p >= c k*, in eighths (40: c = 5)
   int box_lo;
   int ratio64;
   int coef_mean;
@@ -138,6 +143,9 @@ struct SlotDesc {
   int shift_tilt = 0;              // Alg. 3 (d = 2): sets shifted along the rotated axes
   int tilt_base = 0, tilt_height = 0, tilt_hypo = 0;
   int fuse = 1;                    // short rounds may run in the fused kernel
+  int fuse_max_len = 0;            // longest Bluestein length run fused (0: the kernel's limit)
+  int empty_rounds = 1;            // empty rounds in a row that end the recovery
+  int dense_dft = 0;               // short rounds' DFT on the tensor cores (split BF16)
   std::vector<int> shift_blocks;   // block sizes of the shifted sets (block form)
   double tau, rho, delta, sigma;
   int max_rounds;
@@ -147,6 +155,9 @@ struct SlotDesc {
   int64_t p_min = 0;             // floor of the rule
   int64_t p_max;
 };
+
+// ceil(c k) for the prime factor c = c8 / 8, in exact integer arithmetic
+__host__ __device__ inline int64_t prime_floor_ck(int c8, int64_t k) { return ((int64_t)c8 * k + 7) / 8; }
 
 // Engine interface, instantiated for float (FP32 bulk) and double (FP64).
 class EngineBase {

@@ -248,8 +248,9 @@ __device__ __forceinline__ void fused_peel(const SigCfg& c, const SigRun& r, flo
 
 // Residual in the bin domain, set 0 only: every registry entry of the round's start gets its
 // bin h = (w . u) mod p in hreg (-1 when pruned) and takes -p a off Y_0[h].  The other sets are
-// corrected later at the occupied bins only (fused_peel_bins): the empty-bin test reads set 0
-// alone, and the ratio test and read-out read the other sets at occupied bins only.
+// corrected later at the occupied bins only (fused_peel_bins): the candidates come from set 0
+// alone, and the ratio test and read-out read the other sets at occupied bins only (a round
+// without candidates corrects them at every registry entry's bin to test them for the stop rule).
 template <int NS>
 __device__ __forceinline__ void fused_peel_set0(const SigCfg& c, const SigRun& r, float2* Ys, const int64_t* u,
                                                 const int32_t* regw, const double2* rega, int16_t* hreg) {
@@ -459,6 +460,28 @@ __global__ void __launch_bounds__(kSampleThreads, 2) k_fused(FusedArgs a) {
   if (c.peel_bins && lazy && n_cand > 0) {
     fused_peel_bins<NS>(c, r, Ys, occf, a.rega, a.regtw, hreg);
     __syncthreads();
+  }
+  if (NS > 1 && n_cand == 0) {
+    // Set 0 is empty, so the signal would stop; the residual is empty only when the other sets
+    // are too.  Two registry entries of opposite coefficients whose difference this line does
+    // not see cancel in set 0 alone (a read-out that slipped in a coordinate outside the round's
+    // block leaves such a pair).  The other sets' residual differs from f's transform only at
+    // the bins of registry entries: those take their peel first.
+    if (c.peel_bins && lazy) {
+      const int nr = min(r.K_reg, c.reg_cap);
+      for (int j = tid; j < nr; j += blockDim.x)
+        if (hreg[j] >= 0) occf[hreg[j]] = 1;
+      __syncthreads();
+      fused_peel_bins<NS>(c, r, Ys, occf, a.rega, a.regtw, hreg);
+      __syncthreads();
+    }
+    int any = 0;
+    for (int e = tid; e < (NS - 1) * p; e += blockDim.x) {
+      const C2 y = Ys[p + e];
+      any |= y.x * y.x + y.y * y.y > eta * eta ? 1 : 0;
+    }
+    any = __syncthreads_or(any);
+    if (tid == 0 && any) rp->any_occupied = 1;
   }
   fused_classify(c, rp, s, cand, n_cand, Ys, a.ubuf, a.shblk, a.regw, a.rega, a.regtw, a.hash);
   __syncthreads();

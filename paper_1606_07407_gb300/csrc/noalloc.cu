@@ -121,6 +121,9 @@ extern "C" sfft_status sfft_sample_noalloc(int d, int64_t N, int64_t p, const in
   if (d < 1 || d > kNoAllocMaxD || N < 2 || N > (1LL << 23) || p < 2 || p >= (1LL << 22) || K < 0 || !u ||
       !y_out_dev || (K > 0 && (!freqs_dev || !coeffs_dev)) || box_lo > 0 || box_lo < -N)
     return SFFT_ERR_INVALID_ARG;
+  // every mode takes at least 4 bytes of scratch: a K beyond that count cannot fit, and this
+  // check, in 64 bits, comes before K is narrowed to int below
+  if (K > (int64_t)(kNoAllocScratchBytes / sizeof(int32_t))) return SFFT_ERR_CAPACITY;
   NoAllocArgs a;
   memset(&a, 0, sizeof(a));
   a.d = d;

@@ -78,12 +78,19 @@ __device__ void plan_signal(const PlanArgs& a, const SigCfg& c, SigRun& r, const
     hist[r.round - 1].live = r.n_live;
   }
   if (r.active && !a.force) {
-    if (r.round > 0 && !r.any_occupied) {
+    // The residual is empty when c.empty_rounds rounds in a row, on successive line directions,
+    // find no bin of any set above the empty-bin level: a wrong read-out that passed the own-bin
+    // check (wrong outside the round's block, or by a multiple of p inside it) leaves a pair w,
+    // w' that lines not separating them put in one bin, whose shifted sets differ by only about
+    // 2 pi |w_n - w'_n| / N in phase, below the level; a later line of the block where they
+    // differ, with another prime, splits the pair.
+    if (r.round > 0) r.empty_streak = r.any_occupied ? 0 : r.empty_streak + 1;
+    if (r.round > 0 && r.empty_streak >= c.empty_rounds) {
       r.active = 0;                        // the residual is empty: done
       r.status = SFFT_OK;
     } else if (r.err) {
       r.active = 0;
-      r.status = SFFT_ERR_CAPACITY;
+      r.status = (r.err & kErrTimeout) ? SFFT_ERR_TIMEOUT : SFFT_ERR_CAPACITY;
     } else if (r.round >= c.max_rounds || r.round >= a.hard_rounds) {
       r.active = 0;
       r.status = SFFT_ERR_NOT_CONVERGED;
@@ -99,7 +106,7 @@ __device__ void plan_signal(const PlanArgs& a, const SigCfg& c, SigRun& r, const
       p = pt.plist[c.primes_off + (i - 1) % c.n_primes];
     } else {
       const int64_t kstar = max((int64_t)c.k - r.n_live, (int64_t)1);
-      const int64_t lo = max(max((int64_t)c.c * kstar, c.p_min), (int64_t)2);
+      const int64_t lo = max(max(prime_floor_ck(c.c8, kstar), c.p_min), (int64_t)2);
       // pfirst[v] = index of the smallest prime >= v, so the i-th prime >= lo is one lookup away
       const int64_t idx = lo < pt.pfirst_n ? (int64_t)pt.pfirst[lo] + i - 1 : (int64_t)pt.n_ptab;
       p = idx < pt.n_ptab ? pt.ptab[idx] : -1;
@@ -127,6 +134,8 @@ __device__ void plan_signal(const PlanArgs& a, const SigCfg& c, SigRun& r, const
       // fused rounds: short lines, and 2p < L (true of every prime) so that the half line of
       // a fused round has at most L / 4 positions
       r.fused = a.fuse && !r.big && r.L <= c.fuse_L && 2 * p < r.L;
+      r.dense = c.dense_dft && p <= kDenseMaxP && sizeof(T) == 4;
+      if (r.dense) r.fused = 0;
       r.groups = (c.n_sets + kMaxSetGroup - 1) / kMaxSetGroup;
       r.gsize = (c.n_sets + r.groups - 1) / r.groups;
       {

@@ -15,7 +15,7 @@ import torch
 
 from . import build as _build
 
-PREC = {"fp32": 0, "auto": 0, "fp32_fp64ratio": 1, "fp32_only": 2, "fp64": 3}
+PREC = {"fp32": 0, "auto": 0, "fp32_fp64ratio": 1, "fp32_only": 2, "fp64": 3, "fp32_bf16dft": 4}
 STATUS = {0: "ok", 1: "invalid argument", 2: "not converged", 3: "capacity exceeded",
           4: "beyond phase resolution", 5: "more modes than k", 6: "cuda error", 7: "device wait timed out"}
 MAX_ROUNDS = 256
@@ -31,7 +31,16 @@ class SfftError(RuntimeError):
 
 class _PSchedule(C.Structure):
     _fields_ = [("c_prime", C.c_int), ("n_primes", C.c_int), ("primes", C.POINTER(C.c_int64)),
-                ("p_min", C.c_int64)]
+                ("p_min", C.c_int64), ("c_eighths", C.c_int)]
+
+
+def prime_factor_eighths(c) -> int:
+    """The prime factor c of the rule p >= c k* in eighths (the ABI's c_eighths); c must be a
+    multiple of 1/8 in [1/8, 4096] so that ceil(c k*) is exact on every side."""
+    c8 = round(float(c) * 8)
+    if abs(float(c) * 8 - c8) > 1e-9 or not 1 <= c8 <= 8 * 4096:
+        raise ValueError(f"prime factor c = {c} is not a multiple of 1/8 in [1/8, 4096]")
+    return int(c8)
 
 
 class _Tilts(C.Structure):
@@ -52,7 +61,8 @@ class _Opts(C.Structure):
                 ("delta", C.c_double), ("noise_sigma", C.c_double), ("max_rounds", C.c_int),
                 ("profile", C.c_int), ("graph", C.c_int), ("coef_set0", C.c_int), ("residual", C.c_int),
                 ("shift", C.c_int), ("unfused", C.c_int),
-                ("tilt_base", C.c_int), ("tilt_height", C.c_int), ("tilt_hypo", C.c_int)]
+                ("tilt_base", C.c_int), ("tilt_height", C.c_int), ("tilt_hypo", C.c_int),
+                ("fuse_max_len", C.c_int), ("empty_rounds", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -203,11 +213,12 @@ def assign_many(signals, freqs: torch.Tensor, coeffs: torch.Tensor, ks, stream=N
 class Plan:
     """An sfft plan: d, N, k, prime schedule, line directions and precision policy."""
 
-    def __init__(self, d: int, N: int, k: int, blocks=None, dirs=None, primes=None, c: int = 5,
+    def __init__(self, d: int, N: int, k: int, blocks=None, dirs=None, primes=None, c: float = 5,
                  precision: str = "fp32", box_lo: int = 0, tau: float = 0.0, rho: float = 0.0,
                  delta: float = 0.0, noise_sigma: float = 0.0, max_rounds: int = 0, stream=None,
                  profile: bool = False, graph: bool = False, coef: str = "mean", residual: str = "bins",
-                 p_min: int = 0, shift: str = "coord", fuse: bool = True, tilt=None):
+                 p_min: int = 0, shift: str = "coord", fuse: bool = True, tilt=None, fuse_max_len: int = 0,
+                 empty_rounds: int = 0):
         L = load()
         if residual not in RESIDUAL:
             raise ValueError(f"residual must be one of {sorted(RESIDUAL)}")
@@ -215,7 +226,7 @@ class Plan:
         self.precision = precision
         self.cdtype = torch.complex128 if precision == "fp64" else torch.complex64
         self._keep = []
-        ps = _PSchedule(int(c), 0, None, int(p_min))
+        ps = _PSchedule(0, 0, None, int(p_min), prime_factor_eighths(c))
         if primes is not None and len(primes):
             arr = _i64_array(primes)
             self._keep.append(arr)
@@ -233,6 +244,8 @@ class Plan:
         op = _Opts(PREC[precision], int(box_lo), float(tau), float(rho), float(delta), float(noise_sigma),
                    int(max_rounds), 1 if profile else 0, 1 if graph else 0, 1 if coef == "set0" else 0,
                    RESIDUAL[residual], SHIFT[shift], 0 if fuse else 1)
+        op.fuse_max_len = int(fuse_max_len)
+        op.empty_rounds = int(empty_rounds)
         if tilt is not None:   # (base, height, hypo) of the tilted form
             op.tilt_base, op.tilt_height, op.tilt_hypo = (int(v) for v in tilt)
         if stream is None:
@@ -279,6 +292,9 @@ class Plan:
         return fo[:m], co[:m], status, _stats_dict(st)
 
     def sample(self, p: int, u, freqs: torch.Tensor, coeffs: torch.Tensor) -> torch.Tensor:
+        check_mode_arrays(self.d, torch.as_tensor(freqs), torch.as_tensor(coeffs))
+        if len(u) != self.d:
+            raise ValueError(f"u must have {self.d} entries")
         L = load()
         fw = freqs.to(device="cuda", dtype=torch.int32).contiguous()
         ca = coeffs.to(device="cuda", dtype=torch.complex128).contiguous()
@@ -288,6 +304,8 @@ class Plan:
         return y
 
     def dft(self, p: int, y: torch.Tensor) -> torch.Tensor:
+        if y.dim() != 2 or int(y.shape[1]) != int(p) or not 1 <= int(y.shape[0]) <= self.n_sets:
+            raise ValueError(f"y must be [rows <= {self.n_sets}, {int(p)}], got {tuple(y.shape)}")
         L = load()
         y = y.to(device="cuda", dtype=self.cdtype).contiguous()
         Y = torch.empty_like(y)
@@ -295,6 +313,8 @@ class Plan:
         return Y
 
     def classify(self, p: int, u, Y: torch.Tensor, eta_bin: float, capacity: int | None = None):
+        if tuple(Y.shape) != (self.n_sets, int(p)) or len(u) != self.d:
+            raise ValueError(f"Y must be [{self.n_sets}, {int(p)}] and u of {self.d} entries")
         L = load()
         Y = Y.to(device="cuda", dtype=self.cdtype).contiguous()
         cap = int(capacity if capacity is not None else p)
@@ -309,10 +329,35 @@ class Plan:
         return h[:m], w[:m], a[:m]
 
 
+def check_mode_arrays(d: int, freqs, coeffs) -> int:
+    """Raises ValueError unless freqs is [K, d] and coeffs holds K entries; returns K.  The
+    kernels read K d frequencies and K coefficients, so a mismatch would read out of bounds."""
+    if freqs.dim() != 2 or int(freqs.shape[1]) != int(d):
+        raise ValueError(f"freqs must be [K, {d}], got {tuple(freqs.shape)}")
+    if coeffs.dim() != 1 or int(coeffs.shape[0]) != int(freqs.shape[0]):
+        raise ValueError(f"coeffs must hold {int(freqs.shape[0])} entries, got {tuple(coeffs.shape)}")
+    return int(freqs.shape[0])
+
+
+def check_samples_out(out, d: int, p: int, dtype) -> None:
+    """Raises ValueError unless `out` is a contiguous [d + 1, p] tensor of `dtype` (the kernel
+    writes (d + 1) p samples)."""
+    if out.dtype != dtype or tuple(out.shape) != (int(d) + 1, int(p)) or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous {dtype} tensor of shape ({int(d) + 1}, {int(p)}), "
+                         f"got {out.dtype} {tuple(out.shape)}")
+
+
 def sample_noalloc(d: int, N: int, p: int, u, freqs: torch.Tensor, coeffs: torch.Tensor, box_lo: int = 0,
                    stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
     """Samples of kernel (a) through the allocation-free entry point (the library allocates
-    nothing; `out`, if given, receives the complex64 [d+1, p] samples).  Waits for the stream."""
+    nothing; `out`, if given, receives the complex64 [d+1, p] samples).  Shapes and dtypes are
+    checked before any device call.  Waits for the stream."""
+    freqs, coeffs = torch.as_tensor(freqs), torch.as_tensor(coeffs)
+    check_mode_arrays(d, freqs, coeffs)
+    if out is not None:
+        check_samples_out(out, d, p, torch.complex64)
+    if len(u) != int(d):
+        raise ValueError(f"u must have {d} entries")
     L = load()
     fw = freqs.to(device="cuda", dtype=torch.int32).contiguous()
     ca = coeffs.to(device="cuda", dtype=torch.complex128).contiguous()
@@ -338,7 +383,7 @@ def _stats_dict(st: _Stats) -> dict:
 class Batch:
     """Many independent signals recovered together: every kernel launch serves all slots."""
 
-    def __init__(self, plans, stream=None, graph: bool = False):
+    def __init__(self, plans, stream=None, graph: bool = False, profile: bool = False):
         L = load()
         self.plans = list(plans)
         self.n = len(self.plans)
@@ -347,7 +392,8 @@ class Batch:
             stream = torch.cuda.current_stream()
         self.stream = stream
         h = C.c_void_p()
-        _check(L.sfft_batch_create(self.n, arr, C.c_void_p(stream.cuda_stream), 1 if graph else 0, C.byref(h)),
+        flags = (1 if graph else 0) | (2 if profile else 0)
+        _check(L.sfft_batch_create(self.n, arr, C.c_void_p(stream.cuda_stream), flags, C.byref(h)),
                "sfft_batch_create")
         self._h = h
         self.d = [p.d for p in self.plans]

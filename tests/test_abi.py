@@ -137,3 +137,40 @@ def test_batch_results_slice_each_signal_from_the_flat_outputs():
     assert [f.shape[0] for f, _ in res] == [3, 2, 0] and len(res[1:]) == 2
     with pytest.raises(IndexError):
         res[3]
+
+
+def test_sampling_wrappers_reject_bad_shapes_before_any_device_call(monkeypatch):
+    # the kernels read K d frequencies and K coefficients and write (d + 1) p samples: a tensor
+    # of another shape or dtype would be read or written out of bounds, so the binding refuses it
+    # before it loads the library or touches the device
+    torch = pytest.importorskip("torch")
+    from paper_1606_07407_gb300 import sfft as S
+
+    def no_device(*_a, **_k):
+        raise AssertionError("reached the library")
+
+    monkeypatch.setattr(S, "load", no_device)
+    w = torch.zeros((10, 3), dtype=torch.int32)
+    a = torch.zeros((10,), dtype=torch.complex128)
+    u = [1, 0, 0]
+    with pytest.raises(ValueError):
+        S.sample_noalloc(4, 64, 11, [1, 0, 0, 0], w, a)                  # freqs not [K, d]
+    with pytest.raises(ValueError):
+        S.sample_noalloc(3, 64, 11, u, w, a[:5])                         # K coefficients expected
+    with pytest.raises(ValueError):
+        S.sample_noalloc(3, 64, 11, u, w.reshape(-1), a)                 # freqs not two-dimensional
+    with pytest.raises(ValueError):
+        S.sample_noalloc(3, 64, 11, u, w, a, out=torch.empty((4, 10), dtype=torch.complex64))   # too short
+    with pytest.raises(ValueError):
+        S.sample_noalloc(3, 64, 11, u, w, a, out=torch.empty((3, 11), dtype=torch.complex64))   # too few sets
+    with pytest.raises(ValueError):
+        S.sample_noalloc(3, 64, 11, u, w, a, out=torch.empty((4, 11), dtype=torch.complex128))  # wrong dtype
+    with pytest.raises(ValueError):
+        S.sample_noalloc(3, 64, 11, [1, 0], w, a)                        # direction of d entries
+    # the plan-based step wrappers check the same things before their calls
+    plan = S.Plan.__new__(S.Plan)
+    plan.d = 3
+    with pytest.raises(ValueError):
+        plan.sample(11, u, torch.zeros((10, 2), dtype=torch.int32), a)
+    with pytest.raises(ValueError):
+        plan.sample(11, u, w, a[:3])

@@ -19,6 +19,9 @@ pytestmark = pytest.mark.gpu
 
 FP32_COEFF_TOL = 1e-5
 FP64_COEFF_TOL = 1e-12
+# the FP64 policy ends a recovery after one empty round (its read-outs do not slip); the float
+# policies after one per line direction (the oracle's default)
+FP64_EMPTY_ROUNDS = 1
 
 
 @pytest.fixture(scope="module")
@@ -240,6 +243,7 @@ def _run_both(sfft, sig, blocks=None, prec="fp32", dirs=None, primes=None, box_l
     gf, ga = sfft.sort_result(_np(f), _np(a))
     th = O.Thresholds() if prec == "fp64" else O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
     ref = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, blocks, th=th, dirs=dirs,
+                             empty_rounds=FP64_EMPTY_ROUNDS if prec == "fp64" else None,
                              primes=primes, box_lo=box_lo, estimator="mean", residual=residual)
     return gf, ga, status, stats, ref
 
@@ -365,10 +369,12 @@ def test_fig2_collision_story_on_gpu(sfft):
 # ------------------------------------------------------------------ edge cases
 
 def test_empty_signal(sfft):
-    plan = sfft.Plan(3, 1024, 10, blocks=(2, 1))
+    # nothing to find: one empty round per line direction (two blocks) under the float policy,
+    # one under FP64
     s = sfft.Signal(np.zeros((0, 3), np.int32), np.zeros(0, np.complex128), 1024)
-    f, a, status, stats = plan.execute(s)
-    assert status == 0 and f.shape[0] == 0 and stats["rounds"] == 1
+    for prec, rounds in (("fp32", 2), ("fp64", 1)):
+        f, a, status, stats = sfft.Plan(3, 1024, 10, blocks=(2, 1), precision=prec).execute(s)
+        assert status == 0 and f.shape[0] == 0 and stats["rounds"] == rounds
 
 
 def test_single_mode(sfft):
@@ -585,7 +591,7 @@ def test_block_shift_recovery_matches_oracle(sfft, case):
     gf, ga = sfft.sort_result(_np(f), _np(a))
     th = O.Thresholds() if prec == "fp64" else O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
     ref = O.multi_phaseshift(sig.freqs, sig.coeffs, d, N, k, blocks, th=th, box_lo=box, estimator="mean",
-                             residual="bins", shift="block")
+                             residual="bins", shift="block", empty_rounds=FP64_EMPTY_ROUNDS if prec == "fp64" else None)
     _assert_parity(sig, gf, ga, status, stats, ref, FP64_COEFF_TOL if prec == "fp64" else FP32_COEFF_TOL)
     assert stats["samples"] == sum(r["samples"] for r in ref.rounds)
 
@@ -626,7 +632,8 @@ def test_tilt_recovery_matches_oracle(sfft, case):
     gf, ga = sfft.sort_result(_np(f), _np(a))
     th = O.Thresholds() if prec == "fp64" else O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
     ref = O.multi_phaseshift(sig.freqs, sig.coeffs, 2, N, k, th=th, box_lo=box, estimator="mean",
-                             residual=residual, shift="tilt", tilt=tilt)
+                             residual=residual, shift="tilt", tilt=tilt,
+                             empty_rounds=FP64_EMPTY_ROUNDS if prec == "fp64" else None)
     _assert_parity(sig, gf, ga, status, stats, ref, FP64_COEFF_TOL if prec == "fp64" else FP32_COEFF_TOL)
     assert stats["samples"] == sum(r["samples"] for r in ref.rounds)
 
@@ -750,3 +757,189 @@ def test_precision_stress_d20_fp64_recovers_every_mode(sfft):
     order = np.lexsort(sig.freqs.T[::-1])
     assert status == 0 and np.array_equal(gf, sig.freqs[order])
     assert np.max(np.abs(ga - sig.coeffs[order]) / np.abs(sig.coeffs[order])) < 1e-9
+
+
+# ------------------------------------------------------------------ stop rule over every set
+
+@pytest.mark.parametrize("fuse", [True, False])
+def test_stop_rule_reads_every_set(sfft, fuse):
+    # a pair of opposite modes that lines along e_2 cannot separate: unconverged, not a wrong
+    # set reported as converged (fused short rounds and batched kernels alike)
+    from test_oracle_pins import _check_stop_rule
+
+    def recover(w, a, N, dirs, max_rounds):
+        plan = sfft.Plan(2, N, len(w), blocks=(1, 1), dirs=dirs, max_rounds=max_rounds, fuse=fuse)
+        f, c, status, stats = plan.execute(sfft.Signal(w, a, N), allow=(0, 2))
+        gf, ga = sfft.sort_result(_np(f), _np(c))
+        assert (status == 0) == stats["converged"]
+        return status == 0, gf, ga
+
+    fa, ref = _check_stop_rule(recover)
+    assert np.max(np.abs(fa - ref) / np.abs(ref)) < FP32_COEFF_TOL
+
+
+# ------------------------------------------------------------------ the batched mix of independent signals
+
+def _mix_slots_to_check(mix, n_check):
+    """Slots spread over the mix's classes: the largest d, the largest N, the largest k, the
+    smallest k (short lines, fused rounds), then evenly spaced others."""
+    idx = [max(range(len(mix)), key=lambda i: (mix[i][0].d, mix[i][0].k)),
+           max(range(len(mix)), key=lambda i: (mix[i][0].N, mix[i][0].k)),
+           max(range(len(mix)), key=lambda i: mix[i][0].k),
+           min(range(len(mix)), key=lambda i: mix[i][0].k)]
+    step = max(1, len(mix) // max(1, n_check - len(idx)))
+    for i in range(0, len(mix), step):
+        if len(set(idx)) >= n_check:
+            break
+        idx.append(i)
+    return sorted(set(idx))
+
+
+def test_batched_mix_over_the_full_ranges_matches_oracle(sfft):
+    # 256 signals with k ~ U{8..512}, d ~ U{2..8} (nine-set slots beside fused ones),
+    # N = 2^U{10..20} (the double read-out above 2^14 beside the float one), each with the tuned
+    # schedule of its class, one graph launch: every slot's set equals the planted one; sampled
+    # slots equal the oracle's set (same schedule), with coefficients within the float tolerance
+    from paper_1606_07407_gb300 import tuning
+    from paper_1606_07407_gb300.inputs import BASE_SEED, batched_mix
+    mix = batched_mix(256, seed=BASE_SEED + 4 + 77)
+    assert {s.d for s, _ in mix} == set(range(2, 9))
+    assert min(s.N for s, _ in mix) == 1 << 10 and max(s.N for s, _ in mix) == 1 << 20
+    sched = [tuning.schedule(s.d, s.N, s.k) for s, _ in mix]
+    plans = [sfft.Plan(s.d, s.N, s.k, blocks=b, c=sc["c"], p_min=sc["p_min"], fuse_max_len=sc["fuse_max_len"])
+             for (s, b), sc in zip(mix, sched)]
+    res, sts, stats = sfft.Batch(plans, graph=True).execute([sfft.Signal(s.freqs, s.coeffs, s.N) for s, _ in mix])
+    assert sts == [0] * len(mix)
+    got = []
+    for (sig, _), (f, a) in zip(mix, res):
+        gf, ga = sfft.sort_result(_np(f), _np(a))
+        assert np.array_equal(gf, sig.freqs[np.lexsort(sig.freqs.T[::-1])].astype(np.int64))
+        got.append((gf, ga))
+    th = O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
+    for i in _mix_slots_to_check(mix, 10):
+        sig, blocks = mix[i]
+        ref = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, blocks, th=th, estimator="mean",
+                                 residual="bins", c=sched[i]["c"], p_min=sched[i]["p_min"])
+        assert ref.converged and np.array_equal(got[i][0], ref.freqs), i
+        assert np.max(np.abs(got[i][1] - ref.coeffs) / np.abs(ref.coeffs)) < FP32_COEFF_TOL, i
+
+
+def test_paper_estimator_at_the_d5_workload_size(sfft):
+    # a = Y_0[h] / p exactly as printed in Eq. 41 on the d = 5, N = 1024, k = 1000 workload,
+    # against the oracle with the same estimator: the same set and primes
+    wl = WORKLOADS["d5_N1024_k1000"]
+    sig = wl.signal(seed_offset=11)
+    plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=wl.blocks, coef="set0")
+    f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N))
+    gf, ga = sfft.sort_result(_np(f), _np(a))
+    ref = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, wl.blocks,
+                             th=O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25), estimator="set0",
+                             residual="bins")
+    planted = sig.freqs[np.lexsort(sig.freqs.T[::-1])].astype(np.int64)
+    assert status == 0 and ref.converged
+    assert np.array_equal(gf, ref.freqs) and np.array_equal(gf, planted)
+    rel = np.abs(ga - ref.coeffs) / np.abs(ref.coeffs)
+    print(f"Eq. 41 estimator at d = 5, k = 1000: max rel err {rel.max():.3e}, median {np.median(rel):.3e}")
+    # one set's bin carries its own float rounding; the default estimator averages the d + 1 sets'
+    # independent roundings (within 1e-5), so the one-set estimate is held to sqrt(d + 1) times that
+    # (measured: max 1.1e-5, median 2.2e-7)
+    assert rel.max() < FP32_COEFF_TOL * math.sqrt(sig.d + 1)
+
+
+@pytest.mark.parametrize("fuse", [True, False])
+def test_stop_rule_waits_for_every_line_direction(sfft, fuse):
+    # a +-1 pair one unit apart at N = 2^20 that only the third block's line separates: the float
+    # policy recovers all three modes (fused short rounds and batched kernels alike)
+    from test_oracle_pins import _check_every_direction_stop
+
+    def recover(w, a, N):
+        plan = sfft.Plan(3, N, len(w), blocks=(1, 1, 1), fuse=fuse)
+        f, c, status, stats = plan.execute(sfft.Signal(w, a, N), allow=(0, 2))
+        gf, ga = sfft.sort_result(_np(f), _np(c))
+        return status == 0, gf, ga
+
+    fa, ref = _check_every_direction_stop(recover)
+    assert np.max(np.abs(fa - ref) / np.abs(ref)) < FP32_COEFF_TOL
+
+
+# ------------------------------------------------------------------ dense split-BF16 tensor-core DFT
+
+DENSE_FLUSH = 4      # K tiles (32 samples each) per tensor-memory accumulation segment
+
+
+def _split_bf16_dft_tol(p, y, Y=None):
+    # Each operand is split into two BF16 terms, hi = bf16(v) and lo = bf16(v - hi): 8 significant
+    # bits each, so v - hi - lo is below 2^-16 |v| (two round-to-nearest steps of 2^-8), and the
+    # dropped lo_A lo_B is below 2^-16 |A| |B|.  Each of the 2p real products of a bin carries
+    # about 3 2^-16 |A| |B| with |A| <= 1, and these add like a random walk: six standard
+    # deviations of it per row.  The tensor core rounds each MMA's sum into its FP32 accumulator
+    # (12 MMAs per tile, up to 2^-23 of the partial sum each); where the products add coherently
+    # those roundings add up, so the kernel drains the accumulator into registers every
+    # DENSE_FLUSH tiles: at most 12 DENSE_FLUSH 2^-23 |Y| from the segments, plus a 2^-24 |Y| per
+    # register addition (one per segment).
+    rms = np.sqrt(np.mean(np.abs(y) ** 2, axis=1, keepdims=True))
+    walk = 6.0 * 3 * 2.0 ** -16 * math.sqrt(2 * p) * rms
+    seg = 12 * DENSE_FLUSH * 2.0 ** -23 + math.ceil(p / (32 * DENSE_FLUSH)) * 2.0 ** -24
+    mag = np.abs(Y) if Y is not None else 0.0
+    return walk + seg * (mag + 6.0 * math.sqrt(64 * DENSE_FLUSH) * rms)
+
+
+@pytest.mark.parametrize("p", [2, 5, 83, 911, 2039, 4099, 8191])
+def test_dense_bf16_dft_matches_definition(sfft, p):
+    # kernel (b) on the tensor cores (tcgen05, split BF16, FP32 accumulate) for primes up to 8191,
+    # against the DFT by its definition (Eq. 3) in FP64, every bin of every set
+    d = 5
+    plan = sfft.Plan(d, 1024, 2000, precision="fp32_bf16dft")
+    rng = np.random.default_rng(p)
+    y = (rng.standard_normal((d + 1, p)) + 1j * rng.standard_normal((d + 1, p))) * np.array([[1.0], [0.5], [2], [1],
+                                                                                              [3], [0.25]])
+    Y = _np(plan.dft(p, torch.tensor(y.astype(np.complex64), device="cuda")))
+    ref = O.dft(y.astype(np.complex64).astype(np.complex128))
+    err = np.abs(Y - ref)
+    assert np.all(err <= _split_bf16_dft_tol(p, y, ref)), float(err.max())
+    # and the error is split-BF16 sized, not plain BF16 (8 bits: about 2^-8 of each product)
+    rms = np.sqrt(np.mean(np.abs(y) ** 2))
+    if p >= 83:
+        assert err.max() < 2.0 ** -11 * math.sqrt(2 * p) * rms
+
+
+def test_dense_bf16_dft_single_mode_closed_form(sfft):
+    # one mode: Y_0 is p a at bin (w . u) mod p and zero elsewhere, to the split-BF16 error
+    d, N, p = 3, 4096, 4099
+    w = np.array([[1234, 77, 3000]], np.int32)
+    a = np.array([1.5 - 0.5j])
+    plan = sfft.Plan(d, N, 1000, precision="fp32_bf16dft", blocks=(3,))   # primes up to about 5000
+    u = [int(v) for v in O.unwrap_vector(d, N, (3,), 0)]
+    y = plan.sample(p, u, torch.tensor(w, device="cuda"), torch.tensor(a, device="cuda"))
+    Y = _np(plan.dft(p, y))
+    h = int(sum(int(x) * int(v) for x, v in zip(w[0], u)) % p)
+    yc = _np(y).astype(np.complex128)
+    peak = np.zeros((1, p))
+    peak[0, h] = p * abs(a[0])
+    tol = _split_bf16_dft_tol(p, yc[:1], peak)
+    assert abs(Y[0, h] - p * a[0]) <= tol[0, h]
+    Y[0, h] = 0
+    assert np.all(np.abs(Y[0]) <= tol[0])
+
+
+def test_recovery_with_the_dense_bf16_dft_matches_oracle(sfft):
+    # the d = 5, N = 1024, k = 1000 workload with every round's DFT on the tensor cores (its primes
+    # are all below 8191): the same set as the oracle; the coefficients carry the split-BF16 DFT's
+    # error, about 3 2^-16 sqrt(2 / p) |y|_rms / |a| relative, reported here
+    wl = WORKLOADS["d5_N1024_k1000"]
+    sig = wl.signal(seed_offset=21)
+    plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=wl.blocks, precision="fp32_bf16dft")
+    f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N))
+    gf, ga = sfft.sort_result(_np(f), _np(a))
+    ref = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, wl.blocks,
+                             th=O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25), estimator="mean",
+                             residual="bins")
+    planted = sig.freqs[np.lexsort(sig.freqs.T[::-1])].astype(np.int64)
+    assert status == 0 and np.array_equal(gf, ref.freqs) and np.array_equal(gf, planted)
+    assert stats["launches"]["fused"] == 0 and all(p <= 8191 for p in stats["p"])
+    rel = np.abs(ga - ref.coeffs) / np.abs(ref.coeffs)
+    yrms = math.sqrt(float(np.sum(np.abs(sig.coeffs) ** 2)))
+    bound = (6 * 3 * 2.0 ** -16 * math.sqrt(2.0 / min(stats["p"])) * yrms
+             + (12 * DENSE_FLUSH * 2.0 ** -23) * np.abs(ref.coeffs)) / np.abs(ref.coeffs)
+    print(f"split-BF16 DFT recovery: max rel coefficient error {rel.max():.3e}, median {np.median(rel):.3e}")
+    assert np.all(rel < bound)

@@ -473,6 +473,36 @@ def test_stop_rule_reads_every_set():
     assert np.max(np.abs(fa - ref)) < 1e-12
 
 
+SLIP_W = np.array([[100, 200, 300], [101, 200, 300], [5000, 6000, 7000]], dtype=np.int64)
+SLIP_A = np.array([1.0 + 0.0j, -1.0 + 0.0j, 2.0 + 0.0j])
+SLIP_N = 1 << 20
+FLOAT_TH = dict(tau=1e-3, rho=2.0 ** -17, delta=0.25)
+
+
+def _check_every_direction_stop(recover):
+    # Modes 0 and 1 (+1 and -1) differ by one unit in coordinate 1 of N = 2^20: lines along e_2
+    # and e_3 (rounds 1 and 2 with three blocks of one coordinate) put them in one bin, where
+    # set 0 cancels and the shifted set of coordinate 1 holds only p |e^{2 pi i 100/N} -
+    # e^{2 pi i 101/N}| = p 2 pi / N, below the float policies' empty-bin level (2^-17 of the
+    # largest first-round bin, here mode 2's).  Round 2 finds no occupied bin of any set; only the
+    # line along e_1 (round 3) separates the pair.  Every direction must come up empty before
+    # the run stops.
+    conv, fw, fa = recover(SLIP_W, SLIP_A, SLIP_N)
+    order = np.lexsort(SLIP_W.T[::-1])
+    assert conv and np.array_equal(fw, SLIP_W[order])
+    return fa, SLIP_A[order]
+
+
+def test_stop_rule_waits_for_every_line_direction():
+    def recover(w, a, N):
+        res = O.multi_phaseshift(w, a, 3, N, len(w), (1, 1, 1), th=O.Thresholds(**FLOAT_TH), residual="bins")
+        assert [list(O.line_direction(3, N, (1, 1, 1), i)) for i in (1, 2, 3)] == [[0, 1, 0], [0, 0, 1], [1, 0, 0]]
+        assert res.rounds[1]["accepted"] == 0 and res.rounds[2]["accepted"] == 2
+        return res.converged, res.freqs, res.coeffs
+    fa, ref = _check_every_direction_stop(recover)
+    assert np.max(np.abs(fa - ref)) < 1e-12
+
+
 def test_prime_rule_with_a_fractional_factor():
     # c = 5/2 and c = 3/8: round i takes the i-th prime at or above ceil(c k*), found by a sieve
     pr = _sieve(6000)
