@@ -93,10 +93,11 @@ class Job:
         from paper_1606_07407_gb300 import tuning
         self.name = name
         if name == MIX:
+            from paper_1606_07407_gb300.inputs import blocks_for
             mix = batched_mix(MIX_SIGNALS, seed=BASE_SEED + 4 + 1000 * rank)
             self.sigs = [s for s, _ in mix]
-            self.blocks = [b for _, b in mix]
             self.sched = [tuning.schedule(s.d, s.N, s.k) for s in self.sigs]
+            self.blocks = [blocks_for(s.d, s.N, s.k, sc["blocks"]) for s, sc in zip(self.sigs, self.sched)]
             self.homogeneous = False
             self.noise = 0.0
             self.table_sha = tuning.table_sha256()
@@ -123,8 +124,10 @@ class Job:
         pm = sorted({sc["p_min"] for sc in self.sched})
         return {"workload": self.name, "signals_per_step": len(self.sigs), "modes_per_step": self.modes,
                 "k": [min(self.ks), max(self.ks)], "d": [min(ds), max(ds)], "N": [min(ns), max(ns)],
-                "r": [1.0, 10.0], "blocks": "default rule per signal (smallest b with N^b >= 4 c k)",
-                "schedule": f"per (N, k) class from the tuned table: prime factor c in {cs}, prime floor in {pm}",
+                "r": [1.0, 10.0],
+                "schedule": f"per (N, k) class from the tuned table: prime factor c in {cs}, prime floor in {pm}, "
+                            f"block rules {sorted({sc['blocks'] for sc in self.sched})} (narrow: the smallest b with "
+                            f"N^b >= 4 c k; wide: the largest b with N^(b-1) in int64)",
                 "tuned_table_sha256": self.table_sha}
 
     def make_plans(self, sfft, precision, residual, stream, graph=True):
@@ -162,8 +165,10 @@ def oracle_throughput(workload: str, min_seconds: float, max_recoveries: int, se
     n, modes, t_total, exact = 0, 0, 0.0, True
     while n < max_recoveries and (t_total < min_seconds or n == 0):
         if workload == MIX:
-            sig, blocks = mix[(seed_base + n) % MIX_SIGNALS]
+            from paper_1606_07407_gb300.inputs import blocks_for
+            sig, _ = mix[(seed_base + n) % MIX_SIGNALS]
             sched = tuning.schedule(sig.d, sig.N, sig.k)
+            blocks = blocks_for(sig.d, sig.N, sig.k, sched["blocks"])
         else:
             wl = WORKLOADS[workload]
             sig, blocks, sched = (wl.signal(seed_offset=seed_base + n), wl.blocks,
@@ -322,7 +327,9 @@ def _precision_name(prec: str) -> str:
     return {"fp32": "AUTO: float sampling and DFT; phase ratio, read-out and coefficient in double above N = 2^14",
             "fp32_fp64ratio": "float sampling and DFT; phase ratio, read-out and coefficient in double",
             "fp32_only": "every step in float",
-            "fp64": "every step in double"}[prec]
+            "fp64": "every step in double",
+            "fp32_bf16dft": "as AUTO, with the DFT of rounds of p <= 8191 a split-BF16 tensor-core contraction "
+                            "(FP32 accumulate)"}[prec]
 
 
 def run_ours(args):
@@ -616,7 +623,8 @@ def main(argv=None):
     ap.add_argument("--form", default="batched", choices=["batched", "plain"])
     ap.add_argument("--other-steps", type=int, default=1)
     ap.add_argument("--profile-steps", type=int, default=2)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_fp64ratio", "fp32_only", "fp64"],
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_fp64ratio", "fp32_only", "fp64",
+                                                           "fp32_bf16dft"],
                     help="fp32: AUTO (ratio in double above N = 2^14); fp32_fp64ratio: ratio always in double")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -1,15 +1,20 @@
-"""Autotuner of the prime schedule and the fused cut-over per signal class (runs on the GPU).
+"""Autotuner of the prime schedule, the unwrapping blocks and the fused cut-over per signal class
+(runs on the GPU).
 
 A batch of independent signals runs its rounds in lockstep: a round costs the launches of every
 kernel class plus the work of the signals still active, and the batch ends with its slowest
-signal.  Three per-signal choices shape that:
+signal.  Four per-signal choices shape that:
   - the prime factor c of Alg. 2's rule p = i-th prime >= c k* (the paper uses c = 5): fewer
     samples per round against more collisions and so more rounds;
   - a floor p_min on the prime: late rounds (k* small) would otherwise use short lines whose
     bins p |a| are small against the float rounding of the samples, so read-outs at large N
     miss delta for several rounds in a row, or slip to a neighbouring integer;
   - the longest Bluestein length run by the fused kernel (one block per signal runs the whole
-    round) instead of the batched kernels.
+    round) instead of the batched kernels;
+  - the width of the partial unwrapping's blocks (Sec. 4.1): the narrowest that spans 4 c k
+    values, or the widest whose direction fits an int64.  Fewer, wider blocks mean fewer line
+    directions, so fewer empty rounds before the stop rule ends a signal, and fewer modes that
+    share a projected value; with one shifted set per coordinate they cost no precision.
 For each class of (N, k), over the batched workload's dimension range, the tuner draws a
 training and a validation batch, times every candidate on the training batch (CUDA events,
 median of three executes after a warm-up, one CUDA-graph launch each) and keeps the fastest
@@ -31,15 +36,16 @@ import time
 
 import numpy as np
 
-from .inputs import BASE_SEED, Stream, default_blocks, draw_signal
+from .inputs import BASE_SEED, Stream, blocks_for, draw_signal
 from .tuning import TABLE
 
 D_RANGE = (2, 8)
 LOGN_CLASSES = ((10, 14), (15, 16), (17, 18), (19, 20))
 K_CLASSES = ((8, 127), (128, 319), (320, 512))
 C_CANDIDATES = (3.0, 4.0, 5.0, 6.0)
-PMIN_CANDIDATES = (0, 512, 1024, 2048, 4096)
-FUSE_CANDIDATES = (256, 512)          # tried on the best (c, p_min); 0 (the kernel's limit) always
+PMIN_CANDIDATES = (0, 512, 1024, 2048)
+BLOCK_RULES = ("narrow", "wide")      # inputs.blocks_for
+FUSE_CANDIDATES = (256, 512)          # tried on the best (c, p_min, blocks); 0 (the kernel's limit) always
 
 
 def draw_class(n: int, logN: tuple, krange: tuple, seed: int) -> list:
@@ -48,11 +54,8 @@ def draw_class(n: int, logN: tuple, krange: tuple, seed: int) -> list:
     ks = st.integers(n, krange[0], krange[1] + 1)
     ds = st.integers(n, D_RANGE[0], D_RANGE[1] + 1)
     ls = st.integers(n, logN[0], logN[1] + 1)
-    out = []
-    for s in range(n):
-        d, N, k = int(ds[s]), 1 << int(ls[s]), int(ks[s])
-        out.append((draw_signal(d, N, k, seed * 1000003 + s, "uniform", 1.0, 10.0), default_blocks(d, N, k)))
-    return out
+    return [draw_signal(int(ds[s]), 1 << int(ls[s]), int(ks[s]), seed * 1000003 + s, "uniform", 1.0, 10.0)
+            for s in range(n)]
 
 
 class Trial:
@@ -60,15 +63,15 @@ class Trial:
 
     def __init__(self, sfft, torch, sigs):
         self.sfft, self.torch, self.sigs = sfft, torch, sigs
-        self.dev = [sfft.Signal(s.freqs, s.coeffs, s.N) for s, _ in sigs]
-        self.planted = [s.freqs[np.lexsort(s.freqs.T[::-1])].astype(np.int64) for s, _ in sigs]
+        self.dev = [sfft.Signal(s.freqs, s.coeffs, s.N) for s in sigs]
+        self.planted = [s.freqs[np.lexsort(s.freqs.T[::-1])].astype(np.int64) for s in sigs]
 
-    def run(self, c, p_min, fuse_max_len, reps):
+    def run(self, c, p_min, fuse_max_len, blocks, reps):
         sfft, torch = self.sfft, self.torch
-        plans = [sfft.Plan(s.d, s.N, s.k, blocks=b, c=c, p_min=p_min, fuse_max_len=fuse_max_len)
-                 for s, b in self.sigs]
+        plans = [sfft.Plan(s.d, s.N, s.k, blocks=blocks_for(s.d, s.N, s.k, blocks), c=c, p_min=p_min,
+                           fuse_max_len=fuse_max_len) for s in self.sigs]
         batch = sfft.Batch(plans, graph=True)
-        out = batch.outputs(caps=[s.k + 16 for s, _ in self.sigs])
+        out = batch.outputs(caps=[s.k + 16 for s in self.sigs])
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ms, exact, rounds = [], True, 0
         for rep in range(reps + 1):
@@ -105,33 +108,38 @@ def tune(n_signals: int = 192, reps: int = 3, log=print) -> dict:
         valid = Trial(sfft, torch, draw_class(n_signals, logN, krange, BASE_SEED + 901 + 2 * ci))
         results = []
 
-        def consider(c, p_min, fuse):
-            ms, ok, rounds = train.run(c, p_min, fuse, reps)
+        def consider(c, p_min, fuse, blocks):
+            ms, ok, rounds = train.run(c, p_min, fuse, blocks, reps)
             if ok:
-                _, ok, _ = valid.run(c, p_min, fuse, 0)
-            results.append({"c": c, "p_min": p_min, "fuse_max_len": fuse, "ms": ms, "exact": ok, "rounds": rounds})
-            log(f"  logN {logN} k {krange}: c {c} p_min {p_min} fuse {fuse}: {ms:.2f} ms rounds {rounds} "
-                f"exact {ok}", flush=True)
+                _, ok, _ = valid.run(c, p_min, fuse, blocks, 0)
+            results.append({"c": c, "p_min": p_min, "fuse_max_len": fuse, "blocks": blocks, "ms": ms, "exact": ok,
+                            "rounds": rounds})
+            log(f"  logN {logN} k {krange}: c {c} p_min {p_min} fuse {fuse} blocks {blocks}: {ms:.2f} ms "
+                f"rounds {rounds} exact {ok}", flush=True)
 
-        for c, p_min in itertools.product(C_CANDIDATES, PMIN_CANDIDATES):
-            consider(c, p_min, 0)
+        for blocks, c, p_min in itertools.product(BLOCK_RULES, C_CANDIDATES, PMIN_CANDIDATES):
+            consider(c, p_min, 0, blocks)
         good = [r for r in results if r["exact"]]
         if good:
             best = min(good, key=lambda r: r["ms"])
             for fuse in FUSE_CANDIDATES:
-                consider(best["c"], best["p_min"], fuse)
+                consider(best["c"], best["p_min"], fuse, best["blocks"])
             good = [r for r in results if r["exact"]]
             best = min(good, key=lambda r: r["ms"])
         else:
-            best = {"c": 5.0, "p_min": max(PMIN_CANDIDATES), "fuse_max_len": 0, "ms": None, "exact": False}
-        default = next(r for r in results if r["c"] == 5.0 and r["p_min"] == 0 and r["fuse_max_len"] == 0)
+            best = {"c": 5.0, "p_min": max(PMIN_CANDIDATES), "fuse_max_len": 0, "blocks": "wide", "ms": None,
+                    "exact": False}
+        default = next(r for r in results if r["c"] == 5.0 and r["p_min"] == 0 and r["fuse_max_len"] == 0
+                       and r["blocks"] == "narrow")
         classes.append({"d": list(D_RANGE), "logN": list(logN), "k": list(krange), "c": best["c"],
-                        "p_min": best["p_min"], "fuse_max_len": best["fuse_max_len"], "ms": best["ms"],
+                        "p_min": best["p_min"], "fuse_max_len": best["fuse_max_len"], "blocks": best["blocks"],
+                        "ms": best["ms"],
                         "rounds": best.get("rounds"), "exact_candidates": len(good),
                         "default_c5_ms": default["ms"], "default_c5_exact": default["exact"],
                         "candidates": results})
         log(f"class logN {logN} k {krange}: c {best['c']} p_min {best['p_min']} fuse {best['fuse_max_len']} "
-            f"{best['ms']} ms (default c = 5, no floor: {default['ms']:.2f} ms, exact {default['exact']})", flush=True)
+            f"blocks {best['blocks']} {best['ms']} ms (default c = 5, no floor, narrow blocks: {default['ms']:.2f} ms, "
+            f"exact {default['exact']})", flush=True)
         del train, valid
         gc.collect()
     return {"version": 1,
@@ -142,7 +150,7 @@ def tune(n_signals: int = 192, reps: int = 3, log=print) -> dict:
             "objective": "median CUDA-event time of one graph-launched batched execute of the class's "
                          "training batch, among candidates that recovered every signal of the training and "
                          "validation batches exactly",
-            "search": {"c": list(C_CANDIDATES), "p_min": list(PMIN_CANDIDATES),
+            "search": {"c": list(C_CANDIDATES), "p_min": list(PMIN_CANDIDATES), "blocks": list(BLOCK_RULES),
                        "fuse_max_len": [0] + list(FUSE_CANDIDATES)},
             "classes": classes}
 

@@ -192,6 +192,30 @@ def default_blocks(d: int, N: int, k: int, c: int = 5) -> tuple:
     return tuple(base + (1 if q < rem else 0) for q in range(nb))
 
 
+def wide_blocks(d: int, N: int) -> tuple:
+    """Block sizes for partial unwrapping (Sec. 4.1) with the widest blocks whose direction
+    (N^r on a block's r-th coordinate, Eq. 35) stays an int64: b - 1 = the largest r with
+    N^r <= 9e18, ceil(d / b) blocks, sizes as even as possible.  With one shifted set per
+    coordinate the read-out resolves N values from one phase whatever the block, so wide blocks
+    cost no precision; they give fewer line directions and larger projected ranges."""
+    r = 0
+    while r + 1 < d and float(N) ** (r + 1) <= 9.0e18:
+        r += 1
+    b = r + 1
+    nb = -(-d // b)
+    base, rem = divmod(d, nb)
+    return tuple(base + (1 if q < rem else 0) for q in range(nb))
+
+
+def blocks_for(d: int, N: int, k: int, rule: str = "narrow") -> tuple:
+    """Blocks by the named rule: "narrow" (default_blocks) or "wide" (wide_blocks)."""
+    if rule == "wide":
+        return wide_blocks(d, N)
+    if rule == "narrow":
+        return default_blocks(d, N, k)
+    raise ValueError(rule)
+
+
 def batched_mix(n_signals: int = 4096, seed: int = BASE_SEED + 4, k_lo: int = 8, k_hi: int = 512,
                 d_lo: int = 2, d_hi: int = 8, logN_lo: int = 10, logN_hi: int = 20) -> list:
     """Independent signals with k ~ U{k_lo..k_hi}, d ~ U{d_lo..d_hi}, N = 2^U{logN_lo..logN_hi},

@@ -805,7 +805,9 @@ def test_batched_mix_over_the_full_ranges_matches_oracle(sfft):
     mix = batched_mix(256, seed=BASE_SEED + 4 + 77)
     assert {s.d for s, _ in mix} == set(range(2, 9))
     assert min(s.N for s, _ in mix) == 1 << 10 and max(s.N for s, _ in mix) == 1 << 20
+    from paper_1606_07407_gb300.inputs import blocks_for
     sched = [tuning.schedule(s.d, s.N, s.k) for s, _ in mix]
+    mix = [(s, blocks_for(s.d, s.N, s.k, sc["blocks"])) for (s, _), sc in zip(mix, sched)]
     plans = [sfft.Plan(s.d, s.N, s.k, blocks=b, c=sc["c"], p_min=sc["p_min"], fuse_max_len=sc["fuse_max_len"])
              for (s, b), sc in zip(mix, sched)]
     res, sts, stats = sfft.Batch(plans, graph=True).execute([sfft.Signal(s.freqs, s.coeffs, s.N) for s, _ in mix])
