@@ -89,12 +89,12 @@ def sample_traffic(workload: str):
 class Job:
     """The signals one rank recovers per step, with each signal's plan arguments."""
 
-    def __init__(self, name: str, rank: int, batch: int):
+    def __init__(self, name: str, rank: int, batch: int, mix_signals: int = MIX_SIGNALS):
         from paper_1606_07407_gb300 import tuning
         self.name = name
         if name == MIX:
             from paper_1606_07407_gb300.inputs import blocks_for
-            mix = batched_mix(MIX_SIGNALS, seed=BASE_SEED + 4 + 1000 * rank)
+            mix = batched_mix(mix_signals, seed=BASE_SEED + 4 + 1000 * rank)
             self.sigs = [s for s, _ in mix]
             self.sched = [tuning.schedule(s.d, s.N, s.k) for s in self.sigs]
             self.blocks = [blocks_for(s.d, s.N, s.k, sc["blocks"]) for s, sc in zip(self.sigs, self.sched)]
@@ -342,7 +342,7 @@ def run_ours(args):
     _barrier(world)
     from paper_1606_07407_gb300 import sfft
 
-    job = Job(args.workload, rank, args.batch)
+    job = Job(args.workload, rank, args.batch, args.signals)
     stream = torch.cuda.current_stream()
     nb = len(job.sigs)
     # inputs resident in HBM before timing
@@ -620,6 +620,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + [MIX])
     ap.add_argument("--batch", type=int, default=256, help="signals recovered per step (single-shape presets)")
+    ap.add_argument("--signals", type=int, default=MIX_SIGNALS,
+                    help="signals of the mix, drawn the same way (fewer: a smaller case for profiling)")
     ap.add_argument("--form", default="batched", choices=["batched", "plain"])
     ap.add_argument("--other-steps", type=int, default=1)
     ap.add_argument("--profile-steps", type=int, default=2)

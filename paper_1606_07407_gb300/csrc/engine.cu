@@ -81,6 +81,37 @@ __global__ void k_bind_tw(int n, const SigCfg* __restrict__ cfg, const SigRun* _
 // has planned keeps it), then the work counts of the batched kernels and their exclusive
 // scans over the signals.  Sets the graph conditions: some signal active (the round loop),
 // some batched work, some fused round planned.
+// Rows of one signal that one block of the DFT takes together (they share p, the chirp, the
+// filter spectrum and the twiddles): as many as the block has whole-warp groups of the threads a
+// row needs, and as the block's shared memory holds padded rows plus one prefetch row of L.
+template <typename C2>
+__host__ __device__ inline int dft_group_rows(int L, int nthr, int64_t smem_elems, int n_sets) {
+  const int need = fft_threads<C2>(L);
+  int g = nthr / need;
+  const int64_t rowpad = (L + L / 32 + 1) & ~1;
+  while (g > 1 && (int64_t)g * rowpad + L > smem_elems) --g;
+  if (g < 1) g = 1;
+  return g < n_sets ? g : n_sets;
+}
+
+// The round's parameters of every signal not already planned by the fused kernel (stop rule,
+// prime, direction mod p, work geometry: plan_signal), one thread per signal over the whole
+// grid; k_plan then sums and scans the work.
+template <typename T>
+__global__ void k_plan_signals(PlanArgs a, const SigCfg* __restrict__ cfg, SigRun* run, const int32_t* __restrict__ ptab,
+                               int n_ptab, const int32_t* __restrict__ pfirst, int64_t pfirst_n,
+                               const int64_t* __restrict__ dirs, const int64_t* __restrict__ plist, int64_t* ubuf,
+                               HistRec* hist) {
+  const PrimeTables pt{ptab, n_ptab, pfirst, pfirst_n, dirs, plist};
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += gridDim.x * blockDim.x) {
+    SigRun r = run[s];
+    if (!(r.active && r.fused)) {
+      plan_signal<T>(a, cfg[s], r, pt, ubuf, hist, s == 0);
+      run[s] = r;
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg* __restrict__ cfg, SigRun* run,
                                                        RoundCtl* ctl, Scans sc, const int32_t* __restrict__ ptab,
@@ -93,14 +124,9 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
   __shared__ unsigned long long s_key;
   const int n = a.n;
   int64_t tiles = 0, active = 0, fused = 0;
-  // pass 1: stop rule and round parameters of every signal
-  const PrimeTables pt{ptab, n_ptab, pfirst, pfirst_n, dirs, plist};
+  // pass 1: the round's totals (k_plan_signals has planned every signal)
   for (int s = threadIdx.x; s < n; s += blockDim.x) {
-    SigRun r = run[s];
-    if (!(r.active && r.fused)) {
-      plan_signal<T>(a, cfg[s], r, pt, ubuf, hist, s == 0);
-      run[s] = r;
-    }
+    const SigRun& r = run[s];
     if (r.active) {
       active += 1;
       if (r.fused) fused += 1;
@@ -231,7 +257,9 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
           // the dense tensor-core kernel takes the signal's rows (no Bluestein row or filter)
         } else if (!r.big) {
           const bool sm = r.L <= (1 << kSmallFftLog);
-          v[sm ? SC_ROWS_S : SC_ROWS] = c.n_sets;
+          const int g = dft_group_rows<c2<T>>(r.L, sm ? a.dft_thr_s : a.dft_thr_l,
+                                             (sm ? a.dft_smem_s : a.dft_smem_l) / (int64_t)sizeof(c2<T>), c.n_sets);
+          v[sm ? SC_ROWS_S : SC_ROWS] = (c.n_sets + g - 1) / g;   // row groups
           v[sm ? SC_FILT_S : SC_FILT] = r.tab_owner;
         } else {
           int M1, M2, CT, RT;
@@ -429,24 +457,35 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ C2 tw_lo[kTwLo], tw_hi[kSingleMaxLf / kTwLo];
   C2* buf = reinterpret_cast<C2*>(smem_raw);
-  // one block per row (a loop around the unrolled passes would make them spill), last rows first:
-  // the signals at the end of the sampling queue may carry several mode splits to add
-  const int64_t n_rows = small ? ctl->n_rows_s : ctl->n_rows;
-  if ((int64_t)blockIdx.x >= n_rows) return;
-  const int64_t item = n_rows - 1 - blockIdx.x;
+  // one block per group of rows of one signal (a loop around the unrolled passes would make
+  // them spill), last groups first: the signals at the end of the sampling queue may carry
+  // several mode splits to add.  The block's threads split into g warp-aligned teams of
+  // `team` threads, one row each; the rows share p, so the chirp, the filter spectrum and the
+  // twiddles serve them all.
+  const int64_t n_items = small ? ctl->n_rows_s : ctl->n_rows;
+  if ((int64_t)blockIdx.x >= n_items) return;
+  const int64_t item = n_items - 1 - blockIdx.x;
   const int64_t* scan = sc.v[small ? SC_ROWS_S : SC_ROWS];
   const int s = find_slot(scan, n, item);
-  const int row = (int)(item - scan[s]);
   const SigCfg& c = cfg[s];
   const SigRun r = run[s];
   const int L = r.L;
   const int64_t p = r.p;
+  const int g = dft_group_rows<C2>(L, (int)blockDim.x, smem_bytes / (int)sizeof(C2), c.n_sets);
+  const int row0 = (int)(item - scan[s]) * g;
+  const int nrow = min(g, c.n_sets - row0);
+  const int team = ((int)blockDim.x / g) & ~31;
+  const int sr = (int)threadIdx.x / team, lt = (int)threadIdx.x % team;
+  const bool act = sr < nrow;
+  const int row = row0 + (act ? sr : 0);
+  const int rowpad = (L + L / 32 + 1) & ~1;   // even: every row starts 16-byte aligned
+  C2* rb = buf + (act ? sr : 0) * rowpad;
   const C2* chirp = tab + r.tab_at + p;   // the tables and filter of the first signal with this prime
   const C2* B = bhat + r.bhat_at;
-  // With room for a second row of L values after the padded row, the filter spectrum is copied
+  // With room for one more row of L values after the padded rows, the filter spectrum is copied
   // there asynchronously during the forward transform, and then the chirp during the inverse
   // one, so that neither product waits on global memory.
-  const int pfo = (L + L / 32 + 1) & ~1;   // past the padded row, at an even element: 16-byte aligned
+  const int pfo = g * rowpad;
   C2* pf = buf + pfo;
   const bool prefetch = (int64_t)(pfo + L) * (int64_t)sizeof(C2) <= (int64_t)smem_bytes;
   if (prefetch) {
@@ -457,32 +496,38 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   }
   fft_tables(tw_hi, tw_lo, L, tws);
   // loops unrolled so that each thread's global loads are in flight together
+  if (act) {
 #pragma unroll 8
-  for (int x = threadIdx.x; x < L; x += blockDim.x) {
-    C2 v = mk2((T)0, (T)0);
-    if (x < p) {
-      C2 y = sum_splits<T>(part, r, c.n_sets, row, x);
-      if (r.noise_sigma > 0.0) y = cadd(y, black_box_noise<T>(r.noise_seed, r.round, row, x, r.noise_sigma));
-      v = cmul(chirp[x], y);
+    for (int x = lt; x < L; x += team) {
+      C2 v = mk2((T)0, (T)0);
+      if (x < p) {
+        C2 y = sum_splits<T>(part, r, c.n_sets, row, x);
+        if (r.noise_sigma > 0.0) y = cadd(y, black_box_noise<T>(r.noise_seed, r.round, row, x, r.noise_sigma));
+        v = cmul(chirp[x], y);
+      }
+      rb[fpad(x)] = v;
     }
-    buf[fpad(x)] = v;
   }
   __syncthreads();
-  fft_row<C2, false>(buf, L, tw_hi, tw_lo);
+  fft_row<C2, false>(rb, L, tw_hi, tw_lo, lt, team, act);
   if (prefetch) {
     cp_async_wait_all();
     __syncthreads();
+    if (act) {
 #pragma unroll 8
-    for (int k = threadIdx.x; k < L; k += blockDim.x) buf[fpad(k)] = cmul(buf[fpad(k)], pf[k]);
+      for (int k = lt; k < L; k += team) rb[fpad(k)] = cmul(rb[fpad(k)], pf[k]);
+    }
     __syncthreads();   // the spectrum is consumed: the chirp takes its place
     for (int x = threadIdx.x; x < p; x += blockDim.x) cp_async<sizeof(C2)>(pf + x, chirp + x);
     cp_async_commit();
   } else {
+    if (act) {
 #pragma unroll 8
-    for (int k = threadIdx.x; k < L; k += blockDim.x) buf[fpad(k)] = cmul(buf[fpad(k)], B[k]);
+      for (int k = lt; k < L; k += team) rb[fpad(k)] = cmul(rb[fpad(k)], B[k]);
+    }
     __syncthreads();
   }
-  fft_row<C2, true>(buf, L, tw_hi, tw_lo);
+  fft_row<C2, true>(rb, L, tw_hi, tw_lo, lt, team, act);
   if (prefetch) {
     cp_async_wait_all();
     __syncthreads();
@@ -491,16 +536,19 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   const T invL = (T)1 / (T)L;
   C2* out = Y + c.Y_off + (int64_t)row * p;
   T m2 = (T)0;   // largest |Y_0|^2 of this thread (set 0 only), in the transform's precision
+  if (act) {
 #pragma unroll 4
-  for (int64_t h0 = 0; h0 < p; h0 += blockDim.x) {
-    const int64_t h = h0 + threadIdx.x;
-    if (h < p) {
-      const C2 v = cmul(ch[h], cscale(buf[fpad((int)h)], invL));
-      out[h] = v;
-      m2 = fmax(m2, v.x * v.x + v.y * v.y);
+    for (int64_t h0 = 0; h0 < p; h0 += team) {
+      const int64_t h = h0 + lt;
+      if (h < p) {
+        const C2 v = cmul(ch[h], cscale(rb[fpad((int)h)], invL));
+        out[h] = v;
+        m2 = fmax(m2, v.x * v.x + v.y * v.y);
+      }
     }
   }
-  if (row == 0) max_abs_to<T>(&run[s].maxy0_bits, sqrt((double)m2));
+  // whole warps only (teams are warp-aligned): the team of set 0 reports its largest bin
+  if (act && row == 0) max_abs_to<T>(&run[s].maxy0_bits, sqrt((double)m2));
 }
 
 // ------------------------------------------------------------------ DFT, four-step passes for long lengths
@@ -1174,15 +1222,25 @@ class Engine final : public EngineBase {
           p1, L1, t0 + p1, tw_src(), (C2*)bhat_ + pre_bhat[q]);
       ECHK(cudaGetLastError());
     }
-    // the long-row DFT blocks (one per SM by registers) also take the prefetch row where it fits:
-    // a row of L <= 10240 with its spectrum, within the block's shared-memory limit
+    // The long-row DFT blocks take several rows of a signal at a time when they are short enough
+    // (dft_group_rows), plus the prefetch row where it fits.  Their shared memory leaves room for
+    // two blocks per SM (which the registers allow up to 256 threads) unless one row of the
+    // batch's longest length needs more; blocks of 512 threads (lengths above 8192) are one per
+    // SM by registers and take all of it.  The short-row blocks hold one row of 2^kSmallFftLog
+    // and its prefetch row (six blocks per SM by shared memory, eight by registers), or two
+    // shorter rows.
     {
-      int optin = 0;
+      int optin = 0, per_sm = 0;
       ECHK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_));
+      ECHK(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev_));
       const size_t kStatic = (size_t)(kTwLo + kSingleMaxLf / kTwLo) * sizeof(C2);   // k_dft's static tables
-      const int Lp = std::min(1 << small_logL_max_, 10240);
-      const size_t want = (size_t)(Lp + Lp / 32 + Lp) * sizeof(C2);
-      smem_dft_ = std::max(smem_small_, want + kStatic <= (size_t)optin ? want : (size_t)0);
+      const size_t room = (size_t)optin > kStatic + 1024 ? (size_t)optin - kStatic - 1024 : 0;
+      const size_t half = (size_t)per_sm / 2 > kStatic + 2048 ? (size_t)per_sm / 2 - kStatic - 2048 : 0;
+      const size_t cap = small_threads_ <= 256 ? std::min(room, half) : room;
+      smem_dft_ = std::max(smem_small_, cap & ~(size_t)15);
+      const int ls = std::min(small_logL_max_, kSmallFftLog);
+      dft_thr_s_ = std::max(32, (1 << ls) / fft_per_thread<C2>());
+      dft_smem_s_ = (size_t)((((1 << ls) + (1 << ls) / 32 + 1) & ~1) + (1 << ls)) * sizeof(C2);
     }
     ECHK(cudaFuncSetAttribute(k_dft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dft_));
     if (any_big_) {
@@ -1246,14 +1304,11 @@ class Engine final : public EngineBase {
   // with_filters: the filter spectra first, on the same stream (else they were made beside the
   // sampling, see enqueue_batched)
   cudaError_t launch_dft_rows(bool with_filters = true) {
-    const int ls = std::min(small_logL_max_, kSmallFftLog);
-    const int thr_s = std::max(32, (1 << ls) / fft_per_thread<C2>());
-    // short rows: room for the prefetch row too (six blocks per SM by shared memory, eight by registers)
-    const size_t smem_sp = (size_t)((((1 << ls) + (1 << ls) / 32 + 1) & ~1) + (1 << ls)) * sizeof(C2);
     const TwSrc<C2> tws = tw_src();
     if (with_filters) ECHK(launch_filters(st_));
-    k_dft<T><<<(unsigned)rows_max_, thr_s, smem_sp, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_, (C2*)tab_,
-                                                           (C2*)bhat_, tws, (C2*)Y_, 1, (int)smem_sp);
+    k_dft<T><<<(unsigned)rows_max_, dft_thr_s_, dft_smem_s_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
+                                                                   (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 1,
+                                                                   (int)dft_smem_s_);
     ECHK(cudaGetLastError());
     if (small_logL_max_ > kSmallFftLog) {
       k_dft<T><<<(unsigned)rows_max_, small_threads_, smem_dft_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
@@ -1347,11 +1402,14 @@ class Engine final : public EngineBase {
     return cudaGetLastError();
   }
 
-  // the round's plan (one launch)
+  // the round's plan: every signal's parameters over the grid, then the sums and scans in one block
   cudaError_t launch_plan(const PlanArgs& pa, int64_t* launches) {
+    k_plan_signals<T><<<(n_ + 127) / 128, 128, 0, st_>>>(pa, cfg_, run_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_,
+                                                          plist_, u_, hist_);
+    ECHK(cudaGetLastError());
     k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_,
                                             plist_, u_, hist_, powner_);
-    launches[0] += 1;
+    launches[0] += 2;
     return cudaGetLastError();
   }
 
@@ -1554,6 +1612,10 @@ class Engine final : public EngineBase {
     pa.single_max_logL = log2i(single_max_L<T>());
     pa.hard_rounds = hard_rounds;
     pa.fuse = any_fuse_ ? 1 : 0;
+    pa.dft_thr_s = dft_thr_s_;
+    pa.dft_smem_s = (int64_t)dft_smem_s_;
+    pa.dft_thr_l = small_threads_;
+    pa.dft_smem_l = (int64_t)smem_dft_;
     return pa;
   }
 
@@ -1686,6 +1748,9 @@ class Engine final : public EngineBase {
     pa.force = 1;
     pa.force_p = p;
     pa.force_K = K;
+    k_plan_signals<T><<<(n_ + 127) / 128, 128, 0, st_>>>(pa, cfg_, run_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_,
+                                                          plist_, u_, nullptr);
+    ECHK(cudaGetLastError());
     k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_, plist_, u_,
                                             nullptr, powner_);
     ECHK(cudaGetLastError());
@@ -1767,7 +1832,9 @@ class Engine final : public EngineBase {
   int peel_gx_ = 1;         // k_peel blocks per signal
   int logL_big_max_ = 0, small_logL_max_ = 1, small_threads_ = 256, n_ptab_ = 0;
   size_t smem_small_ = 0, smem_bigA_ = 0, smem_bigB_ = 0, bytes_ = 0, host_stage_bytes_ = 0;
-  size_t smem_dft_ = 0;   // the long-row DFT kernel's dynamic shared memory (row + prefetch row)
+  size_t smem_dft_ = 0;   // the long-row DFT kernel's dynamic shared memory (rows + prefetch row)
+  int dft_thr_s_ = 32;     // the short-row DFT launch's block size
+  size_t dft_smem_s_ = 0;  // and dynamic shared memory
   int64_t rows_max_ = 0;
   int64_t Lmax_ = 2, p_max_ = 2, part_cap_ = 0, hash_total_ = 0, k_max_ = 0, kd_max_ = 0, reg_cap_max_ = 0;
   bool any_dense_ = false;   // some slot takes short rounds' DFT on the tensor cores

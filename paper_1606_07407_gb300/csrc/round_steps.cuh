@@ -29,6 +29,8 @@ struct PlanArgs {
   int fuse;             // 0: no round runs fused (step calls)
   cudaGraphConditionalHandle cond_batch;   // graph condition: some signal has batched work
   cudaGraphConditionalHandle cond_fused;   // graph condition: some signal has a fused round planned
+  int dft_thr_s, dft_thr_l;                // block sizes of the short- and long-row DFT launches
+  int64_t dft_smem_s, dft_smem_l;          // and their dynamic shared memory, bytes
 };
 
 __host__ __device__ inline int ceil_log2(int64_t v) {
