@@ -53,13 +53,23 @@ typedef enum {
  * cores: operands split into two BF16 terms each (hi = bf16(v), lo = bf16(v -
  * hi)), three products per pair, FP32 accumulation; longer rounds use the float
  * Bluestein DFT, and no round is fused.  Its DFT carries about 2^-16 of each
- * operand's size instead of float's 2^-24 (at most 64 sample sets). */
+ * operand's size instead of float's 2^-24 (at most 64 sample sets).
+ * FP32_THEN_FP64: sfft_execute runs the rounds in float (as AUTO) until a round accepts fewer
+ * than k* / 64 of the bins (k* the modes left: float's rounding no longer reads them), then
+ * continues in double from the float registry, the round counter and the empty-bin reference
+ * carried over: the double rounds read the modes float could not read and cancel its false
+ * positives.  They keep the float rounds' empty-bin level (rho), below which the float
+ * coefficients' own errors stay: coefficients of the modes found in float keep float's error
+ * (the float policies' tolerance), the others double's.  opts.tau and delta apply to the float
+ * rounds, the double rounds take the FP64 ones.  Plain form only: a batch of such plans is
+ * INVALID_ARG. */
 typedef enum {
   SFFT_PREC_AUTO = 0,
   SFFT_PREC_FP32_FP64RATIO = 1,
   SFFT_PREC_FP32 = 2,
   SFFT_PREC_FP64 = 3,
-  SFFT_PREC_FP32_BF16DFT = 4
+  SFFT_PREC_FP32_BF16DFT = 4,
+  SFFT_PREC_FP32_THEN_FP64 = 5
 } sfft_precision;
 
 typedef struct sfft_plan_s* sfft_plan;

@@ -91,6 +91,7 @@ struct sfft_plan_s {
   cudaStream_t stream = nullptr;
   bool profile = false, graph = false;
   std::unique_ptr<EngineBase> eng;
+  std::unique_ptr<EngineBase> eng64;   // FP32_THEN_FP64: the double rounds after the float ones
 };
 
 struct sfft_batch_s {
@@ -128,7 +129,7 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
   sfft_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  if (o.precision < SFFT_PREC_AUTO || o.precision > SFFT_PREC_FP32_BF16DFT) return SFFT_ERR_INVALID_ARG;
+  if (o.precision < SFFT_PREC_AUTO || o.precision > SFFT_PREC_FP32_THEN_FP64) return SFFT_ERR_INVALID_ARG;
   if (o.box_lo > 0 || o.box_lo < -N) return SFFT_ERR_INVALID_ARG;
   const bool fp64 = o.precision == SFFT_PREC_FP64;
   if (!fp64 && N > (1LL << 23)) return SFFT_ERR_PRECISION;
@@ -160,7 +161,8 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
   D.c8 = 40;   // c = 5 (Sec. 5)
   D.box_lo = o.box_lo;
   P->prec = o.precision;
-  const bool auto_ratio = o.precision == SFFT_PREC_AUTO || o.precision == SFFT_PREC_FP32_BF16DFT;
+  const bool auto_ratio = o.precision == SFFT_PREC_AUTO || o.precision == SFFT_PREC_FP32_BF16DFT ||
+                          o.precision == SFFT_PREC_FP32_THEN_FP64;
   D.ratio64 = (o.precision == SFFT_PREC_FP32_FP64RATIO || fp64 || (auto_ratio && N > (1LL << 14))) ? 1 : 0;
   D.dense_dft = o.precision == SFFT_PREC_FP32_BF16DFT ? 1 : 0;
   D.coef_mean = o.coef_set0 ? 0 : 1;
@@ -297,11 +299,31 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
 
   // the dense DFT takes every sample set of a signal as the N of one MMA (at most 64)
   if (D.dense_dft && (D.shift_block ? 1 + (int)D.shift_blocks.size() : d + 1) > 64) return SFFT_ERR_INVALID_ARG;
+  if (o.precision == SFFT_PREC_FP32_THEN_FP64) D.stall_div = 64;
   std::vector<SlotDesc> slots(1, D);
   EngineBase* e = nullptr;
   sfft_status st = cuda_status(engine_create(fp64, slots, P->stream, P->profile, P->graph, &e));
   if (st != SFFT_OK) return st;
   P->eng.reset(e);
+  if (o.precision == SFFT_PREC_FP32_THEN_FP64) {
+    // the double rounds: FP64 ratio test and read-out, one empty round ends them, no stall
+    // hand-over, nothing fused.  They keep the float rounds' empty-bin level: the float
+    // coefficients' own errors (about 2^-20 relative) stay below it, so the double rounds end once
+    // every mode is found instead of trying to isolate hundreds of residuals of that size.
+    SlotDesc D64 = D;
+    D64.stall_div = 0;
+    D64.ratio64 = 1;
+    D64.fuse = 0;
+    D64.dense_dft = 0;
+    D64.tau = 1e-7;
+    D64.delta = 0.1;
+    D64.empty_rounds = o.empty_rounds > 0 ? o.empty_rounds : 1;
+    std::vector<SlotDesc> s64(1, D64);
+    EngineBase* e64 = nullptr;
+    st = cuda_status(engine_create(true, s64, P->stream, P->profile, P->graph, &e64));
+    if (st != SFFT_OK) return st;
+    P->eng64.reset(e64);
+  }
   *plan_out = P.release();
   return SFFT_OK;
 }
@@ -318,7 +340,10 @@ int sfft_plan_sets(sfft_plan plan) {
   if (!plan) return -1;
   return plan->desc.shift_block ? 1 + (int)plan->desc.shift_blocks.size() : plan->desc.d + 1;
 }
-int64_t sfft_plan_device_bytes(sfft_plan plan) { return plan ? (int64_t)plan->eng->device_bytes() : -1; }
+int64_t sfft_plan_device_bytes(sfft_plan plan) {
+  if (!plan) return -1;
+  return (int64_t)(plan->eng->device_bytes() + (plan->eng64 ? plan->eng64->device_bytes() : 0));
+}
 
 sfft_status sfft_signal_synthetic(int d, int64_t N, int64_t k, const int32_t* freqs_dev, const double* coeffs_dev,
                                   double noise_sigma, uint64_t noise_seed, sfft_signal* signal_out) {
@@ -419,9 +444,42 @@ sfft_status sfft_execute(sfft_plan plan, sfft_signal signal, int64_t capacity, i
   const double ns[1] = {signal->noise_sigma};
   const uint64_t nseed[1] = {signal->noise_seed};
   int st = 0;
+  sfft_stats s1;
+  sfft_stats* st1 = (plan->eng64 && stats) ? &s1 : stats;
   sfft_status cs = cuda_status(
-      plan->eng->run(w, a, ks, caps, ns, nseed, freqs_out_dev, (double2*)coeffs_out_dev, n_found, &st, stats));
+      plan->eng->run(w, a, ks, caps, ns, nseed, freqs_out_dev, (double2*)coeffs_out_dev, n_found, &st, st1));
   if (cs != SFFT_OK) return cs;
+  if (!plan->eng64 || st == SFFT_OK || st == SFFT_ERR_TIMEOUT) {
+    if (st1 != stats && stats) *stats = s1;
+    return (sfft_status)st;
+  }
+  // FP32_THEN_FP64: the double rounds continue from the float registry (the outputs just written)
+  int r0 = 0;
+  double a_ref = 0.0;
+  cs = cuda_status(plan->eng->last_state(&r0, &a_ref));
+  if (cs != SFFT_OK) return cs;
+  plan->eng64->set_seed(freqs_out_dev, (const double2*)coeffs_out_dev, std::min(*n_found, capacity), r0, a_ref);
+  sfft_stats s2;
+  cs = cuda_status(plan->eng64->run(w, a, ks, caps, ns, nseed, freqs_out_dev, (double2*)coeffs_out_dev, n_found,
+                                    &st, stats ? &s2 : nullptr));
+  if (cs != SFFT_OK) return cs;
+  if (stats) {
+    // rounds 1..r0 from the float run, the rest from the double one
+    *stats = s2;
+    stats->samples += s1.samples;
+    stats->terms += s1.terms;
+    stats->terms_fused += s1.terms_fused;
+    for (int i = 0; i < std::min(r0, SFFT_STATS_MAX_ROUNDS); ++i) {
+      stats->p[i] = s1.p[i];
+      stats->K[i] = s1.K[i];
+      stats->accepted[i] = s1.accepted[i];
+      stats->registry[i] = s1.registry[i];
+    }
+    for (int q = 0; q < SFFT_NKCLASS; ++q) {
+      stats->kernel_launches[q] += s1.kernel_launches[q];
+      stats->kernel_ms[q] += s1.kernel_ms[q];
+    }
+  }
   return (sfft_status)st;
 }
 
@@ -435,7 +493,7 @@ sfft_status sfft_batch_create(int n, const sfft_plan* plans, void* stream, int g
   slots.reserve(n);
   bool profile = (graph & SFFT_BATCH_PROFILE) != 0;
   for (int s = 0; s < n; ++s) {
-    if (!plans[s]) return SFFT_ERR_INVALID_ARG;
+    if (!plans[s] || plans[s]->eng64) return SFFT_ERR_INVALID_ARG;   // FP32_THEN_FP64: plain form only
     const bool fp64 = plans[s]->prec == SFFT_PREC_FP64;
     if (s == 0) B->prec = plans[s]->prec;
     if ((B->prec == SFFT_PREC_FP64) != fp64) return SFFT_ERR_INVALID_ARG;

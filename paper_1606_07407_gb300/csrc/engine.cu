@@ -57,6 +57,39 @@ __global__ void k_init(int n, SigRun* run, const int64_t* __restrict__ bindv) {
   }
 }
 
+// A registry to start from (slot 0 of a one-slot engine): entry j takes the seed's key and
+// coefficient, its twiddles e^{2 pi i w . s_n} and a hash slot; the slot's state continues after
+// round0 rounds with the empty-bin reference of the run that found the entries.  Seed keys are
+// distinct (a registry's), so the hash insert compares nothing.
+template <typename T>
+__global__ void k_seed(const SigCfg* __restrict__ cfg, SigRun* run, const int32_t* __restrict__ seed_w,
+                       const double2* __restrict__ seed_a, int n_seed, int round0, double a_ref,
+                       const int32_t* __restrict__ shblk, int32_t* regw, double2* rega, c2<T>* regtw, int32_t* hash) {
+  const SigCfg& c = cfg[0];
+  SigRun* rp = run;
+  const int d = c.d, S = c.n_sets - 1;
+  const int32_t* blk = shblk + c.blk_off;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_seed; j += gridDim.x * blockDim.x) {
+    const int32_t* w = seed_w + (int64_t)j * d;
+    int32_t* rw = regw + c.regw_off + (int64_t)j * d;
+    for (int l = 0; l < d; ++l) rw[l] = w[l];
+    const double2 a = seed_a[j];
+    rega[c.rega_off + j] = a;
+    for (int n = 1; n <= S; ++n) regtw[c.regtw_off + (int64_t)j * S + n - 1] = shift_root<T>(c, blk, w, n, true);
+    int32_t* hs = hash + c.hash_off;
+    int slot = (int)(hash_key(w, d) & (unsigned long long)c.hash_mask);
+    for (int probe = 0; probe <= c.hash_mask; ++probe, slot = (slot + 1) & c.hash_mask)
+      if (atomicCAS(&hs[slot], -1, j) < 0) break;
+    if (a.x != 0.0 || a.y != 0.0) atomicAdd(&rp->n_live, 1);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    rp->K_reg = n_seed;
+    rp->round = round0;
+    rp->a_ref = a_ref;
+    rp->any_occupied = 1;   // the round handed over is no empty round of the stop rule
+  }
+}
+
 // twiddles e^{2 pi i w_j . s_n} of the bound signals' modes, one per shifted set (shift_root)
 template <typename T>
 __global__ void k_bind_tw(int n, const SigCfg* __restrict__ cfg, const SigRun* __restrict__ run,
@@ -1021,6 +1054,7 @@ class Engine final : public EngineBase {
       c.c8 = d.c8;
       c.empty_rounds = std::max(1, d.empty_rounds);
       c.dense_dft = (sizeof(T) == 4 && d.dense_dft) ? 1 : 0;
+      c.stall_div = d.stall_div;
       if (c.dense_dft) any_dense_ = true;
       c.max_rounds = d.max_rounds;
       c.n_dirs = d.n_dirs;
@@ -1507,7 +1541,31 @@ class Engine final : public EngineBase {
     ECHK(cudaMemsetAsync(ctl_, 0, sizeof(RoundCtl), st_));
     const int gx = (int)std::min<int64_t>(std::max<int64_t>((kd_max_ + 255) / 256, 1), 64);
     k_bind_tw<T><<<dim3(gx, n_), 256, 0, st_>>>(n_, cfg_, run_, sig_w_, shblk_, (C2*)tw_);
+    ECHK(cudaGetLastError());
+    if (seed_n_ > 0 && n_ == 1) {
+      const int n_seed = (int)std::min<int64_t>(seed_n_, cfg_host_[0].reg_cap);
+      k_seed<T><<<(n_seed + 255) / 256, 256, 0, st_>>>(cfg_, run_, seed_w_, seed_a_, n_seed, seed_round_, seed_aref_,
+                                                       shblk_, regw_, rega_, (C2*)regtw_, hash_);
+      seed_n_ = 0;   // one run only
+    }
     return cudaGetLastError();
+  }
+
+  void set_seed(const int32_t* w, const double2* a, int64_t n, int round0, double a_ref) override {
+    seed_w_ = w;
+    seed_a_ = a;
+    seed_n_ = n;
+    seed_round_ = round0;
+    seed_aref_ = a_ref;
+  }
+
+  cudaError_t last_state(int* rounds, double* a_ref) override {
+    SigRun r;
+    ECHK(cudaMemcpyAsync(&r, run_, sizeof(SigRun), cudaMemcpyDeviceToHost, st_));
+    ECHK(cudaStreamSynchronize(st_));
+    *rounds = r.round;
+    *a_ref = r.a_ref;
+    return cudaSuccess;
   }
 
   // Adds a conditional node of the given type after the work captured so far on cs, and
@@ -1698,8 +1756,8 @@ class Engine final : public EngineBase {
         stats->registry[i] = hh[i].live;
       }
       if (use_graph_ && !record) {
-        // bodies of the device loop (one plan each), those with batched work, and fused rounds
-        launches[0] += hctl_end->round;
+        // bodies of the device loop (two plan launches each), those with batched work, and fused rounds
+        launches[0] += 2 * hctl_end->round;
         for (int q = 0; q < SFFT_NKCLASS; ++q)
           launches[q] += launch_batched_[q] * hctl_end->bodies_batched + launch_fused_[q] * hctl_end->fused_iters;
       }
@@ -1838,6 +1896,12 @@ class Engine final : public EngineBase {
   int64_t rows_max_ = 0;
   int64_t Lmax_ = 2, p_max_ = 2, part_cap_ = 0, hash_total_ = 0, k_max_ = 0, kd_max_ = 0, reg_cap_max_ = 0;
   bool any_dense_ = false;   // some slot takes short rounds' DFT on the tensor cores
+  // registry seed for the next run (set_seed)
+  const int32_t* seed_w_ = nullptr;
+  const double2* seed_a_ = nullptr;
+  int64_t seed_n_ = 0;
+  int seed_round_ = 0;
+  double seed_aref_ = 0.0;
   std::vector<SigCfg> cfg_host_;
   std::vector<void*> allocs_;
   std::vector<cudaEvent_t> events_;

@@ -37,6 +37,7 @@ struct SigCfg {
   int reg_cap, hash_mask, logL_max;
   int empty_rounds;   // rounds in a row with no bin of any set occupied that end the recovery
   int dense_dft;      // rounds of primes up to kDenseMaxP take the tensor-core dense DFT
+  int stall_div;      // > 0: stop (NOT_CONVERGED) after a round that accepted fewer than k* / stall_div bins
   int64_t N, p_max;
   int64_t p_min;      // floor of the prime rule: the i-th prime >= max(ceil(c k*), p_min)
   double tau, rho, delta, sigma;
@@ -146,6 +147,7 @@ struct SlotDesc {
   int fuse_max_len = 0;            // longest Bluestein length run fused (0: the kernel's limit)
   int empty_rounds = 1;            // empty rounds in a row that end the recovery
   int dense_dft = 0;               // short rounds' DFT on the tensor cores (split BF16)
+  int stall_div = 0;               // stop when a round accepts fewer than k* / stall_div bins
   std::vector<int> shift_blocks;   // block sizes of the shifted sets (block form)
   double tau, rho, delta, sigma;
   int max_rounds;
@@ -172,6 +174,12 @@ class EngineBase {
   virtual cudaError_t step_dft(int64_t p, int n_rows, const void* y, void* Y_out) = 0;
   virtual cudaError_t step_classify(int64_t p, const int64_t* u, const void* Y, double eta, int64_t cap,
                                     int32_t* h_out, int32_t* w_out, double2* a_out, int64_t* n_out, int* err) = 0;
+  // The next run() of a one-slot engine starts from a registry of n entries (w int32 [n x d],
+  // a complex128 [n], device, read by that run before it writes its outputs), after round0
+  // rounds, with the empty-bin reference a_ref of the run that found them.
+  virtual void set_seed(const int32_t* w, const double2* a, int64_t n, int round0, double a_ref) = 0;
+  // slot 0's rounds run and empty-bin reference A_ref after the last run()
+  virtual cudaError_t last_state(int* rounds, double* a_ref) = 0;
   virtual size_t device_bytes() const = 0;
   virtual int64_t max_prime() const = 0;
   virtual int64_t mode_capacity() const = 0;

@@ -93,6 +93,10 @@ __device__ void plan_signal(const PlanArgs& a, const SigCfg& c, SigRun& r, const
     } else if (r.err) {
       r.active = 0;
       r.status = (r.err & kErrTimeout) ? SFFT_ERR_TIMEOUT : SFFT_ERR_CAPACITY;
+    } else if (c.stall_div > 0 && r.round >= 2 &&
+               (int64_t)r.n_acc * c.stall_div < max((int64_t)c.k - r.n_live, (int64_t)1)) {
+      r.active = 0;   // the round found almost none of the modes left: hand over (see stall_div)
+      r.status = SFFT_ERR_NOT_CONVERGED;
     } else if (r.round >= c.max_rounds || r.round >= a.hard_rounds) {
       r.active = 0;
       r.status = SFFT_ERR_NOT_CONVERGED;

@@ -1,11 +1,13 @@
 """The precision study of the d = 20, N = 2^20 workload (|a| log-uniform in [1e-2, 1e2]), on the GPU.
 
-Three arithmetic policies of the same method on the same signal:
+Four arithmetic policies of the same method on the same signal:
   - fp64:          every step in double;
   - fp32:          float sampling and Bluestein DFT, phase ratio, read-out and coefficient in
                    double (the AUTO policy above N = 2^14);
   - fp32_bf16dft:  as fp32, with the DFT of rounds of p <= 8191 a split-BF16 tensor-core
-                   contraction (FP32 accumulation) instead of Bluestein.
+                   contraction (FP32 accumulation) instead of Bluestein;
+  - fp32_then_fp64: the fp32 rounds until a round accepts fewer than k* / 64 bins, then double
+                   rounds continuing from the float registry.
 For each: the exact-recovery rate (planted modes found / k), false positives (found modes not
 planted), the relative coefficient error of the modes found against the planted values and
 against a reference, status, rounds and GPU time of one execute.  At k = 100 000 the reference
@@ -28,7 +30,8 @@ from .inputs import WORKLOADS, draw_signal
 
 ARMS = (("fp64", "all FP64"),
         ("fp32", "FP32 sampling + Bluestein DFT, FP64 ratio"),
-        ("fp32_bf16dft", "FP32 sampling, split-BF16 tensor-core DFT (p <= 8191) / FP32 Bluestein"))
+        ("fp32_bf16dft", "FP32 sampling, split-BF16 tensor-core DFT (p <= 8191) / FP32 Bluestein"),
+        ("fp32_then_fp64", "FP32 rounds until they stall, then FP64 rounds from the float registry"))
 
 
 def compare(freqs, coeffs, ref_freqs, ref_coeffs):

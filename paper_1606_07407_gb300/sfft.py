@@ -15,7 +15,8 @@ import torch
 
 from . import build as _build
 
-PREC = {"fp32": 0, "auto": 0, "fp32_fp64ratio": 1, "fp32_only": 2, "fp64": 3, "fp32_bf16dft": 4}
+PREC = {"fp32": 0, "auto": 0, "fp32_fp64ratio": 1, "fp32_only": 2, "fp64": 3, "fp32_bf16dft": 4,
+        "fp32_then_fp64": 5}
 STATUS = {0: "ok", 1: "invalid argument", 2: "not converged", 3: "capacity exceeded",
           4: "beyond phase resolution", 5: "more modes than k", 6: "cuda error", 7: "device wait timed out"}
 MAX_ROUNDS = 256

@@ -945,3 +945,51 @@ def test_recovery_with_the_dense_bf16_dft_matches_oracle(sfft):
              + (12 * DENSE_FLUSH * 2.0 ** -23) * np.abs(ref.coeffs)) / np.abs(ref.coeffs)
     print(f"split-BF16 DFT recovery: max rel coefficient error {rel.max():.3e}, median {np.median(rel):.3e}")
     assert np.all(rel < bound)
+
+
+# ------------------------------------------------------------------ float rounds, then double rounds
+
+def test_float_then_double_recovers_the_precision_stress_shape(sfft):
+    # d = 20, N = 2^20, |a| log-uniform in [1e-2, 1e2], k = 1000: float rounds alone read only the
+    # modes of |a| >~ 1 and stall (about 40% found); the policy hands the float registry to double
+    # rounds, which find the rest and cancel float false positives: the planted set exactly, the
+    # coefficients of the float-found modes within the float tolerance, the others at double's
+    wl = WORKLOADS["d20_N1048576_k100000"]
+    sig = draw_signal(wl.d, wl.N, 1000, wl.seed + 100, wl.r_dist, wl.r_lo, wl.r_hi)
+    plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=wl.blocks, precision="fp32_then_fp64")
+    f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N))
+    gf, ga = sfft.sort_result(_np(f), _np(a))
+    order = np.lexsort(sig.freqs.T[::-1])
+    assert status == 0 and np.array_equal(gf, sig.freqs[order].astype(np.int64))
+    assert np.max(np.abs(ga - sig.coeffs[order]) / np.abs(sig.coeffs[order])) < FP32_COEFF_TOL
+    ref = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, wl.blocks, residual="bins", estimator="mean")
+    assert np.array_equal(gf, ref.freqs)
+    assert np.max(np.abs(ga - ref.coeffs) / np.abs(ref.coeffs)) < FP32_COEFF_TOL
+    fp32 = sfft.Plan(sig.d, sig.N, sig.k, blocks=wl.blocks, precision="fp32", max_rounds=24)
+    f32, _, st32, _ = fp32.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N), allow=(2,))
+    assert st32 == 2 and f32.shape[0] < sig.k           # float alone does not recover it
+    # the double rounds continue the round counter: their primes are new ones
+    assert len(stats["p"]) == stats["rounds"] and all(p > 0 for p in stats["p"])
+
+
+def test_float_then_double_equals_float_where_float_suffices(sfft):
+    # the d = 5 workload converges in the float rounds: the policy returns their result (the same
+    # set and primes; coefficients to the float tolerance, since float atomics add in any order)
+    wl = WORKLOADS["d5_N1024_k1000"]
+    sig = wl.signal(seed_offset=31)
+    got = []
+    for prec in ("fp32", "fp32_then_fp64"):
+        plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=wl.blocks, precision=prec)
+        f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N))
+        assert status == 0
+        got.append((sfft.sort_result(_np(f), _np(a)), stats["p"]))
+    assert np.array_equal(got[0][0][0], got[1][0][0])
+    assert np.max(np.abs(got[0][0][1] - got[1][0][1]) / np.abs(got[0][0][1])) < FP32_COEFF_TOL
+    assert got[0][1] == got[1][1]
+
+
+def test_float_then_double_is_refused_in_a_batch(sfft):
+    plan = sfft.Plan(2, 1024, 16, precision="fp32_then_fp64")
+    with pytest.raises(sfft.SfftError) as err:
+        sfft.Batch([plan])
+    assert err.value.status == 1
