@@ -62,14 +62,21 @@ typedef enum {
  * coefficients' own errors stay: coefficients of the modes found in float keep float's error
  * (the float policies' tolerance), the others double's.  opts.tau and delta apply to the float
  * rounds, the double rounds take the FP64 ones.  Plain form only: a batch of such plans is
- * INVALID_ARG. */
+ * INVALID_ARG.
+ * DF64: as FP64, except that sampling (Alg. 2's black-box evaluation, the bulk of the work) runs
+ * in double-float on the FP32 pipe: each value a pair of floats hi + lo (about 48 significant
+ * bits), products exact through FMA and sums through two-sum, the samples written in double; the
+ * DFT, ratio test, read-out and coefficients stay in double.  On GPUs whose FP64 rate is a small
+ * fraction of FP32 this is the faster way to double-like accuracy.  Batches of DF64 plans count
+ * as FP64 (they may share a batch only with each other). */
 typedef enum {
   SFFT_PREC_AUTO = 0,
   SFFT_PREC_FP32_FP64RATIO = 1,
   SFFT_PREC_FP32 = 2,
   SFFT_PREC_FP64 = 3,
   SFFT_PREC_FP32_BF16DFT = 4,
-  SFFT_PREC_FP32_THEN_FP64 = 5
+  SFFT_PREC_FP32_THEN_FP64 = 5,
+  SFFT_PREC_DF64 = 6
 } sfft_precision;
 
 typedef struct sfft_plan_s* sfft_plan;

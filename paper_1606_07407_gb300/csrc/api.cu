@@ -103,6 +103,9 @@ struct sfft_batch_s {
   std::unique_ptr<EngineBase> eng;
 };
 
+// policies whose plans run on the double engine
+inline bool double_engine(int prec) { return prec == SFFT_PREC_FP64 || prec == SFFT_PREC_DF64; }
+
 extern "C" {
 
 int sfft_last_cuda_error(void) { return g_last_cuda_error; }
@@ -129,9 +132,9 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
   sfft_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  if (o.precision < SFFT_PREC_AUTO || o.precision > SFFT_PREC_FP32_THEN_FP64) return SFFT_ERR_INVALID_ARG;
+  if (o.precision < SFFT_PREC_AUTO || o.precision > SFFT_PREC_DF64) return SFFT_ERR_INVALID_ARG;
   if (o.box_lo > 0 || o.box_lo < -N) return SFFT_ERR_INVALID_ARG;
-  const bool fp64 = o.precision == SFFT_PREC_FP64;
+  const bool fp64 = o.precision == SFFT_PREC_FP64 || o.precision == SFFT_PREC_DF64;
   if (!fp64 && N > (1LL << 23)) return SFFT_ERR_PRECISION;
   if (o.tau < 0 || o.rho < 0 || o.delta < 0 || o.delta >= 0.5 || o.noise_sigma < 0 || o.max_rounds < 0)
     return SFFT_ERR_INVALID_ARG;
@@ -165,6 +168,7 @@ sfft_status sfft_plan_create(int d, int64_t N, int64_t k, const sfft_pschedule* 
                           o.precision == SFFT_PREC_FP32_THEN_FP64;
   D.ratio64 = (o.precision == SFFT_PREC_FP32_FP64RATIO || fp64 || (auto_ratio && N > (1LL << 14))) ? 1 : 0;
   D.dense_dft = o.precision == SFFT_PREC_FP32_BF16DFT ? 1 : 0;
+  D.df_sample = o.precision == SFFT_PREC_DF64 ? 1 : 0;
   D.coef_mean = o.coef_set0 ? 0 : 1;
   D.peel_bins = o.residual == SFFT_RESIDUAL_BINS ? 1 : 0;
   D.tau = o.tau > 0 ? o.tau : (fp64 ? 1e-7 : 1e-3);
@@ -494,9 +498,10 @@ sfft_status sfft_batch_create(int n, const sfft_plan* plans, void* stream, int g
   bool profile = (graph & SFFT_BATCH_PROFILE) != 0;
   for (int s = 0; s < n; ++s) {
     if (!plans[s] || plans[s]->eng64) return SFFT_ERR_INVALID_ARG;   // FP32_THEN_FP64: plain form only
-    const bool fp64 = plans[s]->prec == SFFT_PREC_FP64;
+    const bool fp64 = double_engine(plans[s]->prec);
     if (s == 0) B->prec = plans[s]->prec;
-    if ((B->prec == SFFT_PREC_FP64) != fp64) return SFFT_ERR_INVALID_ARG;
+    if (double_engine(B->prec) != fp64) return SFFT_ERR_INVALID_ARG;
+    if (fp64 && plans[s]->prec != B->prec) return SFFT_ERR_INVALID_ARG;   // DF64 with DF64 only
     slots.push_back(plans[s]->desc);
     B->d.push_back(plans[s]->desc.d);
     B->k.push_back(plans[s]->desc.k);
@@ -505,7 +510,7 @@ sfft_status sfft_batch_create(int n, const sfft_plan* plans, void* stream, int g
   }
   EngineBase* e = nullptr;
   sfft_status st = cuda_status(
-      engine_create(B->prec == SFFT_PREC_FP64, slots, (cudaStream_t)stream, profile, (graph & SFFT_BATCH_GRAPH) != 0,
+      engine_create(double_engine(B->prec), slots, (cudaStream_t)stream, profile, (graph & SFFT_BATCH_GRAPH) != 0,
                     &e));
   if (st != SFFT_OK) return st;
   B->eng.reset(e);

@@ -375,20 +375,30 @@ __global__ void k_tables(int n, const SigCfg* __restrict__ cfg, const SigRun* __
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     if (e < ntab) {
       const int s = find_slot(sc.v[SC_TAB], n, e);
-      table_entry<T>(run[s].p, run[s].mod_m, e - sc.v[SC_TAB][s], tab + cfg[s].tab_off);
+      const int64_t m = e - sc.v[SC_TAB][s];
+      table_entry<T>(run[s].p, run[s].mod_m, m, tab + cfg[s].tab_off);
+      if constexpr (sizeof(T) == 8) {
+        // the sampler's roots W[m] in double-float (the chirp, read by the DFT, stays double)
+        if (cfg[s].df_sample) df_pack_inplace(tab + cfg[s].tab_off + m);
+      }
       continue;
     }
     const int64_t em = e - ntab;
     const int s = find_slot(sc.v[SC_MODE], n, em);
-    mode_entry<T>(cfg[s], run[s], s, (int)(em - sc.v[SC_MODE][s]), ubuf, sig_w, sig_a, tw, regw, rega, regtw, alpha,
-                  gam, Cm);
+    const int j = (int)(em - sc.v[SC_MODE][s]);
+    mode_entry<T>(cfg[s], run[s], s, j, ubuf, sig_w, sig_a, tw, regw, rega, regtw, alpha, gam, Cm);
+    if constexpr (sizeof(T) == 8) {
+      if (cfg[s].df_sample)
+        for (int nn = 0; nn < cfg[s].n_sets; ++nn) df_pack_inplace(Cm + cfg[s].C_off + j + (int64_t)nn * cfg[s].Kmax);
+    }
   }
 }
 
 // ------------------------------------------------------------------ sampling
 
-// Persistent sampling kernel for the signals whose set groups hold NS sets.
-template <typename T, int NS>
+// Persistent sampling kernel for the signals whose set groups hold NS sets; DF (double engine
+// only) samples in double-float arithmetic, a policy every slot of an engine shares.
+template <typename T, int NS, bool DF>
 __global__ void __launch_bounds__(kSampleThreads, 2) k_sample(int n, const SigCfg* __restrict__ cfg,
                                                            const SigRun* __restrict__ run, RoundCtl* ctl, Scans sc,
                                                            const int32_t* __restrict__ alpha,
@@ -412,8 +422,8 @@ __global__ void __launch_bounds__(kSampleThreads, 2) k_sample(int n, const SigCf
     const int64_t rest = local / r.n_xt;
     const int g = (int)(rest % r.groups);
     const int split = (int)(rest / r.groups);
-    sample_tile<T, NS>(sm, c, r, xt, g, split, alpha + c.mode_off, gam + c.mode_off, Cm + c.C_off,
-                      tab + r.tab_at, part);
+    sample_tile<T, NS, DF>(sm, c, r, xt, g, split, alpha + c.mode_off, gam + c.mode_off, Cm + c.C_off,
+                           tab + r.tab_at, part);
   }
 }
 
@@ -467,9 +477,13 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_filter(int n, const SigCfg* 
 // The tables and filter spectrum of round 1's prime, made once when the engine is created (the
 // prime is fixed by the plan: the first prime >= max(c k, p_min), or the list's first).
 template <typename T>
-__global__ void k_tables_one(int64_t p, unsigned long long mod_m, c2<T>* __restrict__ t) {
-  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < p; m += (int64_t)gridDim.x * blockDim.x)
+__global__ void k_tables_one(int64_t p, unsigned long long mod_m, c2<T>* __restrict__ t, int df) {
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < p; m += (int64_t)gridDim.x * blockDim.x) {
     table_entry<T>(p, mod_m, m, t);
+    if constexpr (sizeof(T) == 8) {
+      if (df) df_pack_inplace(t + m);
+    }
+  }
 }
 
 template <typename T>
@@ -1055,6 +1069,8 @@ class Engine final : public EngineBase {
       c.empty_rounds = std::max(1, d.empty_rounds);
       c.dense_dft = (sizeof(T) == 4 && d.dense_dft) ? 1 : 0;
       c.stall_div = d.stall_div;
+      c.df_sample = (sizeof(T) == 8 && d.df_sample) ? 1 : 0;
+      if (c.df_sample) any_df_ = true;
       if (c.dense_dft) any_dense_ = true;
       c.max_rounds = d.max_rounds;
       c.n_dirs = d.n_dirs;
@@ -1250,7 +1266,8 @@ class Engine final : public EngineBase {
       const int64_t p1 = pre_p[q];
       const int L1 = bluestein_length(2 * p1 - 1);
       C2* t0 = (C2*)tab_ + pre_tab[q];
-      k_tables_one<T><<<(int)std::min<int64_t>((p1 + 255) / 256, 1024), 256, 0, st_>>>(p1, ~0ull / (uint64_t)p1, t0);
+      k_tables_one<T><<<(int)std::min<int64_t>((p1 + 255) / 256, 1024), 256, 0, st_>>>(p1, ~0ull / (uint64_t)p1, t0,
+                                                                                        any_df_ ? 1 : 0);
       ECHK(cudaGetLastError());
       k_filter_one<T><<<1, std::max(32, fft_threads<C2>(L1)), (size_t)(L1 + L1 / 32) * sizeof(C2), st_>>>(
           p1, L1, t0 + p1, tw_src(), (C2*)bhat_ + pre_bhat[q]);
@@ -1370,10 +1387,17 @@ class Engine final : public EngineBase {
   cudaError_t launch_samples(int64_t* launches) {
     for (int ns = 1; ns <= kMaxSetGroup; ++ns) {
       if (!(ns_mask_ & (1u << (ns - 1)))) continue;
-#define SFFT_SAMPLE(NSV)                                                                                        \
-  case NSV:                                                                                                     \
-    k_sample<T, NSV><<<2 * n_sm_, kSampleThreads, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, alpha_, gam_, (C2*)Cm_, \
-                                                            (C2*)tab_, (C2*)part_);                             \
+#define SFFT_SAMPLE(NSV)                                                                                      \
+  case NSV:                                                                                                   \
+    if constexpr (sizeof(T) == 8) {                                                                           \
+      if (any_df_) {                                                                                          \
+        k_sample<T, NSV, true><<<2 * n_sm_, kSampleThreads, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, alpha_,   \
+                                                                      gam_, (C2*)Cm_, (C2*)tab_, (C2*)part_); \
+        break;                                                                                                \
+      }                                                                                                       \
+    }                                                                                                         \
+    k_sample<T, NSV, false><<<2 * n_sm_, kSampleThreads, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, alpha_, gam_, \
+                                                                   (C2*)Cm_, (C2*)tab_, (C2*)part_);         \
     break;
       switch (ns) {
         SFFT_SAMPLE(1)
@@ -1896,6 +1920,7 @@ class Engine final : public EngineBase {
   int64_t rows_max_ = 0;
   int64_t Lmax_ = 2, p_max_ = 2, part_cap_ = 0, hash_total_ = 0, k_max_ = 0, kd_max_ = 0, reg_cap_max_ = 0;
   bool any_dense_ = false;   // some slot takes short rounds' DFT on the tensor cores
+  bool any_df_ = false;      // the slots sample in double-float (tables and coefficients packed for it)
   // registry seed for the next run (set_seed)
   const int32_t* seed_w_ = nullptr;
   const double2* seed_a_ = nullptr;

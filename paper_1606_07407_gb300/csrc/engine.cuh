@@ -38,6 +38,7 @@ struct SigCfg {
   int empty_rounds;   // rounds in a row with no bin of any set occupied that end the recovery
   int dense_dft;      // rounds of primes up to kDenseMaxP take the tensor-core dense DFT
   int stall_div;      // > 0: stop (NOT_CONVERGED) after a round that accepted fewer than k* / stall_div bins
+  int df_sample;      // FP64 engine: sampling in double-float on the FP32 pipe (roots, coefficients packed)
   int64_t N, p_max;
   int64_t p_min;      // floor of the prime rule: the i-th prime >= max(ceil(c k*), p_min)
   double tau, rho, delta, sigma;
@@ -148,6 +149,7 @@ struct SlotDesc {
   int empty_rounds = 1;            // empty rounds in a row that end the recovery
   int dense_dft = 0;               // short rounds' DFT on the tensor cores (split BF16)
   int stall_div = 0;               // stop when a round accepts fewer than k* / stall_div bins
+  int df_sample = 0;               // FP64 engine: double-float sampling
   std::vector<int> shift_blocks;   // block sizes of the shifted sets (block form)
   double tau, rho, delta, sigma;
   int max_rounds;

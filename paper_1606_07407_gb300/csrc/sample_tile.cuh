@@ -13,6 +13,8 @@
 // the first factor shared by the 32 lanes of a row, the second by the rows of a lane.
 #pragma once
 
+#include <type_traits>
+
 #include "engine_kernels.cuh"
 
 namespace sfft {
@@ -106,11 +108,103 @@ __device__ __forceinline__ void accumulate_rows(const SampleSmem<T, NS>& sm, int
   }
 }
 
+// ---- double-float arithmetic on the FP32 pipe: a value is hi + lo with |lo| <= ulp(hi) / 2 (a
+// float2 (hi, lo)), about 48 significant bits.  Products are exact through an FMA (a b - fl(a b)
+// is a float), sums through Knuth's two-sum; the round-to-nearest intrinsics keep the compiler
+// from contracting the error terms away.
+__device__ __forceinline__ float2 df_quick(float s, float e) {   // |e| <= |s|: renormalise
+  const float h = __fadd_rn(s, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  return df_quick(p, e);
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  return df_quick(s, e);
+}
+__device__ __forceinline__ float2 df_sub(float2 a, float2 b) { return df_add(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ double df_value(float2 a) { return (double)a.x + (double)a.y; }
+// a complex value staged as double-float: (re hi, re lo, im hi, im lo) in the 16 bytes of a double2
+__device__ __forceinline__ float4 df_pack(double2 v) {
+  const float rh = (float)v.x, ih = (float)v.y;
+  return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+
+__device__ __forceinline__ void df_pack_inplace(double2* v) {
+  *reinterpret_cast<float4*>(v) = df_pack(*v);
+}
+
+// accumulate_chunk in double-float (the FP64 engine's double-float sampling): the staged roots and
+// coefficients hold df_pack values, the sums P1..P4 are double-float
+template <int NS, int RP, int Q>
+__device__ __forceinline__ void accumulate_chunk_df(const SampleSmem<double, NS>& sm, int lane, int wrow,
+                                                    float2 (&tot)[RP][NS][4]) {
+  float2 acc[Q][NS][4];
+#pragma unroll
+  for (int qq = 0; qq < Q; ++qq)
+#pragma unroll
+    for (int nn = 0; nn < NS; ++nn)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[qq][nn][k] = make_float2(0.0f, 0.0f);
+  for (int jj = 0; jj < kSampleChunk; ++jj) {
+    const float4 L = reinterpret_cast<const float4&>(sm.st.Ls[0][jj][lane]);
+    float2 Er[Q], Ei[Q];
+#pragma unroll
+    for (int qq = 0; qq < Q; ++qq) {
+      const float4 U = reinterpret_cast<const float4&>(sm.st.Us[0][jj][wrow * RP + qq]);
+      const float2 ur = make_float2(U.x, U.y), ui = make_float2(U.z, U.w);
+      const float2 lr = make_float2(L.x, L.y), li = make_float2(L.z, L.w);
+      Er[qq] = df_sub(df_mul(ur, lr), df_mul(ui, li));
+      Ei[qq] = df_add(df_mul(ur, li), df_mul(ui, lr));
+    }
+#pragma unroll
+    for (int nn = 0; nn < NS; ++nn) {
+      const float4 C = reinterpret_cast<const float4&>(sm.st.Cs[0][jj][nn]);
+      const float2 cr = make_float2(C.x, C.y), ci = make_float2(C.z, C.w);
+#pragma unroll
+      for (int qq = 0; qq < Q; ++qq) {
+        acc[qq][nn][0] = df_add(acc[qq][nn][0], df_mul(cr, Er[qq]));   // P1: c_r e_r
+        acc[qq][nn][1] = df_add(acc[qq][nn][1], df_mul(ci, Ei[qq]));   // P2: c_i e_i
+        acc[qq][nn][2] = df_add(acc[qq][nn][2], df_mul(cr, Ei[qq]));   // P3: c_r e_i
+        acc[qq][nn][3] = df_add(acc[qq][nn][3], df_mul(ci, Er[qq]));   // P4: c_i e_r
+      }
+    }
+  }
+#pragma unroll
+  for (int qq = 0; qq < Q; ++qq)
+#pragma unroll
+    for (int nn = 0; nn < NS; ++nn)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) tot[qq][nn][k] = df_add(tot[qq][nn][k], acc[qq][nn][k]);
+}
+
+template <int NS, int RP>
+__device__ __forceinline__ void accumulate_rows_df(const SampleSmem<double, NS>& sm, int lane, int wrow, int nq,
+                                                   float2 (&tot)[RP][NS][4]) {
+  switch (nq) {
+    case 1: if constexpr (RP > 1) accumulate_chunk_df<NS, RP, 1>(sm, lane, wrow, tot); break;
+    case 2: if constexpr (RP > 2) accumulate_chunk_df<NS, RP, 2>(sm, lane, wrow, tot); break;
+    case 3: if constexpr (RP > 3) accumulate_chunk_df<NS, RP, 3>(sm, lane, wrow, tot); break;
+    case 4: if constexpr (RP > 4) accumulate_chunk_df<NS, RP, 4>(sm, lane, wrow, tot); break;
+    default: break;
+  }
+}
+
 // One tile: 32 * kSampleWarps * RP positions of the half line (each giving the samples x and
 // p - x) x the sets of one group x the modes of one split.  Each 32-mode chunk is summed into
 // fresh accumulators that are then added to the running totals (blocked summation), which
 // keeps the float rounding of long mode sums near that of the individual terms.
-template <typename T, int NS>
+// DF (T = double only): the staged data hold df_pack values and the sums run in double-float on
+// the FP32 pipe (one mode group, one stage, as in double); the samples are written in double.
+template <typename T, int NS, bool DF = false>
 __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun& r, int xt, int g, int split,
                             const int32_t* __restrict__ alpha, const int32_t* __restrict__ gam,
                             const c2<T>* __restrict__ Cm, const c2<T>* __restrict__ W, c2<T>* __restrict__ part) {
@@ -170,11 +264,17 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
     cp_async_commit();
   };
 
-  T tot[RP][NS][4];
+  using Acc = std::conditional_t<DF, float2, T>;
+  Acc tot[RP][NS][4];
 #pragma unroll
   for (int q = 0; q < RP; ++q)
 #pragma unroll
-    for (int nn = 0; nn < NS; ++nn) tot[q][nn][0] = tot[q][nn][1] = tot[q][nn][2] = tot[q][nn][3] = (T)0;
+    for (int nn = 0; nn < NS; ++nn)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if constexpr (DF) tot[q][nn][k] = make_float2(0.0f, 0.0f);
+        else tot[q][nn][k] = (T)0;
+      }
 
   if (nchunks > 0) {
     if (tid < kSampleChunk) {
@@ -198,8 +298,13 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
       if (q + 1 < nchunks) issue_data(q + 1, b ^ 1);                     // gathers of the next chunk
       if (tid < kSampleChunk && q + 2 < nchunks) load_index(q + 2, &al_n, &ga_n);   // indices two ahead
     }
-    if (nq == RP) accumulate_chunk<T, NS, RP, RP>(sm, b, grp, G, lane, wrow, tot);
-    else if (nq > 0) accumulate_rows<T, NS, RP>(sm, b, grp, G, lane, wrow, nq, tot);
+    if constexpr (DF) {
+      if (nq == RP) accumulate_chunk_df<NS, RP, RP>(sm, lane, wrow, tot);
+      else if (nq > 0) accumulate_rows_df<NS, RP>(sm, lane, wrow, nq, tot);
+    } else {
+      if (nq == RP) accumulate_chunk<T, NS, RP, RP>(sm, b, grp, G, lane, wrow, tot);
+      else if (nq > 0) accumulate_rows<T, NS, RP>(sm, b, grp, G, lane, wrow, nq, tot);
+    }
     if (S == 2) {
       // stage b is free again: it takes the indices of chunk q + 2
       if (tid < kSampleChunk && q + 2 < nchunks) put_index(b, al_n, ga_n);
@@ -218,6 +323,7 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
       __syncthreads();
     }
   }
+  if constexpr (!DF) {
   if (G > 1) {
     // add the mode groups' sums pairwise into group 0 through the (now free) staging memory:
     // at each step the upper half of the remaining groups hands its sums to the lower half
@@ -247,6 +353,7 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
     }
     if (grp > 0) return;
   }
+  }
   C2* out = part + r.part_off;
 #pragma unroll
   for (int q = 0; q < RP; ++q) {
@@ -257,9 +364,15 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
       for (int nn = 0; nn < NS; ++nn) {
         if (nn < ns_valid) {
           C2* row = out + ((int64_t)split * c.n_sets + n0 + nn) * p;
-          const T P1 = tot[q][nn][0], P2 = tot[q][nn][1], P3 = tot[q][nn][2], P4 = tot[q][nn][3];
-          row[x] = mk2(P1 - P2, P3 + P4);
-          if (mirror) row[p - x] = mk2(P1 + P2, P4 - P3);
+          if constexpr (DF) {
+            const float2 P1 = tot[q][nn][0], P2 = tot[q][nn][1], P3 = tot[q][nn][2], P4 = tot[q][nn][3];
+            row[x] = mk2((T)df_value(df_sub(P1, P2)), (T)df_value(df_add(P3, P4)));
+            if (mirror) row[p - x] = mk2((T)df_value(df_add(P1, P2)), (T)df_value(df_sub(P4, P3)));
+          } else {
+            const T P1 = tot[q][nn][0], P2 = tot[q][nn][1], P3 = tot[q][nn][2], P4 = tot[q][nn][3];
+            row[x] = mk2(P1 - P2, P3 + P4);
+            if (mirror) row[p - x] = mk2(P1 + P2, P4 - P3);
+          }
         }
       }
     }

@@ -1,7 +1,8 @@
 """The precision study of the d = 20, N = 2^20 workload (|a| log-uniform in [1e-2, 1e2]), on the GPU.
 
-Four arithmetic policies of the same method on the same signal:
+Five arithmetic policies of the same method on the same signal:
   - fp64:          every step in double;
+  - df64:          as fp64, the sampling in double-float (pairs of floats) on the FP32 pipe;
   - fp32:          float sampling and Bluestein DFT, phase ratio, read-out and coefficient in
                    double (the AUTO policy above N = 2^14);
   - fp32_bf16dft:  as fp32, with the DFT of rounds of p <= 8191 a split-BF16 tensor-core
@@ -29,6 +30,7 @@ import numpy as np
 from .inputs import WORKLOADS, draw_signal
 
 ARMS = (("fp64", "all FP64"),
+        ("df64", "double-float sampling on the FP32 pipe, FP64 DFT, ratio and read-out"),
         ("fp32", "FP32 sampling + Bluestein DFT, FP64 ratio"),
         ("fp32_bf16dft", "FP32 sampling, split-BF16 tensor-core DFT (p <= 8191) / FP32 Bluestein"),
         ("fp32_then_fp64", "FP32 rounds until they stall, then FP64 rounds from the float registry"))
@@ -46,6 +48,7 @@ def compare(freqs, coeffs, ref_freqs, ref_coeffs):
 
 def run_arm(sfft, torch, sig, blocks, prec):
     plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=blocks, precision=prec, graph=True)
+    plan.execute(sfft.Signal(sig.freqs[:1], sig.coeffs[:1], sig.N), capacity=16, allow=(0, 2, 3, 5))   # warm-up
     dev = sfft.Signal(sig.freqs, sig.coeffs, sig.N)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
@@ -56,7 +59,7 @@ def run_arm(sfft, torch, sig, blocks, prec):
     return gf, ga, status, stats["rounds"], ev0.elapsed_time(ev1) / 1e3
 
 
-def study(k: int, blocks, seed_offset: int, oracle: bool, log=print):
+def study(k: int, blocks, seed_offset: int, oracle: bool, arms=None, log=print):
     import torch
     from . import build as B
     B.build()
@@ -66,8 +69,9 @@ def study(k: int, blocks, seed_offset: int, oracle: bool, log=print):
     planted_f = sig.freqs[np.lexsort(sig.freqs.T[::-1])].astype(np.int64)
     planted_a = sig.coeffs[np.lexsort(sig.freqs.T[::-1])]
     planted = set(map(tuple, planted_f.tolist()))
+    arms = list(arms or [a for a, _ in ARMS])
     results = {}
-    for prec, _ in ARMS:
+    for prec in arms:
         gf, ga, status, rounds, secs = run_arm(sfft, torch, sig, blocks, prec)
         found = set(map(tuple, gf.tolist()))
         n_ok, emax, emed = compare(gf, ga, planted_f, planted_a)
@@ -88,12 +92,14 @@ def study(k: int, blocks, seed_offset: int, oracle: bool, log=print):
                              "recovered": len(set(map(tuple, ref_f.tolist())) & planted),
                              "err_vs_planted_max": omax, "err_vs_planted_median": omed}
         ref_name = "FP64 oracle"
-    else:
+    elif "fp64" in results:
         ref_f, ref_a, ref_name = results["fp64"]["_f"], results["fp64"]["_a"], "fp64 arm"
-    for prec, _ in ARMS:
-        n_c, cmax, cmed = compare(results[prec]["_f"], results[prec]["_a"], ref_f, ref_a)
-        results[prec].update(ref=ref_name, common_with_ref=n_c, err_vs_ref_max=cmax, err_vs_ref_median=cmed)
-    for prec, _ in ARMS:
+    else:
+        ref_name = None
+    for prec in arms:
+        if ref_name:
+            n_c, cmax, cmed = compare(results[prec]["_f"], results[prec]["_a"], ref_f, ref_a)
+            results[prec].update(ref=ref_name, common_with_ref=n_c, err_vs_ref_max=cmax, err_vs_ref_median=cmed)
         del results[prec]["_f"], results[prec]["_a"]
     return {"d": sig.d, "N": sig.N, "k": k, "blocks": list(blocks), "r": "log-uniform [1e-2, 1e2]", "arms": results}
 
@@ -103,10 +109,14 @@ def main(argv=None):
     ap.add_argument("--k", type=int, default=100000)
     ap.add_argument("--oracle-k", type=int, default=1000)
     ap.add_argument("--json", default=None)
+    ap.add_argument("--arms", default=",".join(a for a, _ in ARMS), help="comma-separated subset of the arms")
     args = ap.parse_args(argv)
     blocks = WORKLOADS["d20_N1048576_k100000"].blocks
-    out = {"small": study(args.oracle_k, blocks, 100, oracle=True) if args.oracle_k > 0 else None,
-           "full": study(args.k, blocks, 0, oracle=False) if args.k > 0 else None}
+    arms = [a for a in args.arms.split(",") if a]
+    if any(a not in dict(ARMS) for a in arms):
+        ap.error(f"arms must be among {[a for a, _ in ARMS]}")
+    out = {"small": study(args.oracle_k, blocks, 100, oracle=True, arms=arms) if args.oracle_k > 0 else None,
+           "full": study(args.k, blocks, 0, oracle=False, arms=arms) if args.k > 0 else None}
     text = json.dumps(out, indent=1)
     if args.json:
         with open(args.json, "w") as fh:

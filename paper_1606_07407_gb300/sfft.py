@@ -16,7 +16,7 @@ import torch
 from . import build as _build
 
 PREC = {"fp32": 0, "auto": 0, "fp32_fp64ratio": 1, "fp32_only": 2, "fp64": 3, "fp32_bf16dft": 4,
-        "fp32_then_fp64": 5}
+        "fp32_then_fp64": 5, "df64": 6}
 STATUS = {0: "ok", 1: "invalid argument", 2: "not converged", 3: "capacity exceeded",
           4: "beyond phase resolution", 5: "more modes than k", 6: "cuda error", 7: "device wait timed out"}
 MAX_ROUNDS = 256
@@ -225,7 +225,7 @@ class Plan:
             raise ValueError(f"residual must be one of {sorted(RESIDUAL)}")
         self.d, self.N, self.k = int(d), int(N), int(k)
         self.precision = precision
-        self.cdtype = torch.complex128 if precision == "fp64" else torch.complex64
+        self.cdtype = torch.complex128 if precision in ("fp64", "df64") else torch.complex64
         self._keep = []
         ps = _PSchedule(0, 0, None, int(p_min), prime_factor_eighths(c))
         if primes is not None and len(primes):

@@ -19,6 +19,25 @@ pytestmark = pytest.mark.gpu
 
 FP32_COEFF_TOL = 1e-5
 FP64_COEFF_TOL = 1e-12
+# DF64 (double-float sampling, about 48 significant bits): a sample's error is at most about
+# 2^-46 of sum |a| per operation on its path (8 per term, then the additions of a 32-mode chunk
+# and of the K / 32 chunk sums); a coefficient from p samples then errs by about that over
+# sqrt(p) |a|, so 1e-10 relative leaves a wide margin at the test sizes
+DF64_COEFF_TOL = 1e-10
+
+
+def _df64_sample_tol(K, coeffs):
+    return (8 + 32 + math.ceil(K / 32)) * 2.0 ** -46 * np.sum(np.abs(coeffs))
+
+
+def _double(prec):
+    return prec in ("fp64", "df64")
+
+
+def _sample_tol(prec, K, coeffs):
+    if prec == "df64":
+        return _df64_sample_tol(K, coeffs)
+    return (2.0 ** -20 if prec == "fp32" else 2.0 ** -48) * np.sum(np.abs(coeffs))
 # the FP64 policy ends a recovery after one empty round (its read-outs do not slip); the float
 # policies after one per line direction (the oracle's default)
 FP64_EMPTY_ROUNDS = 1
@@ -41,7 +60,7 @@ def _np(t):
 
 # ------------------------------------------------------------------ kernel (a)
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "df64"])
 @pytest.mark.parametrize("d,N,K,p,blocks", [
     (2, 1024, 16, 83, (1, 1)),        # one tile, one mode chunk
     (3, 4096, 100, 1031, (2, 1)),      # 3 tiles (ragged), 4 mode chunks (ragged)
@@ -55,9 +74,7 @@ def test_samples_match_oracle(sfft, prec, d, N, K, p, blocks):
         u = [int(v) for v in O.unwrap_vector(d, N, blocks, m)]
         y = _np(plan.sample(p, u, torch.tensor(sig.freqs), torch.tensor(sig.coeffs)))
         ref = O.sample_sets(sig.freqs, sig.coeffs, p, u, N)
-        scale = np.sum(np.abs(sig.coeffs))
-        tol = (2.0 ** -20 if prec == "fp32" else 2.0 ** -48) * scale
-        assert np.max(np.abs(y - ref)) < tol
+        assert np.max(np.abs(y - ref)) < _sample_tol(prec, K, sig.coeffs)
 
 
 def test_samples_registry_sign_and_empty(sfft):
@@ -241,9 +258,9 @@ def _run_both(sfft, sig, blocks=None, prec="fp32", dirs=None, primes=None, box_l
                      residual=residual, fuse=fuse, graph=graph)
     f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N))
     gf, ga = sfft.sort_result(_np(f), _np(a))
-    th = O.Thresholds() if prec == "fp64" else O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
+    th = O.Thresholds() if _double(prec) else O.Thresholds(tau=1e-3, rho=2.0 ** -17, delta=0.25)
     ref = O.multi_phaseshift(sig.freqs, sig.coeffs, sig.d, sig.N, sig.k, blocks, th=th, dirs=dirs,
-                             empty_rounds=FP64_EMPTY_ROUNDS if prec == "fp64" else None,
+                             empty_rounds=FP64_EMPTY_ROUNDS if _double(prec) else None,
                              primes=primes, box_lo=box_lo, estimator="mean", residual=residual)
     return gf, ga, status, stats, ref
 
@@ -349,11 +366,13 @@ def test_recovery_shapes(sfft, case):
     _assert_parity(sig, *_run_both(sfft, sig, blocks, dirs=dirs, box_lo=sig.box_lo), FP32_COEFF_TOL)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("residual", ["bins", "samples"])
-def test_recovery_fp64_policy(sfft, residual):
+def test_recovery_fp64_policy(sfft, residual, prec):
     wl = WORKLOADS["d5_N1024_k1000"]
     sig = draw_signal(5, 1024, 300, seed=31, r_lo=1.0, r_hi=10.0)
-    _assert_parity(sig, *_run_both(sfft, sig, wl.blocks, prec="fp64", residual=residual), FP64_COEFF_TOL)
+    _assert_parity(sig, *_run_both(sfft, sig, wl.blocks, prec=prec, residual=residual),
+                   FP64_COEFF_TOL if prec == "fp64" else DF64_COEFF_TOL)
 
 
 def test_fig2_collision_story_on_gpu(sfft):
@@ -372,7 +391,7 @@ def test_empty_signal(sfft):
     # nothing to find: one empty round per line direction (two blocks) under the float policy,
     # one under FP64
     s = sfft.Signal(np.zeros((0, 3), np.int32), np.zeros(0, np.complex128), 1024)
-    for prec, rounds in (("fp32", 2), ("fp64", 1)):
+    for prec, rounds in (("fp32", 2), ("fp64", 1), ("df64", 1)):
         f, a, status, stats = sfft.Plan(3, 1024, 10, blocks=(2, 1), precision=prec).execute(s)
         assert status == 0 and f.shape[0] == 0 and stats["rounds"] == rounds
 
@@ -565,7 +584,7 @@ def test_noisy_d10_workload_full_size(sfft):
 
 # ------------------------------------------------------------------ block shifts (Alg. 2 as printed)
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "df64"])
 def test_block_shift_samples_match_oracle(sfft, prec):
     d, N, K, p, blocks = 5, 6, 300, 1031, (2, 3)
     sig = draw_signal(d, N, K, seed=71, r_lo=1.0, r_hi=10.0, box_lo=-3)
@@ -574,8 +593,7 @@ def test_block_shift_samples_match_oracle(sfft, prec):
     u = [int(v) for v in O.unwrap_vector(d, N, blocks, 1)]
     y = _np(plan.sample(p, u, torch.tensor(sig.freqs), torch.tensor(sig.coeffs)))
     ref = O.sample_sets(sig.freqs, sig.coeffs, p, u, N, shift="block", blocks=blocks)
-    tol = (2.0 ** -20 if prec == "fp32" else 2.0 ** -48) * np.sum(np.abs(sig.coeffs))
-    assert y.shape == ref.shape and np.max(np.abs(y - ref)) < tol
+    assert y.shape == ref.shape and np.max(np.abs(y - ref)) < _sample_tol(prec, K, sig.coeffs)
 
 
 @pytest.mark.parametrize("case", ["d6_auto", "d6_fp64", "paper_d100_fp64"])
@@ -600,7 +618,7 @@ TILT_32 = (84, 13, 85)        # base, height, hypo: base > 2 N for N = 32 (Theor
 TILT_1024 = (2112, 65, 2113)  # base > 2 N for N = 1024
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "df64"])
 def test_tilt_samples_match_oracle(sfft, prec):
     N, K, p = 32, 300, 1031
     sig = draw_signal(2, N, K, seed=81, r_lo=1.0, r_hi=10.0)
@@ -610,8 +628,7 @@ def test_tilt_samples_match_oracle(sfft, prec):
         u = [int(v) for v in u]
         y = _np(plan.sample(p, u, torch.tensor(sig.freqs), torch.tensor(sig.coeffs)))
         ref = O.sample_sets(sig.freqs, sig.coeffs, p, u, N, shift="tilt", tilt=TILT_32)
-        tol = (2.0 ** -20 if prec == "fp32" else 2.0 ** -48) * np.sum(np.abs(sig.coeffs))
-        assert y.shape == ref.shape and np.max(np.abs(y - ref)) < tol
+        assert y.shape == ref.shape and np.max(np.abs(y - ref)) < _sample_tol(prec, K, sig.coeffs)
 
 
 @pytest.mark.parametrize("case", ["N32_fp32", "N32_fp32_unfused", "N32_signed_fp32", "N1024_signed_fp64",
@@ -992,4 +1009,62 @@ def test_float_then_double_is_refused_in_a_batch(sfft):
     plan = sfft.Plan(2, 1024, 16, precision="fp32_then_fp64")
     with pytest.raises(sfft.SfftError) as err:
         sfft.Batch([plan])
+    assert err.value.status == 1
+
+
+# ------------------------------------------------------------------ double-float sampling
+
+def test_double_float_samples_at_the_precision_stress_size(sfft):
+    # d = 20, N = 2^20, K = 100000 modes of |a| log-uniform in [1e-2, 1e2], the first prime of the
+    # workload's schedule: 48 sampled columns of all 21 sets against the oracle, within the
+    # double-float bound, and at least 2^16 times closer than float sampling's bound
+    wl = WORKLOADS["d20_N1048576_k100000"]
+    sig = wl.signal()
+    plan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, precision="df64")
+    p = 500009
+    u = [int(v) for v in O.unwrap_vector(wl.d, wl.N, wl.blocks, 3)]
+    y = _np(plan.sample(p, u, torch.tensor(sig.freqs), torch.tensor(sig.coeffs)))
+    xs = np.array(sorted(set(Stream(9).integers(46, 0, p).tolist()) | {0, p - 1}))
+    ref = O.sample_sets(sig.freqs, sig.coeffs, p, u, wl.N, x_values=xs)
+    err = np.max(np.abs(y[:, xs] - ref))
+    print(f"double-float samples, K = 1e5: max |err| {err:.3e}, sum |a| {np.sum(np.abs(sig.coeffs)):.3e}")
+    assert err < _df64_sample_tol(wl.k, sig.coeffs)
+    assert err < 2.0 ** -16 * _sample_tol("fp32", wl.k, sig.coeffs)
+
+
+def test_double_float_recovers_the_precision_stress_shape(sfft):
+    # the d = 20, N = 2^20 log-uniform shape at k = 1000, where the float policies stall: the
+    # planted set exactly, the oracle's rounds and primes, coefficients within DF64_COEFF_TOL of the
+    # oracle's
+    wl = WORKLOADS["d20_N1048576_k100000"]
+    sig = draw_signal(wl.d, wl.N, 1000, wl.seed + 100, wl.r_dist, wl.r_lo, wl.r_hi)
+    _assert_parity(sig, *_run_both(sfft, sig, wl.blocks, prec="df64"), DF64_COEFF_TOL)
+
+
+def test_precision_stress_d20_df64_recovers_every_mode(sfft):
+    # the full d = 20 precision-stress workload (k = 10^5) under double-float sampling: every
+    # planted mode, coefficients within 1e-9 relative of the planted values (as FP64)
+    wl = WORKLOADS["d20_N1048576_k100000"]
+    sig = wl.signal()
+    plan = sfft.Plan(wl.d, wl.N, wl.k, blocks=wl.blocks, precision="df64", graph=True)
+    f, a, status, stats = plan.execute(sfft.Signal(sig.freqs, sig.coeffs, sig.N))
+    gf, ga = sfft.sort_result(_np(f), _np(a))
+    order = np.lexsort(sig.freqs.T[::-1])
+    assert status == 0 and np.array_equal(gf, sig.freqs[order])
+    rel = np.abs(ga - sig.coeffs[order]) / np.abs(sig.coeffs[order])
+    print(f"df64 d20 k=1e5: rounds {stats['rounds']}, max rel coefficient error {rel.max():.3e}")
+    assert np.max(rel) < 1e-9
+
+
+def test_double_float_batch_matches_one_at_a_time_and_refuses_fp64(sfft):
+    sigs = [draw_signal(4, 1 << 12, 60 + 20 * s, seed=900 + s, r_lo=1.0, r_hi=10.0) for s in range(3)]
+    plans = [sfft.Plan(s.d, s.N, s.k, blocks=(2, 2), precision="df64") for s in sigs]
+    res, sts, _ = sfft.Batch(plans).execute([sfft.Signal(s.freqs, s.coeffs, s.N) for s in sigs])
+    for s, (f, a), st in zip(sigs, res, sts):
+        gf, ga = sfft.sort_result(_np(f), _np(a))
+        order = np.lexsort(s.freqs.T[::-1])
+        assert st == 0 and np.array_equal(gf, s.freqs[order])
+        assert np.max(np.abs(ga - s.coeffs[order]) / np.abs(s.coeffs[order])) < DF64_COEFF_TOL
+    with pytest.raises(sfft.SfftError) as err:
+        sfft.Batch([plans[0], sfft.Plan(4, 1 << 12, 60, blocks=(2, 2), precision="fp64")])
     assert err.value.status == 1
