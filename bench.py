@@ -388,7 +388,20 @@ def _precision_name(prec: str) -> str:
             "fp32_only": "every step in float",
             "fp64": "every step in double",
             "fp32_bf16dft": "as AUTO, with the DFT of rounds of p <= 8191 a split-BF16 tensor-core contraction "
-                            "(FP32 accumulate)"}[prec]
+                            "(FP32 accumulate)",
+            "df64": "double engine with sampling in double-float (pairs of floats on the FP32 pipe, about 48 "
+                    "significant bits); DFT, phase ratio, read-out and coefficient in double"}[prec]
+
+
+def df64_ops_per_term(d: int) -> float:
+    """FP32 operations the double-float sampler spends per term (set x mode x sample): per mode,
+    row pair and lane it forms E = U L (two products of 4 operations, two accumulations of 12)
+    once for the NS sets of its group, then 4 multiply-accumulates of 12 operations per set, and
+    the pair serves two samples.  NS is the set group's size for the d + 1 sets."""
+    ns = d + 1
+    groups = -(-ns // 8)
+    gsize = -(-ns // groups)
+    return (4 * 12 + 32.0 / gsize) / 2.0
 
 
 def run_ours(args):
@@ -502,6 +515,12 @@ def run_ours(args):
         peak = FP64_NOMINAL_TFLOPS
         peak_basis = ("GB300's nominal FP64 rate; the paired evaluation executes 4 of the 8 algorithmic flops of a "
                       "term, so the fraction can exceed 1")
+    elif args.precision == "df64":
+        ops = df64_ops_per_term(job.sigs[0].d)
+        peak = props.multi_processor_count * FP32_ALU_LANES_PER_SM * sm_max * 1e6 * 8.0 / ops / 1e12
+        peak_basis = (f"double-float peak: {props.multi_processor_count} SMs x {FP32_ALU_LANES_PER_SM} FP32 lanes x "
+                      f"{sm_max:.0f} MHz FP32 operations/s x 8 algorithmic flops per term / {ops:.2f} FP32 operations "
+                      f"per term of the double-float sampler")
     tot_class = sum(class_ms.values())
     del pbatch, pout
 
@@ -574,7 +593,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "fp32",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "df64": "df64"}.get(args.precision, "fp32"),
         "data": "synthetic (seeded planted sparse signals, resident in HBM)",
         "config": cfg,
         "other_form": {"form": "plain" if args.form == "batched" else "batched", "value": other_value,
@@ -715,7 +734,7 @@ def main(argv=None):
     ap.add_argument("--other-steps", type=int, default=1)
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_fp64ratio", "fp32_only", "fp64",
-                                                           "fp32_bf16dft"],
+                                                           "fp32_bf16dft", "df64"],
                     help="fp32: AUTO (ratio in double above N = 2^14); fp32_fp64ratio: ratio always in double")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -116,13 +116,6 @@ __device__ __forceinline__ float2 df_quick(float s, float e) {   // |e| <= |s|: 
   const float h = __fadd_rn(s, e);
   return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
 }
-__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
-  const float p = __fmul_rn(a.x, b.x);
-  float e = __fmaf_rn(a.x, b.x, -p);
-  e = __fmaf_rn(a.x, b.y, e);
-  e = __fmaf_rn(a.y, b.x, e);
-  return df_quick(p, e);
-}
 __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
   const float s = __fadd_rn(a.x, b.x);
   const float bb = __fsub_rn(s, a.x);
@@ -141,6 +134,25 @@ __device__ __forceinline__ float4 df_pack(double2 v) {
 __device__ __forceinline__ void df_pack_inplace(double2* v) {
   *reinterpret_cast<float4*>(v) = df_pack(*v);
 }
+// a b as an unnormalised pair (fl(a.hi b.hi), the rest): 4 operations
+__device__ __forceinline__ float2 df_prod(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  return make_float2(p, e);
+}
+// acc += a b with acc left unnormalised: the high parts by two-sum, every low-order term into
+// acc.y (8 operations after the product).  Within a 32-mode chunk acc.y stays below about 32
+// ulps of the largest partial sum, so its own rounding costs no more than renormalising.
+__device__ __forceinline__ void df_mac(float2& acc, float2 a, float2 b) {
+  const float2 q = df_prod(a, b);
+  const float t = __fadd_rn(acc.x, q.x);
+  const float bb = __fsub_rn(t, acc.x);
+  const float err = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(t, bb)), __fsub_rn(q.x, bb));
+  acc.y = __fadd_rn(acc.y, __fadd_rn(err, q.y));
+  acc.x = t;
+}
 
 // accumulate_chunk in double-float (the FP64 engine's double-float sampling): the staged roots and
 // coefficients hold df_pack values, the sums P1..P4 are double-float
@@ -156,14 +168,16 @@ __device__ __forceinline__ void accumulate_chunk_df(const SampleSmem<double, NS>
       for (int k = 0; k < 4; ++k) acc[qq][nn][k] = make_float2(0.0f, 0.0f);
   for (int jj = 0; jj < kSampleChunk; ++jj) {
     const float4 L = reinterpret_cast<const float4&>(sm.st.Ls[0][jj][lane]);
-    float2 Er[Q], Ei[Q];
+    float2 Er[Q], Ei[Q];   // E = U L, unnormalised (|E| = 1: absolute error about 2^-48)
 #pragma unroll
     for (int qq = 0; qq < Q; ++qq) {
       const float4 U = reinterpret_cast<const float4&>(sm.st.Us[0][jj][wrow * RP + qq]);
       const float2 ur = make_float2(U.x, U.y), ui = make_float2(U.z, U.w);
       const float2 lr = make_float2(L.x, L.y), li = make_float2(L.z, L.w);
-      Er[qq] = df_sub(df_mul(ur, lr), df_mul(ui, li));
-      Ei[qq] = df_add(df_mul(ur, li), df_mul(ui, lr));
+      Er[qq] = df_prod(ur, lr);
+      df_mac(Er[qq], make_float2(-ui.x, -ui.y), li);
+      Ei[qq] = df_prod(ur, li);
+      df_mac(Ei[qq], ui, lr);
     }
 #pragma unroll
     for (int nn = 0; nn < NS; ++nn) {
@@ -171,10 +185,10 @@ __device__ __forceinline__ void accumulate_chunk_df(const SampleSmem<double, NS>
       const float2 cr = make_float2(C.x, C.y), ci = make_float2(C.z, C.w);
 #pragma unroll
       for (int qq = 0; qq < Q; ++qq) {
-        acc[qq][nn][0] = df_add(acc[qq][nn][0], df_mul(cr, Er[qq]));   // P1: c_r e_r
-        acc[qq][nn][1] = df_add(acc[qq][nn][1], df_mul(ci, Ei[qq]));   // P2: c_i e_i
-        acc[qq][nn][2] = df_add(acc[qq][nn][2], df_mul(cr, Ei[qq]));   // P3: c_r e_i
-        acc[qq][nn][3] = df_add(acc[qq][nn][3], df_mul(ci, Er[qq]));   // P4: c_i e_r
+        df_mac(acc[qq][nn][0], cr, Er[qq]);   // P1: c_r e_r
+        df_mac(acc[qq][nn][1], ci, Ei[qq]);   // P2: c_i e_i
+        df_mac(acc[qq][nn][2], cr, Ei[qq]);   // P3: c_r e_i
+        df_mac(acc[qq][nn][3], ci, Er[qq]);   // P4: c_i e_r
       }
     }
   }

@@ -17,6 +17,7 @@ shape, the reference is the FP64 oracle (oracle/), whose own error against the p
 stated beside.
 
     python -m paper_1606_07407_gb300.precision_study [--k 100000] [--oracle-k 1000] [--json PATH]
+        [--arms fp64,df64,...] [--no-graph]
 """
 from __future__ import annotations
 
@@ -46,8 +47,8 @@ def compare(freqs, coeffs, ref_freqs, ref_coeffs):
     return len(rel), float(np.max(rel)), float(np.median(rel))
 
 
-def run_arm(sfft, torch, sig, blocks, prec):
-    plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=blocks, precision=prec, graph=True)
+def run_arm(sfft, torch, sig, blocks, prec, graph=True):
+    plan = sfft.Plan(sig.d, sig.N, sig.k, blocks=blocks, precision=prec, graph=graph)
     plan.execute(sfft.Signal(sig.freqs[:1], sig.coeffs[:1], sig.N), capacity=16, allow=(0, 2, 3, 5))   # warm-up
     dev = sfft.Signal(sig.freqs, sig.coeffs, sig.N)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -59,7 +60,7 @@ def run_arm(sfft, torch, sig, blocks, prec):
     return gf, ga, status, stats["rounds"], ev0.elapsed_time(ev1) / 1e3
 
 
-def study(k: int, blocks, seed_offset: int, oracle: bool, arms=None, log=print):
+def study(k: int, blocks, seed_offset: int, oracle: bool, arms=None, graph=True, log=print):
     import torch
     from . import build as B
     B.build()
@@ -72,7 +73,7 @@ def study(k: int, blocks, seed_offset: int, oracle: bool, arms=None, log=print):
     arms = list(arms or [a for a, _ in ARMS])
     results = {}
     for prec in arms:
-        gf, ga, status, rounds, secs = run_arm(sfft, torch, sig, blocks, prec)
+        gf, ga, status, rounds, secs = run_arm(sfft, torch, sig, blocks, prec, graph)
         found = set(map(tuple, gf.tolist()))
         n_ok, emax, emed = compare(gf, ga, planted_f, planted_a)
         results[prec] = {"status": int(status), "rounds": int(rounds), "gpu_s": round(secs, 4),
@@ -110,13 +111,16 @@ def main(argv=None):
     ap.add_argument("--oracle-k", type=int, default=1000)
     ap.add_argument("--json", default=None)
     ap.add_argument("--arms", default=",".join(a for a, _ in ARMS), help="comma-separated subset of the arms")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="rounds enqueued from the host instead of a device-ended CUDA graph (for profilers)")
     args = ap.parse_args(argv)
     blocks = WORKLOADS["d20_N1048576_k100000"].blocks
     arms = [a for a in args.arms.split(",") if a]
     if any(a not in dict(ARMS) for a in arms):
         ap.error(f"arms must be among {[a for a, _ in ARMS]}")
-    out = {"small": study(args.oracle_k, blocks, 100, oracle=True, arms=arms) if args.oracle_k > 0 else None,
-           "full": study(args.k, blocks, 0, oracle=False, arms=arms) if args.k > 0 else None}
+    graph = not args.no_graph
+    out = {"small": study(args.oracle_k, blocks, 100, oracle=True, arms=arms, graph=graph) if args.oracle_k > 0 else None,
+           "full": study(args.k, blocks, 0, oracle=False, arms=arms, graph=graph) if args.k > 0 else None}
     text = json.dumps(out, indent=1)
     if args.json:
         with open(args.json, "w") as fh:
