@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
     __syncthreads();
     if (act) {
 #pragma unroll 8
-      for (int k = lt; k < L; k += team) rb[fpad(k)] = cmul(rb[fpad(k)], pf[k]);
+      for (int k = lt; k < L; k += team) rb[fpad(k)] = cconj(cmul(rb[fpad(k)], pf[k]));
     }
     __syncthreads();   // the spectrum is consumed: the chirp takes its place
     for (int x = threadIdx.x; x < p; x += blockDim.x) cp_async<sizeof(C2)>(pf + x, chirp + x);
@@ -570,11 +570,14 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   } else {
     if (act) {
 #pragma unroll 8
-      for (int k = lt; k < L; k += team) rb[fpad(k)] = cmul(rb[fpad(k)], B[k]);
+      for (int k = lt; k < L; k += team) rb[fpad(k)] = cconj(cmul(rb[fpad(k)], B[k]));
     }
     __syncthreads();
   }
-  fft_row<C2, true>(rb, L, tw_hi, tw_lo, lt, team, act);
+  // the inverse transform as conj(FFT(conj(.))): the product was stored conjugated, the forward
+  // code runs again, and the read-out below conjugates back, so the kernel holds the code of one
+  // direction only (its instruction footprint, with every radix unrolled, is what limits it)
+  fft_row<C2, false>(rb, L, tw_hi, tw_lo, lt, team, act);
   if (prefetch) {
     cp_async_wait_all();
     __syncthreads();
@@ -588,7 +591,7 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
     for (int64_t h0 = 0; h0 < p; h0 += team) {
       const int64_t h = h0 + lt;
       if (h < p) {
-        const C2 v = cmul(ch[h], cscale(rb[fpad((int)h)], invL));
+        const C2 v = cmul(ch[h], cscale(cconj(rb[fpad((int)h)]), invL));
         out[h] = v;
         m2 = fmax(m2, v.x * v.x + v.y * v.y);
       }
@@ -969,6 +972,16 @@ __global__ void k_output(int n, const SigCfg* __restrict__ cfg, SigRun* run, con
   }
 }
 
+// e^{2 pi i j / 1024}, j = 0..1023, in double: the reference points of the float engine's
+// double read-out and coefficient roots (classification)
+__global__ void k_root1k(double2* t) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < 1024; j += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi((double)j / 512.0, &s, &c);
+    t[j] = make_double2(c, s);
+  }
+}
+
 __global__ void k_twiddles(int64_t Lmax, void* twG, int fp64) {
   for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < Lmax; m += (int64_t)gridDim.x * blockDim.x) {
     const int64_t mm = (2 * m > Lmax) ? m - Lmax : m;
@@ -1241,6 +1254,11 @@ class Engine final : public EngineBase {
     stage_hist_ = align16(stage_st_ + (size_t)n_ * sizeof(int));
     host_stage_bytes_ = stage_hist_ + SFFT_STATS_MAX_ROUNDS * sizeof(HistRec);
     ECHK(cudaMallocHost(&host_stage_, host_stage_bytes_));
+    ECHK(alloc(&root1k_, 1024 * sizeof(double2)));
+    k_root1k<<<4, 256, 0, st_>>>((double2*)root1k_);
+    ECHK(cudaGetLastError());
+    for (SigCfg& c : cfg) c.root1k = (const double2*)root1k_;
+    cfg_host_ = cfg;
     ECHK(cudaMemcpyAsync(cfg_, cfg.data(), cfg.size() * sizeof(SigCfg), cudaMemcpyHostToDevice, st_));
     ECHK(cudaMemcpyAsync(ptab_, ptab.data(), ptab.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
     ECHK(cudaMemcpyAsync(pfirst_, pfirst.data(), pfirst.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
@@ -1957,6 +1975,7 @@ class Engine final : public EngineBase {
   int32_t* alpha_ = nullptr;
   int32_t* gam_ = nullptr;
   void* Cm_ = nullptr;
+  void* root1k_ = nullptr;   // double2 [1024]: e^{2 pi i j / 1024}
   unsigned ns_mask_ = 0;   // set-group sizes present among the slots
   void* part_ = nullptr;
   void* twG_ = nullptr;

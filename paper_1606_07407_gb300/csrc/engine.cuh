@@ -59,6 +59,7 @@ struct SigCfg {
   int64_t mode_off;   // int32 [Kmax]        alpha_j = (w_j . u) mod p and 32 alpha_j mod p of the round
   int64_t C_off;      // T2 [n_sets * Kmax]  a_j e^{2 pi i w_{j,n} / N} of the round (registry: -a)
   int Kmax;           // k, plus reg_cap when the registry is sampled
+  const double2* root1k;   // e^{2 pi i j / 1024}, j < 1024, in double (the engine's; shared by its slots)
 };
 
 // Dynamic state of one signal, updated by the kernels of each round.

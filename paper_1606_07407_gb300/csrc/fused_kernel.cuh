@@ -183,16 +183,17 @@ __device__ __noinline__ void fused_convolve(const SigCfg& c, const SigRun& r, co
   const bool act = slot == 0 || data;
   C2* rb = slots + slot * ls;
   fft_row<C2, false, E>(rb, L, tw_hi, tw_lo, lt, nthr, act);
+  // the inverse as conj(FFT(conj(.))): one direction's code in the kernel
   if (data)
-    for (int k = lt; k < L; k += nthr) rb[fpad(k)] = cmul(rb[fpad(k)], slots[fpad(k)]);
+    for (int k = lt; k < L; k += nthr) rb[fpad(k)] = cconj(cmul(rb[fpad(k)], slots[fpad(k)]));
   __syncthreads();
-  fft_row<C2, true, E>(rb, L, tw_hi, tw_lo, lt, nthr, data);
+  fft_row<C2, false, E>(rb, L, tw_hi, tw_lo, lt, nthr, data);
   float m2 = 0.0f;   // largest |Y_0|^2 seen by this thread
   if (data) {
     const C2* chirp = tab_s + p;
     const float invL = 1.0f / (float)L;
     for (int h = lt; h < p; h += nthr) {
-      const C2 v = cmul(chirp[h], cscale(rb[fpad(h)], invL));
+      const C2 v = cmul(chirp[h], cscale(cconj(rb[fpad(h)]), invL));
       Ys[row * p + h] = v;
       m2 = fmaxf(m2, v.x * v.x + v.y * v.y);
     }

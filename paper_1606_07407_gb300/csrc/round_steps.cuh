@@ -334,6 +334,69 @@ __device__ __forceinline__ bool read_coord(R ynx, R yny, R y0x, R y0y, int64_t N
   return true;
 }
 
+// ---- the float engine's double read-out and coefficient roots without double transcendentals
+// (GB300's FP64 pipe runs at 1/64 of the FP32 rate, and a double atan2 or sincospi costs tens of
+// its operations).  Both reduce the angle against a table of e^{2 pi i j / 1024} in double:
+// what is left is below about pi / 1024, where short series are exact to double rounding.
+
+// Arg(z) / (2 pi) for z = re + i im != 0, given af, a float estimate of Arg(z) (within about
+// 1e-3 of it, any multiple of 2 pi apart): k = af's nearest 1024th of a turn in [-512, 512),
+// z e^{-2 pi i k / 1024} has the angle a = atan(t), t = Im / Re, |t| < 4e-3, whose series stops at
+// t^7 (t^9 / 9 < 1e-22); the quotient through a float reciprocal and one Newton step (relative
+// error about 2^-46; a double division where Re is outside float's range).  Turns in
+// [-1/2 - 1e-3, 1/2 + 1e-3].
+__device__ __forceinline__ double arg_turns_fx(const double2* __restrict__ root1k, double re, double im, float af) {
+  int k = __float2int_rn(af * (float)(512.0 / 3.14159265358979323846)) & 1023;
+  if (k >= 512) k -= 1024;
+  const double2 w = root1k[k & 1023];
+  const double re2 = re * w.x + im * w.y;   // z conj(w)
+  const double im2 = im * w.x - re * w.y;
+  double y;
+  if (fabs(re2) > 1e-30 && fabs(re2) < 1e30) {
+    y = (double)__frcp_rn((float)re2);
+    y = y * (2.0 - re2 * y);
+  } else {
+    y = 1.0 / re2;
+  }
+  const double t = im2 * y;
+  const double t2 = t * t;
+  const double a = t * (1.0 + t2 * (-1.0 / 3.0 + t2 * (1.0 / 5.0 + t2 * (-1.0 / 7.0))));
+  return (double)k * (1.0 / 1024.0) + a * (0.5 / 3.14159265358979323846);
+}
+
+// read_coord for float transforms with the read-out in double (the ratio Y_n conj(Y_0) is formed
+// from exact double products of the floats, its angle by arg_turns_fx)
+__device__ __forceinline__ bool read_coord_fx(const double2* __restrict__ root1k, float ynx, float yny, float y0x,
+                                              float y0y, int64_t N, int box_lo, double delta, int64_t* w_out) {
+  const double re = (double)ynx * (double)y0x + (double)yny * (double)y0y;   // Y_n conj(Y_0)
+  const double im = (double)yny * (double)y0x - (double)ynx * (double)y0y;
+  const float af = atan2f(yny, ynx) - atan2f(y0y, y0x);
+  const double v = (double)N * arg_turns_fx(root1k, re, im, af);
+  const double rr = rint(v);
+  if (!(fabs(v - rr) <= delta)) return false;
+  // |rr| <= N / 2 + 1 and -N <= box_lo <= 0: one wrap
+  int64_t wn = (int64_t)rr - box_lo;
+  if (wn < 0) wn += N;
+  else if (wn >= N) wn -= N;
+  *w_out = wn + box_lo;
+  return true;
+}
+
+// e^{2 pi i m / q} in double (0 <= m < q < 2^31, inv_q = 1 / q in double, sc = 1024 / q in
+// float): j = the nearest 1024th of a turn (within one), then the angle left,
+// e = 2 pi (1024 m - j q) / (1024 q), |e| < 0.01, by the Taylor series of cos and sin to e^6 / e^7
+// (the next terms are below 1e-20).
+__device__ __forceinline__ double2 unit_root_fx(const double2* __restrict__ root1k, int64_t m, int64_t q,
+                                                double inv_q, float sc) {
+  const int64_t j = (int64_t)__float2int_rn((float)m * sc);
+  const double e = (double)(1024 * m - j * q) * (inv_q * (3.14159265358979323846 / 512.0));
+  const double e2 = e * e;
+  const double cs = 1.0 + e2 * (-1.0 / 2.0 + e2 * (1.0 / 24.0 + e2 * (-1.0 / 720.0)));
+  const double sn = e * (1.0 + e2 * (-1.0 / 6.0 + e2 * (1.0 / 120.0 + e2 * (-1.0 / 5040.0))));
+  const double2 w = root1k[j & 1023];
+  return make_double2(w.x * cs - w.y * sn, w.x * sn + w.y * cs);
+}
+
 // Block form: Arg(Y_n / Y_0) read as the block's unwrapped frequency w~ = 2 N^{d1} Arg / (2 pi),
 // taken in the window [W_lo, W_lo + N^{d1}) of the box's unwrapped values (W_lo that of
 // (box_lo, ..., box_lo)) and split into its d1 base-N digits, lowest first; false when farther
@@ -406,13 +469,19 @@ __device__ __forceinline__ bool read_tilt(const SigCfg& c, R y1x, R y1y, R y2x, 
 // Read-out of shifted set n (1-based) of an occupied bin: the coordinate it fixes (coordinate
 // form) or the d1 coordinates of block n (block form) go to w (if not null), and their
 // (w_l - box_lo) u_l are added to *bin mod p.
-template <typename R>
+// FX: the transforms are float and the read-out double (read_coord_fx).
+template <typename R, bool FX = false>
 __device__ __forceinline__ bool read_set(const SigCfg& c, const SigRun& r, const int32_t* __restrict__ blk, int n,
                                          R ynx, R yny, R y0x, R y0y, const int64_t* u, uint64_t* bin, int32_t* w) {
   const uint64_t up = (uint64_t)r.p;
   if (!c.shift_block) {
     int64_t wn;
-    if (!read_coord<R>(ynx, yny, y0x, y0y, c.N, c.box_lo, (R)c.delta, &wn)) return false;
+    if constexpr (FX) {
+      if (!read_coord_fx(c.root1k, (float)ynx, (float)yny, (float)y0x, (float)y0y, c.N, c.box_lo, c.delta, &wn))
+        return false;
+    } else {
+      if (!read_coord<R>(ynx, yny, y0x, y0y, c.N, c.box_lo, (R)c.delta, &wn)) return false;
+    }
     if (w) w[n - 1] = (int32_t)wn;
     *bin = mod_barrett((uint64_t)(wn - c.box_lo) * (uint64_t)u[n - 1] + *bin, up, r.mod_m);
     return true;
@@ -466,6 +535,7 @@ template <typename T, typename R>
 __device__ bool decode_bin(const SigCfg& c, const SigRun& r, const int32_t* __restrict__ blk, const c2<T>* Y,
                            const int64_t* u, int64_t h, R y0x, R y0y, R m0, int32_t* w_out) {
   constexpr int kB = 8;
+  constexpr bool FX = sizeof(T) == 4 && sizeof(R) == 8;   // float transforms, double read-out
   const int64_t p = r.p;
   const uint64_t up = (uint64_t)p;
   const int S = c.n_sets - 1;
@@ -482,9 +552,14 @@ __device__ bool decode_bin(const SigCfg& c, const SigRun& r, const int32_t* __re
       const int n = n0 + i;
       if (n > S) break;
       const R ynx = (R)yv[i].x, yny = (R)yv[i].y;
-      const R mn = sqrt(ynx * ynx + yny * yny);
-      if (!(fabs(mn / m0 - (R)1) < (R)c.tau)) return false;   // Eq. 42
-      if (!read_set<R>(c, r, blk, n, ynx, yny, y0x, y0y, u, &bin, w_out)) return false;
+      if constexpr (FX) {   // the magnitudes of float values in float (tau >> float rounding)
+        const float mn = sqrtf(yv[i].x * yv[i].x + yv[i].y * yv[i].y);
+        if (!(fabsf(mn / (float)m0 - 1.0f) < (float)c.tau)) return false;   // Eq. 42
+      } else {
+        const R mn = sqrt(ynx * ynx + yny * yny);
+        if (!(fabs(mn / m0 - (R)1) < (R)c.tau)) return false;   // Eq. 42
+      }
+      if (!read_set<R, FX>(c, r, blk, n, ynx, yny, y0x, y0y, u, &bin, w_out)) return false;
     }
   }
   uint64_t usum = 0;
@@ -507,7 +582,7 @@ __device__ void read_coords(const SigCfg& c, const SigRun& r, const int32_t* __r
   uint64_t bin = 0;
   for (int n = 1; n < c.n_sets; ++n) {
     const c2<T> yn = Y[(int64_t)n * r.p + h];
-    read_set<R>(c, r, blk, n, (R)yn.x, (R)yn.y, y0x, y0y, u, &bin, w_out);
+    read_set<R, sizeof(T) == 4 && sizeof(R) == 8>(c, r, blk, n, (R)yn.x, (R)yn.y, y0x, y0y, u, &bin, w_out);
   }
 }
 
@@ -527,11 +602,23 @@ __device__ double2 coefficient(const SigCfg& c, const SigRun& r, const int32_t* 
     return make_double2((double)y0x * scale, (double)y0y * scale);
   }
   R ax = y0x, ay = y0y;
+  // float transforms, double estimate, coordinate form: the roots from the table (unit_root_fx)
+  constexpr bool FX = sizeof(T) == 4 && sizeof(R) == 8;
+  const bool fx = FX && !c.shift_block && !c.shift_tilt && c.N < (1LL << 31);
+  const double inv_N = fx ? 1.0 / (double)c.N : 0.0;
+  const float sc_N = fx ? 1024.0f / (float)c.N : 0.0f;
   for (int n = 1; n < c.n_sets; ++n) {
     const c2<T> yn = Y[(int64_t)n * r.p + h];
     c2<R> t;   // e^{2 pi i w . s_n}
-    if (sizeof(R) == sizeof(T) && tn != nullptr) t = mk2((R)tn[n - 1].x, (R)tn[n - 1].y);
-    else t = shift_root<R>(c, blk, w, n, true);
+    if (sizeof(R) == sizeof(T) && tn != nullptr) {
+      t = mk2((R)tn[n - 1].x, (R)tn[n - 1].y);
+    } else if (FX && fx) {
+      const int64_t m = w[n - 1] < 0 ? (int64_t)w[n - 1] + c.N : (int64_t)w[n - 1];   // w in the box
+      const double2 q = unit_root_fx(c.root1k, m, c.N, inv_N, sc_N);
+      t = mk2((R)q.x, (R)q.y);
+    } else {
+      t = shift_root<R>(c, blk, w, n, true);
+    }
     ax += (R)yn.x * t.x + (R)yn.y * t.y;     // Y_n conj(t)
     ay += (R)yn.y * t.x - (R)yn.x * t.y;
   }
@@ -569,7 +656,8 @@ __device__ void classify_candidate(const SigCfg& c, SigRun* rp, int s, int64_t h
   int32_t* wreg = dd <= 64 ? wk : nullptr;   // decoded vector kept for the read-out
   bool ok;
   if (c.ratio64) {
-    const double m0d = sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y);
+    const double m0d = sizeof(T) == 4 ? (double)sqrtf((float)(y0.x * y0.x + y0.y * y0.y))
+                                      : sqrt((double)y0.x * (double)y0.x + (double)y0.y * (double)y0.y);
     ok = decode_bin<T, double>(c, r, blk, Y, u, h, (double)y0.x, (double)y0.y, m0d, wreg);
   } else {
     ok = decode_bin<T, T>(c, r, blk, Y, u, h, y0.x, y0.y, sqrt(y0.x * y0.x + y0.y * y0.y), wreg);

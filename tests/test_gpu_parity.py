@@ -223,6 +223,35 @@ def test_classify_matches_oracle(sfft, prec):
         assert abs(g[2] - r[2]) <= 1e-12 * abs(r[2])
 
 
+@pytest.mark.parametrize("N", [1 << 20, 1 << 23, 999_983])
+def test_classify_double_readout_at_large_N(sfft, N):
+    # The float policies' double read-out (phase reduced against a table of 1024th turns, then a
+    # short series) and table-based coefficient roots, at N where float's phase resolution no
+    # longer reads a coordinate: 300 lone modes in distinct bins, float transforms of them, the
+    # same accepted (bin, vector) set as the FP64 oracle on the same values and coefficients
+    # within 1e-12 of its
+    d, p, k = 3, 1031, 300
+    u = [1, 0, 0]
+    st = Stream(N % 1000 + 5)
+    bins = np.unique(st.integers(4 * k, 0, p))[:k]
+    rows = []
+    for b in bins.tolist():
+        w0 = b + p * int(st.integers(1, 0, (N - b) // p)[0])
+        rows.append([w0, int(st.integers(1, 0, N)[0]), int(st.integers(1, 0, N)[0])])
+    w = np.array(rows, dtype=np.int64)
+    a = (1.0 + 9.0 * st.uniform(len(rows))) * np.exp(2j * np.pi * st.uniform(len(rows)))
+    Yc = _designed_transforms(d, N, p, u, w, a).astype(np.complex64)
+    plan = sfft.Plan(d, N, k, blocks=(1, 1, 1), precision="fp32_fp64ratio")
+    eta = 2.0 ** -17 * np.max(np.abs(Yc[0]))
+    h, gw, ga = plan.classify(p, u, torch.tensor(Yc), eta)
+    ref = O.classify(Yc.astype(np.complex128), p, u, N, eta, O.Thresholds(tau=1e-3, delta=0.25), estimator="mean")
+    got = sorted(zip(_np(h).tolist(), map(tuple, _np(gw).tolist()), _np(ga).tolist()))
+    assert [(x[0], x[1]) for x in got] == [(r[0], r[1]) for r in ref]
+    assert len(got) > k // 2
+    for g, r in zip(got, ref):
+        assert abs(g[2] - r[2]) <= 1e-12 * abs(r[2])
+
+
 def plan_tau(prec):
     return 1e-7 if prec == "fp64" else 1e-3
 
