@@ -245,11 +245,13 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
   __syncthreads();
   // pass 2: per-signal work counts and their exclusive scans
   int64_t carry[kNumScans];
+#pragma unroll
   for (int q = 0; q < kNumScans; ++q) carry[q] = 0;
   int64_t part_carry = 0, tile_carry = 0;
   for (int base = 0; base < n; base += blockDim.x) {
     const int s = base + threadIdx.x;
     int64_t v[kNumScans + 1];
+#pragma unroll
     for (int q = 0; q <= kNumScans; ++q) v[q] = 0;
     SigRun r;
     bool batched = false;   // active and not left to the fused kernel
@@ -284,7 +286,10 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
         r.splits = K > 0 ? (K + r.jper - 1) / r.jper : 1;
         v[SC_TAB] = r.tab_owner ? r.p : 0;
         v[SC_MODE] = K;
-        v[SC_SAMP0 + r.gsize - 1] = (int64_t)r.n_xt * r.groups * r.splits;
+        // constant indices only: a computed index would put v in local memory
+#pragma unroll
+        for (int q = 0; q < kMaxSetGroup; ++q)
+          if (q == r.gsize - 1) v[SC_SAMP0 + q] = (int64_t)r.n_xt * r.groups * r.splits;
         v[SC_BINS] = r.p;
         if (r.dense) {
           // the dense tensor-core kernel takes the signal's rows (no Bluestein row or filter)
@@ -292,8 +297,14 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
           const bool sm = r.L <= (1 << kSmallFftLog);
           const int g = dft_group_rows<c2<T>>(r.L, sm ? a.dft_thr_s : a.dft_thr_l,
                                              (sm ? a.dft_smem_s : a.dft_smem_l) / (int64_t)sizeof(c2<T>), c.n_sets);
-          v[sm ? SC_ROWS_S : SC_ROWS] = (c.n_sets + g - 1) / g;   // row groups
-          v[sm ? SC_FILT_S : SC_FILT] = r.tab_owner;
+          const int64_t groups = (c.n_sets + g - 1) / g;   // row groups
+          if (sm) {
+            v[SC_ROWS_S] = groups;
+            v[SC_FILT_S] = r.tab_owner;
+          } else {
+            v[SC_ROWS] = groups;
+            v[SC_FILT] = r.tab_owner;
+          }
         } else {
           int M1, M2, CT, RT;
           big_geom(r.logL, &M1, &M2, &CT, &RT);
@@ -307,12 +318,19 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     int64_t tot[kNumScans + 1];
     block_scan_excl<kNumScans + 1>(v, tot);
     if (s < n) {
+#pragma unroll
       for (int q = 0; q < kNumScans; ++q) sc.v[q][s] = carry[q] + v[q];
-      if (batched) {
-        r.part_off = part_carry + v[kNumScans];
-        run[s] = r;
+      if (batched) {   // the fields pass 2 sets (the whole record would be 224 bytes of stores)
+        SigRun& o = run[s];
+        o.tab_at = r.tab_at;
+        o.bhat_at = r.bhat_at;
+        o.tab_owner = r.tab_owner;
+        o.jper = r.jper;
+        o.splits = r.splits;
+        o.part_off = part_carry + v[kNumScans];
       }
     }
+#pragma unroll
     for (int q = 0; q < kNumScans; ++q) carry[q] += tot[q];
     part_carry += tot[kNumScans];
   }
@@ -322,6 +340,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     if (r.active && !r.fused) powner[r.p] = kNoOwner;
   }
   if (threadIdx.x == 0) {
+#pragma unroll
     for (int q = 0; q < kNumScans; ++q) sc.v[q][n] = carry[q];
     RoundCtl c;
     c.active = (int)tot_active;

@@ -156,7 +156,7 @@ __device__ __forceinline__ int find_slot(const int64_t* __restrict__ scan, int n
 
 // Exclusive scan of V values per thread over the block (a multiple of 32 threads, at most 1024).
 template <int V>
-__device__ void block_scan_excl(int64_t (&v)[V], int64_t (&tot)[V]) {
+__device__ __forceinline__ void block_scan_excl(int64_t (&v)[V], int64_t (&tot)[V]) {
   __shared__ int64_t ws[32][V];
   __shared__ int64_t wt[V];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
