@@ -9,7 +9,7 @@
 
 namespace sfft {
 
-constexpr int kPlanThreads = 256;    // one block; wider blocks spill the 18-wide scans
+constexpr int kPlanThreads = 384;    // one block; 148 registers a thread (512 threads would spill the 19-wide scans)
 constexpr int kSingleMaxLf = 16384;   // one-block Bluestein length, FP32 (data + twiddles in shared memory)
 constexpr int kSingleMaxLd = 8192;    // same for FP64
 constexpr int kBigColElems = 4096;    // elements of one column tile of the four-step passes
