@@ -32,9 +32,17 @@ namespace sfft {
 namespace {
 
 constexpr int kBindArrays = 8;   // per-signal arrays staged by bind()
-// powner[p] between k_plan launches: above every signal index (the byte of a memset fill)
-constexpr int kNoOwnerByte = 0x7F;
-constexpr int32_t kNoOwner = 0x7F7F7F7F;
+// Owner election of the batched signals that share a prime: powner[p] = min over this round's
+// claimants of (0xFFFFFFFF - epoch) << 32 | slot.  A later epoch has the smaller high word, so
+// keys of earlier rounds never win and the table needs no clearing (all ones at creation).
+__device__ __forceinline__ unsigned long long owner_key(unsigned int epoch, int s) {
+  return ((unsigned long long)(0xFFFFFFFFu - epoch) << 32) | (unsigned int)s;
+}
+
+// round 1 of a slot whose root tables and filter were made with the engine: no owner needed
+__device__ __forceinline__ bool uses_engine_tables(const PlanArgs& a, const SigCfg& c, const SigRun& r) {
+  return !a.force && r.round == 1 && c.tab0_off >= 0 && r.p == c.p1;
+}
 
 inline unsigned long long double_bits(double v) {
   unsigned long long u;
@@ -111,9 +119,10 @@ __global__ void k_bind_tw(int n, const SigCfg* __restrict__ cfg, const SigRun* _
 // ------------------------------------------------------------------ plan
 
 // Plans the round of every signal (plan_signal; a signal whose next round the fused kernel
-// has planned keeps it), then the work counts of the batched kernels and their exclusive
-// scans over the signals.  Sets the graph conditions: some signal active (the round loop),
-// some batched work, some fused round planned.
+// has planned keeps it) and gathers the round's totals over the grid (k_plan_signals), then,
+// in one block, the mode splits, the work counts of the batched kernels and their exclusive
+// scans over the signals (k_plan).  Sets the graph conditions: some signal active (the round
+// loop), some batched work, some fused round planned.
 // Rows of one signal that one block of the DFT takes together (they share p, the chirp, the
 // filter spectrum and the twiddles): as many as the block has whole-warp groups of the threads a
 // row needs, and as the block's shared memory holds padded rows plus one prefetch row of L.
@@ -130,11 +139,19 @@ __host__ __device__ inline int dft_group_rows(int L, int nthr, int64_t smem_elem
 // The round's parameters of every signal not already planned by the fused kernel (stop rule,
 // prime, direction mod p, work geometry: plan_signal), one thread per signal over the whole
 // grid; k_plan then sums and scans the work.
+// The same threads then add the round's totals into acc (active and fused signals, batched
+// tiles, and the histogram of n_sets p by mode chunks from which k_plan sizes the mode splits)
+// and elect each shared prime's owner.
 template <typename T>
 __global__ void k_plan_signals(PlanArgs a, const SigCfg* __restrict__ cfg, SigRun* run, const int32_t* __restrict__ ptab,
                                int n_ptab, const int32_t* __restrict__ pfirst, int64_t pfirst_n,
                                const int64_t* __restrict__ dirs, const int64_t* __restrict__ plist, int64_t* ubuf,
-                               HistRec* hist) {
+                               HistRec* hist, PlanAcc* acc, unsigned long long* __restrict__ powner) {
+  __shared__ unsigned long long s_tot[3], s_w[65];
+  for (int i = threadIdx.x; i < 65; i += blockDim.x) s_w[i] = 0ull;
+  if (threadIdx.x < 3) s_tot[threadIdx.x] = 0ull;
+  __syncthreads();
+  const unsigned int epoch = acc->epoch;
   const PrimeTables pt{ptab, n_ptab, pfirst, pfirst_n, dirs, plist};
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += gridDim.x * blockDim.x) {
     SigRun r = run[s];
@@ -142,7 +159,21 @@ __global__ void k_plan_signals(PlanArgs a, const SigCfg* __restrict__ cfg, SigRu
       plan_signal<T>(a, cfg[s], r, pt, ubuf, hist, s == 0);
       run[s] = r;
     }
+    if (r.active) {
+      atomicAdd(&s_tot[1], 1ull);
+      if (r.fused) {
+        atomicAdd(&s_tot[2], 1ull);
+      } else {
+        atomicAdd(&s_tot[0], (unsigned long long)r.n_xt * (unsigned long long)r.groups);
+        atomicAdd(&s_w[min(r.chunks, 64)], (unsigned long long)cfg[s].n_sets * (unsigned long long)r.p);
+        if (!uses_engine_tables(a, cfg[s], r)) atomicMin(&powner[r.p], owner_key(epoch, s));
+      }
+    }
   }
+  __syncthreads();
+  if (threadIdx.x < 3 && s_tot[threadIdx.x]) atomicAdd(&(&acc->tiles)[threadIdx.x], s_tot[threadIdx.x]);
+  for (int i = threadIdx.x; i < 65; i += blockDim.x)
+    if (s_w[i]) atomicAdd(&acc->wsum[i], s_w[i]);
 }
 
 template <typename T>
@@ -151,25 +182,18 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
                                                        int n_ptab, const int32_t* __restrict__ pfirst, int64_t pfirst_n,
                                                        const int64_t* __restrict__ dirs,
                                                        const int64_t* __restrict__ plist, int64_t* ubuf,
-                                                       HistRec* hist, int32_t* __restrict__ powner) {
+                                                       HistRec* hist, PlanAcc* acc,
+                                                       const unsigned long long* __restrict__ powner) {
   __shared__ int s_S;
   __shared__ int64_t s_part;   // partial-sum elements at the chosen S
   __shared__ unsigned long long s_key;
+  __shared__ unsigned long long s_w[65];
   const int n = a.n;
-  int64_t tiles = 0, active = 0, fused = 0;
-  // pass 1: the round's totals (k_plan_signals has planned every signal)
-  for (int s = threadIdx.x; s < n; s += blockDim.x) {
-    const SigRun& r = run[s];
-    if (r.active) {
-      active += 1;
-      if (r.fused) fused += 1;
-      else tiles += (int64_t)r.n_xt * r.groups;
-    }
-  }
-  __syncthreads();
-  const int64_t tot_tiles = block_sum(tiles);
-  const int64_t tot_active = block_sum(active);
-  const int64_t tot_fused = block_sum(fused);
+  // the round's totals, gathered by k_plan_signals
+  const int64_t tot_tiles = (int64_t)acc->tiles;
+  const int64_t tot_active = (int64_t)acc->active;
+  const int64_t tot_fused = (int64_t)acc->fused;
+  for (int i = threadIdx.x; i < 65; i += blockDim.x) s_w[i] = acc->wsum[i];
   // mode splits S (1..64): the persistent sampling kernel's 2 n_sm blocks take tiles x S items of
   // 1/S of the modes each; S minimises its waves per unit of work, ceil(items / blocks) / S, with
   // 12% per extra split for the partial sums it adds and the DFT reads back (then it is halved to
@@ -184,23 +208,19 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     atomicMin(&s_key, (score << 6) | (unsigned long long)(S - 1));
   }
   __syncthreads();
-  if (threadIdx.x == 0) s_S = tot_tiles > 0 ? (int)(s_key & 63ull) + 1 : 1;
-  __syncthreads();
-  for (;;) {
-    const int S = s_S;
-    int64_t part = 0;
-    for (int s = threadIdx.x; s < n; s += blockDim.x) {
-      const SigRun& r = run[s];
-      if (!r.active || r.fused) continue;
-      part += (int64_t)min(S, r.chunks) * cfg[s].n_sets * r.p;
+  if (threadIdx.x == 0) {
+    // partial-sum elements sum_s min(S, chunks_s) n_sets p_s from the histogram by chunks
+    int S = tot_tiles > 0 ? (int)(s_key & 63ull) + 1 : 1;
+    for (;;) {
+      int64_t tot = 0;
+      for (int q = 1; q <= 64; ++q) tot += (int64_t)min(S, q) * (int64_t)s_w[q];
+      s_part = tot;
+      if (tot <= a.part_cap || S == 1) break;
+      S /= 2;
     }
-    const int64_t tot = block_sum(part);
-    __syncthreads();
-    if (threadIdx.x == 0) s_part = tot;
-    if (tot <= a.part_cap || S == 1) break;
-    if (threadIdx.x == 0) s_S = S / 2;
-    __syncthreads();
+    s_S = S;
   }
+  __syncthreads();
   const int S = s_S;
   // Tail of the sampling queue: when the items (tiles unsplit) leave the persistent kernel's last
   // wave mostly empty (rem of 2 n_sm blocks busy), the signals whose tiles fall in that wave split
@@ -232,17 +252,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     if (s_part + tot_extra <= a.part_cap) q_tail = q;
   }
   // Batched signals with the same prime share one copy of the tables (W, chirp) and of the filter
-  // spectrum: that of the first of them, the owner, found through powner[p] (kept at kNoOwner
-  // between launches; set here, read in pass 2, reset after it).  Round 1 with the tables made
-  // with the engine needs no owner.
-  auto uses_engine_tables = [&](const SigRun& r, int s) {
-    return !a.force && r.round == 1 && cfg[s].tab0_off >= 0 && r.p == cfg[s].p1;
-  };
-  for (int s = threadIdx.x; s < n; s += blockDim.x) {
-    const SigRun& r = run[s];
-    if (r.active && !r.fused && !uses_engine_tables(r, s)) atomicMin(&powner[r.p], s);
-  }
-  __syncthreads();
+  // spectrum: that of the first of them, the owner elected in powner[p] by k_plan_signals.  Round
+  // 1 with the tables made with the engine needs no owner.
   // pass 2: per-signal work counts and their exclusive scans
   int64_t carry[kNumScans];
 #pragma unroll
@@ -267,12 +278,12 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
       in_tail = batched && tile_carry + tv[0] + tiles_s > tail_from;
       tile_carry += tt[0];
     }
-    if (batched && uses_engine_tables(r, s)) {
+    if (batched && uses_engine_tables(a, cfg[s], r)) {
       r.tab_at = cfg[s].tab0_off;
       r.bhat_at = cfg[s].bhat0_off;
       r.tab_owner = 0;
     } else if (batched) {
-      const int own = powner[r.p];
+      const int own = (int)(powner[r.p] & 0xFFFFFFFFull);
       r.tab_at = cfg[own].tab_off;
       r.bhat_at = cfg[own].bhat_off;
       r.tab_owner = own == s ? 1 : 0;
@@ -334,11 +345,12 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     for (int q = 0; q < kNumScans; ++q) carry[q] += tot[q];
     part_carry += tot[kNumScans];
   }
-  __syncthreads();   // every owner has been read
-  for (int s = threadIdx.x; s < n; s += blockDim.x) {
-    const SigRun& r = run[s];
-    if (r.active && !r.fused) powner[r.p] = kNoOwner;
+  __syncthreads();   // every total has been read: clear them for the next round
+  if (threadIdx.x == 0) {
+    acc->tiles = acc->active = acc->fused = 0ull;
+    acc->epoch += 1;
   }
+  for (int i = threadIdx.x; i < 65; i += blockDim.x) acc->wsum[i] = 0ull;
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int q = 0; q < kNumScans; ++q) sc.v[q][n] = carry[q];
@@ -1013,6 +1025,19 @@ __global__ void k_twiddles(int64_t Lmax, void* twG, int fp64) {
 
 // ------------------------------------------------------------------ host side
 
+// the smallest prime >= v (trial division; v below 2^40)
+int64_t first_prime_at_least(int64_t v) {
+  for (int64_t q = std::max<int64_t>(v, 2);; ++q) {
+    bool prime = true;
+    for (int64_t f = 2; f * f <= q; ++f)
+      if (q % f == 0) {
+        prime = false;
+        break;
+      }
+    if (prime) return q;
+  }
+}
+
 std::vector<int32_t> sieve_primes(int64_t lim) {
   std::vector<char> comp((size_t)lim + 1, 0);
   std::vector<int32_t> out;
@@ -1087,6 +1112,15 @@ class Engine final : public EngineBase {
       c.fuse_L = (sizeof(T) == 4 && d.fuse) ? fused_max_length(c.n_sets) : 0;
       if (d.fuse_max_len > 0) c.fuse_L = std::min(c.fuse_L, d.fuse_max_len);
       if (c.fuse_L < 32) c.fuse_L = 0;   // below the shortest Bluestein length: nothing is fused
+      if (c.fuse_L > 0) {
+        // the shortest Bluestein length any round of the slot can have is that of the smallest
+        // prime its rule (k* = 1) or list gives; a slot whose rounds are all longer never fuses,
+        // and an engine without fusable slots launches no fused kernel
+        int64_t p_reach;
+        if (!d.primes.empty()) p_reach = *std::min_element(d.primes.begin(), d.primes.end());
+        else p_reach = first_prime_at_least(std::max<int64_t>(std::max<int64_t>((d.c8 + 7) / 8, d.p_min), 2));
+        if (p_reach < 2 || bluestein_length(2 * p_reach - 1) > c.fuse_L) c.fuse_L = 0;
+      }
       c.blk_off = (int64_t)shblk.size();
       if (d.shift_block) {
         int start = 0;
@@ -1239,8 +1273,10 @@ class Engine final : public EngineBase {
     for (int q = 0; q < kNumScans; ++q) ECHK(alloc(&scans_.v[q], (size_t)(n_ + 1) * sizeof(int64_t)));
     ECHK(alloc(&ptab_, ptab.size() * sizeof(int32_t)));
     ECHK(alloc(&pfirst_, pfirst.size() * sizeof(int32_t)));
-    ECHK(alloc(&powner_, (size_t)(pmax_all + 1) * sizeof(int32_t)));
-    ECHK(cudaMemsetAsync(powner_, kNoOwnerByte, (size_t)(pmax_all + 1) * sizeof(int32_t), st_));
+    ECHK(alloc(&powner_, (size_t)(pmax_all + 1) * sizeof(unsigned long long)));
+    ECHK(cudaMemsetAsync(powner_, 0xFF, (size_t)(pmax_all + 1) * sizeof(unsigned long long), st_));
+    ECHK(alloc(&pacc_, sizeof(PlanAcc)));
+    ECHK(cudaMemsetAsync(pacc_, 0, sizeof(PlanAcc), st_));
     ECHK(alloc(&dirs_, std::max<size_t>(dirs.size(), 1) * sizeof(int64_t)));
     ECHK(alloc(&shblk_, std::max<size_t>(shblk.size(), 1) * sizeof(int32_t)));
     ECHK(alloc(&plist_, std::max<size_t>(plist.size(), 1) * sizeof(int64_t)));
@@ -1500,10 +1536,10 @@ class Engine final : public EngineBase {
   // the round's plan: every signal's parameters over the grid, then the sums and scans in one block
   cudaError_t launch_plan(const PlanArgs& pa, int64_t* launches) {
     k_plan_signals<T><<<(n_ + 127) / 128, 128, 0, st_>>>(pa, cfg_, run_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_,
-                                                          plist_, u_, hist_);
+                                                          plist_, u_, hist_, pacc_, powner_);
     ECHK(cudaGetLastError());
     k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_,
-                                            plist_, u_, hist_, powner_);
+                                            plist_, u_, hist_, pacc_, powner_);
     launches[0] += 2;
     return cudaGetLastError();
   }
@@ -1868,10 +1904,10 @@ class Engine final : public EngineBase {
     pa.force_p = p;
     pa.force_K = K;
     k_plan_signals<T><<<(n_ + 127) / 128, 128, 0, st_>>>(pa, cfg_, run_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_,
-                                                          plist_, u_, nullptr);
+                                                          plist_, u_, nullptr, pacc_, powner_);
     ECHK(cudaGetLastError());
     k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_, plist_, u_,
-                                            nullptr, powner_);
+                                            nullptr, pacc_, powner_);
     ECHK(cudaGetLastError());
     return launch_tables();
   }
@@ -1976,7 +2012,8 @@ class Engine final : public EngineBase {
   Scans scans_;
   int32_t* ptab_ = nullptr;
   int32_t* pfirst_ = nullptr;
-  int32_t* powner_ = nullptr;   // [p_max + 1] first batched signal of each prime in k_plan (kNoOwner between)
+  unsigned long long* powner_ = nullptr;   // [p_max + 1] owner election keys (owner_key), all ones at creation
+  PlanAcc* pacc_ = nullptr;                // the round's totals between k_plan_signals and k_plan
   int64_t pfirst_n_ = 0;
   int64_t* dirs_ = nullptr;
   int32_t* shblk_ = nullptr;   // (start, size) per shift block of every slot (block form)

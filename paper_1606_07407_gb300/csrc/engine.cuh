@@ -108,6 +108,15 @@ struct RoundCtl {
   int64_t fused_iters;                        // fused rounds launched (whole run)
 };
 
+// The round's totals, gathered over the grid while the signals are planned (k_plan_signals)
+// and read by k_plan, which clears them for the next round.  epoch numbers the plan launches of
+// the engine (never cleared): the owner election of round e keys powner[p] by e.
+struct PlanAcc {
+  unsigned long long tiles, active, fused;   // batched tiles; active and fused signals
+  unsigned long long wsum[65];               // sum of n_sets p over batched signals with min(chunks, 64) = c
+  unsigned int epoch, pad;
+};
+
 // exclusive scans over signals: tables, modes, DFT rows, filters, bins, four-step passes, DFT
 // rows and filters of short lengths, then sampling tiles for each set-group size 1..kMaxSetGroup
 constexpr int kNumScans = 10 + kMaxSetGroup;
