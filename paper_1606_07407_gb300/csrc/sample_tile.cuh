@@ -37,14 +37,17 @@ template <typename T> constexpr int sample_stages() { return sizeof(T) == 4 ? 2 
 
 // Staged data of one or two 32-mode chunks, overlaid at the end of a tile by the buffer that
 // adds the mode groups' sums (half of the warps' sums at a time).
+// In float the per-set coefficients of a mode are padded to an even count, so that the
+// accumulation reads two sets' values with one 16-byte shared-memory load.
 template <typename T, int NS>
-struct SampleSmem {
+struct alignas(16) SampleSmem {
   static constexpr int S = sample_stages<T>();
   static constexpr int RP = row_pairs(NS);
+  static constexpr int NSP = sizeof(T) == 4 ? ((NS + 1) & ~1) : NS;
   struct Stage {
     c2<T> Ls[S][kSampleChunk][32];
     c2<T> Us[S][kSampleChunk][kSampleWarps * RP];
-    c2<T> Cs[S][kSampleChunk][NS];
+    c2<T> Cs[S][kSampleChunk][NSP];
   };
   static constexpr int kRedValues = (kSampleWarps / 2) * RP * NS * 4 * 32;
   union {
@@ -70,11 +73,18 @@ __device__ __forceinline__ void accumulate_chunk(const SampleSmem<T, NS>& sm, in
   for (int jj = grp; jj < kSampleChunk; jj += G) {
     const C2 L = sm.st.Ls[b][jj][lane];
     C2 E[Q];
+    if constexpr (sizeof(T) == 4 && RP % 2 == 0 && Q % 2 == 0) {   // two rows per 16-byte load
 #pragma unroll
-    for (int qq = 0; qq < Q; ++qq) E[qq] = cmul(sm.st.Us[b][jj][wrow * RP + qq], L);
+      for (int qq = 0; qq < Q; qq += 2) {
+        const float4 u4 = *reinterpret_cast<const float4*>(&sm.st.Us[b][jj][wrow * RP + qq]);
+        E[qq] = cmul(mk2(u4.x, u4.y), L);
+        E[qq + 1] = cmul(mk2(u4.z, u4.w), L);
+      }
+    } else {
 #pragma unroll
-    for (int nn = 0; nn < NS; ++nn) {
-      const C2 cc = sm.st.Cs[b][jj][nn];
+      for (int qq = 0; qq < Q; ++qq) E[qq] = cmul(sm.st.Us[b][jj][wrow * RP + qq], L);
+    }
+    auto term = [&](int nn, C2 cc) {
 #pragma unroll
       for (int qq = 0; qq < Q; ++qq) {
         acc[qq][nn][0] = fma(cc.x, E[qq].x, acc[qq][nn][0]);   // P1: c_r e_r
@@ -82,6 +92,17 @@ __device__ __forceinline__ void accumulate_chunk(const SampleSmem<T, NS>& sm, in
         acc[qq][nn][2] = fma(cc.x, E[qq].y, acc[qq][nn][2]);   // P3: c_r e_i
         acc[qq][nn][3] = fma(cc.y, E[qq].x, acc[qq][nn][3]);   // P4: c_i e_r
       }
+    };
+    if constexpr (sizeof(T) == 4) {   // two sets per 16-byte load (rows padded to even)
+#pragma unroll
+      for (int nn = 0; nn < NS; nn += 2) {
+        const float4 c4 = *reinterpret_cast<const float4*>(&sm.st.Cs[b][jj][nn]);
+        term(nn, mk2(c4.x, c4.y));
+        if (nn + 1 < NS) term(nn + 1, mk2(c4.z, c4.w));
+      }
+    } else {
+#pragma unroll
+      for (int nn = 0; nn < NS; ++nn) term(nn, sm.st.Cs[b][jj][nn]);
     }
   }
 #pragma unroll
@@ -270,8 +291,9 @@ __device__ void sample_tile(SampleSmem<T, NS>& sm, const SigCfg& c, const SigRun
       cp_async<sizeof(C2)>(&sm.st.Us[b][jj][row],
                            W + mod_small((unsigned)sm.be[b][jj] + (unsigned)row * (unsigned)sm.ga[b][jj], p, inv_p));
     }
-    for (int e = tid; e < kSampleChunk * NS; e += kSampleThreads) {
-      const int jj = e / NS, nn = e - jj * NS;
+    constexpr int NSP = SampleSmem<T, NS>::NSP;
+    for (int e = tid; e < kSampleChunk * NSP; e += kSampleThreads) {
+      const int jj = e / NSP, nn = e - jj * NSP;
       if (jj < nj && nn < ns_valid) cp_async<sizeof(C2)>(&sm.st.Cs[b][jj][nn], Cm + (int64_t)(n0 + nn) * c.Kmax + jc + jj);
       else sm.st.Cs[b][jj][nn] = zero;
     }
