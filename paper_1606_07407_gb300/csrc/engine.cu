@@ -1079,6 +1079,11 @@ class Engine final : public EngineBase {
     if (fork_ev_) cudaEventDestroy(fork_ev_);
     if (join_ev_) cudaEventDestroy(join_ev_);
     if (side_) cudaStreamDestroy(side_);
+    for (int q = 0; q < kMaxSetGroup - 1; ++q) {
+      if (samp_join_[q]) cudaEventDestroy(samp_join_[q]);
+      if (samp_st_[q]) cudaStreamDestroy(samp_st_[q]);
+    }
+    if (samp_fork_) cudaEventDestroy(samp_fork_);
     for (void* q : allocs_) cudaFree(q);
     if (host_stage_) cudaFreeHost(host_stage_);
   }
@@ -1394,6 +1399,11 @@ class Engine final : public EngineBase {
     ECHK(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking));
     ECHK(cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming));
     ECHK(cudaEventCreateWithFlags(&join_ev_, cudaEventDisableTiming));
+    ECHK(cudaEventCreateWithFlags(&samp_fork_, cudaEventDisableTiming));
+    for (int q = 0; q < kMaxSetGroup - 1; ++q) {
+      ECHK(cudaStreamCreateWithFlags(&samp_st_[q], cudaStreamNonBlocking));
+      ECHK(cudaEventCreateWithFlags(&samp_join_[q], cudaEventDisableTiming));
+    }
     ECHK(cudaStreamSynchronize(st_));
     return cudaSuccess;
   }
@@ -1427,18 +1437,29 @@ class Engine final : public EngineBase {
 
   // with_filters: the filter spectra first, on the same stream (else they were made beside the
   // sampling, see enqueue_batched)
+  // The short- and long-row launches take different rows: with both present, the short one runs
+  // on a stream of its own beside the long one.
   cudaError_t launch_dft_rows(bool with_filters = true) {
     const TwSrc<C2> tws = tw_src();
     if (with_filters) ECHK(launch_filters(st_));
-    k_dft<T><<<(unsigned)rows_max_, dft_thr_s_, dft_smem_s_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
-                                                                   (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 1,
-                                                                   (int)dft_smem_s_);
+    const bool both = small_logL_max_ > kSmallFftLog;
+    cudaStream_t s_short = st_;
+    if (both) {
+      ECHK(cudaEventRecord(samp_fork_, st_));
+      s_short = samp_st_[0];
+      ECHK(cudaStreamWaitEvent(s_short, samp_fork_, 0));
+    }
+    k_dft<T><<<(unsigned)rows_max_, dft_thr_s_, dft_smem_s_, s_short>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
+                                                                       (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 1,
+                                                                       (int)dft_smem_s_);
     ECHK(cudaGetLastError());
-    if (small_logL_max_ > kSmallFftLog) {
+    if (both) {
+      ECHK(cudaEventRecord(samp_join_[0], s_short));
       k_dft<T><<<(unsigned)rows_max_, small_threads_, smem_dft_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
                                                                          (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 0,
                                                                          (int)smem_dft_);
       ECHK(cudaGetLastError());
+      ECHK(cudaStreamWaitEvent(st_, samp_join_[0], 0));
     }
     return cudaSuccess;
   }
@@ -1457,20 +1478,31 @@ class Engine final : public EngineBase {
   }
 
   // one persistent sampling launch per set-group size present in the batch
+  // The launches are independent (each takes its own queue of tiles): the first runs on the
+  // engine's stream, the others on streams of their own forked from it and joined back, so that
+  // each persistent launch's last, partly empty wave overlaps the next one's blocks.
   cudaError_t launch_samples(int64_t* launches) {
+    int forked = 0;
+    bool first = true;
     for (int ns = 1; ns <= kMaxSetGroup; ++ns) {
       if (!(ns_mask_ & (1u << (ns - 1)))) continue;
+      cudaStream_t s = st_;
+      if (!first) {
+        if (forked == 0) ECHK(cudaEventRecord(samp_fork_, st_));
+        s = samp_st_[forked];
+        ECHK(cudaStreamWaitEvent(s, samp_fork_, 0));
+      }
 #define SFFT_SAMPLE(NSV)                                                                                      \
   case NSV:                                                                                                   \
     if constexpr (sizeof(T) == 8) {                                                                           \
       if (any_df_) {                                                                                          \
-        k_sample<T, NSV, true><<<2 * n_sm_, kSampleThreads, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, alpha_,   \
-                                                                      gam_, (C2*)Cm_, (C2*)tab_, (C2*)part_); \
+        k_sample<T, NSV, true><<<2 * n_sm_, kSampleThreads, 0, s>>>(n_, cfg_, run_, ctl_, scans_, alpha_,     \
+                                                                    gam_, (C2*)Cm_, (C2*)tab_, (C2*)part_);   \
         break;                                                                                                \
       }                                                                                                       \
     }                                                                                                         \
-    k_sample<T, NSV, false><<<2 * n_sm_, kSampleThreads, 0, st_>>>(n_, cfg_, run_, ctl_, scans_, alpha_, gam_, \
-                                                                   (C2*)Cm_, (C2*)tab_, (C2*)part_);         \
+    k_sample<T, NSV, false><<<2 * n_sm_, kSampleThreads, 0, s>>>(n_, cfg_, run_, ctl_, scans_, alpha_, gam_,   \
+                                                                 (C2*)Cm_, (C2*)tab_, (C2*)part_);           \
     break;
       switch (ns) {
         SFFT_SAMPLE(1)
@@ -1486,7 +1518,13 @@ class Engine final : public EngineBase {
 #undef SFFT_SAMPLE
       ECHK(cudaGetLastError());
       if (launches) launches[2] += 1;
+      if (!first) {
+        ECHK(cudaEventRecord(samp_join_[forked], s));
+        ++forked;
+      }
+      first = false;
     }
+    for (int q = 0; q < forked; ++q) ECHK(cudaStreamWaitEvent(st_, samp_join_[q], 0));
     return cudaSuccess;
   }
 
@@ -2005,6 +2043,9 @@ class Engine final : public EngineBase {
   std::vector<cudaEvent_t> events_;
   cudaStream_t side_ = nullptr;                            // filter spectra beside the sampling
   cudaEvent_t fork_ev_ = nullptr, join_ev_ = nullptr;
+  // the sampling launches of the set-group sizes after the first run on streams of their own
+  cudaStream_t samp_st_[kMaxSetGroup - 1] = {};
+  cudaEvent_t samp_fork_ = nullptr, samp_join_[kMaxSetGroup - 1] = {};
   void* host_stage_ = nullptr;
   SigCfg* cfg_ = nullptr;
   SigRun* run_ = nullptr;
