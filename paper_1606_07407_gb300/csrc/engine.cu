@@ -136,69 +136,27 @@ __host__ __device__ inline int dft_group_rows(int L, int nthr, int64_t smem_elem
   return g < n_sets ? g : n_sets;
 }
 
-// The round's parameters of every signal not already planned by the fused kernel (stop rule,
-// prime, direction mod p, work geometry: plan_signal), one thread per signal over the whole
-// grid; k_plan then sums and scans the work.
-// The same threads then add the round's totals into acc (active and fused signals, batched
-// tiles, and the histogram of n_sets p by mode chunks from which k_plan sizes the mode splits)
-// and elect each shared prime's owner.
-template <typename T>
-__global__ void k_plan_signals(PlanArgs a, const SigCfg* __restrict__ cfg, SigRun* run, const int32_t* __restrict__ ptab,
-                               int n_ptab, const int32_t* __restrict__ pfirst, int64_t pfirst_n,
-                               const int64_t* __restrict__ dirs, const int64_t* __restrict__ plist, int64_t* ubuf,
-                               HistRec* hist, PlanAcc* acc, unsigned long long* __restrict__ powner) {
-  __shared__ unsigned long long s_tot[3], s_w[65];
-  for (int i = threadIdx.x; i < 65; i += blockDim.x) s_w[i] = 0ull;
-  if (threadIdx.x < 3) s_tot[threadIdx.x] = 0ull;
-  __syncthreads();
-  const unsigned int epoch = acc->epoch;
-  const PrimeTables pt{ptab, n_ptab, pfirst, pfirst_n, dirs, plist};
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += gridDim.x * blockDim.x) {
-    SigRun r = run[s];
-    if (!(r.active && r.fused)) {
-      plan_signal<T>(a, cfg[s], r, pt, ubuf, hist, s == 0);
-      run[s] = r;
-    }
-    if (r.active) {
-      atomicAdd(&s_tot[1], 1ull);
-      if (r.fused) {
-        atomicAdd(&s_tot[2], 1ull);
-      } else {
-        atomicAdd(&s_tot[0], (unsigned long long)r.n_xt * (unsigned long long)r.groups);
-        atomicAdd(&s_w[min(r.chunks, 64)], (unsigned long long)cfg[s].n_sets * (unsigned long long)r.p);
-        if (!uses_engine_tables(a, cfg[s], r)) atomicMin(&powner[r.p], owner_key(epoch, s));
-      }
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < 3 && s_tot[threadIdx.x]) atomicAdd(&(&acc->tiles)[threadIdx.x], s_tot[threadIdx.x]);
-  for (int i = threadIdx.x; i < 65; i += blockDim.x)
-    if (s_w[i]) atomicAdd(&acc->wsum[i], s_w[i]);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg* __restrict__ cfg, SigRun* run,
-                                                       RoundCtl* ctl, Scans sc, const int32_t* __restrict__ ptab,
-                                                       int n_ptab, const int32_t* __restrict__ pfirst, int64_t pfirst_n,
-                                                       const int64_t* __restrict__ dirs,
-                                                       const int64_t* __restrict__ plist, int64_t* ubuf,
-                                                       HistRec* hist, PlanAcc* acc,
-                                                       const unsigned long long* __restrict__ powner) {
-  __shared__ int s_S;
-  __shared__ int64_t s_part;   // partial-sum elements at the chosen S
+// The round's mode splits, by the last block of k_plan_signals (all of its threads; the round's
+// totals in acc, the blocks' tiles and tail sums in blk).  S (1..64): the persistent sampling
+// kernel's 2 n_sm blocks take tiles x S items of 1/S of the modes each; S minimises its waves per
+// unit of work, ceil(items / blocks) / S, with 12% per extra split for the partial sums it adds
+// and the DFT reads back, then it is halved until the partial sums fit their arena.  Tail: when
+// the items (tiles unsplit) leave the last wave mostly empty (rem of 2 n_sm blocks busy), the
+// signals whose tiles fall in that wave split their modes q ways, so that their work spreads
+// over the idle blocks, if the partial sums still fit.  Also gives each block its exclusive
+// offset in the queue of tiles.
+__device__ void plan_decide(const PlanArgs& a, const SigCfg* __restrict__ cfg, const SigRun* run, const PlanAcc* acc,
+                            PlanBlk* blk, PlanDec* dec, int nblk) {
   __shared__ unsigned long long s_key;
-  __shared__ unsigned long long s_w[65];
-  const int n = a.n;
-  // the round's totals, gathered by k_plan_signals
-  const int64_t tot_tiles = (int64_t)acc->tiles;
-  const int64_t tot_active = (int64_t)acc->active;
-  const int64_t tot_fused = (int64_t)acc->fused;
-  for (int i = threadIdx.x; i < 65; i += blockDim.x) s_w[i] = acc->wsum[i];
-  // mode splits S (1..64): the persistent sampling kernel's 2 n_sm blocks take tiles x S items of
-  // 1/S of the modes each; S minimises its waves per unit of work, ceil(items / blocks) / S, with
-  // 12% per extra split for the partial sums it adds and the DFT reads back (then it is halved to
-  // fit the partial-sum arena).  Thread S - 1 scores S; the smallest score wins, ties to small S.
-  if (threadIdx.x == 0) s_key = ~0ull;
+  __shared__ int s_S;
+  __shared__ int64_t s_part, s_extra;
+  __shared__ int s_bstar;
+  const int64_t tot_tiles = (int64_t)__ldcg(&acc->tiles);
+  if (threadIdx.x == 0) {
+    s_key = ~0ull;
+    s_bstar = nblk;
+    s_extra = 0;
+  }
   __syncthreads();
   if (threadIdx.x < 64 && tot_tiles > 0) {
     const int64_t S = threadIdx.x + 1;
@@ -213,7 +171,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     int S = tot_tiles > 0 ? (int)(s_key & 63ull) + 1 : 1;
     for (;;) {
       int64_t tot = 0;
-      for (int q = 1; q <= 64; ++q) tot += (int64_t)min(S, q) * (int64_t)s_w[q];
+      for (int q = 1; q <= 64; ++q) tot += (int64_t)min(S, q) * (int64_t)__ldcg(&acc->wsum[q]);
       s_part = tot;
       if (tot <= a.part_cap || S == 1) break;
       S /= 2;
@@ -222,136 +180,249 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
   }
   __syncthreads();
   const int S = s_S;
-  // Tail of the sampling queue: when the items (tiles unsplit) leave the persistent kernel's last
-  // wave mostly empty (rem of 2 n_sm blocks busy), the signals whose tiles fall in that wave split
-  // their modes q ways, so their work spreads over the idle blocks, if the partial sums still fit.
   const int64_t slots = 2LL * a.n_sm;
   const int64_t rem = tot_tiles % slots;
   const int64_t tail_from = tot_tiles - rem;   // queue position (in tiles) where the last wave starts
   int q_tail = 1;
   if (S == 1 && rem > 0 && 5 * rem < 4 * slots) {
     const int q = (int)min((int64_t)8, max((int64_t)2, slots / rem));
-    int64_t extra = 0, tcarry = 0;
-    for (int base = 0; base < n; base += blockDim.x) {
-      const int s = base + threadIdx.x;
-      int64_t tv[1] = {0}, tt[1];
-      SigRun r;
+    // blocks' exclusive tile offsets; the first block whose tiles reach into the last wave
+    int64_t carry = 0;
+    for (int base = 0; base < nblk; base += blockDim.x) {
+      const int b = base + threadIdx.x;
+      int64_t tv[1] = {b < nblk ? (int64_t)__ldcg(&blk[b].tiles) : 0}, tt[1];
+      const int64_t tb = tv[0];
+      block_scan_excl<1>(tv, tt);
+      if (b < nblk) {
+        blk[b].tile_off = carry + tv[0];
+        if (carry + tv[0] + tb > tail_from) atomicMin(&s_bstar, b);
+      }
+      carry += tt[0];
+    }
+    __syncthreads();
+    const int bstar = s_bstar;
+    // the blocks after it are in the tail whole; the boundary block signal by signal
+    int64_t extra = 0;
+    for (int b = bstar + 1 + (int)threadIdx.x; b < nblk; b += blockDim.x) extra += (int64_t)__ldcg(&blk[b].extra[q - 2]);
+    if (bstar < nblk) {
+      const int s = bstar * kPlanBlk + (int)threadIdx.x;
       bool batched = false;
-      if (s < n) {
-        r = run[s];
-        batched = r.active && !r.fused;
-        if (batched) tv[0] = (int64_t)r.n_xt * r.groups;
+      int64_t tv[1] = {0}, tt[1];
+      int chunks = 0;
+      int64_t w = 0;
+      if (threadIdx.x < kPlanBlk && s < a.n) {
+        const int active = __ldcg(&run[s].active), fused = __ldcg(&run[s].fused);
+        batched = active && !fused;
+        if (batched) {
+          tv[0] = (int64_t)__ldcg(&run[s].n_xt) * __ldcg(&run[s].groups);
+          chunks = __ldcg(&run[s].chunks);
+          w = (int64_t)cfg[s].n_sets * __ldcg(&run[s].p);
+        }
       }
       const int64_t tiles_s = tv[0];
       block_scan_excl<1>(tv, tt);
-      if (batched && tcarry + tv[0] + tiles_s > tail_from)
-        extra += (int64_t)(min(q, r.chunks) - 1) * cfg[s].n_sets * r.p;
-      tcarry += tt[0];
+      if (batched && __ldcg(&blk[bstar].tile_off) + tv[0] + tiles_s > tail_from)
+        extra += (int64_t)max(min(q, chunks) - 1, 0) * w;
     }
     const int64_t tot_extra = block_sum(extra);
     if (s_part + tot_extra <= a.part_cap) q_tail = q;
   }
+  if (threadIdx.x == 0) {
+    dec->S = S;
+    dec->q_tail = q_tail;
+    dec->tail_from = tail_from;
+  }
+}
+
+// The round's parameters of every signal not already planned by the fused kernel (stop rule,
+// prime, direction mod p, work geometry: plan_signal), one thread per signal over the whole
+// grid; k_plan then sums and scans the work.
+// The same threads then add the round's totals into acc (active and fused signals, batched
+// tiles, and the histogram of n_sets p by mode chunks from which the mode splits are sized),
+// elect each shared prime's owner, and give their block's batched tiles and, for each tail split
+// q = 2..8, the partial sums those splits would add (blk).  The last block to finish (the
+// others' results visible to it through the fence before its arrival) then decides the round's
+// splits: S for every signal, q_tail for those whose tiles fall in the sampling queue's last
+// wave (dec).
+template <typename T>
+__global__ void __launch_bounds__(kPlanBlk) k_plan_signals(PlanArgs a, const SigCfg* __restrict__ cfg, SigRun* run,
+                                                           const int32_t* __restrict__ ptab, int n_ptab,
+                                                           const int32_t* __restrict__ pfirst, int64_t pfirst_n,
+                                                           const int64_t* __restrict__ dirs,
+                                                           const int64_t* __restrict__ plist, int64_t* ubuf,
+                                                           HistRec* hist, PlanAcc* acc,
+                                                           unsigned long long* __restrict__ powner, PlanBlk* blk,
+                                                           PlanDec* dec) {
+  __shared__ unsigned long long s_tot[3], s_w[65], s_extra[7];
+  __shared__ int s_last;
+  for (int i = threadIdx.x; i < 65; i += blockDim.x) s_w[i] = 0ull;
+  if (threadIdx.x < 3) s_tot[threadIdx.x] = 0ull;
+  if (threadIdx.x < 7) s_extra[threadIdx.x] = 0ull;
+  __syncthreads();
+  const unsigned int epoch = acc->epoch;
+  const PrimeTables pt{ptab, n_ptab, pfirst, pfirst_n, dirs, plist};
+  const int s = blockIdx.x * kPlanBlk + threadIdx.x;   // one signal per thread (grid: ceil(n / kPlanBlk))
+  if (s < a.n) {
+    SigRun r = run[s];
+    if (!(r.active && r.fused)) {
+      plan_signal<T>(a, cfg[s], r, pt, ubuf, hist, s == 0);
+      run[s] = r;
+    }
+    if (r.active) {
+      atomicAdd(&s_tot[1], 1ull);
+      if (r.fused) {
+        atomicAdd(&s_tot[2], 1ull);
+      } else {
+        const unsigned long long w = (unsigned long long)cfg[s].n_sets * (unsigned long long)r.p;
+        atomicAdd(&s_tot[0], (unsigned long long)r.n_xt * (unsigned long long)r.groups);
+        atomicAdd(&s_w[min(r.chunks, 64)], w);
+        for (int q = 2; q <= 8; ++q)
+          if (min(q, r.chunks) > 1) atomicAdd(&s_extra[q - 2], (unsigned long long)(min(q, r.chunks) - 1) * w);
+        if (!uses_engine_tables(a, cfg[s], r)) atomicMin(&powner[r.p], owner_key(epoch, s));
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 3 && s_tot[threadIdx.x]) atomicAdd(&(&acc->tiles)[threadIdx.x], s_tot[threadIdx.x]);
+  for (int i = threadIdx.x; i < 65; i += blockDim.x)
+    if (s_w[i]) atomicAdd(&acc->wsum[i], s_w[i]);
+  if (threadIdx.x == 0) blk[blockIdx.x].tiles = s_tot[0];
+  if (threadIdx.x < 7) blk[blockIdx.x].extra[threadIdx.x] = s_extra[threadIdx.x];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&dec->done1, 1u) == gridDim.x - 1 ? 1 : 0;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  plan_decide(a, cfg, run, acc, blk, dec, (int)gridDim.x);
+  if (threadIdx.x == 0) dec->done1 = 0u;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPlanBlk) k_plan_scan(PlanArgs a, const SigCfg* __restrict__ cfg, SigRun* run,
+                                                        RoundCtl* ctl, Scans sc, PlanAcc* acc,
+                                                        const unsigned long long* __restrict__ powner, PlanBlk* blk,
+                                                        PlanDec* dec) {
+  __shared__ int s_last;
+  const int n = a.n;
+  const int S = dec->S, q_tail = dec->q_tail;
+  const int64_t tail_from = dec->tail_from;
+  const int s = blockIdx.x * kPlanBlk + threadIdx.x;
+  int64_t v[kNumScans + 1];
+#pragma unroll
+  for (int q = 0; q <= kNumScans; ++q) v[q] = 0;
+  SigRun r;
+  bool batched = false;   // active and not left to the fused kernel
+  if (s < n) {
+    r = run[s];
+    batched = r.active && !r.fused;
+  }
+  bool in_tail = false;   // the signal's tiles reach into the last wave (split q_tail ways)
+  if (q_tail > 1) {
+    int64_t tv[1] = {batched ? (int64_t)r.n_xt * r.groups : 0}, tt[1];
+    const int64_t tiles_s = tv[0];
+    block_scan_excl<1>(tv, tt);
+    in_tail = batched && blk[blockIdx.x].tile_off + tv[0] + tiles_s > tail_from;
+  }
   // Batched signals with the same prime share one copy of the tables (W, chirp) and of the filter
   // spectrum: that of the first of them, the owner elected in powner[p] by k_plan_signals.  Round
   // 1 with the tables made with the engine needs no owner.
-  // pass 2: per-signal work counts and their exclusive scans
-  int64_t carry[kNumScans];
-#pragma unroll
-  for (int q = 0; q < kNumScans; ++q) carry[q] = 0;
-  int64_t part_carry = 0, tile_carry = 0;
-  for (int base = 0; base < n; base += blockDim.x) {
-    const int s = base + threadIdx.x;
-    int64_t v[kNumScans + 1];
-#pragma unroll
-    for (int q = 0; q <= kNumScans; ++q) v[q] = 0;
-    SigRun r;
-    bool batched = false;   // active and not left to the fused kernel
-    if (s < n) {
-      r = run[s];
-      batched = r.active && !r.fused;
-    }
-    bool in_tail = false;   // the signal's tiles reach into the last wave (split q_tail ways)
-    if (q_tail > 1) {
-      int64_t tv[1] = {batched ? (int64_t)r.n_xt * r.groups : 0}, tt[1];
-      const int64_t tiles_s = tv[0];
-      block_scan_excl<1>(tv, tt);
-      in_tail = batched && tile_carry + tv[0] + tiles_s > tail_from;
-      tile_carry += tt[0];
-    }
-    if (batched && uses_engine_tables(a, cfg[s], r)) {
-      r.tab_at = cfg[s].tab0_off;
-      r.bhat_at = cfg[s].bhat0_off;
-      r.tab_owner = 0;
-    } else if (batched) {
-      const int own = (int)(powner[r.p] & 0xFFFFFFFFull);
-      r.tab_at = cfg[own].tab_off;
-      r.bhat_at = cfg[own].bhat_off;
-      r.tab_owner = own == s ? 1 : 0;
-    }
-    if (s < n) {
-      if (batched) {
-        const SigCfg& c = cfg[s];
-        const int K = a.force ? a.force_K : sampled_modes(c, r);
-        int sp = min(in_tail ? q_tail : S, r.chunks);
-        r.jper = ((r.chunks + sp - 1) / sp) * kSampleChunk;
-        r.splits = K > 0 ? (K + r.jper - 1) / r.jper : 1;
-        v[SC_TAB] = r.tab_owner ? r.p : 0;
-        v[SC_MODE] = K;
-        // constant indices only: a computed index would put v in local memory
-#pragma unroll
-        for (int q = 0; q < kMaxSetGroup; ++q)
-          if (q == r.gsize - 1) v[SC_SAMP0 + q] = (int64_t)r.n_xt * r.groups * r.splits;
-        v[SC_BINS] = r.p;
-        if (r.dense) {
-          // the dense tensor-core kernel takes the signal's rows (no Bluestein row or filter)
-        } else if (!r.big) {
-          const bool sm = r.L <= (1 << kSmallFftLog);
-          const int g = dft_group_rows<c2<T>>(r.L, sm ? a.dft_thr_s : a.dft_thr_l,
-                                             (sm ? a.dft_smem_s : a.dft_smem_l) / (int64_t)sizeof(c2<T>), c.n_sets);
-          const int64_t groups = (c.n_sets + g - 1) / g;   // row groups
-          if (sm) {
-            v[SC_ROWS_S] = groups;
-            v[SC_FILT_S] = r.tab_owner;
-          } else {
-            v[SC_ROWS] = groups;
-            v[SC_FILT] = r.tab_owner;
-          }
-        } else {
-          int M1, M2, CT, RT;
-          big_geom(r.logL, &M1, &M2, &CT, &RT);
-          v[SC_BIGA] = (int64_t)(c.n_sets + 1) * (M2 / CT);
-          v[SC_BIGB] = (int64_t)c.n_sets * (M1 / RT);
-          v[SC_BIGC] = (int64_t)c.n_sets * (M2 / CT);
-        }
-        v[kNumScans] = (int64_t)r.splits * c.n_sets * r.p;
-      }
-    }
-    int64_t tot[kNumScans + 1];
-    block_scan_excl<kNumScans + 1>(v, tot);
-    if (s < n) {
-#pragma unroll
-      for (int q = 0; q < kNumScans; ++q) sc.v[q][s] = carry[q] + v[q];
-      if (batched) {   // the fields pass 2 sets (the whole record would be 224 bytes of stores)
-        SigRun& o = run[s];
-        o.tab_at = r.tab_at;
-        o.bhat_at = r.bhat_at;
-        o.tab_owner = r.tab_owner;
-        o.jper = r.jper;
-        o.splits = r.splits;
-        o.part_off = part_carry + v[kNumScans];
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < kNumScans; ++q) carry[q] += tot[q];
-    part_carry += tot[kNumScans];
+  if (batched && uses_engine_tables(a, cfg[s], r)) {
+    r.tab_at = cfg[s].tab0_off;
+    r.bhat_at = cfg[s].bhat0_off;
+    r.tab_owner = 0;
+  } else if (batched) {
+    const int own = (int)(powner[r.p] & 0xFFFFFFFFull);
+    r.tab_at = cfg[own].tab_off;
+    r.bhat_at = cfg[own].bhat_off;
+    r.tab_owner = own == s ? 1 : 0;
   }
-  __syncthreads();   // every total has been read: clear them for the next round
-  if (threadIdx.x == 0) {
-    acc->tiles = acc->active = acc->fused = 0ull;
-    acc->epoch += 1;
+  if (batched) {
+    const SigCfg& c = cfg[s];
+    const int K = a.force ? a.force_K : sampled_modes(c, r);
+    const int sp = min(in_tail ? q_tail : S, r.chunks);
+    r.jper = ((r.chunks + sp - 1) / sp) * kSampleChunk;
+    r.splits = K > 0 ? (K + r.jper - 1) / r.jper : 1;
+    v[SC_TAB] = r.tab_owner ? r.p : 0;
+    v[SC_MODE] = K;
+    // constant indices only: a computed index would put v in local memory
+#pragma unroll
+    for (int q = 0; q < kMaxSetGroup; ++q)
+      if (q == r.gsize - 1) v[SC_SAMP0 + q] = (int64_t)r.n_xt * r.groups * r.splits;
+    v[SC_BINS] = r.p;
+    if (r.dense) {
+      // the dense tensor-core kernel takes the signal's rows (no Bluestein row or filter)
+    } else if (!r.big) {
+      const bool sm = r.L <= (1 << kSmallFftLog);
+      const int g = dft_group_rows<c2<T>>(r.L, sm ? a.dft_thr_s : a.dft_thr_l,
+                                         (sm ? a.dft_smem_s : a.dft_smem_l) / (int64_t)sizeof(c2<T>), c.n_sets);
+      const int64_t groups = (c.n_sets + g - 1) / g;   // row groups
+      if (sm) {
+        v[SC_ROWS_S] = groups;
+        v[SC_FILT_S] = r.tab_owner;
+      } else {
+        v[SC_ROWS] = groups;
+        v[SC_FILT] = r.tab_owner;
+      }
+    } else {
+      int M1, M2, CT, RT;
+      big_geom(r.logL, &M1, &M2, &CT, &RT);
+      v[SC_BIGA] = (int64_t)(c.n_sets + 1) * (M2 / CT);
+      v[SC_BIGB] = (int64_t)c.n_sets * (M1 / RT);
+      v[SC_BIGC] = (int64_t)c.n_sets * (M2 / CT);
+    }
+    v[kNumScans] = (int64_t)r.splits * c.n_sets * r.p;
   }
-  for (int i = threadIdx.x; i < 65; i += blockDim.x) acc->wsum[i] = 0ull;
+  int64_t tot[kNumScans + 1];
+  block_scan_excl<kNumScans + 1>(v, tot);
+  // offsets within the block; k_plan_offsets adds the block's offset
+  if (s < n) {
+#pragma unroll
+    for (int q = 0; q < kNumScans; ++q) sc.v[q][s] = v[q];
+    if (batched) {   // the fields this pass sets (the whole record would be 224 bytes of stores)
+      SigRun& o = run[s];
+      o.tab_at = r.tab_at;
+      o.bhat_at = r.bhat_at;
+      o.tab_owner = r.tab_owner;
+      o.jper = r.jper;
+      o.splits = r.splits;
+      o.part_off = v[kNumScans];
+    }
+  }
   if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q <= kNumScans; ++q) blk[blockIdx.x].tot[q] = tot[q];
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&dec->done2, 1u) == gridDim.x - 1 ? 1 : 0;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // the last block: exclusive scan of the blocks' totals (kept in blk[b].tot as offsets), the
+  // round's totals into the scans' last entries and the round control, the graph conditions
+  const int nblk = (int)gridDim.x;
+  int64_t carry[kNumScans + 1];
+#pragma unroll
+  for (int q = 0; q <= kNumScans; ++q) carry[q] = 0;
+  for (int base = 0; base < nblk; base += blockDim.x) {
+    const int b = base + threadIdx.x;
+    int64_t bv[kNumScans + 1];
+#pragma unroll
+    for (int q = 0; q <= kNumScans; ++q) bv[q] = b < nblk ? __ldcg(&blk[b].tot[q]) : 0;
+    int64_t bt[kNumScans + 1];
+    block_scan_excl<kNumScans + 1>(bv, bt);
+    if (b < nblk) {
+#pragma unroll
+      for (int q = 0; q <= kNumScans; ++q) blk[b].tot[q] = carry[q] + bv[q];
+    }
+#pragma unroll
+    for (int q = 0; q <= kNumScans; ++q) carry[q] += bt[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int64_t tot_active = (int64_t)acc->active;
+    const int64_t tot_fused = (int64_t)acc->fused;
 #pragma unroll
     for (int q = 0; q < kNumScans; ++q) sc.v[q][n] = carry[q];
     RoundCtl c;
@@ -376,16 +447,32 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(PlanArgs a, const SigCfg*
     c.ctr_rows = c.ctr_filt = 0ull;
     c.n_cand = 0ull;
     c.n_fused_next = 0ull;
-    const bool batched = tot_active > tot_fused;
-    c.bodies_batched = ctl->bodies_batched + (batched ? 1 : 0);
+    const bool any_batched = tot_active > tot_fused;
+    c.bodies_batched = ctl->bodies_batched + (any_batched ? 1 : 0);
     c.fused_iters = ctl->fused_iters;
     *ctl = c;
     if (a.use_cond) {
       cudaGraphSetConditional(a.cond, tot_active > 0 ? 1u : 0u);
-      cudaGraphSetConditional(a.cond_batch, batched ? 1u : 0u);
+      cudaGraphSetConditional(a.cond_batch, any_batched ? 1u : 0u);
       if (a.fuse) cudaGraphSetConditional(a.cond_fused, tot_fused > 0 ? 1u : 0u);   // handle exists
     }
+    // the round's totals are read: clear them for the next round
+    acc->tiles = acc->active = acc->fused = 0ull;
+    acc->epoch += 1;
+    dec->done2 = 0u;
   }
+  for (int i = threadIdx.x; i < 65; i += blockDim.x) acc->wsum[i] = 0ull;
+}
+
+// the blocks' offsets added to the scans and to the partial-sum offsets
+__global__ void __launch_bounds__(kPlanBlk) k_plan_offsets(int n, SigRun* run, Scans sc, const PlanBlk* __restrict__ blk) {
+  const int s = blockIdx.x * kPlanBlk + threadIdx.x;
+  if (s >= n) return;
+  const PlanBlk& b = blk[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < kNumScans; ++q) sc.v[q][s] += b.tot[q];
+  SigRun& r = run[s];
+  if (r.active && !r.fused) r.part_off += b.tot[kNumScans];
 }
 
 // ------------------------------------------------------------------ tables
@@ -1282,6 +1369,9 @@ class Engine final : public EngineBase {
     ECHK(cudaMemsetAsync(powner_, 0xFF, (size_t)(pmax_all + 1) * sizeof(unsigned long long), st_));
     ECHK(alloc(&pacc_, sizeof(PlanAcc)));
     ECHK(cudaMemsetAsync(pacc_, 0, sizeof(PlanAcc), st_));
+    ECHK(alloc(&pblk_, (size_t)((n_ + kPlanBlk - 1) / kPlanBlk) * sizeof(PlanBlk)));
+    ECHK(alloc(&pdec_, sizeof(PlanDec)));
+    ECHK(cudaMemsetAsync(pdec_, 0, sizeof(PlanDec), st_));
     ECHK(alloc(&dirs_, std::max<size_t>(dirs.size(), 1) * sizeof(int64_t)));
     ECHK(alloc(&shblk_, std::max<size_t>(shblk.size(), 1) * sizeof(int32_t)));
     ECHK(alloc(&plist_, std::max<size_t>(plist.size(), 1) * sizeof(int64_t)));
@@ -1571,15 +1661,24 @@ class Engine final : public EngineBase {
     return cudaGetLastError();
   }
 
-  // the round's plan: every signal's parameters over the grid, then the sums and scans in one block
-  cudaError_t launch_plan(const PlanArgs& pa, int64_t* launches) {
-    k_plan_signals<T><<<(n_ + 127) / 128, 128, 0, st_>>>(pa, cfg_, run_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_,
-                                                          plist_, u_, hist_, pacc_, powner_);
+  // The round's plan: every signal's parameters and the round's totals over the grid (its last
+  // block decides the mode splits), the work counts and their scans within blocks (its last
+  // block scans the blocks' totals and writes the round control), then the blocks' offsets.
+  cudaError_t launch_plan_kernels(const PlanArgs& pa, HistRec* hist, int64_t* launches) {
+    const int nblk = (n_ + kPlanBlk - 1) / kPlanBlk;
+    k_plan_signals<T><<<nblk, kPlanBlk, 0, st_>>>(pa, cfg_, run_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_, plist_, u_,
+                                                  hist, pacc_, powner_, pblk_, pdec_);
     ECHK(cudaGetLastError());
-    k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_,
-                                            plist_, u_, hist_, pacc_, powner_);
-    launches[0] += 2;
-    return cudaGetLastError();
+    k_plan_scan<T><<<nblk, kPlanBlk, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, pacc_, powner_, pblk_, pdec_);
+    ECHK(cudaGetLastError());
+    k_plan_offsets<<<nblk, kPlanBlk, 0, st_>>>(n_, run_, scans_, pblk_);
+    ECHK(cudaGetLastError());
+    if (launches) launches[0] += 3;
+    return cudaSuccess;
+  }
+
+  cudaError_t launch_plan(const PlanArgs& pa, int64_t* launches) {
+    return launch_plan_kernels(pa, hist_, launches);
   }
 
   // The batched kernels of a round, over the signals not left to the fused kernel; mark(q)
@@ -1891,8 +1990,8 @@ class Engine final : public EngineBase {
         stats->registry[i] = hh[i].live;
       }
       if (use_graph_ && !record) {
-        // bodies of the device loop (two plan launches each), those with batched work, and fused rounds
-        launches[0] += 2 * hctl_end->round;
+        // bodies of the device loop (three plan launches each), those with batched work, and fused rounds
+        launches[0] += 3 * hctl_end->round;
         for (int q = 0; q < SFFT_NKCLASS; ++q)
           launches[q] += launch_batched_[q] * hctl_end->bodies_batched + launch_fused_[q] * hctl_end->fused_iters;
       }
@@ -1941,12 +2040,7 @@ class Engine final : public EngineBase {
     pa.force = 1;
     pa.force_p = p;
     pa.force_K = K;
-    k_plan_signals<T><<<(n_ + 127) / 128, 128, 0, st_>>>(pa, cfg_, run_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_,
-                                                          plist_, u_, nullptr, pacc_, powner_);
-    ECHK(cudaGetLastError());
-    k_plan<T><<<1, kPlanThreads, 0, st_>>>(pa, cfg_, run_, ctl_, scans_, ptab_, n_ptab_, pfirst_, pfirst_n_, dirs_, plist_, u_,
-                                            nullptr, pacc_, powner_);
-    ECHK(cudaGetLastError());
+    ECHK(launch_plan_kernels(pa, nullptr, nullptr));
     return launch_tables();
   }
 
@@ -2054,7 +2148,9 @@ class Engine final : public EngineBase {
   int32_t* ptab_ = nullptr;
   int32_t* pfirst_ = nullptr;
   unsigned long long* powner_ = nullptr;   // [p_max + 1] owner election keys (owner_key), all ones at creation
-  PlanAcc* pacc_ = nullptr;                // the round's totals between k_plan_signals and k_plan
+  PlanAcc* pacc_ = nullptr;                // the round's totals between the planning kernels
+  PlanBlk* pblk_ = nullptr;                // [ceil(n / kPlanBlk)] per-block planning results
+  PlanDec* pdec_ = nullptr;                // the round's split decision and arrival counters
   int64_t pfirst_n_ = 0;
   int64_t* dirs_ = nullptr;
   int32_t* shblk_ = nullptr;   // (start, size) per shift block of every slot (block form)

@@ -9,7 +9,7 @@
 
 namespace sfft {
 
-constexpr int kPlanThreads = 384;    // one block; 148 registers a thread (512 threads would spill the 19-wide scans)
+constexpr int kPlanBlk = 128;        // signals per block of the planning kernels
 constexpr int kSingleMaxLf = 16384;   // one-block Bluestein length, FP32 (data + twiddles in shared memory)
 constexpr int kSingleMaxLd = 8192;    // same for FP64
 constexpr int kBigColElems = 4096;    // elements of one column tile of the four-step passes
@@ -117,11 +117,28 @@ struct PlanAcc {
   unsigned int epoch, pad;
 };
 
+// The round's split decision (the last block of k_plan_signals) and the arrival counters by
+// which the last block of each planning kernel knows it is last (cleared by that block).
+struct PlanDec {
+  int S, q_tail;
+  int64_t tail_from;
+  unsigned int done1, done2;
+};
+
 // exclusive scans over signals: tables, modes, DFT rows, filters, bins, four-step passes, DFT
 // rows and filters of short lengths, then sampling tiles for each set-group size 1..kMaxSetGroup
 constexpr int kNumScans = 10 + kMaxSetGroup;
 struct Scans {
   int64_t* v[kNumScans];       // each [n + 1]
+};
+
+// Per block of kPlanBlk signals: batched tiles, the partial sums tail splits q = 2..8 would add,
+// the block's offset in the queue of tiles, and its work totals (then exclusive offsets).
+struct PlanBlk {
+  unsigned long long tiles;
+  unsigned long long extra[7];
+  int64_t tile_off;
+  int64_t tot[kNumScans + 1];
 };
 enum { SC_TAB = 0, SC_MODE, SC_ROWS, SC_FILT, SC_BINS, SC_BIGA, SC_BIGB, SC_BIGC, SC_ROWS_S, SC_FILT_S, SC_SAMP0 };
 
