@@ -127,8 +127,8 @@ __global__ void k_bind_tw(int n, const SigCfg* __restrict__ cfg, const SigRun* _
 // filter spectrum and the twiddles): as many as the block has whole-warp groups of the threads a
 // row needs, and as the block's shared memory holds padded rows plus one prefetch row of L.
 template <typename C2>
-__host__ __device__ inline int dft_group_rows(int L, int nthr, int64_t smem_elems, int n_sets) {
-  const int need = fft_threads<C2>(L);
+__host__ __device__ inline int dft_group_rows(int L, int nthr, int64_t smem_elems, int n_sets, int e = 0) {
+  const int need = e == 16 ? fft_threads<C2, 16>(L) : fft_threads<C2>(L);
   int g = nthr / need;
   const int64_t rowpad = (L + L / 32 + 1) & ~1;
   while (g > 1 && (int64_t)g * rowpad + L > smem_elems) --g;
@@ -355,7 +355,8 @@ __global__ void __launch_bounds__(kPlanBlk) k_plan_scan(PlanArgs a, const SigCfg
     } else if (!r.big) {
       const bool sm = r.L <= (1 << kSmallFftLog);
       const int g = dft_group_rows<c2<T>>(r.L, sm ? a.dft_thr_s : a.dft_thr_l,
-                                         (sm ? a.dft_smem_s : a.dft_smem_l) / (int64_t)sizeof(c2<T>), c.n_sets);
+                                         (sm ? a.dft_smem_s : a.dft_smem_l) / (int64_t)sizeof(c2<T>), c.n_sets,
+                                         sm ? 0 : a.dft_e_l);
       const int64_t groups = (c.n_sets + g - 1) / g;   // row groups
       if (sm) {
         v[SC_ROWS_S] = groups;
@@ -613,8 +614,10 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_filter_one(int64_t p, int L,
   filter_spectrum<T>(p, L, chirp, tws, out, reinterpret_cast<C2*>(smem_raw), tw_hi, tw_lo);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __restrict__ cfg, SigRun* run, RoundCtl* ctl, Scans sc,
+// E: complex values a thread holds per pass (32 in float: radix-32 passes, 128 registers, one
+// 512-thread block or two 256-thread blocks per SM; 16: radix-16 passes, two 512-thread blocks)
+template <typename T, int E = fft_per_thread<c2<T>>()>
+__global__ void __launch_bounds__(kFftThreads, (E == 16 && sizeof(T) == 4) ? 2 : 1) k_dft(int n, const SigCfg* __restrict__ cfg, SigRun* run, RoundCtl* ctl, Scans sc,
                       const c2<T>* __restrict__ part, const c2<T>* __restrict__ tab,
                       const c2<T>* __restrict__ bhat, TwSrc<c2<T>> tws, c2<T>* __restrict__ Y, int small,
                       int smem_bytes) {
@@ -636,7 +639,7 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   const SigRun r = run[s];
   const int L = r.L;
   const int64_t p = r.p;
-  const int g = dft_group_rows<C2>(L, (int)blockDim.x, smem_bytes / (int)sizeof(C2), c.n_sets);
+  const int g = dft_group_rows<C2>(L, (int)blockDim.x, smem_bytes / (int)sizeof(C2), c.n_sets, E == 16 ? 16 : 0);
   const int row0 = (int)(item - scan[s]) * g;
   const int nrow = min(g, c.n_sets - row0);
   const int team = ((int)blockDim.x / g) & ~31;
@@ -674,7 +677,7 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
     }
   }
   __syncthreads();
-  fft_row<C2, false>(rb, L, tw_hi, tw_lo, lt, team, act);
+  fft_row<C2, false, E>(rb, L, tw_hi, tw_lo, lt, team, act);
   if (prefetch) {
     cp_async_wait_all();
     __syncthreads();
@@ -695,7 +698,7 @@ __global__ void __launch_bounds__(kFftThreads, 1) k_dft(int n, const SigCfg* __r
   // the inverse transform as conj(FFT(conj(.))): the product was stored conjugated, the forward
   // code runs again, and the read-out below conjugates back, so the kernel holds the code of one
   // direction only (its instruction footprint, with every radix unrolled, is what limits it)
-  fft_row<C2, false>(rb, L, tw_hi, tw_lo, lt, team, act);
+  fft_row<C2, false, E>(rb, L, tw_hi, tw_lo, lt, team, act);
   if (prefetch) {
     cp_async_wait_all();
     __syncthreads();
@@ -1455,13 +1458,18 @@ class Engine final : public EngineBase {
       const size_t kStatic = (size_t)(kTwLo + kSingleMaxLf / kTwLo) * sizeof(C2);   // k_dft's static tables
       const size_t room = (size_t)optin > kStatic + 1024 ? (size_t)optin - kStatic - 1024 : 0;
       const size_t half = (size_t)per_sm / 2 > kStatic + 2048 ? (size_t)per_sm / 2 - kStatic - 2048 : 0;
-      const size_t cap = small_threads_ <= 256 ? std::min(room, half) : room;
+      // float batches with rows up to 8192: radix-16 passes in 512-thread blocks, two per SM
+      dft_e_l_ = (sizeof(T) == 4 && small_logL_max_ <= 13 && kDftE16) ? 16 : 0;
+      dft_thr_l_ = dft_e_l_ == 16 ? std::max(32, (1 << small_logL_max_) / 16) : small_threads_;
+      const size_t cap = (small_threads_ <= 256 || dft_e_l_ == 16) ? std::min(room, half) : room;
       smem_dft_ = std::max(smem_small_, cap & ~(size_t)15);
       const int ls = std::min(small_logL_max_, kSmallFftLog);
       dft_thr_s_ = std::max(32, (1 << ls) / fft_per_thread<C2>());
       dft_smem_s_ = (size_t)((((1 << ls) + (1 << ls) / 32 + 1) & ~1) + (1 << ls)) * sizeof(C2);
     }
     ECHK(cudaFuncSetAttribute(k_dft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dft_));
+    if constexpr (sizeof(T) == 4)
+      ECHK(cudaFuncSetAttribute(k_dft<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dft_));
     if (any_big_) {
       size_t sa = 0, sb = 0;
       for (int lg = single_logL + 1; lg <= logL_big_max_; ++lg) {
@@ -1545,9 +1553,14 @@ class Engine final : public EngineBase {
     ECHK(cudaGetLastError());
     if (both) {
       ECHK(cudaEventRecord(samp_join_[0], s_short));
-      k_dft<T><<<(unsigned)rows_max_, small_threads_, smem_dft_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
-                                                                         (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 0,
-                                                                         (int)smem_dft_);
+      if (sizeof(T) == 4 && dft_e_l_ == 16)
+        k_dft<T, 16><<<(unsigned)rows_max_, dft_thr_l_, smem_dft_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
+                                                                          (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 0,
+                                                                          (int)smem_dft_);
+      else
+        k_dft<T><<<(unsigned)rows_max_, small_threads_, smem_dft_, st_>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
+                                                                           (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 0,
+                                                                           (int)smem_dft_);
       ECHK(cudaGetLastError());
       ECHK(cudaStreamWaitEvent(st_, samp_join_[0], 0));
     }
@@ -1906,7 +1919,8 @@ class Engine final : public EngineBase {
     pa.fuse = any_fuse_ ? 1 : 0;
     pa.dft_thr_s = dft_thr_s_;
     pa.dft_smem_s = (int64_t)dft_smem_s_;
-    pa.dft_thr_l = small_threads_;
+    pa.dft_thr_l = dft_thr_l_;
+    pa.dft_e_l = dft_e_l_;
     pa.dft_smem_l = (int64_t)smem_dft_;
     return pa;
   }
@@ -2121,6 +2135,8 @@ class Engine final : public EngineBase {
   size_t smem_small_ = 0, smem_bigA_ = 0, smem_bigB_ = 0, bytes_ = 0, host_stage_bytes_ = 0;
   size_t smem_dft_ = 0;   // the long-row DFT kernel's dynamic shared memory (rows + prefetch row)
   int dft_thr_s_ = 32;     // the short-row DFT launch's block size
+  int dft_thr_l_ = 256;    // the long-row DFT launch's block size
+  int dft_e_l_ = 0;        // its values per thread and pass (16, or 0: the precision's default)
   size_t dft_smem_s_ = 0;  // and dynamic shared memory
   int64_t rows_max_ = 0;
   int64_t Lmax_ = 2, p_max_ = 2, part_cap_ = 0, hash_total_ = 0, k_max_ = 0, kd_max_ = 0, reg_cap_max_ = 0;

@@ -10,6 +10,10 @@
 namespace sfft {
 
 constexpr int kPlanBlk = 128;        // signals per block of the planning kernels
+#ifndef SFFT_DFT_E16
+#define SFFT_DFT_E16 1
+#endif
+constexpr bool kDftE16 = SFFT_DFT_E16 != 0;   // long-row DFT in radix-16 passes (float, L <= 8192)
 constexpr int kSingleMaxLf = 16384;   // one-block Bluestein length, FP32 (data + twiddles in shared memory)
 constexpr int kSingleMaxLd = 8192;    // same for FP64
 constexpr int kBigColElems = 4096;    // elements of one column tile of the four-step passes
