@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kPlanBlk) k_plan_scan(PlanArgs a, const SigCfg
       const bool sm = r.L <= (1 << kSmallFftLog);
       const int g = dft_group_rows<c2<T>>(r.L, sm ? a.dft_thr_s : a.dft_thr_l,
                                          (sm ? a.dft_smem_s : a.dft_smem_l) / (int64_t)sizeof(c2<T>), c.n_sets,
-                                         sm ? 0 : a.dft_e_l);
+                                         sm ? a.dft_e_s : a.dft_e_l);
       const int64_t groups = (c.n_sets + g - 1) / g;   // row groups
       if (sm) {
         v[SC_ROWS_S] = groups;
@@ -1464,7 +1464,8 @@ class Engine final : public EngineBase {
       const size_t cap = (small_threads_ <= 256 || dft_e_l_ == 16) ? std::min(room, half) : room;
       smem_dft_ = std::max(smem_small_, cap & ~(size_t)15);
       const int ls = std::min(small_logL_max_, kSmallFftLog);
-      dft_thr_s_ = std::max(32, (1 << ls) / fft_per_thread<C2>());
+      dft_e_s_ = (sizeof(T) == 4 && kDftE16) ? 16 : 0;   // short rows in radix-16 passes as well
+      dft_thr_s_ = std::max(32, (1 << ls) / (dft_e_s_ == 16 ? 16 : fft_per_thread<C2>()));
       dft_smem_s_ = (size_t)((((1 << ls) + (1 << ls) / 32 + 1) & ~1) + (1 << ls)) * sizeof(C2);
     }
     ECHK(cudaFuncSetAttribute(k_dft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dft_));
@@ -1547,9 +1548,14 @@ class Engine final : public EngineBase {
       s_short = samp_st_[0];
       ECHK(cudaStreamWaitEvent(s_short, samp_fork_, 0));
     }
-    k_dft<T><<<(unsigned)rows_max_, dft_thr_s_, dft_smem_s_, s_short>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
-                                                                       (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 1,
-                                                                       (int)dft_smem_s_);
+    if (sizeof(T) == 4 && dft_e_s_ == 16)
+      k_dft<T, 16><<<(unsigned)rows_max_, dft_thr_s_, dft_smem_s_, s_short>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
+                                                                              (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 1,
+                                                                              (int)dft_smem_s_);
+    else
+      k_dft<T><<<(unsigned)rows_max_, dft_thr_s_, dft_smem_s_, s_short>>>(n_, cfg_, run_, ctl_, scans_, (C2*)part_,
+                                                                         (C2*)tab_, (C2*)bhat_, tws, (C2*)Y_, 1,
+                                                                         (int)dft_smem_s_);
     ECHK(cudaGetLastError());
     if (both) {
       ECHK(cudaEventRecord(samp_join_[0], s_short));
@@ -1921,6 +1927,7 @@ class Engine final : public EngineBase {
     pa.dft_smem_s = (int64_t)dft_smem_s_;
     pa.dft_thr_l = dft_thr_l_;
     pa.dft_e_l = dft_e_l_;
+    pa.dft_e_s = dft_e_s_;
     pa.dft_smem_l = (int64_t)smem_dft_;
     return pa;
   }
@@ -2137,6 +2144,7 @@ class Engine final : public EngineBase {
   int dft_thr_s_ = 32;     // the short-row DFT launch's block size
   int dft_thr_l_ = 256;    // the long-row DFT launch's block size
   int dft_e_l_ = 0;        // its values per thread and pass (16, or 0: the precision's default)
+  int dft_e_s_ = 0;        // the same for the short-row launch
   size_t dft_smem_s_ = 0;  // and dynamic shared memory
   int64_t rows_max_ = 0;
   int64_t Lmax_ = 2, p_max_ = 2, part_cap_ = 0, hash_total_ = 0, k_max_ = 0, kd_max_ = 0, reg_cap_max_ = 0;

@@ -31,7 +31,7 @@ struct PlanArgs {
   cudaGraphConditionalHandle cond_fused;   // graph condition: some signal has a fused round planned
   int dft_thr_s, dft_thr_l;                // block sizes of the short- and long-row DFT launches
   int64_t dft_smem_s, dft_smem_l;          // and their dynamic shared memory, bytes
-  int dft_e_l;                             // values per thread and pass of the long-row launch (0: default)
+  int dft_e_l, dft_e_s;                    // values per thread and pass of the long- and short-row launches (0: default)
 };
 
 __host__ __device__ inline int ceil_log2(int64_t v) {
