@@ -921,7 +921,11 @@ __global__ void __launch_bounds__(256) k_occupied(int n, const SigCfg* __restric
   const int lane = threadIdx.x & 31;
   const int64_t per = (total + gridDim.x - 1) / gridDim.x;   // bins of this block
   const int64_t lo = blockIdx.x * per, hi = min(total, lo + per);
-  if (threadIdx.x == 0) s_cnt = 0;
+  __shared__ int s_from;   // slot of the first bin of the current tile of 256 bins
+  if (threadIdx.x == 0) {
+    s_cnt = 0;
+    s_from = lo < hi ? find_slot(sc.v[SC_BINS], n, lo) : 0;
+  }
   __syncthreads();
   auto flush = [&]() {   // all threads: copy the gathered candidates out, one atomic
     __syncthreads();
@@ -936,7 +940,8 @@ __global__ void __launch_bounds__(256) k_occupied(int n, const SigCfg* __restric
   for (int64_t b0 = lo; b0 < hi; b0 += blockDim.x) {
     const int64_t e = b0 + threadIdx.x;
     const bool valid = e < hi;
-    const int s = valid ? find_slot(sc.v[SC_BINS], n, e) : -1;
+    // the block's bins are contiguous: search from the slot of the tile's first bin
+    const int s = valid ? find_slot_from(sc.v[SC_BINS], n, e, s_from) : -1;
     const int s0 = __shfl_sync(0xffffffffu, s, 0);
     const bool uni = __all_sync(0xffffffffu, !valid || s == s0);
     bool occ = false;     // set 0 above the level: a candidate for the ratio test
@@ -1014,10 +1019,13 @@ __global__ void __launch_bounds__(256) k_occupied(int n, const SigCfg* __restric
       if (slot < kCandBuf) buf[slot] = make_int2(s, (int)h);
     }
     __syncthreads();
+    // the next tile starts at or after the slot of this tile's last bin
+    if (threadIdx.x == blockDim.x - 1) s_from = valid ? s : s_from;
     if (s_cnt > kCandBuf - (int)blockDim.x) {
       // (kCandBuf >= 2 blockDim: the last tile always fitted)
       flush();
     }
+    __syncthreads();
   }
   flush();
 }

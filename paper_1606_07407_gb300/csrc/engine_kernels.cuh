@@ -154,6 +154,31 @@ __device__ __forceinline__ int find_slot(const int64_t* __restrict__ scan, int n
   return lo;
 }
 
+// find_slot for an item known to lie at or after slot `from` (scan[from] <= item): the item is
+// most often in that slot itself (one load); else a galloping search from it, then a binary one.
+__device__ __forceinline__ int find_slot_from(const int64_t* __restrict__ scan, int n, int64_t item, int from) {
+  int lo = from;
+  if (__ldg(scan + lo + 1) > item) return lo;
+  int hi = lo + 1, step = 1;   // scan[hi] <= item
+  for (;;) {
+    lo = hi;
+    const int nxt = min(lo + step, n);
+    if (nxt == n || __ldg(scan + nxt) > item) {
+      hi = nxt;
+      break;
+    }
+    hi = nxt;
+    step *= 2;
+  }
+  // scan[lo] <= item < scan[hi] (scan[n] is the total, above every item)
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(scan + mid) <= item) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // Exclusive scan of V values per thread over the block (a multiple of 32 threads, at most 1024).
 template <int V>
 __device__ __forceinline__ void block_scan_excl(int64_t (&v)[V], int64_t (&tot)[V]) {
