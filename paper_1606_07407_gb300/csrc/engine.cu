@@ -1,9 +1,11 @@
 // Kernels and host driver of the batched round engine (Algorithm 2 for many
 // signals at once).  One round, for every active signal s of the batch:
 //
-//   k_plan      (one block)  k* = max(k - |R|, 1), p = i-th prime >= c k* (Alg. 2), direction
-//                            u of the round reduced mod p, work geometry, exclusive scans of the
-//                            per-signal work counts; ends the device loop when no signal is left
+//   k_plan_signals, k_plan_scan, k_plan_offsets (grid)
+//                            k* = max(k - |R|, 1), p = i-th prime >= c k* (Alg. 2), direction
+//                            u of the round reduced mod p, work geometry, mode splits, exclusive
+//                            scans of the per-signal work counts; ends the device loop when no
+//                            signal is left
 //   k_tables                 W[m] = e^{2 pi i m / p} and chirp[x] = e^{-pi i x^2 / p}
 //   k_sample    (persistent) y_n[x] = (f - g)(x u / p + e_n / N) for all n (Eq. 41), the modes'
 //                            projection alpha = (w . u) mod p fused into the staging
@@ -13,7 +15,7 @@
 //                            registry with pruning, empty-bin flag for the stop rule
 //
 // The host only enqueues rounds (or launches one CUDA graph whose while-loop the
-// plan kernel ends), and reads results back once.
+// planning kernels end), and reads results back once.
 #include <algorithm>
 #include <cstring>
 #include <memory>
@@ -118,11 +120,12 @@ __global__ void k_bind_tw(int n, const SigCfg* __restrict__ cfg, const SigRun* _
 
 // ------------------------------------------------------------------ plan
 
-// Plans the round of every signal (plan_signal; a signal whose next round the fused kernel
-// has planned keeps it) and gathers the round's totals over the grid (k_plan_signals), then,
-// in one block, the mode splits, the work counts of the batched kernels and their exclusive
-// scans over the signals (k_plan).  Sets the graph conditions: some signal active (the round
-// loop), some batched work, some fused round planned.
+// Planning: every signal's round (plan_signal; a signal whose next round the fused kernel has
+// planned keeps it), the round's totals and the mode splits (k_plan_signals and its last
+// block), the work counts of the batched kernels and their exclusive scans over the signals
+// (k_plan_scan within blocks, its last block across them; k_plan_offsets).  The last block of
+// k_plan_scan sets the graph conditions: some signal active (the round loop), some batched
+// work, some fused round planned.
 // Rows of one signal that one block of the DFT takes together (they share p, the chirp, the
 // filter spectrum and the twiddles): as many as the block has whole-warp groups of the threads a
 // row needs, and as the block's shared memory holds padded rows plus one prefetch row of L.
@@ -236,8 +239,7 @@ __device__ void plan_decide(const PlanArgs& a, const SigCfg* __restrict__ cfg, c
 
 // The round's parameters of every signal not already planned by the fused kernel (stop rule,
 // prime, direction mod p, work geometry: plan_signal), one thread per signal over the whole
-// grid; k_plan then sums and scans the work.
-// The same threads then add the round's totals into acc (active and fused signals, batched
+// grid.  The same threads then add the round's totals into acc (active and fused signals, batched
 // tiles, and the histogram of n_sets p by mode chunks from which the mode splits are sized),
 // elect each shared prime's owner, and give their block's batched tiles and, for each tail split
 // q = 2..8, the partial sums those splits would add (blk).  The last block to finish (the
@@ -1320,7 +1322,7 @@ class Engine final : public EngineBase {
     cfg_host_ = cfg;
     Lmax_ = std::max<int64_t>(next_pow2(2 * pmax_all - 1), 32);
     p_max_ = pmax_all;
-    // a signal takes at most 64 mode splits (k_plan's S), so 64 part_min holds any split choice;
+    // a signal takes at most 64 mode splits (the planner's S), so 64 part_min holds any split choice;
     // small engines (one short signal) stay small, large batches stop at 128 MiB
     part_cap_ = std::max<int64_t>(part_min, std::min<int64_t>((int64_t)(128ll << 20) / (int64_t)sizeof(C2),
                                                               64 * part_min));

@@ -113,7 +113,8 @@ struct RoundCtl {
 };
 
 // The round's totals, gathered over the grid while the signals are planned (k_plan_signals)
-// and read by k_plan, which clears them for the next round.  epoch numbers the plan launches of
+// and read by the last blocks of the planning kernels; the last block of k_plan_scan clears
+// them for the next round.  epoch numbers the plan launches of
 // the engine (never cleared): the owner election of round e keys powner[p] by e.
 struct PlanAcc {
   unsigned long long tiles, active, fused;   // batched tiles; active and fused signals
