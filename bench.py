@@ -2,9 +2,10 @@
 """Benchmark of the sparse-FFT hot path: modes recovered per second at exact frequency recovery.
 
 Default workload (mix4096): 4096 independent signals with k ~ U{8..512}, d ~ U{2..8},
-N = 2^U{10..20}, r ~ U[1, 10], noiseless, each with its own plan (partial-unwrap blocks by the
-default rule, prime schedule from the tuned table), float sampling and DFT with the phase ratio
-in double above N = 2^14.  One step recovers all of them in one batched execute whose rounds run
+N = 2^U{10..20}, r ~ U[1, 10], noiseless, each with its own plan (prime factor, prime floor,
+fused cut-over and unwrapping-block rule from the tuned table of its (N, k) class), float
+sampling and DFT with the phase ratio, read-out and coefficient in double above N = 2^14 (the
+AUTO policy; --precision selects the others, among them df64: double-float sampling).  One step recovers all of them in one batched execute whose rounds run
 as a CUDA graph with a device-ended while loop (the batched form); the plain form, one execute
 per signal, is timed beside it on the same signals.  A step counts only if every recovered
 frequency set equals the planted one.
