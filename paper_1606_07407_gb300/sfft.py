@@ -203,9 +203,13 @@ def assign_many(signals, freqs: torch.Tensor, coeffs: torch.Tensor, ks, stream=N
     n = len(signals)
     if stream is None:
         stream = torch.cuda.current_stream()
-    karr = (C.c_int64 * n)(*[int(k) for k in ks])
-    harr = (C.c_void_p * n)(*[s._h.value for s in signals])
-    _check(load().sfft_signal_assign_many(n, harr, karr, _ptr(freqs), _ptr(coeffs), C.c_void_p(stream.cuda_stream)),
+    karr = np.ascontiguousarray(ks, dtype=np.int64)
+    if karr.shape != (n,):
+        raise ValueError("ks must have one entry per signal")
+    harr = np.fromiter((s._h.value for s in signals), dtype=np.uint64, count=n)
+    _check(load().sfft_signal_assign_many(n, harr.ctypes.data_as(C.POINTER(C.c_void_p)),
+                                          karr.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(freqs), _ptr(coeffs),
+                                          C.c_void_p(stream.cuda_stream)),
            "sfft_signal_assign_many")
     for s, k in zip(signals, ks):
         s.k = int(k)
