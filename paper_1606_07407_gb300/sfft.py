@@ -201,11 +201,11 @@ def assign_many(signals, freqs: torch.Tensor, coeffs: torch.Tensor, ks, stream=N
     freqs (int32 [sum ks, d]) and entries of coeffs (complex128 [sum ks]) following those of the
     signals before it.  Enqueued on the stream (default: torch's current one), not waited for."""
     n = len(signals)
-    if stream is None:
-        stream = torch.cuda.current_stream()
     karr = np.ascontiguousarray(ks, dtype=np.int64)
     if karr.shape != (n,):
         raise ValueError("ks must have one entry per signal")
+    if stream is None:
+        stream = torch.cuda.current_stream()
     harr = np.fromiter((s._h.value for s in signals), dtype=np.uint64, count=n)
     _check(load().sfft_signal_assign_many(n, harr.ctypes.data_as(C.POINTER(C.c_void_p)),
                                           karr.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(freqs), _ptr(coeffs),

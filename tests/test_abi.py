@@ -174,3 +174,56 @@ def test_sampling_wrappers_reject_bad_shapes_before_any_device_call(monkeypatch)
         plan.sample(11, u, torch.zeros((10, 2), dtype=torch.int32), a)
     with pytest.raises(ValueError):
         plan.sample(11, u, w, a[:3])
+
+
+def test_assign_many_rejects_mismatched_counts_before_any_device_call(monkeypatch):
+    # one mode count per handle: a short or long ks list would make the library read past an array
+    torch = pytest.importorskip("torch")
+    from paper_1606_07407_gb300 import sfft as S
+
+    def no_device(*_a, **_k):
+        raise AssertionError("reached the library")
+
+    monkeypatch.setattr(S, "load", no_device)
+
+    class Handle:
+        def __init__(self):
+            self._h = ctypes.c_void_p(None)
+            self.k = 0
+
+    sigs = [Handle(), Handle()]
+    w = torch.zeros((7, 2), dtype=torch.int32)
+    a = torch.zeros((7,), dtype=torch.complex128)
+    with pytest.raises(ValueError):
+        S.assign_many(sigs, w, a, [3])
+    with pytest.raises(ValueError):
+        S.assign_many(sigs, w, a, [3, 2, 2])
+
+
+def test_precision_policy_range_without_gpu(lib):
+    # the policies are AUTO .. DF64 (0 .. 6); anything else is refused before any CUDA call
+    from paper_1606_07407_gb300.sfft import PREC, _Opts
+    assert PREC["df64"] == 6 and PREC["fp32_then_fp64"] == 5 and PREC["fp32_bf16dft"] == 4
+    h = ctypes.c_void_p()
+    for prec in (-1, 7):
+        bad = _Opts(prec, 0, 0.0, 0.0, 0.0, 0.0, 0, 0, 0, 0, 0, 0)
+        assert lib.sfft_plan_create(2, ctypes.c_int64(16), ctypes.c_int64(4), None, None, ctypes.byref(bad), None,
+                                    ctypes.byref(h)) == 1
+
+
+def test_double_float_cost_model_of_the_bench():
+    # (4 products x 12 operations per set, plus 32 for E shared by the group's sets) / 2 samples
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(os.path.dirname(os.path.dirname(
+        os.path.abspath(__file__))), "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert abs(bench.df64_ops_per_term(20) - (48 + 32 / 7) / 2) < 1e-12    # 21 sets: 3 groups of 7
+    assert abs(bench.df64_ops_per_term(4) - (48 + 32 / 5) / 2) < 1e-12     # 5 sets: one group
+    assert abs(bench.df64_ops_per_term(8) - (48 + 32 / 5) / 2) < 1e-12     # 9 sets: 2 groups of 5
+
+
+def test_precision_study_rejects_unknown_arms_before_any_device_work():
+    from paper_1606_07407_gb300 import precision_study as P
+    with pytest.raises(SystemExit):
+        P.main(["--arms", "fp64,bogus"])
