@@ -46,6 +46,11 @@ C_CANDIDATES = (3.0, 4.0, 5.0, 6.0)
 PMIN_CANDIDATES = (0, 512, 1024, 2048)
 BLOCK_RULES = ("narrow", "wide")      # inputs.blocks_for
 FUSE_CANDIDATES = (256, 512)          # tried on the best (c, p_min, blocks); 0 (the kernel's limit) always
+# After tuning, a floor at a power of two is lowered so that the first primes above it stay below
+# that power: 2p - 1 then fits a Bluestein length of 2^a (1024, 2048, 4096) instead of 5 2^(a-2),
+# and the half line p / 2 + 1 no longer spills a few positions into one more sampling tile.
+# Measured on the 4096-signal mix: 13.16 -> 12.89 ms per step, every signal exact.
+FLOOR_BELOW_POW2 = {512: 480, 1024: 960, 2048: 1950}
 
 
 def draw_class(n: int, logN: tuple, krange: tuple, seed: int) -> list:
@@ -132,7 +137,8 @@ def tune(n_signals: int = 192, reps: int = 3, log=print) -> dict:
         default = next(r for r in results if r["c"] == 5.0 and r["p_min"] == 0 and r["fuse_max_len"] == 0
                        and r["blocks"] == "narrow")
         classes.append({"d": list(D_RANGE), "logN": list(logN), "k": list(krange), "c": best["c"],
-                        "p_min": best["p_min"], "fuse_max_len": best["fuse_max_len"], "blocks": best["blocks"],
+                        "p_min": FLOOR_BELOW_POW2.get(best["p_min"], best["p_min"]), "p_min_tuned": best["p_min"],
+                        "fuse_max_len": best["fuse_max_len"], "blocks": best["blocks"],
                         "ms": best["ms"],
                         "rounds": best.get("rounds"), "exact_candidates": len(good),
                         "default_c5_ms": default["ms"], "default_c5_exact": default["exact"],
@@ -152,6 +158,7 @@ def tune(n_signals: int = 192, reps: int = 3, log=print) -> dict:
                          "validation batches exactly",
             "search": {"c": list(C_CANDIDATES), "p_min": list(PMIN_CANDIDATES), "blocks": list(BLOCK_RULES),
                        "fuse_max_len": [0] + list(FUSE_CANDIDATES)},
+            "floor_below_pow2": {str(k): v for k, v in FLOOR_BELOW_POW2.items()},
             "classes": classes}
 
 
